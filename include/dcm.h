@@ -1,0 +1,185 @@
+/*
+ * dcm.h -- C ABI of the GB300 (sm_103a) dynamic cutoff method library
+ * (libdcm.so).
+ *
+ * Method: Springer, "A Scalable, Linear-Time Dynamic Cutoff Algorithm for
+ * Molecular Simulations of Interfacial Systems" (arxiv 1502.03234).  Each
+ * Lennard-Jones particle i carries its own cutoff r_c[i], set from its
+ * distance to the liquid/vapor interface (Eq. 7-8); the interface is found
+ * on a voxel grid (Section 4) and the forces are summed over a full
+ * neighbourhood without Newton's third law (Algorithm 3.2).
+ *
+ * Conventions for every entry point:
+ *   - Return value: DCM_OK (0) or a DCM_ERR_* code; no exception or signal
+ *     crosses the ABI.  dcm_last_error() returns a message for the calling
+ *     thread's most recent failure.
+ *   - Positions/velocities/forces cross the ABI as AoS double[3*N]
+ *     (x0,y0,z0,x1,...), in the caller's particle order ("id order").
+ *     Arrays passed in are copied, never retained.
+ *   - mem = DCM_HOST: host pointers; the call returns when the copy is done.
+ *     mem = DCM_DEVICE: device pointers (e.g. a torch CUDA tensor's
+ *     data_ptr); the copy is enqueued on the handle's stream.
+ *   - Work is enqueued on the CUDA stream given to dcm_create (the library
+ *     makes its own non-blocking stream when given NULL).  Only dcm_get_*,
+ *     dcm_energy_virial, dcm_sync and the DCM_HOST copies block the host.
+ *   - The library owns all device memory it allocates; everything is
+ *     allocated by dcm_create, nothing inside dcm_step.
+ *   - Units are reduced LJ units unless the parameters say otherwise.
+ *   - The box is orthorhombic with origin 0, periodic in x, y and z; every
+ *     cutoff must stay below half the shortest edge minus one link cell
+ *     (DCM_ERR_BOX_TOO_SMALL otherwise).
+ *   - One handle is used by one host thread at a time.
+ */
+#ifndef DCM_H
+#define DCM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DCM_ABI_VERSION 1
+
+enum dcm_status {
+    DCM_OK = 0,
+    DCM_ERR_ARG = 1,            /* invalid argument or parameter */
+    DCM_ERR_OOM = 2,            /* device allocation failed */
+    DCM_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+    DCM_ERR_BOX_TOO_SMALL = 4,  /* rc_max + link cell >= half the shortest edge */
+    DCM_ERR_NOT_CONVERGED = 5,  /* CFSM or K-means hit its iteration cap */
+    DCM_ERR_DEVICE_CHECK = 6,   /* a device-side check failed (non-finite
+                                   position, particle moved more than a box
+                                   edge in one step, bounded wait expired) */
+    DCM_ERR_CANCELLED = 7,      /* work stopped by a cancel request */
+    DCM_ERR_STATE = 8           /* call out of order (e.g. no state set) */
+};
+
+enum { DCM_FP64 = 0,   /* FP64 pair distances, forces and accumulation */
+       DCM_MIXED = 1   /* FP32 pair distances and forces, extended-precision
+                          (2 x FP32) accumulation, FP64 state and reductions */
+};
+enum { DCM_HOST = 0, DCM_DEVICE = 1 };
+
+#define DCM_MAX_CLASSES 8
+
+typedef struct {
+    double lx, ly, lz;
+} dcm_box;
+
+typedef struct {
+    /* Eq. 7-8: cutoff function; rc_min == rc_max is the static cutoff */
+    double rc_min, rc_max, alpha;          /* alpha < 0; thesis uses -0.5 */
+    /* Eq. 1-2, Eq. 4 */
+    double dt, mass, eps, sigma;
+    /* Eq. 10: target voxel edge b; N_x = max(3, floor(L_x / b)) */
+    double voxel;
+    /* binomial smoothing order (even, 0..16; 8 -> sigma = sqrt(2) voxels) */
+    int32_t smooth_order;
+    /* interface detection every detect_every steps (thesis: every other
+       step); 0 = never re-detect inside dcm_step */
+    int32_t detect_every;
+    int32_t kmeans_max_iter;               /* Eq. 14 Lloyd passes, <= 0: 100 */
+    int32_t cfsm_iter_max;                 /* Algorithm 4.3, <= 0: 4*max(N) */
+    double cfsm_eps;                       /* Algorithm 4.3 stop; 0: exact */
+    int32_t precision;                     /* DCM_FP64 or DCM_MIXED */
+    int32_t n_classes;                     /* cutoff classes, 2..8 */
+    double cell_min;                       /* link-cell edge target; <= 0: auto */
+    int32_t reserved[8];
+} dcm_params;
+
+/* Launch shape of the force kernel per cutoff class (the autotuner's
+ * output; see dcm_set_tuning). */
+typedef struct {
+    int32_t lanes[DCM_MAX_CLASSES];        /* lanes per particle: 1..32, pow2 */
+    int32_t block;                         /* threads per block: 64..1024 */
+    int32_t reserved[7];
+} dcm_tuning;
+
+typedef struct {
+    int64_t step;                          /* global step counter */
+    int64_t pairs;                         /* in-cutoff pairs, last force call */
+    int32_t kmeans_iters;                  /* last detection */
+    int32_t cfsm_iters;                    /* last detection */
+    int32_t class_count[DCM_MAX_CLASSES];  /* particles per class */
+    int32_t grid[3];                       /* voxel grid N_x, N_y, N_z */
+    int32_t cells[3];                      /* link-cell grid */
+    double c_liquid, c_vapor;              /* Eq. 14 cluster centres */
+    int64_t guard_rechecks;                /* MIXED: FP64 re-decided pairs */
+    int64_t reserved[6];
+} dcm_stats;
+
+typedef struct dcm_handle dcm_handle;
+
+/* Fills the thesis defaults: rc 3/6, alpha -0.5, dt 0.005, m = eps = sigma
+ * = 1, voxel 1, smoothing order 8, detect_every 2, FP64, 4 classes. */
+void dcm_default_params(dcm_params *p);
+
+/* Creates a single-system handle for n particles in box.  stream is a
+ * cudaStream_t (NULL: the library creates one).  Allocates every device
+ * buffer of the system.  Errors: DCM_ERR_ARG (n < 1, bad parameters),
+ * DCM_ERR_BOX_TOO_SMALL, DCM_ERR_OOM, DCM_ERR_CUDA. */
+int dcm_create(const dcm_box *box, int64_t n, const dcm_params *p,
+               void *stream, dcm_handle **out);
+int dcm_destroy(dcm_handle *h);
+
+/* Copies positions (wrapped into the box) and velocities (NULL: zero) in.
+ * Resets the step counter and marks cutoffs and forces stale. */
+int dcm_set_state(dcm_handle *h, const double *x, const double *v, int mem);
+/* Copies positions, velocities and forces out; each pointer nullable. */
+int dcm_get_state(dcm_handle *h, double *x, double *v, double *f, int mem);
+int dcm_set_step(dcm_handle *h, int64_t step);
+
+/* Supplies per-particle cutoffs directly (double[N], id order), bypassing
+ * interface detection until the next dcm_detect_interface or detection
+ * step.  Each must lie in [rc_min, rc_max]. */
+int dcm_set_cutoffs(dcm_handle *h, const double *rc, int mem);
+
+/* Section 4 + Algorithm 3.1 + Eq. 7: density image (Eq. 9), binomial
+ * smoothing, two-class K-means labels (Eq. 11-14), CFSM distance
+ * (Algorithm 4.3, band r_c,max + h), trilinear particle distance, cutoff
+ * and class of every particle.  Enqueued; DCM_ERR_NOT_CONVERGED is
+ * reported by the next dcm_sync if CFSM hit its cap. */
+int dcm_detect_interface(dcm_handle *h);
+
+/* Link-cell counting sort + Algorithm 3.2 with the cutoffs in use (detects
+ * first if no cutoffs exist yet).  Enqueued. */
+int dcm_compute_forces(dcm_handle *h);
+
+/* nsteps of velocity Verlet (Eq. 1-2) with detection every detect_every
+ * steps and r_c held in between; the loop runs from a CUDA graph with no
+ * host round trip.  Enqueued. */
+int dcm_step(dcm_handle *h, int64_t nsteps);
+
+/* PE = 1/2 sum_i sum_{j: r_ij < r_c[i]} V(r_ij), KE = 1/2 m sum v^2,
+ * w = 1/2 sum_i sum_j (r_ij)_a (F_i<-j)_b for ab = xx yy zz xy xz yz, at the
+ * current positions and cutoffs (deterministic FP64 reduction).  Blocks. */
+int dcm_energy_virial(dcm_handle *h, double *pe, double *ke, double w[6]);
+
+/* Diagnostics (host pointers, blocking, each nullable). */
+int dcm_get_grid(dcm_handle *h, int32_t dims[3], int32_t *counts,
+                 double *smoothed, uint8_t *labels, double *dist);
+int dcm_get_cutoffs(dcm_handle *h, double *d, double *rc, uint8_t *cls);
+int dcm_get_cells(dcm_handle *h, int32_t nc[3], int32_t *cell_start,
+                  int32_t *sorted_id);
+int dcm_get_pair_counts(dcm_handle *h, int32_t *npair);
+int dcm_get_stats(dcm_handle *h, dcm_stats *s);
+
+/* Force-kernel launch shape per cutoff class (see dcm_tuning). */
+int dcm_set_tuning(dcm_handle *h, const dcm_tuning *t);
+int dcm_get_tuning(dcm_handle *h, dcm_tuning *t);
+
+/* Waits for the handle's stream; returns the sticky device error, if any. */
+int dcm_sync(dcm_handle *h);
+/* Total device bytes the handle holds. */
+int64_t dcm_device_bytes(const dcm_handle *h);
+/* Device bytes dcm_create would allocate for this system. */
+int64_t dcm_estimate_bytes(const dcm_box *box, int64_t n, const dcm_params *p);
+
+const char *dcm_last_error(void);
+int dcm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DCM_H */
