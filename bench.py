@@ -1,0 +1,354 @@
+#!/usr/bin/env python3
+"""Benchmark of the DCM hot path: atom-steps/s of the full DCM step
+(velocity Verlet + interface detection every other step + link-cell sort +
+dynamic-cutoff LJ forces) on a synthetic LJ liquid/vapor slab.
+
+Workload (the N = 262,144 slab): density-0.8 jittered-FCC liquid across the
+centre of an L x L x 4L periodic box, vapor elsewhere, T* = 0.7,
+r_c,min = 3, r_c,max = 6 (exponential Eq. 7, alpha = -0.5), 1-sigma voxels,
+detection every 2 steps, dt = 0.005.  The timed arm is the mixed-precision
+path (FP32 pair / FP64 state); the plain FP64 GPU path is measured on the
+same system and reported beside it.
+
+One JSON line on stdout (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle instead, on the host cores, on a bounded sample of the workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "atom-steps/s of DCM step (forces+interface) vs plain FP64 GPU path; p50/p99 latency"
+UNIT = "atom-steps/s"
+N_DEFAULT = 262144
+FP32_LANES_PER_SM = 128          # Blackwell SM: 4 sub-partitions x 32 FP32 lanes
+FLOPS_PER_PAIR = 24              # 8 (distance test) + 16 (LJ force), per in-cutoff pair
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="dcm", choices=["dcm", "reference"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    return ap.parse_args()
+
+
+def workload_config(n, precision):
+    return {"workload": f"LJ liquid/vapor slab N={n}, L x L x 4L periodic, rho_l=0.8, T*=0.7, "
+                        f"DCM r_c 3/6 (Eq. 7, alpha=-0.5), 1-sigma voxels, detection every 2 steps",
+            "n": n, "rc_min": 3.0, "rc_max": 6.0, "detect_every": 2, "dt": 0.005,
+            "precision": precision,
+            "l2": "flushed (256 MiB write) before every timed step; each step timed alone"}
+
+
+# ---- clocks sampled during the timed region ------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.idx), "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+        if self.proc is None or not os.path.exists(self.path):
+            out["reasons"] = ["nvidia-smi unavailable"]
+            return out
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [t.strip() for t in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if sm:
+            out["sm_mhz"] = statistics.median(sm)
+            out["sm_max_mhz"] = max(smax)
+            out["samples"] = len(sm)
+        out["reasons"] = sorted(reasons)
+        return out
+
+
+# ---- reference arm: the FP64 CPU oracle ----------------------------------------------
+def oracle_rate(n_sample: int, target_s: float, max_steps: int = 50, seed: int = 1):
+    """atom-steps/s of the FP64 oracle (all host cores) on an n_sample slab
+    with the same densities, cutoffs and cadence."""
+    import oracle
+    from paper_1502_03234_gb300 import slabgen
+
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    s = slabgen.make_slab(n_sample, seed=seed)
+    p = oracle.RunParams(det=oracle.DetectParams(rc_min=3.0, rc_max=6.0, voxel=1.0),
+                         dt=0.005, cell_min=1.5, detect_every=2)
+    t0 = time.perf_counter()
+    oracle.run(s.x, s.v, s.box, p, 2)                  # setup + 2 steps: calibration
+    t_cal = time.perf_counter() - t0
+    steps = int(max(2, min(max_steps, 2 * round(target_s / max(t_cal, 1e-3)))))
+    t0 = time.perf_counter()
+    oracle.run(s.x, s.v, s.box, p, steps)
+    dt = time.perf_counter() - t0
+    return n_sample * steps / dt, cores, steps, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1502_03234_gb300 import slabgen
+
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    n_sample = 16384
+    s = slabgen.make_slab(n_sample, seed=1)
+    p = oracle.RunParams(det=oracle.DetectParams(rc_min=3.0, rc_max=6.0, voxel=1.0),
+                         dt=0.005, cell_min=1.5, detect_every=2)
+    x, v = s.x, s.v
+    step0 = 0
+    for _ in range(args.warmup):
+        x, v, *_ = oracle.run(x, v, s.box, p, 1, step0=step0)
+        step0 += 1
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        x, v, *_ = oracle.run(x, v, s.box, p, 1, step0=step0)
+        times.append(time.perf_counter() - t0)
+        step0 += 1
+    total = sum(times)
+    value = n_sample * args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args.n, "fp64 CPU oracle"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"N={n_sample} slab of the same shape; each step = setup "
+                                       f"(detect + force) + 1 velocity-Verlet step of the oracle"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---- the GPU arm ---------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+
+        dist_mod.init_process_group("nccl")
+        dist = dist_mod
+    # build once per node, then import
+    if local == 0:
+        import __graft_entry__
+
+        __graft_entry__.build()
+    if dist is not None:
+        dist.barrier()
+    from paper_1502_03234_gb300 import dcm, slabgen
+
+    n = args.n
+    prec = dcm.DCM_MIXED if args.precision == "mixed" else dcm.DCM_FP64
+    slab = slabgen.make_slab(n, seed=1 + rank)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def make_system(precision):
+        sy = dcm.System(slab.box, n, precision=precision, stream=stream.cuda_stream)
+        sy.set_state(slab.x, slab.v)
+        sy.compute_forces()
+        sy.set_timing(True)
+        return sy
+
+    def timed_steps(sy, k, warm):
+        """per-step device times (ms), L2 flushed before each step"""
+        for _ in range(warm):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            sy.step(1)
+        sy.sync()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(k)]
+        force_ms, phase_sum = [], {}
+        for q in range(k):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                ev[q][0].record(stream)
+            sy.step(1)
+            with torch.cuda.stream(stream):
+                ev[q][1].record(stream)
+            ph = sy.phase_times()                       # waits for this step
+            force_ms.append(ph["force"])
+            for key, val in ph.items():
+                phase_sum[key] = phase_sum.get(key, 0.0) + val
+        sy.sync()
+        return [a.elapsed_time(b) for a, b in ev], force_ms, phase_sum
+
+    sy = make_system(prec)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        step_ms, force_ms, phase_sum = timed_steps(sy, args.steps, args.warmup)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    total_ms = sum(step_ms)
+    st = sy.stats()
+    pairs = st.pairs
+    kernels = (st.kernels_plain * (args.steps - args.steps // 2) + st.kernels_detect * (args.steps // 2))
+    x_end, _, _ = sy.get_state()
+    if not np.all(np.isfinite(x_end)):
+        raise RuntimeError("non-finite positions after the timed run")
+    sy.sync()
+
+    # max over ranks, whole-job throughput
+    t_max = total_ms
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * n * args.steps / (t_max * 1e-3)
+
+    # roofline of the dominant kernel (the DCM force kernel, FP32 pipe)
+    clocks = clk.summary()
+    f_avg_ms = sum(force_ms) / len(force_ms)
+    achieved = FLOPS_PER_PAIR * pairs / (f_avg_ms * 1e-3) / 1e12
+    sm_mhz = clocks.get("sm_mhz") or 1477.0
+    peak = 152 * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "k_force (mixed)" if prec == dcm.DCM_MIXED else "k_force (fp64)",
+                "peak_note": "FP32 FMA peak derived from 152 SMs x 128 lanes x 2 flops x the "
+                             "median SM clock sampled during the timed region",
+                "pairs_per_launch": pairs, "force_ms_avg": f_avg_ms}
+
+    # the plain FP64 GPU path on the same system (the comparison the metric names)
+    fp64_info = None
+    if not args.no_fp64_compare and prec == dcm.DCM_MIXED and rank == 0:
+        sy64 = make_system(dcm.DCM_FP64)
+        k64 = max(4, min(20, args.steps // 10) // 2 * 2)
+        s64, f64, _ = timed_steps(sy64, k64, 2)
+        fp64_info = {"value": n * k64 / (sum(s64) * 1e-3), "unit": UNIT, "steps": k64,
+                     "ms_per_step": sum(s64) / k64, "force_ms_avg": sum(f64) / len(f64)}
+        sy64.close()
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if rank == 0 and args.e2e_steps > 0:
+        sy.set_timing(False)
+        xh = torch.from_numpy(np.ascontiguousarray(slab.x)).pin_memory()
+        vh = torch.from_numpy(np.ascontiguousarray(slab.v)).pin_memory()
+        xo = torch.empty_like(xh).pin_memory()
+        vo = torch.empty_like(vh).pin_memory()
+        lib = dcm.lib()
+        px, pv = xh.data_ptr(), vh.data_ptr()
+        pxo, pvo = xo.data_ptr(), vo.data_ptr()
+        import ctypes as C
+
+        sy.sync()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            dcm.check(lib.dcm_set_state(sy.h, C.c_void_p(px), C.c_void_p(pv), dcm.DCM_HOST))
+            dcm.check(lib.dcm_step(sy.h, 1))
+            dcm.check(lib.dcm_get_state(sy.h, C.c_void_p(pxo), C.c_void_p(pvo), None, dcm.DCM_HOST))
+            px, pxo = pxo, px
+            pv, pvo = pvo, pv
+        sy.sync()
+        dt = time.perf_counter() - t0
+        e2e = {"value": n * args.e2e_steps / dt, "unit": UNIT,
+               "h2d_bytes_per_step": 2 * 24 * n, "d2h_bytes_per_step": 2 * 24 * n,
+               "steps": args.e2e_steps,
+               "note": "per step: dcm_set_state (x, v from pinned host) + dcm_step(1) + "
+                       "dcm_get_state (x, v to pinned host); set_state makes the step re-detect "
+                       "and re-force at its start"}
+    sy.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, cores, csteps, cdt = oracle_rate(16384, target_s=12.0)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"N=16384 slab of the same shape, {csteps} oracle steps "
+                         f"({cdt:.1f} s) after a 2-step calibration"}
+
+    if rank == 0:
+        sms = sorted(step_ms)
+        p50 = sms[len(sms) // 2]
+        p99 = sms[min(len(sms) - 1, int(math.ceil(0.99 * len(sms))) - 1)]
+        cfg = workload_config(n, args.precision)
+        cfg["phase_ms_avg"] = {k: v / args.steps for k, v in phase_sum.items()}
+        cfg["fp64_gpu_path"] = fp64_info
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32-pair/f64-state" if prec == dcm.DCM_MIXED else "f64",
+                "data": "synthetic", "config": cfg,
+                "latency_ms": {"p50": p50, "p99": p99, "unit": "ms per step"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(kernels), "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

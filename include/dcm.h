@@ -106,8 +106,14 @@ typedef struct {
     int32_t cells[3];                      /* link-cell grid */
     double c_liquid, c_vapor;              /* Eq. 14 cluster centres */
     int64_t guard_rechecks;                /* MIXED: FP64 re-decided pairs */
-    int64_t reserved[6];
+    int32_t kernels_plain;                 /* kernels one step launches */
+    int32_t kernels_detect;                /* ... in a step with detection */
+    int64_t reserved[5];
 } dcm_stats;
+
+/* Phases of one step, in order, for dcm_get_phase_times. */
+enum { DCM_PHASE_KICK_DRIFT = 0, DCM_PHASE_DETECT = 1, DCM_PHASE_BIN = 2,
+       DCM_PHASE_FORCE = 3, DCM_PHASE_KICK = 4, DCM_NUM_PHASES = 5 };
 
 typedef struct dcm_handle dcm_handle;
 
@@ -168,6 +174,13 @@ int dcm_get_stats(dcm_handle *h, dcm_stats *s);
 /* Force-kernel launch shape per cutoff class (see dcm_tuning). */
 int dcm_set_tuning(dcm_handle *h, const dcm_tuning *t);
 int dcm_get_tuning(dcm_handle *h, dcm_tuning *t);
+
+/* Phase timing: with on != 0 the step graphs record a CUDA event between
+ * phases (a few microseconds of overhead); dcm_get_phase_times waits for
+ * the stream and returns the device milliseconds of each phase of the
+ * most recent step (DCM_PHASE_*; 0 for a phase the step skipped). */
+int dcm_set_timing(dcm_handle *h, int on);
+int dcm_get_phase_times(dcm_handle *h, float ms[DCM_NUM_PHASES]);
 
 /* Waits for the handle's stream; returns the sticky device error, if any. */
 int dcm_sync(dcm_handle *h);

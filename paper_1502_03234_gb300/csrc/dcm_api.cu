@@ -1,0 +1,681 @@
+// dcm_api.cu -- the C ABI of libdcm (see include/dcm.h): handle life cycle,
+// geometry, device allocation, state transfer, the CUDA-graph step loop and
+// the diagnostic read-backs.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "dcm_device.cuh"
+
+static thread_local char g_errmsg[512] = "";
+
+namespace dcm {
+
+int fail(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_errmsg, sizeof(g_errmsg), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int fail_cuda(cudaError_t e, const char *what, const char *file, int line)
+{
+    (void)cudaGetLastError();
+    int code = (e == cudaErrorMemoryAllocation) ? DCM_ERR_OOM : DCM_ERR_CUDA;
+    return fail(code, "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+}
+
+// AoS [N][3] -> SoA [3][N], wrapping into the box
+__global__ void k_aos_to_soa(int n, const double *__restrict__ in, double *out, double L0, double L1,
+                             double L2, int wrap)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double L[3] = {L0, L1, L2};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double v = in[3 * (size_t)i + a];
+        if (wrap) {
+            if (v < 0.0 || v >= L[a]) v = DSUB(v, DMUL(L[a], floor(__ddiv_rn(v, L[a]))));
+            v = wrap_coord(v, L[a]);
+            if (!(v >= 0.0 && v < L[a])) v = 0.0;
+        }
+        out[(size_t)a * n + i] = v;
+    }
+}
+
+__global__ void k_soa_to_aos(int n, const double *__restrict__ in, double *out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) out[3 * (size_t)i + a] = in[(size_t)a * n + i];
+}
+
+static inline int nblk(int64_t n, int b) { return (int)((n + b - 1) / b); }
+
+}  // namespace dcm
+
+using namespace dcm;
+
+// ---------------------------------------------------------------------------
+extern "C" void dcm_default_params(dcm_params *p)
+{
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->rc_min = 3.0;
+    p->rc_max = 6.0;
+    p->alpha = -0.5;
+    p->dt = 0.005;
+    p->mass = 1.0;
+    p->eps = 1.0;
+    p->sigma = 1.0;
+    p->voxel = 1.0;
+    p->smooth_order = 8;
+    p->detect_every = 2;
+    p->kmeans_max_iter = 100;
+    p->cfsm_iter_max = 0;
+    p->cfsm_eps = 0.0;
+    p->precision = DCM_FP64;
+    p->n_classes = 4;
+    p->cell_min = 0.0;
+}
+
+extern "C" const char *dcm_last_error(void) { return g_errmsg; }
+extern "C" int dcm_version(void) { return DCM_ABI_VERSION; }
+
+static int check_params(const dcm_box *box, int64_t n, const dcm_params *p)
+{
+    if (!box || !p) return fail(DCM_ERR_ARG, "null box or params");
+    if (n < 1 || n > (int64_t)0x7fffffff / 4) return fail(DCM_ERR_ARG, "n out of range: %lld", (long long)n);
+    if (!(box->lx > 0 && box->ly > 0 && box->lz > 0)) return fail(DCM_ERR_ARG, "box edges must be > 0");
+    if (!(p->rc_min > 0 && p->rc_max >= p->rc_min)) return fail(DCM_ERR_ARG, "need 0 < rc_min <= rc_max");
+    if (!(p->alpha < 0)) return fail(DCM_ERR_ARG, "alpha must be negative (Eq. 7)");
+    if (!(p->dt > 0 && p->mass > 0 && p->eps > 0 && p->sigma > 0))
+        return fail(DCM_ERR_ARG, "dt, mass, eps, sigma must be > 0");
+    if (!(p->voxel > 0)) return fail(DCM_ERR_ARG, "voxel must be > 0");
+    if (p->smooth_order < 0 || p->smooth_order > 12 || (p->smooth_order & 1))
+        return fail(DCM_ERR_ARG, "smooth_order must be even, 0..12");
+    if (p->precision != DCM_FP64 && p->precision != DCM_MIXED)
+        return fail(DCM_ERR_ARG, "precision must be DCM_FP64 or DCM_MIXED");
+    if (p->n_classes < 2 || p->n_classes > DCM_MAX_CLASSES)
+        return fail(DCM_ERR_ARG, "n_classes must be 2..%d", DCM_MAX_CLASSES);
+    if (p->detect_every < 0) return fail(DCM_ERR_ARG, "detect_every must be >= 0");
+    return DCM_OK;
+}
+
+// geometry of the system (same definitions as the FP64 reference: bins of
+// edge L/n with index min(n-1, floor(x * n/L)), Eq. 7-8 constants)
+static int setup_geometry(const dcm_box *box, int64_t n, const dcm_params *p, Geom &g)
+{
+    memset(&g, 0, sizeof(g));
+    g.n = (int)n;
+    double L[3] = {box->lx, box->ly, box->lz};
+    double target = p->cell_min > 0 ? p->cell_min : 0.5 * p->rc_min;
+    double rcull = p->rc_max * 1.00002 + 1e-4;
+    bool ok = false;
+    for (int tries = 0; tries < 64 && target >= 0.25; ++tries, target *= 0.9) {
+        ok = true;
+        for (int a = 0; a < 3; ++a) {
+            int nc = (int)floor(L[a] / target);
+            nc = nc < 1 ? 1 : nc;
+            double inv = (double)nc / L[a];
+            int s = (int)ceil(rcull * inv);
+            if (2 * s + 1 > nc) ok = false;
+            g.nc[a] = nc;
+            g.inv_c[a] = inv;
+            g.cedge[a] = L[a] / nc;
+            g.smax[a] = s;
+        }
+        if (ok) break;
+    }
+    if (!ok)
+        return fail(DCM_ERR_BOX_TOO_SMALL,
+                    "box too small for rc_max=%g: each edge must exceed 2*rc_max plus a few link cells",
+                    p->rc_max);
+    for (int a = 0; a < 3; ++a) {
+        g.L[a] = L[a];
+        g.halfL[a] = 0.5 * L[a];
+        g.cf[a] = (float)g.cedge[a];
+        g.inv_cf[a] = (float)g.inv_c[a];
+        int gd = (int)floor(L[a] / p->voxel);
+        g.gd[a] = gd < 3 ? 3 : gd;
+        g.inv_h[a] = (double)g.gd[a] / L[a];
+        g.h[a] = L[a] / g.gd[a];
+    }
+    double hmax = fmax(g.h[0], fmax(g.h[1], g.h[2]));
+    g.r_grid = p->rc_max + hmax;
+    g.rc_min = p->rc_min;
+    g.rc_max = p->rc_max;
+    g.alpha = p->alpha;
+    g.K = p->n_classes;
+    if (p->rc_max > p->rc_min) {
+        g.cut_a = (p->rc_max - p->rc_min) / (pow(2.0, p->alpha * p->rc_max) - 1.0);
+        g.cut_b = p->rc_min - g.cut_a;
+        for (int k = 1; k <= g.K - 2; ++k) {
+            double r = p->rc_min + (p->rc_max - p->rc_min) * (double)k / (double)(g.K - 1);
+            g.thr[k - 1] = p->rc_max - log2((r - g.cut_b) / g.cut_a) / p->alpha;
+        }
+    } else {
+        g.cut_a = 0.0;
+        g.cut_b = p->rc_min;
+        for (int k = 1; k <= g.K - 2; ++k) g.thr[k - 1] = 0.0;
+    }
+    g.dt = p->dt;
+    g.hdtm = 0.5 * p->dt / p->mass;
+    g.eps = p->eps;
+    g.sigma = p->sigma;
+    return DCM_OK;
+}
+
+static int64_t bytes_for(const Geom &g, int64_t n, int precision)
+{
+    int64_t ncell = (int64_t)g.nc[0] * g.nc[1] * g.nc[2];
+    int64_t nv = (int64_t)g.gd[0] * g.gd[1] * g.gd[2];
+    int64_t per_p = 3 * 8 * 3 + 8 + 8 + 1 + 4 * 3 + 16 + 4 + 4 + 8 + 48 + 24;
+    if (precision == DCM_FP64) per_p += 32;
+    int64_t per_v = 4 + 4 + 4 + 8 + 1 + 8 + 8 + 4 + 16;
+    int64_t ntiles = (ncell + 2047) / 2048 + 1;
+    return n * per_p + ncell * 8 + 8 + nv * per_v + ntiles * 4 + 4096 + 256 * 8 * 8;
+}
+
+extern "C" int64_t dcm_estimate_bytes(const dcm_box *box, int64_t n, const dcm_params *p)
+{
+    if (check_params(box, n, p)) return -1;
+    Geom g;
+    if (setup_geometry(box, n, p, g)) return -1;
+    return bytes_for(g, n, p->precision);
+}
+
+template <typename T>
+static int dalloc(dcm_handle *h, T **ptr, int64_t count)
+{
+    size_t b = sizeof(T) * (size_t)(count > 0 ? count : 1);
+    cudaError_t e = cudaMalloc((void **)ptr, b);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        return fail_cuda(e, "cudaMalloc", __FILE__, __LINE__);
+    }
+    h->bytes += (int64_t)b;
+    return DCM_OK;
+}
+
+extern "C" int dcm_destroy(dcm_handle *h)
+{
+    if (!h) return DCM_OK;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->g_plain) cudaGraphExecDestroy(h->g_plain);
+    if (h->g_detect) cudaGraphExecDestroy(h->g_detect);
+    for (int q = 0; q <= DCM_NUM_PHASES; ++q)
+        if (h->ev[q]) cudaEventDestroy(h->ev[q]);
+    void *ptrs[] = {h->x, h->v, h->f, h->d, h->rc, h->cls, h->cell_of, h->slot, h->cell_count,
+                    h->cell_start, h->sorted_id, h->scan_tmp, h->sp4, h->spd, h->class_list,
+                    h->class_count_dev, h->B, h->sm1, h->sm2, h->Bs, h->S, h->D0, h->D1, h->stamp,
+                    h->flist, h->fcount, h->kacc, h->npair, h->pe, h->vir, h->red_part, h->red_out,
+                    h->err, h->stats, h->tmp3n};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return DCM_OK;
+}
+
+extern "C" int dcm_create(const dcm_box *box, int64_t n, const dcm_params *p, void *stream,
+                          dcm_handle **out)
+{
+    if (!out) return fail(DCM_ERR_ARG, "null out");
+    *out = nullptr;
+    int rc = check_params(box, n, p);
+    if (rc) return rc;
+    dcm_handle *h = new dcm_handle();
+    memset((void *)h, 0, sizeof(*h));
+    h->box = *box;
+    h->n = n;
+    h->p = *p;
+    if (h->p.kmeans_max_iter <= 0) h->p.kmeans_max_iter = 100;
+    rc = setup_geometry(box, n, p, h->g);
+    if (rc) {
+        delete h;
+        return rc;
+    }
+    // default launch shape: more lanes for larger cutoff classes
+    for (int q = 0; q < DCM_MAX_CLASSES; ++q) h->tune.lanes[q] = q == 0 ? 4 : 8;
+    h->tune.block = 256;
+    cudaGetDevice(&h->device);
+    cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (stream) {
+        h->stream = (cudaStream_t)stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete h;
+            return fail_cuda(e, "cudaStreamCreate", __FILE__, __LINE__);
+        }
+        h->own_stream = true;
+    }
+    h->ncell = (int64_t)h->g.nc[0] * h->g.nc[1] * h->g.nc[2];
+    h->nvox = (int64_t)h->g.gd[0] * h->g.gd[1] * h->g.gd[2];
+    int64_t N = n, nc = h->ncell, nv = h->nvox;
+    int64_t ntiles = (nc + 2047) / 2048 + 1;
+#define ALLOC(ptr, cnt)                 \
+    if ((rc = dalloc(h, &(ptr), (cnt)))) { \
+        dcm_destroy(h);                 \
+        return rc;                      \
+    }
+    ALLOC(h->x, 3 * N);
+    ALLOC(h->v, 3 * N);
+    ALLOC(h->f, 3 * N);
+    ALLOC(h->tmp3n, 3 * N);
+    ALLOC(h->d, N);
+    ALLOC(h->rc, N);
+    ALLOC(h->cls, N);
+    ALLOC(h->cell_of, N);
+    ALLOC(h->slot, N);
+    ALLOC(h->sorted_id, N);
+    ALLOC(h->cell_count, nc);
+    ALLOC(h->cell_start, nc + 1);
+    ALLOC(h->scan_tmp, ntiles);
+    ALLOC(h->sp4, N);
+    if (p->precision == DCM_FP64) ALLOC(h->spd, N);
+    ALLOC(h->class_list, N);
+    ALLOC(h->class_count_dev, 3 * DCM_MAX_CLASSES);
+    ALLOC(h->B, nv);
+    ALLOC(h->sm1, nv);
+    ALLOC(h->sm2, nv);
+    ALLOC(h->Bs, nv);
+    ALLOC(h->S, nv);
+    ALLOC(h->D0, nv);
+    ALLOC(h->D1, nv);
+    ALLOC(h->stamp, nv);
+    ALLOC(h->flist, 4 * nv);
+    ALLOC(h->fcount, 4);
+    ALLOC(h->kacc, 16);
+    ALLOC(h->npair, N);
+    ALLOC(h->pe, N);
+    ALLOC(h->vir, 6 * N);
+    ALLOC(h->red_part, 256 * 8);
+    ALLOC(h->red_out, 8);
+    ALLOC(h->err, 1);
+    ALLOC(h->stats, 1);
+#undef ALLOC
+    cudaMemsetAsync(h->err, 0, sizeof(int), h->stream);
+    cudaMemsetAsync(h->stats, 0, sizeof(DevStats), h->stream);
+    cudaMemsetAsync(h->v, 0, sizeof(double) * 3 * N, h->stream);
+    cudaMemsetAsync(h->f, 0, sizeof(double) * 3 * N, h->stream);
+    cudaMemsetAsync(h->cls, 0, N, h->stream);
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        dcm_destroy(h);
+        return fail_cuda(e, "create sync", __FILE__, __LINE__);
+    }
+    *out = h;
+    return DCM_OK;
+}
+
+static void invalidate_graphs(dcm_handle *h)
+{
+    if (h->g_plain) cudaGraphExecDestroy(h->g_plain);
+    if (h->g_detect) cudaGraphExecDestroy(h->g_detect);
+    h->g_plain = h->g_detect = nullptr;
+    h->graphs_ready = false;
+}
+
+extern "C" int dcm_set_state(dcm_handle *h, const double *x, const double *v, int mem)
+{
+    if (!h || !x) return fail(DCM_ERR_ARG, "null handle or positions");
+    int64_t N = h->n;
+    size_t bytes = sizeof(double) * 3 * (size_t)N;
+    const double *src[2] = {x, v};
+    double *dst[2] = {h->x, h->v};
+    for (int q = 0; q < 2; ++q) {
+        if (!src[q]) {
+            DCM_CHECK_CUDA(cudaMemsetAsync(dst[q], 0, bytes, h->stream));
+            continue;
+        }
+        DCM_CHECK_CUDA(cudaMemcpyAsync(h->tmp3n, src[q], bytes,
+                                       mem == DCM_DEVICE ? cudaMemcpyDeviceToDevice
+                                                         : cudaMemcpyHostToDevice,
+                                       h->stream));
+        k_aos_to_soa<<<nblk(N, 256), 256, 0, h->stream>>>((int)N, h->tmp3n, dst[q], h->g.L[0],
+                                                           h->g.L[1], h->g.L[2], q == 0);
+    }
+    DCM_CHECK_CUDA(cudaGetLastError());
+    if (mem != DCM_DEVICE) DCM_CHECK_CUDA(cudaStreamSynchronize(h->stream));
+    h->have_state = true;
+    h->have_cut = false;
+    h->forces_valid = false;
+    h->cells_valid = false;
+    h->step = 0;
+    return DCM_OK;
+}
+
+extern "C" int dcm_set_step(dcm_handle *h, int64_t step)
+{
+    if (!h || step < 0) return fail(DCM_ERR_ARG, "bad handle or step");
+    h->step = step;
+    return DCM_OK;
+}
+
+extern "C" int dcm_get_state(dcm_handle *h, double *x, double *v, double *f, int mem)
+{
+    if (!h) return fail(DCM_ERR_ARG, "null handle");
+    int64_t N = h->n;
+    size_t bytes = sizeof(double) * 3 * (size_t)N;
+    double *src[3] = {h->x, h->v, h->f};
+    double *dst[3] = {x, v, f};
+    for (int q = 0; q < 3; ++q) {
+        if (!dst[q]) continue;
+        k_soa_to_aos<<<nblk(N, 256), 256, 0, h->stream>>>((int)N, src[q], h->tmp3n);
+        DCM_CHECK_CUDA(cudaGetLastError());
+        DCM_CHECK_CUDA(cudaMemcpyAsync(dst[q], h->tmp3n, bytes,
+                                       mem == DCM_DEVICE ? cudaMemcpyDeviceToDevice
+                                                         : cudaMemcpyDeviceToHost,
+                                       h->stream));
+        if (mem != DCM_DEVICE) DCM_CHECK_CUDA(cudaStreamSynchronize(h->stream));
+    }
+    return DCM_OK;
+}
+
+extern "C" int dcm_set_cutoffs(dcm_handle *h, const double *rc, int mem)
+{
+    if (!h || !rc) return fail(DCM_ERR_ARG, "null handle or cutoffs");
+    int64_t N = h->n;
+    std::vector<double> tmp;
+    if (mem != DCM_DEVICE) {
+        for (int64_t i = 0; i < N; ++i)
+            if (!(rc[i] >= h->p.rc_min && rc[i] <= h->p.rc_max))
+                return fail(DCM_ERR_ARG, "cutoff %lld = %g outside [rc_min, rc_max]",
+                            (long long)i, rc[i]);
+    }
+    DCM_CHECK_CUDA(cudaMemcpyAsync(h->rc, rc, sizeof(double) * N,
+                                   mem == DCM_DEVICE ? cudaMemcpyDeviceToDevice
+                                                     : cudaMemcpyHostToDevice,
+                                   h->stream));
+    int r = launch_classify_rc(h);
+    if (r) return r;
+    if (mem != DCM_DEVICE) DCM_CHECK_CUDA(cudaStreamSynchronize(h->stream));
+    h->have_cut = true;
+    h->forces_valid = false;
+    return DCM_OK;
+}
+
+extern "C" int dcm_detect_interface(dcm_handle *h)
+{
+    if (!h) return fail(DCM_ERR_ARG, "null handle");
+    if (!h->have_state) return fail(DCM_ERR_STATE, "no state set");
+    int r = launch_detect(h);
+    if (r) return r;
+    h->have_cut = true;
+    h->forces_valid = false;
+    return DCM_OK;
+}
+
+static int forces_now(dcm_handle *h, bool energy)
+{
+    if (!h->have_cut) {
+        int r = launch_detect(h);
+        if (r) return r;
+        h->have_cut = true;
+    }
+    int r = launch_bin(h);
+    if (r) return r;
+    r = launch_forces(h, energy);
+    if (r) return r;
+    h->forces_valid = true;
+    return DCM_OK;
+}
+
+extern "C" int dcm_compute_forces(dcm_handle *h)
+{
+    if (!h) return fail(DCM_ERR_ARG, "null handle");
+    if (!h->have_state) return fail(DCM_ERR_STATE, "no state set");
+    return forces_now(h, false);
+}
+
+static void mark(dcm_handle *h, int q, bool capturing)
+{
+    if (!h->timing) return;
+    if (capturing)
+        cudaEventRecordWithFlags(h->ev[q], h->stream, cudaEventRecordExternal);
+    else
+        cudaEventRecord(h->ev[q], h->stream);
+}
+
+// one velocity-Verlet step; detection after the drift when detect is set
+static int enqueue_step(dcm_handle *h, bool detect, bool capturing)
+{
+    int64_t k0 = h->kernels;
+    mark(h, 0, capturing);
+    int r = launch_kick_drift(h);
+    mark(h, 1, capturing);
+    if (!r && detect) r = launch_detect(h);
+    mark(h, 2, capturing);
+    if (!r) r = launch_bin(h);
+    mark(h, 3, capturing);
+    if (!r) r = launch_forces(h, false);
+    mark(h, 4, capturing);
+    if (!r) r = launch_kick(h);
+    mark(h, 5, capturing);
+    (detect ? h->kernels_detect : h->kernels_plain) = (int)(h->kernels - k0);
+    return r;
+}
+
+static int capture(dcm_handle *h, bool detect, cudaGraphExec_t *exec)
+{
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return fail_cuda(e, "begin capture", __FILE__, __LINE__);
+    int r = enqueue_step(h, detect, true);
+    e = cudaStreamEndCapture(h->stream, &graph);
+    if (r || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        (void)cudaGetLastError();
+        return r ? r : fail_cuda(e, "end capture", __FILE__, __LINE__);
+    }
+    e = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail_cuda(e, "graph instantiate", __FILE__, __LINE__);
+    return DCM_OK;
+}
+
+extern "C" int dcm_step(dcm_handle *h, int64_t nsteps)
+{
+    if (!h || nsteps < 0) return fail(DCM_ERR_ARG, "bad handle or nsteps");
+    if (!h->have_state) return fail(DCM_ERR_STATE, "no state set");
+    if (nsteps == 0) return DCM_OK;
+    if (!h->forces_valid) {
+        int r = forces_now(h, false);
+        if (r) return r;
+    }
+    if (!h->graphs_ready) {
+        int r = capture(h, false, &h->g_plain);
+        if (!r) r = capture(h, true, &h->g_detect);
+        if (r) {
+            invalidate_graphs(h);
+            return r;
+        }
+        h->graphs_ready = true;
+    }
+    for (int64_t s = 0; s < nsteps; ++s) {
+        int64_t step = ++h->step;
+        bool det = h->p.detect_every > 0 && step % h->p.detect_every == 0;
+        DCM_CHECK_CUDA(cudaGraphLaunch(det ? h->g_detect : h->g_plain, h->stream));
+        h->last_detect = det;
+    }
+    return DCM_OK;
+}
+
+extern "C" int dcm_set_timing(dcm_handle *h, int on)
+{
+    if (!h) return fail(DCM_ERR_ARG, "null handle");
+    if ((on != 0) == h->timing) return DCM_OK;
+    if (on && !h->ev[0])
+        for (int q = 0; q <= DCM_NUM_PHASES; ++q) DCM_CHECK_CUDA(cudaEventCreate(&h->ev[q]));
+    h->timing = on != 0;
+    invalidate_graphs(h);
+    return DCM_OK;
+}
+
+extern "C" int dcm_get_phase_times(dcm_handle *h, float ms[DCM_NUM_PHASES])
+{
+    if (!h || !ms) return fail(DCM_ERR_ARG, "null handle or output");
+    if (!h->timing || !h->graphs_ready) return fail(DCM_ERR_STATE, "timing off or no step run");
+    DCM_CHECK_CUDA(cudaStreamSynchronize(h->stream));
+    for (int q = 0; q < DCM_NUM_PHASES; ++q) {
+        float t = 0.f;
+        DCM_CHECK_CUDA(cudaEventElapsedTime(&t, h->ev[q], h->ev[q + 1]));
+        ms[q] = t;
+    }
+    return DCM_OK;
+}
+
+extern "C" int dcm_energy_virial(dcm_handle *h, double *pe, double *ke, double w[6])
+{
+    if (!h) return fail(DCM_ERR_ARG, "null handle");
+    if (!h->have_state) return fail(DCM_ERR_STATE, "no state set");
+    int r = forces_now(h, true);
+    if (r) return r;
+    r = launch_reduce_energy(h);
+    if (r) return r;
+    double out[8];
+    DCM_CHECK_CUDA(cudaMemcpyAsync(out, h->red_out, sizeof(out), cudaMemcpyDeviceToHost, h->stream));
+    DCM_CHECK_CUDA(cudaStreamSynchronize(h->stream));
+    if (pe) *pe = out[0];
+    if (ke) *ke = 0.5 * h->p.mass * out[1];
+    if (w)
+        for (int q = 0; q < 6; ++q) w[q] = out[2 + q];
+    return DCM_OK;
+}
+
+extern "C" int dcm_get_grid(dcm_handle *h, int32_t dims[3], int32_t *counts, double *smoothed,
+                            uint8_t *labels, double *dist)
+{
+    if (!h) return fail(DCM_ERR_ARG, "null handle");
+    if (dims)
+        for (int a = 0; a < 3; ++a) dims[a] = h->g.gd[a];
+    size_t nv = (size_t)h->nvox;
+    if (counts) DCM_CHECK_CUDA(cudaMemcpyAsync(counts, h->B, 4 * nv, cudaMemcpyDeviceToHost, h->stream));
+    if (smoothed)
+        DCM_CHECK_CUDA(cudaMemcpyAsync(smoothed, h->Bs, 8 * nv, cudaMemcpyDeviceToHost, h->stream));
+    if (labels) DCM_CHECK_CUDA(cudaMemcpyAsync(labels, h->S, nv, cudaMemcpyDeviceToHost, h->stream));
+    if (dist) {
+        DevStats st;
+        DCM_CHECK_CUDA(cudaMemcpyAsync(&st, h->stats, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
+        DCM_CHECK_CUDA(cudaStreamSynchronize(h->stream));
+        const double *D = st.barrier[3] ? h->D1 : h->D0;
+        DCM_CHECK_CUDA(cudaMemcpyAsync(dist, D, 8 * nv, cudaMemcpyDeviceToHost, h->stream));
+    }
+    DCM_CHECK_CUDA(cudaStreamSynchronize(h->stream));
+    if (dist)
+        for (size_t q = 0; q < nv; ++q)
+            if (dist[q] > h->g.r_grid) dist[q] = h->g.r_grid;   // CFSM cap
+    return DCM_OK;
+}
+
+extern "C" int dcm_get_cutoffs(dcm_handle *h, double *d, double *rc, uint8_t *cls)
+{
+    if (!h) return fail(DCM_ERR_ARG, "null handle");
+    size_t N = (size_t)h->n;
+    if (d) DCM_CHECK_CUDA(cudaMemcpyAsync(d, h->d, 8 * N, cudaMemcpyDeviceToHost, h->stream));
+    if (rc) DCM_CHECK_CUDA(cudaMemcpyAsync(rc, h->rc, 8 * N, cudaMemcpyDeviceToHost, h->stream));
+    if (cls) DCM_CHECK_CUDA(cudaMemcpyAsync(cls, h->cls, N, cudaMemcpyDeviceToHost, h->stream));
+    DCM_CHECK_CUDA(cudaStreamSynchronize(h->stream));
+    return DCM_OK;
+}
+
+extern "C" int dcm_get_cells(dcm_handle *h, int32_t nc[3], int32_t *cell_start, int32_t *sorted_id)
+{
+    if (!h) return fail(DCM_ERR_ARG, "null handle");
+    if (nc)
+        for (int a = 0; a < 3; ++a) nc[a] = h->g.nc[a];
+    if (cell_start)
+        DCM_CHECK_CUDA(cudaMemcpyAsync(cell_start, h->cell_start, 4 * (size_t)(h->ncell + 1),
+                                       cudaMemcpyDeviceToHost, h->stream));
+    if (sorted_id)
+        DCM_CHECK_CUDA(cudaMemcpyAsync(sorted_id, h->sorted_id, 4 * (size_t)h->n,
+                                       cudaMemcpyDeviceToHost, h->stream));
+    DCM_CHECK_CUDA(cudaStreamSynchronize(h->stream));
+    return DCM_OK;
+}
+
+extern "C" int dcm_get_pair_counts(dcm_handle *h, int32_t *npair)
+{
+    if (!h || !npair) return fail(DCM_ERR_ARG, "null handle or output");
+    DCM_CHECK_CUDA(cudaMemcpyAsync(npair, h->npair, 4 * (size_t)h->n, cudaMemcpyDeviceToHost,
+                                   h->stream));
+    DCM_CHECK_CUDA(cudaStreamSynchronize(h->stream));
+    return DCM_OK;
+}
+
+extern "C" int dcm_get_stats(dcm_handle *h, dcm_stats *s)
+{
+    if (!h || !s) return fail(DCM_ERR_ARG, "null handle or output");
+    int r = launch_reduce_pairs(h);
+    if (r) return r;
+    DevStats st;
+    int32_t cc[3 * DCM_MAX_CLASSES];
+    DCM_CHECK_CUDA(cudaMemcpyAsync(&st, h->stats, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
+    DCM_CHECK_CUDA(cudaMemcpyAsync(cc, h->class_count_dev, sizeof(cc), cudaMemcpyDeviceToHost,
+                                   h->stream));
+    DCM_CHECK_CUDA(cudaStreamSynchronize(h->stream));
+    memset(s, 0, sizeof(*s));
+    s->step = h->step;
+    s->pairs = (int64_t)st.pairs;
+    s->kmeans_iters = st.kmeans_iters;
+    s->cfsm_iters = st.cfsm_iters;
+    for (int q = 0; q < h->g.K; ++q) s->class_count[q] = cc[q];
+    for (int a = 0; a < 3; ++a) {
+        s->grid[a] = h->g.gd[a];
+        s->cells[a] = h->g.nc[a];
+    }
+    s->c_liquid = st.c_liquid;
+    s->c_vapor = st.c_vapor;
+    s->guard_rechecks = (int64_t)st.guard_rechecks;
+    s->kernels_plain = h->kernels_plain;
+    s->kernels_detect = h->kernels_detect;
+    return DCM_OK;
+}
+
+extern "C" int dcm_set_tuning(dcm_handle *h, const dcm_tuning *t)
+{
+    if (!h || !t) return fail(DCM_ERR_ARG, "null handle or tuning");
+    for (int q = 0; q < DCM_MAX_CLASSES; ++q) {
+        int G = t->lanes[q];
+        if (G < 1 || G > 32 || (G & (G - 1))) return fail(DCM_ERR_ARG, "lanes must be 1..32, pow2");
+    }
+    if (t->block < 64 || t->block > 256 || (t->block & 31))
+        return fail(DCM_ERR_ARG, "block must be a multiple of 32 in 64..256");
+    h->tune = *t;
+    invalidate_graphs(h);
+    return DCM_OK;
+}
+
+extern "C" int dcm_get_tuning(dcm_handle *h, dcm_tuning *t)
+{
+    if (!h || !t) return fail(DCM_ERR_ARG, "null handle or tuning");
+    *t = h->tune;
+    return DCM_OK;
+}
+
+extern "C" int dcm_sync(dcm_handle *h)
+{
+    if (!h) return fail(DCM_ERR_ARG, "null handle");
+    DCM_CHECK_CUDA(cudaStreamSynchronize(h->stream));
+    int err = 0;
+    DCM_CHECK_CUDA(cudaMemcpy(&err, h->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!err) return DCM_OK;
+    DCM_CHECK_CUDA(cudaMemset(h->err, 0, sizeof(int)));
+    if (err & DEV_ERR_CANCEL) return fail(DCM_ERR_CANCELLED, "cancelled");
+    if (err & DEV_ERR_CFSM_CAP)
+        return fail(DCM_ERR_NOT_CONVERGED, "CFSM reached its iteration cap (device flags 0x%x)", err);
+    return fail(DCM_ERR_DEVICE_CHECK, "device check failed (flags 0x%x: 1 non-finite, 2 jump, "
+                                      "4 barrier timeout, 16 density, 64 bounds)", err);
+}
+
+extern "C" int64_t dcm_device_bytes(const dcm_handle *h) { return h ? h->bytes : 0; }

@@ -1,0 +1,206 @@
+// dcm_cells.cu -- link-cell binning (Section 2.2.1, bins per Section 3.2):
+// an integer counting sort of the particles by cell, bit-exact with the
+// definition (cell index = min(n-1, floor(x * n/L)), ascending particle id
+// inside a cell), followed by the gather of the sorted FP32/FP64 positions
+// the force kernels stream, and per-class lists of sorted slots.
+//
+// HBM bound: ~40 B/particle (positions read, cell/slot/id written twice) plus
+// 16-32 B/particle for the sorted position streams.
+#include "dcm_device.cuh"
+
+namespace dcm {
+
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 8;                       // per thread
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+// cell of every particle + its arrival slot within the cell (atomic order;
+// the order inside a cell is fixed afterwards by k_cell_sort)
+__global__ void k_cell_count(Geom g, const double *__restrict__ x, int32_t *cell_of,
+                             int32_t *slot, int32_t *count)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n) return;
+    int cx = bin_of(x[i], g.inv_c[0], g.nc[0]);
+    int cy = bin_of(x[(size_t)g.n + i], g.inv_c[1], g.nc[1]);
+    int cz = bin_of(x[2 * (size_t)g.n + i], g.inv_c[2], g.nc[2]);
+    int c = cx + g.nc[0] * (cy + g.nc[1] * cz);
+    cell_of[i] = c;
+    slot[i] = atomicAdd(&count[c], 1);
+}
+
+// exclusive scan, pass 1: scan each tile, record the tile total
+__global__ void k_scan_tiles(const int32_t *__restrict__ in, int32_t *out, int32_t *tile_sum,
+                             int64_t m)
+{
+    __shared__ int32_t s[SCAN_THREADS];
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    int32_t v[SCAN_ITEMS];
+    int32_t run = 0;
+#pragma unroll
+    for (int q = 0; q < SCAN_ITEMS; ++q) {
+        int64_t k = base + q;
+        v[q] = k < m ? in[k] : 0;
+        run += v[q];
+    }
+    s[threadIdx.x] = run;
+    __syncthreads();
+    // Hillis-Steele inclusive scan of the per-thread totals
+    for (int off = 1; off < SCAN_THREADS; off <<= 1) {
+        int32_t t = threadIdx.x >= off ? s[threadIdx.x - off] : 0;
+        __syncthreads();
+        s[threadIdx.x] += t;
+        __syncthreads();
+    }
+    int32_t excl = threadIdx.x ? s[threadIdx.x - 1] : 0;
+#pragma unroll
+    for (int q = 0; q < SCAN_ITEMS; ++q) {
+        int64_t k = base + q;
+        if (k < m) out[k] = excl;
+        excl += v[q];
+    }
+    if (threadIdx.x == SCAN_THREADS - 1) tile_sum[blockIdx.x] = s[SCAN_THREADS - 1];
+}
+
+// exclusive scan, pass 2: add the sum of all earlier tiles
+__global__ void k_scan_add(int32_t *out, const int32_t *__restrict__ tile_sum, int64_t m,
+                           int32_t total)
+{
+    __shared__ int32_t s[SCAN_THREADS];
+    int32_t acc = 0;
+    for (int t = threadIdx.x; t < (int)blockIdx.x; t += SCAN_THREADS) acc += tile_sum[t];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = SCAN_THREADS / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+        __syncthreads();
+    }
+    int32_t off = s[0];
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    for (int q = threadIdx.x; q < SCAN_TILE; q += SCAN_THREADS) {
+        int64_t k = base + q;
+        if (k < m) out[k] += off;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[m] = total;
+}
+
+__global__ void k_cell_scatter(int n, const int32_t *__restrict__ cell_of,
+                               const int32_t *__restrict__ slot,
+                               const int32_t *__restrict__ start, int32_t *sorted_id)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    sorted_id[start[cell_of[i]] + slot[i]] = i;
+}
+
+// ascending particle id inside each cell (cells hold a handful of particles)
+__global__ void k_cell_sort(int64_t ncell, const int32_t *__restrict__ start, int32_t *sorted_id)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    int lo = start[c], hi = start[c + 1];
+    for (int a = lo + 1; a < hi; ++a) {
+        int key = sorted_id[a];
+        int b = a - 1;
+        while (b >= lo && sorted_id[b] > key) {
+            sorted_id[b + 1] = sorted_id[b];
+            --b;
+        }
+        sorted_id[b + 1] = key;
+    }
+}
+
+// sorted position streams: sp4 = (x - cell corner in FP32, cell x index),
+// spd = absolute FP64 position (FP64 path only)
+__global__ void k_gather(Geom g, const double *__restrict__ x, const int32_t *__restrict__ sorted_id,
+                         const int32_t *__restrict__ cell_of, float4 *sp4, double4_32a *spd)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= g.n) return;
+    int i = sorted_id[k];
+    int c = cell_of[i];
+    int cx = c % g.nc[0];
+    int cy = (c / g.nc[0]) % g.nc[1];
+    int cz = c / (g.nc[0] * g.nc[1]);
+    double px = x[i], py = x[(size_t)g.n + i], pz = x[2 * (size_t)g.n + i];
+    float ux = (float)DSUB(px, DMUL((double)cx, g.cedge[0]));
+    float uy = (float)DSUB(py, DMUL((double)cy, g.cedge[1]));
+    float uz = (float)DSUB(pz, DMUL((double)cz, g.cedge[2]));
+    sp4[k] = make_float4(ux, uy, uz, (float)cx);
+    if (spd) spd[k] = make_double4_32a(px, py, pz, 0.0);
+}
+
+// per-class lists of sorted slots (warp-aggregated appends keep neighbouring
+// slots together); counts[0..K) must be prefix offsets, cursors[0..K) zero
+__global__ void k_class_lists(int n, int K, const int32_t *__restrict__ sorted_id,
+                              const uint8_t *__restrict__ cls, const int32_t *__restrict__ offs,
+                              int32_t *cursor, int32_t *list)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    int lane = threadIdx.x & 31;
+    int c = k < n ? (int)cls[sorted_id[k]] : -1;
+    unsigned lt = (1u << lane) - 1u;
+    for (int q = 0; q < K; ++q) {
+        unsigned m = __ballot_sync(0xffffffffu, c == q);
+        if (!m) continue;
+        int leader = __ffs(m) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(&cursor[q], __popc(m));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (c == q) list[offs[q] + base + __popc(m & lt)] = k;
+    }
+}
+
+__global__ void k_class_count(int n, int K, const uint8_t *__restrict__ cls, int32_t *count)
+{
+    __shared__ int32_t s[DCM_MAX_CLASSES];
+    if (threadIdx.x < DCM_MAX_CLASSES) s[threadIdx.x] = 0;
+    __syncthreads();
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) atomicAdd(&s[cls[i]], 1);
+    __syncthreads();
+    if (threadIdx.x < K && s[threadIdx.x]) atomicAdd(&count[threadIdx.x], s[threadIdx.x]);
+}
+
+// counts [0..K) -> exclusive offsets [K..2K), cursors [2K..3K) zeroed
+__global__ void k_class_offsets(int K, int32_t *buf)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int run = 0;
+    for (int q = 0; q < K; ++q) {
+        buf[K + q] = run;
+        run += buf[q];
+        buf[2 * K + q] = 0;
+    }
+}
+
+static inline int nblk(int64_t n, int b) { return (int)((n + b - 1) / b); }
+
+int launch_bin(dcm_handle *h)
+{
+    h->kernels += 9;
+    cudaStream_t s = h->stream;
+    int n = (int)h->n;
+    cudaMemsetAsync(h->cell_count, 0, sizeof(int32_t) * h->ncell, s);
+    k_cell_count<<<nblk(n, 256), 256, 0, s>>>(h->g, h->x, h->cell_of, h->slot, h->cell_count);
+    int ntiles = nblk(h->ncell, SCAN_TILE);
+    k_scan_tiles<<<ntiles, SCAN_THREADS, 0, s>>>(h->cell_count, h->cell_start, h->scan_tmp,
+                                                 h->ncell);
+    k_scan_add<<<ntiles, SCAN_THREADS, 0, s>>>(h->cell_start, h->scan_tmp, h->ncell, n);
+    k_cell_scatter<<<nblk(n, 256), 256, 0, s>>>(n, h->cell_of, h->slot, h->cell_start,
+                                                h->sorted_id);
+    k_cell_sort<<<nblk(h->ncell, 256), 256, 0, s>>>(h->ncell, h->cell_start, h->sorted_id);
+    k_gather<<<nblk(n, 256), 256, 0, s>>>(h->g, h->x, h->sorted_id, h->cell_of, h->sp4,
+                                          h->p.precision == DCM_FP64 ? h->spd : nullptr);
+    // class lists of sorted slots for the per-class force launches
+    int K = h->g.K;
+    cudaMemsetAsync(h->class_count_dev, 0, sizeof(int32_t) * 3 * DCM_MAX_CLASSES, s);
+    k_class_count<<<nblk(n, 256), 256, 0, s>>>(n, K, h->cls, h->class_count_dev);
+    k_class_offsets<<<1, 32, 0, s>>>(K, h->class_count_dev);
+    k_class_lists<<<nblk(n, 256), 256, 0, s>>>(n, K, h->sorted_id, h->cls,
+                                               h->class_count_dev + K,
+                                               h->class_count_dev + 2 * K, h->class_list);
+    return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "binning launch");
+}
+
+}  // namespace dcm

@@ -1,0 +1,158 @@
+// dcm_device.cuh -- device helpers shared by the libdcm kernels.
+//
+// Every FP64 expression whose result decides an integer (a bin index, a
+// pair inside/outside the cutoff, a class) or must reproduce a defined
+// value (the Godunov solve, the trilinear lookup) is written with explicit
+// round-to-nearest intrinsics so that the compiler cannot contract it into
+// an FMA.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dcm_internal.cuh"
+
+namespace dcm {
+
+#define DADD(a, b) __dadd_rn((a), (b))
+#define DSUB(a, b) __dsub_rn((a), (b))
+#define DMUL(a, b) __dmul_rn((a), (b))
+
+// bin of coordinate x on n bins of a periodic edge: min(n-1, floor(x*inv))
+__device__ __forceinline__ int bin_of(double x, double inv, int n)
+{
+    int k = (int)floor(DMUL(x, inv));
+    k = k > n - 1 ? n - 1 : k;
+    return k < 0 ? 0 : k;
+}
+
+// minimum image of a coordinate difference (same rule on every code path)
+__device__ __forceinline__ double min_image(double dx, double L, double halfL)
+{
+    if (dx > halfL) return DSUB(dx, L);
+    if (dx < -halfL) return DADD(dx, L);
+    return dx;
+}
+
+// wrap into [0, L) for a move smaller than L
+__device__ __forceinline__ double wrap_coord(double x, double L)
+{
+    if (x < 0.0) x = DADD(x, L);
+    if (x >= L) x = DSUB(x, L);
+    return x;
+}
+
+// r^2 = dx*dx + dy*dy + dz*dz, left to right, no FMA
+__device__ __forceinline__ double r2_rn(double dx, double dy, double dz)
+{
+    return DADD(DADD(DMUL(dx, dx), DMUL(dy, dy)), DMUL(dz, dz));
+}
+
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// error-free sum of two floats (Knuth's TwoSum): s + e == a + b exactly
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    float bp = __fsub_rn(s, a);
+    float ap = __fsub_rn(s, bp);
+    e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+}
+
+// add a float into a (hi, lo) double-float accumulator
+__device__ __forceinline__ void ff_add(float &hi, float &lo, float a)
+{
+    float s, e;
+    two_sum(hi, a, s, e);
+    hi = s;
+    lo = __fadd_rn(lo, e);
+}
+
+// ---- bounded grid barrier for cooperative (co-resident) launches --------
+// words[0] = arrival counter, words[1] = generation.  Gives up after a
+// bounded number of polls, sets DEV_ERR_BARRIER and returns false.
+__device__ __forceinline__ bool grid_barrier(unsigned int *words, int *err)
+{
+    __syncthreads();
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        volatile unsigned int *gen = words + 1;
+        unsigned int g = *gen;
+        __threadfence();
+        unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
+        unsigned int arrived = atomicAdd(words, 1u);
+        int ok = 1;
+        if (arrived == nb - 1) {
+            atomicExch(words, 0u);
+            __threadfence();
+            atomicAdd(words + 1, 1u);
+        } else {
+            long long polls = 0;
+            while (*gen == g) {
+                if (++polls > (1ll << 22)) {   // ~0.5 s with the back-off below
+                    atomicOr(err, DEV_ERR_BARRIER);
+                    ok = 0;
+                    break;
+                }
+                if (*(volatile int *)err & DEV_ERR_BARRIER) {
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// ---- Godunov upwind local solve (Eq. 16-19, per-axis spacing) -----------
+// The same expression sequence as the oracle's definition, FMA-free.
+__device__ __forceinline__ double godunov(double a0, double a1, double a2,
+                                          double h0, double h1, double h2)
+{
+    // stable sort of (a, h) by a
+    if (a1 < a0) { double t = a0; a0 = a1; a1 = t; t = h0; h0 = h1; h1 = t; }
+    if (a2 < a1) {
+        double t = a1; a1 = a2; a2 = t; t = h1; h1 = h2; h2 = t;
+        if (a1 < a0) { t = a0; a0 = a1; a1 = t; t = h0; h0 = h1; h1 = t; }
+    }
+    if (isinf(a0)) return a0;
+    double d2 = DSUB(a1, a0);
+    double d3 = DSUB(a2, a0);
+    double e = h0;
+    if (e <= d2) return DADD(a0, e);
+    double w1 = __ddiv_rn(1.0, DMUL(h0, h0));
+    double w2 = __ddiv_rn(1.0, DMUL(h1, h1));
+    double w3 = __ddiv_rn(1.0, DMUL(h2, h2));
+    double wd2 = DMUL(w2, d2);
+    double A = DADD(w1, w2);
+    double B = wd2;
+    double C = DSUB(DMUL(wd2, d2), 1.0);
+    double disc = DSUB(DMUL(B, B), DMUL(A, C));
+    if (disc < 0.0) disc = 0.0;
+    e = __ddiv_rn(DADD(B, __dsqrt_rn(disc)), A);
+    if (e <= d3) return DADD(a0, e);
+    double wd3 = DMUL(w3, d3);
+    A = DADD(DADD(w1, w2), w3);
+    B = DADD(wd2, wd3);
+    C = DSUB(DADD(DMUL(wd2, d2), DMUL(wd3, d3)), 1.0);
+    disc = DSUB(DMUL(B, B), DMUL(A, C));
+    if (disc < 0.0) disc = 0.0;
+    e = __ddiv_rn(DADD(B, __dsqrt_rn(disc)), A);
+    return DADD(a0, e);
+}
+
+__device__ __forceinline__ double lerp_rn(double a, double b, double t)
+{
+    return DADD(a, DMUL(t, DSUB(b, a)));
+}
+
+}  // namespace dcm

@@ -1,0 +1,370 @@
+// dcm_force.cu -- the DCM force sum, Algorithm 3.2:
+//     F_i = sum_{j != i, |r_ij| < r_c[i]} F_LJ(r_ij)
+// over a full neighbourhood with no Newton-3 (the thesis, Section 3.2: the
+// interaction is asymmetric, so each particle sums its own force only).
+//
+// GPU design (not the thesis's LAMMPS/Verlet-list design):
+//  * Particles are sorted by link cell (cells of edge ~r_c,min/2, the
+//    "improved bins" of Fig. 13b).  For particle i the stencil is walked row
+//    by row: a row is a run of cells along x at fixed (y, z) cell offset and
+//    is contiguous in the sorted arrays.  Rows whose y/z box distance
+//    exceeds r_c[i] are skipped and each row is trimmed in x to the chord of
+//    the cutoff sphere, so the candidates approach the sphere volume.
+//  * G lanes (1..32, per cutoff class) share one particle and stride through
+//    the row, so loads of the sorted float4 stream are coalesced; a shuffle
+//    tree combines the G partial sums.
+//  * Work is handed out warp by warp from a device queue ordered from the
+//    largest-cutoff class down (the GPU analogue of the thesis's
+//    schedule(dynamic,20), Algorithm 5.1): interfacial particles, whose
+//    cutoff makes them 8-13x more expensive, start first and the cheap bulk
+//    fills in behind them.
+//  * DCM_MIXED: positions are stored relative to their cell corner in FP32,
+//    so pair distances carry ~1e-7 absolute error instead of the ~1e-5 of
+//    absolute FP32 coordinates; forces are computed in FP32 and folded
+//    into a 2 x FP32 (TwoSum) accumulator per row; pairs whose r^2 is
+//    within a relative 2^-18 of r_c^2 are re-decided in FP64 with the exact
+//    FP64 rule, so the set of interacting pairs is the same as in FP64.
+//  * DCM_FP64: absolute FP64 positions, minimum image and r^2 evaluated
+//    exactly as the FP64 definition; FP64 forces and accumulation.
+// Bound: FP32 pipe (mixed) or FP64 pipe (FP64); algorithmic work per
+// in-cutoff pair = 8 flops for the distance test + 16 for the force.
+#include "dcm_device.cuh"
+
+namespace dcm {
+
+constexpr int FORCE_THREADS = 256;
+constexpr float GUARD = 3.814697265625e-06f;   // 2^-18
+
+struct ForceArgs {
+    Geom g;
+    const int32_t *class_buf;     // [0..K) counts, [K..2K) offsets
+    const int32_t *class_list;    // sorted slots grouped by class
+    int lanes[DCM_MAX_CLASSES];   // lanes per particle per class
+    const float4 *sp4;
+    const double4_32a *spd;
+    const int32_t *cell_start;
+    const int32_t *sorted_id;
+    const int32_t *cell_of;
+    const double *x;              // id-order SoA (FP64 re-decisions)
+    const double *rc;
+    double *f;
+    int32_t *npair;
+    double *pe, *vir;
+    unsigned int *queue;          // work counter
+    unsigned long long *guard_count;
+    float eps24f, eps48f, eps2f, sig2f;
+    double eps24, eps48, eps2, sig2;
+};
+
+// exact FP64 decision |r_ij| < r_c[i] (the definition's arithmetic)
+__device__ __forceinline__ bool fp64_inside(const ForceArgs &a, int i, int j, double rci2)
+{
+    const Geom &g = a.g;
+    size_t n = (size_t)g.n;
+    double dx = min_image(DSUB(a.x[i], a.x[j]), g.L[0], g.halfL[0]);
+    double dy = min_image(DSUB(a.x[n + i], a.x[n + j]), g.L[1], g.halfL[1]);
+    double dz = min_image(DSUB(a.x[2 * n + i], a.x[2 * n + j]), g.L[2], g.halfL[2]);
+    return r2_rn(dx, dy, dz) < rci2;
+}
+
+template <int PREC, bool ENERGY>
+struct Acc;
+
+template <bool ENERGY>
+struct Acc<DCM_MIXED, ENERGY> {
+    float hx = 0.f, lx = 0.f, hy = 0.f, ly = 0.f, hz = 0.f, lz = 0.f;   // 2xFP32 totals
+    float rx = 0.f, ry = 0.f, rz = 0.f;                                 // row partials
+    float pe = 0.f, v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    __device__ __forceinline__ void fold()
+    {
+        ff_add(hx, lx, rx);
+        ff_add(hy, ly, ry);
+        ff_add(hz, lz, rz);
+        rx = ry = rz = 0.f;
+    }
+};
+
+template <bool ENERGY>
+struct Acc<DCM_FP64, ENERGY> {
+    double fx = 0.0, fy = 0.0, fz = 0.0, pe = 0.0;
+    double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    __device__ __forceinline__ void fold() {}
+};
+
+template <int PREC, bool ENERGY>
+__device__ __forceinline__ void row_segment(const ForceArgs &a, int k, int i, int lane, int G,
+                                            int j0, int j1, float ax, float ay, float az,
+                                            float4 ui, double4_32a pi, float rc2f, float rc2lo,
+                                            float rc2hi, double rci2, Acc<PREC, ENERGY> &acc,
+                                            int &np)
+{
+    const Geom &g = a.g;
+    for (int j = j0 + lane; j < j1; j += G) {
+        if constexpr (PREC == DCM_MIXED) {
+            float4 uj = a.sp4[j];
+            float dx = fmaf(ax - uj.w, g.cf[0], ui.x - uj.x);
+            float dy = ay - uj.y;
+            float dz = az - uj.z;
+            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            if (r2 < rc2hi && j != k) {
+                bool in = r2 < rc2f;
+                if (r2 >= rc2lo) {
+                    in = fp64_inside(a, i, a.sorted_id[j], rci2);
+                    atomicAdd(a.guard_count, 1ull);
+                }
+                if (in) {
+                    float r2inv = rcp_approx(r2);
+                    float sr2 = a.sig2f * r2inv;
+                    float sr6 = sr2 * sr2 * sr2;
+                    float fr = r2inv * sr6 * fmaf(a.eps48f, sr6, -a.eps24f);
+                    acc.rx = fmaf(fr, dx, acc.rx);
+                    acc.ry = fmaf(fr, dy, acc.ry);
+                    acc.rz = fmaf(fr, dz, acc.rz);
+                    ++np;
+                    if constexpr (ENERGY) {
+                        acc.pe = fmaf(a.eps2f * sr6, sr6 - 1.f, acc.pe);
+                        float fx = fr * dx, fy = fr * dy, fz = fr * dz;
+                        acc.v[0] = fmaf(0.5f * dx, fx, acc.v[0]);
+                        acc.v[1] = fmaf(0.5f * dy, fy, acc.v[1]);
+                        acc.v[2] = fmaf(0.5f * dz, fz, acc.v[2]);
+                        acc.v[3] = fmaf(0.5f * dx, fy, acc.v[3]);
+                        acc.v[4] = fmaf(0.5f * dx, fz, acc.v[4]);
+                        acc.v[5] = fmaf(0.5f * dy, fz, acc.v[5]);
+                    }
+                }
+            }
+        } else {
+            double4_32a pj = a.spd[j];
+            double dx = min_image(DSUB(pi.x, pj.x), g.L[0], g.halfL[0]);
+            double dy = min_image(DSUB(pi.y, pj.y), g.L[1], g.halfL[1]);
+            double dz = min_image(DSUB(pi.z, pj.z), g.L[2], g.halfL[2]);
+            double r2 = r2_rn(dx, dy, dz);
+            if (r2 < rci2 && j != k) {
+                double r2inv = 1.0 / r2;
+                double sr2 = a.sig2 * r2inv;
+                double sr6 = sr2 * sr2 * sr2;
+                double fr = r2inv * sr6 * (a.eps48 * sr6 - a.eps24);
+                acc.fx += fr * dx;
+                acc.fy += fr * dy;
+                acc.fz += fr * dz;
+                ++np;
+                if constexpr (ENERGY) {
+                    acc.pe += a.eps2 * sr6 * (sr6 - 1.0);
+                    double fx = fr * dx, fy = fr * dy, fz = fr * dz;
+                    acc.v[0] += 0.5 * dx * fx;
+                    acc.v[1] += 0.5 * dy * fy;
+                    acc.v[2] += 0.5 * dz * fz;
+                    acc.v[3] += 0.5 * dx * fy;
+                    acc.v[4] += 0.5 * dx * fz;
+                    acc.v[5] += 0.5 * dy * fz;
+                }
+            }
+        }
+    }
+    acc.fold();
+}
+
+// box distance along one axis from a point at u in [0, c) of its own cell
+// to the cell at offset d
+__device__ __forceinline__ float box_gap(int d, float u, float c)
+{
+    float gap = d > 0 ? (float)d * c - u : (d < 0 ? u - (float)(d + 1) * c : 0.f);
+    return gap > 0.f ? gap : 0.f;
+}
+
+template <int PREC, bool ENERGY>
+__device__ void particle_force(const ForceArgs &a, int k, int lane, int G, unsigned gmask)
+{
+    const Geom &g = a.g;
+    int i = a.sorted_id[k];
+    float4 ui = a.sp4[k];
+    int c = a.cell_of[i];
+    int cx = (int)ui.w;
+    int cy = (c / g.nc[0]) % g.nc[1];
+    int cz = c / (g.nc[0] * g.nc[1]);
+    double rci = a.rc[i];
+    double rci2 = DMUL(rci, rci);
+    float rc2f = (float)rci2;
+    float rc2lo = rc2f * (1.f - GUARD), rc2hi = rc2f * (1.f + GUARD);
+    // conservative culling radius (covers FP32 geometry error and the guard)
+    float rcull = (float)rci * 1.00002f + 1e-4f;
+    float rcull2 = rcull * rcull;
+    int sx = min(g.smax[0], (int)ceilf(rcull * g.inv_cf[0]));
+    int sy = min(g.smax[1], (int)ceilf(rcull * g.inv_cf[1]));
+    int sz = min(g.smax[2], (int)ceilf(rcull * g.inv_cf[2]));
+    double4_32a pi = make_double4_32a(0, 0, 0, 0);
+    if constexpr (PREC == DCM_FP64) pi = a.spd[k];
+    Acc<PREC, ENERGY> acc;
+    int np = 0;
+    for (int dz = -sz; dz <= sz; ++dz) {
+        float gz = box_gap(dz, ui.z, g.cf[2]);
+        float remz = rcull2 - gz * gz;
+        if (remz < 0.f) continue;
+        int czz = cz + dz;
+        czz += czz < 0 ? g.nc[2] : (czz >= g.nc[2] ? -g.nc[2] : 0);
+        float az = ui.z - (float)dz * g.cf[2];
+        for (int dy = -sy; dy <= sy; ++dy) {
+            float gy = box_gap(dy, ui.y, g.cf[1]);
+            float w2 = remz - gy * gy;
+            if (w2 < 0.f) continue;
+            int cyy = cy + dy;
+            cyy += cyy < 0 ? g.nc[1] : (cyy >= g.nc[1] ? -g.nc[1] : 0);
+            float ay = ui.y - (float)dy * g.cf[1];
+            float w = sqrtf(w2);
+            int xlo = max(-sx, (int)floorf((ui.x - w) * g.inv_cf[0]));
+            int xhi = min(sx, (int)floorf((ui.x + w) * g.inv_cf[0]));
+            int row = g.nc[0] * (cyy + g.nc[1] * czz);
+            int lo = cx + xlo, hi = cx + xhi;
+            if (lo < 0) {
+                // cells at the top end seen through the x = 0 face
+                row_segment<PREC, ENERGY>(a, k, i, lane, G, a.cell_start[row + lo + g.nc[0]],
+                                          a.cell_start[row + g.nc[0]], (float)(cx + g.nc[0]), ay,
+                                          az, ui, pi, rc2f, rc2lo, rc2hi, rci2, acc, np);
+                lo = 0;
+            }
+            if (hi >= g.nc[0]) {
+                row_segment<PREC, ENERGY>(a, k, i, lane, G, a.cell_start[row],
+                                          a.cell_start[row + hi - g.nc[0] + 1],
+                                          (float)(cx - g.nc[0]), ay, az, ui, pi, rc2f, rc2lo,
+                                          rc2hi, rci2, acc, np);
+                hi = g.nc[0] - 1;
+            }
+            if (lo <= hi)
+                row_segment<PREC, ENERGY>(a, k, i, lane, G, a.cell_start[row + lo],
+                                          a.cell_start[row + hi + 1], (float)cx, ay, az, ui, pi,
+                                          rc2f, rc2lo, rc2hi, rci2, acc, np);
+        }
+    }
+    // combine the G lanes of this particle
+    double fx, fy, fz, pe = 0.0, vir[6] = {0, 0, 0, 0, 0, 0};
+    if constexpr (PREC == DCM_MIXED) {
+        fx = (double)acc.hx + (double)acc.lx;
+        fy = (double)acc.hy + (double)acc.ly;
+        fz = (double)acc.hz + (double)acc.lz;
+    } else {
+        fx = acc.fx;
+        fy = acc.fy;
+        fz = acc.fz;
+    }
+    if constexpr (ENERGY) {
+        pe = acc.pe;
+        for (int q = 0; q < 6; ++q) vir[q] = acc.v[q];
+    }
+    for (int off = G >> 1; off > 0; off >>= 1) {
+        fx += __shfl_xor_sync(gmask, fx, off);
+        fy += __shfl_xor_sync(gmask, fy, off);
+        fz += __shfl_xor_sync(gmask, fz, off);
+        np += __shfl_xor_sync(gmask, np, off);
+        if constexpr (ENERGY) {
+            pe += __shfl_xor_sync(gmask, pe, off);
+            for (int q = 0; q < 6; ++q) vir[q] += __shfl_xor_sync(gmask, vir[q], off);
+        }
+    }
+    if (lane == 0) {
+        size_t n = (size_t)g.n;
+        a.f[i] = fx;
+        a.f[n + i] = fy;
+        a.f[2 * n + i] = fz;
+        a.npair[i] = np;
+        if constexpr (ENERGY) {
+            a.pe[i] = pe;
+            for (int q = 0; q < 6; ++q) a.vir[q * n + i] = vir[q];
+        }
+    }
+}
+
+// persistent warps draining the class-ordered work queue
+template <int PREC, bool ENERGY>
+__global__ void __launch_bounds__(FORCE_THREADS) k_force(ForceArgs a)
+{
+    __shared__ int s_cnt[DCM_MAX_CLASSES], s_off[DCM_MAX_CLASSES], s_items[DCM_MAX_CLASSES + 1];
+    const int K = a.g.K;
+    if (threadIdx.x == 0) {
+        int run = 0;
+        // heaviest (largest cutoff) class first
+        for (int q = K - 1, t = 0; q >= 0; --q, ++t) {
+            s_cnt[q] = a.class_buf[q];
+            s_off[q] = a.class_buf[K + q];
+            int per = 32 / a.lanes[q];
+            s_items[t] = run;
+            run += (s_cnt[q] + per - 1) / per;
+        }
+        s_items[K] = run;
+    }
+    __syncthreads();
+    const int total = s_items[K];
+    const int lane32 = threadIdx.x & 31;
+    while (true) {
+        int item = 0;
+        if (lane32 == 0) item = (int)atomicAdd(a.queue, 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= total) break;
+        int t = 0;
+        while (t + 1 < K && item >= s_items[t + 1]) ++t;
+        int q = K - 1 - t;
+        int G = a.lanes[q];
+        int per = 32 / G;
+        int local = (item - s_items[t]) * per + lane32 / G;
+        int lane = lane32 & (G - 1);
+        unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane32 & ~(G - 1)));
+        if (local < s_cnt[q]) {
+            int k = a.class_list[s_off[q] + local];
+            particle_force<PREC, ENERGY>(a, k, lane, G, gmask);
+        }
+        __syncwarp();
+    }
+}
+
+int launch_forces(dcm_handle *h, bool energy)
+{
+    h->kernels += 1;
+    ForceArgs a;
+    a.g = h->g;
+    a.class_buf = h->class_count_dev;
+    a.class_list = h->class_list;
+    for (int q = 0; q < DCM_MAX_CLASSES; ++q) {
+        int G = h->tune.lanes[q];
+        a.lanes[q] = (G >= 1 && G <= 32 && (G & (G - 1)) == 0) ? G : 1;
+    }
+    a.sp4 = h->sp4;
+    a.spd = h->spd;
+    a.cell_start = h->cell_start;
+    a.sorted_id = h->sorted_id;
+    a.cell_of = h->cell_of;
+    a.x = h->x;
+    a.rc = h->rc;
+    a.f = h->f;
+    a.npair = h->npair;
+    a.pe = h->pe;
+    a.vir = h->vir;
+    a.queue = &h->stats->barrier[2];
+    a.guard_count = &h->stats->guard_rechecks;
+    double eps = h->p.eps, sig = h->p.sigma;
+    a.eps24 = 24.0 * eps;
+    a.eps48 = 48.0 * eps;
+    a.eps2 = 2.0 * eps;
+    a.sig2 = sig * sig;
+    a.eps24f = (float)a.eps24;
+    a.eps48f = (float)a.eps48;
+    a.eps2f = (float)a.eps2;
+    a.sig2f = (float)a.sig2;
+    cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), h->stream);
+    int block = h->tune.block >= 64 && h->tune.block <= 1024 ? h->tune.block : FORCE_THREADS;
+    block = block > FORCE_THREADS ? FORCE_THREADS : block;
+    int grid = h->num_sms * (2048 / block);
+    bool fp64 = h->p.precision == DCM_FP64;
+    if (fp64) {
+        if (energy)
+            k_force<DCM_FP64, true><<<grid, block, 0, h->stream>>>(a);
+        else
+            k_force<DCM_FP64, false><<<grid, block, 0, h->stream>>>(a);
+    } else {
+        if (energy)
+            k_force<DCM_MIXED, true><<<grid, block, 0, h->stream>>>(a);
+        else
+            k_force<DCM_MIXED, false><<<grid, block, 0, h->stream>>>(a);
+    }
+    return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "force launch");
+}
+
+}  // namespace dcm

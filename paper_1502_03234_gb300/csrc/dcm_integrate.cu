@@ -1,0 +1,147 @@
+// dcm_integrate.cu -- velocity Verlet (Eq. 1-2) and deterministic FP64
+// reductions for energy, virial and pair counts.
+//
+// HBM bound: a kick-drift reads x, v, f (72 B/particle) and writes x, v
+// (48 B); a kick reads v, f and writes v (48 + 24 B).
+#include "dcm_device.cuh"
+
+namespace dcm {
+
+// v += dt/(2m) F;  x += dt v;  wrap into the box  (first half of a step)
+__global__ void k_kick_drift(Geom g, double *__restrict__ x, double *__restrict__ v,
+                             const double *__restrict__ f, int *err)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n) return;
+    int bad = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        size_t o = (size_t)a * g.n + i;
+        double vi = DADD(v[o], DMUL(g.hdtm, f[o]));
+        double step = DMUL(g.dt, vi);
+        double xi = DADD(x[o], step);
+        if (!(fabs(step) < g.L[a])) bad |= DEV_ERR_JUMP;
+        xi = wrap_coord(xi, g.L[a]);
+        if (!isfinite(xi) || !isfinite(vi)) bad |= DEV_ERR_NONFINITE;
+        if (!(xi >= 0.0 && xi < g.L[a])) {
+            bad |= DEV_ERR_JUMP;
+            xi = 0.0;
+        }
+        v[o] = vi;
+        x[o] = xi;
+    }
+    if (bad) atomicOr(err, bad);
+}
+
+// v += dt/(2m) F  (second half of a step)
+__global__ void k_kick(Geom g, double *__restrict__ v, const double *__restrict__ f)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n) return;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        size_t o = (size_t)a * g.n + i;
+        v[o] = DADD(v[o], DMUL(g.hdtm, f[o]));
+    }
+}
+
+// ---- deterministic reductions -------------------------------------------
+// Fixed partition (RED_BLOCKS contiguous chunks) and a fixed tree order in
+// each block, so the result does not depend on scheduling.
+constexpr int RED_BLOCKS = 256;
+constexpr int RED_THREADS = 256;
+constexpr int RED_VALUES = 8;   // pe, sum v^2, w_xx w_yy w_zz w_xy w_xz w_yz
+
+__global__ void k_reduce_energy_part(int n, const double *__restrict__ pe,
+                                     const double *__restrict__ vir,
+                                     const double *__restrict__ v, double *part)
+{
+    __shared__ double s[RED_VALUES][RED_THREADS];
+    int chunk = (n + RED_BLOCKS - 1) / RED_BLOCKS;
+    int lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
+    double acc[RED_VALUES];
+#pragma unroll
+    for (int q = 0; q < RED_VALUES; ++q) acc[q] = 0.0;
+    for (int i = lo + threadIdx.x; i < hi; i += RED_THREADS) {
+        acc[0] += pe[i];
+        double vx = v[i], vy = v[(size_t)n + i], vz = v[2 * (size_t)n + i];
+        acc[1] += vx * vx + vy * vy + vz * vz;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) acc[2 + q] += vir[(size_t)q * n + i];
+    }
+#pragma unroll
+    for (int q = 0; q < RED_VALUES; ++q) s[q][threadIdx.x] = acc[q];
+    __syncthreads();
+    for (int w = RED_THREADS / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+#pragma unroll
+            for (int q = 0; q < RED_VALUES; ++q) s[q][threadIdx.x] += s[q][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < RED_VALUES) part[blockIdx.x * RED_VALUES + threadIdx.x] = s[threadIdx.x][0];
+}
+
+__global__ void k_reduce_final(const double *part, int nvals, double *out)
+{
+    __shared__ double s[RED_BLOCKS];
+    for (int q = 0; q < nvals; ++q) {
+        s[threadIdx.x] = part[threadIdx.x * nvals + q];
+        __syncthreads();
+        for (int w = RED_BLOCKS / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[q] = s[0];
+        __syncthreads();
+    }
+}
+
+__global__ void k_reduce_pairs(int n, const int32_t *__restrict__ npair,
+                               unsigned long long *out)
+{
+    __shared__ unsigned long long s[RED_THREADS];
+    unsigned long long acc = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        acc += (unsigned long long)npair[i];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = RED_THREADS / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(out, s[0]);   // integer: order-free
+}
+
+static inline int nblk(int64_t n, int b) { return (int)((n + b - 1) / b); }
+
+int launch_kick_drift(dcm_handle *h)
+{
+    h->kernels += 1;
+    k_kick_drift<<<nblk(h->n, 256), 256, 0, h->stream>>>(h->g, h->x, h->v, h->f, h->err);
+    return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "kick_drift launch");
+}
+
+int launch_kick(dcm_handle *h)
+{
+    h->kernels += 1;
+    k_kick<<<nblk(h->n, 256), 256, 0, h->stream>>>(h->g, h->v, h->f);
+    return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "kick launch");
+}
+
+int launch_reduce_energy(dcm_handle *h)
+{
+    k_reduce_energy_part<<<RED_BLOCKS, RED_THREADS, 0, h->stream>>>((int)h->n, h->pe, h->vir,
+                                                                  h->v, h->red_part);
+    k_reduce_final<<<1, RED_BLOCKS, 0, h->stream>>>(h->red_part, RED_VALUES, h->red_out);
+    return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "reduce launch");
+}
+
+int launch_reduce_pairs(dcm_handle *h)
+{
+    cudaMemsetAsync(&h->stats->pairs, 0, sizeof(unsigned long long), h->stream);
+    k_reduce_pairs<<<RED_BLOCKS, RED_THREADS, 0, h->stream>>>((int)h->n, h->npair,
+                                                             &h->stats->pairs);
+    return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "reduce launch");
+}
+
+}  // namespace dcm

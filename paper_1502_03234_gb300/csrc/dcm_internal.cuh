@@ -1,0 +1,153 @@
+// dcm_internal.cuh -- internal declarations of libdcm (sm_103a).
+//
+// Device data layout (all in HBM, allocated once by dcm_create):
+//   state     x, v, f : double SoA [3][N] in the caller's particle order
+//   cutoffs   d, rc   : double [N];  cls : uint8 [N]   (id order)
+//   link cells        : cell_of[N], slot[N] (id order); cell_count[Nc],
+//                       cell_start[Nc+1], sorted_id[N]; sp4[N] float4
+//                       (cell-relative x,y,z in FP32, cell x index) and
+//                       spd[N] double4_32a (absolute x,y,z) in cell order
+//   voxel grid        : B int32, sm1/sm2 uint32 (smoothing passes), Bs double,
+//                       S uint8, D0/D1 double (CFSM ping-pong), stamp int32,
+//                       four frontier lists int32 [Nv]
+//   per-particle      : npair int32, pe double, vir double [6][N]
+// Cells and voxels are indexed x fastest: c = cx + nx*(cy + ny*cz).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/dcm.h"
+
+#define DCM_CHECK_CUDA(call)                                                   \
+    do {                                                                       \
+        cudaError_t e_ = (call);                                               \
+        if (e_ != cudaSuccess) return dcm::fail_cuda(e_, #call, __FILE__, __LINE__); \
+    } while (0)
+
+namespace dcm {
+
+// sticky device error bits (dcm_sync maps them to status codes)
+enum : int {
+    DEV_ERR_NONFINITE = 1,       // non-finite position or velocity
+    DEV_ERR_JUMP = 2,            // moved more than a box edge in one step
+    DEV_ERR_BARRIER = 4,         // a bounded grid barrier gave up
+    DEV_ERR_CFSM_CAP = 8,        // CFSM hit iter_max
+    DEV_ERR_DENSITY = 16,        // voxel count too large for exact smoothing
+    DEV_ERR_CANCEL = 32,         // cancel flag observed
+    DEV_ERR_BOUNDS = 64          // an index check failed
+};
+
+// counters written by device code, read back for dcm_get_stats
+struct DevStats {
+    unsigned long long guard_rechecks;
+    unsigned long long pairs;
+    int kmeans_iters;
+    int cfsm_iters;
+    double c_liquid;
+    double c_vapor;
+    int class_count[DCM_MAX_CLASSES];
+    unsigned int barrier[4];     // grid-barrier counter / generation words
+};
+
+// geometry and parameters passed by value to kernels
+struct Geom {
+    int n;
+    double L[3], halfL[3];
+    int nc[3];                   // link cells per axis
+    double inv_c[3];             // nc / L  (cell index = floor(x * inv_c))
+    double cedge[3];             // L / nc
+    float cf[3], inv_cf[3];      // FP32 copies for the mixed kernels
+    int smax[3];                 // largest stencil radius in cells
+    int gd[3];                   // voxels per axis
+    double inv_h[3];             // gd / L
+    double h[3];                 // L / gd
+    double r_grid;               // CFSM band: rc_max + max h
+    double rc_min, rc_max, alpha, cut_a, cut_b;
+    int K;
+    double thr[DCM_MAX_CLASSES]; // class thresholds on d (descending)
+    double dt, hdtm;             // dt, dt/(2m)
+    double eps, sigma;
+};
+
+}  // namespace dcm
+
+struct dcm_handle {
+    dcm_box box;
+    int64_t n;
+    dcm_params p;
+    dcm_tuning tune;
+    dcm::Geom g;
+    cudaStream_t stream;
+    bool own_stream;
+    int device;
+    int num_sms;
+    int64_t ncell, nvox;
+    int64_t bytes;
+
+    // state
+    double *x, *v, *f;
+    double *tmp3n;               // AoS <-> SoA staging, 3N doubles
+    double *d, *rc;
+    uint8_t *cls;
+    // link cells
+    int32_t *cell_of, *slot, *cell_count, *cell_start, *sorted_id, *scan_tmp;
+    float4 *sp4;
+    double4_32a *spd;
+    int32_t *class_list;         // sorted slots grouped by class
+    int32_t *class_count_dev;    // [K] counts, [K..2K) cursors
+    // grid
+    int32_t *B;
+    uint32_t *sm1, *sm2;
+    double *Bs;
+    uint8_t *S;
+    double *D0, *D1;
+    int32_t *stamp;
+    int32_t *flist;              // 4 * nvox
+    int32_t *fcount;             // 4 counters
+    unsigned long long *kacc;    // k-means accumulators (3 x 4 words)
+    // per particle diagnostics / energies
+    int32_t *npair;
+    double *pe, *vir;
+    double *red_part, *red_out;
+    int *err;
+    dcm::DevStats *stats;
+    double *dfinal;              // which D buffer holds the result
+
+    // host-side status
+    bool have_state, have_cut, forces_valid, cells_valid;
+    int64_t step;
+    int class_count_host[DCM_MAX_CLASSES];
+
+    // CUDA graphs of one step (without / with detection)
+    cudaGraphExec_t g_plain, g_detect;
+    bool graphs_ready;
+    int coop_blocks;             // co-resident blocks for the persistent kernels
+    // kernels launched so far (each launcher adds its count)
+    int64_t kernels;
+    int kernels_plain, kernels_detect;
+    // phase timing: events[0..DCM_NUM_PHASES] bracket the phases
+    bool timing;
+    cudaEvent_t ev[DCM_NUM_PHASES + 1];
+    bool last_detect;
+};
+
+namespace dcm {
+
+int fail(int code, const char *fmt, ...);
+int fail_cuda(cudaError_t e, const char *what, const char *file, int line);
+
+// launchers (each enqueues on h->stream; return DCM_OK or an error code)
+int launch_kick_drift(dcm_handle *h);
+int launch_kick(dcm_handle *h);
+int launch_bin(dcm_handle *h);
+int launch_forces(dcm_handle *h, bool energy);
+int launch_detect(dcm_handle *h);
+int launch_reduce_energy(dcm_handle *h);
+int launch_reduce_pairs(dcm_handle *h);
+int launch_classify_rc(dcm_handle *h);   // classes from supplied rc
+
+// lower-level helpers
+int coop_grid_size(dcm_handle *h, const void *kernel, int block, size_t smem);
+
+}  // namespace dcm

@@ -1,0 +1,367 @@
+"""Thin ctypes binding of libdcm.so (include/dcm.h).
+
+Argument marshalling only: every step of the method runs in the CUDA
+library.  The functions keep the C names (``dcm_create``, ``dcm_step``, ...);
+``System`` wraps a handle for convenience.  Loading fails loudly when the
+library is missing -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdcm.so")
+
+DCM_OK = 0
+DCM_ERR_ARG, DCM_ERR_OOM, DCM_ERR_CUDA, DCM_ERR_BOX_TOO_SMALL = 1, 2, 3, 4
+DCM_ERR_NOT_CONVERGED, DCM_ERR_DEVICE_CHECK, DCM_ERR_CANCELLED, DCM_ERR_STATE = 5, 6, 7, 8
+DCM_FP64, DCM_MIXED = 0, 1
+DCM_HOST, DCM_DEVICE = 0, 1
+DCM_MAX_CLASSES = 8
+
+#: every entry point include/dcm.h declares (checked by the ABI test)
+EXPORTS = [
+    "dcm_default_params", "dcm_create", "dcm_destroy", "dcm_set_state", "dcm_get_state",
+    "dcm_set_step", "dcm_set_cutoffs", "dcm_detect_interface", "dcm_compute_forces",
+    "dcm_step", "dcm_energy_virial", "dcm_get_grid", "dcm_get_cutoffs", "dcm_get_cells",
+    "dcm_get_pair_counts", "dcm_get_stats", "dcm_set_tuning", "dcm_get_tuning", "dcm_sync",
+    "dcm_device_bytes", "dcm_estimate_bytes", "dcm_last_error", "dcm_version",
+    "dcm_set_timing", "dcm_get_phase_times",
+]
+DCM_NUM_PHASES = 5
+PHASES = ("kick_drift", "detect", "bin", "force", "kick")
+
+
+class DcmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libdcm error {code}: {msg}")
+        self.code = code
+
+
+class dcm_box(C.Structure):
+    _fields_ = [("lx", C.c_double), ("ly", C.c_double), ("lz", C.c_double)]
+
+
+class dcm_params(C.Structure):
+    _fields_ = [("rc_min", C.c_double), ("rc_max", C.c_double), ("alpha", C.c_double),
+                ("dt", C.c_double), ("mass", C.c_double), ("eps", C.c_double),
+                ("sigma", C.c_double), ("voxel", C.c_double), ("smooth_order", C.c_int32),
+                ("detect_every", C.c_int32), ("kmeans_max_iter", C.c_int32),
+                ("cfsm_iter_max", C.c_int32), ("cfsm_eps", C.c_double),
+                ("precision", C.c_int32), ("n_classes", C.c_int32), ("cell_min", C.c_double),
+                ("reserved", C.c_int32 * 8)]
+
+
+class dcm_tuning(C.Structure):
+    _fields_ = [("lanes", C.c_int32 * DCM_MAX_CLASSES), ("block", C.c_int32),
+                ("reserved", C.c_int32 * 7)]
+
+
+class dcm_stats(C.Structure):
+    _fields_ = [("step", C.c_int64), ("pairs", C.c_int64), ("kmeans_iters", C.c_int32),
+                ("cfsm_iters", C.c_int32), ("class_count", C.c_int32 * DCM_MAX_CLASSES),
+                ("grid", C.c_int32 * 3), ("cells", C.c_int32 * 3), ("c_liquid", C.c_double),
+                ("c_vapor", C.c_double), ("guard_rechecks", C.c_int64),
+                ("kernels_plain", C.c_int32), ("kernels_detect", C.c_int32),
+                ("reserved", C.c_int64 * 5)]
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libdcm.so (build it first with ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libdcm.so not built at {LIB_PATH}; run __graft_entry__.build()")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, i64, dp = C.c_void_p, C.c_int32, C.c_int64, C.c_void_p
+    P = C.POINTER
+    sig = {
+        "dcm_default_params": (None, [P(dcm_params)]),
+        "dcm_create": (C.c_int, [P(dcm_box), i64, P(dcm_params), vp, P(vp)]),
+        "dcm_destroy": (C.c_int, [vp]),
+        "dcm_set_state": (C.c_int, [vp, dp, dp, C.c_int]),
+        "dcm_get_state": (C.c_int, [vp, dp, dp, dp, C.c_int]),
+        "dcm_set_step": (C.c_int, [vp, i64]),
+        "dcm_set_cutoffs": (C.c_int, [vp, dp, C.c_int]),
+        "dcm_detect_interface": (C.c_int, [vp]),
+        "dcm_compute_forces": (C.c_int, [vp]),
+        "dcm_step": (C.c_int, [vp, i64]),
+        "dcm_energy_virial": (C.c_int, [vp, dp, dp, dp]),
+        "dcm_get_grid": (C.c_int, [vp, dp, dp, dp, dp, dp]),
+        "dcm_get_cutoffs": (C.c_int, [vp, dp, dp, dp]),
+        "dcm_get_cells": (C.c_int, [vp, dp, dp, dp]),
+        "dcm_get_pair_counts": (C.c_int, [vp, dp]),
+        "dcm_get_stats": (C.c_int, [vp, P(dcm_stats)]),
+        "dcm_set_tuning": (C.c_int, [vp, P(dcm_tuning)]),
+        "dcm_get_tuning": (C.c_int, [vp, P(dcm_tuning)]),
+        "dcm_sync": (C.c_int, [vp]),
+        "dcm_device_bytes": (i64, [vp]),
+        "dcm_estimate_bytes": (i64, [P(dcm_box), i64, P(dcm_params)]),
+        "dcm_last_error": (C.c_char_p, []),
+        "dcm_set_timing": (C.c_int, [vp, C.c_int]),
+        "dcm_get_phase_times": (C.c_int, [vp, dp]),
+        "dcm_version": (C.c_int, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def check(code: int) -> None:
+    if code != DCM_OK:
+        raise DcmError(code, lib().dcm_last_error().decode(errors="replace"))
+
+
+def _ptr(a):
+    """(pointer, mem) for a numpy array or a torch CUDA tensor."""
+    if a is None:
+        return None, DCM_HOST
+    if hasattr(a, "data_ptr") and getattr(a, "is_cuda", False):
+        return C.c_void_p(a.data_ptr()), DCM_DEVICE
+    return a.ctypes.data_as(C.c_void_p), DCM_HOST
+
+
+def default_params(**over) -> dcm_params:
+    p = dcm_params()
+    lib().dcm_default_params(C.byref(p))
+    for k, v in over.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+# ---- the C names ------------------------------------------------------------
+def dcm_create(box, n: int, params: dcm_params | None = None, stream=None):
+    h = C.c_void_p()
+    b = dcm_box(*box)
+    p = params if params is not None else default_params()
+    s = C.c_void_p(stream) if stream else None
+    check(lib().dcm_create(C.byref(b), int(n), C.byref(p), s, C.byref(h)))
+    return h
+
+
+def dcm_destroy(h) -> None:
+    check(lib().dcm_destroy(h))
+
+
+def dcm_set_state(h, x, v=None) -> None:
+    px, mx = _ptr(x)
+    pv, mv = _ptr(v)
+    if v is not None and mv != mx:
+        raise ValueError("x and v must live in the same memory space")
+    check(lib().dcm_set_state(h, px, pv, mx))
+
+
+def dcm_get_state(h, n: int):
+    x = np.empty((n, 3))
+    v = np.empty((n, 3))
+    f = np.empty((n, 3))
+    check(lib().dcm_get_state(h, _ptr(x)[0], _ptr(v)[0], _ptr(f)[0], DCM_HOST))
+    return x, v, f
+
+
+def dcm_set_step(h, step: int) -> None:
+    check(lib().dcm_set_step(h, int(step)))
+
+
+def dcm_set_cutoffs(h, rc) -> None:
+    p, m = _ptr(rc)
+    check(lib().dcm_set_cutoffs(h, p, m))
+
+
+def dcm_detect_interface(h) -> None:
+    check(lib().dcm_detect_interface(h))
+
+
+def dcm_compute_forces(h) -> None:
+    check(lib().dcm_compute_forces(h))
+
+
+def dcm_step(h, nsteps: int) -> None:
+    check(lib().dcm_step(h, int(nsteps)))
+
+
+def dcm_energy_virial(h):
+    pe, ke = C.c_double(), C.c_double()
+    w = (C.c_double * 6)()
+    check(lib().dcm_energy_virial(h, C.byref(pe), C.byref(ke), w))
+    return pe.value, ke.value, np.array(list(w))
+
+
+def dcm_get_grid(h):
+    dims = np.zeros(3, np.int32)
+    check(lib().dcm_get_grid(h, _ptr(dims)[0], None, None, None, None))
+    nv = int(np.prod(dims))
+    counts = np.empty(nv, np.int32)
+    sm = np.empty(nv)
+    lab = np.empty(nv, np.uint8)
+    dist = np.empty(nv)
+    check(lib().dcm_get_grid(h, _ptr(dims)[0], _ptr(counts)[0], _ptr(sm)[0], _ptr(lab)[0],
+                             _ptr(dist)[0]))
+    return tuple(int(q) for q in dims), counts, sm, lab, dist
+
+
+def dcm_get_cutoffs(h, n: int):
+    d = np.empty(n)
+    rc = np.empty(n)
+    cls = np.empty(n, np.uint8)
+    check(lib().dcm_get_cutoffs(h, _ptr(d)[0], _ptr(rc)[0], _ptr(cls)[0]))
+    return d, rc, cls
+
+
+def dcm_get_cells(h, n: int):
+    nc = np.zeros(3, np.int32)
+    check(lib().dcm_get_cells(h, _ptr(nc)[0], None, None))
+    ncell = int(np.prod(nc))
+    start = np.empty(ncell + 1, np.int32)
+    sid = np.empty(n, np.int32)
+    check(lib().dcm_get_cells(h, _ptr(nc)[0], _ptr(start)[0], _ptr(sid)[0]))
+    return tuple(int(q) for q in nc), start, sid
+
+
+def dcm_get_pair_counts(h, n: int):
+    out = np.empty(n, np.int32)
+    check(lib().dcm_get_pair_counts(h, _ptr(out)[0]))
+    return out
+
+
+def dcm_get_stats(h) -> dcm_stats:
+    s = dcm_stats()
+    check(lib().dcm_get_stats(h, C.byref(s)))
+    return s
+
+
+def dcm_set_tuning(h, lanes, block: int = 256) -> None:
+    t = dcm_tuning()
+    for q in range(DCM_MAX_CLASSES):
+        t.lanes[q] = int(lanes[min(q, len(lanes) - 1)])
+    t.block = int(block)
+    check(lib().dcm_set_tuning(h, C.byref(t)))
+
+
+def dcm_get_tuning(h) -> dcm_tuning:
+    t = dcm_tuning()
+    check(lib().dcm_get_tuning(h, C.byref(t)))
+    return t
+
+
+def dcm_set_timing(h, on: bool) -> None:
+    check(lib().dcm_set_timing(h, 1 if on else 0))
+
+
+def dcm_get_phase_times(h) -> dict:
+    ms = np.zeros(DCM_NUM_PHASES, np.float32)
+    check(lib().dcm_get_phase_times(h, ms.ctypes.data_as(C.c_void_p)))
+    return {k: float(v) for k, v in zip(PHASES, ms)}
+
+
+def dcm_sync(h) -> None:
+    check(lib().dcm_sync(h))
+
+
+def dcm_device_bytes(h) -> int:
+    return int(lib().dcm_device_bytes(h))
+
+
+def dcm_estimate_bytes(box, n: int, params: dcm_params | None = None) -> int:
+    b = dcm_box(*box)
+    p = params if params is not None else default_params()
+    return int(lib().dcm_estimate_bytes(C.byref(b), int(n), C.byref(p)))
+
+
+# ---- convenience wrapper ------------------------------------------------------
+class System:
+    """One DCM system on the GPU (a dcm_handle)."""
+
+    def __init__(self, box, n: int, params: dcm_params | None = None, stream=None, **over):
+        if params is None:
+            params = default_params(**over)
+        else:
+            for k, v in over.items():
+                setattr(params, k, v)
+        self.box = tuple(float(b) for b in box)
+        self.n = int(n)
+        self.params = params
+        self.h = dcm_create(self.box, self.n, params, stream)
+
+    def close(self):
+        if self.h:
+            dcm_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, x, v=None):
+        if not (hasattr(x, "is_cuda") and x.is_cuda):
+            x = np.ascontiguousarray(x, np.float64)
+            v = None if v is None else np.ascontiguousarray(v, np.float64)
+        dcm_set_state(self.h, x, v)
+
+    def get_state(self):
+        return dcm_get_state(self.h, self.n)
+
+    def set_cutoffs(self, rc):
+        dcm_set_cutoffs(self.h, np.ascontiguousarray(rc, np.float64))
+
+    def detect_interface(self):
+        dcm_detect_interface(self.h)
+
+    def compute_forces(self):
+        dcm_compute_forces(self.h)
+
+    def step(self, nsteps: int):
+        dcm_step(self.h, nsteps)
+
+    def energy_virial(self):
+        return dcm_energy_virial(self.h)
+
+    def grid(self):
+        return dcm_get_grid(self.h)
+
+    def cutoffs(self):
+        return dcm_get_cutoffs(self.h, self.n)
+
+    def cells(self):
+        return dcm_get_cells(self.h, self.n)
+
+    def pair_counts(self):
+        return dcm_get_pair_counts(self.h, self.n)
+
+    def stats(self) -> dcm_stats:
+        return dcm_get_stats(self.h)
+
+    def set_tuning(self, lanes, block=256):
+        dcm_set_tuning(self.h, lanes, block)
+
+    def sync(self):
+        dcm_sync(self.h)
+
+    def set_timing(self, on: bool = True):
+        dcm_set_timing(self.h, on)
+
+    def phase_times(self) -> dict:
+        return dcm_get_phase_times(self.h)
+
+    def device_bytes(self) -> int:
+        return dcm_device_bytes(self.h)

