@@ -182,6 +182,31 @@ int dcm_get_tuning(dcm_handle *h, dcm_tuning *t);
 int dcm_set_timing(dcm_handle *h, int on);
 int dcm_get_phase_times(dcm_handle *h, float ms[DCM_NUM_PHASES]);
 
+/* ---- ensembles: many independent systems in one handle --------------------
+ * Batched form of the same method (no counterpart in the thesis, which runs
+ * one system per MPI job): count systems of their own box, size and
+ * parameters share one handle; every kernel of a step covers all of them
+ * and the force kernel is a single persistent launch draining one work
+ * queue over every system and cutoff class, so small systems fill the GPU
+ * together.  Precision, detect_every, n_classes and smooth_order must be
+ * the same for all systems.  Particles of system k occupy the slots
+ * [first, first + count) of the concatenated arrays that dcm_set_state,
+ * dcm_get_state, dcm_set_cutoffs, dcm_get_cutoffs and dcm_get_pair_counts
+ * use; dcm_energy_virial returns the sums over all systems; dcm_get_grid and
+ * dcm_get_cells describe system 0.  dcm_create is the count = 1 case. */
+int dcm_ensemble_create(int count, const dcm_box *boxes, const int64_t *n,
+                        const dcm_params *params, void *stream, dcm_handle **out);
+int dcm_system_count(const dcm_handle *h);
+int dcm_system_range(const dcm_handle *h, int k, int64_t *first, int64_t *count);
+/* state of system k alone (AoS double[3*count]); set marks cutoffs and
+ * forces of the whole handle stale */
+int dcm_ensemble_set_state(dcm_handle *h, int k, const double *x, const double *v,
+                           int mem);
+int dcm_ensemble_get_state(dcm_handle *h, int k, double *x, double *v, double *f,
+                           int mem);
+int dcm_ensemble_energy_virial(dcm_handle *h, int k, double *pe, double *ke,
+                               double w[6]);
+
 /* Waits for the handle's stream; returns the sticky device error, if any. */
 int dcm_sync(dcm_handle *h);
 /* Total device bytes the handle holds. */

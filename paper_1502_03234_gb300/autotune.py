@@ -1,0 +1,127 @@
+"""Autotuner of the DCM force kernel's launch shape.
+
+Tunes, on the live system, (a) the link-cell edge (a fraction of r_c,min:
+smaller cells trim the candidate volume towards the cutoff sphere, larger
+ones cut per-row overhead), (b) the threads per block and (c) per cutoff
+class the number of lanes that share one particle (1..32).  Interfacial
+classes (large r_c, 8-13x the pairs of bulk particles) want more lanes; the
+bulk wants fewer lanes and less per-row overhead.  The search is a
+coordinate descent over the classes, heaviest class first, timed with the
+library's per-phase CUDA events (the force phase of real steps).
+
+Results are cached per (N bucket, r_c,min, r_c,max, precision) in a JSON
+file, so systems of similar size reuse the choice without re-tuning.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import statistics
+from dataclasses import asdict, dataclass, field
+
+from . import dcm
+
+CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_tuning_cache.json")
+LANES = (1, 2, 4, 8, 16, 32)
+CELL_FRACTIONS = (1.0 / 3.0, 0.4, 0.5, 2.0 / 3.0)
+BLOCKS = (128, 256)
+
+
+@dataclass
+class Tuning:
+    cell_min: float
+    block: int
+    lanes: list = field(default_factory=lambda: [4, 8, 8, 8, 8, 8, 8, 8])
+    force_ms: float = float("nan")
+
+
+def key(n: int, rc_min: float, rc_max: float, precision: int) -> str:
+    return f"n2^{round(math.log2(max(n, 1)))}|rc{rc_min:g}/{rc_max:g}|p{precision}"
+
+
+def load_cache(path: str = CACHE) -> dict:
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def save_cache(cache: dict, path: str = CACHE) -> None:
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "w") as fh:
+        json.dump(cache, fh, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def force_ms(sy: dcm.System, reps: int = 5) -> float:
+    """median device time of the force phase over reps steps"""
+    sy.set_timing(True)
+    sy.step(1)
+    out = []
+    for _ in range(reps):
+        sy.step(1)
+        out.append(sy.phase_times()["force"])
+    return statistics.median(out)
+
+
+def _system(box, x, v, params: dcm.dcm_params, cell_min: float, stream=None) -> dcm.System:
+    p = dcm.dcm_params.from_buffer_copy(params)
+    p.cell_min = cell_min
+    sy = dcm.System(box, len(x), p, stream=stream)
+    sy.set_state(x, v)
+    sy.compute_forces()
+    return sy
+
+
+def tune(box, x, v, params: dcm.dcm_params, *, reps: int = 5, stream=None,
+         fractions=CELL_FRACTIONS, blocks=BLOCKS, lanes=LANES, log=None) -> Tuning:
+    """Search cell edge x block x lanes-per-class on this system's state."""
+    K = params.n_classes
+    best: Tuning | None = None
+    for frac in fractions:
+        cell = frac * params.rc_min
+        try:
+            sy = _system(box, x, v, params, cell, stream)
+        except dcm.DcmError:
+            continue
+        try:
+            for block in blocks:
+                cur = [4] + [8] * (dcm.DCM_MAX_CLASSES - 1)
+                sy.set_tuning(cur, block)
+                t_cur = force_ms(sy, reps)
+                for q in reversed(range(K)):          # heaviest class first
+                    for G in lanes:
+                        if G == cur[q]:
+                            continue
+                        trial = list(cur)
+                        trial[q] = G
+                        sy.set_tuning(trial, block)
+                        t = force_ms(sy, reps)
+                        if t < t_cur:
+                            cur, t_cur = trial, t
+                if log:
+                    log(f"cell {cell:.3f} block {block} lanes {cur[:K]} force {t_cur:.4f} ms")
+                if best is None or t_cur < best.force_ms:
+                    best = Tuning(cell_min=cell, block=block, lanes=cur, force_ms=t_cur)
+        finally:
+            sy.close()
+    if best is None:
+        raise RuntimeError("autotune: no cell size fits this box")
+    return best
+
+
+def tuned_system(box, x, v, params: dcm.dcm_params, *, stream=None, cache_path: str = CACHE,
+                 retune: bool = False, log=None) -> tuple[dcm.System, Tuning]:
+    """A system built with the cached (or freshly tuned) launch shape."""
+    cache = load_cache(cache_path)
+    k = key(len(x), params.rc_min, params.rc_max, params.precision)
+    if retune or k not in cache:
+        t = tune(box, x, v, params, stream=stream, log=log)
+        cache[k] = asdict(t)
+        save_cache(cache, cache_path)
+    t = Tuning(**cache[k])
+    sy = _system(box, x, v, params, t.cell_min, stream)
+    sy.set_tuning(t.lanes, t.block)
+    return sy, t

@@ -31,31 +31,34 @@ int fail_cuda(cudaError_t e, const char *what, const char *file, int line)
     return fail(code, "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
 }
 
-// AoS [N][3] -> SoA [3][N], wrapping into the box
-__global__ void k_aos_to_soa(int n, const double *__restrict__ in, double *out, double L0, double L1,
-                             double L2, int wrap)
+// AoS [n][3] -> SoA slice [3][N] at particles p0 .. p0+n, wrapping positions
+// into their system's box
+__global__ void k_aos_to_soa(Batch b, int64_t p0, int64_t n, const double *__restrict__ in,
+                             double *out, int wrap)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double L[3] = {L0, L1, L2};
+    const Geom &g = b.sys[sys_of(b.p_off, b.M, p0 + i)];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        double v = in[3 * (size_t)i + a];
+        double v = in[3 * i + a];
         if (wrap) {
-            if (v < 0.0 || v >= L[a]) v = DSUB(v, DMUL(L[a], floor(__ddiv_rn(v, L[a]))));
-            v = wrap_coord(v, L[a]);
-            if (!(v >= 0.0 && v < L[a])) v = 0.0;
+            double L = g.L[a];
+            if (v < 0.0 || v >= L) v = DSUB(v, DMUL(L, floor(__ddiv_rn(v, L))));
+            v = wrap_coord(v, L);
+            if (!(v >= 0.0 && v < L)) v = 0.0;
         }
-        out[(size_t)a * n + i] = v;
+        out[(size_t)a * b.N + p0 + i] = v;
     }
 }
 
-__global__ void k_soa_to_aos(int n, const double *__restrict__ in, double *out)
+__global__ void k_soa_to_aos(int64_t N, int64_t p0, int64_t n, const double *__restrict__ in,
+                             double *out)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) out[3 * (size_t)i + a] = in[(size_t)a * n + i];
+    for (int a = 0; a < 3; ++a) out[3 * i + a] = in[(size_t)a * N + p0 + i];
 }
 
 static inline int nblk(int64_t n, int b) { return (int)((n + b - 1) / b); }
@@ -171,13 +174,23 @@ static int setup_geometry(const dcm_box *box, int64_t n, const dcm_params *p, Ge
     g.hdtm = 0.5 * p->dt / p->mass;
     g.eps = p->eps;
     g.sigma = p->sigma;
+    g.eps24 = 24.0 * p->eps;
+    g.eps48 = 48.0 * p->eps;
+    g.eps2 = 2.0 * p->eps;
+    g.sig2 = p->sigma * p->sigma;
+    g.eps24f = (float)g.eps24;
+    g.eps48f = (float)g.eps48;
+    g.eps2f = (float)g.eps2;
+    g.sig2f = (float)g.sig2;
+    g.ncell = (int64_t)g.nc[0] * g.nc[1] * g.nc[2];
+    g.nvox = (int64_t)g.gd[0] * g.gd[1] * g.gd[2];
     return DCM_OK;
 }
 
 static int64_t bytes_for(const Geom &g, int64_t n, int precision)
 {
-    int64_t ncell = (int64_t)g.nc[0] * g.nc[1] * g.nc[2];
-    int64_t nv = (int64_t)g.gd[0] * g.gd[1] * g.gd[2];
+    int64_t ncell = g.ncell;
+    int64_t nv = g.nvox;
     int64_t per_p = 3 * 8 * 3 + 8 + 8 + 1 + 4 * 3 + 16 + 4 + 4 + 8 + 48 + 24;
     if (precision == DCM_FP64) per_p += 32;
     int64_t per_v = 4 + 4 + 4 + 8 + 1 + 8 + 8 + 4 + 16;
@@ -218,35 +231,75 @@ extern "C" int dcm_destroy(dcm_handle *h)
                     h->cell_start, h->sorted_id, h->scan_tmp, h->sp4, h->spd, h->class_list,
                     h->class_count_dev, h->B, h->sm1, h->sm2, h->Bs, h->S, h->D0, h->D1, h->stamp,
                     h->flist, h->fcount, h->kacc, h->npair, h->pe, h->vir, h->red_part, h->red_out,
-                    h->err, h->stats, h->tmp3n};
+                    h->err, h->stats, h->tmp3n, h->geo_dev, h->off_dev};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete[] h->geo_host;
+    delete[] h->par_host;
+    delete[] h->off_host;
     delete h;
     return DCM_OK;
 }
 
-extern "C" int dcm_create(const dcm_box *box, int64_t n, const dcm_params *p, void *stream,
-                          dcm_handle **out)
+// one creation path for M >= 1 systems; the shared run-time fields
+// (precision, detection cadence and caps, classes, smoothing) come from
+// system 0's parameters and must agree across systems
+static int create_systems(int M, const dcm_box *boxes, const int64_t *ns, const dcm_params *ps,
+                          void *stream, dcm_handle **out)
 {
     if (!out) return fail(DCM_ERR_ARG, "null out");
     *out = nullptr;
-    int rc = check_params(box, n, p);
-    if (rc) return rc;
+    if (M < 1 || M > MAX_SYSTEMS) return fail(DCM_ERR_ARG, "system count must be 1..%d", MAX_SYSTEMS);
+    if (!boxes || !ns || !ps) return fail(DCM_ERR_ARG, "null boxes, sizes or params");
+    int64_t ntot = 0;
+    for (int k = 0; k < M; ++k) {
+        int rc = check_params(&boxes[k], ns[k], &ps[k]);
+        if (rc) return rc;
+        const dcm_params &a = ps[0], &q = ps[k];
+        if (q.precision != a.precision || q.detect_every != a.detect_every ||
+            q.n_classes != a.n_classes || q.smooth_order != a.smooth_order)
+            return fail(DCM_ERR_ARG, "system %d: precision, detect_every, n_classes and "
+                                     "smooth_order must match system 0", k);
+        ntot += ns[k];
+    }
+    if (ntot > (int64_t)0x7fffffff / 4) return fail(DCM_ERR_ARG, "too many particles in total");
     dcm_handle *h = new dcm_handle();
     memset((void *)h, 0, sizeof(*h));
-    h->box = *box;
-    h->n = n;
-    h->p = *p;
+    h->M = M;
+    h->box = boxes[0];
+    h->n = ntot;
+    h->p = ps[0];
     if (h->p.kmeans_max_iter <= 0) h->p.kmeans_max_iter = 100;
-    rc = setup_geometry(box, n, p, h->g);
-    if (rc) {
-        delete h;
-        return rc;
+    h->geo_host = new Geom[M];
+    h->par_host = new dcm_params[M];
+    h->off_host = new int64_t[3 * (M + 1)];
+    int64_t *po = h->off_host, *co = po + (M + 1), *vo = co + (M + 1);
+    po[0] = co[0] = vo[0] = 0;
+    for (int k = 0; k < M; ++k) {
+        h->par_host[k] = ps[k];
+        int rc = setup_geometry(&boxes[k], ns[k], &ps[k], h->geo_host[k]);
+        if (rc) {
+            dcm_destroy(h);
+            return rc;
+        }
+        Geom &g = h->geo_host[k];
+        g.K = ps[0].n_classes;
+        g.p0 = po[k];
+        g.c0 = co[k];
+        g.v0 = vo[k];
+        po[k + 1] = po[k] + ns[k];
+        co[k + 1] = co[k] + g.ncell;
+        vo[k + 1] = vo[k] + g.nvox;
     }
+    if (co[M] > (int64_t)0x7fffffff - 2 || vo[M] > (int64_t)0x7fffffff / 4) {
+        dcm_destroy(h);
+        return fail(DCM_ERR_ARG, "too many cells or voxels in total");
+    }
+    h->g = h->geo_host[0];
     // default launch shape: more lanes for larger cutoff classes
-    for (int q = 0; q < DCM_MAX_CLASSES; ++q) h->tune.lanes[q] = q == 0 ? 4 : 8;
-    h->tune.block = 256;
+    for (int q = 0; q < DCM_MAX_CLASSES; ++q) h->tune.lanes[q] = q == 0 ? 2 : (q == 1 ? 1 : 2);
+    h->tune.block = 128;
     cudaGetDevice(&h->device);
     cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
     if (stream) {
@@ -254,20 +307,23 @@ extern "C" int dcm_create(const dcm_box *box, int64_t n, const dcm_params *p, vo
     } else {
         cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) {
-            delete h;
+            dcm_destroy(h);
             return fail_cuda(e, "cudaStreamCreate", __FILE__, __LINE__);
         }
         h->own_stream = true;
     }
-    h->ncell = (int64_t)h->g.nc[0] * h->g.nc[1] * h->g.nc[2];
-    h->nvox = (int64_t)h->g.gd[0] * h->g.gd[1] * h->g.gd[2];
-    int64_t N = n, nc = h->ncell, nv = h->nvox;
+    h->ncell = co[M];
+    h->nvox = vo[M];
+    int64_t N = ntot, nc = h->ncell, nv = h->nvox;
     int64_t ntiles = (nc + 2047) / 2048 + 1;
+    int rc;
 #define ALLOC(ptr, cnt)                 \
     if ((rc = dalloc(h, &(ptr), (cnt)))) { \
         dcm_destroy(h);                 \
         return rc;                      \
     }
+    ALLOC(h->geo_dev, M);
+    ALLOC(h->off_dev, 3 * (M + 1));
     ALLOC(h->x, 3 * N);
     ALLOC(h->v, 3 * N);
     ALLOC(h->f, 3 * N);
@@ -282,7 +338,7 @@ extern "C" int dcm_create(const dcm_box *box, int64_t n, const dcm_params *p, vo
     ALLOC(h->cell_start, nc + 1);
     ALLOC(h->scan_tmp, ntiles);
     ALLOC(h->sp4, N);
-    if (p->precision == DCM_FP64) ALLOC(h->spd, N);
+    if (h->p.precision == DCM_FP64) ALLOC(h->spd, N);
     ALLOC(h->class_list, N);
     ALLOC(h->class_count_dev, 3 * DCM_MAX_CLASSES);
     ALLOC(h->B, nv);
@@ -295,15 +351,27 @@ extern "C" int dcm_create(const dcm_box *box, int64_t n, const dcm_params *p, vo
     ALLOC(h->stamp, nv);
     ALLOC(h->flist, 4 * nv);
     ALLOC(h->fcount, 4);
-    ALLOC(h->kacc, 16);
+    ALLOC(h->kacc, 9 * (int64_t)M);
     ALLOC(h->npair, N);
     ALLOC(h->pe, N);
     ALLOC(h->vir, 6 * N);
     ALLOC(h->red_part, 256 * 8);
-    ALLOC(h->red_out, 8);
+    ALLOC(h->red_out, 8 * (int64_t)M);
     ALLOC(h->err, 1);
     ALLOC(h->stats, 1);
 #undef ALLOC
+    h->b.sys = h->geo_dev;
+    h->b.p_off = h->off_dev;
+    h->b.c_off = h->off_dev + (M + 1);
+    h->b.v_off = h->off_dev + 2 * (M + 1);
+    h->b.M = M;
+    h->b.K = h->p.n_classes;
+    h->b.N = N;
+    h->b.NC = nc;
+    h->b.NV = nv;
+    cudaMemcpyAsync(h->geo_dev, h->geo_host, sizeof(Geom) * M, cudaMemcpyHostToDevice, h->stream);
+    cudaMemcpyAsync(h->off_dev, h->off_host, sizeof(int64_t) * 3 * (M + 1), cudaMemcpyHostToDevice,
+                    h->stream);
     cudaMemsetAsync(h->err, 0, sizeof(int), h->stream);
     cudaMemsetAsync(h->stats, 0, sizeof(DevStats), h->stream);
     cudaMemsetAsync(h->v, 0, sizeof(double) * 3 * N, h->stream);
@@ -314,7 +382,35 @@ extern "C" int dcm_create(const dcm_box *box, int64_t n, const dcm_params *p, vo
         dcm_destroy(h);
         return fail_cuda(e, "create sync", __FILE__, __LINE__);
     }
+    rc = prepare_kernels(h);
+    if (rc) {
+        dcm_destroy(h);
+        return rc;
+    }
     *out = h;
+    return DCM_OK;
+}
+
+extern "C" int dcm_create(const dcm_box *box, int64_t n, const dcm_params *p, void *stream,
+                          dcm_handle **out)
+{
+    if (!box || !p) return fail(DCM_ERR_ARG, "null box or params");
+    return create_systems(1, box, &n, p, stream, out);
+}
+
+extern "C" int dcm_ensemble_create(int count, const dcm_box *boxes, const int64_t *n,
+                                   const dcm_params *params, void *stream, dcm_handle **out)
+{
+    return create_systems(count, boxes, n, params, stream, out);
+}
+
+extern "C" int dcm_system_count(const dcm_handle *h) { return h ? h->M : 0; }
+
+extern "C" int dcm_system_range(const dcm_handle *h, int k, int64_t *first, int64_t *count)
+{
+    if (!h || k < 0 || k >= h->M) return fail(DCM_ERR_ARG, "bad handle or system index");
+    if (first) *first = h->geo_host[k].p0;
+    if (count) *count = h->geo_host[k].n;
     return DCM_OK;
 }
 
@@ -326,24 +422,24 @@ static void invalidate_graphs(dcm_handle *h)
     h->graphs_ready = false;
 }
 
-extern "C" int dcm_set_state(dcm_handle *h, const double *x, const double *v, int mem)
+static int set_state_range(dcm_handle *h, int64_t p0, int64_t n, const double *x,
+                           const double *v, int mem)
 {
-    if (!h || !x) return fail(DCM_ERR_ARG, "null handle or positions");
-    int64_t N = h->n;
-    size_t bytes = sizeof(double) * 3 * (size_t)N;
+    size_t bytes = sizeof(double) * 3 * (size_t)n;
     const double *src[2] = {x, v};
     double *dst[2] = {h->x, h->v};
     for (int q = 0; q < 2; ++q) {
         if (!src[q]) {
-            DCM_CHECK_CUDA(cudaMemsetAsync(dst[q], 0, bytes, h->stream));
+            for (int a = 0; a < 3; ++a)
+                DCM_CHECK_CUDA(cudaMemsetAsync(dst[q] + (size_t)a * h->n + p0, 0,
+                                               sizeof(double) * n, h->stream));
             continue;
         }
         DCM_CHECK_CUDA(cudaMemcpyAsync(h->tmp3n, src[q], bytes,
                                        mem == DCM_DEVICE ? cudaMemcpyDeviceToDevice
                                                          : cudaMemcpyHostToDevice,
                                        h->stream));
-        k_aos_to_soa<<<nblk(N, 256), 256, 0, h->stream>>>((int)N, h->tmp3n, dst[q], h->g.L[0],
-                                                           h->g.L[1], h->g.L[2], q == 0);
+        k_aos_to_soa<<<nblk(n, 256), 256, 0, h->stream>>>(h->b, p0, n, h->tmp3n, dst[q], q == 0);
     }
     DCM_CHECK_CUDA(cudaGetLastError());
     if (mem != DCM_DEVICE) DCM_CHECK_CUDA(cudaStreamSynchronize(h->stream));
@@ -351,8 +447,48 @@ extern "C" int dcm_set_state(dcm_handle *h, const double *x, const double *v, in
     h->have_cut = false;
     h->forces_valid = false;
     h->cells_valid = false;
-    h->step = 0;
     return DCM_OK;
+}
+
+static int get_state_range(dcm_handle *h, int64_t p0, int64_t n, double *x, double *v, double *f,
+                           int mem)
+{
+    size_t bytes = sizeof(double) * 3 * (size_t)n;
+    double *src[3] = {h->x, h->v, h->f};
+    double *dst[3] = {x, v, f};
+    for (int q = 0; q < 3; ++q) {
+        if (!dst[q]) continue;
+        k_soa_to_aos<<<nblk(n, 256), 256, 0, h->stream>>>(h->n, p0, n, src[q], h->tmp3n);
+        DCM_CHECK_CUDA(cudaGetLastError());
+        DCM_CHECK_CUDA(cudaMemcpyAsync(dst[q], h->tmp3n, bytes,
+                                       mem == DCM_DEVICE ? cudaMemcpyDeviceToDevice
+                                                         : cudaMemcpyDeviceToHost,
+                                       h->stream));
+        if (mem != DCM_DEVICE) DCM_CHECK_CUDA(cudaStreamSynchronize(h->stream));
+    }
+    return DCM_OK;
+}
+
+extern "C" int dcm_set_state(dcm_handle *h, const double *x, const double *v, int mem)
+{
+    if (!h || !x) return fail(DCM_ERR_ARG, "null handle or positions");
+    int r = set_state_range(h, 0, h->n, x, v, mem);
+    if (!r) h->step = 0;
+    return r;
+}
+
+extern "C" int dcm_ensemble_set_state(dcm_handle *h, int k, const double *x, const double *v,
+                                      int mem)
+{
+    if (!h || !x || k < 0 || k >= h->M) return fail(DCM_ERR_ARG, "bad handle, system or positions");
+    return set_state_range(h, h->geo_host[k].p0, h->geo_host[k].n, x, v, mem);
+}
+
+extern "C" int dcm_ensemble_get_state(dcm_handle *h, int k, double *x, double *v, double *f,
+                                      int mem)
+{
+    if (!h || k < 0 || k >= h->M) return fail(DCM_ERR_ARG, "bad handle or system");
+    return get_state_range(h, h->geo_host[k].p0, h->geo_host[k].n, x, v, f, mem);
 }
 
 extern "C" int dcm_set_step(dcm_handle *h, int64_t step)
@@ -365,21 +501,7 @@ extern "C" int dcm_set_step(dcm_handle *h, int64_t step)
 extern "C" int dcm_get_state(dcm_handle *h, double *x, double *v, double *f, int mem)
 {
     if (!h) return fail(DCM_ERR_ARG, "null handle");
-    int64_t N = h->n;
-    size_t bytes = sizeof(double) * 3 * (size_t)N;
-    double *src[3] = {h->x, h->v, h->f};
-    double *dst[3] = {x, v, f};
-    for (int q = 0; q < 3; ++q) {
-        if (!dst[q]) continue;
-        k_soa_to_aos<<<nblk(N, 256), 256, 0, h->stream>>>((int)N, src[q], h->tmp3n);
-        DCM_CHECK_CUDA(cudaGetLastError());
-        DCM_CHECK_CUDA(cudaMemcpyAsync(dst[q], h->tmp3n, bytes,
-                                       mem == DCM_DEVICE ? cudaMemcpyDeviceToDevice
-                                                         : cudaMemcpyDeviceToHost,
-                                       h->stream));
-        if (mem != DCM_DEVICE) DCM_CHECK_CUDA(cudaStreamSynchronize(h->stream));
-    }
-    return DCM_OK;
+    return get_state_range(h, 0, h->n, x, v, f, mem);
 }
 
 extern "C" int dcm_set_cutoffs(dcm_handle *h, const double *rc, int mem)
@@ -388,10 +510,13 @@ extern "C" int dcm_set_cutoffs(dcm_handle *h, const double *rc, int mem)
     int64_t N = h->n;
     std::vector<double> tmp;
     if (mem != DCM_DEVICE) {
-        for (int64_t i = 0; i < N; ++i)
-            if (!(rc[i] >= h->p.rc_min && rc[i] <= h->p.rc_max))
-                return fail(DCM_ERR_ARG, "cutoff %lld = %g outside [rc_min, rc_max]",
-                            (long long)i, rc[i]);
+        for (int k = 0; k < h->M; ++k) {
+            const Geom &g = h->geo_host[k];
+            for (int64_t i = g.p0; i < g.p0 + g.n; ++i)
+                if (!(rc[i] >= g.rc_min && rc[i] <= g.rc_max))
+                    return fail(DCM_ERR_ARG, "cutoff %lld = %g outside [rc_min, rc_max]",
+                                (long long)i, rc[i]);
+        }
     }
     DCM_CHECK_CUDA(cudaMemcpyAsync(h->rc, rc, sizeof(double) * N,
                                    mem == DCM_DEVICE ? cudaMemcpyDeviceToDevice
@@ -535,21 +660,47 @@ extern "C" int dcm_get_phase_times(dcm_handle *h, float ms[DCM_NUM_PHASES])
     return DCM_OK;
 }
 
-extern "C" int dcm_energy_virial(dcm_handle *h, double *pe, double *ke, double w[6])
+static int energies(dcm_handle *h, std::vector<double> &out)
 {
-    if (!h) return fail(DCM_ERR_ARG, "null handle");
     if (!h->have_state) return fail(DCM_ERR_STATE, "no state set");
     int r = forces_now(h, true);
     if (r) return r;
-    r = launch_reduce_energy(h);
+    for (int k = 0; k < h->M && !r; ++k) r = launch_reduce_energy(h, k);
     if (r) return r;
-    double out[8];
-    DCM_CHECK_CUDA(cudaMemcpyAsync(out, h->red_out, sizeof(out), cudaMemcpyDeviceToHost, h->stream));
+    out.resize(8 * (size_t)h->M);
+    DCM_CHECK_CUDA(cudaMemcpyAsync(out.data(), h->red_out, sizeof(double) * out.size(),
+                                   cudaMemcpyDeviceToHost, h->stream));
     DCM_CHECK_CUDA(cudaStreamSynchronize(h->stream));
-    if (pe) *pe = out[0];
-    if (ke) *ke = 0.5 * h->p.mass * out[1];
+    return DCM_OK;
+}
+
+static void energy_of(const dcm_handle *h, const double *o, int k, double *pe, double *ke,
+                      double *w, bool add)
+{
+    double m = h->par_host[k].mass;
+    if (pe) *pe = (add ? *pe : 0.0) + o[0];
+    if (ke) *ke = (add ? *ke : 0.0) + 0.5 * m * o[1];
     if (w)
-        for (int q = 0; q < 6; ++q) w[q] = out[2 + q];
+        for (int q = 0; q < 6; ++q) w[q] = (add ? w[q] : 0.0) + o[2 + q];
+}
+
+extern "C" int dcm_energy_virial(dcm_handle *h, double *pe, double *ke, double w[6])
+{
+    if (!h) return fail(DCM_ERR_ARG, "null handle");
+    std::vector<double> out;
+    int r = energies(h, out);
+    if (r) return r;
+    for (int k = 0; k < h->M; ++k) energy_of(h, out.data() + 8 * k, k, pe, ke, w, k > 0);
+    return DCM_OK;
+}
+
+extern "C" int dcm_ensemble_energy_virial(dcm_handle *h, int k, double *pe, double *ke, double w[6])
+{
+    if (!h || k < 0 || k >= h->M) return fail(DCM_ERR_ARG, "bad handle or system");
+    std::vector<double> out;
+    int r = energies(h, out);
+    if (r) return r;
+    energy_of(h, out.data() + 8 * k, k, pe, ke, w, false);
     return DCM_OK;
 }
 
@@ -559,7 +710,7 @@ extern "C" int dcm_get_grid(dcm_handle *h, int32_t dims[3], int32_t *counts, dou
     if (!h) return fail(DCM_ERR_ARG, "null handle");
     if (dims)
         for (int a = 0; a < 3; ++a) dims[a] = h->g.gd[a];
-    size_t nv = (size_t)h->nvox;
+    size_t nv = (size_t)h->g.nvox;   // system 0 (voxels of system 0 come first)
     if (counts) DCM_CHECK_CUDA(cudaMemcpyAsync(counts, h->B, 4 * nv, cudaMemcpyDeviceToHost, h->stream));
     if (smoothed)
         DCM_CHECK_CUDA(cudaMemcpyAsync(smoothed, h->Bs, 8 * nv, cudaMemcpyDeviceToHost, h->stream));
@@ -594,11 +745,12 @@ extern "C" int dcm_get_cells(dcm_handle *h, int32_t nc[3], int32_t *cell_start, 
     if (!h) return fail(DCM_ERR_ARG, "null handle");
     if (nc)
         for (int a = 0; a < 3; ++a) nc[a] = h->g.nc[a];
+    // system 0: its cells and sorted slots come first in the concatenation
     if (cell_start)
-        DCM_CHECK_CUDA(cudaMemcpyAsync(cell_start, h->cell_start, 4 * (size_t)(h->ncell + 1),
+        DCM_CHECK_CUDA(cudaMemcpyAsync(cell_start, h->cell_start, 4 * (size_t)(h->g.ncell + 1),
                                        cudaMemcpyDeviceToHost, h->stream));
     if (sorted_id)
-        DCM_CHECK_CUDA(cudaMemcpyAsync(sorted_id, h->sorted_id, 4 * (size_t)h->n,
+        DCM_CHECK_CUDA(cudaMemcpyAsync(sorted_id, h->sorted_id, 4 * (size_t)h->g.n,
                                        cudaMemcpyDeviceToHost, h->stream));
     DCM_CHECK_CUDA(cudaStreamSynchronize(h->stream));
     return DCM_OK;
@@ -629,7 +781,7 @@ extern "C" int dcm_get_stats(dcm_handle *h, dcm_stats *s)
     s->pairs = (int64_t)st.pairs;
     s->kmeans_iters = st.kmeans_iters;
     s->cfsm_iters = st.cfsm_iters;
-    for (int q = 0; q < h->g.K; ++q) s->class_count[q] = cc[q];
+    for (int q = 0; q < h->b.K; ++q) s->class_count[q] = cc[q];
     for (int a = 0; a < 3; ++a) {
         s->grid[a] = h->g.gd[a];
         s->cells[a] = h->g.nc[a];

@@ -16,15 +16,17 @@ constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 
 // cell of every particle + its arrival slot within the cell (atomic order;
 // the order inside a cell is fixed afterwards by k_cell_sort)
-__global__ void k_cell_count(Geom g, const double *__restrict__ x, int32_t *cell_of,
+// (cells of all systems are concatenated: cell_of holds the global index)
+__global__ void k_cell_count(Batch b, const double *__restrict__ x, int32_t *cell_of,
                              int32_t *slot, int32_t *count)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.n) return;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b.N) return;
+    const Geom &g = b.sys[sys_of(b.p_off, b.M, i)];
     int cx = bin_of(x[i], g.inv_c[0], g.nc[0]);
-    int cy = bin_of(x[(size_t)g.n + i], g.inv_c[1], g.nc[1]);
-    int cz = bin_of(x[2 * (size_t)g.n + i], g.inv_c[2], g.nc[2]);
-    int c = cx + g.nc[0] * (cy + g.nc[1] * cz);
+    int cy = bin_of(x[(size_t)b.N + i], g.inv_c[1], g.nc[1]);
+    int cz = bin_of(x[2 * (size_t)b.N + i], g.inv_c[2], g.nc[2]);
+    int c = (int)g.c0 + cx + g.nc[0] * (cy + g.nc[1] * cz);
     cell_of[i] = c;
     slot[i] = atomicAdd(&count[c], 1);
 }
@@ -112,17 +114,19 @@ __global__ void k_cell_sort(int64_t ncell, const int32_t *__restrict__ start, in
 
 // sorted position streams: sp4 = (x - cell corner in FP32, cell x index),
 // spd = absolute FP64 position (FP64 path only)
-__global__ void k_gather(Geom g, const double *__restrict__ x, const int32_t *__restrict__ sorted_id,
+__global__ void k_gather(Batch b, const double *__restrict__ x, const int32_t *__restrict__ sorted_id,
                          const int32_t *__restrict__ cell_of, float4 *sp4, double4_32a *spd)
 {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= g.n) return;
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= b.N) return;
+    // sorted slots keep the systems' particle ranges
+    const Geom &g = b.sys[sys_of(b.p_off, b.M, k)];
     int i = sorted_id[k];
-    int c = cell_of[i];
+    int c = cell_of[i] - (int)g.c0;
     int cx = c % g.nc[0];
     int cy = (c / g.nc[0]) % g.nc[1];
     int cz = c / (g.nc[0] * g.nc[1]);
-    double px = x[i], py = x[(size_t)g.n + i], pz = x[2 * (size_t)g.n + i];
+    double px = x[i], py = x[(size_t)b.N + i], pz = x[2 * (size_t)b.N + i];
     float ux = (float)DSUB(px, DMUL((double)cx, g.cedge[0]));
     float uy = (float)DSUB(py, DMUL((double)cy, g.cedge[1]));
     float uz = (float)DSUB(pz, DMUL((double)cz, g.cedge[2]));
@@ -182,7 +186,7 @@ int launch_bin(dcm_handle *h)
     cudaStream_t s = h->stream;
     int n = (int)h->n;
     cudaMemsetAsync(h->cell_count, 0, sizeof(int32_t) * h->ncell, s);
-    k_cell_count<<<nblk(n, 256), 256, 0, s>>>(h->g, h->x, h->cell_of, h->slot, h->cell_count);
+    k_cell_count<<<nblk(n, 256), 256, 0, s>>>(h->b, h->x, h->cell_of, h->slot, h->cell_count);
     int ntiles = nblk(h->ncell, SCAN_TILE);
     k_scan_tiles<<<ntiles, SCAN_THREADS, 0, s>>>(h->cell_count, h->cell_start, h->scan_tmp,
                                                  h->ncell);
@@ -190,10 +194,10 @@ int launch_bin(dcm_handle *h)
     k_cell_scatter<<<nblk(n, 256), 256, 0, s>>>(n, h->cell_of, h->slot, h->cell_start,
                                                 h->sorted_id);
     k_cell_sort<<<nblk(h->ncell, 256), 256, 0, s>>>(h->ncell, h->cell_start, h->sorted_id);
-    k_gather<<<nblk(n, 256), 256, 0, s>>>(h->g, h->x, h->sorted_id, h->cell_of, h->sp4,
+    k_gather<<<nblk(n, 256), 256, 0, s>>>(h->b, h->x, h->sorted_id, h->cell_of, h->sp4,
                                           h->p.precision == DCM_FP64 ? h->spd : nullptr);
     // class lists of sorted slots for the per-class force launches
-    int K = h->g.K;
+    int K = h->b.K;
     cudaMemsetAsync(h->class_count_dev, 0, sizeof(int32_t) * 3 * DCM_MAX_CLASSES, s);
     k_class_count<<<nblk(n, 256), 256, 0, s>>>(n, K, h->cls, h->class_count_dev);
     k_class_offsets<<<1, 32, 0, s>>>(K, h->class_count_dev);

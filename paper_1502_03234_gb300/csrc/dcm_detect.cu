@@ -7,7 +7,8 @@
 //             pass 3 in uint64 -> FP64, which gives exactly the numbers an
 //             FP64 evaluation gives (all < 2^53) at integer-pipe cost.
 //   K-means   Eq. 14, K = 2, Lloyd iterations from (max, min) in one
-//             cooperative kernel; sums are exact integers, so the
+//             cooperative kernel, every system with its own centres and
+//             stopping point; sums are exact integers, so the
 //             threshold (c_l + c_v)/2 and the labels (Eq. 11-12) are
 //             bit-identical to the definition.  Liquid sets of successive
 //             iterations are threshold sets, hence nested: equal counts
@@ -29,14 +30,15 @@ namespace dcm {
 
 constexpr int DET_THREADS = 256;
 
-__global__ void k_density(Geom g, const double *__restrict__ x, int32_t *B)
+__global__ void k_density(Batch b, const double *__restrict__ x, int32_t *B)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.n) return;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b.N) return;
+    const Geom &g = b.sys[sys_of(b.p_off, b.M, i)];
     int gx = bin_of(x[i], g.inv_h[0], g.gd[0]);
-    int gy = bin_of(x[(size_t)g.n + i], g.inv_h[1], g.gd[1]);
-    int gz = bin_of(x[2 * (size_t)g.n + i], g.inv_h[2], g.gd[2]);
-    atomicAdd(&B[gx + g.gd[0] * (gy + g.gd[1] * gz)], 1);
+    int gy = bin_of(x[(size_t)b.N + i], g.inv_h[1], g.gd[1]);
+    int gz = bin_of(x[2 * (size_t)b.N + i], g.inv_h[2], g.gd[2]);
+    atomicAdd(&B[g.v0 + gx + g.gd[0] * (gy + (int64_t)g.gd[1] * gz)], 1);
 }
 
 struct SmoothW {
@@ -45,17 +47,18 @@ struct SmoothW {
     uint32_t bmax;      // largest voxel count for which pass 2 cannot overflow
 };
 
-// one periodic 1D pass along AXIS (0 = x, 1 = y, 2 = z)
+// one periodic 1D pass along AXIS (0 = x, 1 = y, 2 = z) of every system
 template <int AXIS, typename TIN, typename TOUT>
-__global__ void k_smooth(const TIN *__restrict__ in, TOUT *out, int nx, int ny, int nz, SmoothW w,
-                         int *err)
+__global__ void k_smooth(Batch b, const TIN *__restrict__ in, TOUT *out, SmoothW w, int *err)
 {
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t nv = (int64_t)nx * ny * nz;
-    if (v >= nv) return;
-    int x = (int)(v % nx);
-    int y = (int)((v / nx) % ny);
-    int z = (int)(v / ((int64_t)nx * ny));
+    if (v >= b.NV) return;
+    const Geom &g = b.sys[sys_of(b.v_off, b.M, v)];
+    const int nx = g.gd[0], ny = g.gd[1], nz = g.gd[2];
+    int64_t lv = v - g.v0;
+    int x = (int)(lv % nx);
+    int y = (int)((lv / nx) % ny);
+    int z = (int)(lv / ((int64_t)nx * ny));
     int n = AXIS == 0 ? nx : (AXIS == 1 ? ny : nz);
     int c = AXIS == 0 ? x : (AXIS == 1 ? y : z);
     int64_t stride = AXIS == 0 ? 1 : (AXIS == 1 ? (int64_t)nx : (int64_t)nx * ny);
@@ -81,102 +84,183 @@ __global__ void k_smooth(const TIN *__restrict__ in, TOUT *out, int nx, int ny, 
     }
 }
 
-// ---- K-means (Eq. 14, K = 2) -------------------------------------------------
-// acc words: [0] max, [1] min, [2] total, then 3 rotating (count, sum) pairs
-__global__ void k_kmeans_init(unsigned long long *acc)
+// ---- K-means (Eq. 14, K = 2), all systems in one cooperative kernel ------------
+// global accumulators per system s (9 words): [0] max, [1] min, [2] total,
+// then three rotating (count, sum) pairs
+constexpr int KACC = 9;
+
+__global__ void k_kmeans_init(int M, unsigned long long *acc)
 {
-    acc[0] = 0ull;
-    acc[1] = ~0ull;
-    acc[2] = 0ull;
-    for (int q = 3; q < 9; ++q) acc[q] = 0ull;
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= M) return;
+    unsigned long long *a = acc + (int64_t)KACC * s;
+    a[0] = 0ull;
+    a[1] = ~0ull;
+    for (int q = 2; q < KACC; ++q) a[q] = 0ull;
 }
 
-__device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v,
-                                                            unsigned long long *sh)
-{
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    __syncthreads();
-    if (l == 0) sh[w] = v;
-    __syncthreads();
-    unsigned long long t = 0;
-    if (threadIdx.x == 0)
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[q];
-    return t;   // valid in thread 0
-}
+struct KmeansArgs {
+    Batch b;
+    const double *Bs;
+    uint8_t *S;
+    int max_iter;
+    unsigned long long *acc;
+    unsigned int *bar;
+    int *err;
+    DevStats *st;
+};
 
-__global__ void __launch_bounds__(DET_THREADS)
-    k_kmeans(const double *__restrict__ Bs, int64_t nv, uint8_t *S, int max_iter,
-             unsigned long long *acc, unsigned int *bar, int *err, DevStats *st)
+// per-block shared state: centres, previous liquid count, threshold and the
+// done flag of every system (every block derives the same values from the
+// same global sums, so no broadcast is needed)
+__global__ void __launch_bounds__(DET_THREADS) k_kmeans(KmeansArgs a)
 {
-    __shared__ unsigned long long sh[DET_THREADS / 32];
-    int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t nth = (int64_t)gridDim.x * blockDim.x;
-    // extremes and the total (exact integers)
-    unsigned long long mx = 0, mn = ~0ull, tot = 0;
-    for (int64_t v = tid; v < nv; v += nth) {
-        unsigned long long b = (unsigned long long)Bs[v];
-        mx = b > mx ? b : mx;
-        mn = b < mn ? b : mn;
-        tot += b;
+    extern __shared__ unsigned char smem[];
+    const int M = a.b.M;
+    double *s_cl = (double *)smem;
+    double *s_cv = s_cl + M;
+    double *s_thr = s_cv + M;
+    long long *s_prev = (long long *)(s_thr + M);
+    unsigned long long *s_c0 = (unsigned long long *)(s_prev + M);   // block partials
+    unsigned long long *s_c1 = s_c0 + M;
+    unsigned long long *s_c2 = s_c1 + M;
+    int *s_done = (int *)(s_c2 + M);
+    __shared__ int s_left;
+    const int64_t NV = a.b.NV;
+    int64_t chunk = (NV + gridDim.x - 1) / gridDim.x;
+    int64_t lo = (int64_t)blockIdx.x * chunk, hi = lo + chunk < NV ? lo + chunk : NV;
+
+    // phase A: extremes and totals (exact integers)
+    for (int s = threadIdx.x; s < M; s += blockDim.x) {
+        s_c0[s] = 0ull;
+        s_c1[s] = ~0ull;
+        s_c2[s] = 0ull;
     }
-    for (int off = 16; off > 0; off >>= 1) {
-        unsigned long long o = __shfl_xor_sync(0xffffffffu, mx, off);
-        mx = o > mx ? o : mx;
-        o = __shfl_xor_sync(0xffffffffu, mn, off);
-        mn = o < mn ? o : mn;
+    __syncthreads();
+    {
+        int cur = -1;
+        unsigned long long mx = 0, mn = ~0ull, tot = 0;
+        for (int64_t v = lo + threadIdx.x; v < hi; v += blockDim.x) {
+            int s = sys_of(a.b.v_off, M, v);
+            if (s != cur) {
+                if (cur >= 0) {
+                    atomicMax(&s_c0[cur], mx);
+                    atomicMin(&s_c1[cur], mn);
+                    atomicAdd(&s_c2[cur], tot);
+                }
+                cur = s;
+                mx = 0;
+                mn = ~0ull;
+                tot = 0;
+            }
+            unsigned long long bv = (unsigned long long)a.Bs[v];
+            mx = bv > mx ? bv : mx;
+            mn = bv < mn ? bv : mn;
+            tot += bv;
+        }
+        if (cur >= 0) {
+            atomicMax(&s_c0[cur], mx);
+            atomicMin(&s_c1[cur], mn);
+            atomicAdd(&s_c2[cur], tot);
+        }
     }
-    if ((threadIdx.x & 31) == 0) {
-        atomicMax(&acc[0], mx);
-        atomicMin(&acc[1], mn);
+    __syncthreads();
+    for (int s = threadIdx.x; s < M; s += blockDim.x) {
+        if (s_c1[s] == ~0ull) continue;   // no voxel of s in this block
+        unsigned long long *g = a.acc + (int64_t)KACC * s;
+        atomicMax(&g[0], s_c0[s]);
+        atomicMin(&g[1], s_c1[s]);
+        atomicAdd(&g[2], s_c2[s]);
     }
-    unsigned long long t = block_sum_u64(tot, sh);
-    if (threadIdx.x == 0) atomicAdd(&acc[2], t);
-    if (!grid_barrier(bar, err)) return;
+    if (!grid_barrier(a.bar, a.err)) return;
     // values other blocks produced are read through L2 (ld.global.cg): the
     // per-SM L1 caches are not coherent across a grid barrier
-    double cl = (double)__ldcg(&acc[0]), cv = (double)__ldcg(&acc[1]);
-    unsigned long long total = __ldcg(&acc[2]);
-    long long prev = -1;
-    double thr = DMUL(DADD(cl, cv), 0.5);
-    int it = 0;
-    for (; it < max_iter;) {
-        thr = DMUL(DADD(cl, cv), 0.5);
-        unsigned long long *cur = acc + 3 + 2 * (it % 3);
-        unsigned long long cnt = 0, sum = 0;
-        for (int64_t v = tid; v < nv; v += nth) {
-            double b = Bs[v];
-            if (b >= thr) {
-                cnt++;
-                sum += (unsigned long long)b;
-            }
-        }
-        unsigned long long bc = block_sum_u64(cnt, sh);
-        unsigned long long bs = block_sum_u64(sum, sh);
-        if (threadIdx.x == 0) {
-            atomicAdd(&cur[0], bc);
-            atomicAdd(&cur[1], bs);
-            if (blockIdx.x == 0) {   // clear the pair used two passes ahead
-                unsigned long long *nxt = acc + 3 + 2 * ((it + 1) % 3);
-                nxt[0] = 0ull;
-                nxt[1] = 0ull;
-            }
-        }
-        if (!grid_barrier(bar, err)) return;
-        long long nl = (long long)__ldcg(&cur[0]);
-        unsigned long long sl = __ldcg(&cur[1]);
-        ++it;
-        if (nl == prev) break;   // same threshold set as the previous pass
-        long long nvap = nv - nl;
-        if (nl > 0) cl = (double)sl / (double)nl;
-        if (nvap > 0) cv = (double)(total - sl) / (double)nvap;
-        prev = nl;
+    for (int s = threadIdx.x; s < M; s += blockDim.x) {
+        const unsigned long long *g = a.acc + (int64_t)KACC * s;
+        s_cl[s] = (double)__ldcg(&g[0]);
+        s_cv[s] = (double)__ldcg(&g[1]);
+        s_prev[s] = -1;
+        s_done[s] = 0;
+        s_thr[s] = DMUL(DADD(s_cl[s], s_cv[s]), 0.5);
     }
-    for (int64_t v = tid; v < nv; v += nth) S[v] = Bs[v] >= thr ? 0 : 1;
-    if (tid == 0) {
-        st->kmeans_iters = it;
-        st->c_liquid = cl;
-        st->c_vapor = cv;
+    __syncthreads();
+    int it = 0;
+    while (it < a.max_iter) {
+        for (int s = threadIdx.x; s < M; s += blockDim.x) {
+            s_c0[s] = 0ull;
+            s_c1[s] = 0ull;
+        }
+        __syncthreads();
+        int cur = -1;
+        unsigned long long cnt = 0, sum = 0;
+        for (int64_t v = lo + threadIdx.x; v < hi; v += blockDim.x) {
+            int s = sys_of(a.b.v_off, M, v);
+            if (s != cur) {
+                if (cur >= 0 && cnt) {
+                    atomicAdd(&s_c0[cur], cnt);
+                    atomicAdd(&s_c1[cur], sum);
+                }
+                cur = s;
+                cnt = 0;
+                sum = 0;
+            }
+            if (s_done[s]) continue;
+            double bv = a.Bs[v];
+            if (bv >= s_thr[s]) {
+                cnt++;
+                sum += (unsigned long long)bv;
+            }
+        }
+        if (cur >= 0 && cnt) {
+            atomicAdd(&s_c0[cur], cnt);
+            atomicAdd(&s_c1[cur], sum);
+        }
+        __syncthreads();
+        for (int s = threadIdx.x; s < M; s += blockDim.x) {
+            unsigned long long *g = a.acc + (int64_t)KACC * s + 3 + 2 * (it % 3);
+            if (s_c0[s]) {
+                atomicAdd(&g[0], s_c0[s]);
+                atomicAdd(&g[1], s_c1[s]);
+            }
+            if (blockIdx.x == 0) {   // clear the pair of the next pass
+                unsigned long long *nx = a.acc + (int64_t)KACC * s + 3 + 2 * ((it + 1) % 3);
+                nx[0] = 0ull;
+                nx[1] = 0ull;
+            }
+        }
+        if (!grid_barrier(a.bar, a.err)) return;
+        ++it;
+        if (threadIdx.x == 0) s_left = 0;
+        __syncthreads();
+        for (int s = threadIdx.x; s < M; s += blockDim.x) {
+            if (s_done[s]) continue;
+            const unsigned long long *g = a.acc + (int64_t)KACC * s + 3 + 2 * ((it - 1) % 3);
+            long long nl = (long long)__ldcg(&g[0]);
+            unsigned long long sl = __ldcg(&g[1]);
+            if (nl == s_prev[s]) {   // same threshold set as the previous pass
+                s_done[s] = 1;
+                continue;
+            }
+            const Geom &geo = a.b.sys[s];
+            long long nvap = geo.nvox - nl;
+            unsigned long long total = __ldcg(&a.acc[(int64_t)KACC * s + 2]);
+            if (nl > 0) s_cl[s] = (double)sl / (double)nl;
+            if (nvap > 0) s_cv[s] = (double)(total - sl) / (double)nvap;
+            s_prev[s] = nl;
+            s_thr[s] = DMUL(DADD(s_cl[s], s_cv[s]), 0.5);
+            atomicAdd(&s_left, 1);
+        }
+        __syncthreads();
+        if (s_left == 0) break;
+    }
+    for (int64_t v = lo + threadIdx.x; v < hi; v += blockDim.x) {
+        int s = sys_of(a.b.v_off, M, v);
+        a.S[v] = a.Bs[v] >= s_thr[s] ? 0 : 1;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.st->kmeans_iters = it;
+        a.st->c_liquid = s_cl[0];
+        a.st->c_vapor = s_cv[0];
     }
 }
 
@@ -188,24 +272,27 @@ __device__ __forceinline__ int64_t vox(int x, int y, int z, int nx, int ny)
 
 // D0 = D1 = 0 on vapor, +inf on liquid; frontier 0 = liquid voxels with a
 // vapor face neighbour (the "interfacial boxes")
-__global__ void k_cfsm_init(int nx, int ny, int nz, const uint8_t *__restrict__ S, double *D0,
-                            double *D1, int32_t *stamp, int32_t *list0, int32_t *fcount)
+__global__ void k_cfsm_init(Batch b, const uint8_t *__restrict__ S, double *D0, double *D1,
+                            int32_t *stamp, int32_t *list0, int32_t *fcount)
 {
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t nv = (int64_t)nx * ny * nz;
-    if (v >= nv) return;
+    if (v >= b.NV) return;
     bool vap = S[v] == 1;
     double d = vap ? 0.0 : __longlong_as_double(0x7ff0000000000000ll);
     D0[v] = d;
     D1[v] = d;
     int st = -1;
     if (!vap) {
-        int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((int64_t)nx * ny));
+        const Geom &g = b.sys[sys_of(b.v_off, b.M, v)];
+        const int nx = g.gd[0], ny = g.gd[1], nz = g.gd[2];
+        const uint8_t *Sg = S + g.v0;
+        int64_t lv = v - g.v0;
+        int x = (int)(lv % nx), y = (int)((lv / nx) % ny), z = (int)(lv / ((int64_t)nx * ny));
         int xm = x ? x - 1 : nx - 1, xp = x + 1 < nx ? x + 1 : 0;
         int ym = y ? y - 1 : ny - 1, yp = y + 1 < ny ? y + 1 : 0;
         int zm = z ? z - 1 : nz - 1, zp = z + 1 < nz ? z + 1 : 0;
-        if (S[vox(xm, y, z, nx, ny)] | S[vox(xp, y, z, nx, ny)] | S[vox(x, ym, z, nx, ny)] |
-            S[vox(x, yp, z, nx, ny)] | S[vox(x, y, zm, nx, ny)] | S[vox(x, y, zp, nx, ny)]) {
+        if (Sg[vox(xm, y, z, nx, ny)] | Sg[vox(xp, y, z, nx, ny)] | Sg[vox(x, ym, z, nx, ny)] |
+            Sg[vox(x, yp, z, nx, ny)] | Sg[vox(x, y, zm, nx, ny)] | Sg[vox(x, y, zp, nx, ny)]) {
             list0[atomicAdd(&fcount[0], 1)] = (int32_t)v;
             st = 0;
         }
@@ -214,9 +301,7 @@ __global__ void k_cfsm_init(int nx, int ny, int nz, const uint8_t *__restrict__ 
 }
 
 struct CfsmArgs {
-    int nx, ny, nz;
-    double h0, h1, h2;
-    double r_grid;
+    Batch b;
     int iter_max;
     int64_t cap;              // capacity of one frontier list
     const uint8_t *S;
@@ -234,7 +319,6 @@ __global__ void __launch_bounds__(DET_THREADS) k_cfsm(CfsmArgs a)
 {
     int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t nth = (int64_t)gridDim.x * blockDim.x;
-    const int nx = a.nx, ny = a.ny, nz = a.nz;
     int k = 0;
     bool converged = false;
     for (; k < a.iter_max; ++k) {
@@ -248,34 +332,55 @@ __global__ void __launch_bounds__(DET_THREADS) k_cfsm(CfsmArgs a)
             break;
         }
         if (tid == 0) a.fcount[(k + 2) & 3] = 0;   // list two passes ahead
-        for (int64_t q = tid; q < nf; q += nth) {
-            int v = __ldcg(&F[q]);
-            int x = v % nx, y = (v / nx) % ny, z = v / (nx * ny);
-            int xm = x ? x - 1 : nx - 1, xp = x + 1 < nx ? x + 1 : 0;
-            int ym = y ? y - 1 : ny - 1, yp = y + 1 < ny ? y + 1 : 0;
-            int zm = z ? z - 1 : nz - 1, zp = z + 1 < nz ? z + 1 : 0;
-            int64_t nb[6] = {vox(xm, y, z, nx, ny), vox(xp, y, z, nx, ny),
-                             vox(x, ym, z, nx, ny), vox(x, yp, z, nx, ny),
-                             vox(x, y, zm, nx, ny), vox(x, y, zp, nx, ny)};
-            // D and the lists were written by other blocks in the previous
-            // pass: read them through L2 (ld.global.cg), not a stale L1
-            double old = __ldcg(&X[v]);
-            double ax = fmin(__ldcg(&X[nb[0]]), __ldcg(&X[nb[1]]));
-            double ay = fmin(__ldcg(&X[nb[2]]), __ldcg(&X[nb[3]]));
-            double az = fmin(__ldcg(&X[nb[4]]), __ldcg(&X[nb[5]]));
-            double dbar = godunov(ax, ay, az, a.h0, a.h1, a.h2);
-            bool changed = dbar < old && dbar <= a.r_grid;
-            Y[v] = changed ? dbar : old;
-            if (changed) {
-                // the voxel itself (so Y catches up next pass) and its liquid
-                // face neighbours are recomputed in the next pass
-                if (atomicExch(&a.stamp[v], k + 1) != k + 1) Fn[atomicAdd(&a.fcount[(k + 1) & 3], 1)] = v;
-                for (int e = 0; e < 6; ++e) {
-                    int64_t u = nb[e];
-                    if (a.S[u] == 1) continue;
-                    if (atomicExch(&a.stamp[u], k + 1) != k + 1)
-                        Fn[atomicAdd(&a.fcount[(k + 1) & 3], 1)] = (int32_t)u;
+        int32_t push[7];
+        for (int64_t q0 = tid - (tid & 31); q0 < nf; q0 += nth) {
+            int64_t q = q0 + (tid & 31);
+            bool active = q < nf;
+            bool changed = false;
+            if (active) {
+                int v = __ldcg(&F[q]);
+                const Geom &g = a.b.sys[sys_of(a.b.v_off, a.b.M, v)];
+                const int nx = g.gd[0], ny = g.gd[1], nz = g.gd[2];
+                int64_t lv = v - g.v0;
+                int x = (int)(lv % nx), y = (int)((lv / nx) % ny), z = (int)(lv / ((int64_t)nx * ny));
+                int xm = x ? x - 1 : nx - 1, xp = x + 1 < nx ? x + 1 : 0;
+                int ym = y ? y - 1 : ny - 1, yp = y + 1 < ny ? y + 1 : 0;
+                int zm = z ? z - 1 : nz - 1, zp = z + 1 < nz ? z + 1 : 0;
+                int64_t nb[6] = {g.v0 + vox(xm, y, z, nx, ny), g.v0 + vox(xp, y, z, nx, ny),
+                                 g.v0 + vox(x, ym, z, nx, ny), g.v0 + vox(x, yp, z, nx, ny),
+                                 g.v0 + vox(x, y, zm, nx, ny), g.v0 + vox(x, y, zp, nx, ny)};
+                // D and the lists were written by other blocks in the previous
+                // pass: read them through L2 (ld.global.cg), not a stale L1
+                double old = __ldcg(&X[v]);
+                double ax = fmin(__ldcg(&X[nb[0]]), __ldcg(&X[nb[1]]));
+                double ay = fmin(__ldcg(&X[nb[2]]), __ldcg(&X[nb[3]]));
+                double az = fmin(__ldcg(&X[nb[4]]), __ldcg(&X[nb[5]]));
+                double dbar = godunov(ax, ay, az, g.h[0], g.h[1], g.h[2]);
+                changed = dbar < old && dbar <= g.r_grid;
+                Y[v] = changed ? dbar : old;
+                if (changed) {
+                    // the voxel itself (so Y catches up next pass) and its
+                    // liquid face neighbours are recomputed in the next pass
+                    push[0] = atomicExch(&a.stamp[v], k + 1) != k + 1 ? v : -1;
+                    for (int e = 0; e < 6; ++e) {
+                        int64_t u = nb[e];
+                        push[1 + e] = (a.S[u] == 0 && atomicExch(&a.stamp[u], k + 1) != k + 1)
+                                          ? (int32_t)u
+                                          : -1;
+                    }
                 }
+            }
+            // warp-aggregated append: one atomic per warp and slot
+            for (int e = 0; e < 7; ++e) {
+                int32_t item = changed ? push[e] : -1;
+                unsigned m = __ballot_sync(0xffffffffu, item >= 0);
+                if (!m) continue;
+                int leader = __ffs(m) - 1;
+                int base = 0;
+                if ((int)(threadIdx.x & 31) == leader)
+                    base = atomicAdd(&a.fcount[(k + 1) & 3], __popc(m));
+                base = __shfl_sync(0xffffffffu, base, leader);
+                if (item >= 0) Fn[base + __popc(m & ((1u << (threadIdx.x & 31)) - 1u))] = item;
             }
         }
         if (!grid_barrier(a.bar, a.err)) return;
@@ -289,18 +394,19 @@ __global__ void __launch_bounds__(DET_THREADS) k_cfsm(CfsmArgs a)
 }
 
 // ---- Algorithm 3.1 + Eq. 7-8 ----------------------------------------------------
-__global__ void k_cutoff(Geom g, const double *__restrict__ x, const double *__restrict__ D0,
+__global__ void k_cutoff(Batch b, const double *__restrict__ x, const double *__restrict__ D0,
                          const double *__restrict__ D1, const int *__restrict__ result, double *d,
                          double *rc, uint8_t *cls)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.n) return;
-    const double *D = *result ? D1 : D0;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b.N) return;
+    const Geom &g = b.sys[sys_of(b.p_off, b.M, i)];
+    const double *D = (*result ? D1 : D0) + g.v0;
     int i0[3], i1[3];
     double t[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        double gg = DSUB(DMUL(x[(size_t)a * g.n + i], g.inv_h[a]), 0.5);
+        double gg = DSUB(DMUL(x[(size_t)a * b.N + i], g.inv_h[a]), 0.5);
         double fl = floor(gg);
         t[a] = DSUB(gg, fl);
         int lo = (int)fl;
@@ -311,17 +417,32 @@ __global__ void k_cutoff(Geom g, const double *__restrict__ x, const double *__r
         i1[a] = hi;
     }
     const int nx = g.gd[0], ny = g.gd[1];
+    const double rg = g.r_grid;
     auto Dv = [&](int X, int Y, int Z) {
         double v = D[X + (int64_t)nx * (Y + (int64_t)ny * Z)];
-        return v < g.r_grid ? v : g.r_grid;   // voxels CFSM never reached
+        return v < rg ? v : rg;   // voxels CFSM never reached
     };
-    double c00 = lerp_rn(Dv(i0[0], i0[1], i0[2]), Dv(i1[0], i0[1], i0[2]), t[0]);
-    double c10 = lerp_rn(Dv(i0[0], i1[1], i0[2]), Dv(i1[0], i1[1], i0[2]), t[0]);
-    double c01 = lerp_rn(Dv(i0[0], i0[1], i1[2]), Dv(i1[0], i0[1], i1[2]), t[0]);
-    double c11 = lerp_rn(Dv(i0[0], i1[1], i1[2]), Dv(i1[0], i1[1], i1[2]), t[0]);
-    double c0 = lerp_rn(c00, c10, t[1]);
-    double c1 = lerp_rn(c01, c11, t[1]);
-    double di = lerp_rn(c0, c1, t[2]);
+    double v000 = Dv(i0[0], i0[1], i0[2]), v100 = Dv(i1[0], i0[1], i0[2]);
+    double v010 = Dv(i0[0], i1[1], i0[2]), v110 = Dv(i1[0], i1[1], i0[2]);
+    double v001 = Dv(i0[0], i0[1], i1[2]), v101 = Dv(i1[0], i0[1], i1[2]);
+    double v011 = Dv(i0[0], i1[1], i1[2]), v111 = Dv(i1[0], i1[1], i1[2]);
+    long long b0 = __double_as_longlong(v000);
+    bool flat = b0 == __double_as_longlong(v100) && b0 == __double_as_longlong(v010) &&
+                b0 == __double_as_longlong(v110) && b0 == __double_as_longlong(v001) &&
+                b0 == __double_as_longlong(v101) && b0 == __double_as_longlong(v011) &&
+                b0 == __double_as_longlong(v111);
+    double di;
+    if (flat) {
+        di = v000;   // a + t (a - a) == a exactly: the lerps reproduce it
+    } else {
+        double c00 = lerp_rn(v000, v100, t[0]);
+        double c10 = lerp_rn(v010, v110, t[0]);
+        double c01 = lerp_rn(v001, v101, t[0]);
+        double c11 = lerp_rn(v011, v111, t[0]);
+        double c0 = lerp_rn(c00, c10, t[1]);
+        double c1 = lerp_rn(c01, c11, t[1]);
+        di = lerp_rn(c0, c1, t[2]);
+    }
     double r;
     if (di <= 0.0)
         r = g.rc_max;
@@ -332,7 +453,7 @@ __global__ void k_cutoff(Geom g, const double *__restrict__ x, const double *__r
     int c = 0;
     if (di < g.rc_max) {
         c = 1;
-        for (int k = 0; k < g.K - 2; ++k) c += di < g.thr[k] ? 1 : 0;
+        for (int k = 0; k < b.K - 2; ++k) c += di < g.thr[k] ? 1 : 0;
     }
     d[i] = di;
     rc[i] = r;
@@ -340,16 +461,17 @@ __global__ void k_cutoff(Geom g, const double *__restrict__ x, const double *__r
 }
 
 // classes for cutoffs supplied directly (scheduling only)
-__global__ void k_classify_rc(Geom g, const double *__restrict__ rc, uint8_t *cls)
+__global__ void k_classify_rc(Batch b, const double *__restrict__ rc, uint8_t *cls)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.n) return;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b.N) return;
+    const Geom &g = b.sys[sys_of(b.p_off, b.M, i)];
     double r = rc[i];
     int c = 0;
     if (r > g.rc_min) {
         c = 1;
-        for (int k = 1; k <= g.K - 2; ++k) {
-            double edge = g.rc_min + (g.rc_max - g.rc_min) * (double)k / (double)(g.K - 1);
+        for (int k = 1; k <= b.K - 2; ++k) {
+            double edge = g.rc_min + (g.rc_max - g.rc_min) * (double)k / (double)(b.K - 1);
             c += r > edge ? 1 : 0;
         }
     }
@@ -360,16 +482,16 @@ static inline int nblk(int64_t n, int b) { return (int)((n + b - 1) / b); }
 
 int launch_classify_rc(dcm_handle *h)
 {
-    k_classify_rc<<<nblk(h->n, 256), 256, 0, h->stream>>>(h->g, h->rc, h->cls);
+    k_classify_rc<<<nblk(h->n, 256), 256, 0, h->stream>>>(h->b, h->rc, h->cls);
     return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "classify launch");
 }
 
-static int coop_launch(dcm_handle *h, const void *fn, int grid, void **args)
+static int coop_launch(dcm_handle *h, const void *fn, int grid, size_t smem, void **args)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(DET_THREADS);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = h->stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -391,18 +513,31 @@ int coop_grid_size(dcm_handle *h, const void *kernel, int block, size_t smem)
     return h->num_sms * per_sm;
 }
 
+static size_t kmeans_smem(int M) { return (size_t)M * (4 * 8 + 3 * 8 + 4); }
+
+int prepare_kernels(dcm_handle *h)
+{
+    size_t smem = kmeans_smem(h->M);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute((const void *)k_kmeans,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return fail_cuda(e, "k_kmeans shared memory", __FILE__, __LINE__);
+    }
+    return DCM_OK;
+}
+
 int launch_detect(dcm_handle *h)
 {
     h->kernels += h->p.smooth_order > 0 ? 9 : 7;
     cudaStream_t s = h->stream;
-    const Geom &g = h->g;
-    int n = (int)h->n;
-    int64_t nv = h->nvox;
+    const Batch &b = h->b;
+    int64_t nv = b.NV;
     // Eq. 9
     cudaMemsetAsync(h->B, 0, sizeof(int32_t) * nv, s);
-    k_density<<<nblk(n, 256), 256, 0, s>>>(g, h->x, h->B);
+    k_density<<<nblk(b.N, 256), 256, 0, s>>>(b, h->x, h->B);
     // smoothing
     int order = h->p.smooth_order;
+    int vb = nblk(nv, DET_THREADS);
     if (order > 0) {
         SmoothW w;
         w.order = order;
@@ -411,61 +546,48 @@ int launch_detect(dcm_handle *h)
         for (int r = 1; r <= order; ++r)
             for (int k = r; k >= 1; --k) w.w[k] += w.w[k - 1];
         uint64_t pass = 1ull << order;   // sum of the weights
-        w.bmax = (uint32_t)((0xffffffffull / (pass * pass)) < 0xffffffffull
-                                ? 0xffffffffull / (pass * pass)
-                                : 0xffffffffull);
-        int vb = nblk(nv, DET_THREADS);
-        k_smooth<0, int32_t, uint32_t><<<vb, DET_THREADS, 0, s>>>(h->B, h->sm1, g.gd[0], g.gd[1],
-                                                                 g.gd[2], w, h->err);
-        k_smooth<1, uint32_t, uint32_t><<<vb, DET_THREADS, 0, s>>>(h->sm1, h->sm2, g.gd[0],
-                                                                  g.gd[1], g.gd[2], w, h->err);
-        k_smooth<2, uint32_t, double><<<vb, DET_THREADS, 0, s>>>(h->sm2, h->Bs, g.gd[0], g.gd[1],
-                                                                g.gd[2], w, h->err);
+        w.bmax = (uint32_t)(0xffffffffull / (pass * pass));
+        k_smooth<0, int32_t, uint32_t><<<vb, DET_THREADS, 0, s>>>(b, h->B, h->sm1, w, h->err);
+        k_smooth<1, uint32_t, uint32_t><<<vb, DET_THREADS, 0, s>>>(b, h->sm1, h->sm2, w, h->err);
+        k_smooth<2, uint32_t, double><<<vb, DET_THREADS, 0, s>>>(b, h->sm2, h->Bs, w, h->err);
     } else {
         SmoothW w;
         w.order = 0;
         w.w[0] = 1;
         w.bmax = 0xffffffffu;
-        k_smooth<0, int32_t, double><<<nblk(nv, DET_THREADS), DET_THREADS, 0, s>>>(
-            h->B, h->Bs, g.gd[0], g.gd[1], g.gd[2], w, h->err);
+        k_smooth<0, int32_t, double><<<vb, DET_THREADS, 0, s>>>(b, h->B, h->Bs, w, h->err);
     }
     // K-means labels
-    k_kmeans_init<<<1, 1, 0, s>>>(h->kacc);
+    k_kmeans_init<<<nblk(b.M, 128), 128, 0, s>>>(b.M, h->kacc);
     cudaMemsetAsync(h->stats->barrier, 0, 2 * sizeof(unsigned int), s);
     {
-        const double *Bs = h->Bs;
-        int64_t nvv = nv;
-        uint8_t *S = h->S;
-        int mi = h->p.kmeans_max_iter > 0 ? h->p.kmeans_max_iter : 100;
-        unsigned long long *acc = h->kacc;
-        unsigned int *bar = h->stats->barrier;
-        int *err = h->err;
-        DevStats *st = h->stats;
-        void *args[] = {(void *)&Bs, (void *)&nvv, (void *)&S, (void *)&mi,
-                        (void *)&acc, (void *)&bar, (void *)&err, (void *)&st};
-        int grid = coop_grid_size(h, (const void *)k_kmeans, DET_THREADS, 0);
+        KmeansArgs a;
+        a.b = b;
+        a.Bs = h->Bs;
+        a.S = h->S;
+        a.max_iter = h->p.kmeans_max_iter > 0 ? h->p.kmeans_max_iter : 100;
+        a.acc = h->kacc;
+        a.bar = h->stats->barrier;
+        a.err = h->err;
+        a.st = h->stats;
+        void *args[] = {(void *)&a};
+        size_t smem = kmeans_smem(b.M);
+        int grid = coop_grid_size(h, (const void *)k_kmeans, DET_THREADS, smem);
         int64_t need = (nv + DET_THREADS - 1) / DET_THREADS;
         if (grid > need) grid = (int)(need > 0 ? need : 1);
-        int rc = coop_launch(h, (const void *)k_kmeans, grid, args);
+        int rc = coop_launch(h, (const void *)k_kmeans, grid, smem, args);
         if (rc) return rc;
     }
     // CFSM
     cudaMemsetAsync(h->fcount, 0, 4 * sizeof(int32_t), s);
-    k_cfsm_init<<<nblk(nv, DET_THREADS), DET_THREADS, 0, s>>>(g.gd[0], g.gd[1], g.gd[2], h->S,
-                                                              h->D0, h->D1, h->stamp, h->flist,
-                                                              h->fcount);
+    k_cfsm_init<<<vb, DET_THREADS, 0, s>>>(b, h->S, h->D0, h->D1, h->stamp, h->flist, h->fcount);
     cudaMemsetAsync(h->stats->barrier, 0, 2 * sizeof(unsigned int), s);
     {
         CfsmArgs a;
-        a.nx = g.gd[0];
-        a.ny = g.gd[1];
-        a.nz = g.gd[2];
-        a.h0 = g.h[0];
-        a.h1 = g.h[1];
-        a.h2 = g.h[2];
-        a.r_grid = g.r_grid;
-        int dmax = g.gd[0] > g.gd[1] ? g.gd[0] : g.gd[1];
-        dmax = dmax > g.gd[2] ? dmax : g.gd[2];
+        a.b = b;
+        int dmax = 1;
+        for (int q = 0; q < b.M; ++q)
+            for (int ax = 0; ax < 3; ++ax) dmax = h->geo_host[q].gd[ax] > dmax ? h->geo_host[q].gd[ax] : dmax;
         a.iter_max = h->p.cfsm_iter_max > 0 ? h->p.cfsm_iter_max : 4 * dmax;
         a.cap = nv;
         a.S = h->S;
@@ -480,12 +602,12 @@ int launch_detect(dcm_handle *h)
         a.st = h->stats;
         void *args[] = {(void *)&a};
         int grid = coop_grid_size(h, (const void *)k_cfsm, DET_THREADS, 0);
-        int rc = coop_launch(h, (const void *)k_cfsm, grid, args);
+        int rc = coop_launch(h, (const void *)k_cfsm, grid, 0, args);
         if (rc) return rc;
     }
     // Algorithm 3.1 + Eq. 7
-    k_cutoff<<<nblk(n, 256), 256, 0, s>>>(g, h->x, h->D0, h->D1, (const int *)&h->stats->barrier[3],
-                                          h->d, h->rc, h->cls);
+    k_cutoff<<<nblk(b.N, 256), 256, 0, s>>>(b, h->x, h->D0, h->D1,
+                                            (const int *)&h->stats->barrier[3], h->d, h->rc, h->cls);
     return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "detect launch");
 }
 

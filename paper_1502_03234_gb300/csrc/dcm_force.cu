@@ -36,7 +36,7 @@ constexpr int FORCE_THREADS = 256;
 constexpr float GUARD = 3.814697265625e-06f;   // 2^-18
 
 struct ForceArgs {
-    Geom g;
+    Batch b;
     const int32_t *class_buf;     // [0..K) counts, [K..2K) offsets
     const int32_t *class_list;    // sorted slots grouped by class
     int lanes[DCM_MAX_CLASSES];   // lanes per particle per class
@@ -52,15 +52,13 @@ struct ForceArgs {
     double *pe, *vir;
     unsigned int *queue;          // work counter
     unsigned long long *guard_count;
-    float eps24f, eps48f, eps2f, sig2f;
-    double eps24, eps48, eps2, sig2;
 };
 
 // exact FP64 decision |r_ij| < r_c[i] (the definition's arithmetic)
-__device__ __forceinline__ bool fp64_inside(const ForceArgs &a, int i, int j, double rci2)
+__device__ __forceinline__ bool fp64_inside(const ForceArgs &a, const Geom &g, int i, int j,
+                                            double rci2)
 {
-    const Geom &g = a.g;
-    size_t n = (size_t)g.n;
+    size_t n = (size_t)a.b.N;
     double dx = min_image(DSUB(a.x[i], a.x[j]), g.L[0], g.halfL[0]);
     double dy = min_image(DSUB(a.x[n + i], a.x[n + j]), g.L[1], g.halfL[1]);
     double dz = min_image(DSUB(a.x[2 * n + i], a.x[2 * n + j]), g.L[2], g.halfL[2]);
@@ -92,16 +90,16 @@ struct Acc<DCM_FP64, ENERGY> {
 };
 
 template <int PREC, bool ENERGY>
-__device__ __forceinline__ void row_segment(const ForceArgs &a, int k, int i, int lane, int G,
+__device__ __forceinline__ void row_segment(const ForceArgs &a, const Geom &g, int k, int i,
+                                            int lane, int G,
                                             int j0, int j1, float ax, float ay, float az,
                                             float4 ui, double4_32a pi, float rc2f, float rc2lo,
                                             float rc2hi, double rci2, Acc<PREC, ENERGY> &acc,
-                                            int &np)
+                                            int &np, int &ng)
 {
-    const Geom &g = a.g;
-    for (int j = j0 + lane; j < j1; j += G) {
-        if constexpr (PREC == DCM_MIXED) {
-            float4 uj = a.sp4[j];
+    if constexpr (PREC == DCM_MIXED) {
+        // one candidate: FP32 distance on cell-relative coordinates
+        auto pair = [&](int j, float4 uj) {
             float dx = fmaf(ax - uj.w, g.cf[0], ui.x - uj.x);
             float dy = ay - uj.y;
             float dz = az - uj.z;
@@ -109,20 +107,20 @@ __device__ __forceinline__ void row_segment(const ForceArgs &a, int k, int i, in
             if (r2 < rc2hi && j != k) {
                 bool in = r2 < rc2f;
                 if (r2 >= rc2lo) {
-                    in = fp64_inside(a, i, a.sorted_id[j], rci2);
-                    atomicAdd(a.guard_count, 1ull);
+                    in = fp64_inside(a, g, i, a.sorted_id[j], rci2);
+                    ++ng;
                 }
                 if (in) {
                     float r2inv = rcp_approx(r2);
-                    float sr2 = a.sig2f * r2inv;
+                    float sr2 = g.sig2f * r2inv;
                     float sr6 = sr2 * sr2 * sr2;
-                    float fr = r2inv * sr6 * fmaf(a.eps48f, sr6, -a.eps24f);
+                    float fr = r2inv * sr6 * fmaf(g.eps48f, sr6, -g.eps24f);
                     acc.rx = fmaf(fr, dx, acc.rx);
                     acc.ry = fmaf(fr, dy, acc.ry);
                     acc.rz = fmaf(fr, dz, acc.rz);
                     ++np;
                     if constexpr (ENERGY) {
-                        acc.pe = fmaf(a.eps2f * sr6, sr6 - 1.f, acc.pe);
+                        acc.pe = fmaf(g.eps2f * sr6, sr6 - 1.f, acc.pe);
                         float fx = fr * dx, fy = fr * dy, fz = fr * dz;
                         acc.v[0] = fmaf(0.5f * dx, fx, acc.v[0]);
                         acc.v[1] = fmaf(0.5f * dy, fy, acc.v[1]);
@@ -133,7 +131,18 @@ __device__ __forceinline__ void row_segment(const ForceArgs &a, int k, int i, in
                     }
                 }
             }
-        } else {
+        };
+        int j = j0 + lane;
+        // two independent loads in flight before any arithmetic
+        for (; j + G < j1; j += 2 * G) {
+            float4 u0 = a.sp4[j], u1 = a.sp4[j + G];
+            pair(j, u0);
+            pair(j + G, u1);
+        }
+        for (; j < j1; j += G) pair(j, a.sp4[j]);
+        acc.fold();
+    } else {
+        for (int j = j0 + lane; j < j1; j += G) {
             double4_32a pj = a.spd[j];
             double dx = min_image(DSUB(pi.x, pj.x), g.L[0], g.halfL[0]);
             double dy = min_image(DSUB(pi.y, pj.y), g.L[1], g.halfL[1]);
@@ -141,15 +150,15 @@ __device__ __forceinline__ void row_segment(const ForceArgs &a, int k, int i, in
             double r2 = r2_rn(dx, dy, dz);
             if (r2 < rci2 && j != k) {
                 double r2inv = 1.0 / r2;
-                double sr2 = a.sig2 * r2inv;
+                double sr2 = g.sig2 * r2inv;
                 double sr6 = sr2 * sr2 * sr2;
-                double fr = r2inv * sr6 * (a.eps48 * sr6 - a.eps24);
+                double fr = r2inv * sr6 * (g.eps48 * sr6 - g.eps24);
                 acc.fx += fr * dx;
                 acc.fy += fr * dy;
                 acc.fz += fr * dz;
                 ++np;
                 if constexpr (ENERGY) {
-                    acc.pe += a.eps2 * sr6 * (sr6 - 1.0);
+                    acc.pe += g.eps2 * sr6 * (sr6 - 1.0);
                     double fx = fr * dx, fy = fr * dy, fz = fr * dz;
                     acc.v[0] += 0.5 * dx * fx;
                     acc.v[1] += 0.5 * dy * fy;
@@ -161,7 +170,6 @@ __device__ __forceinline__ void row_segment(const ForceArgs &a, int k, int i, in
             }
         }
     }
-    acc.fold();
 }
 
 // box distance along one axis from a point at u in [0, c) of its own cell
@@ -173,12 +181,12 @@ __device__ __forceinline__ float box_gap(int d, float u, float c)
 }
 
 template <int PREC, bool ENERGY>
-__device__ void particle_force(const ForceArgs &a, int k, int lane, int G, unsigned gmask)
+__device__ __forceinline__ void particle_force(const ForceArgs &a, int k, int lane, int G, unsigned gmask, int &ng)
 {
-    const Geom &g = a.g;
+    const Geom &g = a.b.sys[sys_of(a.b.p_off, a.b.M, k)];
     int i = a.sorted_id[k];
     float4 ui = a.sp4[k];
-    int c = a.cell_of[i];
+    int c = a.cell_of[i] - (int)g.c0;
     int cx = (int)ui.w;
     int cy = (c / g.nc[0]) % g.nc[1];
     int cz = c / (g.nc[0] * g.nc[1]);
@@ -213,26 +221,26 @@ __device__ void particle_force(const ForceArgs &a, int k, int lane, int G, unsig
             float w = sqrtf(w2);
             int xlo = max(-sx, (int)floorf((ui.x - w) * g.inv_cf[0]));
             int xhi = min(sx, (int)floorf((ui.x + w) * g.inv_cf[0]));
-            int row = g.nc[0] * (cyy + g.nc[1] * czz);
+            int row = (int)g.c0 + g.nc[0] * (cyy + g.nc[1] * czz);
             int lo = cx + xlo, hi = cx + xhi;
             if (lo < 0) {
                 // cells at the top end seen through the x = 0 face
-                row_segment<PREC, ENERGY>(a, k, i, lane, G, a.cell_start[row + lo + g.nc[0]],
+                row_segment<PREC, ENERGY>(a, g, k, i, lane, G, a.cell_start[row + lo + g.nc[0]],
                                           a.cell_start[row + g.nc[0]], (float)(cx + g.nc[0]), ay,
-                                          az, ui, pi, rc2f, rc2lo, rc2hi, rci2, acc, np);
+                                          az, ui, pi, rc2f, rc2lo, rc2hi, rci2, acc, np, ng);
                 lo = 0;
             }
             if (hi >= g.nc[0]) {
-                row_segment<PREC, ENERGY>(a, k, i, lane, G, a.cell_start[row],
+                row_segment<PREC, ENERGY>(a, g, k, i, lane, G, a.cell_start[row],
                                           a.cell_start[row + hi - g.nc[0] + 1],
                                           (float)(cx - g.nc[0]), ay, az, ui, pi, rc2f, rc2lo,
-                                          rc2hi, rci2, acc, np);
+                                          rc2hi, rci2, acc, np, ng);
                 hi = g.nc[0] - 1;
             }
             if (lo <= hi)
-                row_segment<PREC, ENERGY>(a, k, i, lane, G, a.cell_start[row + lo],
+                row_segment<PREC, ENERGY>(a, g, k, i, lane, G, a.cell_start[row + lo],
                                           a.cell_start[row + hi + 1], (float)cx, ay, az, ui, pi,
-                                          rc2f, rc2lo, rc2hi, rci2, acc, np);
+                                          rc2f, rc2lo, rc2hi, rci2, acc, np, ng);
         }
     }
     // combine the G lanes of this particle
@@ -261,7 +269,7 @@ __device__ void particle_force(const ForceArgs &a, int k, int lane, int G, unsig
         }
     }
     if (lane == 0) {
-        size_t n = (size_t)g.n;
+        size_t n = (size_t)a.b.N;
         a.f[i] = fx;
         a.f[n + i] = fy;
         a.f[2 * n + i] = fz;
@@ -275,10 +283,10 @@ __device__ void particle_force(const ForceArgs &a, int k, int lane, int G, unsig
 
 // persistent warps draining the class-ordered work queue
 template <int PREC, bool ENERGY>
-__global__ void __launch_bounds__(FORCE_THREADS) k_force(ForceArgs a)
+__global__ void __launch_bounds__(FORCE_THREADS, 3) k_force(ForceArgs a)
 {
     __shared__ int s_cnt[DCM_MAX_CLASSES], s_off[DCM_MAX_CLASSES], s_items[DCM_MAX_CLASSES + 1];
-    const int K = a.g.K;
+    const int K = a.b.K;
     if (threadIdx.x == 0) {
         int run = 0;
         // heaviest (largest cutoff) class first
@@ -294,6 +302,7 @@ __global__ void __launch_bounds__(FORCE_THREADS) k_force(ForceArgs a)
     __syncthreads();
     const int total = s_items[K];
     const int lane32 = threadIdx.x & 31;
+    int ng = 0;   // guard-band re-decisions (diagnostic), one atomic per block
     while (true) {
         int item = 0;
         if (lane32 == 0) item = (int)atomicAdd(a.queue, 1u);
@@ -309,17 +318,24 @@ __global__ void __launch_bounds__(FORCE_THREADS) k_force(ForceArgs a)
         unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane32 & ~(G - 1)));
         if (local < s_cnt[q]) {
             int k = a.class_list[s_off[q] + local];
-            particle_force<PREC, ENERGY>(a, k, lane, G, gmask);
+            particle_force<PREC, ENERGY>(a, k, lane, G, gmask, ng);
         }
         __syncwarp();
     }
+    for (int off = 16; off > 0; off >>= 1) ng += __shfl_xor_sync(0xffffffffu, ng, off);
+    __shared__ int s_ng;
+    if (threadIdx.x == 0) s_ng = 0;
+    __syncthreads();
+    if (lane32 == 0 && ng) atomicAdd(&s_ng, ng);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_ng) atomicAdd(a.guard_count, (unsigned long long)s_ng);
 }
 
 int launch_forces(dcm_handle *h, bool energy)
 {
     h->kernels += 1;
     ForceArgs a;
-    a.g = h->g;
+    a.b = h->b;
     a.class_buf = h->class_count_dev;
     a.class_list = h->class_list;
     for (int q = 0; q < DCM_MAX_CLASSES; ++q) {
@@ -339,18 +355,8 @@ int launch_forces(dcm_handle *h, bool energy)
     a.vir = h->vir;
     a.queue = &h->stats->barrier[2];
     a.guard_count = &h->stats->guard_rechecks;
-    double eps = h->p.eps, sig = h->p.sigma;
-    a.eps24 = 24.0 * eps;
-    a.eps48 = 48.0 * eps;
-    a.eps2 = 2.0 * eps;
-    a.sig2 = sig * sig;
-    a.eps24f = (float)a.eps24;
-    a.eps48f = (float)a.eps48;
-    a.eps2f = (float)a.eps2;
-    a.sig2f = (float)a.sig2;
     cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), h->stream);
-    int block = h->tune.block >= 64 && h->tune.block <= 1024 ? h->tune.block : FORCE_THREADS;
-    block = block > FORCE_THREADS ? FORCE_THREADS : block;
+    int block = h->tune.block >= 64 && h->tune.block <= FORCE_THREADS ? h->tune.block : FORCE_THREADS;
     int grid = h->num_sms * (2048 / block);
     bool fp64 = h->p.precision == DCM_FP64;
     if (fp64) {

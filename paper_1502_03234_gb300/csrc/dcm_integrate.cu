@@ -7,23 +7,27 @@
 
 namespace dcm {
 
-// v += dt/(2m) F;  x += dt v;  wrap into the box  (first half of a step)
-__global__ void k_kick_drift(Geom g, double *__restrict__ x, double *__restrict__ v,
+// v += dt/(2m) F;  x += dt v;  wrap into the box  (first half of a step).
+// GB300 issues FP64 at 1/64 of the FP32 rate, so the update uses two fused
+// multiply-adds per component and integer tests of the exponent bits.
+__global__ void k_kick_drift(Batch b, double *__restrict__ x, double *__restrict__ v,
                              const double *__restrict__ f, int *err)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.n) return;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b.N) return;
+    const Geom &g = b.sys[sys_of(b.p_off, b.M, i)];
     int bad = 0;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        size_t o = (size_t)a * g.n + i;
-        double vi = DADD(v[o], DMUL(g.hdtm, f[o]));
-        double step = DMUL(g.dt, vi);
-        double xi = DADD(x[o], step);
-        if (!(fabs(step) < g.L[a])) bad |= DEV_ERR_JUMP;
+        size_t o = (size_t)a * b.N + i;
+        double vi = fma(g.hdtm, f[o], v[o]);
+        double xi = fma(g.dt, vi, x[o]);
+        // non-finite: exponent bits all ones
+        if (((__double_as_longlong(xi) >> 52) & 0x7ff) == 0x7ff ||
+            ((__double_as_longlong(vi) >> 52) & 0x7ff) == 0x7ff)
+            bad |= DEV_ERR_NONFINITE;
         xi = wrap_coord(xi, g.L[a]);
-        if (!isfinite(xi) || !isfinite(vi)) bad |= DEV_ERR_NONFINITE;
-        if (!(xi >= 0.0 && xi < g.L[a])) {
+        if (!(xi >= 0.0 && xi < g.L[a])) {   // moved more than one box edge
             bad |= DEV_ERR_JUMP;
             xi = 0.0;
         }
@@ -34,14 +38,15 @@ __global__ void k_kick_drift(Geom g, double *__restrict__ x, double *__restrict_
 }
 
 // v += dt/(2m) F  (second half of a step)
-__global__ void k_kick(Geom g, double *__restrict__ v, const double *__restrict__ f)
+__global__ void k_kick(Batch b, double *__restrict__ v, const double *__restrict__ f)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.n) return;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b.N) return;
+    const double hdtm = b.sys[sys_of(b.p_off, b.M, i)].hdtm;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        size_t o = (size_t)a * g.n + i;
-        v[o] = DADD(v[o], DMUL(g.hdtm, f[o]));
+        size_t o = (size_t)a * b.N + i;
+        v[o] = fma(hdtm, f[o], v[o]);
     }
 }
 
@@ -52,22 +57,26 @@ constexpr int RED_BLOCKS = 256;
 constexpr int RED_THREADS = 256;
 constexpr int RED_VALUES = 8;   // pe, sum v^2, w_xx w_yy w_zz w_xy w_xz w_yz
 
-__global__ void k_reduce_energy_part(int n, const double *__restrict__ pe,
+// partial sums over the particles [p0, p0 + n) of one system
+__global__ void k_reduce_energy_part(int64_t p0, int n, int64_t N, const double *__restrict__ pe,
                                      const double *__restrict__ vir,
                                      const double *__restrict__ v, double *part)
 {
     __shared__ double s[RED_VALUES][RED_THREADS];
     int chunk = (n + RED_BLOCKS - 1) / RED_BLOCKS;
     int lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
+    pe += p0;
+    vir += p0;
+    v += p0;
     double acc[RED_VALUES];
 #pragma unroll
     for (int q = 0; q < RED_VALUES; ++q) acc[q] = 0.0;
     for (int i = lo + threadIdx.x; i < hi; i += RED_THREADS) {
         acc[0] += pe[i];
-        double vx = v[i], vy = v[(size_t)n + i], vz = v[2 * (size_t)n + i];
+        double vx = v[i], vy = v[(size_t)N + i], vz = v[2 * (size_t)N + i];
         acc[1] += vx * vx + vy * vy + vz * vz;
 #pragma unroll
-        for (int q = 0; q < 6; ++q) acc[2 + q] += vir[(size_t)q * n + i];
+        for (int q = 0; q < 6; ++q) acc[2 + q] += vir[(size_t)q * N + i];
     }
 #pragma unroll
     for (int q = 0; q < RED_VALUES; ++q) s[q][threadIdx.x] = acc[q];
@@ -96,12 +105,13 @@ __global__ void k_reduce_final(const double *part, int nvals, double *out)
     }
 }
 
-__global__ void k_reduce_pairs(int n, const int32_t *__restrict__ npair,
+__global__ void k_reduce_pairs(int64_t n, const int32_t *__restrict__ npair,
                                unsigned long long *out)
 {
     __shared__ unsigned long long s[RED_THREADS];
     unsigned long long acc = 0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
         acc += (unsigned long long)npair[i];
     s[threadIdx.x] = acc;
     __syncthreads();
@@ -117,29 +127,31 @@ static inline int nblk(int64_t n, int b) { return (int)((n + b - 1) / b); }
 int launch_kick_drift(dcm_handle *h)
 {
     h->kernels += 1;
-    k_kick_drift<<<nblk(h->n, 256), 256, 0, h->stream>>>(h->g, h->x, h->v, h->f, h->err);
+    k_kick_drift<<<nblk(h->n, 256), 256, 0, h->stream>>>(h->b, h->x, h->v, h->f, h->err);
     return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "kick_drift launch");
 }
 
 int launch_kick(dcm_handle *h)
 {
     h->kernels += 1;
-    k_kick<<<nblk(h->n, 256), 256, 0, h->stream>>>(h->g, h->v, h->f);
+    k_kick<<<nblk(h->n, 256), 256, 0, h->stream>>>(h->b, h->v, h->f);
     return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "kick launch");
 }
 
-int launch_reduce_energy(dcm_handle *h)
+// energy and virial of system k into red_out[8*k .. 8*k+8)
+int launch_reduce_energy(dcm_handle *h, int k)
 {
-    k_reduce_energy_part<<<RED_BLOCKS, RED_THREADS, 0, h->stream>>>((int)h->n, h->pe, h->vir,
+    const Geom &g = h->geo_host[k];
+    k_reduce_energy_part<<<RED_BLOCKS, RED_THREADS, 0, h->stream>>>(g.p0, g.n, h->n, h->pe, h->vir,
                                                                   h->v, h->red_part);
-    k_reduce_final<<<1, RED_BLOCKS, 0, h->stream>>>(h->red_part, RED_VALUES, h->red_out);
+    k_reduce_final<<<1, RED_BLOCKS, 0, h->stream>>>(h->red_part, RED_VALUES, h->red_out + 8 * k);
     return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "reduce launch");
 }
 
 int launch_reduce_pairs(dcm_handle *h)
 {
     cudaMemsetAsync(&h->stats->pairs, 0, sizeof(unsigned long long), h->stream);
-    k_reduce_pairs<<<RED_BLOCKS, RED_THREADS, 0, h->stream>>>((int)h->n, h->npair,
+    k_reduce_pairs<<<RED_BLOCKS, RED_THREADS, 0, h->stream>>>(h->n, h->npair,
                                                              &h->stats->pairs);
     return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "reduce launch");
 }

@@ -1,6 +1,13 @@
 // dcm_internal.cuh -- internal declarations of libdcm (sm_103a).
 //
-// Device data layout (all in HBM, allocated once by dcm_create):
+// A handle holds M >= 1 independent systems (M = 1 from dcm_create, M =
+// count from dcm_ensemble_create).  Every kernel works on all systems at
+// once: per-system arrays are concatenated and each element finds its
+// system from the offset tables (p_off over particles, c_off over link
+// cells, v_off over voxels) of the device system table.
+//
+// Device data layout (all in HBM, allocated once at creation; N, Nc, Nv are
+// totals over the systems):
 //   state     x, v, f : double SoA [3][N] in the caller's particle order
 //   cutoffs   d, rc   : double [N];  cls : uint8 [N]   (id order)
 //   link cells        : cell_of[N], slot[N] (id order); cell_count[Nc],
@@ -42,13 +49,15 @@ enum : int {
 struct DevStats {
     unsigned long long guard_rechecks;
     unsigned long long pairs;
-    int kmeans_iters;
-    int cfsm_iters;
-    double c_liquid;
+    int kmeans_iters;            // largest over the systems
+    int cfsm_iters;              // passes of the last CFSM run
+    double c_liquid;             // system 0
     double c_vapor;
     int class_count[DCM_MAX_CLASSES];
-    unsigned int barrier[4];     // grid-barrier counter / generation words
+    unsigned int barrier[4];     // [0..1] grid barrier, [2] force queue, [3] CFSM result buffer
 };
+
+constexpr int MAX_SYSTEMS = 1024;
 
 // geometry and parameters passed by value to kernels
 struct Geom {
@@ -68,16 +77,55 @@ struct Geom {
     double thr[DCM_MAX_CLASSES]; // class thresholds on d (descending)
     double dt, hdtm;             // dt, dt/(2m)
     double eps, sigma;
+    double eps24, eps48, eps2, sig2;     // LJ force/energy constants
+    float eps24f, eps48f, eps2f, sig2f;
+    // this system's slices of the concatenated arrays
+    int64_t p0, c0, v0;
+    int64_t ncell, nvox;
 };
+
+// the system table every kernel receives
+struct Batch {
+    const Geom *sys;             // device table [M]
+    const int64_t *p_off;        // [M+1] particle offsets
+    const int64_t *c_off;        // [M+1] cell offsets
+    const int64_t *v_off;        // [M+1] voxel offsets
+    int M;
+    int K;                       // cutoff classes (same for all systems)
+    int64_t N, NC, NV;           // totals
+};
+
+// system owning element idx of a concatenated array (largest s with off[s] <= idx)
+__device__ __forceinline__ int sys_of(const int64_t *off, int M, int64_t idx)
+{
+    int lo = 0, hi = M - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&off[mid]) <= idx)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
 
 }  // namespace dcm
 
 struct dcm_handle {
-    dcm_box box;
-    int64_t n;
-    dcm_params p;
+    int M;                       // systems in this handle
+    dcm_box box;                 // system 0 (single-system convenience)
+    int64_t n;                   // total particles
+    dcm_params p;                // system 0's parameters (shared fields:
+                                 // precision, detect_every, n_classes,
+                                 // smooth_order, iteration caps)
     dcm_tuning tune;
-    dcm::Geom g;
+    dcm::Geom g;                 // system 0's geometry
+    dcm::Geom *geo_host;         // [M]
+    dcm_params *par_host;        // [M]
+    int64_t *off_host;           // [3*(M+1)]: p_off, c_off, v_off
+    dcm::Geom *geo_dev;
+    int64_t *off_dev;
+    dcm::Batch b;
     cudaStream_t stream;
     bool own_stream;
     int device;
@@ -105,11 +153,12 @@ struct dcm_handle {
     int32_t *stamp;
     int32_t *flist;              // 4 * nvox
     int32_t *fcount;             // 4 counters
-    unsigned long long *kacc;    // k-means accumulators (3 x 4 words)
     // per particle diagnostics / energies
     int32_t *npair;
     double *pe, *vir;
     double *red_part, *red_out;
+    unsigned long long *kacc;    // K-means accumulators: M x (max, min, total, 3 x (count, sum))
+    double *kstate;              // K-means per-system centres / previous counts: M x 4
     int *err;
     dcm::DevStats *stats;
     double *dfinal;              // which D buffer holds the result
@@ -143,11 +192,12 @@ int launch_kick(dcm_handle *h);
 int launch_bin(dcm_handle *h);
 int launch_forces(dcm_handle *h, bool energy);
 int launch_detect(dcm_handle *h);
-int launch_reduce_energy(dcm_handle *h);
+int launch_reduce_energy(dcm_handle *h, int k);
 int launch_reduce_pairs(dcm_handle *h);
 int launch_classify_rc(dcm_handle *h);   // classes from supplied rc
 
 // lower-level helpers
 int coop_grid_size(dcm_handle *h, const void *kernel, int block, size_t smem);
+int prepare_kernels(dcm_handle *h);      // per-handle kernel attributes
 
 }  // namespace dcm

@@ -29,7 +29,9 @@ EXPORTS = [
     "dcm_step", "dcm_energy_virial", "dcm_get_grid", "dcm_get_cutoffs", "dcm_get_cells",
     "dcm_get_pair_counts", "dcm_get_stats", "dcm_set_tuning", "dcm_get_tuning", "dcm_sync",
     "dcm_device_bytes", "dcm_estimate_bytes", "dcm_last_error", "dcm_version",
-    "dcm_set_timing", "dcm_get_phase_times",
+    "dcm_set_timing", "dcm_get_phase_times", "dcm_ensemble_create", "dcm_system_count",
+    "dcm_system_range", "dcm_ensemble_set_state", "dcm_ensemble_get_state",
+    "dcm_ensemble_energy_virial",
 ]
 DCM_NUM_PHASES = 5
 PHASES = ("kick_drift", "detect", "bin", "force", "kick")
@@ -106,6 +108,13 @@ def lib() -> C.CDLL:
         "dcm_estimate_bytes": (i64, [P(dcm_box), i64, P(dcm_params)]),
         "dcm_last_error": (C.c_char_p, []),
         "dcm_set_timing": (C.c_int, [vp, C.c_int]),
+        "dcm_ensemble_create": (C.c_int, [C.c_int, P(dcm_box), P(i64), P(dcm_params), vp,
+                                          P(vp)]),
+        "dcm_system_count": (C.c_int, [vp]),
+        "dcm_system_range": (C.c_int, [vp, C.c_int, P(i64), P(i64)]),
+        "dcm_ensemble_set_state": (C.c_int, [vp, C.c_int, dp, dp, C.c_int]),
+        "dcm_ensemble_get_state": (C.c_int, [vp, C.c_int, dp, dp, dp, C.c_int]),
+        "dcm_ensemble_energy_virial": (C.c_int, [vp, C.c_int, dp, dp, dp]),
         "dcm_get_phase_times": (C.c_int, [vp, dp]),
         "dcm_version": (C.c_int, []),
     }
@@ -280,6 +289,46 @@ def dcm_estimate_bytes(box, n: int, params: dcm_params | None = None) -> int:
     return int(lib().dcm_estimate_bytes(C.byref(b), int(n), C.byref(p)))
 
 
+def dcm_ensemble_create(boxes, ns, params_list, stream=None):
+    m = len(ns)
+    B = (dcm_box * m)(*[dcm_box(*b) for b in boxes])
+    Nn = (C.c_int64 * m)(*[int(x) for x in ns])
+    Pp = (dcm_params * m)(*params_list)
+    h = C.c_void_p()
+    s = C.c_void_p(stream) if stream else None
+    check(lib().dcm_ensemble_create(m, B, Nn, Pp, s, C.byref(h)))
+    return h
+
+
+def dcm_system_count(h) -> int:
+    return int(lib().dcm_system_count(h))
+
+
+def dcm_system_range(h, k: int):
+    a, b = C.c_int64(), C.c_int64()
+    check(lib().dcm_system_range(h, int(k), C.byref(a), C.byref(b)))
+    return a.value, b.value
+
+
+def dcm_ensemble_set_state(h, k: int, x, v=None) -> None:
+    px, mx = _ptr(x)
+    pv, _ = _ptr(v)
+    check(lib().dcm_ensemble_set_state(h, int(k), px, pv, mx))
+
+
+def dcm_ensemble_get_state(h, k: int, n: int):
+    x, v, f = np.empty((n, 3)), np.empty((n, 3)), np.empty((n, 3))
+    check(lib().dcm_ensemble_get_state(h, int(k), _ptr(x)[0], _ptr(v)[0], _ptr(f)[0], DCM_HOST))
+    return x, v, f
+
+
+def dcm_ensemble_energy_virial(h, k: int):
+    pe, ke = C.c_double(), C.c_double()
+    w = (C.c_double * 6)()
+    check(lib().dcm_ensemble_energy_virial(h, int(k), C.byref(pe), C.byref(ke), w))
+    return pe.value, ke.value, np.array(list(w))
+
+
 # ---- convenience wrapper ------------------------------------------------------
 class System:
     """One DCM system on the GPU (a dcm_handle)."""
@@ -365,3 +414,26 @@ class System:
 
     def device_bytes(self) -> int:
         return dcm_device_bytes(self.h)
+
+
+class Ensemble(System):
+    """Many independent systems in one handle: one set of kernels and one
+    persistent force launch per step for all of them."""
+
+    def __init__(self, boxes, ns, params_list, stream=None):
+        self.boxes = [tuple(float(q) for q in b) for b in boxes]
+        self.ns = [int(q) for q in ns]
+        self.n = sum(self.ns)
+        self.params = params_list[0]
+        self.h = dcm_ensemble_create(self.boxes, self.ns, params_list, stream)
+        self.ranges = [dcm_system_range(self.h, k) for k in range(len(self.ns))]
+
+    def set_system_state(self, k, x, v=None):
+        dcm_ensemble_set_state(self.h, k, np.ascontiguousarray(x, np.float64),
+                               None if v is None else np.ascontiguousarray(v, np.float64))
+
+    def get_system_state(self, k):
+        return dcm_ensemble_get_state(self.h, k, self.ns[k])
+
+    def system_energy(self, k):
+        return dcm_ensemble_energy_virial(self.h, k)
