@@ -33,12 +33,15 @@ UNIT = "atom-steps/s"
 N_DEFAULT = 262144
 FP32_LANES_PER_SM = 128          # Blackwell SM: 4 sub-partitions x 32 FP32 lanes
 FLOPS_PER_PAIR = 24              # 8 (distance test) + 16 (LJ force), per in-cutoff pair
+# DRAM bytes (read + write) per force launch from the committed ncu capture
+# (profiles/k_force_N262144_mixed.md); None once the kernel changes
+FORCE_TRAFFIC = {"mixed": 10.73e6, "fp64": None}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="dcm", choices=["dcm", "reference"])
     ap.add_argument("--n", type=int, default=N_DEFAULT)
@@ -151,17 +154,13 @@ def run_reference(args):
     p = oracle.RunParams(det=oracle.DetectParams(rc_min=3.0, rc_max=6.0, voxel=1.0),
                          dt=0.005, cell_min=1.5, detect_every=2)
     x, v = s.x, s.v
-    step0 = 0
-    for _ in range(args.warmup):
-        x, v, *_ = oracle.run(x, v, s.box, p, 1, step0=step0)
-        step0 += 1
-    times = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        x, v, *_ = oracle.run(x, v, s.box, p, 1, step0=step0)
-        times.append(time.perf_counter() - t0)
-        step0 += 1
-    total = sum(times)
+    if args.warmup > 0:
+        x, v, *_ = oracle.run(x, v, s.box, p, args.warmup)
+    # one call for all timed steps: its setup (one detection + one force
+    # evaluation) is the only work beyond the K steps
+    t0 = time.perf_counter()
+    oracle.run(x, v, s.box, p, args.steps, step0=args.warmup)
+    total = time.perf_counter() - t0
     value = n_sample * args.steps / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -169,8 +168,9 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(args.n, "fp64 CPU oracle"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"N={n_sample} slab of the same shape; each step = setup "
-                                       f"(detect + force) + 1 velocity-Verlet step of the oracle"},
+                             "sample": f"N={n_sample} slab of the same shape and cutoffs "
+                                       f"(atom-steps/s is size-independent for this linear-time "
+                                       f"method); K oracle steps in one run after W warm-up steps"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -274,7 +274,8 @@ def main():
     sm_mhz = clocks.get("sm_mhz") or 1477.0
     peak = 152 * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak,
+                "traffic": FORCE_TRAFFIC.get(args.precision) if n == N_DEFAULT else None,
                 "kernel": "k_force (mixed)" if prec == dcm.DCM_MIXED else "k_force (fp64)",
                 "peak_note": "FP32 FMA peak derived from 152 SMs x 128 lanes x 2 flops x the "
                              "median SM clock sampled during the timed region",

@@ -209,6 +209,14 @@ int dcm_ensemble_energy_virial(dcm_handle *h, int k, double *pe, double *ke,
 
 /* Waits for the handle's stream; returns the sticky device error, if any. */
 int dcm_sync(dcm_handle *h);
+/* Failure-detection self-check (no counterpart in the thesis): launches the
+ * library's bounded grid barrier with one block that never arrives.  The
+ * waiting block gives up after its poll limit (well under a second), flags
+ * the device error and returns, so the call returns DCM_ERR_DEVICE_CHECK
+ * and the handle stays usable.  Any other result means waits are not
+ * bounded. */
+int dcm_check_bounded_wait(dcm_handle *h);
+
 /* Total device bytes the handle holds. */
 int64_t dcm_device_bytes(const dcm_handle *h);
 /* Device bytes dcm_create would allocate for this system. */

@@ -831,3 +831,11 @@ extern "C" int dcm_sync(dcm_handle *h)
 }
 
 extern "C" int64_t dcm_device_bytes(const dcm_handle *h) { return h ? h->bytes : 0; }
+
+extern "C" int dcm_check_bounded_wait(dcm_handle *h)
+{
+    if (!h) return fail(DCM_ERR_ARG, "null handle");
+    int r = launch_barrier_timeout_check(h);
+    if (r) return r;
+    return dcm_sync(h);
+}

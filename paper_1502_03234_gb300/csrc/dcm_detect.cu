@@ -513,6 +513,24 @@ int coop_grid_size(dcm_handle *h, const void *kernel, int block, size_t smem)
     return h->num_sms * per_sm;
 }
 
+// Failure-detection check of the bounded grid barrier: block 1 leaves
+// without arriving, so block 0 waits for an arrival that never comes; the
+// bounded poll gives up, sets DEV_ERR_BARRIER and the kernel returns.
+__global__ void k_barrier_timeout_check(unsigned int *bar, int *err)
+{
+    if (blockIdx.x == 1) return;
+    grid_barrier(bar, err);
+}
+
+int launch_barrier_timeout_check(dcm_handle *h)
+{
+    cudaMemsetAsync(h->stats->barrier, 0, 2 * sizeof(unsigned int), h->stream);
+    unsigned int *bar = h->stats->barrier;
+    int *err = h->err;
+    void *args[] = {(void *)&bar, (void *)&err};
+    return coop_launch(h, (const void *)k_barrier_timeout_check, 2, 0, args);
+}
+
 static size_t kmeans_smem(int M) { return (size_t)M * (4 * 8 + 3 * 8 + 4); }
 
 int prepare_kernels(dcm_handle *h)

@@ -92,18 +92,24 @@ __device__ __forceinline__ bool grid_barrier(unsigned int *words, int *err)
             __threadfence();
             atomicAdd(words + 1, 1u);
         } else {
+            // tight polling first (a healthy barrier completes in a few
+            // microseconds), then back off; the error word is read only every
+            // 256 polls.  The limit bounds the wait to well under a second.
             long long polls = 0;
             while (*gen == g) {
-                if (++polls > (1ll << 22)) {   // ~0.5 s with the back-off below
-                    atomicOr(err, DEV_ERR_BARRIER);
-                    ok = 0;
-                    break;
+                ++polls;
+                if ((polls & 255) == 0) {
+                    if (polls > (1ll << 21)) {
+                        atomicOr(err, DEV_ERR_BARRIER);
+                        ok = 0;
+                        break;
+                    }
+                    if (*(volatile int *)err & DEV_ERR_BARRIER) {
+                        ok = 0;
+                        break;
+                    }
                 }
-                if (*(volatile int *)err & DEV_ERR_BARRIER) {
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(64);
+                if (polls > 4096) __nanosleep(128);
             }
         }
         __threadfence();

@@ -199,5 +199,6 @@ int launch_classify_rc(dcm_handle *h);   // classes from supplied rc
 // lower-level helpers
 int coop_grid_size(dcm_handle *h, const void *kernel, int block, size_t smem);
 int prepare_kernels(dcm_handle *h);      // per-handle kernel attributes
+int launch_barrier_timeout_check(dcm_handle *h);
 
 }  // namespace dcm

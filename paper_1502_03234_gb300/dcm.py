@@ -31,7 +31,7 @@ EXPORTS = [
     "dcm_device_bytes", "dcm_estimate_bytes", "dcm_last_error", "dcm_version",
     "dcm_set_timing", "dcm_get_phase_times", "dcm_ensemble_create", "dcm_system_count",
     "dcm_system_range", "dcm_ensemble_set_state", "dcm_ensemble_get_state",
-    "dcm_ensemble_energy_virial",
+    "dcm_ensemble_energy_virial", "dcm_check_bounded_wait",
 ]
 DCM_NUM_PHASES = 5
 PHASES = ("kick_drift", "detect", "bin", "force", "kick")
@@ -111,6 +111,7 @@ def lib() -> C.CDLL:
         "dcm_ensemble_create": (C.c_int, [C.c_int, P(dcm_box), P(i64), P(dcm_params), vp,
                                           P(vp)]),
         "dcm_system_count": (C.c_int, [vp]),
+        "dcm_check_bounded_wait": (C.c_int, [vp]),
         "dcm_system_range": (C.c_int, [vp, C.c_int, P(i64), P(i64)]),
         "dcm_ensemble_set_state": (C.c_int, [vp, C.c_int, dp, dp, C.c_int]),
         "dcm_ensemble_get_state": (C.c_int, [vp, C.c_int, dp, dp, dp, C.c_int]),

@@ -39,11 +39,16 @@ def fcc_edge(rho: float = RHO_L) -> float:
     return (4.0 / rho) ** (1.0 / 3.0)
 
 
-def box_for(n: int, rho_l: float = RHO_L, rho_v: float = RHO_V) -> tuple[int, tuple]:
-    """(n_x FCC cells, (Lx, Ly, Lz)) for an N-particle slab."""
+def box_for(n: int, rho_l: float = RHO_L, rho_v: float = RHO_V,
+            min_edge: float | None = None) -> tuple[int, tuple]:
+    """(n_x FCC cells, (Lx, Ly, Lz)) for an N-particle slab.  min_edge raises
+    the lateral edge for small N (the slab then gets thinner), so that a
+    cutoff of about (min_edge - a few cells)/2 still fits the minimum image."""
     a = fcc_edge(rho_l)
     lx_target = (n / (rho_l * 4.0 / 3.0 + rho_v * 8.0 / 3.0)) ** (1.0 / 3.0)
     nx = max(1, int(round(lx_target / a)))
+    if min_edge:
+        nx = max(nx, int(math.ceil(min_edge / a)))
     L = nx * a
     return nx, (L, L, 4.0 * L)
 
@@ -125,14 +130,15 @@ def maxwell(rng, n: int, temperature: float, mass: float = 1.0) -> np.ndarray:
 
 def make_slab(n: int, temperature: float = 0.7, seed: int = 0, *, rho_l: float = RHO_L,
               rho_v: float = RHO_V, jitter: float = 0.05, min_sep: float = 0.8,
-              capillary_amp: float = 0.0, mass: float = 1.0) -> Slab:
+              capillary_amp: float = 0.0, mass: float = 1.0,
+              min_edge: float | None = None) -> Slab:
     """Jittered-FCC liquid slab across the box centre plus uniform vapor.
 
     capillary_amp > 0 perturbs both liquid/vapor planes by three sinusoidal
     modes with independent random phases (|h| <= capillary_amp)."""
     rng = np.random.default_rng(seed)
     a = fcc_edge(rho_l)
-    nx, box = box_for(n, rho_l, rho_v)
+    nx, box = box_for(n, rho_l, rho_v, min_edge)
     Lx, Ly, Lz = box
     denom = 4 * nx * nx - rho_v * Lx * Ly * a
     nz = int(math.floor((n - rho_v * Lx * Ly * Lz) / denom))
