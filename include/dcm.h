@@ -217,6 +217,44 @@ int dcm_sync(dcm_handle *h);
  * bounded. */
 int dcm_check_bounded_wait(dcm_handle *h);
 
+/* ---- allocation-free link-cell sort ------------------------------------------
+ * The thesis has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory when they need a cell list -- a host
+ * application whose memory pool owns the whole device and forbids
+ * allocations outside it, or a latency-bound loop that cannot afford
+ * cudaMalloc/cudaFree (both synchronise the device).  It returns the same
+ * cell list as the handle-based path (dcm_get_cells): cells of edge L/nc,
+ * cell index = min(nc-1, floor(x * nc/L)) per axis, x fastest, particles of
+ * a cell in ascending index.
+ *
+ *   x          device, AoS double[3*n], positions already wrapped into the box
+ *   n          1 .. DCM_NOALLOC_MAX_PARTICLES
+ *   box, nc    box edges and cells per axis; nc[0]*nc[1]*nc[2] must not
+ *              exceed DCM_NOALLOC_MAX_CELLS
+ *   cell_start device int32[ncell + 1], written (exclusive prefix of counts)
+ *   sorted_id  device int32[n], written (particle indices in cell order)
+ *   stream     cudaStream_t the work is enqueued on (NULL: legacy stream)
+ *
+ * It calls no cudaMalloc, cudaFree or allocating library routine: its scratch
+ * (per-cell counts, per-particle slots, scan sums) is one fixed device array
+ * of DCM_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
+ * the process exits.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress) with the device current; make that first
+ * call before any stream capture.  All calls share the array and it keeps the
+ * last call's contents (the counts are cleared at the start of each call), so
+ * calls that overlap on the GPU -- on different streams or devices' shared
+ * contexts without ordering between them -- race and must be serialised by
+ * the caller.  Errors: DCM_ERR_ARG for a null pointer, a non-positive edge or
+ * cell count, or sizes beyond the maxima (nothing is launched); DCM_ERR_CUDA
+ * if the set-up or a launch fails.  Returns after enqueueing the work. */
+#define DCM_NOALLOC_MAX_PARTICLES (1 << 19)
+#define DCM_NOALLOC_MAX_CELLS (1 << 20)
+#define DCM_NOALLOC_SCRATCH_BYTES \
+    (4 * (DCM_NOALLOC_MAX_CELLS + DCM_NOALLOC_MAX_PARTICLES + (DCM_NOALLOC_MAX_CELLS + 2047) / 2048))
+int dcm_cell_sort_noalloc(const double *x, int64_t n, const dcm_box *box,
+                          const int32_t nc[3], int32_t *cell_start,
+                          int32_t *sorted_id, void *stream);
+
 /* Total device bytes the handle holds. */
 int64_t dcm_device_bytes(const dcm_handle *h);
 /* Device bytes dcm_create would allocate for this system. */

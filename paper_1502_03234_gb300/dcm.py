@@ -31,7 +31,7 @@ EXPORTS = [
     "dcm_device_bytes", "dcm_estimate_bytes", "dcm_last_error", "dcm_version",
     "dcm_set_timing", "dcm_get_phase_times", "dcm_ensemble_create", "dcm_system_count",
     "dcm_system_range", "dcm_ensemble_set_state", "dcm_ensemble_get_state",
-    "dcm_ensemble_energy_virial", "dcm_check_bounded_wait",
+    "dcm_ensemble_energy_virial", "dcm_check_bounded_wait", "dcm_cell_sort_noalloc",
 ]
 DCM_NUM_PHASES = 5
 PHASES = ("kick_drift", "detect", "bin", "force", "kick")
@@ -112,6 +112,7 @@ def lib() -> C.CDLL:
                                           P(vp)]),
         "dcm_system_count": (C.c_int, [vp]),
         "dcm_check_bounded_wait": (C.c_int, [vp]),
+        "dcm_cell_sort_noalloc": (C.c_int, [dp, i64, P(dcm_box), dp, dp, dp, vp]),
         "dcm_system_range": (C.c_int, [vp, C.c_int, P(i64), P(i64)]),
         "dcm_ensemble_set_state": (C.c_int, [vp, C.c_int, dp, dp, C.c_int]),
         "dcm_ensemble_get_state": (C.c_int, [vp, C.c_int, dp, dp, dp, C.c_int]),
@@ -288,6 +289,18 @@ def dcm_estimate_bytes(box, n: int, params: dcm_params | None = None) -> int:
     b = dcm_box(*box)
     p = params if params is not None else default_params()
     return int(lib().dcm_estimate_bytes(C.byref(b), int(n), C.byref(p)))
+
+
+def dcm_cell_sort_noalloc(x_dev, n: int, box, nc, cell_start_dev, sorted_id_dev,
+                          stream=None) -> None:
+    """Allocation-free link-cell sort on device buffers (torch CUDA tensors:
+    x float64 [n, 3], cell_start int32 [ncell + 1], sorted_id int32 [n])."""
+    b = dcm_box(*box)
+    ncv = (C.c_int32 * 3)(*[int(q) for q in nc])
+    s = C.c_void_p(stream) if stream else None
+    check(lib().dcm_cell_sort_noalloc(C.c_void_p(x_dev.data_ptr()), int(n), C.byref(b), ncv,
+                                      C.c_void_p(cell_start_dev.data_ptr()),
+                                      C.c_void_p(sorted_id_dev.data_ptr()), s))
 
 
 def dcm_ensemble_create(boxes, ns, params_list, stream=None):
