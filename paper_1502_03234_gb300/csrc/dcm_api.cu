@@ -351,7 +351,7 @@ static int create_systems(int M, const dcm_box *boxes, const int64_t *ns, const 
     ALLOC(h->stamp, nv);
     ALLOC(h->flist, 4 * nv);
     ALLOC(h->fcount, 4);
-    ALLOC(h->kacc, 9 * (int64_t)M);
+    ALLOC(h->kacc, 9 * 16 * (int64_t)M);   // K-means sums, 16 spread slots each
     ALLOC(h->npair, N);
     ALLOC(h->pe, N);
     ALLOC(h->vir, 6 * N);

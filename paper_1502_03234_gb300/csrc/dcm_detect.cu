@@ -55,48 +55,62 @@ __global__ void k_smooth(Batch b, const TIN *__restrict__ in, TOUT *out, SmoothW
     if (v >= b.NV) return;
     const Geom &g = b.sys[sys_of(b.v_off, b.M, v)];
     const int nx = g.gd[0], ny = g.gd[1], nz = g.gd[2];
-    int64_t lv = v - g.v0;
-    int x = (int)(lv % nx);
-    int y = (int)((lv / nx) % ny);
-    int z = (int)(lv / ((int64_t)nx * ny));
-    int n = AXIS == 0 ? nx : (AXIS == 1 ? ny : nz);
-    int c = AXIS == 0 ? x : (AXIS == 1 ? y : z);
-    int64_t stride = AXIS == 0 ? 1 : (AXIS == 1 ? (int64_t)nx : (int64_t)nx * ny);
-    int64_t base = v - (int64_t)c * stride;
-    int half = w.order / 2;
+    const int lv = (int)(v - g.v0);              // 32-bit index math
+    const int x = lv % nx, yz = lv / nx;
+    const int y = yz % ny, z = yz / ny;
+    const int n = AXIS == 0 ? nx : (AXIS == 1 ? ny : nz);
+    const int c = AXIS == 0 ? x : (AXIS == 1 ? y : z);
+    const int stride = AXIS == 0 ? 1 : (AXIS == 1 ? nx : nx * ny);
+    const TIN *line = in + (v - (int64_t)c * stride);
+    const int half = w.order / 2;
     if constexpr (AXIS == 0) {
         if ((uint32_t)in[v] > w.bmax) atomicOr(err, DEV_ERR_DENSITY);
     }
+    // periodic tap index: one conditional wrap while the kernel fits in the
+    // line, a full modulo only for lines shorter than the kernel
+    auto tap = [&](int k) {
+        int q = c + k - half;
+        if (n > w.order) {
+            q += q < 0 ? n : 0;
+            q -= q >= n ? n : 0;
+        } else {
+            q = ((q % n) + n) % n;
+        }
+        return line[q * stride];
+    };
     if constexpr (sizeof(TOUT) == 8) {
         unsigned long long s = 0;
-        for (int k = 0; k <= w.order; ++k) {
-            int q = ((c + k - half) % n + n) % n;
-            s += (unsigned long long)w.w[k] * (unsigned long long)in[base + (int64_t)q * stride];
-        }
+        for (int k = 0; k <= w.order; ++k) s += (unsigned long long)w.w[k] * (unsigned long long)tap(k);
         out[v] = (TOUT)s;
     } else {
         uint32_t s = 0;
-        for (int k = 0; k <= w.order; ++k) {
-            int q = ((c + k - half) % n + n) % n;
-            s += w.w[k] * (uint32_t)in[base + (int64_t)q * stride];
-        }
+        for (int k = 0; k <= w.order; ++k) s += w.w[k] * (uint32_t)tap(k);
         out[v] = (TOUT)s;
     }
 }
 
 // ---- K-means (Eq. 14, K = 2), all systems in one cooperative kernel ------------
-// global accumulators per system s (9 words): [0] max, [1] min, [2] total,
-// then three rotating (count, sum) pairs
-constexpr int KACC = 9;
+// global accumulators per system s, each spread over SPREAD slots (a block
+// adds into slot blockIdx % SPREAD, readers sum the slots) so that hundreds
+// of blocks do not serialise on one address: [max | min | total] then three
+// rotating (count | sum) pairs
+constexpr int SPREAD = 16;
+constexpr int KACC = 9 * SPREAD;
 
 __global__ void k_kmeans_init(int M, unsigned long long *acc)
 {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= M) return;
-    unsigned long long *a = acc + (int64_t)KACC * s;
-    a[0] = 0ull;
-    a[1] = ~0ull;
-    for (int q = 2; q < KACC; ++q) a[q] = 0ull;
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (int64_t)M * KACC) return;
+    int w = (int)(q % KACC) / SPREAD;
+    acc[q] = w == 1 ? ~0ull : 0ull;
+}
+
+__device__ __forceinline__ unsigned long long spread_sum(const unsigned long long *p)
+{
+    unsigned long long t = 0;
+#pragma unroll
+    for (int q = 0; q < SPREAD; ++q) t += __ldcg(&p[q]);
+    return t;
 }
 
 struct KmeansArgs {
@@ -109,6 +123,30 @@ struct KmeansArgs {
     int *err;
     DevStats *st;
 };
+
+// warp-level reduction of a per-lane value when every lane holds the same
+// system (the common case); otherwise each lane adds its own value
+template <int OP>
+__device__ __forceinline__ void warp_flush(int cur, unsigned long long v, unsigned long long *slot)
+{
+    const unsigned full = 0xffffffffu;
+    int c0 = __shfl_sync(full, cur, 0);
+    if (__all_sync(full, cur == c0)) {
+        for (int off = 16; off > 0; off >>= 1) {
+            unsigned long long o = __shfl_xor_sync(full, v, off);
+            v = OP == 0 ? v + o : (OP == 1 ? (o > v ? o : v) : (o < v ? o : v));
+        }
+        if ((threadIdx.x & 31) == 0 && cur >= 0) {
+            if (OP == 0) atomicAdd(&slot[c0], v);
+            else if (OP == 1) atomicMax(&slot[c0], v);
+            else atomicMin(&slot[c0], v);
+        }
+    } else if (cur >= 0) {
+        if (OP == 0) atomicAdd(&slot[cur], v);
+        else if (OP == 1) atomicMax(&slot[cur], v);
+        else atomicMin(&slot[cur], v);
+    }
+}
 
 // per-block shared state: centres, previous liquid count, threshold and the
 // done flag of every system (every block derives the same values from the
@@ -158,27 +196,32 @@ __global__ void __launch_bounds__(DET_THREADS) k_kmeans(KmeansArgs a)
             mn = bv < mn ? bv : mn;
             tot += bv;
         }
-        if (cur >= 0) {
-            atomicMax(&s_c0[cur], mx);
-            atomicMin(&s_c1[cur], mn);
-            atomicAdd(&s_c2[cur], tot);
-        }
+        warp_flush<1>(cur, mx, s_c0);
+        warp_flush<2>(cur, mn, s_c1);
+        warp_flush<0>(cur, tot, s_c2);
     }
     __syncthreads();
+    const int slot = blockIdx.x % SPREAD;
     for (int s = threadIdx.x; s < M; s += blockDim.x) {
         if (s_c1[s] == ~0ull) continue;   // no voxel of s in this block
         unsigned long long *g = a.acc + (int64_t)KACC * s;
-        atomicMax(&g[0], s_c0[s]);
-        atomicMin(&g[1], s_c1[s]);
-        atomicAdd(&g[2], s_c2[s]);
+        atomicMax(&g[0 * SPREAD + slot], s_c0[s]);
+        atomicMin(&g[1 * SPREAD + slot], s_c1[s]);
+        atomicAdd(&g[2 * SPREAD + slot], s_c2[s]);
     }
     if (!grid_barrier(a.bar, a.err)) return;
     // values other blocks produced are read through L2 (ld.global.cg): the
     // per-SM L1 caches are not coherent across a grid barrier
     for (int s = threadIdx.x; s < M; s += blockDim.x) {
         const unsigned long long *g = a.acc + (int64_t)KACC * s;
-        s_cl[s] = (double)__ldcg(&g[0]);
-        s_cv[s] = (double)__ldcg(&g[1]);
+        unsigned long long mx = 0, mn = ~0ull;
+        for (int q = 0; q < SPREAD; ++q) {
+            unsigned long long u = __ldcg(&g[q]), l = __ldcg(&g[SPREAD + q]);
+            mx = u > mx ? u : mx;
+            mn = l < mn ? l : mn;
+        }
+        s_cl[s] = (double)mx;
+        s_cv[s] = (double)mn;
         s_prev[s] = -1;
         s_done[s] = 0;
         s_thr[s] = DMUL(DADD(s_cl[s], s_cv[s]), 0.5);
@@ -211,21 +254,18 @@ __global__ void __launch_bounds__(DET_THREADS) k_kmeans(KmeansArgs a)
                 sum += (unsigned long long)bv;
             }
         }
-        if (cur >= 0 && cnt) {
-            atomicAdd(&s_c0[cur], cnt);
-            atomicAdd(&s_c1[cur], sum);
-        }
+        warp_flush<0>(cur, cnt, s_c0);
+        warp_flush<0>(cur, sum, s_c1);
         __syncthreads();
         for (int s = threadIdx.x; s < M; s += blockDim.x) {
-            unsigned long long *g = a.acc + (int64_t)KACC * s + 3 + 2 * (it % 3);
+            unsigned long long *g = a.acc + (int64_t)KACC * s + (3 + 2 * (it % 3)) * SPREAD;
             if (s_c0[s]) {
-                atomicAdd(&g[0], s_c0[s]);
-                atomicAdd(&g[1], s_c1[s]);
+                atomicAdd(&g[slot], s_c0[s]);
+                atomicAdd(&g[SPREAD + slot], s_c1[s]);
             }
             if (blockIdx.x == 0) {   // clear the pair of the next pass
-                unsigned long long *nx = a.acc + (int64_t)KACC * s + 3 + 2 * ((it + 1) % 3);
-                nx[0] = 0ull;
-                nx[1] = 0ull;
+                unsigned long long *nx = a.acc + (int64_t)KACC * s + (3 + 2 * ((it + 1) % 3)) * SPREAD;
+                for (int q = 0; q < 2 * SPREAD; ++q) nx[q] = 0ull;
             }
         }
         if (!grid_barrier(a.bar, a.err)) return;
@@ -234,16 +274,16 @@ __global__ void __launch_bounds__(DET_THREADS) k_kmeans(KmeansArgs a)
         __syncthreads();
         for (int s = threadIdx.x; s < M; s += blockDim.x) {
             if (s_done[s]) continue;
-            const unsigned long long *g = a.acc + (int64_t)KACC * s + 3 + 2 * ((it - 1) % 3);
-            long long nl = (long long)__ldcg(&g[0]);
-            unsigned long long sl = __ldcg(&g[1]);
+            const unsigned long long *g = a.acc + (int64_t)KACC * s + (3 + 2 * ((it - 1) % 3)) * SPREAD;
+            long long nl = (long long)spread_sum(g);
+            unsigned long long sl = spread_sum(g + SPREAD);
             if (nl == s_prev[s]) {   // same threshold set as the previous pass
                 s_done[s] = 1;
                 continue;
             }
             const Geom &geo = a.b.sys[s];
             long long nvap = geo.nvox - nl;
-            unsigned long long total = __ldcg(&a.acc[(int64_t)KACC * s + 2]);
+            unsigned long long total = spread_sum(a.acc + (int64_t)KACC * s + 2 * SPREAD);
             if (nl > 0) s_cl[s] = (double)sl / (double)nl;
             if (nvap > 0) s_cv[s] = (double)(total - sl) / (double)nvap;
             s_prev[s] = nl;
@@ -286,8 +326,9 @@ __global__ void k_cfsm_init(Batch b, const uint8_t *__restrict__ S, double *D0, 
         const Geom &g = b.sys[sys_of(b.v_off, b.M, v)];
         const int nx = g.gd[0], ny = g.gd[1], nz = g.gd[2];
         const uint8_t *Sg = S + g.v0;
-        int64_t lv = v - g.v0;
-        int x = (int)(lv % nx), y = (int)((lv / nx) % ny), z = (int)(lv / ((int64_t)nx * ny));
+        int lv = (int)(v - g.v0);
+        int x = lv % nx, yz = lv / nx;
+        int y = yz % ny, z = yz / ny;
         int xm = x ? x - 1 : nx - 1, xp = x + 1 < nx ? x + 1 : 0;
         int ym = y ? y - 1 : ny - 1, yp = y + 1 < ny ? y + 1 : 0;
         int zm = z ? z - 1 : nz - 1, zp = z + 1 < nz ? z + 1 : 0;
@@ -332,23 +373,25 @@ __global__ void __launch_bounds__(DET_THREADS) k_cfsm(CfsmArgs a)
             break;
         }
         if (tid == 0) a.fcount[(k + 2) & 3] = 0;   // list two passes ahead
-        int32_t push[7];
-        for (int64_t q0 = tid - (tid & 31); q0 < nf; q0 += nth) {
-            int64_t q = q0 + (tid & 31);
-            bool active = q < nf;
-            bool changed = false;
-            if (active) {
+        const int lane = (int)(threadIdx.x & 31);
+        for (int64_t q0 = tid - lane; q0 < nf; q0 += nth) {
+            int q = (int)q0 + lane;
+            int32_t push[7];
+            int npush = 0;
+            if (q < nf) {
                 int v = __ldcg(&F[q]);
                 const Geom &g = a.b.sys[sys_of(a.b.v_off, a.b.M, v)];
                 const int nx = g.gd[0], ny = g.gd[1], nz = g.gd[2];
-                int64_t lv = v - g.v0;
-                int x = (int)(lv % nx), y = (int)((lv / nx) % ny), z = (int)(lv / ((int64_t)nx * ny));
+                const int v0 = (int)g.v0;
+                int lv = v - v0;                         // 32-bit index math
+                int x = lv % nx, yz = lv / nx;
+                int y = yz % ny, z = yz / ny;
                 int xm = x ? x - 1 : nx - 1, xp = x + 1 < nx ? x + 1 : 0;
                 int ym = y ? y - 1 : ny - 1, yp = y + 1 < ny ? y + 1 : 0;
                 int zm = z ? z - 1 : nz - 1, zp = z + 1 < nz ? z + 1 : 0;
-                int64_t nb[6] = {g.v0 + vox(xm, y, z, nx, ny), g.v0 + vox(xp, y, z, nx, ny),
-                                 g.v0 + vox(x, ym, z, nx, ny), g.v0 + vox(x, yp, z, nx, ny),
-                                 g.v0 + vox(x, y, zm, nx, ny), g.v0 + vox(x, y, zp, nx, ny)};
+                int nb[6] = {v0 + xm + nx * yz, v0 + xp + nx * yz,
+                             v0 + x + nx * (ym + ny * z), v0 + x + nx * (yp + ny * z),
+                             v0 + x + nx * (y + ny * zm), v0 + x + nx * (y + ny * zp)};
                 // D and the lists were written by other blocks in the previous
                 // pass: read them through L2 (ld.global.cg), not a stale L1
                 double old = __ldcg(&X[v]);
@@ -356,31 +399,38 @@ __global__ void __launch_bounds__(DET_THREADS) k_cfsm(CfsmArgs a)
                 double ay = fmin(__ldcg(&X[nb[2]]), __ldcg(&X[nb[3]]));
                 double az = fmin(__ldcg(&X[nb[4]]), __ldcg(&X[nb[5]]));
                 double dbar = godunov(ax, ay, az, g.h[0], g.h[1], g.h[2]);
-                changed = dbar < old && dbar <= g.r_grid;
+                bool changed = dbar < old && dbar <= g.r_grid;
                 Y[v] = changed ? dbar : old;
                 if (changed) {
                     // the voxel itself (so Y catches up next pass) and its
-                    // liquid face neighbours are recomputed in the next pass
-                    push[0] = atomicExch(&a.stamp[v], k + 1) != k + 1 ? v : -1;
-                    for (int e = 0; e < 6; ++e) {
-                        int64_t u = nb[e];
-                        push[1 + e] = (a.S[u] == 0 && atomicExch(&a.stamp[u], k + 1) != k + 1)
-                                          ? (int32_t)u
-                                          : -1;
-                    }
+                    // liquid face neighbours are recomputed in the next pass;
+                    // the seven stamp exchanges are independent of each other
+                    int cand[7] = {v, nb[0], nb[1], nb[2], nb[3], nb[4], nb[5]};
+                    bool liq[7];
+                    liq[0] = true;
+#pragma unroll
+                    for (int e = 1; e < 7; ++e) liq[e] = a.S[cand[e]] == 0;
+                    int prev[7];
+#pragma unroll
+                    for (int e = 0; e < 7; ++e) prev[e] = liq[e] ? atomicExch(&a.stamp[cand[e]], k + 1) : k + 1;
+#pragma unroll
+                    for (int e = 0; e < 7; ++e)
+                        if (prev[e] != k + 1) push[npush++] = cand[e];
                 }
             }
-            // warp-aggregated append: one atomic per warp and slot
-            for (int e = 0; e < 7; ++e) {
-                int32_t item = changed ? push[e] : -1;
-                unsigned m = __ballot_sync(0xffffffffu, item >= 0);
-                if (!m) continue;
-                int leader = __ffs(m) - 1;
+            // one append per warp: exclusive scan of the lanes' counts
+            int incl = npush;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                int t = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= off) incl += t;
+            }
+            int total = __shfl_sync(0xffffffffu, incl, 31);
+            if (total) {
                 int base = 0;
-                if ((int)(threadIdx.x & 31) == leader)
-                    base = atomicAdd(&a.fcount[(k + 1) & 3], __popc(m));
-                base = __shfl_sync(0xffffffffu, base, leader);
-                if (item >= 0) Fn[base + __popc(m & ((1u << (threadIdx.x & 31)) - 1u))] = item;
+                if (lane == 31) base = atomicAdd(&a.fcount[(k + 1) & 3], total);
+                base = __shfl_sync(0xffffffffu, base, 31) + incl - npush;
+                for (int e = 0; e < npush; ++e) Fn[base + e] = push[e];
             }
         }
         if (!grid_barrier(a.bar, a.err)) return;
@@ -418,9 +468,12 @@ __global__ void k_cutoff(Batch b, const double *__restrict__ x, const double *__
     }
     const int nx = g.gd[0], ny = g.gd[1];
     const double rg = g.r_grid;
+    const long long rgb = __double_as_longlong(rg);
+    // distances are >= 0 (or +inf), so min(v, r_grid) is an integer
+    // comparison of the bit patterns (no FP64 compare on the slow pipe)
     auto Dv = [&](int X, int Y, int Z) {
         double v = D[X + (int64_t)nx * (Y + (int64_t)ny * Z)];
-        return v < rg ? v : rg;   // voxels CFSM never reached
+        return __double_as_longlong(v) < rgb ? v : rg;   // voxels CFSM never reached
     };
     double v000 = Dv(i0[0], i0[1], i0[2]), v100 = Dv(i1[0], i0[1], i0[2]);
     double v010 = Dv(i0[0], i1[1], i0[2]), v110 = Dv(i1[0], i1[1], i0[2]);
@@ -443,17 +496,22 @@ __global__ void k_cutoff(Batch b, const double *__restrict__ x, const double *__
         double c1 = lerp_rn(c01, c11, t[1]);
         di = lerp_rn(c0, c1, t[2]);
     }
+    // d >= 0 here (a convex combination of non-negative distances), so the
+    // comparisons below are exact integer comparisons of the bit patterns
+    const long long db = __double_as_longlong(di);
+    const long long rmaxb = __double_as_longlong(g.rc_max);
     double r;
-    if (di <= 0.0)
+    if (db <= 0)
         r = g.rc_max;
-    else if (di >= g.rc_max)
+    else if (db >= rmaxb)
         r = g.rc_min;
     else
         r = DADD(DMUL(g.cut_a, exp2(DMUL(g.alpha, DSUB(g.rc_max, di)))), g.cut_b);
     int c = 0;
-    if (di < g.rc_max) {
+    if (db < rmaxb) {
         c = 1;
-        for (int k = 0; k < b.K - 2; ++k) c += di < g.thr[k] ? 1 : 0;
+        for (int k = 0; k < b.K - 2; ++k)
+            c += db < __double_as_longlong(g.thr[k]) ? 1 : 0;   // thresholds are >= 0
     }
     d[i] = di;
     rc[i] = r;
@@ -576,7 +634,7 @@ int launch_detect(dcm_handle *h)
         k_smooth<0, int32_t, double><<<vb, DET_THREADS, 0, s>>>(b, h->B, h->Bs, w, h->err);
     }
     // K-means labels
-    k_kmeans_init<<<nblk(b.M, 128), 128, 0, s>>>(b.M, h->kacc);
+    k_kmeans_init<<<nblk((int64_t)b.M * KACC, 256), 256, 0, s>>>(b.M, h->kacc);
     cudaMemsetAsync(h->stats->barrier, 0, 2 * sizeof(unsigned int), s);
     {
         KmeansArgs a;

@@ -42,6 +42,29 @@ __device__ __forceinline__ double wrap_coord(double x, double L)
     return x;
 }
 
+// The same wrap with the comparisons done on the IEEE bit patterns (for
+// L > 0 and non-NaN x, x < 0 is the sign bit and, for x >= 0, x >= L is an
+// integer comparison of the patterns): GB300 runs FP64 compares on its
+// FP64 pipe at 1/64 of the FP32 rate.  Returns false when x is still out of
+// [0, L) afterwards (a move of more than one edge).
+__device__ __forceinline__ bool wrap_coord_bits(double &x, double L)
+{
+    const long long Lb = __double_as_longlong(L);
+    long long b = __double_as_longlong(x);
+    if (b < 0) {                              // sign bit: x < 0 (or -0)
+        x = DADD(x, L);
+        b = __double_as_longlong(x);
+    } else if (b >= Lb) {
+        x = DSUB(x, L);
+        b = __double_as_longlong(x);
+    }
+    if (b == (long long)0x8000000000000000ll) {   // -0 -> +0
+        x = 0.0;
+        b = 0;
+    }
+    return b >= 0 && b < Lb;
+}
+
 // r^2 = dx*dx + dy*dy + dz*dz, left to right, no FMA
 __device__ __forceinline__ double r2_rn(double dx, double dy, double dz)
 {

@@ -26,8 +26,7 @@ __global__ void k_kick_drift(Batch b, double *__restrict__ x, double *__restrict
         if (((__double_as_longlong(xi) >> 52) & 0x7ff) == 0x7ff ||
             ((__double_as_longlong(vi) >> 52) & 0x7ff) == 0x7ff)
             bad |= DEV_ERR_NONFINITE;
-        xi = wrap_coord(xi, g.L[a]);
-        if (!(xi >= 0.0 && xi < g.L[a])) {   // moved more than one box edge
+        if (!wrap_coord_bits(xi, g.L[a])) {   // moved more than one box edge
             bad |= DEV_ERR_JUMP;
             xi = 0.0;
         }
