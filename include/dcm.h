@@ -85,7 +85,16 @@ typedef struct {
     int32_t precision;                     /* DCM_FP64 or DCM_MIXED */
     int32_t n_classes;                     /* cutoff classes, 2..8 */
     double cell_min;                       /* link-cell edge target; <= 0: auto */
-    int32_t reserved[8];
+    /* Verlet-list skin r_s in sigma (Section 2.2.1, Algorithm 3.3).  0: walk
+       the link cells directly every step.  > 0: each particle keeps a list
+       of every j within r_c[i] + skin, rebuilt (with a fresh cell sort)
+       when 2 x (largest displacement since the build) + (largest growth of
+       a cutoff since the build) reaches the skin, or when the list storage
+       would overflow (that step falls back to the direct walk).  Requires
+       at most 2^24 particles per handle and a stencil of at most 7 cells
+       in y and z. */
+    double skin;
+    int32_t reserved[6];
 } dcm_params;
 
 /* Launch shape of the force kernel per cutoff class (the autotuner's
@@ -108,7 +117,9 @@ typedef struct {
     int64_t guard_rechecks;                /* MIXED: FP64 re-decided pairs */
     int32_t kernels_plain;                 /* kernels one step launches */
     int32_t kernels_detect;                /* ... in a step with detection */
-    int64_t reserved[5];
+    int64_t list_builds;                   /* Verlet-list builds so far */
+    int64_t list_entries;                  /* entries of the current lists */
+    int64_t reserved[3];
 } dcm_stats;
 
 /* Phases of one step, in order, for dcm_get_phase_times. */

@@ -110,6 +110,7 @@ static int check_params(const dcm_box *box, int64_t n, const dcm_params *p)
     if (p->n_classes < 2 || p->n_classes > DCM_MAX_CLASSES)
         return fail(DCM_ERR_ARG, "n_classes must be 2..%d", DCM_MAX_CLASSES);
     if (p->detect_every < 0) return fail(DCM_ERR_ARG, "detect_every must be >= 0");
+    if (!(p->skin >= 0) || p->skin > 2.0) return fail(DCM_ERR_ARG, "skin must be in [0, 2] sigma");
     return DCM_OK;
 }
 
@@ -121,7 +122,8 @@ static int setup_geometry(const dcm_box *box, int64_t n, const dcm_params *p, Ge
     g.n = (int)n;
     double L[3] = {box->lx, box->ly, box->lz};
     double target = p->cell_min > 0 ? p->cell_min : 0.5 * p->rc_min;
-    double rcull = p->rc_max * 1.00002 + 1e-4;
+    double reach = p->rc_max + (p->skin > 0 ? p->skin : 0.0);   // Verlet lists reach r_c + skin
+    double rcull = reach * 1.00002 + 1e-4;
     bool ok = false;
     for (int tries = 0; tries < 64 && target >= 0.25; ++tries, target *= 0.9) {
         ok = true;
@@ -174,6 +176,7 @@ static int setup_geometry(const dcm_box *box, int64_t n, const dcm_params *p, Ge
     g.hdtm = 0.5 * p->dt / p->mass;
     g.eps = p->eps;
     g.sigma = p->sigma;
+    g.skin = p->skin > 0 ? p->skin : 0.0;
     g.eps24 = 24.0 * p->eps;
     g.eps48 = 48.0 * p->eps;
     g.eps2 = 2.0 * p->eps;
@@ -187,6 +190,19 @@ static int setup_geometry(const dcm_box *box, int64_t n, const dcm_params *p, Ge
     return DCM_OK;
 }
 
+// Verlet-list entries reserved for one system: every particle may hold
+// the neighbours of a sphere of r_c,max + skin, but no more than three times
+// those of r_c,min + skin (bulk particles are the vast majority), at a
+// density bound of 1.0
+static int64_t list_cap(const Geom &g, int64_t n)
+{
+    if (g.skin <= 0) return 0;
+    const double c43pi = 4.18879020478639;
+    double big = c43pi * pow(g.rc_max + g.skin, 3.0);
+    double small = 3.0 * c43pi * pow(g.rc_min + g.skin, 3.0);
+    return n * (int64_t)ceil(big < small ? big : small) + 1024;
+}
+
 static int64_t bytes_for(const Geom &g, int64_t n, int precision)
 {
     int64_t ncell = g.ncell;
@@ -195,7 +211,8 @@ static int64_t bytes_for(const Geom &g, int64_t n, int precision)
     if (precision == DCM_FP64) per_p += 32;
     int64_t per_v = 4 + 4 + 4 + 8 + 1 + 8 + 8 + 4 + 16;
     int64_t ntiles = (ncell + 2047) / 2048 + 1;
-    return n * per_p + ncell * 8 + 8 + nv * per_v + ntiles * 4 + 4096 + 256 * 8 * 8;
+    int64_t lists = g.skin > 0 ? 4 * list_cap(g, n) + n * (4 + 4 + 24 + 8) : 0;
+    return n * per_p + ncell * 8 + 8 + nv * per_v + ntiles * 4 + 4096 + 256 * 8 * 8 + lists;
 }
 
 extern "C" int64_t dcm_estimate_bytes(const dcm_box *box, int64_t n, const dcm_params *p)
@@ -231,7 +248,8 @@ extern "C" int dcm_destroy(dcm_handle *h)
                     h->cell_start, h->sorted_id, h->scan_tmp, h->sp4, h->spd, h->class_list,
                     h->class_count_dev, h->B, h->sm1, h->sm2, h->Bs, h->S, h->D0, h->D1, h->stamp,
                     h->flist, h->fcount, h->kacc, h->npair, h->pe, h->vir, h->red_part, h->red_out,
-                    h->err, h->stats, h->tmp3n, h->geo_dev, h->off_dev};
+                    h->err, h->stats, h->tmp3n, h->geo_dev, h->off_dev, h->nl, h->nl_cnt,
+                    h->nl_start, h->nl_tiles, h->x_ref, h->rl_ref, h->lflags};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -359,6 +377,32 @@ static int create_systems(int M, const dcm_box *boxes, const int64_t *ns, const 
     ALLOC(h->red_out, 8 * (int64_t)M);
     ALLOC(h->err, 1);
     ALLOC(h->stats, 1);
+    bool lists = false;
+    int64_t cap = 0;
+    for (int k = 0; k < M; ++k) {
+        cap += list_cap(h->geo_host[k], ns[k]);
+        lists = lists || h->geo_host[k].skin > 0;
+    }
+    if (lists) {
+        for (int k = 0; k < M; ++k)
+            if (h->geo_host[k].skin <= 0 || h->geo_host[k].smax[1] > 7 || h->geo_host[k].smax[2] > 7) {
+                dcm_destroy(h);
+                return fail(DCM_ERR_ARG, "system %d: Verlet lists need skin > 0 in every system "
+                                         "and a stencil of at most 7 cells in y and z", k);
+            }
+        if (N >= (1 << 24)) {
+            dcm_destroy(h);
+            return fail(DCM_ERR_ARG, "Verlet lists hold at most 2^24 particles per handle");
+        }
+        h->nl_cap = cap;
+        ALLOC(h->nl, cap);
+        ALLOC(h->nl_cnt, N);
+        ALLOC(h->nl_start, N + 1);
+        ALLOC(h->nl_tiles, (N + 2047) / 2048 + 1);
+        ALLOC(h->x_ref, 3 * N);
+        ALLOC(h->rl_ref, N);
+        ALLOC(h->lflags, LF_WORDS);
+    }
 #undef ALLOC
     h->b.sys = h->geo_dev;
     h->b.p_off = h->off_dev;
@@ -377,6 +421,12 @@ static int create_systems(int M, const dcm_box *boxes, const int64_t *ns, const 
     cudaMemsetAsync(h->v, 0, sizeof(double) * 3 * N, h->stream);
     cudaMemsetAsync(h->f, 0, sizeof(double) * 3 * N, h->stream);
     cudaMemsetAsync(h->cls, 0, N, h->stream);
+    if (h->nl) {
+        cudaMemsetAsync(h->lflags, 0, sizeof(int) * LF_WORDS, h->stream);
+        cudaMemsetAsync(h->lflags + LF_MINHEAD, 0x7f, sizeof(int), h->stream);   // ~3.4e38
+        cudaMemsetAsync(h->x_ref, 0, sizeof(double) * 3 * N, h->stream);
+        cudaMemsetAsync(h->rl_ref, 0, sizeof(float) * N, h->stream);
+    }
     cudaError_t e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {
         dcm_destroy(h);
@@ -526,7 +576,9 @@ extern "C" int dcm_set_cutoffs(dcm_handle *h, const double *rc, int mem)
     if (r) return r;
     if (mem != DCM_DEVICE) DCM_CHECK_CUDA(cudaStreamSynchronize(h->stream));
     h->have_cut = true;
+    h->cut_detected = false;
     h->forces_valid = false;
+    invalidate_graphs(h);   // the captured list builds depend on where cutoffs come from
     return DCM_OK;
 }
 
@@ -534,9 +586,11 @@ extern "C" int dcm_detect_interface(dcm_handle *h)
 {
     if (!h) return fail(DCM_ERR_ARG, "null handle");
     if (!h->have_state) return fail(DCM_ERR_STATE, "no state set");
+    if (!h->cut_detected) invalidate_graphs(h);   // list builds anticipate detected cutoffs
     int r = launch_detect(h);
     if (r) return r;
     h->have_cut = true;
+    h->cut_detected = true;
     h->forces_valid = false;
     return DCM_OK;
 }
@@ -547,8 +601,9 @@ static int forces_now(dcm_handle *h, bool energy)
         int r = launch_detect(h);
         if (r) return r;
         h->have_cut = true;
+        h->cut_detected = true;
     }
-    int r = launch_bin(h);
+    int r = h->nl ? launch_list_step(h, true) : launch_bin(h);
     if (r) return r;
     r = launch_forces(h, energy);
     if (r) return r;
@@ -581,7 +636,7 @@ static int enqueue_step(dcm_handle *h, bool detect, bool capturing)
     mark(h, 1, capturing);
     if (!r && detect) r = launch_detect(h);
     mark(h, 2, capturing);
-    if (!r) r = launch_bin(h);
+    if (!r) r = h->nl ? launch_list_step(h, false) : launch_bin(h);
     mark(h, 3, capturing);
     if (!r) r = launch_forces(h, false);
     mark(h, 4, capturing);
@@ -791,6 +846,8 @@ extern "C" int dcm_get_stats(dcm_handle *h, dcm_stats *s)
     s->guard_rechecks = (int64_t)st.guard_rechecks;
     s->kernels_plain = h->kernels_plain;
     s->kernels_detect = h->kernels_detect;
+    s->list_builds = (int64_t)st.list_builds;
+    s->list_entries = (int64_t)st.list_entries;
     return DCM_OK;
 }
 

@@ -17,11 +17,15 @@ constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 // cell of every particle + its arrival slot within the cell (atomic order;
 // the order inside a cell is fixed afterwards by k_cell_sort)
 // (cells of all systems are concatenated: cell_of holds the global index)
+// gate: nullptr = always run; otherwise the kernel does nothing while *gate
+// is 0 (a step that keeps its Verlet lists keeps its cell sort too)
+__device__ __forceinline__ bool gated_off(const int *gate) { return gate && *gate == 0; }
+
 __global__ void k_cell_count(Batch b, const double *__restrict__ x, int32_t *cell_of,
-                             int32_t *slot, int32_t *count)
+                             int32_t *slot, int32_t *count, const int *gate)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= b.N) return;
+    if (i >= b.N || gated_off(gate)) return;
     const Geom &g = b.sys[sys_of(b.p_off, b.M, i)];
     int cx = bin_of(x[i], g.inv_c[0], g.nc[0]);
     int cy = bin_of(x[(size_t)b.N + i], g.inv_c[1], g.nc[1]);
@@ -33,9 +37,10 @@ __global__ void k_cell_count(Batch b, const double *__restrict__ x, int32_t *cel
 
 // exclusive scan, pass 1: scan each tile, record the tile total
 __global__ void k_scan_tiles(const int32_t *__restrict__ in, int32_t *out, int32_t *tile_sum,
-                             int64_t m)
+                             int64_t m, const int *gate)
 {
     __shared__ int32_t s[SCAN_THREADS];
+    if (gated_off(gate)) return;
     int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
     int32_t v[SCAN_ITEMS];
     int32_t run = 0;
@@ -65,10 +70,12 @@ __global__ void k_scan_tiles(const int32_t *__restrict__ in, int32_t *out, int32
 }
 
 // exclusive scan, pass 2: add the sum of all earlier tiles
+// total >= 0: out[m] = total; total < 0: out[m] = the sum of all inputs
 __global__ void k_scan_add(int32_t *out, const int32_t *__restrict__ tile_sum, int64_t m,
-                           int32_t total)
+                           int32_t total, int ntiles, const int *gate)
 {
     __shared__ int32_t s[SCAN_THREADS];
+    if (gated_off(gate)) return;
     int32_t acc = 0;
     for (int t = threadIdx.x; t < (int)blockIdx.x; t += SCAN_THREADS) acc += tile_sum[t];
     s[threadIdx.x] = acc;
@@ -83,23 +90,26 @@ __global__ void k_scan_add(int32_t *out, const int32_t *__restrict__ tile_sum, i
         int64_t k = base + q;
         if (k < m) out[k] += off;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) out[m] = total;
+    if (blockIdx.x == ntiles - 1 && threadIdx.x == 0)
+        out[m] = total >= 0 ? total : off + tile_sum[blockIdx.x];
 }
 
 __global__ void k_cell_scatter(int n, const int32_t *__restrict__ cell_of,
                                const int32_t *__restrict__ slot,
-                               const int32_t *__restrict__ start, int32_t *sorted_id)
+                               const int32_t *__restrict__ start, int32_t *sorted_id,
+                               const int *gate)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= n || gated_off(gate)) return;
     sorted_id[start[cell_of[i]] + slot[i]] = i;
 }
 
 // ascending particle id inside each cell (cells hold a handful of particles)
-__global__ void k_cell_sort(int64_t ncell, const int32_t *__restrict__ start, int32_t *sorted_id)
+__global__ void k_cell_sort(int64_t ncell, const int32_t *__restrict__ start, int32_t *sorted_id,
+                            const int *gate)
 {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncell) return;
+    if (c >= ncell || gated_off(gate)) return;
     int lo = start[c], hi = start[c + 1];
     for (int a = lo + 1; a < hi; ++a) {
         int key = sorted_id[a];
@@ -127,10 +137,17 @@ __global__ void k_gather(Batch b, const double *__restrict__ x, const int32_t *_
     int cy = (c / g.nc[0]) % g.nc[1];
     int cz = c / (g.nc[0] * g.nc[1]);
     double px = x[i], py = x[(size_t)b.N + i], pz = x[2 * (size_t)b.N + i];
-    float ux = (float)DSUB(px, DMUL((double)cx, g.cedge[0]));
-    float uy = (float)DSUB(py, DMUL((double)cy, g.cedge[1]));
-    float uz = (float)DSUB(pz, DMUL((double)cz, g.cedge[2]));
-    sp4[k] = make_float4(ux, uy, uz, (float)cx);
+    double u[3] = {DSUB(px, DMUL((double)cx, g.cedge[0])), DSUB(py, DMUL((double)cy, g.cedge[1])),
+                   DSUB(pz, DMUL((double)cz, g.cedge[2]))};
+    // between Verlet-list builds a particle keeps the cell of the build; one
+    // that wrapped through the box is folded back next to that cell
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float uf = (float)u[a];
+        if (uf > (float)g.halfL[a]) u[a] = DSUB(u[a], g.L[a]);
+        else if (uf < -(float)g.halfL[a]) u[a] = DADD(u[a], g.L[a]);
+    }
+    sp4[k] = make_float4((float)u[0], (float)u[1], (float)u[2], (float)cx);
     if (spd) spd[k] = make_double4_32a(px, py, pz, 0.0);
 }
 
@@ -180,20 +197,29 @@ __global__ void k_class_offsets(int K, int32_t *buf)
 
 static inline int nblk(int64_t n, int b) { return (int)((n + b - 1) / b); }
 
-int launch_bin(dcm_handle *h)
+int launch_scan(dcm_handle *h, const int32_t *in, int32_t *out, int32_t *tiles, int64_t m,
+                int32_t total, const int *gate)
 {
-    h->kernels += 9;
+    int ntiles = nblk(m, SCAN_TILE);
+    k_scan_tiles<<<ntiles, SCAN_THREADS, 0, h->stream>>>(in, out, tiles, m, gate);
+    k_scan_add<<<ntiles, SCAN_THREADS, 0, h->stream>>>(out, tiles, m, total, ntiles, gate);
+    h->kernels += 2;
+    return DCM_OK;
+}
+
+// cell sort (skipped while *gate == 0), then the gather of the sorted
+// streams from the current positions and the per-class lists
+int launch_bin_gated(dcm_handle *h, const int *gate)
+{
     cudaStream_t s = h->stream;
     int n = (int)h->n;
+    h->kernels += 7;
     cudaMemsetAsync(h->cell_count, 0, sizeof(int32_t) * h->ncell, s);
-    k_cell_count<<<nblk(n, 256), 256, 0, s>>>(h->b, h->x, h->cell_of, h->slot, h->cell_count);
-    int ntiles = nblk(h->ncell, SCAN_TILE);
-    k_scan_tiles<<<ntiles, SCAN_THREADS, 0, s>>>(h->cell_count, h->cell_start, h->scan_tmp,
-                                                 h->ncell);
-    k_scan_add<<<ntiles, SCAN_THREADS, 0, s>>>(h->cell_start, h->scan_tmp, h->ncell, n);
+    k_cell_count<<<nblk(n, 256), 256, 0, s>>>(h->b, h->x, h->cell_of, h->slot, h->cell_count, gate);
+    launch_scan(h, h->cell_count, h->cell_start, h->scan_tmp, h->ncell, n, gate);
     k_cell_scatter<<<nblk(n, 256), 256, 0, s>>>(n, h->cell_of, h->slot, h->cell_start,
-                                                h->sorted_id);
-    k_cell_sort<<<nblk(h->ncell, 256), 256, 0, s>>>(h->ncell, h->cell_start, h->sorted_id);
+                                                h->sorted_id, gate);
+    k_cell_sort<<<nblk(h->ncell, 256), 256, 0, s>>>(h->ncell, h->cell_start, h->sorted_id, gate);
     k_gather<<<nblk(n, 256), 256, 0, s>>>(h->b, h->x, h->sorted_id, h->cell_of, h->sp4,
                                           h->p.precision == DCM_FP64 ? h->spd : nullptr);
     // class lists of sorted slots for the per-class force launches
@@ -206,5 +232,7 @@ int launch_bin(dcm_handle *h)
                                                h->class_count_dev + 2 * K, h->class_list);
     return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "binning launch");
 }
+
+int launch_bin(dcm_handle *h) { return launch_bin_gated(h, nullptr); }
 
 }  // namespace dcm

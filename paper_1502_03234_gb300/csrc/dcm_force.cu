@@ -52,6 +52,16 @@ struct ForceArgs {
     double *pe, *vir;
     unsigned int *queue;          // work counter
     unsigned long long *guard_count;
+    // Verlet lists (skin > 0): used while *list_ok
+    const int *list_ok;
+    const int32_t *nl_start;
+    const int32_t *nl;
+    // list build (k_list_walk)
+    int32_t *nl_cnt, *nl_w;
+    float *rl_ref;
+    const double *d;
+    float list_delta;
+    const int *gate;
 };
 
 // exact FP64 decision |r_ij| < r_c[i] (the definition's arithmetic)
@@ -181,6 +191,49 @@ __device__ __forceinline__ float box_gap(int d, float u, float c)
 }
 
 template <int PREC, bool ENERGY>
+__device__ __forceinline__ void reduce_and_store(const ForceArgs &a, Acc<PREC, ENERGY> &acc, int i,
+                                                 int lane, int G, unsigned gmask, int np)
+{
+    // combine the G lanes of this particle
+    double fx, fy, fz, pe = 0.0, vir[6] = {0, 0, 0, 0, 0, 0};
+    if constexpr (PREC == DCM_MIXED) {
+        fx = (double)acc.hx + (double)acc.lx;
+        fy = (double)acc.hy + (double)acc.ly;
+        fz = (double)acc.hz + (double)acc.lz;
+    } else {
+        fx = acc.fx;
+        fy = acc.fy;
+        fz = acc.fz;
+    }
+    if constexpr (ENERGY) {
+        pe = acc.pe;
+        for (int q = 0; q < 6; ++q) vir[q] = acc.v[q];
+    }
+    for (int off = G >> 1; off > 0; off >>= 1) {
+        fx += __shfl_xor_sync(gmask, fx, off);
+        fy += __shfl_xor_sync(gmask, fy, off);
+        fz += __shfl_xor_sync(gmask, fz, off);
+        np += __shfl_xor_sync(gmask, np, off);
+        if constexpr (ENERGY) {
+            pe += __shfl_xor_sync(gmask, pe, off);
+            for (int q = 0; q < 6; ++q) vir[q] += __shfl_xor_sync(gmask, vir[q], off);
+        }
+    }
+    if (lane == 0) {
+        size_t n = (size_t)a.b.N;
+        a.f[i] = fx;
+        a.f[n + i] = fy;
+        a.f[2 * n + i] = fz;
+        a.npair[i] = np;
+        if constexpr (ENERGY) {
+            a.pe[i] = pe;
+            for (int q = 0; q < 6; ++q) a.vir[q * n + i] = vir[q];
+        }
+    }
+}
+
+
+template <int PREC, bool ENERGY>
 __device__ __forceinline__ void particle_force(const ForceArgs &a, int k, int lane, int G, unsigned gmask, int &ng)
 {
     const Geom &g = a.b.sys[sys_of(a.b.p_off, a.b.M, k)];
@@ -243,41 +296,279 @@ __device__ __forceinline__ void particle_force(const ForceArgs &a, int k, int la
                                           rc2f, rc2lo, rc2hi, rci2, acc, np, ng);
         }
     }
-    // combine the G lanes of this particle
-    double fx, fy, fz, pe = 0.0, vir[6] = {0, 0, 0, 0, 0, 0};
-    if constexpr (PREC == DCM_MIXED) {
-        fx = (double)acc.hx + (double)acc.lx;
-        fy = (double)acc.hy + (double)acc.ly;
-        fz = (double)acc.hz + (double)acc.lz;
+    reduce_and_store<PREC, ENERGY>(a, acc, i, lane, G, gmask, np);
+}
+
+// Algorithm 3.2 over particle k's Verlet list (entries: sorted slot j,
+// cell row offsets dy, dz); same pair rule, same FP64 re-decision at the
+// cutoff edge, so the interacting pairs are those of the direct walk
+template <int PREC, bool ENERGY>
+__device__ __forceinline__ void particle_force_list(const ForceArgs &a, int k, int lane, int G,
+                                                    unsigned gmask, int &ng)
+{
+    const Geom &g = a.b.sys[sys_of(a.b.p_off, a.b.M, k)];
+    int i = a.sorted_id[k];
+    float4 ui = a.sp4[k];
+    double rci = a.rc[i];
+    double rci2 = DMUL(rci, rci);
+    float rc2f = (float)rci2;
+    float rc2lo = rc2f * (1.f - GUARD), rc2hi = rc2f * (1.f + GUARD);
+    const float ncx = (float)g.nc[0], halfnc = 0.5f * (float)g.nc[0];
+    const float cx0 = g.cf[0], cy0 = g.cf[1], cz0 = g.cf[2];
+    double4_32a pi = make_double4_32a(0, 0, 0, 0);
+    if constexpr (PREC == DCM_FP64) pi = a.spd[k];
+    Acc<PREC, ENERGY> acc;
+    int np = 0;
+    const int e0 = a.nl_start[k], e1 = a.nl_start[k + 1];
+    auto one = [&](int e, float4 uj) {
+        int j = e & 0xffffff;
+        if constexpr (PREC == DCM_MIXED) {
+            float dyc = (float)(((e >> 24) & 15) - 8);
+            float dzc = (float)((int)((unsigned)e >> 28) - 8);
+            float dcx = ui.w - uj.w;
+            dcx -= dcx > halfnc ? ncx : 0.f;
+            dcx += dcx < -halfnc ? ncx : 0.f;
+            float dx = fmaf(dcx, cx0, ui.x - uj.x);
+            float dy = fmaf(-dyc, cy0, ui.y) - uj.y;
+            float dz = fmaf(-dzc, cz0, ui.z) - uj.z;
+            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            if (r2 < rc2hi) {
+                bool in = r2 < rc2f;
+                if (r2 >= rc2lo) {
+                    in = fp64_inside(a, g, i, a.sorted_id[j], rci2);
+                    ++ng;
+                }
+                if (in) {
+                    float r2inv = rcp_approx(r2);
+                    float sr2 = g.sig2f * r2inv;
+                    float sr6 = sr2 * sr2 * sr2;
+                    float fr = r2inv * sr6 * fmaf(g.eps48f, sr6, -g.eps24f);
+                    acc.rx = fmaf(fr, dx, acc.rx);
+                    acc.ry = fmaf(fr, dy, acc.ry);
+                    acc.rz = fmaf(fr, dz, acc.rz);
+                    ++np;
+                    if constexpr (ENERGY) {
+                        acc.pe = fmaf(g.eps2f * sr6, sr6 - 1.f, acc.pe);
+                        float fx = fr * dx, fy = fr * dy, fz = fr * dz;
+                        acc.v[0] = fmaf(0.5f * dx, fx, acc.v[0]);
+                        acc.v[1] = fmaf(0.5f * dy, fy, acc.v[1]);
+                        acc.v[2] = fmaf(0.5f * dz, fz, acc.v[2]);
+                        acc.v[3] = fmaf(0.5f * dx, fy, acc.v[3]);
+                        acc.v[4] = fmaf(0.5f * dx, fz, acc.v[4]);
+                        acc.v[5] = fmaf(0.5f * dy, fz, acc.v[5]);
+                    }
+                }
+            }
+        } else {
+            double4_32a pj = a.spd[j];
+            double dx = min_image(DSUB(pi.x, pj.x), g.L[0], g.halfL[0]);
+            double dy = min_image(DSUB(pi.y, pj.y), g.L[1], g.halfL[1]);
+            double dz = min_image(DSUB(pi.z, pj.z), g.L[2], g.halfL[2]);
+            double r2 = r2_rn(dx, dy, dz);
+            if (r2 < rci2) {
+                double r2inv = 1.0 / r2;
+                double sr2 = g.sig2 * r2inv;
+                double sr6 = sr2 * sr2 * sr2;
+                double fr = r2inv * sr6 * (g.eps48 * sr6 - g.eps24);
+                acc.fx += fr * dx;
+                acc.fy += fr * dy;
+                acc.fz += fr * dz;
+                ++np;
+                if constexpr (ENERGY) {
+                    acc.pe += g.eps2 * sr6 * (sr6 - 1.0);
+                    double fx = fr * dx, fy = fr * dy, fz = fr * dz;
+                    acc.v[0] += 0.5 * dx * fx;
+                    acc.v[1] += 0.5 * dy * fy;
+                    acc.v[2] += 0.5 * dz * fz;
+                    acc.v[3] += 0.5 * dx * fy;
+                    acc.v[4] += 0.5 * dx * fz;
+                    acc.v[5] += 0.5 * dy * fz;
+                }
+            }
+        }
+    };
+    int p = e0 + lane;
+    constexpr bool MIX = PREC == DCM_MIXED;
+    for (; p + G < e1; p += 2 * G) {
+        int ea = a.nl[p], eb = a.nl[p + G];
+        float4 ua = MIX ? a.sp4[ea & 0xffffff] : make_float4(0, 0, 0, 0);
+        float4 ub = MIX ? a.sp4[eb & 0xffffff] : make_float4(0, 0, 0, 0);
+        one(ea, ua);
+        one(eb, ub);
+        if constexpr (MIX) {
+            if (((p - e0) & (64 * G - 1)) == 0) acc.fold();   // 2xFP32 fold every 64 pairs
+        }
+    }
+    for (; p < e1; p += G) {
+        int ea = a.nl[p];
+        one(ea, MIX ? a.sp4[ea & 0xffffff] : make_float4(0, 0, 0, 0));
+    }
+    acc.fold();
+    reduce_and_store<PREC, ENERGY>(a, acc, i, lane, G, gmask, np);
+}
+
+// Verlet-list radius of particle i: the cutoff it would get if its distance
+// to the interface dropped by delta (so small moves of the detected interface
+// do not force a rebuild), never below its current cutoff, plus the skin
+__device__ __forceinline__ float list_radius(const Geom &g, double rci, double di, float delta)
+{
+    float r = (float)rci;
+    if (delta > 0.f && g.rc_max > g.rc_min) {
+        float dd = fmaxf((float)di - delta, 0.f);
+        float rmax = (float)g.rc_max, rmin = (float)g.rc_min;
+        float ra = dd <= 0.f ? rmax
+                 : (dd >= rmax ? rmin
+                               : fmaf((float)g.cut_a, exp2f((float)g.alpha * (rmax - dd)), (float)g.cut_b));
+        r = fmaxf(r, ra);
+    }
+    return r * 1.00001f + (float)g.skin + 1e-4f;
+}
+
+// one particle of the list build: the direct row walk with radius
+// list_radius; COUNT stores the number of entries, FILL writes them in
+// walk order (a ballot over the G lanes keeps the order)
+template <bool FILL>
+__device__ __forceinline__ void list_particle(const ForceArgs &a, int k, int lane, int G,
+                                              unsigned gmask)
+{
+    const Geom &g = a.b.sys[sys_of(a.b.p_off, a.b.M, k)];
+    int i = a.sorted_id[k];
+    float4 ui = a.sp4[k];
+    int c = a.cell_of[i] - (int)g.c0;
+    int cx = (int)ui.w;
+    int cy = (c / g.nc[0]) % g.nc[1];
+    int cz = c / (g.nc[0] * g.nc[1]);
+    float rl = list_radius(g, a.rc[i], a.d[i], a.list_delta);
+    float rl2 = rl * rl;
+    float rcull = rl * 1.00002f + 1e-4f;
+    float rcull2 = rcull * rcull;
+    int sx = min(g.smax[0], (int)ceilf(rcull * g.inv_cf[0]));
+    int sy = min(g.smax[1], (int)ceilf(rcull * g.inv_cf[1]));
+    int sz = min(g.smax[2], (int)ceilf(rcull * g.inv_cf[2]));
+    const int gbase = (threadIdx.x & 31) & ~(G - 1);
+    const unsigned gbits = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
+    const unsigned below = (1u << lane) - 1u;
+    int n = 0;
+    int32_t *out = FILL ? a.nl_w + a.nl_start[k] : nullptr;
+    for (int dz = -sz; dz <= sz; ++dz) {
+        float gz = box_gap(dz, ui.z, g.cf[2]);
+        float remz = rcull2 - gz * gz;
+        if (remz < 0.f) continue;
+        int czz = cz + dz;
+        czz += czz < 0 ? g.nc[2] : (czz >= g.nc[2] ? -g.nc[2] : 0);
+        float az = ui.z - (float)dz * g.cf[2];
+        for (int dy = -sy; dy <= sy; ++dy) {
+            float gy = box_gap(dy, ui.y, g.cf[1]);
+            float w2 = remz - gy * gy;
+            if (w2 < 0.f) continue;
+            int cyy = cy + dy;
+            cyy += cyy < 0 ? g.nc[1] : (cyy >= g.nc[1] ? -g.nc[1] : 0);
+            float ay = ui.y - (float)dy * g.cf[1];
+            float w = sqrtf(w2);
+            int xlo = max(-sx, (int)floorf((ui.x - w) * g.inv_cf[0]));
+            int xhi = min(sx, (int)floorf((ui.x + w) * g.inv_cf[0]));
+            int row = (int)g.c0 + g.nc[0] * (cyy + g.nc[1] * czz);
+            uint32_t tag = ((uint32_t)(dy + 8) << 24) | ((uint32_t)(dz + 8) << 28);
+            int lo = cx + xlo, hi = cx + xhi;
+            for (int q = 0; q < 3; ++q) {
+                int j0, j1;
+                float ax;
+                if (q == 0) {            // cells at the top end seen through x = 0
+                    if (lo >= 0) continue;
+                    j0 = a.cell_start[row + lo + g.nc[0]];
+                    j1 = a.cell_start[row + g.nc[0]];
+                    ax = (float)(cx + g.nc[0]);
+                } else if (q == 1) {     // cells at the bottom end seen through x = L
+                    if (hi < g.nc[0]) continue;
+                    j0 = a.cell_start[row];
+                    j1 = a.cell_start[row + hi - g.nc[0] + 1];
+                    ax = (float)(cx - g.nc[0]);
+                } else {
+                    int l2 = lo < 0 ? 0 : lo, h2 = hi >= g.nc[0] ? g.nc[0] - 1 : hi;
+                    if (l2 > h2) continue;
+                    j0 = a.cell_start[row + l2];
+                    j1 = a.cell_start[row + h2 + 1];
+                    ax = (float)cx;
+                }
+                for (int base = j0; base < j1; base += G) {
+                    int j = base + lane;
+                    bool hit = false;
+                    if (j < j1 && j != k) {
+                        float4 uj = a.sp4[j];
+                        float ddx = fmaf(ax - uj.w, g.cf[0], ui.x - uj.x);
+                        float ddy = ay - uj.y;
+                        float ddz = az - uj.z;
+                        hit = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz)) < rl2;
+                    }
+                    if constexpr (FILL) {
+                        unsigned m = (__ballot_sync(gmask, hit) >> gbase) & gbits;
+                        if (hit) out[n + __popc(m & below)] = (int32_t)((uint32_t)j | tag);
+                        n += __popc(m);
+                    } else {
+                        n += hit ? 1 : 0;
+                    }
+                }
+            }
+        }
+    }
+    if constexpr (!FILL) {
+        for (int off = G >> 1; off > 0; off >>= 1) n += __shfl_xor_sync(gmask, n, off);
+        if (lane == 0) a.nl_cnt[k] = n;
     } else {
-        fx = acc.fx;
-        fy = acc.fy;
-        fz = acc.fz;
+        if (lane == 0) a.rl_ref[i] = rl;
     }
-    if constexpr (ENERGY) {
-        pe = acc.pe;
-        for (int q = 0; q < 6; ++q) vir[q] = acc.v[q];
-    }
-    for (int off = G >> 1; off > 0; off >>= 1) {
-        fx += __shfl_xor_sync(gmask, fx, off);
-        fy += __shfl_xor_sync(gmask, fy, off);
-        fz += __shfl_xor_sync(gmask, fz, off);
-        np += __shfl_xor_sync(gmask, np, off);
-        if constexpr (ENERGY) {
-            pe += __shfl_xor_sync(gmask, pe, off);
-            for (int q = 0; q < 6; ++q) vir[q] += __shfl_xor_sync(gmask, vir[q], off);
+}
+
+// the class-ordered work queue shared by the force and list kernels
+struct Queue {
+    int cnt[DCM_MAX_CLASSES], off[DCM_MAX_CLASSES], items[DCM_MAX_CLASSES + 1];
+};
+
+__device__ __forceinline__ void queue_init(const ForceArgs &a, Queue &sq)
+{
+    const int K = a.b.K;
+    if (threadIdx.x == 0) {
+        int run = 0;
+        // heaviest (largest cutoff) class first
+        for (int q = K - 1, t = 0; q >= 0; --q, ++t) {
+            sq.cnt[q] = a.class_buf[q];
+            sq.off[q] = a.class_buf[K + q];
+            int per = 32 / a.lanes[q];
+            sq.items[t] = run;
+            run += (sq.cnt[q] + per - 1) / per;
         }
+        sq.items[K] = run;
     }
-    if (lane == 0) {
-        size_t n = (size_t)a.b.N;
-        a.f[i] = fx;
-        a.f[n + i] = fy;
-        a.f[2 * n + i] = fz;
-        a.npair[i] = np;
-        if constexpr (ENERGY) {
-            a.pe[i] = pe;
-            for (int q = 0; q < 6; ++q) a.vir[q * n + i] = vir[q];
-        }
+}
+
+template <bool FILL>
+__global__ void __launch_bounds__(FORCE_THREADS, 3) k_list_walk(ForceArgs a)
+{
+    __shared__ Queue sq;
+    __shared__ int s_run;
+    queue_init(a, sq);
+    if (threadIdx.x == 0) s_run = *a.gate;
+    __syncthreads();
+    if (!s_run) return;
+    const int K = a.b.K;
+    const int total = sq.items[K];
+    const int lane32 = threadIdx.x & 31;
+    while (true) {
+        int item = 0;
+        if (lane32 == 0) item = (int)atomicAdd(a.queue, 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= total) break;
+        int t = 0;
+        while (t + 1 < K && item >= sq.items[t + 1]) ++t;
+        int q = K - 1 - t;
+        int G = a.lanes[q];
+        int per = 32 / G;
+        int local = (item - sq.items[t]) * per + lane32 / G;
+        int lane = lane32 & (G - 1);
+        unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane32 & ~(G - 1)));
+        if (local < sq.cnt[q]) list_particle<FILL>(a, sq.off[q] >= 0 ? a.class_list[sq.off[q] + local] : 0,
+                                                    lane, G, gmask);
+        __syncwarp();
     }
 }
 
@@ -299,9 +590,12 @@ __global__ void __launch_bounds__(FORCE_THREADS, 3) k_force(ForceArgs a)
         }
         s_items[K] = run;
     }
+    __shared__ int s_list;
+    if (threadIdx.x == 0) s_list = a.list_ok ? *a.list_ok : 0;
     __syncthreads();
     const int total = s_items[K];
     const int lane32 = threadIdx.x & 31;
+    const bool use_list = s_list != 0;
     int ng = 0;   // guard-band re-decisions (diagnostic), one atomic per block
     while (true) {
         int item = 0;
@@ -318,7 +612,10 @@ __global__ void __launch_bounds__(FORCE_THREADS, 3) k_force(ForceArgs a)
         unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane32 & ~(G - 1)));
         if (local < s_cnt[q]) {
             int k = a.class_list[s_off[q] + local];
-            particle_force<PREC, ENERGY>(a, k, lane, G, gmask, ng);
+            if (use_list)
+                particle_force_list<PREC, ENERGY>(a, k, lane, G, gmask, ng);
+            else
+                particle_force<PREC, ENERGY>(a, k, lane, G, gmask, ng);
         }
         __syncwarp();
     }
@@ -331,10 +628,50 @@ __global__ void __launch_bounds__(FORCE_THREADS, 3) k_force(ForceArgs a)
     if (threadIdx.x == 0 && s_ng) atomicAdd(a.guard_count, (unsigned long long)s_ng);
 }
 
+static void fill_args(dcm_handle *h, ForceArgs &a);
+
+int launch_list_walk(dcm_handle *h, bool fill, const int *gate, float delta)
+{
+    h->kernels += 1;
+    ForceArgs a;
+    fill_args(h, a);
+    a.gate = gate;
+    a.list_delta = delta;
+    cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), h->stream);
+    int block = h->tune.block >= 64 && h->tune.block <= FORCE_THREADS ? h->tune.block : FORCE_THREADS;
+    int grid = h->num_sms * (2048 / block);
+    if (fill)
+        k_list_walk<true><<<grid, block, 0, h->stream>>>(a);
+    else
+        k_list_walk<false><<<grid, block, 0, h->stream>>>(a);
+    return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "list walk launch");
+}
+
 int launch_forces(dcm_handle *h, bool energy)
 {
     h->kernels += 1;
     ForceArgs a;
+    fill_args(h, a);
+    cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), h->stream);
+    int block = h->tune.block >= 64 && h->tune.block <= FORCE_THREADS ? h->tune.block : FORCE_THREADS;
+    int grid = h->num_sms * (2048 / block);
+    bool fp64 = h->p.precision == DCM_FP64;
+    if (fp64) {
+        if (energy)
+            k_force<DCM_FP64, true><<<grid, block, 0, h->stream>>>(a);
+        else
+            k_force<DCM_FP64, false><<<grid, block, 0, h->stream>>>(a);
+    } else {
+        if (energy)
+            k_force<DCM_MIXED, true><<<grid, block, 0, h->stream>>>(a);
+        else
+            k_force<DCM_MIXED, false><<<grid, block, 0, h->stream>>>(a);
+    }
+    return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "force launch");
+}
+
+static void fill_args(dcm_handle *h, ForceArgs &a)
+{
     a.b = h->b;
     a.class_buf = h->class_count_dev;
     a.class_list = h->class_list;
@@ -355,22 +692,15 @@ int launch_forces(dcm_handle *h, bool energy)
     a.vir = h->vir;
     a.queue = &h->stats->barrier[2];
     a.guard_count = &h->stats->guard_rechecks;
-    cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), h->stream);
-    int block = h->tune.block >= 64 && h->tune.block <= FORCE_THREADS ? h->tune.block : FORCE_THREADS;
-    int grid = h->num_sms * (2048 / block);
-    bool fp64 = h->p.precision == DCM_FP64;
-    if (fp64) {
-        if (energy)
-            k_force<DCM_FP64, true><<<grid, block, 0, h->stream>>>(a);
-        else
-            k_force<DCM_FP64, false><<<grid, block, 0, h->stream>>>(a);
-    } else {
-        if (energy)
-            k_force<DCM_MIXED, true><<<grid, block, 0, h->stream>>>(a);
-        else
-            k_force<DCM_MIXED, false><<<grid, block, 0, h->stream>>>(a);
-    }
-    return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "force launch");
+    a.list_ok = h->nl ? h->lflags + LF_OK : nullptr;
+    a.nl_start = h->nl_start;
+    a.nl = h->nl;
+    a.nl_cnt = h->nl_cnt;
+    a.nl_w = h->nl;
+    a.rl_ref = h->rl_ref;
+    a.d = h->d;
+    a.list_delta = 0.f;
+    a.gate = nullptr;
 }
 
 }  // namespace dcm

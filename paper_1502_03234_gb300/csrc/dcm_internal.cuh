@@ -55,7 +55,12 @@ struct DevStats {
     double c_vapor;
     int class_count[DCM_MAX_CLASSES];
     unsigned int barrier[4];     // [0..1] grid barrier, [2] force queue, [3] CFSM result buffer
+    unsigned long long list_builds;
+    unsigned long long list_entries;
 };
+
+// Verlet-list control words (device): see dcm_list.cu
+enum { LF_REBUILD = 0, LF_OK = 1, LF_MAXDISP = 2, LF_MINHEAD = 3, LF_DONE = 4, LF_WORDS = 8 };
 
 constexpr int MAX_SYSTEMS = 1024;
 
@@ -77,6 +82,7 @@ struct Geom {
     double thr[DCM_MAX_CLASSES]; // class thresholds on d (descending)
     double dt, hdtm;             // dt, dt/(2m)
     double eps, sigma;
+    double skin;                 // Verlet-list skin (0: direct cell walk)
     double eps24, eps48, eps2, sig2;     // LJ force/energy constants
     float eps24f, eps48f, eps2f, sig2f;
     // this system's slices of the concatenated arrays
@@ -153,6 +159,14 @@ struct dcm_handle {
     int32_t *stamp;
     int32_t *flist;              // 4 * nvox
     int32_t *fcount;             // 4 counters
+    // Verlet lists (skin > 0), indexed by sorted slot of the last build
+    int32_t *nl;                 // entries: j | (dy+8) << 24 | (dz+8) << 28
+    int64_t nl_cap;
+    int32_t *nl_cnt, *nl_start, *nl_tiles;
+    double *x_ref;               // positions at the build (id order)
+    float *rl_ref;               // list radius of each particle at the build
+    bool cut_detected;           // cutoffs come from detection (lists anticipate d moves)
+    int *lflags;                 // LF_* words
     // per particle diagnostics / energies
     int32_t *npair;
     double *pe, *vir;
@@ -189,8 +203,13 @@ int fail_cuda(cudaError_t e, const char *what, const char *file, int line);
 // launchers (each enqueues on h->stream; return DCM_OK or an error code)
 int launch_kick_drift(dcm_handle *h);
 int launch_kick(dcm_handle *h);
-int launch_bin(dcm_handle *h);
-int launch_forces(dcm_handle *h, bool energy);
+int launch_bin(dcm_handle *h);                      // full cell sort + classes
+int launch_bin_gated(dcm_handle *h, const int *gate); // sort only if *gate, then classes
+int launch_scan(dcm_handle *h, const int32_t *in, int32_t *out, int32_t *tiles, int64_t m,
+                int32_t total, const int *gate);     // exclusive scan (total < 0: out[m] = sum)
+int launch_list_step(dcm_handle *h, bool force_rebuild);  // decide, [rebin], lists
+int launch_list_walk(dcm_handle *h, bool fill, const int *gate, float delta);
+int launch_forces(dcm_handle *h, bool energy);   // list mode when skin > 0 and the lists are ok
 int launch_detect(dcm_handle *h);
 int launch_reduce_energy(dcm_handle *h, int k);
 int launch_reduce_pairs(dcm_handle *h);

@@ -1,0 +1,129 @@
+// dcm_list.cu -- Verlet pair lists with a skin for the DCM force (Section
+// 2.2.1 and Algorithm 3.3 of the thesis: store every j within r_c[i] + r_s,
+// reuse the list while no particle moved r_s/2).
+//
+// With per-particle cutoffs the reuse condition also covers cutoff growth:
+// a pair inside r_c[i](t) now was within r_c[i](t) + 2 d_max at the build,
+// so the list of particle i (all j within its list radius R_i) stays
+// complete while
+//     2 * d_max < min_i (R_i - r_c[i](t)),
+// with d_max the largest displacement since the build.  R_i is the cutoff
+// particle i would get if its interface distance dropped by one sigma, plus
+// the skin: the detected interface jitters by about a voxel, and Eq. 7 is
+// steep near d = r_c,max, so lists sized by the current cutoff alone would be
+// rebuilt at nearly every detection.  Every step one
+// kernel measures both maxima and decides; the cell sort and the list build
+// that follow are launched every step but do nothing unless the decision
+// was "rebuild", so the step stays one fixed CUDA graph.
+//
+// Lists are indexed by the sorted slot k of the build; an entry holds the
+// sorted slot j of a neighbour (24 bits) and its row's cell offsets dy, dz
+// (4 bits each); the x offset comes from the cell x index stored with j's
+// position.  If the entries would not fit the storage reserved at creation,
+// that step uses the direct cell walk and the next step rebuilds.
+#include "dcm_device.cuh"
+
+namespace dcm {
+
+// largest displacement^2 since the build and the smallest cutoff headroom
+// R_i - r_c[i]; the last block to finish turns them into the decision
+__global__ void k_list_check(Batch b, const double *__restrict__ x, const double *__restrict__ x_ref,
+                             const double *__restrict__ rc, const float *__restrict__ rl_ref,
+                             int *lf, int force)
+{
+    float md = 0.f, mh = 3.0e38f;
+    const size_t N = (size_t)b.N;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < b.N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float dx = (float)(x[i] - x_ref[i]);
+        float dy = (float)(x[N + i] - x_ref[N + i]);
+        float dz = (float)(x[2 * N + i] - x_ref[2 * N + i]);
+        // a coordinate wrapped through the box shows up as a jump of about
+        // one box edge: fold it back (moves are far below half an edge)
+        const Geom &g = b.sys[sys_of(b.p_off, b.M, i)];
+        float Lx = (float)g.L[0], Ly = (float)g.L[1], Lz = (float)g.L[2];
+        dx -= Lx * rintf(dx / Lx);
+        dy -= Ly * rintf(dy / Ly);
+        dz -= Lz * rintf(dz / Lz);
+        md = fmaxf(md, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        mh = fminf(mh, fmaxf(rl_ref[i] - (float)rc[i], 0.f));
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        md = fmaxf(md, __shfl_xor_sync(0xffffffffu, md, off));
+        mh = fminf(mh, __shfl_xor_sync(0xffffffffu, mh, off));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        // non-negative floats order like their bit patterns
+        atomicMax(&lf[LF_MAXDISP], __float_as_int(md));
+        atomicMin(&lf[LF_MINHEAD], __float_as_int(mh));
+    }
+    __syncthreads();
+    __shared__ int s_last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&lf[LF_DONE], 1) == (int)(gridDim.x * gridDim.y * gridDim.z) - 1;
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        float d2 = __int_as_float(atomicExch(&lf[LF_MAXDISP], 0));
+        float head = __int_as_float(atomicExch(&lf[LF_MINHEAD], 0x7f7f7f7f));
+        int ok = atomicAdd(&lf[LF_OK], 0);
+        int rebuild = force || !ok || (2.f * sqrtf(d2) >= head);
+        lf[LF_REBUILD] = rebuild;
+        lf[LF_DONE] = 0;
+    }
+}
+
+// after the count scan: does the list fit?  FILL gate = rebuild && fits
+__global__ void k_list_total(int64_t N, const int32_t *__restrict__ start, int64_t cap, int *lf,
+                             DevStats *st)
+{
+    if (lf[LF_REBUILD] == 0) {
+        lf[LF_WORDS - 1] = 0;    // no fill on a step that keeps its lists
+        return;
+    }
+    int64_t total = start[N];
+    int ok = total <= cap;
+    lf[LF_OK] = ok;
+    lf[LF_WORDS - 1] = ok;       // fill gate
+    st->list_builds += 1ull;
+    st->list_entries = (unsigned long long)total;
+}
+
+__global__ void k_list_save(int64_t N, const double *__restrict__ x, double *x_ref, const int *gate)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N || *gate == 0) return;
+    x_ref[i] = x[i];
+    x_ref[N + i] = x[N + i];
+    x_ref[2 * N + i] = x[2 * N + i];
+}
+
+static inline int nblk(int64_t n, int b) { return (int)((n + b - 1) / b); }
+
+// decide, [cell sort], gather + classes, [list count, scan, fill, save]
+int launch_list_step(dcm_handle *h, bool force_rebuild)
+{
+    cudaStream_t s = h->stream;
+    int64_t N = h->n;
+    int cgrid = h->num_sms * 2;
+    k_list_check<<<cgrid, 256, 0, s>>>(h->b, h->x, h->x_ref, h->rc, h->rl_ref, h->lflags,
+                                        force_rebuild ? 1 : 0);
+    const int *rebuild = h->lflags + LF_REBUILD;
+    const int *fill = h->lflags + (LF_WORDS - 1);
+    int r = launch_bin_gated(h, rebuild);
+    if (r) return r;
+    float delta = h->cut_detected ? 1.0f : 0.0f;
+    r = launch_list_walk(h, false, rebuild, delta);
+    if (r) return r;
+    launch_scan(h, h->nl_cnt, h->nl_start, h->nl_tiles, N, -1, rebuild);
+    k_list_total<<<1, 1, 0, s>>>(N, h->nl_start, h->nl_cap, h->lflags, h->stats);
+    r = launch_list_walk(h, true, fill, delta);
+    if (r) return r;
+    k_list_save<<<nblk(N, 256), 256, 0, s>>>(N, h->x, h->x_ref, fill);
+    h->kernels += 3;
+    return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "list launch");
+}
+
+}  // namespace dcm

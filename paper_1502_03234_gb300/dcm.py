@@ -54,7 +54,7 @@ class dcm_params(C.Structure):
                 ("detect_every", C.c_int32), ("kmeans_max_iter", C.c_int32),
                 ("cfsm_iter_max", C.c_int32), ("cfsm_eps", C.c_double),
                 ("precision", C.c_int32), ("n_classes", C.c_int32), ("cell_min", C.c_double),
-                ("reserved", C.c_int32 * 8)]
+                ("skin", C.c_double), ("reserved", C.c_int32 * 6)]
 
 
 class dcm_tuning(C.Structure):
@@ -68,7 +68,8 @@ class dcm_stats(C.Structure):
                 ("grid", C.c_int32 * 3), ("cells", C.c_int32 * 3), ("c_liquid", C.c_double),
                 ("c_vapor", C.c_double), ("guard_rechecks", C.c_int64),
                 ("kernels_plain", C.c_int32), ("kernels_detect", C.c_int32),
-                ("reserved", C.c_int64 * 5)]
+                ("list_builds", C.c_int64), ("list_entries", C.c_int64),
+                ("reserved", C.c_int64 * 3)]
 
 
 _lib = None

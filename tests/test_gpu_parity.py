@@ -148,3 +148,62 @@ def test_ten_steps_positions(dcm, orc, prec):
     print(f"prec {prec}: |E(10)-E(0)|/|E(0)| = {abs(e1 - e0) / abs(e0):.3e} "
           f"(oracle {abs((ep[-1] + ek[-1]) - (ep[0] + ek[0])) / abs(ep[0] + ek[0]):.3e})")
     assert abs(e1 - e0) / abs(e0) < 1e-3
+
+
+# ---- Verlet lists (skin > 0): the same pairs as the direct walk, always --------
+@pytest.mark.parametrize("prec,skin", [(0, 0.4), (1, 0.4), (1, 0.25)])
+def test_list_mode_forces(dcm, orc, prec, skin):
+    s = slabgen.make_slab(16000, seed=40)
+    with dcm.System(s.box, len(s.x), precision=prec, skin=skin) as sy:
+        sy.set_state(s.x, s.v)
+        sy.compute_forces()
+        _, rc, _ = sy.cutoffs()
+        x, _, f = sy.get_state()
+        npair = sy.pair_counts()
+        nc, _, _ = sy.cells()
+        st = sy.stats()
+    assert st.list_builds >= 1 and st.list_entries > 0
+    ref = orc.forces(x, rc, s.box, nc)
+    assert np.array_equal(npair, ref.npair)
+    err = np.linalg.norm(f - ref.f, axis=1)
+    fmag = np.linalg.norm(ref.f, axis=1)
+    extra = 0.0 if prec == 0 else 5e-4
+    assert np.all(err <= FP64_ABS + FP64_REL * fmag + extra), err.max()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_list_mode_stays_complete_while_reused(dcm, orc, prec):
+    # after many steps of list reuse and rebuilds the interacting pairs must
+    # still be exactly those of the definition at the current positions
+    s = slabgen.make_slab(9001, seed=41)
+    with dcm.System(s.box, len(s.x), precision=prec, skin=0.3) as sy:
+        sy.set_state(s.x, s.v)
+        sy.step(150)
+        sy.sync()
+        st = sy.stats()
+        npair = sy.pair_counts()
+        _, rc, _ = sy.cutoffs()
+        x, _, f = sy.get_state()
+        nc, _, _ = sy.cells()
+    assert st.list_builds >= 3, st.list_builds          # rebuilt along the way
+    assert st.list_builds < 150                          # and reused in between
+    ref = orc.forces(x, rc, s.box, nc)
+    assert np.array_equal(npair, ref.npair)
+    err = np.linalg.norm(f - ref.f, axis=1)
+    fmag = np.linalg.norm(ref.f, axis=1)
+    extra = 0.0 if prec == 0 else 5e-4
+    assert np.all(err <= FP64_ABS + FP64_REL * fmag + extra), err.max()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_list_mode_ten_steps_match_oracle(dcm, orc, prec):
+    s = slabgen.make_slab(16000, seed=10)
+    with dcm.System(s.box, len(s.x), precision=prec, skin=0.4) as sy:
+        sy.set_state(s.x, s.v)
+        sy.step(10)
+        sy.sync()
+        x, _, _ = sy.get_state()
+    p = orc.RunParams(det=orc.DetectParams(rc_min=3.0, rc_max=6.0, voxel=1.0), dt=0.005,
+                      detect_every=2, cell_min=1.5)
+    xr, *_ = orc.run(s.x, s.v, s.box, p, 10)
+    assert np.abs(_minimg(x - xr, s.box)).max() < 1e-4
