@@ -156,6 +156,8 @@ static int setup_geometry(const dcm_box *box, int64_t n, const dcm_params *p, Ge
     }
     double hmax = fmax(g.h[0], fmax(g.h[1], g.h[2]));
     g.r_grid = p->rc_max + hmax;
+    for (int a = 0; a < 3; ++a) g.w_h[a] = 1.0 / (g.h[a] * g.h[a]);
+    g.e_min = 1.0 / sqrt(g.w_h[0] + g.w_h[1] + g.w_h[2]);
     g.rc_min = p->rc_min;
     g.rc_max = p->rc_max;
     g.alpha = p->alpha;

@@ -24,6 +24,8 @@
 // Bound: HBM/L2 (the grid holds ~3.7 voxels per particle at 1 sigma voxels).
 #include <cooperative_groups.h>
 
+#include <type_traits>
+
 #include "dcm_device.cuh"
 
 namespace dcm {
@@ -87,6 +89,54 @@ __global__ void k_smooth(Batch b, const TIN *__restrict__ in, TOUT *out, SmoothW
         for (int k = 0; k <= w.order; ++k) s += w.w[k] * (uint32_t)tap(k);
         out[v] = (TOUT)s;
     }
+}
+
+// the default order 8 (weights C(8,k)) with the taps unrolled at compile
+// time: interior voxels index their line directly, only the 8 voxels nearest
+// the periodic seam wrap
+template <int AXIS, typename TIN, typename TOUT>
+__global__ void __launch_bounds__(256) k_smooth8(Batch b, const TIN *__restrict__ in, TOUT *out,
+                                                 uint32_t bmax, int *err)
+{
+    constexpr uint32_t W[9] = {1, 8, 28, 56, 70, 56, 28, 8, 1};
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= b.NV) return;
+    const Geom &g = b.sys[sys_of(b.v_off, b.M, v)];
+    const int nx = g.gd[0], ny = g.gd[1], nz = g.gd[2];
+    const int lv = (int)(v - g.v0);
+    int c, n, stride;
+    if constexpr (AXIS == 0) {
+        c = lv % nx;
+        n = nx;
+        stride = 1;
+    } else if constexpr (AXIS == 1) {
+        c = (lv / nx) % ny;
+        n = ny;
+        stride = nx;
+    } else {
+        c = lv / (nx * ny);
+        n = nz;
+        stride = nx * ny;
+    }
+    const TIN *line = in + (v - (int64_t)c * stride);
+    if constexpr (AXIS == 0) {
+        if ((uint32_t)in[v] > bmax) atomicOr(err, DEV_ERR_DENSITY);
+    }
+    using ACC = typename std::conditional<sizeof(TOUT) == 8, unsigned long long, uint32_t>::type;
+    ACC sum = 0;
+    if (c >= 4 && c + 4 < n) {
+        const TIN *p = line + (int64_t)(c - 4) * stride;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) sum += (ACC)W[k] * (ACC)(uint32_t)p[(int64_t)k * stride];
+    } else {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            int q = c + k - 4;
+            q = ((q % n) + n) % n;
+            sum += (ACC)W[k] * (ACC)(uint32_t)line[(int64_t)q * stride];
+        }
+    }
+    out[v] = (TOUT)sum;
 }
 
 // ---- K-means (Eq. 14, K = 2), all systems in one cooperative kernel ------------
@@ -395,11 +445,22 @@ __global__ void __launch_bounds__(DET_THREADS) k_cfsm(CfsmArgs a)
                 // D and the lists were written by other blocks in the previous
                 // pass: read them through L2 (ld.global.cg), not a stale L1
                 double old = __ldcg(&X[v]);
-                double ax = fmin(__ldcg(&X[nb[0]]), __ldcg(&X[nb[1]]));
-                double ay = fmin(__ldcg(&X[nb[2]]), __ldcg(&X[nb[3]]));
-                double az = fmin(__ldcg(&X[nb[4]]), __ldcg(&X[nb[5]]));
-                double dbar = godunov(ax, ay, az, g.h[0], g.h[1], g.h[2]);
-                bool changed = dbar < old && dbar <= g.r_grid;
+                double ax = dmin_nonneg(__ldcg(&X[nb[0]]), __ldcg(&X[nb[1]]));
+                double ay = dmin_nonneg(__ldcg(&X[nb[2]]), __ldcg(&X[nb[3]]));
+                double az = dmin_nonneg(__ldcg(&X[nb[4]]), __ldcg(&X[nb[5]]));
+                // any Godunov solution is at least min(a) + 1/sqrt(sum w): when
+                // that cannot beat the current value the solve is skipped
+                // (a lower bound with a relative margin, so no update is lost)
+                double amin = dmin_nonneg(ax, dmin_nonneg(ay, az));
+                bool changed = false;
+                double dbar = old;
+                if (!isinf(amin) &&
+                    __double_as_longlong(old) > __double_as_longlong(amin + 0.999999 * g.e_min)) {
+                    dbar = godunov_w(ax, ay, az, g.h[0], g.h[1], g.h[2], g.w_h[0], g.w_h[1], g.w_h[2]);
+                    // non-negative doubles: compare the bit patterns
+                    changed = __double_as_longlong(dbar) < __double_as_longlong(old) &&
+                              __double_as_longlong(dbar) <= __double_as_longlong(g.r_grid);
+                }
                 Y[v] = changed ? dbar : old;
                 if (changed) {
                     // the voxel itself (so Y catches up next pass) and its
@@ -623,9 +684,15 @@ int launch_detect(dcm_handle *h)
             for (int k = r; k >= 1; --k) w.w[k] += w.w[k - 1];
         uint64_t pass = 1ull << order;   // sum of the weights
         w.bmax = (uint32_t)(0xffffffffull / (pass * pass));
-        k_smooth<0, int32_t, uint32_t><<<vb, DET_THREADS, 0, s>>>(b, h->B, h->sm1, w, h->err);
-        k_smooth<1, uint32_t, uint32_t><<<vb, DET_THREADS, 0, s>>>(b, h->sm1, h->sm2, w, h->err);
-        k_smooth<2, uint32_t, double><<<vb, DET_THREADS, 0, s>>>(b, h->sm2, h->Bs, w, h->err);
+        if (order == 8) {
+            k_smooth8<0, int32_t, uint32_t><<<vb, DET_THREADS, 0, s>>>(b, h->B, h->sm1, w.bmax, h->err);
+            k_smooth8<1, uint32_t, uint32_t><<<vb, DET_THREADS, 0, s>>>(b, h->sm1, h->sm2, w.bmax, h->err);
+            k_smooth8<2, uint32_t, double><<<vb, DET_THREADS, 0, s>>>(b, h->sm2, h->Bs, w.bmax, h->err);
+        } else {
+            k_smooth<0, int32_t, uint32_t><<<vb, DET_THREADS, 0, s>>>(b, h->B, h->sm1, w, h->err);
+            k_smooth<1, uint32_t, uint32_t><<<vb, DET_THREADS, 0, s>>>(b, h->sm1, h->sm2, w, h->err);
+            k_smooth<2, uint32_t, double><<<vb, DET_THREADS, 0, s>>>(b, h->sm2, h->Bs, w, h->err);
+        }
     } else {
         SmoothW w;
         w.order = 0;

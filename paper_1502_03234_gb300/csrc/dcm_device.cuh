@@ -143,24 +143,26 @@ __device__ __forceinline__ bool grid_barrier(unsigned int *words, int *err)
 }
 
 // ---- Godunov upwind local solve (Eq. 16-19, per-axis spacing) -----------
-// The same expression sequence as the oracle's definition, FMA-free.
-__device__ __forceinline__ double godunov(double a0, double a1, double a2,
-                                          double h0, double h1, double h2)
+// The same expression sequence as the oracle's definition, FMA-free; the
+// weights w_k = 1/h_k^2 come precomputed (the same IEEE quotients).
+__device__ __forceinline__ double godunov_w(double a0, double a1, double a2, double h0, double h1,
+                                            double h2, double w1, double w2, double w3)
 {
-    // stable sort of (a, h) by a
-    if (a1 < a0) { double t = a0; a0 = a1; a1 = t; t = h0; h0 = h1; h1 = t; }
+    // stable sort of (a, h, w) by a
+    if (a1 < a0) {
+        double t = a0; a0 = a1; a1 = t; t = h0; h0 = h1; h1 = t; t = w1; w1 = w2; w2 = t;
+    }
     if (a2 < a1) {
-        double t = a1; a1 = a2; a2 = t; t = h1; h1 = h2; h2 = t;
-        if (a1 < a0) { t = a0; a0 = a1; a1 = t; t = h0; h0 = h1; h1 = t; }
+        double t = a1; a1 = a2; a2 = t; t = h1; h1 = h2; h2 = t; t = w2; w2 = w3; w3 = t;
+        if (a1 < a0) {
+            t = a0; a0 = a1; a1 = t; t = h0; h0 = h1; h1 = t; t = w1; w1 = w2; w2 = t;
+        }
     }
     if (isinf(a0)) return a0;
     double d2 = DSUB(a1, a0);
     double d3 = DSUB(a2, a0);
     double e = h0;
     if (e <= d2) return DADD(a0, e);
-    double w1 = __ddiv_rn(1.0, DMUL(h0, h0));
-    double w2 = __ddiv_rn(1.0, DMUL(h1, h1));
-    double w3 = __ddiv_rn(1.0, DMUL(h2, h2));
     double wd2 = DMUL(w2, d2);
     double A = DADD(w1, w2);
     double B = wd2;
@@ -177,6 +179,19 @@ __device__ __forceinline__ double godunov(double a0, double a1, double a2,
     if (disc < 0.0) disc = 0.0;
     e = __ddiv_rn(DADD(B, __dsqrt_rn(disc)), A);
     return DADD(a0, e);
+}
+
+__device__ __forceinline__ double godunov(double a0, double a1, double a2, double h0, double h1,
+                                          double h2)
+{
+    return godunov_w(a0, a1, a2, h0, h1, h2, __ddiv_rn(1.0, DMUL(h0, h0)),
+                     __ddiv_rn(1.0, DMUL(h1, h1)), __ddiv_rn(1.0, DMUL(h2, h2)));
+}
+
+// min of two non-negative doubles (or +inf) by their bit patterns
+__device__ __forceinline__ double dmin_nonneg(double a, double b)
+{
+    return __double_as_longlong(a) < __double_as_longlong(b) ? a : b;
 }
 
 __device__ __forceinline__ double lerp_rn(double a, double b, double t)

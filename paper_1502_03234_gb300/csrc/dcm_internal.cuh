@@ -77,6 +77,8 @@ struct Geom {
     double inv_h[3];             // gd / L
     double h[3];                 // L / gd
     double r_grid;               // CFSM band: rc_max + max h
+    double w_h[3];               // 1 / h^2 per axis (the Godunov weights)
+    double e_min;                // 1 / sqrt(sum w): smallest possible Godunov step
     double rc_min, rc_max, alpha, cut_a, cut_b;
     int K;
     double thr[DCM_MAX_CLASSES]; // class thresholds on d (descending)
