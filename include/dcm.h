@@ -97,12 +97,19 @@ typedef struct {
     int32_t reserved[6];
 } dcm_params;
 
-/* Launch shape of the force kernel per cutoff class (the autotuner's
- * output; see dcm_set_tuning). */
+/* Force walk variants (dcm_tuning.walk).  DCM_WALK_WARP: one warp per
+ * particle over its flattened candidate list (DCM_MIXED without Verlet
+ * lists; other configurations use DCM_WALK_LANES whatever is set).
+ * DCM_WALK_LANES: lanes[] lanes per particle walk its stencil rows. */
+enum { DCM_WALK_WARP = 0, DCM_WALK_LANES = 1 };
+
+/* Launch shape of the force kernel (the autotuner's output; see
+ * dcm_set_tuning).  lanes[] and block apply to DCM_WALK_LANES. */
 typedef struct {
     int32_t lanes[DCM_MAX_CLASSES];        /* lanes per particle: 1..32, pow2 */
-    int32_t block;                         /* threads per block: 64..1024 */
-    int32_t reserved[7];
+    int32_t block;                         /* threads per block: 64..256 */
+    int32_t walk;                          /* DCM_WALK_WARP (default) or DCM_WALK_LANES */
+    int32_t reserved[6];
 } dcm_tuning;
 
 typedef struct {

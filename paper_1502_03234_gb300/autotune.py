@@ -3,10 +3,11 @@
 Tunes, on the live system, (a) the link-cell edge (a fraction of r_c,min:
 smaller cells trim the candidate volume towards the cutoff sphere, larger
 ones cut per-row overhead), (b) the threads per block and (c) per cutoff
-class the number of lanes that share one particle (1..32).  Interfacial
-classes (large r_c, 8-13x the pairs of bulk particles) want more lanes; the
-bulk wants fewer lanes and less per-row overhead.  The search is a
-coordinate descent over the classes, heaviest class first, timed with the
+class the number of lanes that share one particle (1..32) for the lanes
+walk, against the warp-per-particle walk.  Interfacial classes (large r_c,
+8-13x the pairs of bulk particles) want more lanes; the bulk wants fewer
+lanes and less per-row overhead.  The lanes search is a coordinate descent
+over the classes, heaviest class first; every candidate is timed with the
 library's per-phase CUDA events (the force phase of real steps).
 
 Results are cached per (N bucket, r_c,min, r_c,max, precision) in a JSON
@@ -34,10 +35,11 @@ class Tuning:
     block: int
     lanes: list = field(default_factory=lambda: [4, 8, 8, 8, 8, 8, 8, 8])
     force_ms: float = float("nan")
+    walk: int = dcm.DCM_WALK_WARP
 
 
 def key(n: int, rc_min: float, rc_max: float, precision: int) -> str:
-    return f"n2^{round(math.log2(max(n, 1)))}|rc{rc_min:g}/{rc_max:g}|p{precision}"
+    return f"v2|n2^{round(math.log2(max(n, 1)))}|rc{rc_min:g}/{rc_max:g}|p{precision}"
 
 
 def load_cache(path: str = CACHE) -> dict:
@@ -77,7 +79,8 @@ def _system(box, x, v, params: dcm.dcm_params, cell_min: float, stream=None) -> 
 
 def tune(box, x, v, params: dcm.dcm_params, *, reps: int = 5, stream=None,
          fractions=CELL_FRACTIONS, blocks=BLOCKS, lanes=LANES, log=None) -> Tuning:
-    """Search cell edge x block x lanes-per-class on this system's state."""
+    """Search cell edge x (warp walk | block x lanes-per-class) on this
+    system's state."""
     K = params.n_classes
     best: Tuning | None = None
     for frac in fractions:
@@ -87,6 +90,14 @@ def tune(box, x, v, params: dcm.dcm_params, *, reps: int = 5, stream=None,
         except dcm.DcmError:
             continue
         try:
+            if params.precision == dcm.DCM_MIXED and params.skin == 0:
+                sy.set_tuning([1], 128, dcm.DCM_WALK_WARP)
+                t_w = force_ms(sy, reps)
+                if log:
+                    log(f"cell {cell:.3f} warp walk force {t_w:.4f} ms")
+                if best is None or t_w < best.force_ms:
+                    best = Tuning(cell_min=cell, block=128, lanes=[1] * dcm.DCM_MAX_CLASSES,
+                                  force_ms=t_w, walk=dcm.DCM_WALK_WARP)
             for block in blocks:
                 cur = [4] + [8] * (dcm.DCM_MAX_CLASSES - 1)
                 sy.set_tuning(cur, block)
@@ -104,7 +115,8 @@ def tune(box, x, v, params: dcm.dcm_params, *, reps: int = 5, stream=None,
                 if log:
                     log(f"cell {cell:.3f} block {block} lanes {cur[:K]} force {t_cur:.4f} ms")
                 if best is None or t_cur < best.force_ms:
-                    best = Tuning(cell_min=cell, block=block, lanes=cur, force_ms=t_cur)
+                    best = Tuning(cell_min=cell, block=block, lanes=cur, force_ms=t_cur,
+                                  walk=dcm.DCM_WALK_LANES)
         finally:
             sy.close()
     if best is None:
@@ -123,5 +135,5 @@ def tuned_system(box, x, v, params: dcm.dcm_params, *, stream=None, cache_path: 
         save_cache(cache, cache_path)
     t = Tuning(**cache[k])
     sy = _system(box, x, v, params, t.cell_min, stream)
-    sy.set_tuning(t.lanes, t.block)
+    sy.set_tuning(t.lanes, t.block, t.walk)
     return sy, t

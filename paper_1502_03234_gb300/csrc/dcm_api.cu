@@ -210,7 +210,7 @@ static int64_t bytes_for(const Geom &g, int64_t n, int precision)
     int64_t ncell = g.ncell;
     int64_t nv = g.nvox;
     int64_t per_p = 3 * 8 * 3 + 8 + 8 + 1 + 4 * 3 + 16 + 4 + 4 + 8 + 48 + 24;
-    if (precision == DCM_FP64) per_p += 32;
+    per_p += 32;   // spd (FP64) or rq + pk (MIXED)
     int64_t per_v = 4 + 4 + 4 + 8 + 1 + 8 + 8 + 4 + 16;
     int64_t ntiles = (ncell + 2047) / 2048 + 1;
     int64_t lists = g.skin > 0 ? 4 * list_cap(g, n) + n * (4 + 4 + 24 + 8) : 0;
@@ -247,7 +247,7 @@ extern "C" int dcm_destroy(dcm_handle *h)
     for (int q = 0; q <= DCM_NUM_PHASES; ++q)
         if (h->ev[q]) cudaEventDestroy(h->ev[q]);
     void *ptrs[] = {h->x, h->v, h->f, h->d, h->rc, h->cls, h->cell_of, h->slot, h->cell_count,
-                    h->cell_start, h->sorted_id, h->scan_tmp, h->sp4, h->spd, h->class_list,
+                    h->cell_start, h->sorted_id, h->scan_tmp, h->sp4, h->spd, h->rq, h->pk, h->class_list,
                     h->class_count_dev, h->B, h->sm1, h->sm2, h->Bs, h->S, h->D0, h->D1, h->stamp,
                     h->flist, h->fcount, h->kacc, h->npair, h->pe, h->vir, h->red_part, h->red_out,
                     h->err, h->stats, h->tmp3n, h->geo_dev, h->off_dev, h->nl, h->nl_cnt,
@@ -320,6 +320,7 @@ static int create_systems(int M, const dcm_box *boxes, const int64_t *ns, const 
     // default launch shape: more lanes for larger cutoff classes
     for (int q = 0; q < DCM_MAX_CLASSES; ++q) h->tune.lanes[q] = q == 0 ? 2 : (q == 1 ? 1 : 2);
     h->tune.block = 128;
+    h->tune.walk = DCM_WALK_WARP;
     cudaGetDevice(&h->device);
     cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
     if (stream) {
@@ -359,6 +360,10 @@ static int create_systems(int M, const dcm_box *boxes, const int64_t *ns, const 
     ALLOC(h->scan_tmp, ntiles);
     ALLOC(h->sp4, N);
     if (h->p.precision == DCM_FP64) ALLOC(h->spd, N);
+    if (h->p.precision != DCM_FP64) {
+        ALLOC(h->rq, N);
+        ALLOC(h->pk, N);
+    }
     ALLOC(h->class_list, N);
     ALLOC(h->class_count_dev, 3 * DCM_MAX_CLASSES);
     ALLOC(h->B, nv);
@@ -862,6 +867,8 @@ extern "C" int dcm_set_tuning(dcm_handle *h, const dcm_tuning *t)
     }
     if (t->block < 64 || t->block > 256 || (t->block & 31))
         return fail(DCM_ERR_ARG, "block must be a multiple of 32 in 64..256");
+    if (t->walk != DCM_WALK_WARP && t->walk != DCM_WALK_LANES)
+        return fail(DCM_ERR_ARG, "walk must be DCM_WALK_WARP or DCM_WALK_LANES");
     h->tune = *t;
     invalidate_graphs(h);
     return DCM_OK;

@@ -125,7 +125,8 @@ __global__ void k_cell_sort(int64_t ncell, const int32_t *__restrict__ start, in
 // sorted position streams: sp4 = (x - cell corner in FP32, cell x index),
 // spd = absolute FP64 position (FP64 path only)
 __global__ void k_gather(Batch b, const double *__restrict__ x, const int32_t *__restrict__ sorted_id,
-                         const int32_t *__restrict__ cell_of, float4 *sp4, double4_32a *spd)
+                         const int32_t *__restrict__ cell_of, float4 *sp4, double4_32a *spd,
+                         const double *__restrict__ rc, float4 *rq, int4 *pk)
 {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= b.N) return;
@@ -149,6 +150,16 @@ __global__ void k_gather(Batch b, const double *__restrict__ x, const int32_t *_
     }
     sp4[k] = make_float4((float)u[0], (float)u[1], (float)u[2], (float)cx);
     if (spd) spd[k] = make_double4_32a(px, py, pz, 0.0);
+    if (rq) {
+        // the force walk's per-particle constants, once per particle here
+        // instead of once per warp there: FP32 r_c^2 with its 2^-18 guard
+        // band and the conservative culling radius
+        double r = rc[i];
+        float rc2f = (float)DMUL(r, r);
+        rq[k] = make_float4(rc2f, rc2f * (1.f - 3.814697265625e-06f), rc2f * (1.f + 3.814697265625e-06f),
+                            (float)r * 1.00002f + 1e-4f);
+        pk[k] = make_int4(i, cy, cz, 0);
+    }
 }
 
 // per-class lists of sorted slots (warp-aggregated appends keep neighbouring
@@ -221,7 +232,8 @@ int launch_bin_gated(dcm_handle *h, const int *gate)
                                                 h->sorted_id, gate);
     k_cell_sort<<<nblk(h->ncell, 256), 256, 0, s>>>(h->ncell, h->cell_start, h->sorted_id, gate);
     k_gather<<<nblk(n, 256), 256, 0, s>>>(h->b, h->x, h->sorted_id, h->cell_of, h->sp4,
-                                          h->p.precision == DCM_FP64 ? h->spd : nullptr);
+                                          h->p.precision == DCM_FP64 ? h->spd : nullptr, h->rc,
+                                          h->rq, h->pk);
     // class lists of sorted slots for the per-class force launches
     int K = h->b.K;
     cudaMemsetAsync(h->class_count_dev, 0, sizeof(int32_t) * 3 * DCM_MAX_CLASSES, s);

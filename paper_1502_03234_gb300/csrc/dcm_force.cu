@@ -42,6 +42,8 @@ struct ForceArgs {
     int lanes[DCM_MAX_CLASSES];   // lanes per particle per class
     const float4 *sp4;
     const double4_32a *spd;
+    const float4 *rq;             // MIXED: r_c^2, guard band, culling radius per slot
+    const int4 *pk;               // MIXED: id, cell y, cell z per slot
     const int32_t *cell_start;
     const int32_t *sorted_id;
     const int32_t *cell_of;
@@ -628,6 +630,301 @@ __global__ void __launch_bounds__(FORCE_THREADS, 3) k_force(ForceArgs a)
     if (threadIdx.x == 0 && s_ng) atomicAdd(a.guard_count, (unsigned long long)s_ng);
 }
 
+// ---- warp per particle over a flattened candidate list (mixed precision) ----
+// The lanes kernel above gives each particle G lanes that walk its stencil
+// rows one after another; rows hold a handful of candidates, so the lanes of
+// a warp spend much of their time in different loop phases.  Here one warp
+// owns one particle and every step is lane-parallel:
+//  1. rows: lane L sets up row L of a pass of 32 stencil rows (box-gap
+//     culling and the x chord, as in particle_force); the non-empty rows are
+//     compacted into a per-warp table with their offsets in one flattened
+//     candidate list (a warp prefix sum of the row lengths);
+//  2. candidates: lane L takes list positions base + L; its row is found
+//     from a 32-bit mask of the row starts inside the chunk (one warp OR
+//     reduction and a popcount), so a chunk may span any number of rows;
+//     the pair test and the force are evaluated without branches (the FP64
+//     re-decision at the cutoff edge is the only branch, and it is rare);
+//  3. the 32 lane partials are summed exactly: each FP32 partial is split
+//     into a multiple of 2^-8 and a remainder, both scaled to integers and
+//     added with warp integer reductions, so the total is the exact sum of
+//     the partials (up to 2^-30 per partial), independent of lane order.
+constexpr int FW_THREADS = 128;
+constexpr int FW_WARPS = FW_THREADS / 32;
+constexpr int FW_ROWS = 128;                 // row table entries per warp
+constexpr int FW_GRAB = 4;                   // particles per queue grab
+constexpr float FW_FIX_LIMIT = 65536.f;      // |partial| bound of the exact sum
+
+struct FwTable {
+    int4 ri[FW_ROWS];        // list offset P, main start, main length, wrapped start
+    float4 rf[FW_ROWS];      // x cell shift (main, wrapped), row y, row z
+    int rp[FW_ROWS];         // P again, read conflict-free by the row search
+};
+
+// Exact warp sum of FP32 partials whose magnitude is below FW_FIX_LIMIT, as
+// the fixed-point integer V = sum * 2^30 (|V| < 2^52).  Integer pipes only:
+// on this GPU one FP64 warp instruction costs as much issue time as dozens
+// of FP32 ones, and this runs once per particle, not once per pair.
+__device__ __forceinline__ long long warp_fixed_sum(float p)
+{
+    int hp = __float2int_rn(p * 256.f);
+    float rem = fmaf((float)hp, -0.00390625f, p);          // exact
+    int lp = __float2int_rn(rem * 1073741824.f);            // rem * 2^30, |.| <= 2^21
+    long long H = __reduce_add_sync(0xffffffffu, hp);
+    long long Lo = __reduce_add_sync(0xffffffffu, lp);
+    return H * 4194304ll + Lo;
+}
+
+// V * 2^-30 as a double, built from its bits (exact: |V| < 2^53)
+__device__ __forceinline__ double fixed_to_double(long long V)
+{
+    if (V == 0) return 0.0;
+    unsigned long long sign = (unsigned long long)V & 0x8000000000000000ull;
+    unsigned long long m = (unsigned long long)(V < 0 ? -V : V);
+    int e = 63 - __clzll(m);                                 // leading bit, <= 52
+    unsigned long long mant = (m << (52 - e)) & 0x000FFFFFFFFFFFFFull;
+    return __longlong_as_double(
+        (long long)(sign | ((unsigned long long)(e - 30 + 1023) << 52) | mant));
+}
+
+__device__ __forceinline__ double warp_tree_sum(float p)
+{
+    double d = (double)p;
+    for (int off = 16; off > 0; off >>= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
+    return d;
+}
+
+template <bool ENERGY>
+__device__ __forceinline__ void particle_force_warp(const ForceArgs &a, FwTable &tb, int k,
+                                                    int lane, int &ng)
+{
+    const Geom &g = a.b.sys[sys_of(a.b.p_off, a.b.M, k)];
+    const float4 ui = a.sp4[k];
+    const float4 q4 = a.rq[k];
+    const int4 pk = a.pk[k];
+    const int i = pk.x, cy = pk.y, cz = pk.z;
+    const int cx = (int)ui.w;
+    const float rc2f = q4.x, rc2lo = q4.y, rc2hi = q4.z, rcull = q4.w;
+    const float rcull2 = rcull * rcull;
+    const int sx = min(g.smax[0], (int)ceilf(rcull * g.inv_cf[0]));
+    const int sy = min(g.smax[1], (int)ceilf(rcull * g.inv_cf[1]));
+    const int sz = min(g.smax[2], (int)ceilf(rcull * g.inv_cf[2]));
+    const int ny_ = 2 * sy + 1;
+    const int nrows = ny_ * (2 * sz + 1);
+    const float inv_ny = rcp_approx((float)ny_);
+    const int nc0 = g.nc[0];
+    const float cf0 = g.cf[0];
+    const float sig2f = g.sig2f, eps48f = g.eps48f, eps24f = g.eps24f;
+    const unsigned lane_le = 0xffffffffu >> (31 - lane);
+    float fx = 0.f, fy = 0.f, fz = 0.f, pe = 0.f;
+    float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f, v4 = 0.f, v5 = 0.f;
+    int np = 0;
+    int ntab = 0, T = 0;
+    for (int r0 = 0; r0 < nrows; r0 += 32) {
+        // ---- 1. one stencil row per lane
+        const int r = r0 + lane;
+        int len = 0, j0a = 0, len1 = 0, j0b = 0;
+        float fa = 0.f, fb = 0.f, ay = 0.f, az = 0.f;
+        if (r < nrows) {
+            int dzi = (int)(((float)r + 0.5f) * inv_ny);    // r / ny_ (exact for these sizes)
+            int dz = dzi - sz, dy = r - dzi * ny_ - sy;
+            float gz = box_gap(dz, ui.z, g.cf[2]);
+            float remz = rcull2 - gz * gz;
+            float gy = box_gap(dy, ui.y, g.cf[1]);
+            float w2 = remz - gy * gy;
+            if (remz >= 0.f && w2 >= 0.f) {
+                int czz = cz + dz;
+                czz += czz < 0 ? g.nc[2] : (czz >= g.nc[2] ? -g.nc[2] : 0);
+                int cyy = cy + dy;
+                cyy += cyy < 0 ? g.nc[1] : (cyy >= g.nc[1] ? -g.nc[1] : 0);
+                az = ui.z - (float)dz * g.cf[2];
+                ay = ui.y - (float)dy * g.cf[1];
+                float w = sqrtf(w2);
+                int xlo = max(-sx, (int)floorf((ui.x - w) * g.inv_cf[0]));
+                int xhi = min(sx, (int)floorf((ui.x + w) * g.inv_cf[0]));
+                int row = (int)g.c0 + nc0 * (cyy + g.nc[1] * czz);
+                int lo = cx + xlo, hi = cx + xhi;
+                int len2 = 0;
+                if (lo < 0) {
+                    // cells at the top end seen through the x = 0 face
+                    j0b = a.cell_start[row + lo + nc0];
+                    len2 = a.cell_start[row + nc0] - j0b;
+                    fb = (float)(cx + nc0);
+                    lo = 0;
+                } else if (hi >= nc0) {
+                    j0b = a.cell_start[row];
+                    len2 = a.cell_start[row + hi - nc0 + 1] - j0b;
+                    fb = (float)(cx - nc0);
+                    hi = nc0 - 1;
+                }
+                if (lo <= hi) {
+                    j0a = a.cell_start[row + lo];
+                    len1 = a.cell_start[row + hi + 1] - j0a;
+                }
+                fa = (float)cx;
+                len = len1 + len2;
+            }
+        }
+        // compact the non-empty rows into the table
+        int incl = len;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += t;
+        }
+        const unsigned ne = __ballot_sync(0xffffffffu, len > 0);
+        if (len > 0) {
+            int e = ntab + __popc(ne & (lane_le >> 1));
+            int P = T + incl - len;
+            tb.ri[e] = make_int4(P, j0a, len1, j0b);
+            tb.rf[e] = make_float4(fa, fb, ay, az);
+            tb.rp[e] = P;
+        }
+        ntab += __popc(ne);
+        T += __shfl_sync(0xffffffffu, incl, 31);
+        if (ntab <= FW_ROWS - 32 && r0 + 32 < nrows) continue;
+        __syncwarp();
+        // ---- 2. the flattened candidates, 32 per chunk
+        int S = 0;   // rows that start before the chunk
+        for (int base = 0; base < T; base += 32) {
+            int q = S + lane;
+            unsigned d = (unsigned)((q < ntab ? tb.rp[q] : 0x7fffffff) - base);
+            unsigned M = __reduce_or_sync(0xffffffffu, d < 32u ? 1u << d : 0u);
+            int rowi = S + __popc(M & lane_le) - 1;
+            S += __popc(M);
+            int p = base + lane;
+            if (p < T) {
+                int4 ri = tb.ri[rowi];
+                float4 rf = tb.rf[rowi];
+                int t = p - ri.x;
+                bool wr = t >= ri.z;
+                int j = wr ? ri.w + (t - ri.z) : ri.y + t;
+                float ax = wr ? rf.y : rf.x;
+                float4 uj = a.sp4[j];
+                float dx = fmaf(ax - uj.w, cf0, ui.x - uj.x);
+                float dy = rf.z - uj.y;
+                float dz = rf.w - uj.z;
+                float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                bool in = r2 < rc2f && j != k;
+                if (r2 >= rc2lo && r2 < rc2hi && j != k) {
+                    double rci = a.rc[i];
+                    in = fp64_inside(a, g, i, a.sorted_id[j], DMUL(rci, rci));
+                    ++ng;
+                }
+                float r2inv = rcp_approx(r2);
+                float sr2 = sig2f * r2inv;
+                float sr6 = sr2 * sr2 * sr2;
+                float fr = r2inv * sr6 * fmaf(eps48f, sr6, -eps24f);
+                fr = in ? fr : 0.f;
+                fx = fmaf(fr, dx, fx);
+                fy = fmaf(fr, dy, fy);
+                fz = fmaf(fr, dz, fz);
+                np += in ? 1 : 0;
+                if constexpr (ENERGY) {
+                    pe += in ? g.eps2f * sr6 * (sr6 - 1.f) : 0.f;
+                    float gx = fr * dx, gy = fr * dy, gz = fr * dz;
+                    v0 = fmaf(0.5f * dx, gx, v0);
+                    v1 = fmaf(0.5f * dy, gy, v1);
+                    v2 = fmaf(0.5f * dz, gz, v2);
+                    v3 = fmaf(0.5f * dx, gy, v3);
+                    v4 = fmaf(0.5f * dx, gz, v4);
+                    v5 = fmaf(0.5f * dy, gz, v5);
+                }
+            }
+        }
+        __syncwarp();
+        ntab = 0;
+        T = 0;
+    }
+    // ---- 3. sum the lane partials; lane q writes value q
+    bool small = fabsf(fx) < FW_FIX_LIMIT && fabsf(fy) < FW_FIX_LIMIT && fabsf(fz) < FW_FIX_LIMIT;
+    if constexpr (ENERGY)
+        small = small && fabsf(pe) < FW_FIX_LIMIT && fabsf(v0) < FW_FIX_LIMIT &&
+                fabsf(v1) < FW_FIX_LIMIT && fabsf(v2) < FW_FIX_LIMIT && fabsf(v3) < FW_FIX_LIMIT &&
+                fabsf(v4) < FW_FIX_LIMIT && fabsf(v5) < FW_FIX_LIMIT;
+    const size_t n = (size_t)a.b.N;
+    const int npt = __reduce_add_sync(0xffffffffu, np);
+    if (lane == 3) a.npair[i] = npt;
+    if (__all_sync(0xffffffffu, small)) {
+        long long V = 0, t;
+        t = warp_fixed_sum(fx); V = lane == 0 ? t : V;
+        t = warp_fixed_sum(fy); V = lane == 1 ? t : V;
+        t = warp_fixed_sum(fz); V = lane == 2 ? t : V;
+        if constexpr (ENERGY) {
+            t = warp_fixed_sum(pe); V = lane == 4 ? t : V;
+            t = warp_fixed_sum(v0); V = lane == 5 ? t : V;
+            t = warp_fixed_sum(v1); V = lane == 6 ? t : V;
+            t = warp_fixed_sum(v2); V = lane == 7 ? t : V;
+            t = warp_fixed_sum(v3); V = lane == 8 ? t : V;
+            t = warp_fixed_sum(v4); V = lane == 9 ? t : V;
+            t = warp_fixed_sum(v5); V = lane == 10 ? t : V;
+        }
+        const double out = fixed_to_double(V);
+        if (lane < 3) a.f[lane * n + i] = out;
+        if constexpr (ENERGY) {
+            if (lane == 4) a.pe[i] = out;
+            if (lane >= 5 && lane < 11) a.vir[(lane - 5) * n + i] = out;
+        }
+    } else {
+        // a partial beyond the fixed-point range (or not finite): FP64 tree
+        double Fx = warp_tree_sum(fx), Fy = warp_tree_sum(fy), Fz = warp_tree_sum(fz);
+        if (lane < 3) a.f[lane * n + i] = lane == 0 ? Fx : (lane == 1 ? Fy : Fz);
+        if constexpr (ENERGY) {
+            double s7[7] = {warp_tree_sum(pe), warp_tree_sum(v0), warp_tree_sum(v1),
+                            warp_tree_sum(v2), warp_tree_sum(v3), warp_tree_sum(v4),
+                            warp_tree_sum(v5)};
+            if (lane == 4) a.pe[i] = s7[0];
+#pragma unroll
+            for (int e = 0; e < 6; ++e)
+                if (lane == 5 + e) a.vir[e * n + i] = s7[1 + e];
+        }
+    }
+}
+
+template <bool ENERGY>
+__global__ void __launch_bounds__(FW_THREADS, 8) k_force_warp(ForceArgs a)
+{
+    __shared__ FwTable s_tab[FW_WARPS];
+    __shared__ int s_cnt[DCM_MAX_CLASSES], s_off[DCM_MAX_CLASSES], s_items[DCM_MAX_CLASSES + 1];
+    const int K = a.b.K;
+    if (threadIdx.x == 0) {
+        int run = 0;
+        // heaviest (largest cutoff) class first
+        for (int q = K - 1, t = 0; q >= 0; --q, ++t) {
+            s_cnt[q] = a.class_buf[q];
+            s_off[q] = a.class_buf[K + q];
+            s_items[t] = run;
+            run += s_cnt[q];
+        }
+        s_items[K] = run;
+    }
+    __syncthreads();
+    const int total = s_items[K];
+    const int lane = threadIdx.x & 31;
+    FwTable &tb = s_tab[threadIdx.x >> 5];
+    int ng = 0;
+    while (true) {
+        int item0 = 0;
+        if (lane == 0) item0 = (int)atomicAdd(a.queue, (unsigned)FW_GRAB);
+        item0 = __shfl_sync(0xffffffffu, item0, 0);
+        if (item0 >= total) break;
+        const int item1 = min(item0 + FW_GRAB, total);
+        int t = 0;
+        for (int item = item0; item < item1; ++item) {
+            while (t + 1 < K && item >= s_items[t + 1]) ++t;
+            int q = K - 1 - t;
+            int k = a.class_list[s_off[q] + (item - s_items[t])];
+            particle_force_warp<ENERGY>(a, tb, k, lane, ng);
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) ng += __shfl_xor_sync(0xffffffffu, ng, off);
+    __shared__ int s_ng;
+    if (threadIdx.x == 0) s_ng = 0;
+    __syncthreads();
+    if (lane == 0 && ng) atomicAdd(&s_ng, ng);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_ng) atomicAdd(a.guard_count, (unsigned long long)s_ng);
+}
+
 static void fill_args(dcm_handle *h, ForceArgs &a);
 
 int launch_list_walk(dcm_handle *h, bool fill, const int *gate, float delta)
@@ -656,6 +953,14 @@ int launch_forces(dcm_handle *h, bool energy)
     int block = h->tune.block >= 64 && h->tune.block <= FORCE_THREADS ? h->tune.block : FORCE_THREADS;
     int grid = h->num_sms * (2048 / block);
     bool fp64 = h->p.precision == DCM_FP64;
+    if (!fp64 && !h->nl && h->tune.walk == DCM_WALK_WARP) {
+        int g2 = h->num_sms * 8;
+        if (energy)
+            k_force_warp<true><<<g2, FW_THREADS, 0, h->stream>>>(a);
+        else
+            k_force_warp<false><<<g2, FW_THREADS, 0, h->stream>>>(a);
+        return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "force launch");
+    }
     if (fp64) {
         if (energy)
             k_force<DCM_FP64, true><<<grid, block, 0, h->stream>>>(a);
@@ -681,6 +986,8 @@ static void fill_args(dcm_handle *h, ForceArgs &a)
     }
     a.sp4 = h->sp4;
     a.spd = h->spd;
+    a.rq = h->rq;
+    a.pk = h->pk;
     a.cell_start = h->cell_start;
     a.sorted_id = h->sorted_id;
     a.cell_of = h->cell_of;

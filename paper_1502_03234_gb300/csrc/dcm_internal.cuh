@@ -13,7 +13,9 @@
 //   link cells        : cell_of[N], slot[N] (id order); cell_count[Nc],
 //                       cell_start[Nc+1], sorted_id[N]; sp4[N] float4
 //                       (cell-relative x,y,z in FP32, cell x index) and
-//                       spd[N] double4_32a (absolute x,y,z) in cell order
+//                       spd[N] double4_32a (absolute x,y,z) in cell order;
+//                       MIXED: rq[N] float4 (r_c^2 and its guard band, culling
+//                       radius) and pk[N] int4 (id, cell y, cell z) in cell order
 //   voxel grid        : B int32, sm1/sm2 uint32 (smoothing passes), Bs double,
 //                       S uint8, D0/D1 double (CFSM ping-pong), stamp int32,
 //                       four frontier lists int32 [Nv]
@@ -150,6 +152,8 @@ struct dcm_handle {
     int32_t *cell_of, *slot, *cell_count, *cell_start, *sorted_id, *scan_tmp;
     float4 *sp4;
     double4_32a *spd;
+    float4 *rq;                  // MIXED: per sorted slot r_c^2, guard band, culling radius
+    int4 *pk;                    // MIXED: per sorted slot particle id, cell y, cell z
     int32_t *class_list;         // sorted slots grouped by class
     int32_t *class_count_dev;    // [K] counts, [K..2K) cursors
     // grid

@@ -21,6 +21,7 @@ DCM_ERR_NOT_CONVERGED, DCM_ERR_DEVICE_CHECK, DCM_ERR_CANCELLED, DCM_ERR_STATE = 
 DCM_FP64, DCM_MIXED = 0, 1
 DCM_HOST, DCM_DEVICE = 0, 1
 DCM_MAX_CLASSES = 8
+DCM_WALK_WARP, DCM_WALK_LANES = 0, 1
 
 #: every entry point include/dcm.h declares (checked by the ABI test)
 EXPORTS = [
@@ -59,7 +60,7 @@ class dcm_params(C.Structure):
 
 class dcm_tuning(C.Structure):
     _fields_ = [("lanes", C.c_int32 * DCM_MAX_CLASSES), ("block", C.c_int32),
-                ("reserved", C.c_int32 * 7)]
+                ("walk", C.c_int32), ("reserved", C.c_int32 * 6)]
 
 
 class dcm_stats(C.Structure):
@@ -254,11 +255,12 @@ def dcm_get_stats(h) -> dcm_stats:
     return s
 
 
-def dcm_set_tuning(h, lanes, block: int = 256) -> None:
+def dcm_set_tuning(h, lanes, block: int = 256, walk: int = None) -> None:
     t = dcm_tuning()
     for q in range(DCM_MAX_CLASSES):
         t.lanes[q] = int(lanes[min(q, len(lanes) - 1)])
     t.block = int(block)
+    t.walk = DCM_WALK_LANES if walk is None else int(walk)
     check(lib().dcm_set_tuning(h, C.byref(t)))
 
 
@@ -415,8 +417,9 @@ class System:
     def stats(self) -> dcm_stats:
         return dcm_get_stats(self.h)
 
-    def set_tuning(self, lanes, block=256):
-        dcm_set_tuning(self.h, lanes, block)
+    def set_tuning(self, lanes, block=256, walk=None):
+        """lanes/block select the lanes walk unless walk=DCM_WALK_WARP"""
+        dcm_set_tuning(self.h, lanes, block, walk)
 
     def sync(self):
         dcm_sync(self.h)

@@ -260,7 +260,8 @@ class DcmBackend(Backend):
         stream = self.torch.cuda.Stream()
         sy = self.dcm.System(job.box, job.n, self._params(job), stream=stream.cuda_stream)
         if self.tune:
-            sy.set_tuning(self.tune.get("lanes", [2, 1, 2, 2]), self.tune.get("block", 128))
+            sy.set_tuning(self.tune.get("lanes", [2, 1, 2, 2]), self.tune.get("block", 128),
+                          self.tune.get("walk", self.dcm.DCM_WALK_WARP))
         sy.set_state(job.x, job.v)
         return {"sys": sy, "stream": stream, "events": deque()}
 

@@ -45,12 +45,12 @@ def test_ensemble_members_equal_single_runs(dcm, prec):
         ens.step(12)
         ens.sync()
         got = [ens.get_system_state(k) for k in range(len(mem))]
-        lanes = list(dcm.dcm_get_tuning(ens.h).lanes)
-        block = dcm.dcm_get_tuning(ens.h).block
+        tun = dcm.dcm_get_tuning(ens.h)
+        lanes, block, walk = list(tun.lanes), tun.block, tun.walk
         e_mix = [ens.system_energy(k) for k in range(len(mem))]
     for k, (s, rcmax) in enumerate(mem):
         with dcm.System(s.box, len(s.x), dcm.default_params(precision=prec, rc_max=rcmax)) as one:
-            one.set_tuning(lanes, block)
+            one.set_tuning(lanes, block, walk)
             one.set_state(s.x, s.v)
             one.step(12)
             one.sync()

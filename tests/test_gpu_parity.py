@@ -73,9 +73,11 @@ def test_detection_parity(dcm, orc, n, seed, rc):
     assert st.cfsm_iters > 0 and st.kmeans_iters > 0
 
 
-def _force_check(dcm, orc, s, prec, rc_pair=(3.0, 6.0)):
+def _force_check(dcm, orc, s, prec, rc_pair=(3.0, 6.0), walk=None, **kw):
     n = len(s.x)
-    with dcm.System(s.box, n, precision=prec, rc_min=rc_pair[0], rc_max=rc_pair[1]) as sy:
+    with dcm.System(s.box, n, precision=prec, rc_min=rc_pair[0], rc_max=rc_pair[1], **kw) as sy:
+        if walk is not None:
+            sy.set_tuning([2, 1, 2, 2], 128, walk)
         sy.set_state(s.x, s.v)
         sy.detect_interface()
         sy.compute_forces()
@@ -101,10 +103,18 @@ def test_forces_fp64(dcm, orc, n, seed):
     np.testing.assert_allclose(w, ref.vir, rtol=1e-9, atol=1e-8)
 
 
-@pytest.mark.parametrize("n,seed", [(16000, 7), (3333, 8)])
-def test_forces_mixed(dcm, orc, n, seed):
+@pytest.mark.parametrize("walk", ["warp", "lanes"])
+@pytest.mark.parametrize("n,seed,rc_pair,cell", [(16000, 7, (3.0, 6.0), None),
+                                                 (3333, 8, (3.0, 6.0), None),
+                                                 (6000, 11, (3.0, 7.0), 1.0)])
+def test_forces_mixed(dcm, orc, n, seed, rc_pair, cell, walk):
+    # the last case: 1-sigma cells and r_c,max = 7 give up to 225 stencil rows,
+    # more than one row table of the warp walk, and wrapped rows in a small box
     s = slabgen.make_slab(n, seed=seed)
-    err, fmag, ref, (pe, ke, w), x, rc = _force_check(dcm, orc, s, dcm.DCM_MIXED)
+    kw = {} if cell is None else {"cell_min": cell}
+    w_sel = dcm.DCM_WALK_WARP if walk == "warp" else dcm.DCM_WALK_LANES
+    err, fmag, ref, (pe, ke, w), x, rc = _force_check(dcm, orc, s, dcm.DCM_MIXED, rc_pair,
+                                                      walk=w_sel, **kw)
     # bound: FP64 tolerance + MIX_COND * (the largest pair force scale); the
     # per-pair scale is bounded by |F| + 24 * (number of close pairs)
     rel = err / np.maximum(fmag, 1e-12)
@@ -113,6 +123,7 @@ def test_forces_mixed(dcm, orc, n, seed):
     assert np.all(err <= FP64_ABS + FP64_REL * fmag + 5e-4), err.max()
     assert np.percentile(rel, 50) < 1e-5
     assert pe == pytest.approx(ref.pe.sum(), rel=1e-5)
+    np.testing.assert_allclose(w, ref.vir, rtol=1e-4, atol=1e-2)
 
 
 def test_static_limit_newton3(dcm, orc):
