@@ -12,6 +12,20 @@ same system and reported beside it.
 
 One JSON line on stdout (rank 0).  ``--impl reference`` times the FP64 CPU
 oracle instead, on the host cores, on a bounded sample of the workload.
+
+Other workloads (one GPU, one JSON line each; not the default):
+  --workload wavy      N = 2,097,152 slab whose two interfaces carry
+                       capillary-wave-like sinusoidal z offsets (amplitude
+                       1 sigma, random phases), r_c 3/7, mixed precision,
+                       200 steps, plus a weak-scaling sweep in N (--sweep)
+  --workload ensemble  64 independent slabs, N log-uniform in [4096, 131072],
+                       T* uniform in [0.65, 0.85], one handle (one persistent
+                       force launch per step, the step a CUDA graph), launch
+                       shape tuned on the live ensemble, 500 steps
+  --workload serving   Poisson request stream (20 req/s), N log-uniform in
+                       [2048, 524288], nsteps uniform in [100, 2000], HBM
+                       budget 120 GB, continuous batching: p50/p99 latency
+                       and aggregate atom-steps/s
 """
 from __future__ import annotations
 
@@ -34,14 +48,15 @@ N_DEFAULT = 262144
 FP32_LANES_PER_SM = 128          # Blackwell SM: 4 sub-partitions x 32 FP32 lanes
 FLOPS_PER_PAIR = 24              # 8 (distance test) + 16 (LJ force), per in-cutoff pair
 # DRAM bytes (read + write) per force launch from the committed ncu capture
-# (profiles/k_force_N262144_mixed.md); None once the kernel changes
-FORCE_TRAFFIC = {"mixed": 10.73e6, "fp64": None}
+# (profiles/k_force_warp_N262144_mixed.md); None once the kernel changes
+FORCE_TRAFFIC = {"mixed": 14.96e6, "fp64": None}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 1000; wavy 200; ensemble 500)")
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="dcm", choices=["dcm", "reference"])
     ap.add_argument("--n", type=int, default=N_DEFAULT)
@@ -49,7 +64,15 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
-    return ap.parse_args()
+    ap.add_argument("--workload", default="slab", choices=["slab", "wavy", "ensemble", "serving"])
+    ap.add_argument("--sweep", default="131072,262144,524288,1048576",
+                    help="wavy: further N of the weak-scaling sweep")
+    ap.add_argument("--sweep-steps", type=int, default=40)
+    ap.add_argument("--requests", type=int, default=120, help="serving: trace length")
+    a = ap.parse_args()
+    if a.steps is None:
+        a.steps = {"slab": 1000, "wavy": 200, "ensemble": 500, "serving": 0}[a.workload]
+    return a
 
 
 def workload_config(n, precision):
@@ -176,11 +199,148 @@ def run_reference(args):
     return 0
 
 
+
+# ---- further workloads (one GPU) -------------------------------------------------------
+def _timed(sy, stream, flush, k, warm):
+    """per-step device times (ms) with L2 flushed before each step, and the
+    per-phase sums of the library's own step events"""
+    import torch
+
+    for _ in range(warm):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        sy.step(1)
+    sy.sync()
+    out, phase = [], {}
+    for _ in range(k):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            e0.record(stream)
+        sy.step(1)
+        with torch.cuda.stream(stream):
+            e1.record(stream)
+        for key, val in sy.phase_times().items():
+            phase[key] = phase.get(key, 0.0) + val / k
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return out, phase
+
+
+def _pct(v, q):
+    v = sorted(v)
+    return v[min(len(v) - 1, max(0, int(math.ceil(q / 100.0 * len(v))) - 1))]
+
+
+def run_workload(args):
+    import numpy as np
+    import torch
+
+    if int(os.environ.get("RANK", "0")) != 0:
+        return 0
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1502_03234_gb300 import autotune, dcm, serving, slabgen
+
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    line = {"n_gpus": 1, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32-pair/f64-state", "data": "synthetic",
+            "unit": UNIT}
+    with Clocks(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        if args.workload == "wavy":
+            def wavy(n, steps, warm):
+                s = slabgen.make_slab(n, seed=3, capillary_amp=1.0)
+                sy = dcm.System(s.box, n, precision=dcm.DCM_MIXED, rc_min=3.0, rc_max=7.0,
+                                stream=stream.cuda_stream)
+                sy.set_state(s.x, s.v)
+                sy.compute_forces()
+                sy.set_timing(True)
+                ms, ph = _timed(sy, stream, flush, steps, warm)
+                st = sy.stats()
+                x, _, _ = sy.get_state()
+                sy.close()
+                if not np.all(np.isfinite(x)):
+                    raise RuntimeError("non-finite positions")
+                return n * steps / (sum(ms) * 1e-3), ms, ph, st
+
+            n = 2097152
+            value, ms, ph, st = wavy(n, args.steps, args.warmup)
+            sweep = {}
+            for nn in [int(q) for q in args.sweep.split(",") if q]:
+                sweep[str(nn)] = wavy(nn, args.sweep_steps, 3)[0]
+            sweep[str(n)] = value
+            line.update({
+                "metric": "atom-steps/s of the DCM step, capillary-wave slab", "value": value,
+                "steps": args.steps, "ms_per_step": sum(ms) / len(ms),
+                "config": {"workload": f"LJ slab N={n}, L x L x 4L periodic, two interfaces "
+                                       f"with sinusoidal z offsets (amplitude 1 sigma, random "
+                                       f"phases), DCM r_c 3/7, 1-sigma voxels, detection every "
+                                       f"2 steps, mixed precision",
+                           "n": n, "rc_min": 3.0, "rc_max": 7.0, "phase_ms_avg": ph,
+                           "pairs_per_particle": st.pairs / n,
+                           "l2": "flushed (256 MiB write) before every timed step"},
+                "latency_ms": {"p50": _pct(ms, 50), "p99": _pct(ms, 99), "unit": "ms per step"},
+                "weak_scaling_in_n": {"unit": UNIT, "steps": args.sweep_steps, "values": sweep}})
+        elif args.workload == "ensemble":
+            mem = slabgen.make_ensemble(64, 4096, 131072, 0.65, 0.85, seed=0)
+            boxes = [m.slab.box for m in mem]
+            ns = [m.n for m in mem]
+            params = [dcm.default_params(precision=dcm.DCM_MIXED) for _ in mem]
+            ens = dcm.Ensemble(boxes, ns, params, stream=stream.cuda_stream)
+            for k, m in enumerate(mem):
+                ens.set_system_state(k, m.slab.x, m.slab.v)
+            ens.compute_forces()
+            choice = autotune.tune_live(ens)
+            ens.set_timing(True)
+            ms, ph = _timed(ens, stream, flush, args.steps, args.warmup)
+            st = ens.stats()
+            kernels = st.kernels_plain * (args.steps - args.steps // 2) + \
+                st.kernels_detect * (args.steps // 2)
+            ens.close()
+            ntot = sum(ns)
+            value = ntot * args.steps / (sum(ms) * 1e-3)
+            line.update({
+                "metric": "atom-steps/s of the DCM step, batched ensemble", "value": value,
+                "steps": args.steps, "ms_per_step": sum(ms) / len(ms),
+                "config": {"workload": "64 independent LJ slabs in one handle, N log-uniform in "
+                                       "[4096, 131072], T* uniform in [0.65, 0.85], own boxes, "
+                                       "DCM r_c 3/6, mixed precision; one persistent force "
+                                       "launch per step, each step one CUDA graph",
+                           "systems": len(ns), "n_total": ntot, "n_min": min(ns),
+                           "n_max": max(ns), "phase_ms_avg": ph, "tuning": choice,
+                           "l2": "flushed (256 MiB write) before every timed step"},
+                "latency_ms": {"p50": _pct(ms, 50), "p99": _pct(ms, 99), "unit": "ms per step"},
+                "gpu_launches": int(kernels)})
+        else:
+            rep = serving.serve_trace(count=args.requests, rate=20.0, n_min=2048, n_max=524288,
+                                      steps_min=100, steps_max=2000, budget_gb=120.0,
+                                      precision=dcm.DCM_MIXED)
+            summ = rep.summary()
+            line.update({
+                "metric": "aggregate atom-steps/s of a served request stream; p50/p99 latency",
+                "value": summ["atom_steps_per_s"], "steps": None, "ms_per_step": None,
+                "config": {"workload": f"Poisson stream of {args.requests} slab requests at 20 "
+                                       f"req/s, N log-uniform in [2048, 524288], nsteps uniform "
+                                       f"in [100, 2000], 120 GB HBM budget, continuous batching "
+                                       f"(up to 16 resident slots, 50-step chunks), mixed "
+                                       f"precision", "requests": args.requests},
+                "latency_s": summ["latency_s"], "serving": summ})
+    line["clocks"] = clk.summary()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ---- the GPU arm ---------------------------------------------------------------------
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "slab":
+        return run_workload(args)
 
     import numpy as np
     import torch
@@ -276,7 +436,7 @@ def main():
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
                 "traffic": FORCE_TRAFFIC.get(args.precision) if n == N_DEFAULT else None,
-                "kernel": "k_force (mixed)" if prec == dcm.DCM_MIXED else "k_force (fp64)",
+                "kernel": "k_force_warp (mixed)" if prec == dcm.DCM_MIXED else "k_force (fp64)",
                 "peak_note": "FP32 FMA peak derived from 152 SMs x 128 lanes x 2 flops x the "
                              "median SM clock sampled during the timed region",
                 "pairs_per_launch": pairs, "force_ms_avg": f_avg_ms}

@@ -124,6 +124,34 @@ def tune(box, x, v, params: dcm.dcm_params, *, reps: int = 5, stream=None,
     return best
 
 
+# launch shapes tried on a live handle (cell edge fixed at creation)
+LIVE_CANDIDATES = (
+    {"walk": dcm.DCM_WALK_WARP, "lanes": [1], "block": 128},
+    {"walk": dcm.DCM_WALK_LANES, "lanes": [2, 1, 2, 2], "block": 128},
+    {"walk": dcm.DCM_WALK_LANES, "lanes": [2, 2, 4, 4], "block": 128},
+    {"walk": dcm.DCM_WALK_LANES, "lanes": [4, 4, 8, 8], "block": 256},
+)
+
+
+def tune_live(sy: dcm.System, *, reps: int = 5, candidates=LIVE_CANDIDATES, log=None) -> dict:
+    """Time each launch shape on a live handle (a System or an Ensemble: the
+    ensemble's one persistent force launch covers every member), keep the
+    fastest and leave it set.  Returns the choice with its force time."""
+    best = None
+    for c in candidates:
+        try:
+            sy.set_tuning(c["lanes"], c["block"], c["walk"])
+        except dcm.DcmError:
+            continue
+        t = force_ms(sy, reps)
+        if log:
+            log(f"walk {c['walk']} lanes {c['lanes']} block {c['block']}: force {t:.4f} ms")
+        if best is None or t < best["force_ms"]:
+            best = dict(c, force_ms=t)
+    sy.set_tuning(best["lanes"], best["block"], best["walk"])
+    return best
+
+
 def tuned_system(box, x, v, params: dcm.dcm_params, *, stream=None, cache_path: str = CACHE,
                  retune: bool = False, log=None) -> tuple[dcm.System, Tuning]:
     """A system built with the cached (or freshly tuned) launch shape."""
