@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--skin", type=float, default=0.5,
+                    help="Verlet-list skin in sigma (0: direct link-cell walk every step)")
     ap.add_argument("--workload", default="slab", choices=["slab", "wavy", "ensemble", "serving"])
     ap.add_argument("--sweep", default="131072,262144,524288,1048576",
                     help="wavy: further N of the weak-scaling sweep")
@@ -81,6 +83,15 @@ def workload_config(n, precision):
             "n": n, "rc_min": 3.0, "rc_max": 6.0, "detect_every": 2, "dt": 0.005,
             "precision": precision,
             "l2": "flushed (256 MiB write) before every timed step; each step timed alone"}
+
+
+def force_kernel_name(dcm, sy, prec, skin):
+    if prec != dcm.DCM_MIXED:
+        return "k_force (fp64)"
+    walk = dcm.dcm_get_tuning(sy.h).walk
+    if walk != dcm.DCM_WALK_WARP:
+        return "k_force lanes walk (mixed)"
+    return "k_force_list_warp + k_force_warp (mixed, Verlet lists)" if skin > 0 else "k_force_warp (mixed)"
 
 
 # ---- clocks sampled during the timed region ------------------------------------
@@ -255,7 +266,7 @@ def run_workload(args):
             def wavy(n, steps, warm):
                 s = slabgen.make_slab(n, seed=3, capillary_amp=1.0)
                 sy = dcm.System(s.box, n, precision=dcm.DCM_MIXED, rc_min=3.0, rc_max=7.0,
-                                stream=stream.cuda_stream)
+                                skin=args.skin, stream=stream.cuda_stream)
                 sy.set_state(s.x, s.v)
                 sy.compute_forces()
                 sy.set_timing(True)
@@ -280,7 +291,8 @@ def run_workload(args):
                                        f"with sinusoidal z offsets (amplitude 1 sigma, random "
                                        f"phases), DCM r_c 3/7, 1-sigma voxels, detection every "
                                        f"2 steps, mixed precision",
-                           "n": n, "rc_min": 3.0, "rc_max": 7.0, "phase_ms_avg": ph,
+                           "n": n, "rc_min": 3.0, "rc_max": 7.0, "skin": args.skin,
+                           "phase_ms_avg": ph,
                            "pairs_per_particle": st.pairs / n,
                            "l2": "flushed (256 MiB write) before every timed step"},
                 "latency_ms": {"p50": _pct(ms, 50), "p99": _pct(ms, 99), "unit": "ms per step"},
@@ -289,7 +301,7 @@ def run_workload(args):
             mem = slabgen.make_ensemble(64, 4096, 131072, 0.65, 0.85, seed=0)
             boxes = [m.slab.box for m in mem]
             ns = [m.n for m in mem]
-            params = [dcm.default_params(precision=dcm.DCM_MIXED) for _ in mem]
+            params = [dcm.default_params(precision=dcm.DCM_MIXED, skin=args.skin) for _ in mem]
             ens = dcm.Ensemble(boxes, ns, params, stream=stream.cuda_stream)
             for k, m in enumerate(mem):
                 ens.set_system_state(k, m.slab.x, m.slab.v)
@@ -310,7 +322,7 @@ def run_workload(args):
                                        "[4096, 131072], T* uniform in [0.65, 0.85], own boxes, "
                                        "DCM r_c 3/6, mixed precision; one persistent force "
                                        "launch per step, each step one CUDA graph",
-                           "systems": len(ns), "n_total": ntot, "n_min": min(ns),
+                           "systems": len(ns), "n_total": ntot, "n_min": min(ns), "skin": args.skin,
                            "n_max": max(ns), "phase_ms_avg": ph, "tuning": choice,
                            "l2": "flushed (256 MiB write) before every timed step"},
                 "latency_ms": {"p50": _pct(ms, 50), "p99": _pct(ms, 99), "unit": "ms per step"},
@@ -318,7 +330,7 @@ def run_workload(args):
         else:
             rep = serving.serve_trace(count=args.requests, rate=20.0, n_min=2048, n_max=524288,
                                       steps_min=100, steps_max=2000, budget_gb=120.0,
-                                      precision=dcm.DCM_MIXED)
+                                      precision=dcm.DCM_MIXED, skin=args.skin)
             summ = rep.summary()
             line.update({
                 "metric": "aggregate atom-steps/s of a served request stream; p50/p99 latency",
@@ -327,7 +339,7 @@ def run_workload(args):
                                        f"req/s, N log-uniform in [2048, 524288], nsteps uniform "
                                        f"in [100, 2000], 120 GB HBM budget, continuous batching "
                                        f"(up to 16 resident slots, 50-step chunks), mixed "
-                                       f"precision", "requests": args.requests},
+                                       f"precision", "requests": args.requests, "skin": args.skin},
                 "latency_s": summ["latency_s"], "serving": summ})
     line["clocks"] = clk.summary()
     print(json.dumps(line), flush=True)
@@ -371,7 +383,8 @@ def main():
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
     def make_system(precision):
-        sy = dcm.System(slab.box, n, precision=precision, stream=stream.cuda_stream)
+        sy = dcm.System(slab.box, n, precision=precision, stream=stream.cuda_stream,
+                        skin=args.skin)
         sy.set_state(slab.x, slab.v)
         sy.compute_forces()
         sy.set_timing(True)
@@ -435,8 +448,9 @@ def main():
     peak = 152 * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
-                "traffic": FORCE_TRAFFIC.get(args.precision) if n == N_DEFAULT else None,
-                "kernel": "k_force_warp (mixed)" if prec == dcm.DCM_MIXED else "k_force (fp64)",
+                "traffic": (FORCE_TRAFFIC.get(args.precision)
+                            if n == N_DEFAULT and args.skin == 0 else None),
+                "kernel": force_kernel_name(dcm, sy, prec, args.skin),
                 "peak_note": "FP32 FMA peak derived from 152 SMs x 128 lanes x 2 flops x the "
                              "median SM clock sampled during the timed region",
                 "pairs_per_launch": pairs, "force_ms_avg": f_avg_ms}
@@ -494,6 +508,7 @@ def main():
         p50 = sms[len(sms) // 2]
         p99 = sms[min(len(sms) - 1, int(math.ceil(0.99 * len(sms))) - 1)]
         cfg = workload_config(n, args.precision)
+        cfg["skin"] = args.skin
         cfg["phase_ms_avg"] = {k: v / args.steps for k, v in phase_sum.items()}
         cfg["fp64_gpu_path"] = fp64_info
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,

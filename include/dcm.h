@@ -94,7 +94,13 @@ typedef struct {
        at most 2^24 particles per handle and a stencil of at most 7 cells
        in y and z. */
     double skin;
-    int32_t reserved[6];
+    /* Verlet lists built by the warp walk (DCM_MIXED, DCM_WALK_WARP): each
+       particle's entry capacity is list_density x (4/3) pi R^3 + 8 for its
+       list radius R; <= 0: 1.0 per sigma^3.  A list that would overflow
+       leaves that step's forces to the direct walk and raises the density
+       by 25 % for the next build (per handle: system 0's value). */
+    float list_density;
+    int32_t reserved[5];
 } dcm_params;
 
 /* Force walk variants (dcm_tuning.walk).  DCM_WALK_WARP: one warp per
@@ -109,7 +115,9 @@ typedef struct {
     int32_t lanes[DCM_MAX_CLASSES];        /* lanes per particle: 1..32, pow2 */
     int32_t block;                         /* threads per block: 64..256 */
     int32_t walk;                          /* DCM_WALK_WARP (default) or DCM_WALK_LANES */
-    int32_t reserved[6];
+    int32_t list_lanes;                    /* warp walk + Verlet lists: lanes per particle of
+                                              the list force, 4, 8, 16 or 32 (0: 8) */
+    int32_t reserved[5];
 } dcm_tuning;
 
 typedef struct {

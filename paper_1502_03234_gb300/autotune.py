@@ -134,13 +134,15 @@ LIVE_CANDIDATES = (
 
 
 def tune_live(sy: dcm.System, *, reps: int = 5, candidates=LIVE_CANDIDATES, log=None) -> dict:
+    # (with Verlet lists, add list_lanes to a candidate to choose the lanes
+    # per particle of the list force)
     """Time each launch shape on a live handle (a System or an Ensemble: the
     ensemble's one persistent force launch covers every member), keep the
     fastest and leave it set.  Returns the choice with its force time."""
     best = None
     for c in candidates:
         try:
-            sy.set_tuning(c["lanes"], c["block"], c["walk"])
+            sy.set_tuning(c["lanes"], c["block"], c["walk"], c.get("list_lanes", 8))
         except dcm.DcmError:
             continue
         t = force_ms(sy, reps)
@@ -148,7 +150,7 @@ def tune_live(sy: dcm.System, *, reps: int = 5, candidates=LIVE_CANDIDATES, log=
             log(f"walk {c['walk']} lanes {c['lanes']} block {c['block']}: force {t:.4f} ms")
         if best is None or t < best["force_ms"]:
             best = dict(c, force_ms=t)
-    sy.set_tuning(best["lanes"], best["block"], best["walk"])
+    sy.set_tuning(best["lanes"], best["block"], best["walk"], best.get("list_lanes", 8))
     return best
 
 

@@ -84,6 +84,7 @@ extern "C" void dcm_default_params(dcm_params *p)
     p->detect_every = 2;
     p->kmeans_max_iter = 100;
     p->cfsm_iter_max = 0;
+    p->list_density = 1.0f;
     p->cfsm_eps = 0.0;
     p->precision = DCM_FP64;
     p->n_classes = 4;
@@ -321,6 +322,7 @@ static int create_systems(int M, const dcm_box *boxes, const int64_t *ns, const 
     for (int q = 0; q < DCM_MAX_CLASSES; ++q) h->tune.lanes[q] = q == 0 ? 2 : (q == 1 ? 1 : 2);
     h->tune.block = 128;
     h->tune.walk = DCM_WALK_WARP;
+    h->tune.list_lanes = 8;
     cudaGetDevice(&h->device);
     cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
     if (stream) {
@@ -431,6 +433,11 @@ static int create_systems(int M, const dcm_box *boxes, const int64_t *ns, const 
     if (h->nl) {
         cudaMemsetAsync(h->lflags, 0, sizeof(int) * LF_WORDS, h->stream);
         cudaMemsetAsync(h->lflags + LF_MINHEAD, 0x7f, sizeof(int), h->stream);   // ~3.4e38
+        // capacity density of the warp list fill (float bits); a host member
+        // so the asynchronous copy reads live memory
+        h->list_scale0 = h->par_host[0].list_density > 0.f ? h->par_host[0].list_density : 1.0f;
+        cudaMemcpyAsync(h->lflags + LF_SCALE, &h->list_scale0, sizeof(float), cudaMemcpyHostToDevice,
+                        h->stream);
         cudaMemsetAsync(h->x_ref, 0, sizeof(double) * 3 * N, h->stream);
         cudaMemsetAsync(h->rl_ref, 0, sizeof(float) * N, h->stream);
     }
@@ -869,6 +876,9 @@ extern "C" int dcm_set_tuning(dcm_handle *h, const dcm_tuning *t)
         return fail(DCM_ERR_ARG, "block must be a multiple of 32 in 64..256");
     if (t->walk != DCM_WALK_WARP && t->walk != DCM_WALK_LANES)
         return fail(DCM_ERR_ARG, "walk must be DCM_WALK_WARP or DCM_WALK_LANES");
+    if (t->list_lanes != 0 && t->list_lanes != 4 && t->list_lanes != 8 && t->list_lanes != 16 &&
+        t->list_lanes != 32)
+        return fail(DCM_ERR_ARG, "list_lanes must be 4, 8, 16 or 32 (0: 8)");
     h->tune = *t;
     invalidate_graphs(h);
     return DCM_OK;

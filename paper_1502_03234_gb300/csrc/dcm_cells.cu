@@ -126,7 +126,8 @@ __global__ void k_cell_sort(int64_t ncell, const int32_t *__restrict__ start, in
 // spd = absolute FP64 position (FP64 path only)
 __global__ void k_gather(Batch b, const double *__restrict__ x, const int32_t *__restrict__ sorted_id,
                          const int32_t *__restrict__ cell_of, float4 *sp4, double4_32a *spd,
-                         const double *__restrict__ rc, float4 *rq, int4 *pk)
+                         const double *__restrict__ rc, float4 *rq, int4 *pk,
+                         const double *__restrict__ dist, const int *lf, float delta, int32_t *capk)
 {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= b.N) return;
@@ -158,7 +159,17 @@ __global__ void k_gather(Batch b, const double *__restrict__ x, const int32_t *_
         float rc2f = (float)DMUL(r, r);
         rq[k] = make_float4(rc2f, rc2f * (1.f - 3.814697265625e-06f), rc2f * (1.f + 3.814697265625e-06f),
                             (float)r * 1.00002f + 1e-4f);
-        pk[k] = make_int4(i, cy, cz, 0);
+        int w = 0;
+        if (capk && lf[LF_REBUILD]) {
+            // a Verlet-list build follows: list radius and the entry
+            // capacity of this particle, (4/3) pi R^3 at the density bound
+            // scale (1.0 sigma^-3 unless a list overflowed before) + 8
+            float rl = list_radius(g, r, dist[i], delta);
+            float scale = __int_as_float(lf[LF_SCALE]);
+            capk[k] = (int32_t)ceilf(scale * 4.18879020f * rl * rl * rl) + 8;
+            w = __float_as_int(rl);
+        }
+        pk[k] = make_int4(i, cy, cz, w);
     }
 }
 
@@ -231,9 +242,11 @@ int launch_bin_gated(dcm_handle *h, const int *gate)
     k_cell_scatter<<<nblk(n, 256), 256, 0, s>>>(n, h->cell_of, h->slot, h->cell_start,
                                                 h->sorted_id, gate);
     k_cell_sort<<<nblk(h->ncell, 256), 256, 0, s>>>(h->ncell, h->cell_start, h->sorted_id, gate);
+    const bool wl = h->nl && h->list_warp;
     k_gather<<<nblk(n, 256), 256, 0, s>>>(h->b, h->x, h->sorted_id, h->cell_of, h->sp4,
                                           h->p.precision == DCM_FP64 ? h->spd : nullptr, h->rc,
-                                          h->rq, h->pk);
+                                          h->rq, h->pk, h->d, h->lflags,
+                                          h->cut_detected ? 1.0f : 0.0f, wl ? h->nl_cnt : nullptr);
     // class lists of sorted slots for the per-class force launches
     int K = h->b.K;
     cudaMemsetAsync(h->class_count_dev, 0, sizeof(int32_t) * 3 * DCM_MAX_CLASSES, s);

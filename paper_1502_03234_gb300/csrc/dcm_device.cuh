@@ -199,4 +199,21 @@ __device__ __forceinline__ double lerp_rn(double a, double b, double t)
     return DADD(a, DMUL(t, DSUB(b, a)));
 }
 
+// Verlet-list radius of particle i: the cutoff it would get if its distance
+// to the interface dropped by delta (so small moves of the detected interface
+// do not force a rebuild), never below its current cutoff, plus the skin
+__device__ __forceinline__ float list_radius(const Geom &g, double rci, double di, float delta)
+{
+    float r = (float)rci;
+    if (delta > 0.f && g.rc_max > g.rc_min) {
+        float dd = fmaxf((float)di - delta, 0.f);
+        float rmax = (float)g.rc_max, rmin = (float)g.rc_min;
+        float ra = dd <= 0.f ? rmax
+                 : (dd >= rmax ? rmin
+                               : fmaf((float)g.cut_a, exp2f((float)g.alpha * (rmax - dd)), (float)g.cut_b));
+        r = fmaxf(r, ra);
+    }
+    return r * 1.00001f + (float)g.skin + 1e-4f;
+}
+
 }  // namespace dcm

@@ -54,6 +54,8 @@ struct ForceArgs {
     double *pe, *vir;
     unsigned int *queue;          // work counter
     unsigned long long *guard_count;
+    unsigned long long *list_entries;
+    int *list_flags;              // LF_* words (Verlet lists)
     // Verlet lists (skin > 0): used while *list_ok
     const int *list_ok;
     const int32_t *nl_start;
@@ -75,6 +77,14 @@ __device__ __forceinline__ bool fp64_inside(const ForceArgs &a, const Geom &g, i
     double dy = min_image(DSUB(a.x[n + i], a.x[n + j]), g.L[1], g.halfL[1]);
     double dz = min_image(DSUB(a.x[2 * n + i], a.x[2 * n + j]), g.L[2], g.halfL[2]);
     return r2_rn(dx, dy, dz) < rci2;
+}
+
+// the same decision out of line, for kernels that keep registers for the
+// common path (it runs for ~1e-4 of the candidates)
+__device__ __noinline__ bool fp64_inside_rc(const ForceArgs &a, const Geom &g, int i, int j)
+{
+    double rci = a.rc[i];
+    return fp64_inside(a, g, i, a.sorted_id[j], DMUL(rci, rci));
 }
 
 template <int PREC, bool ENERGY>
@@ -409,23 +419,6 @@ __device__ __forceinline__ void particle_force_list(const ForceArgs &a, int k, i
     reduce_and_store<PREC, ENERGY>(a, acc, i, lane, G, gmask, np);
 }
 
-// Verlet-list radius of particle i: the cutoff it would get if its distance
-// to the interface dropped by delta (so small moves of the detected interface
-// do not force a rebuild), never below its current cutoff, plus the skin
-__device__ __forceinline__ float list_radius(const Geom &g, double rci, double di, float delta)
-{
-    float r = (float)rci;
-    if (delta > 0.f && g.rc_max > g.rc_min) {
-        float dd = fmaxf((float)di - delta, 0.f);
-        float rmax = (float)g.rc_max, rmin = (float)g.rc_min;
-        float ra = dd <= 0.f ? rmax
-                 : (dd >= rmax ? rmin
-                               : fmaf((float)g.cut_a, exp2f((float)g.alpha * (rmax - dd)), (float)g.cut_b));
-        r = fmaxf(r, ra);
-    }
-    return r * 1.00001f + (float)g.skin + 1e-4f;
-}
-
 // one particle of the list build: the direct row walk with radius
 // list_radius; COUNT stores the number of entries, FILL writes them in
 // walk order (a ballot over the G lanes keeps the order)
@@ -652,12 +645,14 @@ constexpr int FW_THREADS = 128;
 constexpr int FW_WARPS = FW_THREADS / 32;
 constexpr int FW_ROWS = 128;                 // row table entries per warp
 constexpr int FW_GRAB = 4;                   // particles per queue grab
+constexpr int FW_LIST_G = 8;                 // lanes per particle of the list kernel
 constexpr float FW_FIX_LIMIT = 65536.f;      // |partial| bound of the exact sum
 
 struct FwTable {
     int4 ri[FW_ROWS];        // list offset P, main start, main length, wrapped start
     float4 rf[FW_ROWS];      // x cell shift (main, wrapped), row y, row z
     int rp[FW_ROWS];         // P again, read conflict-free by the row search
+    int rt[FW_ROWS];         // Verlet-list tag of the row: (dy + 8) << 24 | (dz + 8) << 28
 };
 
 // Exact warp sum of FP32 partials whose magnitude is below FW_FIX_LIMIT, as
@@ -693,9 +688,94 @@ __device__ __forceinline__ double warp_tree_sum(float p)
     return d;
 }
 
+// lane partials of one particle: pair force, pair count, PE, virial
 template <bool ENERGY>
+struct WarpAcc {
+    float fx = 0.f, fy = 0.f, fz = 0.f, pe = 0.f;
+    float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f, v4 = 0.f, v5 = 0.f;
+    int np = 0;
+
+    // one candidate (dx, dy, dz) = r_i - r_j with in = "inside r_c[i]"
+    __device__ __forceinline__ void pair(const Geom &g, float dx, float dy, float dz, float r2,
+                                         bool in)
+    {
+        float r2inv = rcp_approx(r2);
+        float sr2 = g.sig2f * r2inv;
+        float sr6 = sr2 * sr2 * sr2;
+        float fr = r2inv * sr6 * fmaf(g.eps48f, sr6, -g.eps24f);
+        fr = in ? fr : 0.f;
+        fx = fmaf(fr, dx, fx);
+        fy = fmaf(fr, dy, fy);
+        fz = fmaf(fr, dz, fz);
+        np += in ? 1 : 0;
+        if constexpr (ENERGY) {
+            pe += in ? g.eps2f * sr6 * (sr6 - 1.f) : 0.f;
+            float gx = fr * dx, gy = fr * dy, gz = fr * dz;
+            v0 = fmaf(0.5f * dx, gx, v0);
+            v1 = fmaf(0.5f * dy, gy, v1);
+            v2 = fmaf(0.5f * dz, gz, v2);
+            v3 = fmaf(0.5f * dx, gy, v3);
+            v4 = fmaf(0.5f * dx, gz, v4);
+            v5 = fmaf(0.5f * dy, gz, v5);
+        }
+    }
+
+    // sum the lane partials and store particle i's results; lane q writes value q
+    __device__ __forceinline__ void store(const ForceArgs &a, int i, int lane)
+    {
+        bool small = fabsf(fx) < FW_FIX_LIMIT && fabsf(fy) < FW_FIX_LIMIT && fabsf(fz) < FW_FIX_LIMIT;
+        if constexpr (ENERGY)
+            small = small && fabsf(pe) < FW_FIX_LIMIT && fabsf(v0) < FW_FIX_LIMIT &&
+                    fabsf(v1) < FW_FIX_LIMIT && fabsf(v2) < FW_FIX_LIMIT &&
+                    fabsf(v3) < FW_FIX_LIMIT && fabsf(v4) < FW_FIX_LIMIT && fabsf(v5) < FW_FIX_LIMIT;
+        const size_t n = (size_t)a.b.N;
+        const int npt = __reduce_add_sync(0xffffffffu, np);
+        if (lane == 3) a.npair[i] = npt;
+        if (__all_sync(0xffffffffu, small)) {
+            long long V = 0, t;
+            t = warp_fixed_sum(fx); V = lane == 0 ? t : V;
+            t = warp_fixed_sum(fy); V = lane == 1 ? t : V;
+            t = warp_fixed_sum(fz); V = lane == 2 ? t : V;
+            if constexpr (ENERGY) {
+                t = warp_fixed_sum(pe); V = lane == 4 ? t : V;
+                t = warp_fixed_sum(v0); V = lane == 5 ? t : V;
+                t = warp_fixed_sum(v1); V = lane == 6 ? t : V;
+                t = warp_fixed_sum(v2); V = lane == 7 ? t : V;
+                t = warp_fixed_sum(v3); V = lane == 8 ? t : V;
+                t = warp_fixed_sum(v4); V = lane == 9 ? t : V;
+                t = warp_fixed_sum(v5); V = lane == 10 ? t : V;
+            }
+            const double out = fixed_to_double(V);
+            if (lane < 3) a.f[lane * n + i] = out;
+            if constexpr (ENERGY) {
+                if (lane == 4) a.pe[i] = out;
+                if (lane >= 5 && lane < 11) a.vir[(lane - 5) * n + i] = out;
+            }
+        } else {
+            // a partial beyond the fixed-point range (or not finite): FP64 tree
+            double Fx = warp_tree_sum(fx), Fy = warp_tree_sum(fy), Fz = warp_tree_sum(fz);
+            if (lane < 3) a.f[lane * n + i] = lane == 0 ? Fx : (lane == 1 ? Fy : Fz);
+            if constexpr (ENERGY) {
+                double s7[7] = {warp_tree_sum(pe), warp_tree_sum(v0), warp_tree_sum(v1),
+                                warp_tree_sum(v2), warp_tree_sum(v3), warp_tree_sum(v4),
+                                warp_tree_sum(v5)};
+                if (lane == 4) a.pe[i] = s7[0];
+#pragma unroll
+                for (int e = 0; e < 6; ++e)
+                    if (lane == 5 + e) a.vir[e * n + i] = s7[1 + e];
+            }
+        }
+    }
+};
+
+// Direct walk of particle k (sorted slot).  FILL (a Verlet-list rebuild):
+// the walk also covers the list radius R_k of the gather kernel and appends
+// every neighbour within R_k to k's list, in walk order, up to the capacity
+// the gather kernel gave it; the forces still use r_c[i] only.
+template <bool ENERGY, bool FILL>
 __device__ __forceinline__ void particle_force_warp(const ForceArgs &a, FwTable &tb, int k,
-                                                    int lane, int &ng)
+                                                    int lane, int &ng, bool fill_on,
+                                                    long long &entries)
 {
     const Geom &g = a.b.sys[sys_of(a.b.p_off, a.b.M, k)];
     const float4 ui = a.sp4[k];
@@ -703,7 +783,19 @@ __device__ __forceinline__ void particle_force_warp(const ForceArgs &a, FwTable 
     const int4 pk = a.pk[k];
     const int i = pk.x, cy = pk.y, cz = pk.z;
     const int cx = (int)ui.w;
-    const float rc2f = q4.x, rc2lo = q4.y, rc2hi = q4.z, rcull = q4.w;
+    const float rc2f = q4.x, rc2lo = q4.y, rc2hi = q4.z;
+    float rl2 = 0.f, rcull = q4.w;
+    int32_t *out = nullptr;
+    int cap = 0, cnt = 0;
+    if constexpr (FILL) {
+        if (fill_on) {
+            const float rl = __int_as_float(pk.w);
+            rl2 = rl * rl;
+            rcull = fmaxf(rcull, rl * 1.00002f + 1e-4f);
+            out = a.nl_w + a.nl_start[k];
+            cap = a.nl_cnt[k];
+        }
+    }
     const float rcull2 = rcull * rcull;
     const int sx = min(g.smax[0], (int)ceilf(rcull * g.inv_cf[0]));
     const int sy = min(g.smax[1], (int)ceilf(rcull * g.inv_cf[1]));
@@ -713,16 +805,13 @@ __device__ __forceinline__ void particle_force_warp(const ForceArgs &a, FwTable 
     const float inv_ny = rcp_approx((float)ny_);
     const int nc0 = g.nc[0];
     const float cf0 = g.cf[0];
-    const float sig2f = g.sig2f, eps48f = g.eps48f, eps24f = g.eps24f;
     const unsigned lane_le = 0xffffffffu >> (31 - lane);
-    float fx = 0.f, fy = 0.f, fz = 0.f, pe = 0.f;
-    float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f, v4 = 0.f, v5 = 0.f;
-    int np = 0;
+    WarpAcc<ENERGY> acc;
     int ntab = 0, T = 0;
     for (int r0 = 0; r0 < nrows; r0 += 32) {
         // ---- 1. one stencil row per lane
         const int r = r0 + lane;
-        int len = 0, j0a = 0, len1 = 0, j0b = 0;
+        int len = 0, j0a = 0, len1 = 0, j0b = 0, tag = 0;
         float fa = 0.f, fb = 0.f, ay = 0.f, az = 0.f;
         if (r < nrows) {
             int dzi = (int)(((float)r + 0.5f) * inv_ny);    // r / ny_ (exact for these sizes)
@@ -762,6 +851,7 @@ __device__ __forceinline__ void particle_force_warp(const ForceArgs &a, FwTable 
                 }
                 fa = (float)cx;
                 len = len1 + len2;
+                tag = (int)(((uint32_t)(dy + 8) << 24) | ((uint32_t)(dz + 8) << 28));
             }
         }
         // compact the non-empty rows into the table
@@ -778,6 +868,7 @@ __device__ __forceinline__ void particle_force_warp(const ForceArgs &a, FwTable 
             tb.ri[e] = make_int4(P, j0a, len1, j0b);
             tb.rf[e] = make_float4(fa, fb, ay, az);
             tb.rp[e] = P;
+            if constexpr (FILL) tb.rt[e] = tag;
         }
         ntab += __popc(ne);
         T += __shfl_sync(0xffffffffu, incl, 31);
@@ -792,12 +883,14 @@ __device__ __forceinline__ void particle_force_warp(const ForceArgs &a, FwTable 
             int rowi = S + __popc(M & lane_le) - 1;
             S += __popc(M);
             int p = base + lane;
+            bool hit = false;
+            int j = 0;
             if (p < T) {
                 int4 ri = tb.ri[rowi];
                 float4 rf = tb.rf[rowi];
                 int t = p - ri.x;
                 bool wr = t >= ri.z;
-                int j = wr ? ri.w + (t - ri.z) : ri.y + t;
+                j = wr ? ri.w + (t - ri.z) : ri.y + t;
                 float ax = wr ? rf.y : rf.x;
                 float4 uj = a.sp4[j];
                 float dx = fmaf(ax - uj.w, cf0, ui.x - uj.x);
@@ -810,119 +903,295 @@ __device__ __forceinline__ void particle_force_warp(const ForceArgs &a, FwTable 
                     in = fp64_inside(a, g, i, a.sorted_id[j], DMUL(rci, rci));
                     ++ng;
                 }
-                float r2inv = rcp_approx(r2);
-                float sr2 = sig2f * r2inv;
-                float sr6 = sr2 * sr2 * sr2;
-                float fr = r2inv * sr6 * fmaf(eps48f, sr6, -eps24f);
-                fr = in ? fr : 0.f;
-                fx = fmaf(fr, dx, fx);
-                fy = fmaf(fr, dy, fy);
-                fz = fmaf(fr, dz, fz);
-                np += in ? 1 : 0;
-                if constexpr (ENERGY) {
-                    pe += in ? g.eps2f * sr6 * (sr6 - 1.f) : 0.f;
-                    float gx = fr * dx, gy = fr * dy, gz = fr * dz;
-                    v0 = fmaf(0.5f * dx, gx, v0);
-                    v1 = fmaf(0.5f * dy, gy, v1);
-                    v2 = fmaf(0.5f * dz, gz, v2);
-                    v3 = fmaf(0.5f * dx, gy, v3);
-                    v4 = fmaf(0.5f * dx, gz, v4);
-                    v5 = fmaf(0.5f * dy, gz, v5);
+                acc.pair(g, dx, dy, dz, r2, in);
+                if constexpr (FILL) hit = fill_on && r2 < rl2 && j != k;
+            }
+            if constexpr (FILL) {
+                const unsigned hm = __ballot_sync(0xffffffffu, hit);
+                if (hit) {
+                    int at = cnt + __popc(hm & (lane_le >> 1));
+                    if (at < cap) out[at] = (int32_t)((uint32_t)j | (uint32_t)tb.rt[rowi]);
                 }
+                cnt += __popc(hm);
             }
         }
         __syncwarp();
         ntab = 0;
         T = 0;
     }
-    // ---- 3. sum the lane partials; lane q writes value q
-    bool small = fabsf(fx) < FW_FIX_LIMIT && fabsf(fy) < FW_FIX_LIMIT && fabsf(fz) < FW_FIX_LIMIT;
+    if constexpr (FILL) {
+        if (fill_on && lane == 0) {
+            a.nl_cnt[k] = min(cnt, cap);
+            a.rl_ref[i] = __int_as_float(pk.w);
+            if (cnt > cap) atomicOr(a.list_flags + LF_OVERFLOW, 1);
+            entries += min(cnt, cap);
+        }
+    }
+    acc.store(a, i, lane);
+}
+
+// exact sum over the G lanes of one group (G a power of two <= 32): the
+// same split into a multiple of 2^-8 and a remainder as warp_fixed_sum,
+// added by an integer butterfly inside the group
+template <int G>
+__device__ __forceinline__ long long group_fixed_sum(float p)
+{
+    int hp = __float2int_rn(p * 256.f);
+    float rem = fmaf((float)hp, -0.00390625f, p);
+    int lp = __float2int_rn(rem * 1073741824.f);
+#pragma unroll
+    for (int off = G >> 1; off > 0; off >>= 1) {
+        hp += __shfl_xor_sync(0xffffffffu, hp, off);
+        lp += __shfl_xor_sync(0xffffffffu, lp, off);
+    }
+    return (long long)hp * 4194304ll + lp;
+}
+
+template <int G>
+__device__ __forceinline__ double group_tree_sum(float p)
+{
+    double d = (double)p;
+#pragma unroll
+    for (int off = G >> 1; off > 0; off >>= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
+    return d;
+}
+
+// Particle k over its Verlet list, G lanes (one group) per particle, 32/G
+// particles per warp: the list is flat, so a group needs no row structure
+// and the per-particle work (loads, the exact sum, the stores) is shared by
+// 32/G particles per warp instruction.  Entries: j | (dy + 8) << 24 |
+// (dz + 8) << 28; the cell x offset comes from the cell x indices stored
+// with the positions (every true offset is below half the cells along x).
+// Same pair rule and FP64 re-decision as the direct walk.  k < 0: an idle
+// group (past the end of the queue).
+template <bool ENERGY, int G>
+__device__ __forceinline__ void particle_force_list_group(const ForceArgs &a, int k, int gl,
+                                                          int &ng)
+{
+    WarpAcc<ENERGY> acc;
+    int i = 0;
+    if (k >= 0) {
+        const Geom &g = a.b.sys[sys_of(a.b.p_off, a.b.M, k)];
+        const float4 ui = a.sp4[k];
+        const float4 q4 = a.rq[k];
+        i = a.pk[k].x;
+        const float rc2f = q4.x, rc2lo = q4.y, rc2hi = q4.z;
+        const float ncx = (float)g.nc[0], halfnc = 0.5f * (float)g.nc[0];
+        const float cf0 = g.cf[0], cf1 = g.cf[1], cf2 = g.cf[2];
+        const int32_t *list = a.nl + a.nl_start[k];
+        const int cnt = a.nl_cnt[k];
+        auto one = [&](int e, float4 uj) {
+            int j = e & 0xffffff;
+            float dyc = (float)(((e >> 24) & 15) - 8);
+            float dzc = (float)((int)((unsigned)e >> 28) - 8);
+            float dcx = ui.w - uj.w;
+            dcx -= dcx > halfnc ? ncx : 0.f;
+            dcx += dcx < -halfnc ? ncx : 0.f;
+            float dx = fmaf(dcx, cf0, ui.x - uj.x);
+            float dy = fmaf(-dyc, cf1, ui.y) - uj.y;
+            float dz = fmaf(-dzc, cf2, ui.z) - uj.z;
+            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            bool in = r2 < rc2f;
+            if (r2 >= rc2lo && r2 < rc2hi) {
+                double rci = a.rc[i];
+                in = fp64_inside(a, g, i, a.sorted_id[j], DMUL(rci, rci));
+                ++ng;
+            }
+            acc.pair(g, dx, dy, dz, r2, in);
+        };
+        int p = gl;
+        // two entries of the lane in flight per iteration
+        for (; p + G < cnt; p += 2 * G) {
+            int e0 = __ldcs(list + p), e1 = __ldcs(list + p + G);
+            float4 u0 = a.sp4[e0 & 0xffffff], u1 = a.sp4[e1 & 0xffffff];
+            one(e0, u0);
+            one(e1, u1);
+        }
+        if (p < cnt) {
+            int e0 = __ldcs(list + p);
+            one(e0, a.sp4[e0 & 0xffffff]);
+        }
+    }
+    // ---- sums over the group; lane q of the group writes value q
+    bool small = fabsf(acc.fx) < FW_FIX_LIMIT && fabsf(acc.fy) < FW_FIX_LIMIT &&
+                 fabsf(acc.fz) < FW_FIX_LIMIT;
     if constexpr (ENERGY)
-        small = small && fabsf(pe) < FW_FIX_LIMIT && fabsf(v0) < FW_FIX_LIMIT &&
-                fabsf(v1) < FW_FIX_LIMIT && fabsf(v2) < FW_FIX_LIMIT && fabsf(v3) < FW_FIX_LIMIT &&
-                fabsf(v4) < FW_FIX_LIMIT && fabsf(v5) < FW_FIX_LIMIT;
+        small = small && fabsf(acc.pe) < FW_FIX_LIMIT && fabsf(acc.v0) < FW_FIX_LIMIT &&
+                fabsf(acc.v1) < FW_FIX_LIMIT && fabsf(acc.v2) < FW_FIX_LIMIT &&
+                fabsf(acc.v3) < FW_FIX_LIMIT && fabsf(acc.v4) < FW_FIX_LIMIT &&
+                fabsf(acc.v5) < FW_FIX_LIMIT;
     const size_t n = (size_t)a.b.N;
-    const int npt = __reduce_add_sync(0xffffffffu, np);
-    if (lane == 3) a.npair[i] = npt;
+    int npt = acc.np;
+#pragma unroll
+    for (int off = G >> 1; off > 0; off >>= 1) npt += __shfl_xor_sync(0xffffffffu, npt, off);
     if (__all_sync(0xffffffffu, small)) {
         long long V = 0, t;
-        t = warp_fixed_sum(fx); V = lane == 0 ? t : V;
-        t = warp_fixed_sum(fy); V = lane == 1 ? t : V;
-        t = warp_fixed_sum(fz); V = lane == 2 ? t : V;
+        t = group_fixed_sum<G>(acc.fx); V = gl == 0 ? t : V;
+        t = group_fixed_sum<G>(acc.fy); V = gl == 1 ? t : V;
+        t = group_fixed_sum<G>(acc.fz); V = gl == 2 ? t : V;
         if constexpr (ENERGY) {
-            t = warp_fixed_sum(pe); V = lane == 4 ? t : V;
-            t = warp_fixed_sum(v0); V = lane == 5 ? t : V;
-            t = warp_fixed_sum(v1); V = lane == 6 ? t : V;
-            t = warp_fixed_sum(v2); V = lane == 7 ? t : V;
-            t = warp_fixed_sum(v3); V = lane == 8 ? t : V;
-            t = warp_fixed_sum(v4); V = lane == 9 ? t : V;
-            t = warp_fixed_sum(v5); V = lane == 10 ? t : V;
+            t = group_fixed_sum<G>(acc.pe); V = gl == 4 ? t : V;
+            t = group_fixed_sum<G>(acc.v0); V = gl == 5 ? t : V;
+            t = group_fixed_sum<G>(acc.v1); V = gl == 6 ? t : V;
+            t = group_fixed_sum<G>(acc.v2); V = gl == 7 ? t : V;
+            t = group_fixed_sum<G>(acc.v3); V = gl == 8 ? t : V;
+            t = group_fixed_sum<G>(acc.v4); V = gl == 9 ? t : V;
+            t = group_fixed_sum<G>(acc.v5); V = gl == 10 ? t : V;
         }
-        const double out = fixed_to_double(V);
-        if (lane < 3) a.f[lane * n + i] = out;
-        if constexpr (ENERGY) {
-            if (lane == 4) a.pe[i] = out;
-            if (lane >= 5 && lane < 11) a.vir[(lane - 5) * n + i] = out;
+        if (k >= 0) {
+            const double out = fixed_to_double(V);
+            if (gl < 3) a.f[gl * n + i] = out;
+            if (gl == 3) a.npair[i] = npt;
+            if constexpr (ENERGY) {
+                if (gl == 4) a.pe[i] = out;
+                if (gl >= 5 && gl < 11) a.vir[(gl - 5) * n + i] = out;
+            }
         }
     } else {
-        // a partial beyond the fixed-point range (or not finite): FP64 tree
-        double Fx = warp_tree_sum(fx), Fy = warp_tree_sum(fy), Fz = warp_tree_sum(fz);
-        if (lane < 3) a.f[lane * n + i] = lane == 0 ? Fx : (lane == 1 ? Fy : Fz);
+        double F[3] = {group_tree_sum<G>(acc.fx), group_tree_sum<G>(acc.fy),
+                       group_tree_sum<G>(acc.fz)};
+        double s7[7] = {0, 0, 0, 0, 0, 0, 0};
         if constexpr (ENERGY) {
-            double s7[7] = {warp_tree_sum(pe), warp_tree_sum(v0), warp_tree_sum(v1),
-                            warp_tree_sum(v2), warp_tree_sum(v3), warp_tree_sum(v4),
-                            warp_tree_sum(v5)};
-            if (lane == 4) a.pe[i] = s7[0];
-#pragma unroll
-            for (int e = 0; e < 6; ++e)
-                if (lane == 5 + e) a.vir[e * n + i] = s7[1 + e];
+            s7[0] = group_tree_sum<G>(acc.pe);
+            s7[1] = group_tree_sum<G>(acc.v0);
+            s7[2] = group_tree_sum<G>(acc.v1);
+            s7[3] = group_tree_sum<G>(acc.v2);
+            s7[4] = group_tree_sum<G>(acc.v3);
+            s7[5] = group_tree_sum<G>(acc.v4);
+            s7[6] = group_tree_sum<G>(acc.v5);
+        }
+        if (k >= 0 && gl == 0) {
+            for (int c = 0; c < 3; ++c) a.f[c * n + i] = F[c];
+            a.npair[i] = npt;
+            if constexpr (ENERGY) {
+                a.pe[i] = s7[0];
+                for (int c = 0; c < 6; ++c) a.vir[c * n + i] = s7[1 + c];
+            }
         }
     }
 }
 
-template <bool ENERGY>
+// the class-ordered queue (heaviest class first), FW_GRAB particles per grab
+struct FwQueue {
+    int cnt[DCM_MAX_CLASSES], off[DCM_MAX_CLASSES], items[DCM_MAX_CLASSES + 1];
+
+    __device__ __forceinline__ void init(const ForceArgs &a)
+    {
+        const int K = a.b.K;
+        if (threadIdx.x == 0) {
+            int run = 0;
+            for (int q = K - 1, t = 0; q >= 0; --q, ++t) {
+                cnt[q] = a.class_buf[q];
+                off[q] = a.class_buf[K + q];
+                items[t] = run;
+                run += cnt[q];
+            }
+            items[K] = run;
+        }
+    }
+
+    template <typename F>
+    __device__ __forceinline__ void drain(const ForceArgs &a, int lane, F &&fn)
+    {
+        const int K = a.b.K;
+        const int total = items[K];
+        while (true) {
+            int item0 = 0;
+            if (lane == 0) item0 = (int)atomicAdd(a.queue, (unsigned)FW_GRAB);
+            item0 = __shfl_sync(0xffffffffu, item0, 0);
+            if (item0 >= total) break;
+            const int item1 = min(item0 + FW_GRAB, total);
+            int t = 0;
+            for (int item = item0; item < item1; ++item) {
+                while (t + 1 < K && item >= items[t + 1]) ++t;
+                int q = K - 1 - t;
+                fn(a.class_list[off[q] + (item - items[t])]);
+            }
+        }
+    }
+};
+
+// guard re-decisions and list entries of the block: one atomic each
+__device__ __forceinline__ void block_counts(const ForceArgs &a, int ng, long long entries)
+{
+    __shared__ int s_ng;
+    __shared__ unsigned long long s_ent;
+    const int lane = threadIdx.x & 31;
+    for (int off = 16; off > 0; off >>= 1) {
+        ng += __shfl_xor_sync(0xffffffffu, ng, off);
+        entries += __shfl_xor_sync(0xffffffffu, entries, off);
+    }
+    if (threadIdx.x == 0) {
+        s_ng = 0;
+        s_ent = 0ull;
+    }
+    __syncthreads();
+    if (lane == 0 && ng) atomicAdd(&s_ng, ng);
+    if (lane == 0 && entries) atomicAdd(&s_ent, (unsigned long long)entries);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_ng) atomicAdd(a.guard_count, (unsigned long long)s_ng);
+    if (threadIdx.x == 0 && s_ent) atomicAdd(a.list_entries, s_ent);
+}
+
+// direct walk; FILL: runs only on a Verlet-list rebuild step and fills the
+// lists when the fill gate is open
+template <bool ENERGY, bool FILL>
 __global__ void __launch_bounds__(FW_THREADS, 8) k_force_warp(ForceArgs a)
 {
     __shared__ FwTable s_tab[FW_WARPS];
-    __shared__ int s_cnt[DCM_MAX_CLASSES], s_off[DCM_MAX_CLASSES], s_items[DCM_MAX_CLASSES + 1];
-    const int K = a.b.K;
+    __shared__ FwQueue sq;
+    __shared__ int s_run, s_fill;
+    sq.init(a);
     if (threadIdx.x == 0) {
-        int run = 0;
-        // heaviest (largest cutoff) class first
-        for (int q = K - 1, t = 0; q >= 0; --q, ++t) {
-            s_cnt[q] = a.class_buf[q];
-            s_off[q] = a.class_buf[K + q];
-            s_items[t] = run;
-            run += s_cnt[q];
-        }
-        s_items[K] = run;
+        s_run = FILL ? a.list_flags[LF_REBUILD] : 1;
+        s_fill = FILL ? a.list_flags[LF_WORDS - 1] : 0;
     }
     __syncthreads();
-    const int total = s_items[K];
+    if (!s_run) return;
     const int lane = threadIdx.x & 31;
+    const bool fill_on = s_fill != 0;
     FwTable &tb = s_tab[threadIdx.x >> 5];
+    int ng = 0;
+    long long entries = 0;
+    sq.drain(a, lane, [&](int k) {
+        particle_force_warp<ENERGY, FILL>(a, tb, k, lane, ng, fill_on, entries);
+    });
+    block_counts(a, ng, entries);
+}
+
+// Verlet-list forces; runs only on a step that keeps its lists.  A warp
+// takes 32/G consecutive queue items per grab, one per lane group.
+template <bool ENERGY, int G>
+__global__ void __launch_bounds__(FW_THREADS, 8) k_force_list_warp(ForceArgs a)
+{
+    __shared__ FwQueue sq;
+    __shared__ int s_run;
+    sq.init(a);
+    if (threadIdx.x == 0) s_run = a.list_flags[LF_REBUILD] == 0;
+    __syncthreads();
+    if (!s_run) return;
+    constexpr int PER = 32 / G;
+    const int lane = threadIdx.x & 31;
+    const int grp = lane / G, gl = lane & (G - 1);
+    const int K = a.b.K;
+    const int total = sq.items[K];
     int ng = 0;
     while (true) {
         int item0 = 0;
-        if (lane == 0) item0 = (int)atomicAdd(a.queue, (unsigned)FW_GRAB);
+        if (lane == 0) item0 = (int)atomicAdd(a.queue, (unsigned)PER);
         item0 = __shfl_sync(0xffffffffu, item0, 0);
         if (item0 >= total) break;
-        const int item1 = min(item0 + FW_GRAB, total);
-        int t = 0;
-        for (int item = item0; item < item1; ++item) {
-            while (t + 1 < K && item >= s_items[t + 1]) ++t;
+        const int item = item0 + grp;
+        int k = -1;
+        if (item < total) {
+            int t = 0;
+            while (t + 1 < K && item >= sq.items[t + 1]) ++t;
             int q = K - 1 - t;
-            int k = a.class_list[s_off[q] + (item - s_items[t])];
-            particle_force_warp<ENERGY>(a, tb, k, lane, ng);
+            k = a.class_list[sq.off[q] + (item - sq.items[t])];
         }
+        particle_force_list_group<ENERGY, G>(a, k, gl, ng);
     }
-    for (int off = 16; off > 0; off >>= 1) ng += __shfl_xor_sync(0xffffffffu, ng, off);
-    __shared__ int s_ng;
-    if (threadIdx.x == 0) s_ng = 0;
-    __syncthreads();
-    if (lane == 0 && ng) atomicAdd(&s_ng, ng);
-    __syncthreads();
-    if (threadIdx.x == 0 && s_ng) atomicAdd(a.guard_count, (unsigned long long)s_ng);
+    block_counts(a, ng, 0);
 }
 
 static void fill_args(dcm_handle *h, ForceArgs &a);
@@ -953,12 +1222,35 @@ int launch_forces(dcm_handle *h, bool energy)
     int block = h->tune.block >= 64 && h->tune.block <= FORCE_THREADS ? h->tune.block : FORCE_THREADS;
     int grid = h->num_sms * (2048 / block);
     bool fp64 = h->p.precision == DCM_FP64;
+    const int g2 = h->num_sms * 8;
     if (!fp64 && !h->nl && h->tune.walk == DCM_WALK_WARP) {
-        int g2 = h->num_sms * 8;
         if (energy)
-            k_force_warp<true><<<g2, FW_THREADS, 0, h->stream>>>(a);
+            k_force_warp<true, false><<<g2, FW_THREADS, 0, h->stream>>>(a);
         else
-            k_force_warp<false><<<g2, FW_THREADS, 0, h->stream>>>(a);
+            k_force_warp<false, false><<<g2, FW_THREADS, 0, h->stream>>>(a);
+        return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "force launch");
+    }
+    if (h->nl && h->list_warp) {
+        // rebuild step: direct walk + list fill; other steps: the lists.
+        // Both are launched, each returns at once unless it is its step.
+        h->kernels += 1;
+        if (energy)
+            k_force_warp<true, true><<<g2, FW_THREADS, 0, h->stream>>>(a);
+        else
+            k_force_warp<false, true><<<g2, FW_THREADS, 0, h->stream>>>(a);
+        cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), h->stream);
+        const int G = h->tune.list_lanes > 0 ? h->tune.list_lanes : FW_LIST_G;
+        if (energy) {
+            k_force_list_warp<true, 8><<<g2, FW_THREADS, 0, h->stream>>>(a);   // energy steps are rare
+        } else if (G == 4) {
+            k_force_list_warp<false, 4><<<g2, FW_THREADS, 0, h->stream>>>(a);
+        } else if (G == 16) {
+            k_force_list_warp<false, 16><<<g2, FW_THREADS, 0, h->stream>>>(a);
+        } else if (G == 32) {
+            k_force_list_warp<false, 32><<<g2, FW_THREADS, 0, h->stream>>>(a);
+        } else {
+            k_force_list_warp<false, 8><<<g2, FW_THREADS, 0, h->stream>>>(a);
+        }
         return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "force launch");
     }
     if (fp64) {
@@ -999,6 +1291,8 @@ static void fill_args(dcm_handle *h, ForceArgs &a)
     a.vir = h->vir;
     a.queue = &h->stats->barrier[2];
     a.guard_count = &h->stats->guard_rechecks;
+    a.list_entries = &h->stats->list_entries;
+    a.list_flags = h->lflags;
     a.list_ok = h->nl ? h->lflags + LF_OK : nullptr;
     a.nl_start = h->nl_start;
     a.nl = h->nl;

@@ -62,7 +62,11 @@ struct DevStats {
 };
 
 // Verlet-list control words (device): see dcm_list.cu
-enum { LF_REBUILD = 0, LF_OK = 1, LF_MAXDISP = 2, LF_MINHEAD = 3, LF_DONE = 4, LF_WORDS = 8 };
+// Verlet-list control words: rebuild decision, lists valid, the two maxima
+// of the check, its block counter, a per-particle capacity overflow seen by
+// the last fill, the capacity density scale (float bits), the fill gate
+enum { LF_REBUILD = 0, LF_OK = 1, LF_MAXDISP = 2, LF_MINHEAD = 3, LF_DONE = 4, LF_OVERFLOW = 5,
+       LF_SCALE = 6, LF_WORDS = 8 };
 
 constexpr int MAX_SYSTEMS = 1024;
 
@@ -172,6 +176,8 @@ struct dcm_handle {
     double *x_ref;               // positions at the build (id order)
     float *rl_ref;               // list radius of each particle at the build
     bool cut_detected;           // cutoffs come from detection (lists anticipate d moves)
+    bool list_warp;              // lists built and walked by the warp kernels (set per capture)
+    float list_scale0;           // initial capacity density of those lists
     int *lflags;                 // LF_* words
     // per particle diagnostics / energies
     int32_t *npair;

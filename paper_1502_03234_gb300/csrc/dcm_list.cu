@@ -69,6 +69,13 @@ __global__ void k_list_check(Batch b, const double *__restrict__ x, const double
         float d2 = __int_as_float(atomicExch(&lf[LF_MAXDISP], 0));
         float head = __int_as_float(atomicExch(&lf[LF_MINHEAD], 0x7f7f7f7f));
         int ok = atomicAdd(&lf[LF_OK], 0);
+        if (atomicExch(&lf[LF_OVERFLOW], 0)) {
+            // a particle had more neighbours than its capacity at the last
+            // fill: its list is incomplete, rebuild with 25 % more room
+            ok = 0;
+            lf[LF_OK] = 0;
+            lf[LF_SCALE] = __float_as_int(__int_as_float(lf[LF_SCALE]) * 1.25f);
+        }
         int rebuild = force || !ok || (2.f * sqrtf(d2) >= head);
         lf[LF_REBUILD] = rebuild;
         lf[LF_DONE] = 0;
@@ -77,7 +84,7 @@ __global__ void k_list_check(Batch b, const double *__restrict__ x, const double
 
 // after the count scan: does the list fit?  FILL gate = rebuild && fits
 __global__ void k_list_total(int64_t N, const int32_t *__restrict__ start, int64_t cap, int *lf,
-                             DevStats *st)
+                             DevStats *st, int fill_counts)
 {
     if (lf[LF_REBUILD] == 0) {
         lf[LF_WORDS - 1] = 0;    // no fill on a step that keeps its lists
@@ -88,7 +95,8 @@ __global__ void k_list_total(int64_t N, const int32_t *__restrict__ start, int64
     lf[LF_OK] = ok;
     lf[LF_WORDS - 1] = ok;       // fill gate
     st->list_builds += 1ull;
-    st->list_entries = (unsigned long long)total;
+    // the warp fill walk adds its entries (start[] sums capacities there)
+    st->list_entries = fill_counts ? 0ull : (unsigned long long)total;
 }
 
 __global__ void k_list_save(int64_t N, const double *__restrict__ x, double *x_ref, const int *gate)
@@ -102,23 +110,36 @@ __global__ void k_list_save(int64_t N, const double *__restrict__ x, double *x_r
 
 static inline int nblk(int64_t n, int b) { return (int)((n + b - 1) / b); }
 
-// decide, [cell sort], gather + classes, [list count, scan, fill, save]
+// decide, [cell sort], gather + classes, then
+//  warp kernels (MIXED, warp walk): [capacity scan, total, save]; the list
+//      fill happens in the force phase, inside the direct force walk of the
+//      rebuild step (launch_forces);
+//  lanes kernels: [list count, scan, total, fill, save]
 int launch_list_step(dcm_handle *h, bool force_rebuild)
 {
     cudaStream_t s = h->stream;
     int64_t N = h->n;
     int cgrid = h->num_sms * 2;
+    h->list_warp = h->p.precision == DCM_MIXED && h->tune.walk == DCM_WALK_WARP;
     k_list_check<<<cgrid, 256, 0, s>>>(h->b, h->x, h->x_ref, h->rc, h->rl_ref, h->lflags,
                                         force_rebuild ? 1 : 0);
     const int *rebuild = h->lflags + LF_REBUILD;
     const int *fill = h->lflags + (LF_WORDS - 1);
     int r = launch_bin_gated(h, rebuild);
     if (r) return r;
+    if (h->list_warp) {
+        // the gather wrote each particle's capacity into nl_cnt
+        launch_scan(h, h->nl_cnt, h->nl_start, h->nl_tiles, N, -1, rebuild);
+        k_list_total<<<1, 1, 0, s>>>(N, h->nl_start, h->nl_cap, h->lflags, h->stats, 1);
+        k_list_save<<<nblk(N, 256), 256, 0, s>>>(N, h->x, h->x_ref, fill);
+        h->kernels += 3;
+        return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "list launch");
+    }
     float delta = h->cut_detected ? 1.0f : 0.0f;
     r = launch_list_walk(h, false, rebuild, delta);
     if (r) return r;
     launch_scan(h, h->nl_cnt, h->nl_start, h->nl_tiles, N, -1, rebuild);
-    k_list_total<<<1, 1, 0, s>>>(N, h->nl_start, h->nl_cap, h->lflags, h->stats);
+    k_list_total<<<1, 1, 0, s>>>(N, h->nl_start, h->nl_cap, h->lflags, h->stats, 0);
     r = launch_list_walk(h, true, fill, delta);
     if (r) return r;
     k_list_save<<<nblk(N, 256), 256, 0, s>>>(N, h->x, h->x_ref, fill);

@@ -55,12 +55,13 @@ class dcm_params(C.Structure):
                 ("detect_every", C.c_int32), ("kmeans_max_iter", C.c_int32),
                 ("cfsm_iter_max", C.c_int32), ("cfsm_eps", C.c_double),
                 ("precision", C.c_int32), ("n_classes", C.c_int32), ("cell_min", C.c_double),
-                ("skin", C.c_double), ("reserved", C.c_int32 * 6)]
+                ("skin", C.c_double), ("list_density", C.c_float),
+                ("reserved", C.c_int32 * 5)]
 
 
 class dcm_tuning(C.Structure):
     _fields_ = [("lanes", C.c_int32 * DCM_MAX_CLASSES), ("block", C.c_int32),
-                ("walk", C.c_int32), ("reserved", C.c_int32 * 6)]
+                ("walk", C.c_int32), ("list_lanes", C.c_int32), ("reserved", C.c_int32 * 5)]
 
 
 class dcm_stats(C.Structure):
@@ -255,12 +256,13 @@ def dcm_get_stats(h) -> dcm_stats:
     return s
 
 
-def dcm_set_tuning(h, lanes, block: int = 256, walk: int = None) -> None:
+def dcm_set_tuning(h, lanes, block: int = 256, walk: int = None, list_lanes: int = 8) -> None:
     t = dcm_tuning()
     for q in range(DCM_MAX_CLASSES):
         t.lanes[q] = int(lanes[min(q, len(lanes) - 1)])
     t.block = int(block)
     t.walk = DCM_WALK_LANES if walk is None else int(walk)
+    t.list_lanes = int(list_lanes)
     check(lib().dcm_set_tuning(h, C.byref(t)))
 
 
@@ -417,9 +419,9 @@ class System:
     def stats(self) -> dcm_stats:
         return dcm_get_stats(self.h)
 
-    def set_tuning(self, lanes, block=256, walk=None):
+    def set_tuning(self, lanes, block=256, walk=None, list_lanes=8):
         """lanes/block select the lanes walk unless walk=DCM_WALK_WARP"""
-        dcm_set_tuning(self.h, lanes, block, walk)
+        dcm_set_tuning(self.h, lanes, block, walk, list_lanes)
 
     def sync(self):
         dcm_sync(self.h)

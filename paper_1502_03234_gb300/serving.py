@@ -238,7 +238,8 @@ class DcmBackend(Backend):
     """One libdcm handle per admitted request, each on its own CUDA stream;
     the state stays on the device between chunks."""
 
-    def __init__(self, precision: int | None = None, tune: dict | None = None):
+    def __init__(self, precision: int | None = None, tune: dict | None = None,
+                 skin: float | None = None):
         import torch
 
         from . import dcm
@@ -247,10 +248,13 @@ class DcmBackend(Backend):
         self.dcm = dcm
         self.precision = dcm.DCM_MIXED if precision is None else precision
         self.tune = tune or {}
+        self.skin = skin
 
     def _params(self, job: Job):
         p = job.params if job.params is not None else self.dcm.default_params()
         p.precision = self.precision
+        if self.skin is not None:
+            p.skin = self.skin
         return p
 
     def estimate(self, job: Job) -> int:
@@ -300,12 +304,12 @@ def trace_jobs(requests, min_edge: float | None = 17.0) -> list:
 
 def serve_trace(count=400, rate=20.0, n_min=2048, n_max=524288, steps_min=100, steps_max=2000,
                 budget_gb=120.0, max_slots=16, chunk=50, seed=0, precision=None,
-                realtime=True) -> Report:
+                realtime=True, skin=None) -> Report:
     from . import slabgen
 
     reqs = slabgen.make_trace(count, rate, n_min, n_max, steps_min, steps_max, seed=seed)
     jobs = trace_jobs(reqs)
-    srv = Server(DcmBackend(precision), int(budget_gb * 2**30), max_slots, chunk)
+    srv = Server(DcmBackend(precision, skin=skin), int(budget_gb * 2**30), max_slots, chunk)
     return srv.run(jobs, realtime=realtime)
 
 

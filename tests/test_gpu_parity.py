@@ -162,10 +162,15 @@ def test_ten_steps_positions(dcm, orc, prec):
 
 
 # ---- Verlet lists (skin > 0): the same pairs as the direct walk, always --------
-@pytest.mark.parametrize("prec,skin", [(0, 0.4), (1, 0.4), (1, 0.25)])
-def test_list_mode_forces(dcm, orc, prec, skin):
+WALKS = {"warp": 0, "lanes": 1}
+
+
+@pytest.mark.parametrize("prec,skin,walk", [(0, 0.4, "lanes"), (1, 0.4, "warp"), (1, 0.25, "warp"),
+                                            (1, 0.4, "lanes")])
+def test_list_mode_forces(dcm, orc, prec, skin, walk):
     s = slabgen.make_slab(16000, seed=40)
     with dcm.System(s.box, len(s.x), precision=prec, skin=skin) as sy:
+        sy.set_tuning([2, 1, 2, 2], 128, WALKS[walk])
         sy.set_state(s.x, s.v)
         sy.compute_forces()
         _, rc, _ = sy.cutoffs()
@@ -182,12 +187,13 @@ def test_list_mode_forces(dcm, orc, prec, skin):
     assert np.all(err <= FP64_ABS + FP64_REL * fmag + extra), err.max()
 
 
-@pytest.mark.parametrize("prec", [0, 1])
-def test_list_mode_stays_complete_while_reused(dcm, orc, prec):
+@pytest.mark.parametrize("prec,walk", [(0, "lanes"), (1, "warp"), (1, "lanes")])
+def test_list_mode_stays_complete_while_reused(dcm, orc, prec, walk):
     # after many steps of list reuse and rebuilds the interacting pairs must
     # still be exactly those of the definition at the current positions
     s = slabgen.make_slab(9001, seed=41)
     with dcm.System(s.box, len(s.x), precision=prec, skin=0.3) as sy:
+        sy.set_tuning([2, 1, 2, 2], 128, WALKS[walk])
         sy.set_state(s.x, s.v)
         sy.step(150)
         sy.sync()
@@ -204,6 +210,28 @@ def test_list_mode_stays_complete_while_reused(dcm, orc, prec):
     fmag = np.linalg.norm(ref.f, axis=1)
     extra = 0.0 if prec == 0 else 5e-4
     assert np.all(err <= FP64_ABS + FP64_REL * fmag + extra), err.max()
+
+
+def test_list_capacity_overflow_recovers(dcm, orc):
+    # capacities far too small: every build overflows, the overflowing step
+    # keeps its direct-walk forces, the density bound grows by 25 % per
+    # build until the lists fit; forces stay exact throughout
+    s = slabgen.make_slab(9001, seed=42)
+    with dcm.System(s.box, len(s.x), precision=1, skin=0.3, list_density=0.05) as sy:
+        sy.set_state(s.x, s.v)
+        sy.step(40)
+        sy.sync()
+        st = sy.stats()
+        npair = sy.pair_counts()
+        _, rc, _ = sy.cutoffs()
+        x, _, f = sy.get_state()
+        nc, _, _ = sy.cells()
+    assert st.list_builds >= 12, st.list_builds   # 0.05 * 1.25^k reaches ~0.8 after 13
+    ref = orc.forces(x, rc, s.box, nc)
+    assert np.array_equal(npair, ref.npair)
+    err = np.linalg.norm(f - ref.f, axis=1)
+    fmag = np.linalg.norm(ref.f, axis=1)
+    assert np.all(err <= FP64_ABS + FP64_REL * fmag + 5e-4), err.max()
 
 
 @pytest.mark.parametrize("prec", [0, 1])
