@@ -198,6 +198,19 @@ __device__ __forceinline__ void warp_flush(int cur, unsigned long long v, unsign
     }
 }
 
+// The smoothed densities are exact integers below 2^53 held as doubles.  The
+// voxel loops never touch the FP64 pipe (one FP64 warp instruction costs
+// dozens of issue slots here): a non-negative double compares like its bit
+// pattern, and its integer value comes from the bits by a shift.
+__device__ __forceinline__ unsigned long long exact_u64(double d)
+{
+    unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    if (b == 0ull) return 0ull;
+    int e = (int)(b >> 52) - 1023;                       // 0 <= e <= 52
+    unsigned long long m = (b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+    return m >> (52 - e);
+}
+
 // per-block shared state: centres, previous liquid count, threshold and the
 // done flag of every system (every block derives the same values from the
 // same global sums, so no broadcast is needed)
@@ -241,7 +254,7 @@ __global__ void __launch_bounds__(DET_THREADS) k_kmeans(KmeansArgs a)
                 mn = ~0ull;
                 tot = 0;
             }
-            unsigned long long bv = (unsigned long long)a.Bs[v];
+            unsigned long long bv = exact_u64(a.Bs[v]);
             mx = bv > mx ? bv : mx;
             mn = bv < mn ? bv : mn;
             tot += bv;
@@ -299,9 +312,9 @@ __global__ void __launch_bounds__(DET_THREADS) k_kmeans(KmeansArgs a)
             }
             if (s_done[s]) continue;
             double bv = a.Bs[v];
-            if (bv >= s_thr[s]) {
+            if (__double_as_longlong(bv) >= __double_as_longlong(s_thr[s])) {
                 cnt++;
-                sum += (unsigned long long)bv;
+                sum += exact_u64(bv);
             }
         }
         warp_flush<0>(cur, cnt, s_c0);
@@ -345,7 +358,7 @@ __global__ void __launch_bounds__(DET_THREADS) k_kmeans(KmeansArgs a)
     }
     for (int64_t v = lo + threadIdx.x; v < hi; v += blockDim.x) {
         int s = sys_of(a.b.v_off, M, v);
-        a.S[v] = a.Bs[v] >= s_thr[s] ? 0 : 1;
+        a.S[v] = __double_as_longlong(a.Bs[v]) >= __double_as_longlong(s_thr[s]) ? 0 : 1;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.st->kmeans_iters = it;
@@ -448,6 +461,12 @@ __global__ void __launch_bounds__(DET_THREADS) k_cfsm(CfsmArgs a)
                 double ax = dmin_nonneg(__ldcg(&X[nb[0]]), __ldcg(&X[nb[1]]));
                 double ay = dmin_nonneg(__ldcg(&X[nb[2]]), __ldcg(&X[nb[3]]));
                 double az = dmin_nonneg(__ldcg(&X[nb[4]]), __ldcg(&X[nb[5]]));
+                // the labels of the face neighbours, loaded with the distances
+                // (read-only in this kernel) so the push below waits on nothing
+                bool liq[7];
+                liq[0] = true;
+#pragma unroll
+                for (int e = 1; e < 7; ++e) liq[e] = __ldg(&a.S[nb[e - 1]]) == 0;
                 // any Godunov solution is at least min(a) + 1/sqrt(sum w): when
                 // that cannot beat the current value the solve is skipped
                 // (a lower bound with a relative margin, so no update is lost)
@@ -467,10 +486,6 @@ __global__ void __launch_bounds__(DET_THREADS) k_cfsm(CfsmArgs a)
                     // liquid face neighbours are recomputed in the next pass;
                     // the seven stamp exchanges are independent of each other
                     int cand[7] = {v, nb[0], nb[1], nb[2], nb[3], nb[4], nb[5]};
-                    bool liq[7];
-                    liq[0] = true;
-#pragma unroll
-                    for (int e = 1; e < 7; ++e) liq[e] = a.S[cand[e]] == 0;
                     int prev[7];
 #pragma unroll
                     for (int e = 0; e < 7; ++e) prev[e] = liq[e] ? atomicExch(&a.stamp[cand[e]], k + 1) : k + 1;

@@ -97,43 +97,48 @@ __device__ __forceinline__ void ff_add(float &hi, float &lo, float a)
 }
 
 // ---- bounded grid barrier for cooperative (co-resident) launches --------
-// words[0] = arrival counter, words[1] = generation.  Gives up after a
-// bounded number of polls, sets DEV_ERR_BARRIER and returns false.
+// words[0] counts arrivals and is never reset inside a launch: the k-th
+// barrier of the launch is complete when the count reaches k * (blocks),
+// and a block learns k from the value its own arrival returned.  One atomic
+// per block and polling with acquire loads; no reset or generation word, so
+// the last block to arrive does no extra round trips.  words[0] must be zero
+// at launch.  Gives up after a bounded number of polls, sets
+// DEV_ERR_BARRIER and returns false.
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p)
+{
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
 __device__ __forceinline__ bool grid_barrier(unsigned int *words, int *err)
 {
     __syncthreads();
     __shared__ int s_ok;
     if (threadIdx.x == 0) {
-        volatile unsigned int *gen = words + 1;
-        unsigned int g = *gen;
+        const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
         __threadfence();
-        unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
-        unsigned int arrived = atomicAdd(words, 1u);
+        const unsigned int arrived = atomicAdd(words, 1u);
+        const unsigned int target = (arrived / nb + 1u) * nb;
         int ok = 1;
-        if (arrived == nb - 1) {
-            atomicExch(words, 0u);
-            __threadfence();
-            atomicAdd(words + 1, 1u);
-        } else {
-            // tight polling first (a healthy barrier completes in a few
-            // microseconds), then back off; the error word is read only every
-            // 256 polls.  The limit bounds the wait to well under a second.
-            long long polls = 0;
-            while (*gen == g) {
-                ++polls;
-                if ((polls & 255) == 0) {
-                    if (polls > (1ll << 21)) {
-                        atomicOr(err, DEV_ERR_BARRIER);
-                        ok = 0;
-                        break;
-                    }
-                    if (*(volatile int *)err & DEV_ERR_BARRIER) {
-                        ok = 0;
-                        break;
-                    }
+        // tight polling first (a healthy barrier completes in a few
+        // microseconds), then back off; the error word is read only every
+        // 256 polls.  The limit bounds the wait to well under a second.
+        long long polls = 0;
+        while ((int)(ld_acquire_u32(words) - target) < 0) {
+            ++polls;
+            if ((polls & 255) == 0) {
+                if (polls > (1ll << 21)) {
+                    atomicOr(err, DEV_ERR_BARRIER);
+                    ok = 0;
+                    break;
                 }
-                if (polls > 4096) __nanosleep(128);
+                if (*(volatile int *)err & DEV_ERR_BARRIER) {
+                    ok = 0;
+                    break;
+                }
             }
+            if (polls > 4096) __nanosleep(128);
         }
         __threadfence();
         s_ok = ok;
