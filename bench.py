@@ -46,10 +46,29 @@ METRIC = "atom-steps/s of DCM step (forces+interface) vs plain FP64 GPU path; p5
 UNIT = "atom-steps/s"
 N_DEFAULT = 262144
 FP32_LANES_PER_SM = 128          # Blackwell SM: 4 sub-partitions x 32 FP32 lanes
+
+
+def _hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6800.0                # fallback figure when the measured file is absent
+
+
+HBM_PEAK_GBS = _hbm_peak()
 FLOPS_PER_PAIR = 24              # 8 (distance test) + 16 (LJ force), per in-cutoff pair
 # DRAM bytes (read + write) per force launch from the committed ncu capture
 # (profiles/k_force_warp_N262144_mixed.md); None once the kernel changes
 FORCE_TRAFFIC = {"mixed": 14.96e6, "fp64": None}
+# DRAM bytes per launch of the Verlet-list force kernel (k_force_list_warp, skin 0.5,
+# N = 262,144) from the committed capture (profiles/k_force_list_warp_N262144_mixed.md)
+LIST_TRAFFIC = 248.78e6 + 3.94e6
+# bytes the list kernel must move per particle besides its list entries: own
+# position, cutoff constants, id/cell, list start and count, queue slot, the
+# force written and the pair count
+LIST_BYTES_PER_PARTICLE = 16 + 16 + 16 + 4 + 4 + 4 + 24 + 4
+LIST_BYTES_PER_ENTRY = 4
 
 
 def parse():
@@ -153,7 +172,7 @@ class Clocks:
 
 
 # ---- reference arm: the FP64 CPU oracle ----------------------------------------------
-def oracle_rate(n_sample: int, target_s: float, max_steps: int = 50, seed: int = 1):
+def oracle_rate(n_sample: int, target_s: float, max_steps: int = 2000, seed: int = 1):
     """atom-steps/s of the FP64 oracle (all host cores) on an n_sample slab
     with the same densities, cutoffs and cadence."""
     import oracle
@@ -399,7 +418,8 @@ def main():
         sy.sync()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(k)]
-        force_ms, phase_sum = [], {}
+        force_ms, phase_sum, rebuilt = [], {}, []
+        b_prev = sy.stats().list_builds
         for q in range(k):
             with torch.cuda.stream(stream):
                 flush.zero_()
@@ -409,9 +429,13 @@ def main():
                 ev[q][1].record(stream)
             ph = sy.phase_times()                       # waits for this step
             force_ms.append(ph["force"])
+            b_now = sy.stats().list_builds               # (outside the timed events)
+            rebuilt.append(b_now != b_prev)
+            b_prev = b_now
             for key, val in ph.items():
                 phase_sum[key] = phase_sum.get(key, 0.0) + val
         sy.sync()
+        timed_steps.rebuilt = rebuilt
         return [a.elapsed_time(b) for a, b in ev], force_ms, phase_sum
 
     sy = make_system(prec)
@@ -440,20 +464,45 @@ def main():
         t_max = float(t.item())
     value = world * n * args.steps / (t_max * 1e-3)
 
-    # roofline of the dominant kernel (the DCM force kernel, FP32 pipe)
+    # roofline of the dominant kernel
     clocks = clk.summary()
+    rebuilt = timed_steps.rebuilt
     f_avg_ms = sum(force_ms) / len(force_ms)
-    achieved = FLOPS_PER_PAIR * pairs / (f_avg_ms * 1e-3) / 1e12
     sm_mhz = clocks.get("sm_mhz") or 1477.0
-    peak = 152 * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak,
-                "traffic": (FORCE_TRAFFIC.get(args.precision)
-                            if n == N_DEFAULT and args.skin == 0 else None),
-                "kernel": force_kernel_name(dcm, sy, prec, args.skin),
-                "peak_note": "FP32 FMA peak derived from 152 SMs x 128 lanes x 2 flops x the "
-                             "median SM clock sampled during the timed region",
-                "pairs_per_launch": pairs, "force_ms_avg": f_avg_ms}
+    fp32_peak = 152 * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    list_steps = [t for t, r in zip(force_ms, rebuilt) if not r]
+    if prec == dcm.DCM_MIXED and args.skin > 0 and list_steps:
+        # Verlet-list steps: the force phase is k_force_list_warp (plus the
+        # empty launch of the rebuild kernel).  It streams each particle's
+        # list from HBM (arithmetic intensity ~3 flop/B, under the HBM roof)
+        l_ms = sum(list_steps) / len(list_steps)
+        entries = st.list_entries
+        alg_bytes = LIST_BYTES_PER_ENTRY * entries + LIST_BYTES_PER_PARTICLE * n
+        achieved = alg_bytes / (l_ms * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                    "frac": achieved / HBM_PEAK_GBS,
+                    "traffic": LIST_TRAFFIC if n == N_DEFAULT and args.skin == 0.5 else None,
+                    "kernel": "k_force_list_warp (mixed, Verlet lists)",
+                    "peak_note": "measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                    "algorithmic_bytes_per_launch": alg_bytes, "list_entries": entries,
+                    "launch_ms_avg": l_ms, "launches": len(list_steps),
+                    "flops_view": {"achieved": FLOPS_PER_PAIR * pairs / (l_ms * 1e-3) / 1e12,
+                                   "peak": fp32_peak, "unit": "TFLOP/s",
+                                   "frac": FLOPS_PER_PAIR * pairs / (l_ms * 1e-3) / 1e12 / fp32_peak},
+                    "rebuild_steps": sum(rebuilt),
+                    "rebuild_force_ms_avg": (sum(t for t, r in zip(force_ms, rebuilt) if r) /
+                                             max(1, sum(rebuilt))),
+                    "force_ms_avg_all_steps": f_avg_ms, "pairs_per_launch": pairs}
+    else:
+        achieved = FLOPS_PER_PAIR * pairs / (f_avg_ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                    "frac": achieved / fp32_peak,
+                    "traffic": (FORCE_TRAFFIC.get(args.precision)
+                                if n == N_DEFAULT and args.skin == 0 else None),
+                    "kernel": force_kernel_name(dcm, sy, prec, args.skin),
+                    "peak_note": "FP32 FMA peak derived from 152 SMs x 128 lanes x 2 flops x the "
+                                 "median SM clock sampled during the timed region",
+                    "pairs_per_launch": pairs, "force_ms_avg": f_avg_ms}
 
     # the plain FP64 GPU path on the same system (the comparison the metric names)
     fp64_info = None
