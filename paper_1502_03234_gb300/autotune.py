@@ -127,6 +127,7 @@ def tune(box, x, v, params: dcm.dcm_params, *, reps: int = 5, stream=None,
 # launch shapes tried on a live handle (cell edge fixed at creation)
 LIVE_CANDIDATES = (
     {"walk": dcm.DCM_WALK_WARP, "lanes": [1], "block": 128},
+    {"walk": dcm.DCM_WALK_WARP, "lanes": [1], "block": 128, "list_lanes": 4},
     {"walk": dcm.DCM_WALK_LANES, "lanes": [2, 1, 2, 2], "block": 128},
     {"walk": dcm.DCM_WALK_LANES, "lanes": [2, 2, 4, 4], "block": 128},
     {"walk": dcm.DCM_WALK_LANES, "lanes": [4, 4, 8, 8], "block": 256},
