@@ -211,7 +211,7 @@ static int64_t bytes_for(const Geom &g, int64_t n, int precision)
     int64_t ncell = g.ncell;
     int64_t nv = g.nvox;
     int64_t per_p = 3 * 8 * 3 + 8 + 8 + 1 + 4 * 3 + 16 + 4 + 4 + 8 + 48 + 24;
-    per_p += 32;   // spd (FP64) or rq + pk (MIXED)
+    per_p += 36;   // spd (FP64) or rq + pk + inv (MIXED)
     int64_t per_v = 4 + 4 + 4 + 8 + 1 + 8 + 8 + 4 + 16;
     int64_t ntiles = (ncell + 2047) / 2048 + 1;
     int64_t lists = g.skin > 0 ? 4 * list_cap(g, n) + n * (4 + 4 + 24 + 8) : 0;
@@ -248,7 +248,7 @@ extern "C" int dcm_destroy(dcm_handle *h)
     for (int q = 0; q <= DCM_NUM_PHASES; ++q)
         if (h->ev[q]) cudaEventDestroy(h->ev[q]);
     void *ptrs[] = {h->x, h->v, h->f, h->d, h->rc, h->cls, h->cell_of, h->slot, h->cell_count,
-                    h->cell_start, h->sorted_id, h->scan_tmp, h->sp4, h->spd, h->rq, h->pk, h->class_list,
+                    h->cell_start, h->sorted_id, h->scan_tmp, h->sp4, h->spd, h->rq, h->pk, h->inv, h->class_list,
                     h->class_count_dev, h->B, h->sm1, h->sm2, h->Bs, h->S, h->D0, h->D1, h->stamp,
                     h->flist, h->fcount, h->kacc, h->npair, h->pe, h->vir, h->red_part, h->red_out,
                     h->err, h->stats, h->tmp3n, h->geo_dev, h->off_dev, h->nl, h->nl_cnt,
@@ -365,6 +365,7 @@ static int create_systems(int M, const dcm_box *boxes, const int64_t *ns, const 
     if (h->p.precision != DCM_FP64) {
         ALLOC(h->rq, N);
         ALLOC(h->pk, N);
+        ALLOC(h->inv, N);
     }
     ALLOC(h->class_list, N);
     ALLOC(h->class_count_dev, 3 * DCM_MAX_CLASSES);
@@ -430,6 +431,7 @@ static int create_systems(int M, const dcm_box *boxes, const int64_t *ns, const 
     cudaMemsetAsync(h->v, 0, sizeof(double) * 3 * N, h->stream);
     cudaMemsetAsync(h->f, 0, sizeof(double) * 3 * N, h->stream);
     cudaMemsetAsync(h->cls, 0, N, h->stream);
+    if (h->inv) launch_iota(h, h->inv, N);       // a valid permutation before the first sort
     if (h->nl) {
         cudaMemsetAsync(h->lflags, 0, sizeof(int) * LF_WORDS, h->stream);
         cudaMemsetAsync(h->lflags + LF_MINHEAD, 0x7f, sizeof(int), h->stream);   // ~3.4e38
@@ -617,6 +619,7 @@ static int forces_now(dcm_handle *h, bool energy)
         h->have_cut = true;
         h->cut_detected = true;
     }
+    h->step_detect = true;                       // classes may have changed
     int r = h->nl ? launch_list_step(h, true) : launch_bin(h);
     if (r) return r;
     r = launch_forces(h, energy);
@@ -645,6 +648,8 @@ static void mark(dcm_handle *h, int q, bool capturing)
 static int enqueue_step(dcm_handle *h, bool detect, bool capturing)
 {
     int64_t k0 = h->kernels;
+    list_mode(h);
+    h->step_detect = detect;
     mark(h, 0, capturing);
     int r = launch_kick_drift(h);
     mark(h, 1, capturing);

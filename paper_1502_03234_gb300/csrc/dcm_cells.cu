@@ -127,38 +127,26 @@ __global__ void k_cell_sort(int64_t ncell, const int32_t *__restrict__ start, in
 __global__ void k_gather(Batch b, const double *__restrict__ x, const int32_t *__restrict__ sorted_id,
                          const int32_t *__restrict__ cell_of, float4 *sp4, double4_32a *spd,
                          const double *__restrict__ rc, float4 *rq, int4 *pk,
-                         const double *__restrict__ dist, const int *lf, float delta, int32_t *capk)
+                         const double *__restrict__ dist, const int *lf, float delta, int32_t *capk,
+                         int32_t *inv, const int *gate)
 {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= b.N) return;
+    if (k >= b.N || gated_off(gate)) return;
     // sorted slots keep the systems' particle ranges
     const Geom &g = b.sys[sys_of(b.p_off, b.M, k)];
     int i = sorted_id[k];
     int c = cell_of[i] - (int)g.c0;
-    int cx = c % g.nc[0];
-    int cy = (c / g.nc[0]) % g.nc[1];
-    int cz = c / (g.nc[0] * g.nc[1]);
     double px = x[i], py = x[(size_t)b.N + i], pz = x[2 * (size_t)b.N + i];
-    double u[3] = {DSUB(px, DMUL((double)cx, g.cedge[0])), DSUB(py, DMUL((double)cy, g.cedge[1])),
-                   DSUB(pz, DMUL((double)cz, g.cedge[2]))};
-    // between Verlet-list builds a particle keeps the cell of the build; one
-    // that wrapped through the box is folded back next to that cell
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        float uf = (float)u[a];
-        if (uf > (float)g.halfL[a]) u[a] = DSUB(u[a], g.L[a]);
-        else if (uf < -(float)g.halfL[a]) u[a] = DADD(u[a], g.L[a]);
-    }
-    sp4[k] = make_float4((float)u[0], (float)u[1], (float)u[2], (float)cx);
+    sp4[k] = cell_rel_position(g, px, py, pz, c);
     if (spd) spd[k] = make_double4_32a(px, py, pz, 0.0);
+    if (inv) inv[i] = (int32_t)k;
     if (rq) {
         // the force walk's per-particle constants, once per particle here
-        // instead of once per warp there: FP32 r_c^2 with its 2^-18 guard
-        // band and the conservative culling radius
+        // instead of once per warp there
         double r = rc[i];
-        float rc2f = (float)DMUL(r, r);
-        rq[k] = make_float4(rc2f, rc2f * (1.f - 3.814697265625e-06f), rc2f * (1.f + 3.814697265625e-06f),
-                            (float)r * 1.00002f + 1e-4f);
+        rq[k] = rc_constants(r);
+        int cy = (c / g.nc[0]) % g.nc[1];
+        int cz = c / (g.nc[0] * g.nc[1]);
         int w = 0;
         if (capk && lf[LF_REBUILD]) {
             // a Verlet-list build follows: list radius and the entry
@@ -173,12 +161,19 @@ __global__ void k_gather(Batch b, const double *__restrict__ x, const int32_t *_
     }
 }
 
+__global__ void k_class_zero(int32_t *buf, const int *gate)
+{
+    if (gated_off(gate)) return;
+    if (threadIdx.x < 3 * DCM_MAX_CLASSES) buf[threadIdx.x] = 0;
+}
+
 // per-class lists of sorted slots (warp-aggregated appends keep neighbouring
 // slots together); counts[0..K) must be prefix offsets, cursors[0..K) zero
 __global__ void k_class_lists(int n, int K, const int32_t *__restrict__ sorted_id,
                               const uint8_t *__restrict__ cls, const int32_t *__restrict__ offs,
-                              int32_t *cursor, int32_t *list)
+                              int32_t *cursor, int32_t *list, const int *gate)
 {
+    if (gated_off(gate)) return;
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     int lane = threadIdx.x & 31;
     int c = k < n ? (int)cls[sorted_id[k]] : -1;
@@ -194,8 +189,10 @@ __global__ void k_class_lists(int n, int K, const int32_t *__restrict__ sorted_i
     }
 }
 
-__global__ void k_class_count(int n, int K, const uint8_t *__restrict__ cls, int32_t *count)
+__global__ void k_class_count(int n, int K, const uint8_t *__restrict__ cls, int32_t *count,
+                              const int *gate)
 {
+    if (gated_off(gate)) return;
     __shared__ int32_t s[DCM_MAX_CLASSES];
     if (threadIdx.x < DCM_MAX_CLASSES) s[threadIdx.x] = 0;
     __syncthreads();
@@ -206,8 +203,9 @@ __global__ void k_class_count(int n, int K, const uint8_t *__restrict__ cls, int
 }
 
 // counts [0..K) -> exclusive offsets [K..2K), cursors [2K..3K) zeroed
-__global__ void k_class_offsets(int K, int32_t *buf)
+__global__ void k_class_offsets(int K, int32_t *buf, const int *gate)
 {
+    if (gated_off(gate)) return;
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     int run = 0;
     for (int q = 0; q < K; ++q) {
@@ -230,12 +228,16 @@ int launch_scan(dcm_handle *h, const int32_t *in, int32_t *out, int32_t *tiles, 
 }
 
 // cell sort (skipped while *gate == 0), then the gather of the sorted
-// streams from the current positions and the per-class lists
-int launch_bin_gated(dcm_handle *h, const int *gate)
+// streams from the current positions and the per-class lists.  With the
+// warp Verlet-list kernels the drift and the cutoff kernel keep the sorted
+// positions and cutoff constants current between builds, so the gather
+// runs only with the sort; the class lists are redone when the sort ran or
+// the classes changed (class_gate null: always).
+int launch_bin_gated(dcm_handle *h, const int *gate, const int *class_gate)
 {
     cudaStream_t s = h->stream;
     int n = (int)h->n;
-    h->kernels += 7;
+    h->kernels += 8;
     cudaMemsetAsync(h->cell_count, 0, sizeof(int32_t) * h->ncell, s);
     k_cell_count<<<nblk(n, 256), 256, 0, s>>>(h->b, h->x, h->cell_of, h->slot, h->cell_count, gate);
     launch_scan(h, h->cell_count, h->cell_start, h->scan_tmp, h->ncell, n, gate);
@@ -246,18 +248,20 @@ int launch_bin_gated(dcm_handle *h, const int *gate)
     k_gather<<<nblk(n, 256), 256, 0, s>>>(h->b, h->x, h->sorted_id, h->cell_of, h->sp4,
                                           h->p.precision == DCM_FP64 ? h->spd : nullptr, h->rc,
                                           h->rq, h->pk, h->d, h->lflags,
-                                          h->cut_detected ? 1.0f : 0.0f, wl ? h->nl_cnt : nullptr);
-    // class lists of sorted slots for the per-class force launches
+                                          h->cut_detected ? 1.0f : 0.0f, wl ? h->nl_cnt : nullptr,
+                                          h->inv, wl ? gate : nullptr);
+    // class lists of sorted slots for the force work queue
     int K = h->b.K;
-    cudaMemsetAsync(h->class_count_dev, 0, sizeof(int32_t) * 3 * DCM_MAX_CLASSES, s);
-    k_class_count<<<nblk(n, 256), 256, 0, s>>>(n, K, h->cls, h->class_count_dev);
-    k_class_offsets<<<1, 32, 0, s>>>(K, h->class_count_dev);
+    k_class_zero<<<1, 32, 0, s>>>(h->class_count_dev, class_gate);
+    k_class_count<<<nblk(n, 256), 256, 0, s>>>(n, K, h->cls, h->class_count_dev, class_gate);
+    k_class_offsets<<<1, 32, 0, s>>>(K, h->class_count_dev, class_gate);
     k_class_lists<<<nblk(n, 256), 256, 0, s>>>(n, K, h->sorted_id, h->cls,
                                                h->class_count_dev + K,
-                                               h->class_count_dev + 2 * K, h->class_list);
+                                               h->class_count_dev + 2 * K, h->class_list,
+                                               class_gate);
     return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "binning launch");
 }
 
-int launch_bin(dcm_handle *h) { return launch_bin_gated(h, nullptr); }
+int launch_bin(dcm_handle *h) { return launch_bin_gated(h, nullptr, nullptr); }
 
 }  // namespace dcm

@@ -520,9 +520,11 @@ __global__ void __launch_bounds__(DET_THREADS) k_cfsm(CfsmArgs a)
 }
 
 // ---- Algorithm 3.1 + Eq. 7-8 ----------------------------------------------------
+// rq given (warp Verlet-list kernels): the new cutoff's force constants go
+// straight to the particle's sorted slot inv[i]
 __global__ void k_cutoff(Batch b, const double *__restrict__ x, const double *__restrict__ D0,
                          const double *__restrict__ D1, const int *__restrict__ result, double *d,
-                         double *rc, uint8_t *cls)
+                         double *rc, uint8_t *cls, float4 *rq, const int32_t *__restrict__ inv)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= b.N) return;
@@ -592,6 +594,7 @@ __global__ void k_cutoff(Batch b, const double *__restrict__ x, const double *__
     d[i] = di;
     rc[i] = r;
     cls[i] = (uint8_t)c;
+    if (rq) rq[inv[i]] = rc_constants(r);
 }
 
 // classes for cutoffs supplied directly (scheduling only)
@@ -767,8 +770,10 @@ int launch_detect(dcm_handle *h)
         if (rc) return rc;
     }
     // Algorithm 3.1 + Eq. 7
+    const bool wl = h->nl && h->list_warp;
     k_cutoff<<<nblk(b.N, 256), 256, 0, s>>>(b, h->x, h->D0, h->D1,
-                                            (const int *)&h->stats->barrier[3], h->d, h->rc, h->cls);
+                                            (const int *)&h->stats->barrier[3], h->d, h->rc, h->cls,
+                                            wl ? h->rq : nullptr, h->inv);
     return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "detect launch");
 }
 

@@ -221,4 +221,35 @@ __device__ __forceinline__ float list_radius(const Geom &g, double rci, double d
     return r * 1.00001f + (float)g.skin + 1e-4f;
 }
 
+// FP32 position of a particle relative to the corner of its link cell
+// (cell index c_local within its system) and that cell's x index; a particle
+// that wrapped through the box since its cell was assigned (between
+// Verlet-list builds) is folded back next to that cell.  Shared by the
+// gather kernel and the drift, which must produce the same bits.
+__device__ __forceinline__ float4 cell_rel_position(const Geom &g, double px, double py, double pz,
+                                                   int c_local)
+{
+    int cx = c_local % g.nc[0];
+    int cy = (c_local / g.nc[0]) % g.nc[1];
+    int cz = c_local / (g.nc[0] * g.nc[1]);
+    double u[3] = {DSUB(px, DMUL((double)cx, g.cedge[0])), DSUB(py, DMUL((double)cy, g.cedge[1])),
+                   DSUB(pz, DMUL((double)cz, g.cedge[2]))};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float uf = (float)u[a];
+        if (uf > (float)g.halfL[a]) u[a] = DSUB(u[a], g.L[a]);
+        else if (uf < -(float)g.halfL[a]) u[a] = DADD(u[a], g.L[a]);
+    }
+    return make_float4((float)u[0], (float)u[1], (float)u[2], (float)cx);
+}
+
+// the force walks' per-particle cutoff constants: FP32 r_c^2, its 2^-18
+// guard band below and above, and the conservative culling radius
+__device__ __forceinline__ float4 rc_constants(double r)
+{
+    float rc2f = (float)DMUL(r, r);
+    return make_float4(rc2f, rc2f * (1.f - 3.814697265625e-06f), rc2f * (1.f + 3.814697265625e-06f),
+                       (float)r * 1.00002f + 1e-4f);
+}
+
 }  // namespace dcm

@@ -10,13 +10,18 @@ namespace dcm {
 // v += dt/(2m) F;  x += dt v;  wrap into the box  (first half of a step).
 // GB300 issues FP64 at 1/64 of the FP32 rate, so the update uses two fused
 // multiply-adds per component and integer tests of the exponent bits.
+// With sp4 given (warp Verlet-list kernels) the drift also refreshes the
+// particle's FP32 cell-relative position at its sorted slot inv[i], in the
+// cell of the last sort, so no gather pass is needed between list builds.
 __global__ void k_kick_drift(Batch b, double *__restrict__ x, double *__restrict__ v,
-                             const double *__restrict__ f, int *err)
+                             const double *__restrict__ f, int *err, float4 *sp4,
+                             const int32_t *__restrict__ inv, const int32_t *__restrict__ cell_of)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= b.N) return;
     const Geom &g = b.sys[sys_of(b.p_off, b.M, i)];
     int bad = 0;
+    double xn[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         size_t o = (size_t)a * b.N + i;
@@ -32,8 +37,16 @@ __global__ void k_kick_drift(Batch b, double *__restrict__ x, double *__restrict
         }
         v[o] = vi;
         x[o] = xi;
+        xn[a] = xi;
     }
     if (bad) atomicOr(err, bad);
+    if (sp4) sp4[inv[i]] = cell_rel_position(g, xn[0], xn[1], xn[2], cell_of[i] - (int)g.c0);
+}
+
+__global__ void k_iota(int32_t *p, int64_t n)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = (int32_t)i;
 }
 
 // v += dt/(2m) F  (second half of a step)
@@ -126,8 +139,15 @@ static inline int nblk(int64_t n, int b) { return (int)((n + b - 1) / b); }
 int launch_kick_drift(dcm_handle *h)
 {
     h->kernels += 1;
-    k_kick_drift<<<nblk(h->n, 256), 256, 0, h->stream>>>(h->b, h->x, h->v, h->f, h->err);
+    const bool wl = h->nl && h->list_warp;
+    k_kick_drift<<<nblk(h->n, 256), 256, 0, h->stream>>>(h->b, h->x, h->v, h->f, h->err,
+                                                         wl ? h->sp4 : nullptr, h->inv, h->cell_of);
     return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "kick_drift launch");
+}
+
+void launch_iota(dcm_handle *h, int32_t *p, int64_t n)
+{
+    k_iota<<<nblk(n, 256), 256, 0, h->stream>>>(p, n);
 }
 
 int launch_kick(dcm_handle *h)

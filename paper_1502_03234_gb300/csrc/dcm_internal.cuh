@@ -157,6 +157,7 @@ struct dcm_handle {
     float4 *sp4;
     double4_32a *spd;
     float4 *rq;                  // MIXED: per sorted slot r_c^2, guard band, culling radius
+    int32_t *inv;                // sorted slot of each particle (id order), MIXED
     int4 *pk;                    // MIXED: per sorted slot particle id, cell y, cell z
     int32_t *class_list;         // sorted slots grouped by class
     int32_t *class_count_dev;    // [K] counts, [K..2K) cursors
@@ -177,6 +178,7 @@ struct dcm_handle {
     float *rl_ref;               // list radius of each particle at the build
     bool cut_detected;           // cutoffs come from detection (lists anticipate d moves)
     bool list_warp;              // lists built and walked by the warp kernels (set per capture)
+    bool step_detect;            // the step being enqueued re-detects the interface
     float list_scale0;           // initial capacity density of those lists
     int *lflags;                 // LF_* words
     // per particle diagnostics / energies
@@ -216,7 +218,9 @@ int fail_cuda(cudaError_t e, const char *what, const char *file, int line);
 int launch_kick_drift(dcm_handle *h);
 int launch_kick(dcm_handle *h);
 int launch_bin(dcm_handle *h);                      // full cell sort + classes
-int launch_bin_gated(dcm_handle *h, const int *gate); // sort only if *gate, then classes
+int launch_bin_gated(dcm_handle *h, const int *gate, const int *class_gate);  // sort, gather, classes
+void list_mode(dcm_handle *h);          // sets list_warp from precision, tuning and lists
+void launch_iota(dcm_handle *h, int32_t *p, int64_t n);
 int launch_scan(dcm_handle *h, const int32_t *in, int32_t *out, int32_t *tiles, int64_t m,
                 int32_t total, const int *gate);     // exclusive scan (total < 0: out[m] = sum)
 int launch_list_step(dcm_handle *h, bool force_rebuild);  // decide, [rebin], lists

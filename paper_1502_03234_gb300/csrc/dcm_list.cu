@@ -110,6 +110,11 @@ __global__ void k_list_save(int64_t N, const double *__restrict__ x, double *x_r
 
 static inline int nblk(int64_t n, int b) { return (int)((n + b - 1) / b); }
 
+void list_mode(dcm_handle *h)
+{
+    h->list_warp = h->nl && h->p.precision == DCM_MIXED && h->tune.walk == DCM_WALK_WARP;
+}
+
 // decide, [cell sort], gather + classes, then
 //  warp kernels (MIXED, warp walk): [capacity scan, total, save]; the list
 //      fill happens in the force phase, inside the direct force walk of the
@@ -120,12 +125,13 @@ int launch_list_step(dcm_handle *h, bool force_rebuild)
     cudaStream_t s = h->stream;
     int64_t N = h->n;
     int cgrid = h->num_sms * 2;
-    h->list_warp = h->p.precision == DCM_MIXED && h->tune.walk == DCM_WALK_WARP;
+    list_mode(h);
     k_list_check<<<cgrid, 256, 0, s>>>(h->b, h->x, h->x_ref, h->rc, h->rl_ref, h->lflags,
                                         force_rebuild ? 1 : 0);
     const int *rebuild = h->lflags + LF_REBUILD;
     const int *fill = h->lflags + (LF_WORDS - 1);
-    int r = launch_bin_gated(h, rebuild);
+    // class lists change with a detection or with the sort
+    int r = launch_bin_gated(h, rebuild, h->list_warp && !h->step_detect ? rebuild : nullptr);
     if (r) return r;
     if (h->list_warp) {
         // the gather wrote each particle's capacity into nl_cnt
