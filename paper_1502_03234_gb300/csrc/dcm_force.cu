@@ -646,6 +646,8 @@ constexpr int FW_WARPS = FW_THREADS / 32;
 constexpr int FW_ROWS = 128;                 // row table entries per warp
 constexpr int FW_GRAB = 4;                   // particles per queue grab
 constexpr int FW_LIST_G = 8;                 // lanes per particle of the list kernel
+constexpr int FW_LIST_U = 4;                 // list entries in flight per lane
+constexpr int FW_LIST_MINB = 6;              // resident blocks per SM of the list kernel (80 registers)
 constexpr float FW_FIX_LIMIT = 65536.f;      // |partial| bound of the exact sum
 
 struct FwTable {
@@ -1000,14 +1002,19 @@ __device__ __forceinline__ void particle_force_list_group(const ForceArgs &a, in
             acc.pair(g, dx, dy, dz, r2, in);
         };
         int p = gl;
-        // two entries of the lane in flight per iteration
-        for (; p + G < cnt; p += 2 * G) {
-            int e0 = __ldcs(list + p), e1 = __ldcs(list + p + G);
-            float4 u0 = a.sp4[e0 & 0xffffff], u1 = a.sp4[e1 & 0xffffff];
-            one(e0, u0);
-            one(e1, u1);
+        // FW_LIST_U entries of the lane in flight per iteration: all entry
+        // loads, then all position loads, then the arithmetic
+        for (; p + (FW_LIST_U - 1) * G < cnt; p += FW_LIST_U * G) {
+            int e[FW_LIST_U];
+            float4 u[FW_LIST_U];
+#pragma unroll
+            for (int q = 0; q < FW_LIST_U; ++q) e[q] = __ldcs(list + p + q * G);
+#pragma unroll
+            for (int q = 0; q < FW_LIST_U; ++q) u[q] = a.sp4[e[q] & 0xffffff];
+#pragma unroll
+            for (int q = 0; q < FW_LIST_U; ++q) one(e[q], u[q]);
         }
-        if (p < cnt) {
+        for (; p < cnt; p += G) {
             int e0 = __ldcs(list + p);
             one(e0, a.sp4[e0 & 0xffffff]);
         }
@@ -1162,7 +1169,7 @@ __global__ void __launch_bounds__(FW_THREADS, 8) k_force_warp(ForceArgs a)
 // Verlet-list forces; runs only on a step that keeps its lists.  A warp
 // takes 32/G consecutive queue items per grab, one per lane group.
 template <bool ENERGY, int G>
-__global__ void __launch_bounds__(FW_THREADS, 8) k_force_list_warp(ForceArgs a)
+__global__ void __launch_bounds__(FW_THREADS, FW_LIST_MINB) k_force_list_warp(ForceArgs a)
 {
     __shared__ FwQueue sq;
     __shared__ int s_run;
