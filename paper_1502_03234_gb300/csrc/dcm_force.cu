@@ -1247,16 +1247,17 @@ int launch_forces(dcm_handle *h, bool energy)
             k_force_warp<false, true><<<g2, FW_THREADS, 0, h->stream>>>(a);
         cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), h->stream);
         const int G = h->tune.list_lanes > 0 ? h->tune.list_lanes : FW_LIST_G;
+        const int gl = h->num_sms * FW_LIST_MINB;   // persistent: the resident blocks
         if (energy) {
-            k_force_list_warp<true, 8><<<g2, FW_THREADS, 0, h->stream>>>(a);   // energy steps are rare
+            k_force_list_warp<true, 8><<<gl, FW_THREADS, 0, h->stream>>>(a);   // energy steps are rare
         } else if (G == 4) {
-            k_force_list_warp<false, 4><<<g2, FW_THREADS, 0, h->stream>>>(a);
+            k_force_list_warp<false, 4><<<gl, FW_THREADS, 0, h->stream>>>(a);
         } else if (G == 16) {
-            k_force_list_warp<false, 16><<<g2, FW_THREADS, 0, h->stream>>>(a);
+            k_force_list_warp<false, 16><<<gl, FW_THREADS, 0, h->stream>>>(a);
         } else if (G == 32) {
-            k_force_list_warp<false, 32><<<g2, FW_THREADS, 0, h->stream>>>(a);
+            k_force_list_warp<false, 32><<<gl, FW_THREADS, 0, h->stream>>>(a);
         } else {
-            k_force_list_warp<false, 8><<<g2, FW_THREADS, 0, h->stream>>>(a);
+            k_force_list_warp<false, 8><<<gl, FW_THREADS, 0, h->stream>>>(a);
         }
         return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "force launch");
     }
