@@ -63,9 +63,13 @@ def test_ensemble_members_equal_single_runs(dcm, prec):
         assert e_mix[k][0] == e_one[0] and e_mix[k][1] == e_one[1]
 
 
-def test_ensemble_members_match_oracle(dcm, orc):
+@pytest.mark.parametrize("prec,skin", [(0, 0.0), (1, 0.5)])
+def test_ensemble_members_match_oracle(dcm, orc, prec, skin):
+    # with Verlet lists (skin 0.5, the benchmark setting) the ensemble shares
+    # one rebuild decision, so a member's lists are rebuilt on a schedule set
+    # by all members: still the same pairs, checked against the oracle
     mem = _members()
-    params = [dcm.default_params(precision=0, rc_max=rcmax) for _, rcmax in mem]
+    params = [dcm.default_params(precision=prec, rc_max=rcmax, skin=skin) for _, rcmax in mem]
     with dcm.Ensemble([s.box for s, _ in mem], [len(s.x) for s, _ in mem], params) as ens:
         for k, (s, _) in enumerate(mem):
             ens.set_system_state(k, s.x, s.v)

@@ -8,8 +8,8 @@ from paper_1502_03234_gb300 import slabgen
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("prec", [0, 1])
-def test_results_same_alone_and_in_the_mix(prec):
+@pytest.mark.parametrize("prec,skin", [(0, None), (1, None), (1, 0.5)])
+def test_results_same_alone_and_in_the_mix(prec, skin):
     import __graft_entry__
 
     __graft_entry__.build()
@@ -22,7 +22,7 @@ def test_results_same_alone_and_in_the_mix(prec):
         return [sv.Job(rid=k, n=n, nsteps=st, box=s.box, x=s.x, v=s.v, arrival=0.0)
                 for k, ((n, st), s) in enumerate(zip(spec, slabs))]
 
-    backend = sv.DcmBackend(precision=prec)
+    backend = sv.DcmBackend(precision=prec, skin=skin)
     mix = jobs()
     rep = sv.Server(backend, budget_bytes=8 << 30, max_slots=4, chunk_steps=10).run(mix, realtime=False)
     assert all(j.status == sv.DONE for j in mix), [j.error for j in mix]
