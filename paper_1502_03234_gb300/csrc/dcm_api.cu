@@ -38,7 +38,7 @@ __global__ void k_aos_to_soa(Batch b, int64_t p0, int64_t n, const double *__res
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const Geom &g = b.sys[sys_of(b.p_off, b.M, p0 + i)];
+    const Geom &g = b.sys[sys_p(b, p0 + i)];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         double v = in[3 * i + a];
@@ -210,9 +210,9 @@ static int64_t bytes_for(const Geom &g, int64_t n, int precision)
 {
     int64_t ncell = g.ncell;
     int64_t nv = g.nvox;
-    int64_t per_p = 3 * 8 * 3 + 8 + 8 + 1 + 4 * 3 + 16 + 4 + 4 + 8 + 48 + 24;
+    int64_t per_p = 3 * 8 * 3 + 8 + 8 + 1 + 4 * 3 + 16 + 4 + 4 + 8 + 48 + 24 + 2;
     per_p += 36;   // spd (FP64) or rq + pk + inv (MIXED)
-    int64_t per_v = 4 + 4 + 4 + 8 + 1 + 8 + 8 + 4 + 16;
+    int64_t per_v = 4 + 4 + 4 + 8 + 1 + 8 + 8 + 4 + 16 + 2;
     int64_t ntiles = (ncell + 2047) / 2048 + 1;
     int64_t lists = g.skin > 0 ? 4 * list_cap(g, n) + n * (4 + 4 + 24 + 8) : 0;
     return n * per_p + ncell * 8 + 8 + nv * per_v + ntiles * 4 + 4096 + 256 * 8 * 8 + lists;
@@ -248,7 +248,7 @@ extern "C" int dcm_destroy(dcm_handle *h)
     for (int q = 0; q <= DCM_NUM_PHASES; ++q)
         if (h->ev[q]) cudaEventDestroy(h->ev[q]);
     void *ptrs[] = {h->x, h->v, h->f, h->d, h->rc, h->cls, h->cell_of, h->slot, h->cell_count,
-                    h->cell_start, h->sorted_id, h->scan_tmp, h->sp4, h->spd, h->rq, h->pk, h->inv, h->class_list,
+                    h->cell_start, h->sorted_id, h->scan_tmp, h->sp4, h->spd, h->rq, h->pk, h->inv, h->psys, h->vsys, h->class_list,
                     h->class_count_dev, h->B, h->sm1, h->sm2, h->Bs, h->S, h->D0, h->D1, h->stamp,
                     h->flist, h->fcount, h->kacc, h->npair, h->pe, h->vir, h->red_part, h->red_out,
                     h->err, h->stats, h->tmp3n, h->geo_dev, h->off_dev, h->nl, h->nl_cnt,
@@ -362,6 +362,10 @@ static int create_systems(int M, const dcm_box *boxes, const int64_t *ns, const 
     ALLOC(h->scan_tmp, ntiles);
     ALLOC(h->sp4, N);
     if (h->p.precision == DCM_FP64) ALLOC(h->spd, N);
+    if (M > 1) {
+        ALLOC(h->psys, N);
+        ALLOC(h->vsys, nv);
+    }
     if (h->p.precision != DCM_FP64) {
         ALLOC(h->rq, N);
         ALLOC(h->pk, N);
@@ -418,6 +422,8 @@ static int create_systems(int M, const dcm_box *boxes, const int64_t *ns, const 
     h->b.p_off = h->off_dev;
     h->b.c_off = h->off_dev + (M + 1);
     h->b.v_off = h->off_dev + 2 * (M + 1);
+    h->b.psys = h->psys;
+    h->b.vsys = h->vsys;
     h->b.M = M;
     h->b.K = h->p.n_classes;
     h->b.N = N;
@@ -432,6 +438,7 @@ static int create_systems(int M, const dcm_box *boxes, const int64_t *ns, const 
     cudaMemsetAsync(h->f, 0, sizeof(double) * 3 * N, h->stream);
     cudaMemsetAsync(h->cls, 0, N, h->stream);
     if (h->inv) launch_iota(h, h->inv, N);       // a valid permutation before the first sort
+    if (M > 1) launch_sys_tables(h);
     if (h->nl) {
         cudaMemsetAsync(h->lflags, 0, sizeof(int) * LF_WORDS, h->stream);
         cudaMemsetAsync(h->lflags + LF_MINHEAD, 0x7f, sizeof(int), h->stream);   // ~3.4e38

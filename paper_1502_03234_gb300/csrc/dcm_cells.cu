@@ -26,7 +26,7 @@ __global__ void k_cell_count(Batch b, const double *__restrict__ x, int32_t *cel
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= b.N || gated_off(gate)) return;
-    const Geom &g = b.sys[sys_of(b.p_off, b.M, i)];
+    const Geom &g = b.sys[sys_p(b, i)];
     int cx = bin_of(x[i], g.inv_c[0], g.nc[0]);
     int cy = bin_of(x[(size_t)b.N + i], g.inv_c[1], g.nc[1]);
     int cz = bin_of(x[2 * (size_t)b.N + i], g.inv_c[2], g.nc[2]);
@@ -133,7 +133,7 @@ __global__ void k_gather(Batch b, const double *__restrict__ x, const int32_t *_
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= b.N || gated_off(gate)) return;
     // sorted slots keep the systems' particle ranges
-    const Geom &g = b.sys[sys_of(b.p_off, b.M, k)];
+    const Geom &g = b.sys[sys_p(b, k)];
     int i = sorted_id[k];
     int c = cell_of[i] - (int)g.c0;
     double px = x[i], py = x[(size_t)b.N + i], pz = x[2 * (size_t)b.N + i];

@@ -36,7 +36,7 @@ __global__ void k_density(Batch b, const double *__restrict__ x, int32_t *B)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= b.N) return;
-    const Geom &g = b.sys[sys_of(b.p_off, b.M, i)];
+    const Geom &g = b.sys[sys_p(b, i)];
     int gx = bin_of(x[i], g.inv_h[0], g.gd[0]);
     int gy = bin_of(x[(size_t)b.N + i], g.inv_h[1], g.gd[1]);
     int gz = bin_of(x[2 * (size_t)b.N + i], g.inv_h[2], g.gd[2]);
@@ -55,7 +55,7 @@ __global__ void k_smooth(Batch b, const TIN *__restrict__ in, TOUT *out, SmoothW
 {
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= b.NV) return;
-    const Geom &g = b.sys[sys_of(b.v_off, b.M, v)];
+    const Geom &g = b.sys[sys_v(b, v)];
     const int nx = g.gd[0], ny = g.gd[1], nz = g.gd[2];
     const int lv = (int)(v - g.v0);              // 32-bit index math
     const int x = lv % nx, yz = lv / nx;
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(256) k_smooth8(Batch b, const TIN *__restrict_
     constexpr uint32_t W[9] = {1, 8, 28, 56, 70, 56, 28, 8, 1};
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= b.NV) return;
-    const Geom &g = b.sys[sys_of(b.v_off, b.M, v)];
+    const Geom &g = b.sys[sys_v(b, v)];
     const int nx = g.gd[0], ny = g.gd[1], nz = g.gd[2];
     const int lv = (int)(v - g.v0);
     int c, n, stride;
@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(DET_THREADS) k_kmeans(KmeansArgs a)
         int cur = -1;
         unsigned long long mx = 0, mn = ~0ull, tot = 0;
         for (int64_t v = lo + threadIdx.x; v < hi; v += blockDim.x) {
-            int s = sys_of(a.b.v_off, M, v);
+            int s = sys_v(a.b, v);
             if (s != cur) {
                 if (cur >= 0) {
                     atomicMax(&s_c0[cur], mx);
@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(DET_THREADS) k_kmeans(KmeansArgs a)
         int cur = -1;
         unsigned long long cnt = 0, sum = 0;
         for (int64_t v = lo + threadIdx.x; v < hi; v += blockDim.x) {
-            int s = sys_of(a.b.v_off, M, v);
+            int s = sys_v(a.b, v);
             if (s != cur) {
                 if (cur >= 0 && cnt) {
                     atomicAdd(&s_c0[cur], cnt);
@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(DET_THREADS) k_kmeans(KmeansArgs a)
         if (s_left == 0) break;
     }
     for (int64_t v = lo + threadIdx.x; v < hi; v += blockDim.x) {
-        int s = sys_of(a.b.v_off, M, v);
+        int s = sys_v(a.b, v);
         a.S[v] = __double_as_longlong(a.Bs[v]) >= __double_as_longlong(s_thr[s]) ? 0 : 1;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -386,7 +386,7 @@ __global__ void k_cfsm_init(Batch b, const uint8_t *__restrict__ S, double *D0, 
     D1[v] = d;
     int st = -1;
     if (!vap) {
-        const Geom &g = b.sys[sys_of(b.v_off, b.M, v)];
+        const Geom &g = b.sys[sys_v(b, v)];
         const int nx = g.gd[0], ny = g.gd[1], nz = g.gd[2];
         const uint8_t *Sg = S + g.v0;
         int lv = (int)(v - g.v0);
@@ -443,7 +443,7 @@ __global__ void __launch_bounds__(DET_THREADS) k_cfsm(CfsmArgs a)
             int npush = 0;
             if (q < nf) {
                 int v = __ldcg(&F[q]);
-                const Geom &g = a.b.sys[sys_of(a.b.v_off, a.b.M, v)];
+                const Geom &g = a.b.sys[sys_v(a.b, v)];
                 const int nx = g.gd[0], ny = g.gd[1], nz = g.gd[2];
                 const int v0 = (int)g.v0;
                 int lv = v - v0;                         // 32-bit index math
@@ -528,7 +528,7 @@ __global__ void k_cutoff(Batch b, const double *__restrict__ x, const double *__
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= b.N) return;
-    const Geom &g = b.sys[sys_of(b.p_off, b.M, i)];
+    const Geom &g = b.sys[sys_p(b, i)];
     const double *D = (*result ? D1 : D0) + g.v0;
     int i0[3], i1[3];
     double t[3];
@@ -602,7 +602,7 @@ __global__ void k_classify_rc(Batch b, const double *__restrict__ rc, uint8_t *c
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= b.N) return;
-    const Geom &g = b.sys[sys_of(b.p_off, b.M, i)];
+    const Geom &g = b.sys[sys_p(b, i)];
     double r = rc[i];
     int c = 0;
     if (r > g.rc_min) {

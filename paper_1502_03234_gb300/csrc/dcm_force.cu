@@ -248,7 +248,7 @@ __device__ __forceinline__ void reduce_and_store(const ForceArgs &a, Acc<PREC, E
 template <int PREC, bool ENERGY>
 __device__ __forceinline__ void particle_force(const ForceArgs &a, int k, int lane, int G, unsigned gmask, int &ng)
 {
-    const Geom &g = a.b.sys[sys_of(a.b.p_off, a.b.M, k)];
+    const Geom &g = a.b.sys[sys_p(a.b, k)];
     int i = a.sorted_id[k];
     float4 ui = a.sp4[k];
     int c = a.cell_of[i] - (int)g.c0;
@@ -318,7 +318,7 @@ template <int PREC, bool ENERGY>
 __device__ __forceinline__ void particle_force_list(const ForceArgs &a, int k, int lane, int G,
                                                     unsigned gmask, int &ng)
 {
-    const Geom &g = a.b.sys[sys_of(a.b.p_off, a.b.M, k)];
+    const Geom &g = a.b.sys[sys_p(a.b, k)];
     int i = a.sorted_id[k];
     float4 ui = a.sp4[k];
     double rci = a.rc[i];
@@ -426,7 +426,7 @@ template <bool FILL>
 __device__ __forceinline__ void list_particle(const ForceArgs &a, int k, int lane, int G,
                                               unsigned gmask)
 {
-    const Geom &g = a.b.sys[sys_of(a.b.p_off, a.b.M, k)];
+    const Geom &g = a.b.sys[sys_p(a.b, k)];
     int i = a.sorted_id[k];
     float4 ui = a.sp4[k];
     int c = a.cell_of[i] - (int)g.c0;
@@ -779,7 +779,7 @@ __device__ __forceinline__ void particle_force_warp(const ForceArgs &a, FwTable 
                                                     int lane, int &ng, bool fill_on,
                                                     long long &entries)
 {
-    const Geom &g = a.b.sys[sys_of(a.b.p_off, a.b.M, k)];
+    const Geom &g = a.b.sys[sys_p(a.b, k)];
     const float4 ui = a.sp4[k];
     const float4 q4 = a.rq[k];
     const int4 pk = a.pk[k];
@@ -973,7 +973,7 @@ __device__ __forceinline__ void particle_force_list_group(const ForceArgs &a, in
     WarpAcc<ENERGY> acc;
     int i = 0;
     if (k >= 0) {
-        const Geom &g = a.b.sys[sys_of(a.b.p_off, a.b.M, k)];
+        const Geom &g = a.b.sys[sys_p(a.b, k)];
         const float4 ui = a.sp4[k];
         const float4 q4 = a.rq[k];
         i = a.pk[k].x;

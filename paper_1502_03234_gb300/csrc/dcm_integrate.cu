@@ -19,7 +19,7 @@ __global__ void k_kick_drift(Batch b, double *__restrict__ x, double *__restrict
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= b.N) return;
-    const Geom &g = b.sys[sys_of(b.p_off, b.M, i)];
+    const Geom &g = b.sys[sys_p(b, i)];
     int bad = 0;
     double xn[3];
 #pragma unroll
@@ -54,7 +54,7 @@ __global__ void k_kick(Batch b, double *__restrict__ v, const double *__restrict
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= b.N) return;
-    const double hdtm = b.sys[sys_of(b.p_off, b.M, i)].hdtm;
+    const double hdtm = b.sys[sys_p(b, i)].hdtm;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         size_t o = (size_t)a * b.N + i;
@@ -143,6 +143,21 @@ int launch_kick_drift(dcm_handle *h)
     k_kick_drift<<<nblk(h->n, 256), 256, 0, h->stream>>>(h->b, h->x, h->v, h->f, h->err,
                                                          wl ? h->sp4 : nullptr, h->inv, h->cell_of);
     return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "kick_drift launch");
+}
+
+__global__ void k_sys_table(const int64_t *__restrict__ off, int M, int64_t n, uint16_t *out)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (uint16_t)sys_of(off, M, i);
+}
+
+// the system of every particle and voxel, once at creation
+void launch_sys_tables(dcm_handle *h)
+{
+    const int M = h->M;
+    k_sys_table<<<nblk(h->n, 256), 256, 0, h->stream>>>(h->off_dev, M, h->n, h->psys);
+    k_sys_table<<<nblk(h->nvox, 256), 256, 0, h->stream>>>(h->off_dev + 2 * (M + 1), M, h->nvox,
+                                                            h->vsys);
 }
 
 void launch_iota(dcm_handle *h, int32_t *p, int64_t n)

@@ -104,10 +104,16 @@ struct Batch {
     const int64_t *p_off;        // [M+1] particle offsets
     const int64_t *c_off;        // [M+1] cell offsets
     const int64_t *v_off;        // [M+1] voxel offsets
+    const uint16_t *psys;        // [N] system of each particle (null when M == 1)
+    const uint16_t *vsys;        // [NV] system of each voxel (null when M == 1)
     int M;
     int K;                       // cutoff classes (same for all systems)
     int64_t N, NC, NV;           // totals
 };
+
+// system of particle i / voxel v: a table lookup (M == 1: system 0)
+__device__ __forceinline__ int sys_p(const Batch &b, int64_t i) { return b.M == 1 ? 0 : (int)b.psys[i]; }
+__device__ __forceinline__ int sys_v(const Batch &b, int64_t v) { return b.M == 1 ? 0 : (int)b.vsys[v]; }
 
 // system owning element idx of a concatenated array (largest s with off[s] <= idx)
 __device__ __forceinline__ int sys_of(const int64_t *off, int M, int64_t idx)
@@ -158,6 +164,7 @@ struct dcm_handle {
     double4_32a *spd;
     float4 *rq;                  // MIXED: per sorted slot r_c^2, guard band, culling radius
     int32_t *inv;                // sorted slot of each particle (id order), MIXED
+    uint16_t *psys, *vsys;       // system of each particle / voxel (M > 1)
     int4 *pk;                    // MIXED: per sorted slot particle id, cell y, cell z
     int32_t *class_list;         // sorted slots grouped by class
     int32_t *class_count_dev;    // [K] counts, [K..2K) cursors
@@ -221,6 +228,7 @@ int launch_bin(dcm_handle *h);                      // full cell sort + classes
 int launch_bin_gated(dcm_handle *h, const int *gate, const int *class_gate);  // sort, gather, classes
 void list_mode(dcm_handle *h);          // sets list_warp from precision, tuning and lists
 void launch_iota(dcm_handle *h, int32_t *p, int64_t n);
+void launch_sys_tables(dcm_handle *h);
 int launch_scan(dcm_handle *h, const int32_t *in, int32_t *out, int32_t *tiles, int64_t m,
                 int32_t total, const int *gate);     // exclusive scan (total < 0: out[m] = sum)
 int launch_list_step(dcm_handle *h, bool force_rebuild);  // decide, [rebin], lists

@@ -40,7 +40,7 @@ __global__ void k_list_check(Batch b, const double *__restrict__ x, const double
         float dz = (float)(x[2 * N + i] - x_ref[2 * N + i]);
         // a coordinate wrapped through the box shows up as a jump of about
         // one box edge: fold it back (moves are far below half an edge)
-        const Geom &g = b.sys[sys_of(b.p_off, b.M, i)];
+        const Geom &g = b.sys[sys_p(b, i)];
         float Lx = (float)g.L[0], Ly = (float)g.L[1], Lz = (float)g.L[2];
         dx -= Lx * rintf(dx / Lx);
         dy -= Ly * rintf(dy / Ly);
