@@ -1,0 +1,90 @@
+"""GPU parity on the degenerate inputs of the method: a box with no
+interface (all vapor: dilute gas; all liquid: a dense lattice filling the
+box), the smallest box the default stencil allows, and an empty system.
+Labels, classes and pair counts bit-exact, distances within 1e-12, forces
+within the mixed-precision bound, against the FP64 oracle."""
+import numpy as np
+import pytest
+
+from paper_1502_03234_gb300 import slabgen
+
+pytestmark = pytest.mark.gpu
+
+FP64_REL, FP64_ABS = 1e-5, 1e-6
+
+
+@pytest.fixture(scope="module")
+def dcm():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1502_03234_gb300 import dcm as d
+
+    return d
+
+
+def _fcc(cells, a, jitter, seed):
+    rng = np.random.default_rng(seed)
+    base = np.array([[0, 0, 0], [0.5, 0.5, 0], [0.5, 0, 0.5], [0, 0.5, 0.5]])
+    g = np.stack(np.meshgrid(np.arange(cells), np.arange(cells), np.arange(cells),
+                             indexing="ij"), -1).reshape(-1, 1, 3)
+    x = ((g + base[None]) * a).reshape(-1, 3)
+    x += rng.uniform(-jitter, jitter, x.shape)
+    box = (cells * a,) * 3
+    return np.mod(x, box[0]), box
+
+
+def _check(dcm, orc, x, v, box, prec, skin=0.0):
+    n = len(x)
+    with dcm.System(box, n, precision=prec, skin=skin) as sy:
+        sy.set_state(x, v)
+        sy.detect_interface()
+        sy.compute_forces()
+        xg, _, f = sy.get_state()
+        dims, B, Bs, S, D = sy.grid()
+        d, rc, cls = sy.cutoffs()
+        npair = sy.pair_counts()
+        nc, _, _ = sy.cells()
+    det = orc.detect(xg, box, orc.DetectParams(rc_min=3.0, rc_max=6.0, voxel=1.0))
+    assert np.array_equal(B, det.B)
+    assert np.array_equal(S, det.S)
+    np.testing.assert_allclose(D, det.D, atol=1e-12, rtol=0)
+    np.testing.assert_allclose(d, det.d, atol=1e-12, rtol=0)
+    assert np.array_equal(cls, det.cls)
+    ref = orc.forces(xg, rc, box, nc)
+    assert np.array_equal(npair, ref.npair)
+    err = np.linalg.norm(f - ref.f, axis=1)
+    fmag = np.linalg.norm(ref.f, axis=1)
+    extra = 0.0 if prec == dcm.DCM_FP64 else 5e-4
+    assert np.all(err <= FP64_ABS + FP64_REL * fmag + extra), err.max()
+    return S
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_all_vapor_box(dcm, orc, prec):
+    box = (22.0, 22.0, 22.0)
+    x, v = slabgen.make_gas(600, box, seed=51)
+    _check(dcm, orc, x, v, box, prec)
+
+
+@pytest.mark.parametrize("prec,skin", [(0, 0.0), (1, 0.0), (1, 0.5)])
+def test_all_liquid_box(dcm, orc, prec, skin):
+    x, box = _fcc(10, slabgen.fcc_edge(0.8), 0.05, seed=52)       # 4000 atoms, no vapor
+    rng = np.random.default_rng(53)
+    v = rng.normal(0.0, np.sqrt(0.7), x.shape)
+    _check(dcm, orc, x, v, box, prec, skin)
+
+
+@pytest.mark.parametrize("edge,skin", [(13.6, 0.0), (16.6, 0.5)])
+def test_smallest_box_for_the_stencil(dcm, orc, edge, skin):
+    # the cell stencil must not wrap onto itself: 2 s_max + 1 <= cells per
+    # edge, with s_max the stencil of r_c,max (+ skin with Verlet lists):
+    # 9 cells of 1.5 sigma for r_c,max = 6, 11 for 6.5
+    s = slabgen.make_slab(2048, seed=54, min_edge=edge)
+    _check(dcm, orc, s.x, s.v, s.box, 1, skin)
+
+
+def test_empty_system_is_rejected(dcm):
+    with pytest.raises(dcm.DcmError) as e:
+        dcm.System((20.0, 20.0, 80.0), 0)
+    assert e.value.code == dcm.DCM_ERR_ARG
