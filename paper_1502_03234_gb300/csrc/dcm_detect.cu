@@ -31,6 +31,8 @@
 namespace dcm {
 
 constexpr int DET_THREADS = 256;
+constexpr int CFSM_TAIL_CTAS = 8;           // one portable cluster
+constexpr int CFSM_TAIL_THREADS = 512;
 
 __global__ void k_density(Batch b, const double *__restrict__ x, int32_t *B)
 {
@@ -414,102 +416,144 @@ struct CfsmArgs {
     int32_t *lists;           // 4 * cap
     int32_t *fcount;          // 4 counters
     int *result;              // which buffer holds the result
+    int *kpass;               // first pass of the tail kernel
+    int nf_switch;            // frontier size below which the tail kernel runs
     unsigned int *bar;
     int *err;
     DevStats *st;
 };
 
+// one pass k of the frontier iteration: items q = tid, tid + nth, ... of
+// frontier list k & 3 (nf items), pushes into list (k + 1) & 3
+__device__ __forceinline__ void cfsm_pass(const CfsmArgs &a, int k, int nf, int64_t tid, int64_t nth)
+{
+    const double *X = (k & 1) ? a.D1 : a.D0;
+    double *Y = (k & 1) ? a.D0 : a.D1;
+    int32_t *F = a.lists + (int64_t)(k & 3) * a.cap;
+    int32_t *Fn = a.lists + (int64_t)((k + 1) & 3) * a.cap;
+    if (tid == 0) a.fcount[(k + 2) & 3] = 0;   // list two passes ahead
+    const int lane = (int)(threadIdx.x & 31);
+    for (int64_t q0 = tid - lane; q0 < nf; q0 += nth) {
+        int q = (int)q0 + lane;
+        int32_t push[7];
+        int npush = 0;
+        if (q < nf) {
+            int v = __ldcg(&F[q]);
+            const Geom &g = a.b.sys[sys_v(a.b, v)];
+            const int nx = g.gd[0], ny = g.gd[1], nz = g.gd[2];
+            const int v0 = (int)g.v0;
+            int lv = v - v0;                         // 32-bit index math
+            int x = lv % nx, yz = lv / nx;
+            int y = yz % ny, z = yz / ny;
+            int xm = x ? x - 1 : nx - 1, xp = x + 1 < nx ? x + 1 : 0;
+            int ym = y ? y - 1 : ny - 1, yp = y + 1 < ny ? y + 1 : 0;
+            int zm = z ? z - 1 : nz - 1, zp = z + 1 < nz ? z + 1 : 0;
+            int nb[6] = {v0 + xm + nx * yz, v0 + xp + nx * yz,
+                         v0 + x + nx * (ym + ny * z), v0 + x + nx * (yp + ny * z),
+                         v0 + x + nx * (y + ny * zm), v0 + x + nx * (y + ny * zp)};
+            // D and the lists were written by other blocks in the previous
+            // pass: read them through L2 (ld.global.cg), not a stale L1
+            double old = __ldcg(&X[v]);
+            double ax = dmin_nonneg(__ldcg(&X[nb[0]]), __ldcg(&X[nb[1]]));
+            double ay = dmin_nonneg(__ldcg(&X[nb[2]]), __ldcg(&X[nb[3]]));
+            double az = dmin_nonneg(__ldcg(&X[nb[4]]), __ldcg(&X[nb[5]]));
+            // the labels of the face neighbours, loaded with the distances
+            // (read-only in this kernel) so the push below waits on nothing
+            bool liq[7];
+            liq[0] = true;
+#pragma unroll
+            for (int e = 1; e < 7; ++e) liq[e] = __ldg(&a.S[nb[e - 1]]) == 0;
+            // any Godunov solution is at least min(a) + 1/sqrt(sum w): when
+            // that cannot beat the current value the solve is skipped
+            // (a lower bound with a relative margin, so no update is lost)
+            double amin = dmin_nonneg(ax, dmin_nonneg(ay, az));
+            bool changed = false;
+            double dbar = old;
+            if (!isinf(amin) &&
+                __double_as_longlong(old) > __double_as_longlong(amin + 0.999999 * g.e_min)) {
+                dbar = godunov_w(ax, ay, az, g.h[0], g.h[1], g.h[2], g.w_h[0], g.w_h[1], g.w_h[2]);
+                // non-negative doubles: compare the bit patterns
+                changed = __double_as_longlong(dbar) < __double_as_longlong(old) &&
+                          __double_as_longlong(dbar) <= __double_as_longlong(g.r_grid);
+            }
+            Y[v] = changed ? dbar : old;
+            if (changed) {
+                // the voxel itself (so Y catches up next pass) and its
+                // liquid face neighbours are recomputed in the next pass;
+                // the seven stamp exchanges are independent of each other
+                int cand[7] = {v, nb[0], nb[1], nb[2], nb[3], nb[4], nb[5]};
+                int prev[7];
+#pragma unroll
+                for (int e = 0; e < 7; ++e) prev[e] = liq[e] ? atomicExch(&a.stamp[cand[e]], k + 1) : k + 1;
+#pragma unroll
+                for (int e = 0; e < 7; ++e)
+                    if (prev[e] != k + 1) push[npush++] = cand[e];
+            }
+        }
+        // one append per warp: exclusive scan of the lanes' counts
+        int incl = npush;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += t;
+        }
+        int total = __shfl_sync(0xffffffffu, incl, 31);
+        if (total) {
+            int base = 0;
+            if (lane == 31) base = atomicAdd(&a.fcount[(k + 1) & 3], total);
+            base = __shfl_sync(0xffffffffu, base, 31) + incl - npush;
+            for (int e = 0; e < npush; ++e) Fn[base + e] = push[e];
+        }
+    }
+}
+
+// the passes over large frontiers, all SMs, a grid barrier between passes;
+// once the frontier falls below nf_switch the tail kernel takes over (its
+// passes are short latency chains that a grid barrier would dominate)
 __global__ void __launch_bounds__(DET_THREADS) k_cfsm(CfsmArgs a)
 {
-    int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
     int k = 0;
+    for (; k < a.iter_max; ++k) {
+        const int nf = ((volatile int32_t *)a.fcount)[k & 3];
+        if (nf < a.nf_switch) break;             // (also nf == 0: converged)
+        cfsm_pass(a, k, nf, tid, nth);
+        if (!grid_barrier(a.bar, a.err)) return;
+    }
+    if (tid == 0) *a.kpass = k;
+}
+
+__device__ __forceinline__ void cluster_sync_all()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n"
+                 "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ unsigned cluster_rank()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// the remaining passes in one thread-block cluster: the hardware cluster
+// barrier replaces the grid barrier; ends the iteration (result, statistics,
+// the not-converged flag)
+__global__ void __launch_bounds__(CFSM_TAIL_THREADS) k_cfsm_tail(CfsmArgs a)
+{
+    const int64_t tid = (int64_t)cluster_rank() * blockDim.x + threadIdx.x;
+    const int64_t nth = (int64_t)CFSM_TAIL_CTAS * blockDim.x;
+    int k = __ldcg(a.kpass);
     bool converged = false;
     for (; k < a.iter_max; ++k) {
-        const double *X = (k & 1) ? a.D1 : a.D0;
-        double *Y = (k & 1) ? a.D0 : a.D1;
-        int32_t *F = a.lists + (int64_t)(k & 3) * a.cap;
-        int32_t *Fn = a.lists + (int64_t)((k + 1) & 3) * a.cap;
-        int nf = ((volatile int32_t *)a.fcount)[k & 3];
+        const int nf = ((volatile int32_t *)a.fcount)[k & 3];
         if (nf == 0) {
             converged = true;
             break;
         }
-        if (tid == 0) a.fcount[(k + 2) & 3] = 0;   // list two passes ahead
-        const int lane = (int)(threadIdx.x & 31);
-        for (int64_t q0 = tid - lane; q0 < nf; q0 += nth) {
-            int q = (int)q0 + lane;
-            int32_t push[7];
-            int npush = 0;
-            if (q < nf) {
-                int v = __ldcg(&F[q]);
-                const Geom &g = a.b.sys[sys_v(a.b, v)];
-                const int nx = g.gd[0], ny = g.gd[1], nz = g.gd[2];
-                const int v0 = (int)g.v0;
-                int lv = v - v0;                         // 32-bit index math
-                int x = lv % nx, yz = lv / nx;
-                int y = yz % ny, z = yz / ny;
-                int xm = x ? x - 1 : nx - 1, xp = x + 1 < nx ? x + 1 : 0;
-                int ym = y ? y - 1 : ny - 1, yp = y + 1 < ny ? y + 1 : 0;
-                int zm = z ? z - 1 : nz - 1, zp = z + 1 < nz ? z + 1 : 0;
-                int nb[6] = {v0 + xm + nx * yz, v0 + xp + nx * yz,
-                             v0 + x + nx * (ym + ny * z), v0 + x + nx * (yp + ny * z),
-                             v0 + x + nx * (y + ny * zm), v0 + x + nx * (y + ny * zp)};
-                // D and the lists were written by other blocks in the previous
-                // pass: read them through L2 (ld.global.cg), not a stale L1
-                double old = __ldcg(&X[v]);
-                double ax = dmin_nonneg(__ldcg(&X[nb[0]]), __ldcg(&X[nb[1]]));
-                double ay = dmin_nonneg(__ldcg(&X[nb[2]]), __ldcg(&X[nb[3]]));
-                double az = dmin_nonneg(__ldcg(&X[nb[4]]), __ldcg(&X[nb[5]]));
-                // the labels of the face neighbours, loaded with the distances
-                // (read-only in this kernel) so the push below waits on nothing
-                bool liq[7];
-                liq[0] = true;
-#pragma unroll
-                for (int e = 1; e < 7; ++e) liq[e] = __ldg(&a.S[nb[e - 1]]) == 0;
-                // any Godunov solution is at least min(a) + 1/sqrt(sum w): when
-                // that cannot beat the current value the solve is skipped
-                // (a lower bound with a relative margin, so no update is lost)
-                double amin = dmin_nonneg(ax, dmin_nonneg(ay, az));
-                bool changed = false;
-                double dbar = old;
-                if (!isinf(amin) &&
-                    __double_as_longlong(old) > __double_as_longlong(amin + 0.999999 * g.e_min)) {
-                    dbar = godunov_w(ax, ay, az, g.h[0], g.h[1], g.h[2], g.w_h[0], g.w_h[1], g.w_h[2]);
-                    // non-negative doubles: compare the bit patterns
-                    changed = __double_as_longlong(dbar) < __double_as_longlong(old) &&
-                              __double_as_longlong(dbar) <= __double_as_longlong(g.r_grid);
-                }
-                Y[v] = changed ? dbar : old;
-                if (changed) {
-                    // the voxel itself (so Y catches up next pass) and its
-                    // liquid face neighbours are recomputed in the next pass;
-                    // the seven stamp exchanges are independent of each other
-                    int cand[7] = {v, nb[0], nb[1], nb[2], nb[3], nb[4], nb[5]};
-                    int prev[7];
-#pragma unroll
-                    for (int e = 0; e < 7; ++e) prev[e] = liq[e] ? atomicExch(&a.stamp[cand[e]], k + 1) : k + 1;
-#pragma unroll
-                    for (int e = 0; e < 7; ++e)
-                        if (prev[e] != k + 1) push[npush++] = cand[e];
-                }
-            }
-            // one append per warp: exclusive scan of the lanes' counts
-            int incl = npush;
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                int t = __shfl_up_sync(0xffffffffu, incl, off);
-                if (lane >= off) incl += t;
-            }
-            int total = __shfl_sync(0xffffffffu, incl, 31);
-            if (total) {
-                int base = 0;
-                if (lane == 31) base = atomicAdd(&a.fcount[(k + 1) & 3], total);
-                base = __shfl_sync(0xffffffffu, base, 31) + incl - npush;
-                for (int e = 0; e < npush; ++e) Fn[base + e] = push[e];
-            }
-        }
-        if (!grid_barrier(a.bar, a.err)) return;
+        cfsm_pass(a, k, nf, tid, nth);
+        cluster_sync_all();
     }
     if (tid == 0) {
         // after pass k-1 the current values are in the buffer it wrote
@@ -758,6 +802,8 @@ int launch_detect(dcm_handle *h)
         a.lists = h->flist;
         a.fcount = h->fcount;
         a.result = (int *)&h->stats->barrier[3];
+        a.kpass = (int *)&h->stats->barrier[4];
+        a.nf_switch = 256;          // measured: 262k, 2M and ensemble detection all best here
         a.bar = h->stats->barrier;
         a.err = h->err;
         a.st = h->stats;
@@ -768,6 +814,21 @@ int launch_detect(dcm_handle *h)
         int grid = h->num_sms;
         int rc = coop_launch(h, (const void *)k_cfsm, grid, 0, args);
         if (rc) return rc;
+        // the small frontiers of the last passes: one cluster of 8 SMs
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(CFSM_TAIL_CTAS);
+        cfg.blockDim = dim3(CFSM_TAIL_THREADS);
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = CFSM_TAIL_CTAS;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaError_t e = cudaLaunchKernelExC(&cfg, (const void *)k_cfsm_tail, args);
+        if (e != cudaSuccess) return fail_cuda(e, "cfsm tail launch", __FILE__, __LINE__);
+        h->kernels += 1;
     }
     // Algorithm 3.1 + Eq. 7
     const bool wl = h->nl && h->list_warp;

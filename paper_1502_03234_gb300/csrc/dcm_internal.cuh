@@ -56,7 +56,8 @@ struct DevStats {
     double c_liquid;             // system 0
     double c_vapor;
     int class_count[DCM_MAX_CLASSES];
-    unsigned int barrier[4];     // [0..1] grid barrier, [2] force queue, [3] CFSM result buffer
+    unsigned int barrier[6];     // [0..1] grid barrier, [2] force queue, [3] CFSM result buffer,
+                                 // [4] first CFSM pass of the cluster tail
     unsigned long long list_builds;
     unsigned long long list_entries;
 };
