@@ -79,14 +79,6 @@ __device__ __forceinline__ bool fp64_inside(const ForceArgs &a, const Geom &g, i
     return r2_rn(dx, dy, dz) < rci2;
 }
 
-// the same decision out of line, for kernels that keep registers for the
-// common path (it runs for ~1e-4 of the candidates)
-__device__ __noinline__ bool fp64_inside_rc(const ForceArgs &a, const Geom &g, int i, int j)
-{
-    double rci = a.rc[i];
-    return fp64_inside(a, g, i, a.sorted_id[j], DMUL(rci, rci));
-}
-
 template <int PREC, bool ENERGY>
 struct Acc;
 
