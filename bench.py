@@ -35,6 +35,7 @@ import math
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -85,6 +86,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--skin", type=float, default=0.5,
                     help="Verlet-list skin in sigma (0: direct link-cell walk every step)")
+    ap.add_argument("--list-margin", type=float, default=1.0,
+                    help="interface-distance margin of the Verlet-list radius in sigma")
     ap.add_argument("--workload", default="slab", choices=["slab", "wavy", "ensemble", "serving"])
     ap.add_argument("--sweep", default="131072,262144,524288,1048576",
                     help="wavy: further N of the weak-scaling sweep")
@@ -122,7 +125,9 @@ class Clocks:
     def __init__(self, gpu_index=0):
         self.idx = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # raw samples: $DCM_CLOCKS_DIR (default: the temp directory)
+        out = os.environ.get("DCM_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out, f"clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
@@ -231,9 +236,30 @@ def run_reference(args):
 
 
 # ---- further workloads (one GPU) -------------------------------------------------------
+def _launches(st, kinds):
+    """kernels the timed steps launched: each step is one CUDA graph whose
+    kernel count depends on detection and, with Verlet lists, on whether the
+    step rebuilt them (the rebuild-only kernels sit in conditional nodes)"""
+    n = 0
+    for det, rebuilt in kinds:
+        if det:
+            n += st.kernels_detect if rebuilt else st.kernels_detect_reuse
+        else:
+            n += st.kernels_plain if rebuilt else st.kernels_plain_reuse
+    return n
+
+
+def _kind(sy, builds_before):
+    """(detected, rebuilt) of the step just run"""
+    st = sy.stats()
+    every = sy.params.detect_every
+    return (every > 0 and st.step % every == 0, st.list_builds != builds_before), st.list_builds
+
+
 def _timed(sy, stream, flush, k, warm):
     """per-step device times (ms) with L2 flushed before each step, and the
-    per-phase sums of the library's own step events"""
+    per-phase sums of the library's own step events; the steps' kinds go to
+    _timed.kinds"""
     import torch
 
     for _ in range(warm):
@@ -241,7 +267,8 @@ def _timed(sy, stream, flush, k, warm):
             flush.zero_()
         sy.step(1)
     sy.sync()
-    out, phase = [], {}
+    out, phase, kinds = [], {}, []
+    builds = sy.stats().list_builds
     for _ in range(k):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -255,6 +282,9 @@ def _timed(sy, stream, flush, k, warm):
             phase[key] = phase.get(key, 0.0) + val / k
         e1.synchronize()
         out.append(e0.elapsed_time(e1))
+        kind, builds = _kind(sy, builds)
+        kinds.append(kind)
+    _timed.kinds = kinds
     return out, phase
 
 
@@ -329,8 +359,7 @@ def run_workload(args):
             ens.set_timing(True)
             ms, ph = _timed(ens, stream, flush, args.steps, args.warmup)
             st = ens.stats()
-            kernels = st.kernels_plain * (args.steps - args.steps // 2) + \
-                st.kernels_detect * (args.steps // 2)
+            kernels = _launches(st, _timed.kinds)
             ens.close()
             ntot = sum(ns)
             value = ntot * args.steps / (sum(ms) * 1e-3)
@@ -403,7 +432,7 @@ def main():
 
     def make_system(precision):
         sy = dcm.System(slab.box, n, precision=precision, stream=stream.cuda_stream,
-                        skin=args.skin)
+                        skin=args.skin, list_margin=args.list_margin)
         sy.set_state(slab.x, slab.v)
         sy.compute_forces()
         sy.set_timing(True)
@@ -418,7 +447,7 @@ def main():
         sy.sync()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(k)]
-        force_ms, phase_sum, rebuilt = [], {}, []
+        force_ms, phase_sum, rebuilt, kinds = [], {}, [], []
         b_prev = sy.stats().list_builds
         for q in range(k):
             with torch.cuda.stream(stream):
@@ -429,13 +458,15 @@ def main():
                 ev[q][1].record(stream)
             ph = sy.phase_times()                       # waits for this step
             force_ms.append(ph["force"])
-            b_now = sy.stats().list_builds               # (outside the timed events)
+            kind, b_now = _kind(sy, b_prev)              # (outside the timed events)
+            kinds.append(kind)
             rebuilt.append(b_now != b_prev)
             b_prev = b_now
             for key, val in ph.items():
                 phase_sum[key] = phase_sum.get(key, 0.0) + val
         sy.sync()
         timed_steps.rebuilt = rebuilt
+        timed_steps.kinds = kinds
         return [a.elapsed_time(b) for a, b in ev], force_ms, phase_sum
 
     sy = make_system(prec)
@@ -450,7 +481,7 @@ def main():
     total_ms = sum(step_ms)
     st = sy.stats()
     pairs = st.pairs
-    kernels = (st.kernels_plain * (args.steps - args.steps // 2) + st.kernels_detect * (args.steps // 2))
+    kernels = _launches(st, timed_steps.kinds)
     x_end, _, _ = sy.get_state()
     if not np.all(np.isfinite(x_end)):
         raise RuntimeError("non-finite positions after the timed run")
@@ -558,6 +589,7 @@ def main():
         p99 = sms[min(len(sms) - 1, int(math.ceil(0.99 * len(sms))) - 1)]
         cfg = workload_config(n, args.precision)
         cfg["skin"] = args.skin
+        cfg["list_margin"] = args.list_margin
         cfg["phase_ms_avg"] = {k: v / args.steps for k, v in phase_sum.items()}
         cfg["fp64_gpu_path"] = fp64_info
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,

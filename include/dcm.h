@@ -87,12 +87,13 @@ typedef struct {
     double cell_min;                       /* link-cell edge target; <= 0: auto */
     /* Verlet-list skin r_s in sigma (Section 2.2.1, Algorithm 3.3).  0: walk
        the link cells directly every step.  > 0: each particle keeps a list
-       of every j within r_c[i] + skin, rebuilt (with a fresh cell sort)
-       when 2 x (largest displacement since the build) + (largest growth of
-       a cutoff since the build) reaches the skin, or when the list storage
-       would overflow (that step falls back to the direct walk).  Requires
-       at most 2^24 particles per handle and a stencil of at most 7 cells
-       in y and z. */
+       of every j within its list radius R_i (r_c[i] + skin, see
+       list_margin), rebuilt (with a fresh cell sort) once some particle's
+       displacement since the build plus the largest displacement reaches
+       its headroom R_i - r_c[i](t), or when the list storage would
+       overflow (that step falls back to the direct walk).  Requires at most
+       2^24 particles per handle and a stencil of at most 7 cells in y and
+       z. */
     double skin;
     /* Verlet lists built by the warp walk (DCM_MIXED, DCM_WALK_WARP): each
        particle's entry capacity is list_density x (4/3) pi R^3 + 8 for its
@@ -100,7 +101,13 @@ typedef struct {
        leaves that step's forces to the direct walk and raises the density
        by 25 % for the next build (per handle: system 0's value). */
     float list_density;
-    int32_t reserved[5];
+    /* With detected cutoffs, each list radius is the cutoff the particle
+       would get if its interface distance fell by list_margin sigma, plus
+       the skin, so that the jitter of the detected interface does not force
+       a rebuild at every detection.  0: 1 sigma; < 0: no margin (per
+       handle: system 0's value). */
+    float list_margin;
+    int32_t reserved[4];
 } dcm_params;
 
 /* Force walk variants (dcm_tuning.walk).  DCM_WALK_WARP: one warp per
@@ -130,11 +137,17 @@ typedef struct {
     int32_t cells[3];                      /* link-cell grid */
     double c_liquid, c_vapor;              /* Eq. 14 cluster centres */
     int64_t guard_rechecks;                /* MIXED: FP64 re-decided pairs */
-    int32_t kernels_plain;                 /* kernels one step launches */
+    int32_t kernels_plain;                 /* kernels one step launches (with
+                                              Verlet lists: a step that rebuilds
+                                              them) */
     int32_t kernels_detect;                /* ... in a step with detection */
     int64_t list_builds;                   /* Verlet-list builds so far */
     int64_t list_entries;                  /* entries of the current lists */
-    int64_t reserved[3];
+    int32_t kernels_plain_reuse;           /* kernels of a step that reuses its
+                                              Verlet lists (= kernels_plain
+                                              without lists) */
+    int32_t kernels_detect_reuse;          /* ... in a step with detection */
+    int64_t reserved[2];
 } dcm_stats;
 
 /* Phases of one step, in order, for dcm_get_phase_times. */

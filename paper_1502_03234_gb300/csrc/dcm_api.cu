@@ -85,6 +85,7 @@ extern "C" void dcm_default_params(dcm_params *p)
     p->kmeans_max_iter = 100;
     p->cfsm_iter_max = 0;
     p->list_density = 1.0f;
+    p->list_margin = 1.0f;
     p->cfsm_eps = 0.0;
     p->precision = DCM_FP64;
     p->n_classes = 4;
@@ -256,6 +257,7 @@ extern "C" int dcm_destroy(dcm_handle *h)
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    if (h->side) cudaStreamDestroy(h->side);
     delete[] h->geo_host;
     delete[] h->par_host;
     delete[] h->off_host;
@@ -441,10 +443,12 @@ static int create_systems(int M, const dcm_box *boxes, const int64_t *ns, const 
     if (M > 1) launch_sys_tables(h);
     if (h->nl) {
         cudaMemsetAsync(h->lflags, 0, sizeof(int) * LF_WORDS, h->stream);
-        cudaMemsetAsync(h->lflags + LF_MINHEAD, 0x7f, sizeof(int), h->stream);   // ~3.4e38
+        cudaMemsetAsync(h->lflags + LF_EXCESS, 0x80, sizeof(int), h->stream);    // LF_EXCESS_RESET
         // capacity density of the warp list fill (float bits); a host member
         // so the asynchronous copy reads live memory
         h->list_scale0 = h->par_host[0].list_density > 0.f ? h->par_host[0].list_density : 1.0f;
+        const float lm = h->par_host[0].list_margin;
+        h->list_margin = lm > 0.f ? lm : (lm < 0.f ? 0.f : 1.0f);
         cudaMemcpyAsync(h->lflags + LF_SCALE, &h->list_scale0, sizeof(float), cudaMemcpyHostToDevice,
                         h->stream);
         cudaMemsetAsync(h->x_ref, 0, sizeof(double) * 3 * N, h->stream);
@@ -651,10 +655,97 @@ static void mark(dcm_handle *h, int q, bool capturing)
         cudaEventRecord(h->ev[q], h->stream);
 }
 
+// ---- conditional branches of a captured step ----------------------------
+namespace dcm {
+
+int branch_open(dcm_handle *h, Branch &b, int nbody, int which)
+{
+    b.active = false;
+    if (!h->capturing || !h->list_warp) return DCM_OK;
+    cudaStreamCaptureStatus st;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *edges = nullptr;
+    size_t ndeps = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(h->stream, &st, nullptr, &g, &deps, &edges, &ndeps);
+    if (e != cudaSuccess) return fail_cuda(e, "capture info", __FILE__, __LINE__);
+    if (st != cudaStreamCaptureStatusActive) return fail(DCM_ERR_STATE, "branch outside a capture");
+    cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
+    p.conditional.handle = h->cond[which];
+    p.conditional.type = cudaGraphCondTypeIf;
+    p.conditional.size = (unsigned)nbody;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, g, deps, edges, ndeps, &p);
+    if (e != cudaSuccess) return fail_cuda(e, "conditional node", __FILE__, __LINE__);
+    e = cudaStreamUpdateCaptureDependencies(h->stream, &node, nullptr, 1,
+                                            cudaStreamSetCaptureDependencies);
+    if (e != cudaSuccess) return fail_cuda(e, "capture dependencies", __FILE__, __LINE__);
+    b.nbody = nbody;
+    b.cur = 0;
+    b.body[0] = p.conditional.phGraph_out[0];
+    b.body[1] = nbody > 1 ? p.conditional.phGraph_out[1] : nullptr;
+    e = cudaStreamBeginCaptureToGraph(h->side, b.body[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return fail_cuda(e, "body capture", __FILE__, __LINE__);
+    b.main = h->stream;
+    h->stream = h->side;
+    b.active = true;
+    return DCM_OK;
+}
+
+static int count_kernel_nodes(cudaGraph_t g)
+{
+    size_t n = 0;
+    if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess) return -1;
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (n && cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return -1;
+    int k = 0;
+    for (cudaGraphNode_t q : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(q, &t) != cudaSuccess) return -1;
+        k += t == cudaGraphNodeTypeKernel;
+    }
+    return k;
+}
+
+static int branch_end_body(dcm_handle *h, Branch &b)
+{
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->side, &g);
+    if (e != cudaSuccess) return fail_cuda(e, "end body capture", __FILE__, __LINE__);
+    int k = count_kernel_nodes(b.body[b.cur]);
+    if (k < 0) return fail(DCM_ERR_CUDA, "graph node count");
+    h->br_kernels[b.cur] += k;
+    return DCM_OK;
+}
+
+int branch_else(dcm_handle *h, Branch &b)
+{
+    if (!b.active) return DCM_OK;
+    if (b.nbody < 2 || b.cur != 0) return fail(DCM_ERR_STATE, "branch has no else body");
+    int r = branch_end_body(h, b);
+    if (r) return r;
+    b.cur = 1;
+    cudaError_t e = cudaStreamBeginCaptureToGraph(h->side, b.body[1], nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return fail_cuda(e, "body capture", __FILE__, __LINE__);
+    return DCM_OK;
+}
+
+int branch_close(dcm_handle *h, Branch &b)
+{
+    if (!b.active) return DCM_OK;
+    int r = branch_end_body(h, b);
+    h->stream = b.main;
+    b.active = false;
+    return r;
+}
+
+}  // namespace dcm
+
 // one velocity-Verlet step; detection after the drift when detect is set
 static int enqueue_step(dcm_handle *h, bool detect, bool capturing)
 {
-    int64_t k0 = h->kernels;
     list_mode(h);
     h->step_detect = detect;
     mark(h, 0, capturing);
@@ -668,22 +759,48 @@ static int enqueue_step(dcm_handle *h, bool detect, bool capturing)
     mark(h, 4, capturing);
     if (!r) r = launch_kick(h);
     mark(h, 5, capturing);
-    (detect ? h->kernels_detect : h->kernels_plain) = (int)(h->kernels - k0);
     return r;
 }
 
 static int capture(dcm_handle *h, bool detect, cudaGraphExec_t *exec)
 {
     cudaGraph_t graph = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+    if (!h->side) {
+        cudaError_t e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return fail_cuda(e, "cudaStreamCreate", __FILE__, __LINE__);
+    }
+    cudaStream_t main = h->stream;
+    cudaError_t e = cudaStreamBeginCapture(main, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return fail_cuda(e, "begin capture", __FILE__, __LINE__);
-    int r = enqueue_step(h, detect, true);
-    e = cudaStreamEndCapture(h->stream, &graph);
+    // the rebuild decision of this graph's list check (default: rebuild);
+    // only graphs with branches may hold a handle
+    list_mode(h);
+    if (h->list_warp) {
+        cudaStreamCaptureStatus st;
+        cudaGraph_t g = nullptr;
+        e = cudaStreamGetCaptureInfo(main, &st, nullptr, &g);
+        for (int q = 0; q < 2 && e == cudaSuccess; ++q)
+            e = cudaGraphConditionalHandleCreate(&h->cond[q], g, 1, cudaGraphCondAssignDefault);
+    }
+    int r = e == cudaSuccess ? DCM_OK : fail_cuda(e, "conditional handle", __FILE__, __LINE__);
+    h->capturing = true;
+    h->br_kernels[0] = h->br_kernels[1] = 0;
+    if (!r) r = enqueue_step(h, detect, true);
+    h->capturing = false;
+    if (h->stream != main) {                 // an error inside a branch body
+        cudaGraph_t body = nullptr;
+        (void)cudaStreamEndCapture(h->side, &body);
+        h->stream = main;
+    }
+    e = cudaStreamEndCapture(main, &graph);
     if (r || e != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);
         (void)cudaGetLastError();
         return r ? r : fail_cuda(e, "end capture", __FILE__, __LINE__);
     }
+    int top = count_kernel_nodes(graph);
+    (detect ? h->kernels_detect : h->kernels_plain) = top + h->br_kernels[0];
+    (detect ? h->kernels_detect_reuse : h->kernels_plain_reuse) = top + h->br_kernels[1];
     e = cudaGraphInstantiate(exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return fail_cuda(e, "graph instantiate", __FILE__, __LINE__);
@@ -872,6 +989,8 @@ extern "C" int dcm_get_stats(dcm_handle *h, dcm_stats *s)
     s->guard_rechecks = (int64_t)st.guard_rechecks;
     s->kernels_plain = h->kernels_plain;
     s->kernels_detect = h->kernels_detect;
+    s->kernels_plain_reuse = h->kernels_plain_reuse;
+    s->kernels_detect_reuse = h->kernels_detect_reuse;
     s->list_builds = (int64_t)st.list_builds;
     s->list_entries = (int64_t)st.list_entries;
     return DCM_OK;

@@ -223,7 +223,6 @@ int launch_scan(dcm_handle *h, const int32_t *in, int32_t *out, int32_t *tiles, 
     int ntiles = nblk(m, SCAN_TILE);
     k_scan_tiles<<<ntiles, SCAN_THREADS, 0, h->stream>>>(in, out, tiles, m, gate);
     k_scan_add<<<ntiles, SCAN_THREADS, 0, h->stream>>>(out, tiles, m, total, ntiles, gate);
-    h->kernels += 2;
     return DCM_OK;
 }
 
@@ -233,11 +232,10 @@ int launch_scan(dcm_handle *h, const int32_t *in, int32_t *out, int32_t *tiles, 
 // positions and cutoff constants current between builds, so the gather
 // runs only with the sort; the class lists are redone when the sort ran or
 // the classes changed (class_gate null: always).
-int launch_bin_gated(dcm_handle *h, const int *gate, const int *class_gate)
+int launch_sort_gather(dcm_handle *h, const int *gate)
 {
     cudaStream_t s = h->stream;
     int n = (int)h->n;
-    h->kernels += 8;
     cudaMemsetAsync(h->cell_count, 0, sizeof(int32_t) * h->ncell, s);
     k_cell_count<<<nblk(n, 256), 256, 0, s>>>(h->b, h->x, h->cell_of, h->slot, h->cell_count, gate);
     launch_scan(h, h->cell_count, h->cell_start, h->scan_tmp, h->ncell, n, gate);
@@ -248,9 +246,16 @@ int launch_bin_gated(dcm_handle *h, const int *gate, const int *class_gate)
     k_gather<<<nblk(n, 256), 256, 0, s>>>(h->b, h->x, h->sorted_id, h->cell_of, h->sp4,
                                           h->p.precision == DCM_FP64 ? h->spd : nullptr, h->rc,
                                           h->rq, h->pk, h->d, h->lflags,
-                                          h->cut_detected ? 1.0f : 0.0f, wl ? h->nl_cnt : nullptr,
+                                          h->cut_detected ? h->list_margin : 0.0f, wl ? h->nl_cnt : nullptr,
                                           h->inv, wl ? gate : nullptr);
-    // class lists of sorted slots for the force work queue
+    return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "binning launch");
+}
+
+// class lists of sorted slots for the force work queue
+int launch_classes(dcm_handle *h, const int *class_gate)
+{
+    cudaStream_t s = h->stream;
+    int n = (int)h->n;
     int K = h->b.K;
     k_class_zero<<<1, 32, 0, s>>>(h->class_count_dev, class_gate);
     k_class_count<<<nblk(n, 256), 256, 0, s>>>(n, K, h->cls, h->class_count_dev, class_gate);
@@ -259,7 +264,13 @@ int launch_bin_gated(dcm_handle *h, const int *gate, const int *class_gate)
                                                h->class_count_dev + K,
                                                h->class_count_dev + 2 * K, h->class_list,
                                                class_gate);
-    return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "binning launch");
+    return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "class launch");
+}
+
+int launch_bin_gated(dcm_handle *h, const int *gate, const int *class_gate)
+{
+    int r = launch_sort_gather(h, gate);
+    return r ? r : launch_classes(h, class_gate);
 }
 
 int launch_bin(dcm_handle *h) { return launch_bin_gated(h, nullptr, nullptr); }

@@ -727,7 +727,6 @@ int prepare_kernels(dcm_handle *h)
 
 int launch_detect(dcm_handle *h)
 {
-    h->kernels += h->p.smooth_order > 0 ? 9 : 7;
     cudaStream_t s = h->stream;
     const Batch &b = h->b;
     int64_t nv = b.NV;
@@ -828,7 +827,6 @@ int launch_detect(dcm_handle *h)
         cfg.numAttrs = 1;
         cudaError_t e = cudaLaunchKernelExC(&cfg, (const void *)k_cfsm_tail, args);
         if (e != cudaSuccess) return fail_cuda(e, "cfsm tail launch", __FILE__, __LINE__);
-        h->kernels += 1;
     }
     // Algorithm 3.1 + Eq. 7
     const bool wl = h->nl && h->list_warp;

@@ -1197,7 +1197,6 @@ static void fill_args(dcm_handle *h, ForceArgs &a);
 
 int launch_list_walk(dcm_handle *h, bool fill, const int *gate, float delta)
 {
-    h->kernels += 1;
     ForceArgs a;
     fill_args(h, a);
     a.gate = gate;
@@ -1214,10 +1213,10 @@ int launch_list_walk(dcm_handle *h, bool fill, const int *gate, float delta)
 
 int launch_forces(dcm_handle *h, bool energy)
 {
-    h->kernels += 1;
     ForceArgs a;
     fill_args(h, a);
-    cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), h->stream);
+    const bool list_warp = h->nl && h->list_warp;
+    if (!list_warp) cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), h->stream);
     int block = h->tune.block >= 64 && h->tune.block <= FORCE_THREADS ? h->tune.block : FORCE_THREADS;
     int grid = h->num_sms * (2048 / block);
     bool fp64 = h->p.precision == DCM_FP64;
@@ -1229,14 +1228,21 @@ int launch_forces(dcm_handle *h, bool energy)
             k_force_warp<false, false><<<g2, FW_THREADS, 0, h->stream>>>(a);
         return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "force launch");
     }
-    if (h->nl && h->list_warp) {
+    if (list_warp) {
         // rebuild step: direct walk + list fill; other steps: the lists.
-        // Both are launched, each returns at once unless it is its step.
-        h->kernels += 1;
+        // Eagerly both are launched and each returns at once unless it is
+        // its step; a captured step holds them in the two bodies of a graph
+        // IF node on the rebuild decision.
+        Branch br;
+        int r = branch_open(h, br, 2, 1);
+        if (r) return r;
+        cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), h->stream);
         if (energy)
             k_force_warp<true, true><<<g2, FW_THREADS, 0, h->stream>>>(a);
         else
             k_force_warp<false, true><<<g2, FW_THREADS, 0, h->stream>>>(a);
+        r = branch_else(h, br);
+        if (r) return r;
         cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), h->stream);
         const int G = h->tune.list_lanes > 0 ? h->tune.list_lanes : FW_LIST_G;
         const int gl = h->num_sms * FW_LIST_MINB;   // persistent: the resident blocks
@@ -1251,7 +1257,9 @@ int launch_forces(dcm_handle *h, bool energy)
         } else {
             k_force_list_warp<false, 8><<<gl, FW_THREADS, 0, h->stream>>>(a);
         }
-        return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "force launch");
+        if (cudaGetLastError() != cudaSuccess) r = fail(DCM_ERR_CUDA, "force launch");
+        int r2 = branch_close(h, br);
+        return r ? r : r2;
     }
     if (fp64) {
         if (energy)

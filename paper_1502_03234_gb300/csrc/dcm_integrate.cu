@@ -138,7 +138,6 @@ static inline int nblk(int64_t n, int b) { return (int)((n + b - 1) / b); }
 
 int launch_kick_drift(dcm_handle *h)
 {
-    h->kernels += 1;
     const bool wl = h->nl && h->list_warp;
     k_kick_drift<<<nblk(h->n, 256), 256, 0, h->stream>>>(h->b, h->x, h->v, h->f, h->err,
                                                          wl ? h->sp4 : nullptr, h->inv, h->cell_of);
@@ -167,7 +166,6 @@ void launch_iota(dcm_handle *h, int32_t *p, int64_t n)
 
 int launch_kick(dcm_handle *h)
 {
-    h->kernels += 1;
     k_kick<<<nblk(h->n, 256), 256, 0, h->stream>>>(h->b, h->v, h->f);
     return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "kick launch");
 }

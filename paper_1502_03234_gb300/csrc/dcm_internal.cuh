@@ -66,8 +66,11 @@ struct DevStats {
 // Verlet-list control words: rebuild decision, lists valid, the two maxima
 // of the check, its block counter, a per-particle capacity overflow seen by
 // the last fill, the capacity density scale (float bits), the fill gate
-enum { LF_REBUILD = 0, LF_OK = 1, LF_MAXDISP = 2, LF_MINHEAD = 3, LF_DONE = 4, LF_OVERFLOW = 5,
+enum { LF_REBUILD = 0, LF_OK = 1, LF_MAXDISP = 2, LF_EXCESS = 3, LF_DONE = 4, LF_OVERFLOW = 5,
        LF_SCALE = 6, LF_WORDS = 8 };
+// LF_EXCESS holds an order-preserving int image of a float; this is the
+// image of -3.39e38 (every byte 0x80, so a memset writes it too)
+constexpr int LF_EXCESS_RESET = (int)0x80808080u;
 
 constexpr int MAX_SYSTEMS = 1024;
 
@@ -188,6 +191,7 @@ struct dcm_handle {
     bool list_warp;              // lists built and walked by the warp kernels (set per capture)
     bool step_detect;            // the step being enqueued re-detects the interface
     float list_scale0;           // initial capacity density of those lists
+    float list_margin;           // interface-distance margin of the list radius (sigma)
     int *lflags;                 // LF_* words
     // per particle diagnostics / energies
     int32_t *npair;
@@ -208,9 +212,15 @@ struct dcm_handle {
     cudaGraphExec_t g_plain, g_detect;
     bool graphs_ready;
     int coop_blocks;             // co-resident blocks for the persistent kernels
-    // kernels launched so far (each launcher adds its count)
-    int64_t kernels;
-    int kernels_plain, kernels_detect;
+    // conditional branches of a captured step: k_list_check sets `cond` to
+    // the rebuild decision, graph IF nodes on it hold the rebuild-only work
+    cudaStream_t side;                  // records the branch bodies
+    cudaGraphConditionalHandle cond[2]; // of the graph being captured: list step, forces
+                                        // (a handle serves one conditional node)
+    bool capturing;                     // enqueue_step is recording a graph
+    int br_kernels[2];                  // kernels in bodies taken on rebuild / reuse
+    // kernel nodes of one captured step: [plain, detect] x [rebuild, reuse]
+    int kernels_plain, kernels_detect, kernels_plain_reuse, kernels_detect_reuse;
     // phase timing: events[0..DCM_NUM_PHASES] bracket the phases
     bool timing;
     cudaEvent_t ev[DCM_NUM_PHASES + 1];
@@ -227,6 +237,8 @@ int launch_kick_drift(dcm_handle *h);
 int launch_kick(dcm_handle *h);
 int launch_bin(dcm_handle *h);                      // full cell sort + classes
 int launch_bin_gated(dcm_handle *h, const int *gate, const int *class_gate);  // sort, gather, classes
+int launch_sort_gather(dcm_handle *h, const int *gate);    // cell sort + gather
+int launch_classes(dcm_handle *h, const int *class_gate);  // class lists
 void list_mode(dcm_handle *h);          // sets list_warp from precision, tuning and lists
 void launch_iota(dcm_handle *h, int32_t *p, int64_t n);
 void launch_sys_tables(dcm_handle *h);
@@ -239,6 +251,22 @@ int launch_detect(dcm_handle *h);
 int launch_reduce_energy(dcm_handle *h, int k);
 int launch_reduce_pairs(dcm_handle *h);
 int launch_classify_rc(dcm_handle *h);   // classes from supplied rc
+
+// A branch of a captured step on the Verlet-list rebuild decision (a CUDA
+// graph IF node on one of h->cond).  Between branch_open and branch_close the work
+// enqueued on h->stream is recorded into body 0, taken on a step that
+// rebuilds the lists, and after branch_else into body 1, taken on a step that
+// reuses them.  Outside a capture, or without the warp list kernels, the
+// three calls do nothing and the kernels' own gates decide.
+struct Branch {
+    bool active;
+    int nbody, cur;
+    cudaGraph_t body[2];
+    cudaStream_t main;
+};
+int branch_open(dcm_handle *h, Branch &b, int nbody, int which);   // which: h->cond[which]
+int branch_else(dcm_handle *h, Branch &b);
+int branch_close(dcm_handle *h, Branch &b);
 
 // lower-level helpers
 int coop_grid_size(dcm_handle *h, const void *kernel, int block, size_t smem);

@@ -3,15 +3,17 @@
 // reuse the list while no particle moved r_s/2).
 //
 // With per-particle cutoffs the reuse condition also covers cutoff growth:
-// a pair inside r_c[i](t) now was within r_c[i](t) + 2 d_max at the build,
-// so the list of particle i (all j within its list radius R_i) stays
-// complete while
-//     2 * d_max < min_i (R_i - r_c[i](t)),
-// with d_max the largest displacement since the build.  R_i is the cutoff
-// particle i would get if its interface distance dropped by one sigma, plus
-// the skin: the detected interface jitters by about a voxel, and Eq. 7 is
-// steep near d = r_c,max, so lists sized by the current cutoff alone would be
-// rebuilt at nearly every detection.  Every step one
+// a pair inside r_c[i](t) now was closer than r_c[i](t) + |d_i| + d_max at
+// the build (d_i the displacement of i since the build, d_max the largest
+// one), so the list of particle i (all j within its list radius R_i) stays
+// complete while |d_i| + d_max < R_i - r_c[i](t) for every i, that is while
+//     d_max + max_i (|d_i| - (R_i - r_c[i](t))) < 0,
+// both maxima taken in one pass.  (The usual rule 2 d_max < min_i headroom
+// is the special case |d_i| = d_max for all i, and rebuilds more often.)
+// R_i is the cutoff particle i would get if its interface distance dropped
+// by a margin (list_margin, 1 sigma by default), plus the skin: the detected interface jitters by about a
+// voxel, and Eq. 7 is steep near d = r_c,max, so lists sized by the current
+// cutoff alone would be rebuilt at nearly every detection.  Every step one
 // kernel measures both maxima and decides; the cell sort and the list build
 // that follow are launched every step but do nothing unless the decision
 // was "rebuild", so the step stays one fixed CUDA graph.
@@ -25,13 +27,22 @@
 
 namespace dcm {
 
-// largest displacement^2 since the build and the smallest cutoff headroom
-// R_i - r_c[i]; the last block to finish turns them into the decision
+// order-preserving int image of a float (for atomicMax over signed values)
+__device__ __forceinline__ int ordered_int(float f)
+{
+    int b = __float_as_int(f);
+    return b >= 0 ? b : b ^ 0x7fffffff;
+}
+
+// largest displacement since the build and the largest excess of a
+// particle's own displacement over its headroom R_i - r_c[i]; the last block
+// to finish turns them into the decision
 __global__ void k_list_check(Batch b, const double *__restrict__ x, const double *__restrict__ x_ref,
                              const double *__restrict__ rc, const float *__restrict__ rl_ref,
-                             int *lf, int force)
+                             int *lf, int force, cudaGraphConditionalHandle cond0,
+                             cudaGraphConditionalHandle cond1, int set_cond)
 {
-    float md = 0.f, mh = 3.0e38f;
+    float md = 0.f, mq = -3.0e38f;
     const size_t N = (size_t)b.N;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < b.N;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -45,17 +56,18 @@ __global__ void k_list_check(Batch b, const double *__restrict__ x, const double
         dx -= Lx * rintf(dx / Lx);
         dy -= Ly * rintf(dy / Ly);
         dz -= Lz * rintf(dz / Lz);
-        md = fmaxf(md, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-        mh = fminf(mh, fmaxf(rl_ref[i] - (float)rc[i], 0.f));
+        float d = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        md = fmaxf(md, d);
+        mq = fmaxf(mq, d - fmaxf(rl_ref[i] - (float)rc[i], 0.f));
     }
     for (int off = 16; off > 0; off >>= 1) {
         md = fmaxf(md, __shfl_xor_sync(0xffffffffu, md, off));
-        mh = fminf(mh, __shfl_xor_sync(0xffffffffu, mh, off));
+        mq = fmaxf(mq, __shfl_xor_sync(0xffffffffu, mq, off));
     }
     if ((threadIdx.x & 31) == 0) {
         // non-negative floats order like their bit patterns
         atomicMax(&lf[LF_MAXDISP], __float_as_int(md));
-        atomicMin(&lf[LF_MINHEAD], __float_as_int(mh));
+        atomicMax(&lf[LF_EXCESS], ordered_int(mq));
     }
     __syncthreads();
     __shared__ int s_last;
@@ -66,8 +78,9 @@ __global__ void k_list_check(Batch b, const double *__restrict__ x, const double
     __syncthreads();
     if (s_last && threadIdx.x == 0) {
         __threadfence();
-        float d2 = __int_as_float(atomicExch(&lf[LF_MAXDISP], 0));
-        float head = __int_as_float(atomicExch(&lf[LF_MINHEAD], 0x7f7f7f7f));
+        float dmax = __int_as_float(atomicExch(&lf[LF_MAXDISP], 0));
+        // the image is its own inverse; reset to the image of -3.4e38
+        float excess = __int_as_float(ordered_int(__int_as_float(atomicExch(&lf[LF_EXCESS], LF_EXCESS_RESET))));
         int ok = atomicAdd(&lf[LF_OK], 0);
         if (atomicExch(&lf[LF_OVERFLOW], 0)) {
             // a particle had more neighbours than its capacity at the last
@@ -76,9 +89,13 @@ __global__ void k_list_check(Batch b, const double *__restrict__ x, const double
             lf[LF_OK] = 0;
             lf[LF_SCALE] = __float_as_int(__int_as_float(lf[LF_SCALE]) * 1.25f);
         }
-        int rebuild = force || !ok || (2.f * sqrtf(d2) >= head);
+        int rebuild = force || !ok || (dmax + excess >= 0.f);
         lf[LF_REBUILD] = rebuild;
         lf[LF_DONE] = 0;
+        if (set_cond) {
+            cudaGraphSetConditional(cond0, (unsigned)rebuild);
+            cudaGraphSetConditional(cond1, (unsigned)rebuild);
+        }
     }
 }
 
@@ -118,30 +135,44 @@ void list_mode(dcm_handle *h)
 // decide, [cell sort], gather + classes, then
 //  warp kernels (MIXED, warp walk): [capacity scan, total, save]; the list
 //      fill happens in the force phase, inside the direct force walk of the
-//      rebuild step (launch_forces);
+//      rebuild step (launch_forces).  In a captured step the bracketed work
+//      sits in a graph IF node on the decision, so a step that reuses its
+//      lists launches none of it;
 //  lanes kernels: [list count, scan, total, fill, save]
 int launch_list_step(dcm_handle *h, bool force_rebuild)
 {
-    cudaStream_t s = h->stream;
     int64_t N = h->n;
     int cgrid = h->num_sms * 2;
     list_mode(h);
-    k_list_check<<<cgrid, 256, 0, s>>>(h->b, h->x, h->x_ref, h->rc, h->rl_ref, h->lflags,
-                                        force_rebuild ? 1 : 0);
+    const bool set_cond = h->capturing && h->list_warp;
+    k_list_check<<<cgrid, 256, 0, h->stream>>>(h->b, h->x, h->x_ref, h->rc, h->rl_ref, h->lflags,
+                                               force_rebuild ? 1 : 0, h->cond[0], h->cond[1],
+                                               set_cond ? 1 : 0);
     const int *rebuild = h->lflags + LF_REBUILD;
     const int *fill = h->lflags + (LF_WORDS - 1);
-    // class lists change with a detection or with the sort
-    int r = launch_bin_gated(h, rebuild, h->list_warp && !h->step_detect ? rebuild : nullptr);
-    if (r) return r;
     if (h->list_warp) {
-        // the gather wrote each particle's capacity into nl_cnt
-        launch_scan(h, h->nl_cnt, h->nl_start, h->nl_tiles, N, -1, rebuild);
-        k_list_total<<<1, 1, 0, s>>>(N, h->nl_start, h->nl_cap, h->lflags, h->stats, 1);
-        k_list_save<<<nblk(N, 256), 256, 0, s>>>(N, h->x, h->x_ref, fill);
-        h->kernels += 3;
-        return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "list launch");
+        Branch br;
+        int r = branch_open(h, br, 1, 0);
+        if (!r) r = launch_sort_gather(h, rebuild);
+        // class lists change with a detection or with the sort
+        if (!r && !h->step_detect) r = launch_classes(h, rebuild);
+        if (!r) {
+            // the gather wrote each particle's capacity into nl_cnt
+            cudaStream_t s = h->stream;
+            launch_scan(h, h->nl_cnt, h->nl_start, h->nl_tiles, N, -1, rebuild);
+            k_list_total<<<1, 1, 0, s>>>(N, h->nl_start, h->nl_cap, h->lflags, h->stats, 1);
+            k_list_save<<<nblk(N, 256), 256, 0, s>>>(N, h->x, h->x_ref, fill);
+            if (cudaGetLastError() != cudaSuccess) r = fail(DCM_ERR_CUDA, "list launch");
+        }
+        int r2 = branch_close(h, br);
+        if (!r) r = r2;
+        if (!r && h->step_detect) r = launch_classes(h, nullptr);
+        return r;
     }
-    float delta = h->cut_detected ? 1.0f : 0.0f;
+    cudaStream_t s = h->stream;
+    int r = launch_bin_gated(h, rebuild, nullptr);
+    if (r) return r;
+    float delta = h->cut_detected ? h->list_margin : 0.0f;
     r = launch_list_walk(h, false, rebuild, delta);
     if (r) return r;
     launch_scan(h, h->nl_cnt, h->nl_start, h->nl_tiles, N, -1, rebuild);
@@ -149,7 +180,6 @@ int launch_list_step(dcm_handle *h, bool force_rebuild)
     r = launch_list_walk(h, true, fill, delta);
     if (r) return r;
     k_list_save<<<nblk(N, 256), 256, 0, s>>>(N, h->x, h->x_ref, fill);
-    h->kernels += 3;
     return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "list launch");
 }
 

@@ -56,7 +56,7 @@ class dcm_params(C.Structure):
                 ("cfsm_iter_max", C.c_int32), ("cfsm_eps", C.c_double),
                 ("precision", C.c_int32), ("n_classes", C.c_int32), ("cell_min", C.c_double),
                 ("skin", C.c_double), ("list_density", C.c_float),
-                ("reserved", C.c_int32 * 5)]
+                ("list_margin", C.c_float), ("reserved", C.c_int32 * 4)]
 
 
 class dcm_tuning(C.Structure):
@@ -71,7 +71,8 @@ class dcm_stats(C.Structure):
                 ("c_vapor", C.c_double), ("guard_rechecks", C.c_int64),
                 ("kernels_plain", C.c_int32), ("kernels_detect", C.c_int32),
                 ("list_builds", C.c_int64), ("list_entries", C.c_int64),
-                ("reserved", C.c_int64 * 3)]
+                ("kernels_plain_reuse", C.c_int32), ("kernels_detect_reuse", C.c_int32),
+                ("reserved", C.c_int64 * 2)]
 
 
 _lib = None

@@ -13,7 +13,7 @@ pytestmark = pytest.mark.gpu
 FP64_REL, FP64_ABS = 1e-5, 1e-6
 # MIXED: FP32 pair arithmetic on cell-relative coordinates; a pair force of
 # magnitude |F_ij| carries a relative error of ~14 * 2^-23 from r^-13, so the
-# per-particle bound scales with sum_j |F_ij| (see DESIGN.md)
+# per-particle bound scales with sum_j |F_ij|
 MIX_COND = 2e-5
 
 
@@ -210,6 +210,29 @@ def test_list_mode_stays_complete_while_reused(dcm, orc, prec, walk):
     fmag = np.linalg.norm(ref.f, axis=1)
     extra = 0.0 if prec == 0 else 5e-4
     assert np.all(err <= FP64_ABS + FP64_REL * fmag + extra), err.max()
+
+
+def test_step_graph_branches_on_rebuild(dcm):
+    # with the warp list kernels each captured step holds the rebuild-only
+    # work in graph IF nodes: a step that reuses its lists launches fewer
+    # kernels; without lists (or with the lanes kernels) there is no branch
+    s = slabgen.make_slab(9001, seed=43)
+    counts = {}
+    for skin, walk in ((0.3, "warp"), (0.3, "lanes"), (0.0, "warp")):
+        with dcm.System(s.box, len(s.x), precision=1, skin=skin) as sy:
+            sy.set_tuning([2, 1, 2, 2], 128, WALKS[walk])
+            sy.set_state(s.x, s.v)
+            sy.step(4)
+            sy.sync()
+            st = sy.stats()
+            counts[skin, walk] = (st.kernels_plain, st.kernels_plain_reuse,
+                                  st.kernels_detect, st.kernels_detect_reuse)
+    kp, kpr, kd, kdr = counts[0.3, "warp"]
+    assert 0 < kpr < kp and 0 < kdr < kd, counts
+    assert kd - kdr == kp - kpr - 4, counts      # class lists run on every detection
+    for key in ((0.3, "lanes"), (0.0, "warp")):
+        kp, kpr, kd, kdr = counts[key]
+        assert kp == kpr > 0 and kd == kdr > kp, counts
 
 
 def test_list_capacity_overflow_recovers(dcm, orc):
