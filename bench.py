@@ -64,7 +64,7 @@ FLOPS_PER_PAIR = 24              # 8 (distance test) + 16 (LJ force), per in-cut
 FORCE_TRAFFIC = {"mixed": 14.96e6, "fp64": None}
 # DRAM bytes per launch of the Verlet-list force kernel (k_force_list_warp, skin 0.5,
 # N = 262,144) from the committed capture (profiles/k_force_list_warp_N262144_mixed.md)
-LIST_TRAFFIC = 248.78e6 + 3.94e6
+LIST_TRAFFIC = {"k_force_list_warp": 248.78e6 + 3.94e6}
 # bytes the list kernel must move per particle besides its list entries: own
 # position, cutoff constants, id/cell, list start and count, queue slot, the
 # force written and the pair count
@@ -86,6 +86,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--skin", type=float, default=0.5,
                     help="Verlet-list skin in sigma (0: direct link-cell walk every step)")
+    ap.add_argument("--step-graph", default="branched", choices=["branched", "flat"],
+                    help="flat: no conditional nodes in the step graph (for per-kernel profiling)")
     ap.add_argument("--list-margin", type=float, default=1.0,
                     help="interface-distance margin of the Verlet-list radius in sigma")
     ap.add_argument("--workload", default="slab", choices=["slab", "wavy", "ensemble", "serving"])
@@ -104,7 +106,7 @@ def workload_config(n, precision):
                         f"DCM r_c 3/6 (Eq. 7, alpha=-0.5), 1-sigma voxels, detection every 2 steps",
             "n": n, "rc_min": 3.0, "rc_max": 6.0, "detect_every": 2, "dt": 0.005,
             "precision": precision,
-            "l2": "flushed (256 MiB write) before every timed step; each step timed alone"}
+            "l2": L2_NOTE + "; each step timed alone"}
 
 
 def force_kernel_name(dcm, sy, prec, skin):
@@ -236,6 +238,24 @@ def run_reference(args):
 
 
 # ---- further workloads (one GPU) -------------------------------------------------------
+class L2Flush:
+    """Evicts the timed program's data from the 129 MB L2 before a step: a
+    256 MiB write, then a 256 MiB read, so that the write's dirty lines are
+    written back here rather than inside the next timed step."""
+
+    def __init__(self, torch):
+        self.w = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+        self.r = torch.zeros(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def __call__(self):
+        self.w.zero_()
+        self.s = self.r.amax()
+
+
+L2_NOTE = ("flushed before every timed step (256 MiB write, then a 256 MiB read that "
+           "drains the write's dirty lines)")
+
+
 def _launches(st, kinds):
     """kernels the timed steps launched: each step is one CUDA graph whose
     kernel count depends on detection and, with Verlet lists, on whether the
@@ -264,7 +284,7 @@ def _timed(sy, stream, flush, k, warm):
 
     for _ in range(warm):
         with torch.cuda.stream(stream):
-            flush.zero_()
+            flush()
         sy.step(1)
     sy.sync()
     out, phase, kinds = [], {}, []
@@ -273,7 +293,7 @@ def _timed(sy, stream, flush, k, warm):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         with torch.cuda.stream(stream):
-            flush.zero_()
+            flush()
             e0.record(stream)
         sy.step(1)
         with torch.cuda.stream(stream):
@@ -306,7 +326,7 @@ def run_workload(args):
     from paper_1502_03234_gb300 import autotune, dcm, serving, slabgen
 
     stream = torch.cuda.Stream()
-    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    flush = L2Flush(torch)
     line = {"n_gpus": 1, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32-pair/f64-state", "data": "synthetic",
             "unit": UNIT}
@@ -343,7 +363,7 @@ def run_workload(args):
                            "n": n, "rc_min": 3.0, "rc_max": 7.0, "skin": args.skin,
                            "phase_ms_avg": ph,
                            "pairs_per_particle": st.pairs / n,
-                           "l2": "flushed (256 MiB write) before every timed step"},
+                           "l2": L2_NOTE},
                 "latency_ms": {"p50": _pct(ms, 50), "p99": _pct(ms, 99), "unit": "ms per step"},
                 "weak_scaling_in_n": {"unit": UNIT, "steps": args.sweep_steps, "values": sweep}})
         elif args.workload == "ensemble":
@@ -372,7 +392,7 @@ def run_workload(args):
                                        "launch per step, each step one CUDA graph",
                            "systems": len(ns), "n_total": ntot, "n_min": min(ns), "skin": args.skin,
                            "n_max": max(ns), "phase_ms_avg": ph, "tuning": choice,
-                           "l2": "flushed (256 MiB write) before every timed step"},
+                           "l2": L2_NOTE},
                 "latency_ms": {"p50": _pct(ms, 50), "p99": _pct(ms, 99), "unit": "ms per step"},
                 "gpu_launches": int(kernels)})
         else:
@@ -428,21 +448,26 @@ def main():
     prec = dcm.DCM_MIXED if args.precision == "mixed" else dcm.DCM_FP64
     slab = slabgen.make_slab(n, seed=1 + rank)
     stream = torch.cuda.Stream()
-    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    flush = L2Flush(torch)
 
     def make_system(precision):
         sy = dcm.System(slab.box, n, precision=precision, stream=stream.cuda_stream,
                         skin=args.skin, list_margin=args.list_margin)
+        if args.step_graph == "flat":
+            sy.set_step_graph(dcm.DCM_GRAPH_FLAT)
         sy.set_state(slab.x, slab.v)
         sy.compute_forces()
-        sy.set_timing(True)
         return sy
 
-    def timed_steps(sy, k, warm):
-        """per-step device times (ms), L2 flushed before each step"""
+    def timed_steps(sy, k, warm, phases):
+        """per-step device times (ms), L2 flushed before each step; with
+        phases, the step graph also records the library's per-phase events
+        (force time per step for the roofline), which adds event nodes to
+        every step, so the headline pass runs without them"""
+        sy.set_timing(phases)
         for _ in range(warm):
             with torch.cuda.stream(stream):
-                flush.zero_()
+                flush()
             sy.step(1)
         sy.sync()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -451,19 +476,20 @@ def main():
         b_prev = sy.stats().list_builds
         for q in range(k):
             with torch.cuda.stream(stream):
-                flush.zero_()
+                flush()
                 ev[q][0].record(stream)
             sy.step(1)
             with torch.cuda.stream(stream):
                 ev[q][1].record(stream)
-            ph = sy.phase_times()                       # waits for this step
-            force_ms.append(ph["force"])
+            if phases:
+                ph = sy.phase_times()                   # waits for this step
+                force_ms.append(ph["force"])
+                for key, val in ph.items():
+                    phase_sum[key] = phase_sum.get(key, 0.0) + val
             kind, b_now = _kind(sy, b_prev)              # (outside the timed events)
             kinds.append(kind)
             rebuilt.append(b_now != b_prev)
             b_prev = b_now
-            for key, val in ph.items():
-                phase_sum[key] = phase_sum.get(key, 0.0) + val
         sy.sync()
         timed_steps.rebuilt = rebuilt
         timed_steps.kinds = kinds
@@ -474,14 +500,23 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     with Clocks(local) as clk:
-        step_ms, force_ms, phase_sum = timed_steps(sy, args.steps, args.warmup)
+        step_ms, _, _ = timed_steps(sy, args.steps, args.warmup, False)
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
     total_ms = sum(step_ms)
     st = sy.stats()
-    pairs = st.pairs
     kernels = _launches(st, timed_steps.kinds)
+    # the same steps again on a second system from the same start (the
+    # trajectory is deterministic), this time with the per-phase events:
+    # force time per step for the roofline and the phase breakdown; not part
+    # of the headline number
+    phase_steps = args.steps
+    sy_ph = make_system(prec)
+    _, force_ms, phase_sum = timed_steps(sy_ph, phase_steps, args.warmup, True)
+    st = sy_ph.stats()
+    pairs = st.pairs
+    sy_ph.close()
     x_end, _, _ = sy.get_state()
     if not np.all(np.isfinite(x_end)):
         raise RuntimeError("non-finite positions after the timed run")
@@ -508,12 +543,14 @@ def main():
         # list from HBM (arithmetic intensity ~3 flop/B, under the HBM roof)
         l_ms = sum(list_steps) / len(list_steps)
         entries = st.list_entries
+        lkernel = "k_force_list_warp"
         alg_bytes = LIST_BYTES_PER_ENTRY * entries + LIST_BYTES_PER_PARTICLE * n
         achieved = alg_bytes / (l_ms * 1e-3) / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": HBM_PEAK_GBS, "unit": "GB/s",
                     "frac": achieved / HBM_PEAK_GBS,
-                    "traffic": LIST_TRAFFIC if n == N_DEFAULT and args.skin == 0.5 else None,
-                    "kernel": "k_force_list_warp (mixed, Verlet lists)",
+                    "traffic": (LIST_TRAFFIC.get(lkernel) if n == N_DEFAULT and args.skin == 0.5
+                                and args.list_margin == 1.0 else None),
+                    "kernel": f"{lkernel} (mixed, Verlet lists)",
                     "peak_note": "measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                     "algorithmic_bytes_per_launch": alg_bytes, "list_entries": entries,
                     "launch_ms_avg": l_ms, "launches": len(list_steps),
@@ -540,7 +577,7 @@ def main():
     if not args.no_fp64_compare and prec == dcm.DCM_MIXED and rank == 0:
         sy64 = make_system(dcm.DCM_FP64)
         k64 = max(4, min(20, args.steps // 10) // 2 * 2)
-        s64, f64, _ = timed_steps(sy64, k64, 2)
+        s64, f64, _ = timed_steps(sy64, k64, 2, True)
         fp64_info = {"value": n * k64 / (sum(s64) * 1e-3), "unit": UNIT, "steps": k64,
                      "ms_per_step": sum(s64) / k64, "force_ms_avg": sum(f64) / len(f64)}
         sy64.close()
@@ -590,7 +627,9 @@ def main():
         cfg = workload_config(n, args.precision)
         cfg["skin"] = args.skin
         cfg["list_margin"] = args.list_margin
-        cfg["phase_ms_avg"] = {k: v / args.steps for k, v in phase_sum.items()}
+        cfg["phase_ms_avg"] = {k: v / phase_steps for k, v in phase_sum.items()}
+        cfg["phase_note"] = ("per-phase CUDA events inside the step graph, on a second run of the "
+                             "same steps from the same start (the timed run records none)")
         cfg["fp64_gpu_path"] = fp64_info
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,

@@ -116,6 +116,15 @@ typedef struct {
  * DCM_WALK_LANES: lanes[] lanes per particle walk its stencil rows. */
 enum { DCM_WALK_WARP = 0, DCM_WALK_LANES = 1 };
 
+/* Shape of the CUDA graph of one step (dcm_tuning.step_graph).  With the
+ * warp Verlet-list kernels, DCM_GRAPH_BRANCHED (default) puts the work of a
+ * list rebuild and the list force in conditional nodes on the rebuild
+ * decision, so a step launches only the kernels it needs; DCM_GRAPH_FLAT
+ * launches every kernel every step and each returns at once when it is not
+ * its step (same results; profilers that cannot trace kernels inside
+ * conditional graphs see every kernel). */
+enum { DCM_GRAPH_BRANCHED = 0, DCM_GRAPH_FLAT = 1 };
+
 /* Launch shape of the force kernel (the autotuner's output; see
  * dcm_set_tuning).  lanes[] and block apply to DCM_WALK_LANES. */
 typedef struct {
@@ -124,7 +133,8 @@ typedef struct {
     int32_t walk;                          /* DCM_WALK_WARP (default) or DCM_WALK_LANES */
     int32_t list_lanes;                    /* warp walk + Verlet lists: lanes per particle of
                                               the list force, 4, 8, 16 or 32 (0: 8) */
-    int32_t reserved[5];
+    int32_t step_graph;                    /* DCM_GRAPH_BRANCHED or DCM_GRAPH_FLAT */
+    int32_t reserved[4];
 } dcm_tuning;
 
 typedef struct {

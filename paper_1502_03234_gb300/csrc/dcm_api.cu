@@ -661,7 +661,7 @@ namespace dcm {
 int branch_open(dcm_handle *h, Branch &b, int nbody, int which)
 {
     b.active = false;
-    if (!h->capturing || !h->list_warp) return DCM_OK;
+    if (!h->branching) return DCM_OK;
     cudaStreamCaptureStatus st;
     cudaGraph_t g = nullptr;
     const cudaGraphNode_t *deps = nullptr;
@@ -775,7 +775,8 @@ static int capture(dcm_handle *h, bool detect, cudaGraphExec_t *exec)
     // the rebuild decision of this graph's list check (default: rebuild);
     // only graphs with branches may hold a handle
     list_mode(h);
-    if (h->list_warp) {
+    h->branching = h->list_warp && h->tune.step_graph == DCM_GRAPH_BRANCHED;
+    if (h->branching) {
         cudaStreamCaptureStatus st;
         cudaGraph_t g = nullptr;
         e = cudaStreamGetCaptureInfo(main, &st, nullptr, &g);
@@ -783,10 +784,9 @@ static int capture(dcm_handle *h, bool detect, cudaGraphExec_t *exec)
             e = cudaGraphConditionalHandleCreate(&h->cond[q], g, 1, cudaGraphCondAssignDefault);
     }
     int r = e == cudaSuccess ? DCM_OK : fail_cuda(e, "conditional handle", __FILE__, __LINE__);
-    h->capturing = true;
     h->br_kernels[0] = h->br_kernels[1] = 0;
     if (!r) r = enqueue_step(h, detect, true);
-    h->capturing = false;
+    h->branching = false;
     if (h->stream != main) {                 // an error inside a branch body
         cudaGraph_t body = nullptr;
         (void)cudaStreamEndCapture(h->side, &body);
@@ -1010,6 +1010,8 @@ extern "C" int dcm_set_tuning(dcm_handle *h, const dcm_tuning *t)
     if (t->list_lanes != 0 && t->list_lanes != 4 && t->list_lanes != 8 && t->list_lanes != 16 &&
         t->list_lanes != 32)
         return fail(DCM_ERR_ARG, "list_lanes must be 4, 8, 16 or 32 (0: 8)");
+    if (t->step_graph != DCM_GRAPH_BRANCHED && t->step_graph != DCM_GRAPH_FLAT)
+        return fail(DCM_ERR_ARG, "step_graph must be DCM_GRAPH_BRANCHED or DCM_GRAPH_FLAT");
     h->tune = *t;
     invalidate_graphs(h);
     return DCM_OK;

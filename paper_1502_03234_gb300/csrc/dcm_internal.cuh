@@ -217,7 +217,7 @@ struct dcm_handle {
     cudaStream_t side;                  // records the branch bodies
     cudaGraphConditionalHandle cond[2]; // of the graph being captured: list step, forces
                                         // (a handle serves one conditional node)
-    bool capturing;                     // enqueue_step is recording a graph
+    bool branching;                     // enqueue_step is recording a graph with branches
     int br_kernels[2];                  // kernels in bodies taken on rebuild / reuse
     // kernel nodes of one captured step: [plain, detect] x [rebuild, reuse]
     int kernels_plain, kernels_detect, kernels_plain_reuse, kernels_detect_reuse;

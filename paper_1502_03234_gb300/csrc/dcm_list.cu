@@ -144,7 +144,7 @@ int launch_list_step(dcm_handle *h, bool force_rebuild)
     int64_t N = h->n;
     int cgrid = h->num_sms * 2;
     list_mode(h);
-    const bool set_cond = h->capturing && h->list_warp;
+    const bool set_cond = h->branching;
     k_list_check<<<cgrid, 256, 0, h->stream>>>(h->b, h->x, h->x_ref, h->rc, h->rl_ref, h->lflags,
                                                force_rebuild ? 1 : 0, h->cond[0], h->cond[1],
                                                set_cond ? 1 : 0);

@@ -22,6 +22,7 @@ DCM_FP64, DCM_MIXED = 0, 1
 DCM_HOST, DCM_DEVICE = 0, 1
 DCM_MAX_CLASSES = 8
 DCM_WALK_WARP, DCM_WALK_LANES = 0, 1
+DCM_GRAPH_BRANCHED, DCM_GRAPH_FLAT = 0, 1
 
 #: every entry point include/dcm.h declares (checked by the ABI test)
 EXPORTS = [
@@ -61,7 +62,8 @@ class dcm_params(C.Structure):
 
 class dcm_tuning(C.Structure):
     _fields_ = [("lanes", C.c_int32 * DCM_MAX_CLASSES), ("block", C.c_int32),
-                ("walk", C.c_int32), ("list_lanes", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("walk", C.c_int32), ("list_lanes", C.c_int32), ("step_graph", C.c_int32),
+                ("reserved", C.c_int32 * 4)]
 
 
 class dcm_stats(C.Structure):
@@ -264,6 +266,7 @@ def dcm_set_tuning(h, lanes, block: int = 256, walk: int = None, list_lanes: int
     t.block = int(block)
     t.walk = DCM_WALK_LANES if walk is None else int(walk)
     t.list_lanes = int(list_lanes)
+    t.step_graph = dcm_get_tuning(h).step_graph          # kept (see set_step_graph)
     check(lib().dcm_set_tuning(h, C.byref(t)))
 
 
@@ -423,6 +426,12 @@ class System:
     def set_tuning(self, lanes, block=256, walk=None, list_lanes=8):
         """lanes/block select the lanes walk unless walk=DCM_WALK_WARP"""
         dcm_set_tuning(self.h, lanes, block, walk, list_lanes)
+
+    def set_step_graph(self, shape: int):
+        """DCM_GRAPH_BRANCHED (default) or DCM_GRAPH_FLAT"""
+        t = dcm_get_tuning(self.h)
+        t.step_graph = int(shape)
+        check(lib().dcm_set_tuning(self.h, C.byref(t)))
 
     def sync(self):
         dcm_sync(self.h)

@@ -212,27 +212,77 @@ def test_list_mode_stays_complete_while_reused(dcm, orc, prec, walk):
     assert np.all(err <= FP64_ABS + FP64_REL * fmag + extra), err.max()
 
 
+@pytest.mark.parametrize("lanes", [4, 8, 16])
+def test_list_force_kernel_on_a_reuse_step(dcm, orc, lanes):
+    # the forces of a step that reused its lists come from the list kernel
+    # (4, 8 or 16 lanes per particle): the same pairs as the definition at
+    # the current positions
+    s = slabgen.make_slab(12000, seed=44)
+    with dcm.System(s.box, len(s.x), precision=1, skin=0.4) as sy:
+        sy.set_tuning([2, 1, 2, 2], 128, WALKS["warp"], lanes)
+        sy.set_state(s.x, s.v)
+        sy.step(3)
+        for _ in range(30):
+            b0 = sy.stats().list_builds
+            sy.step(1)
+            sy.sync()
+            if sy.stats().list_builds == b0:
+                break
+        else:
+            pytest.fail("no step reused its lists")
+        npair = sy.pair_counts()
+        _, rc, _ = sy.cutoffs()
+        x, _, f = sy.get_state()
+        nc, _, _ = sy.cells()
+    ref = orc.forces(x, rc, s.box, nc)
+    assert np.array_equal(npair, ref.npair)
+    err = np.linalg.norm(f - ref.f, axis=1)
+    fmag = np.linalg.norm(ref.f, axis=1)
+    assert np.all(err <= FP64_ABS + FP64_REL * fmag + 5e-4), err.max()
+
+
 def test_step_graph_branches_on_rebuild(dcm):
     # with the warp list kernels each captured step holds the rebuild-only
     # work in graph IF nodes: a step that reuses its lists launches fewer
     # kernels; without lists (or with the lanes kernels) there is no branch
     s = slabgen.make_slab(9001, seed=43)
     counts = {}
-    for skin, walk in ((0.3, "warp"), (0.3, "lanes"), (0.0, "warp")):
+    for skin, walk, flat in ((0.3, "warp", 0), (0.3, "lanes", 0), (0.0, "warp", 0),
+                             (0.3, "warp", 1)):
         with dcm.System(s.box, len(s.x), precision=1, skin=skin) as sy:
             sy.set_tuning([2, 1, 2, 2], 128, WALKS[walk])
+            sy.set_step_graph(dcm.DCM_GRAPH_FLAT if flat else dcm.DCM_GRAPH_BRANCHED)
             sy.set_state(s.x, s.v)
             sy.step(4)
             sy.sync()
             st = sy.stats()
-            counts[skin, walk] = (st.kernels_plain, st.kernels_plain_reuse,
-                                  st.kernels_detect, st.kernels_detect_reuse)
-    kp, kpr, kd, kdr = counts[0.3, "warp"]
+            counts[skin, walk, flat] = (st.kernels_plain, st.kernels_plain_reuse,
+                                        st.kernels_detect, st.kernels_detect_reuse)
+    kp, kpr, kd, kdr = counts[0.3, "warp", 0]
     assert 0 < kpr < kp and 0 < kdr < kd, counts
     assert kd - kdr == kp - kpr - 4, counts      # class lists run on every detection
-    for key in ((0.3, "lanes"), (0.0, "warp")):
+    for key in ((0.3, "lanes", 0), (0.0, "warp", 0), (0.3, "warp", 1)):
         kp, kpr, kd, kdr = counts[key]
         assert kp == kpr > 0 and kd == kdr > kp, counts
+
+
+def test_step_graph_shapes_agree(dcm):
+    # the branched and the flat step graph run the same kernels on the same
+    # data: bit-identical trajectories
+    s = slabgen.make_slab(9001, seed=45)
+    out = []
+    for shape in (dcm.DCM_GRAPH_BRANCHED, dcm.DCM_GRAPH_FLAT):
+        with dcm.System(s.box, len(s.x), precision=1, skin=0.3) as sy:
+            sy.set_tuning([2, 1, 2, 2], 128, WALKS["warp"])
+            sy.set_step_graph(shape)
+            sy.set_state(s.x, s.v)
+            sy.step(40)
+            sy.sync()
+            x, v, f = sy.get_state()
+            out.append((x, v, f, sy.stats().list_builds))
+    assert out[0][3] == out[1][3] >= 2
+    for a, b in zip(out[0][:3], out[1][:3]):
+        assert np.array_equal(a, b)
 
 
 def test_list_capacity_overflow_recovers(dcm, orc):
