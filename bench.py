@@ -84,10 +84,14 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
-    ap.add_argument("--skin", type=float, default=0.5,
+    ap.add_argument("--skin", type=float, default=0.7,
                     help="Verlet-list skin in sigma (0: direct link-cell walk every step)")
     ap.add_argument("--step-graph", default="branched", choices=["branched", "flat"],
                     help="flat: no conditional nodes in the step graph (for per-kernel profiling)")
+    ap.add_argument("--skin-time", type=float, default=0.06,
+                    help="velocity-adaptive skin shares: share = clamp(skin_time |v|, skin_floor, "
+                         "skin/2); 0: skin/2 for every particle")
+    ap.add_argument("--skin-floor", type=float, default=0.08)
     ap.add_argument("--list-margin", type=float, default=1.0,
                     help="interface-distance margin of the Verlet-list radius in sigma")
     ap.add_argument("--workload", default="slab", choices=["slab", "wavy", "ensemble", "serving"])
@@ -282,28 +286,36 @@ def _timed(sy, stream, flush, k, warm):
     _timed.kinds"""
     import torch
 
-    for _ in range(warm):
-        with torch.cuda.stream(stream):
-            flush()
-        sy.step(1)
-    sy.sync()
-    out, phase, kinds = [], {}, []
-    builds = sy.stats().list_builds
-    for _ in range(k):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        with torch.cuda.stream(stream):
-            flush()
-            e0.record(stream)
-        sy.step(1)
-        with torch.cuda.stream(stream):
-            e1.record(stream)
-        for key, val in sy.phase_times().items():
-            phase[key] = phase.get(key, 0.0) + val / k
-        e1.synchronize()
-        out.append(e0.elapsed_time(e1))
-        kind, builds = _kind(sy, builds)
-        kinds.append(kind)
+    def run(nsteps, phases):
+        sy.set_timing(phases)
+        for _ in range(warm):
+            with torch.cuda.stream(stream):
+                flush()
+            sy.step(1)
+        sy.sync()
+        out, phase, kinds = [], {}, []
+        builds = sy.stats().list_builds
+        for _ in range(nsteps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                flush()
+                e0.record(stream)
+            sy.step(1)
+            with torch.cuda.stream(stream):
+                e1.record(stream)
+            if phases:
+                for key, val in sy.phase_times().items():
+                    phase[key] = phase.get(key, 0.0) + val / nsteps
+            e1.synchronize()
+            out.append(e0.elapsed_time(e1))
+            kind, builds = _kind(sy, builds)
+            kinds.append(kind)
+        return out, phase, kinds
+
+    # timed without the per-phase events; the phases over the next steps
+    out, _, kinds = run(k, False)
+    _, phase, _ = run(min(k, 100), True)
     _timed.kinds = kinds
     return out, phase
 
@@ -335,10 +347,10 @@ def run_workload(args):
             def wavy(n, steps, warm):
                 s = slabgen.make_slab(n, seed=3, capillary_amp=1.0)
                 sy = dcm.System(s.box, n, precision=dcm.DCM_MIXED, rc_min=3.0, rc_max=7.0,
-                                skin=args.skin, stream=stream.cuda_stream)
+                                skin=args.skin, skin_time=args.skin_time,
+                                skin_floor=args.skin_floor, stream=stream.cuda_stream)
                 sy.set_state(s.x, s.v)
                 sy.compute_forces()
-                sy.set_timing(True)
                 ms, ph = _timed(sy, stream, flush, steps, warm)
                 st = sy.stats()
                 x, _, _ = sy.get_state()
@@ -361,6 +373,7 @@ def run_workload(args):
                                        f"phases), DCM r_c 3/7, 1-sigma voxels, detection every "
                                        f"2 steps, mixed precision",
                            "n": n, "rc_min": 3.0, "rc_max": 7.0, "skin": args.skin,
+                           "skin_time": args.skin_time, "skin_floor": args.skin_floor,
                            "phase_ms_avg": ph,
                            "pairs_per_particle": st.pairs / n,
                            "l2": L2_NOTE},
@@ -370,13 +383,14 @@ def run_workload(args):
             mem = slabgen.make_ensemble(64, 4096, 131072, 0.65, 0.85, seed=0)
             boxes = [m.slab.box for m in mem]
             ns = [m.n for m in mem]
-            params = [dcm.default_params(precision=dcm.DCM_MIXED, skin=args.skin) for _ in mem]
+            params = [dcm.default_params(precision=dcm.DCM_MIXED, skin=args.skin,
+                                         skin_time=args.skin_time, skin_floor=args.skin_floor)
+                      for _ in mem]
             ens = dcm.Ensemble(boxes, ns, params, stream=stream.cuda_stream)
             for k, m in enumerate(mem):
                 ens.set_system_state(k, m.slab.x, m.slab.v)
             ens.compute_forces()
             choice = autotune.tune_live(ens)
-            ens.set_timing(True)
             ms, ph = _timed(ens, stream, flush, args.steps, args.warmup)
             st = ens.stats()
             kernels = _launches(st, _timed.kinds)
@@ -391,6 +405,7 @@ def run_workload(args):
                                        "DCM r_c 3/6, mixed precision; one persistent force "
                                        "launch per step, each step one CUDA graph",
                            "systems": len(ns), "n_total": ntot, "n_min": min(ns), "skin": args.skin,
+                           "skin_time": args.skin_time, "skin_floor": args.skin_floor,
                            "n_max": max(ns), "phase_ms_avg": ph, "tuning": choice,
                            "l2": L2_NOTE},
                 "latency_ms": {"p50": _pct(ms, 50), "p99": _pct(ms, 99), "unit": "ms per step"},
@@ -398,7 +413,8 @@ def run_workload(args):
         else:
             rep = serving.serve_trace(count=args.requests, rate=20.0, n_min=2048, n_max=524288,
                                       steps_min=100, steps_max=2000, budget_gb=120.0,
-                                      precision=dcm.DCM_MIXED, skin=args.skin)
+                                      precision=dcm.DCM_MIXED, skin=args.skin,
+                                      skin_time=args.skin_time, skin_floor=args.skin_floor)
             summ = rep.summary()
             line.update({
                 "metric": "aggregate atom-steps/s of a served request stream; p50/p99 latency",
@@ -407,7 +423,8 @@ def run_workload(args):
                                        f"req/s, N log-uniform in [2048, 524288], nsteps uniform "
                                        f"in [100, 2000], 120 GB HBM budget, continuous batching "
                                        f"(up to 16 resident slots, 50-step chunks), mixed "
-                                       f"precision", "requests": args.requests, "skin": args.skin},
+                                       f"precision", "requests": args.requests, "skin": args.skin,
+                           "skin_time": args.skin_time, "skin_floor": args.skin_floor},
                 "latency_s": summ["latency_s"], "serving": summ})
     line["clocks"] = clk.summary()
     print(json.dumps(line), flush=True)
@@ -452,7 +469,8 @@ def main():
 
     def make_system(precision):
         sy = dcm.System(slab.box, n, precision=precision, stream=stream.cuda_stream,
-                        skin=args.skin, list_margin=args.list_margin)
+                        skin=args.skin, list_margin=args.list_margin, skin_time=args.skin_time,
+                        skin_floor=args.skin_floor)
         if args.step_graph == "flat":
             sy.set_step_graph(dcm.DCM_GRAPH_FLAT)
         sy.set_state(slab.x, slab.v)
@@ -627,6 +645,8 @@ def main():
         cfg = workload_config(n, args.precision)
         cfg["skin"] = args.skin
         cfg["list_margin"] = args.list_margin
+        cfg["skin_time"] = args.skin_time
+        cfg["skin_floor"] = args.skin_floor
         cfg["phase_ms_avg"] = {k: v / phase_steps for k, v in phase_sum.items()}
         cfg["phase_note"] = ("per-phase CUDA events inside the step graph, on a second run of the "
                              "same steps from the same start (the timed run records none)")

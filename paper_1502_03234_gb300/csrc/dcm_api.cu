@@ -113,6 +113,9 @@ static int check_params(const dcm_box *box, int64_t n, const dcm_params *p)
         return fail(DCM_ERR_ARG, "n_classes must be 2..%d", DCM_MAX_CLASSES);
     if (p->detect_every < 0) return fail(DCM_ERR_ARG, "detect_every must be >= 0");
     if (!(p->skin >= 0) || p->skin > 2.0) return fail(DCM_ERR_ARG, "skin must be in [0, 2] sigma");
+    if (!(p->skin_time >= 0.f) || !(p->skin_floor >= 0.f) ||
+        (p->skin_time > 0.f && p->skin_floor > 0.5 * p->skin))
+        return fail(DCM_ERR_ARG, "skin_time, skin_floor must be >= 0, skin_floor <= skin/2");
     return DCM_OK;
 }
 
@@ -181,6 +184,8 @@ static int setup_geometry(const dcm_box *box, int64_t n, const dcm_params *p, Ge
     g.eps = p->eps;
     g.sigma = p->sigma;
     g.skin = p->skin > 0 ? p->skin : 0.0;
+    g.skin_time = p->skin_time;
+    g.skin_floor = p->skin_floor;
     g.eps24 = 24.0 * p->eps;
     g.eps48 = 48.0 * p->eps;
     g.eps2 = 2.0 * p->eps;
@@ -215,7 +220,7 @@ static int64_t bytes_for(const Geom &g, int64_t n, int precision)
     per_p += 36;   // spd (FP64) or rq + pk + inv (MIXED)
     int64_t per_v = 4 + 4 + 4 + 8 + 1 + 8 + 8 + 4 + 16 + 2;
     int64_t ntiles = (ncell + 2047) / 2048 + 1;
-    int64_t lists = g.skin > 0 ? 4 * list_cap(g, n) + n * (4 + 4 + 24 + 8) : 0;
+    int64_t lists = g.skin > 0 ? 4 * list_cap(g, n) + n * (4 + 4 + 24 + 8 + 8) : 0;
     return n * per_p + ncell * 8 + 8 + nv * per_v + ntiles * 4 + 4096 + 256 * 8 * 8 + lists;
 }
 
@@ -253,7 +258,7 @@ extern "C" int dcm_destroy(dcm_handle *h)
                     h->class_count_dev, h->B, h->sm1, h->sm2, h->Bs, h->S, h->D0, h->D1, h->stamp,
                     h->flist, h->fcount, h->kacc, h->npair, h->pe, h->vir, h->red_part, h->red_out,
                     h->err, h->stats, h->tmp3n, h->geo_dev, h->off_dev, h->nl, h->nl_cnt,
-                    h->nl_start, h->nl_tiles, h->x_ref, h->rl_ref, h->lflags};
+                    h->nl_start, h->nl_tiles, h->x_ref, h->rl_ref, h->sh_ref, h->sh, h->lflags};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -417,6 +422,8 @@ static int create_systems(int M, const dcm_box *boxes, const int64_t *ns, const 
         ALLOC(h->nl_tiles, (N + 2047) / 2048 + 1);
         ALLOC(h->x_ref, 3 * N);
         ALLOC(h->rl_ref, N);
+        ALLOC(h->sh_ref, N);
+        ALLOC(h->sh, N);
         ALLOC(h->lflags, LF_WORDS);
     }
 #undef ALLOC
@@ -444,6 +451,7 @@ static int create_systems(int M, const dcm_box *boxes, const int64_t *ns, const 
     if (h->nl) {
         cudaMemsetAsync(h->lflags, 0, sizeof(int) * LF_WORDS, h->stream);
         cudaMemsetAsync(h->lflags + LF_EXCESS, 0x80, sizeof(int), h->stream);    // LF_EXCESS_RESET
+        cudaMemsetAsync(h->lflags + LF_PARTNER, 0x80, sizeof(int), h->stream);
         // capacity density of the warp list fill (float bits); a host member
         // so the asynchronous copy reads live memory
         h->list_scale0 = h->par_host[0].list_density > 0.f ? h->par_host[0].list_density : 1.0f;
@@ -451,8 +459,13 @@ static int create_systems(int M, const dcm_box *boxes, const int64_t *ns, const 
         h->list_margin = lm > 0.f ? lm : (lm < 0.f ? 0.f : 1.0f);
         cudaMemcpyAsync(h->lflags + LF_SCALE, &h->list_scale0, sizeof(float), cudaMemcpyHostToDevice,
                         h->stream);
+        // every entry a valid slot from the start (entries past a list's
+        // count are never read, but stay harmless if they were)
+        cudaMemsetAsync(h->nl, 0, sizeof(int32_t) * h->nl_cap, h->stream);
         cudaMemsetAsync(h->x_ref, 0, sizeof(double) * 3 * N, h->stream);
         cudaMemsetAsync(h->rl_ref, 0, sizeof(float) * N, h->stream);
+        cudaMemsetAsync(h->sh_ref, 0, sizeof(float) * N, h->stream);
+        cudaMemsetAsync(h->sh, 0, sizeof(float) * N, h->stream);
     }
     cudaError_t e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {
@@ -1014,6 +1027,10 @@ extern "C" int dcm_set_tuning(dcm_handle *h, const dcm_tuning *t)
         return fail(DCM_ERR_ARG, "step_graph must be DCM_GRAPH_BRANCHED or DCM_GRAPH_FLAT");
     h->tune = *t;
     invalidate_graphs(h);
+    // the two list layouts differ (the warp kernels place each list at its
+    // capacity offset and keep its length in nl_cnt, the lanes kernels pack
+    // them): the next step rebuilds the lists for the kernels now selected
+    if (h->nl) DCM_CHECK_CUDA(cudaMemsetAsync(h->lflags + LF_OK, 0, sizeof(int), h->stream));
     return DCM_OK;
 }
 

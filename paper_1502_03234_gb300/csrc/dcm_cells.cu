@@ -124,10 +124,11 @@ __global__ void k_cell_sort(int64_t ncell, const int32_t *__restrict__ start, in
 
 // sorted position streams: sp4 = (x - cell corner in FP32, cell x index),
 // spd = absolute FP64 position (FP64 path only)
-__global__ void k_gather(Batch b, const double *__restrict__ x, const int32_t *__restrict__ sorted_id,
+__global__ void k_gather(Batch b, const double *__restrict__ x, const double *__restrict__ v,
+                         const int32_t *__restrict__ sorted_id,
                          const int32_t *__restrict__ cell_of, float4 *sp4, double4_32a *spd,
-                         const double *__restrict__ rc, float4 *rq, int4 *pk,
-                         const double *__restrict__ dist, const int *lf, float delta, int32_t *capk,
+                         const double *__restrict__ rc, float4 *rq, int4 *pk, float *sh,
+                         const double *__restrict__ dist, int *lf, float delta, int32_t *capk,
                          int32_t *inv, const int *gate)
 {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -149,13 +150,24 @@ __global__ void k_gather(Batch b, const double *__restrict__ x, const int32_t *_
         int cz = c / (g.nc[0] * g.nc[1]);
         int w = 0;
         if (capk && lf[LF_REBUILD]) {
-            // a Verlet-list build follows: list radius and the entry
-            // capacity of this particle, (4/3) pi R^3 at the density bound
+            // a Verlet-list build follows: the skin share and own list
+            // radius of this particle, and its entry capacity, (4/3) pi R^3
+            // for R = own radius + the largest share at the density bound
             // scale (1.0 sigma^-3 unless a list overflowed before) + 8
-            float rl = list_radius(g, r, dist[i], delta);
+            const size_t N = (size_t)b.N;
+            const float vx = (float)v[i], vy = (float)v[N + i], vz = (float)v[2 * N + i];
+            const float share = skin_share(g, sqrtf(fmaf(vx, vx, fmaf(vy, vy, vz * vz))));
+            const float rl = list_radius(g, r, dist[i], delta, share);
+            const float R = rl + 0.5f * (float)g.skin;
             float scale = __int_as_float(lf[LF_SCALE]);
-            capk[k] = (int32_t)ceilf(scale * 4.18879020f * rl * rl * rl) + 8;
+            capk[k] = (int32_t)ceilf(scale * 4.18879020f * R * R * R) + 8;
             w = __float_as_int(rl);
+            sh[k] = share;
+            // non-negative floats order like their bit patterns; one
+            // atomic per warp
+            const unsigned act = __activemask();
+            const unsigned mx = __reduce_max_sync(act, (unsigned)__float_as_int(share));
+            if ((threadIdx.x & 31) == __ffs(act) - 1) atomicMax(&lf[LF_SHMAX], (int)mx);
         }
         pk[k] = make_int4(i, cy, cz, w);
     }
@@ -243,9 +255,9 @@ int launch_sort_gather(dcm_handle *h, const int *gate)
                                                 h->sorted_id, gate);
     k_cell_sort<<<nblk(h->ncell, 256), 256, 0, s>>>(h->ncell, h->cell_start, h->sorted_id, gate);
     const bool wl = h->nl && h->list_warp;
-    k_gather<<<nblk(n, 256), 256, 0, s>>>(h->b, h->x, h->sorted_id, h->cell_of, h->sp4,
+    k_gather<<<nblk(n, 256), 256, 0, s>>>(h->b, h->x, h->v, h->sorted_id, h->cell_of, h->sp4,
                                           h->p.precision == DCM_FP64 ? h->spd : nullptr, h->rc,
-                                          h->rq, h->pk, h->d, h->lflags,
+                                          h->rq, h->pk, h->sh, h->d, h->lflags,
                                           h->cut_detected ? h->list_margin : 0.0f, wl ? h->nl_cnt : nullptr,
                                           h->inv, wl ? gate : nullptr);
     return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "binning launch");

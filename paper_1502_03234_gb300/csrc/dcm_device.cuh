@@ -204,10 +204,14 @@ __device__ __forceinline__ double lerp_rn(double a, double b, double t)
     return DADD(a, DMUL(t, DSUB(b, a)));
 }
 
-// Verlet-list radius of particle i: the cutoff it would get if its distance
-// to the interface dropped by delta (so small moves of the detected interface
-// do not force a rebuild), never below its current cutoff, plus the skin
-__device__ __forceinline__ float list_radius(const Geom &g, double rci, double di, float delta)
+// Own Verlet-list radius of particle i: the cutoff it would get if its
+// interface distance dropped by delta (so small moves of the detected
+// interface do not force a rebuild), never below its current cutoff, plus
+// its skin share; a pair (i, j) is listed while closer than this plus j's
+// share.  The margin (1e-5 relative + 1e-4) covers the FP32 distances of
+// the build; the reuse check takes it off again.
+__device__ __forceinline__ float list_radius(const Geom &g, double rci, double di, float delta,
+                                             float share)
 {
     float r = (float)rci;
     if (delta > 0.f && g.rc_max > g.rc_min) {
@@ -218,7 +222,22 @@ __device__ __forceinline__ float list_radius(const Geom &g, double rci, double d
                                : fmaf((float)g.cut_a, exp2f((float)g.alpha * (rmax - dd)), (float)g.cut_b));
         r = fmaxf(r, ra);
     }
-    return r * 1.00001f + (float)g.skin + 1e-4f;
+    return r * 1.00001f + 1e-4f + share;
+}
+
+// an own list radius without the build margin (for the reuse check)
+__device__ __forceinline__ float list_radius_unpadded(float rl, float share)
+{
+    return (rl - share - 1e-4f) * 0.99999f + share;
+}
+
+// skin share of a particle with speed |v|: skin/2, or clamp(skin_time |v|,
+// skin_floor, skin/2) with velocity-adaptive skins
+__device__ __forceinline__ float skin_share(const Geom &g, float speed)
+{
+    const float half = 0.5f * (float)g.skin;
+    if (g.skin_time <= 0.f) return half;
+    return fminf(fmaxf(g.skin_time * speed, g.skin_floor), half);
 }
 
 // FP32 position of a particle relative to the corner of its link cell

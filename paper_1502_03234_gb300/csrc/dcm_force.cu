@@ -62,7 +62,9 @@ struct ForceArgs {
     const int32_t *nl;
     // list build (k_list_walk)
     int32_t *nl_cnt, *nl_w;
-    float *rl_ref;
+    float *rl_ref;                // own list radius of each particle at the build (id order)
+    float *sh_ref;                // skin share of each particle at the build (id order)
+    const float *sh;              // skin share per sorted slot (warp fill)
     const double *d;
     float list_delta;
     const int *gate;
@@ -425,7 +427,9 @@ __device__ __forceinline__ void list_particle(const ForceArgs &a, int k, int lan
     int cx = (int)ui.w;
     int cy = (c / g.nc[0]) % g.nc[1];
     int cz = c / (g.nc[0] * g.nc[1]);
-    float rl = list_radius(g, a.rc[i], a.d[i], a.list_delta);
+    // uniform skin shares here: the pair radius is the own radius + skin/2
+    const float share = 0.5f * (float)g.skin;
+    float rl = list_radius(g, a.rc[i], a.d[i], a.list_delta, share) + share;
     float rl2 = rl * rl;
     float rcull = rl * 1.00002f + 1e-4f;
     float rcull2 = rcull * rcull;
@@ -502,7 +506,10 @@ __device__ __forceinline__ void list_particle(const ForceArgs &a, int k, int lan
         for (int off = G >> 1; off > 0; off >>= 1) n += __shfl_xor_sync(gmask, n, off);
         if (lane == 0) a.nl_cnt[k] = n;
     } else {
-        if (lane == 0) a.rl_ref[i] = rl;
+        if (lane == 0) {
+            a.rl_ref[i] = rl - share;
+            a.sh_ref[i] = share;
+        }
     }
 }
 
@@ -778,14 +785,15 @@ __device__ __forceinline__ void particle_force_warp(const ForceArgs &a, FwTable 
     const int i = pk.x, cy = pk.y, cz = pk.z;
     const int cx = (int)ui.w;
     const float rc2f = q4.x, rc2lo = q4.y, rc2hi = q4.z;
-    float rl2 = 0.f, rcull = q4.w;
+    float rl = 0.f, rcull = q4.w;
     int32_t *out = nullptr;
     int cap = 0, cnt = 0;
     if constexpr (FILL) {
         if (fill_on) {
-            const float rl = __int_as_float(pk.w);
-            rl2 = rl * rl;
-            rcull = fmaxf(rcull, rl * 1.00002f + 1e-4f);
+            // pair (i, j) listed while closer than i's own radius + j's share
+            rl = __int_as_float(pk.w);
+            const float shmax = __int_as_float(a.list_flags[LF_SHMAX]);
+            rcull = fmaxf(rcull, (rl + shmax) * 1.00002f + 1e-4f);
             out = a.nl_w + a.nl_start[k];
             cap = a.nl_cnt[k];
         }
@@ -898,7 +906,12 @@ __device__ __forceinline__ void particle_force_warp(const ForceArgs &a, FwTable 
                     ++ng;
                 }
                 acc.pair(g, dx, dy, dz, r2, in);
-                if constexpr (FILL) hit = fill_on && r2 < rl2 && j != k;
+                if constexpr (FILL) {
+                    if (fill_on) {
+                        const float rp = rl + a.sh[j];
+                        hit = r2 < rp * rp && j != k;
+                    }
+                }
             }
             if constexpr (FILL) {
                 const unsigned hm = __ballot_sync(0xffffffffu, hit);
@@ -916,7 +929,8 @@ __device__ __forceinline__ void particle_force_warp(const ForceArgs &a, FwTable 
     if constexpr (FILL) {
         if (fill_on && lane == 0) {
             a.nl_cnt[k] = min(cnt, cap);
-            a.rl_ref[i] = __int_as_float(pk.w);
+            a.rl_ref[i] = rl;
+            a.sh_ref[i] = a.sh[k];
             if (cnt > cap) atomicOr(a.list_flags + LF_OVERFLOW, 1);
             entries += min(cnt, cap);
         }
@@ -1143,7 +1157,7 @@ __global__ void __launch_bounds__(FW_THREADS, 8) k_force_warp(ForceArgs a)
     sq.init(a);
     if (threadIdx.x == 0) {
         s_run = FILL ? a.list_flags[LF_REBUILD] : 1;
-        s_fill = FILL ? a.list_flags[LF_WORDS - 1] : 0;
+        s_fill = FILL ? a.list_flags[LF_FILL] : 0;
     }
     __syncthreads();
     if (!s_run) return;
@@ -1307,6 +1321,8 @@ static void fill_args(dcm_handle *h, ForceArgs &a)
     a.nl_cnt = h->nl_cnt;
     a.nl_w = h->nl;
     a.rl_ref = h->rl_ref;
+    a.sh_ref = h->sh_ref;
+    a.sh = h->sh;
     a.d = h->d;
     a.list_delta = 0.f;
     a.gate = nullptr;

@@ -65,11 +65,12 @@ struct DevStats {
 // Verlet-list control words (device): see dcm_list.cu
 // Verlet-list control words: rebuild decision, lists valid, the two maxima
 // of the check, its block counter, a per-particle capacity overflow seen by
-// the last fill, the capacity density scale (float bits), the fill gate
-enum { LF_REBUILD = 0, LF_OK = 1, LF_MAXDISP = 2, LF_EXCESS = 3, LF_DONE = 4, LF_OVERFLOW = 5,
-       LF_SCALE = 6, LF_WORDS = 8 };
-// LF_EXCESS holds an order-preserving int image of a float; this is the
-// image of -3.39e38 (every byte 0x80, so a memset writes it too)
+// the last fill, the capacity density scale (float bits), the largest skin
+// share of the build (float bits), the fill gate
+enum { LF_REBUILD = 0, LF_OK = 1, LF_PARTNER = 2, LF_EXCESS = 3, LF_DONE = 4, LF_OVERFLOW = 5,
+       LF_SCALE = 6, LF_SHMAX = 7, LF_FILL = 8, LF_WORDS = 9 };
+// LF_PARTNER and LF_EXCESS hold order-preserving int images of floats; this
+// is the image of -3.39e38 (every byte 0x80, so a memset writes it too)
 constexpr int LF_EXCESS_RESET = (int)0x80808080u;
 
 constexpr int MAX_SYSTEMS = 1024;
@@ -95,6 +96,7 @@ struct Geom {
     double dt, hdtm;             // dt, dt/(2m)
     double eps, sigma;
     double skin;                 // Verlet-list skin (0: direct cell walk)
+    float skin_time, skin_floor; // velocity-adaptive skin shares (skin_time 0: skin/2 each)
     double eps24, eps48, eps2, sig2;     // LJ force/energy constants
     float eps24f, eps48f, eps2f, sig2f;
     // this system's slices of the concatenated arrays
@@ -186,7 +188,9 @@ struct dcm_handle {
     int64_t nl_cap;
     int32_t *nl_cnt, *nl_start, *nl_tiles;
     double *x_ref;               // positions at the build (id order)
-    float *rl_ref;               // list radius of each particle at the build
+    float *rl_ref;               // own list radius of each particle at the build (id order)
+    float *sh_ref;               // skin share of each particle at the build (id order)
+    float *sh;                   // skin share per sorted slot (the fill's partners)
     bool cut_detected;           // cutoffs come from detection (lists anticipate d moves)
     bool list_warp;              // lists built and walked by the warp kernels (set per capture)
     bool step_detect;            // the step being enqueued re-detects the interface

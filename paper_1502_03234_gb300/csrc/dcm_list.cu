@@ -2,21 +2,25 @@
 // 2.2.1 and Algorithm 3.3 of the thesis: store every j within r_c[i] + r_s,
 // reuse the list while no particle moved r_s/2).
 //
-// With per-particle cutoffs the reuse condition also covers cutoff growth:
-// a pair inside r_c[i](t) now was closer than r_c[i](t) + |d_i| + d_max at
-// the build (d_i the displacement of i since the build, d_max the largest
-// one), so the list of particle i (all j within its list radius R_i) stays
-// complete while |d_i| + d_max < R_i - r_c[i](t) for every i, that is while
-//     d_max + max_i (|d_i| - (R_i - r_c[i](t))) < 0,
-// both maxima taken in one pass.  (The usual rule 2 d_max < min_i headroom
-// is the special case |d_i| = d_max for all i, and rebuilds more often.)
-// R_i is the cutoff particle i would get if its interface distance dropped
-// by a margin (list_margin, 1 sigma by default), plus the skin: the detected interface jitters by about a
-// voxel, and Eq. 7 is steep near d = r_c,max, so lists sized by the current
-// cutoff alone would be rebuilt at nearly every detection.  Every step one
-// kernel measures both maxima and decides; the cell sort and the list build
-// that follow are launched every step but do nothing unless the decision
-// was "rebuild", so the step stays one fixed CUDA graph.
+// With per-particle cutoffs the reuse condition also covers cutoff growth,
+// and each particle carries its own share s_i of the skin: particle i's
+// list holds every j closer than R_i + s_j at the build, where R_i is i's
+// own list radius (anticipated cutoff + s_i).  A pair inside r_c[i](t) now
+// was closer than r_c[i](t) + |d_i| + |d_j| at the build (d the
+// displacements since), so every list stays complete while
+//     max_i (|d_i| - (R_i - r_c[i](t))) + max_j (|d_j| - s_j) < 0,
+// both maxima taken in one pass.  With uniform shares s = skin/2 this is
+// the usual rule "no two displacements add up to the skin"; with
+// velocity-adaptive shares (s_i growing with the particle's speed at the
+// build) slow particles keep short lists and the few fast ones do not
+// force early rebuilds.
+// The anticipated cutoff in R_i is the one particle i would get if its
+// interface distance dropped by a margin (list_margin, 1 sigma by default):
+// the detected interface jitters by about a voxel, and Eq. 7 is steep near
+// d = r_c,max, so lists sized by the current cutoff alone would be rebuilt
+// at nearly every detection.  Every step one kernel measures both maxima
+// and decides; the cell sort and the list build that follow run only on a
+// rebuild step (graph IF nodes, or their own gates when launched eagerly).
 //
 // Lists are indexed by the sorted slot k of the build; an entry holds the
 // sorted slot j of a neighbour (24 bits) and its row's cell offsets dy, dz
@@ -34,15 +38,15 @@ __device__ __forceinline__ int ordered_int(float f)
     return b >= 0 ? b : b ^ 0x7fffffff;
 }
 
-// largest displacement since the build and the largest excess of a
-// particle's own displacement over its headroom R_i - r_c[i]; the last block
-// to finish turns them into the decision
+// the two maxima of the reuse condition; the last block to finish turns
+// them into the decision
 __global__ void k_list_check(Batch b, const double *__restrict__ x, const double *__restrict__ x_ref,
                              const double *__restrict__ rc, const float *__restrict__ rl_ref,
-                             int *lf, int force, cudaGraphConditionalHandle cond0,
-                             cudaGraphConditionalHandle cond1, int set_cond)
+                             const float *__restrict__ sh_ref, int *lf, int force,
+                             cudaGraphConditionalHandle cond0, cudaGraphConditionalHandle cond1,
+                             int set_cond)
 {
-    float md = 0.f, mq = -3.0e38f;
+    float mp = -3.0e38f, mq = -3.0e38f;
     const size_t N = (size_t)b.N;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < b.N;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -56,17 +60,17 @@ __global__ void k_list_check(Batch b, const double *__restrict__ x, const double
         dx -= Lx * rintf(dx / Lx);
         dy -= Ly * rintf(dy / Ly);
         dz -= Lz * rintf(dz / Lz);
-        float d = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-        md = fmaxf(md, d);
-        mq = fmaxf(mq, d - fmaxf(rl_ref[i] - (float)rc[i], 0.f));
+        const float d = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        const float s = sh_ref[i];
+        mp = fmaxf(mp, d - s);
+        mq = fmaxf(mq, d - (list_radius_unpadded(rl_ref[i], s) - (float)rc[i]));
     }
     for (int off = 16; off > 0; off >>= 1) {
-        md = fmaxf(md, __shfl_xor_sync(0xffffffffu, md, off));
+        mp = fmaxf(mp, __shfl_xor_sync(0xffffffffu, mp, off));
         mq = fmaxf(mq, __shfl_xor_sync(0xffffffffu, mq, off));
     }
     if ((threadIdx.x & 31) == 0) {
-        // non-negative floats order like their bit patterns
-        atomicMax(&lf[LF_MAXDISP], __float_as_int(md));
+        atomicMax(&lf[LF_PARTNER], ordered_int(mp));
         atomicMax(&lf[LF_EXCESS], ordered_int(mq));
     }
     __syncthreads();
@@ -78,8 +82,8 @@ __global__ void k_list_check(Batch b, const double *__restrict__ x, const double
     __syncthreads();
     if (s_last && threadIdx.x == 0) {
         __threadfence();
-        float dmax = __int_as_float(atomicExch(&lf[LF_MAXDISP], 0));
-        // the image is its own inverse; reset to the image of -3.4e38
+        // the images are their own inverses; reset both to that of -3.4e38
+        float partner = __int_as_float(ordered_int(__int_as_float(atomicExch(&lf[LF_PARTNER], LF_EXCESS_RESET))));
         float excess = __int_as_float(ordered_int(__int_as_float(atomicExch(&lf[LF_EXCESS], LF_EXCESS_RESET))));
         int ok = atomicAdd(&lf[LF_OK], 0);
         if (atomicExch(&lf[LF_OVERFLOW], 0)) {
@@ -89,8 +93,9 @@ __global__ void k_list_check(Batch b, const double *__restrict__ x, const double
             lf[LF_OK] = 0;
             lf[LF_SCALE] = __float_as_int(__int_as_float(lf[LF_SCALE]) * 1.25f);
         }
-        int rebuild = force || !ok || (dmax + excess >= 0.f);
+        int rebuild = force || !ok || (partner + excess >= 0.f);
         lf[LF_REBUILD] = rebuild;
+        if (rebuild) lf[LF_SHMAX] = 0;          // the gather of the build takes the max
         lf[LF_DONE] = 0;
         if (set_cond) {
             cudaGraphSetConditional(cond0, (unsigned)rebuild);
@@ -104,13 +109,13 @@ __global__ void k_list_total(int64_t N, const int32_t *__restrict__ start, int64
                              DevStats *st, int fill_counts)
 {
     if (lf[LF_REBUILD] == 0) {
-        lf[LF_WORDS - 1] = 0;    // no fill on a step that keeps its lists
+        lf[LF_FILL] = 0;         // no fill on a step that keeps its lists
         return;
     }
     int64_t total = start[N];
     int ok = total <= cap;
     lf[LF_OK] = ok;
-    lf[LF_WORDS - 1] = ok;       // fill gate
+    lf[LF_FILL] = ok;            // fill gate
     st->list_builds += 1ull;
     // the warp fill walk adds its entries (start[] sums capacities there)
     st->list_entries = fill_counts ? 0ull : (unsigned long long)total;
@@ -145,11 +150,11 @@ int launch_list_step(dcm_handle *h, bool force_rebuild)
     int cgrid = h->num_sms * 2;
     list_mode(h);
     const bool set_cond = h->branching;
-    k_list_check<<<cgrid, 256, 0, h->stream>>>(h->b, h->x, h->x_ref, h->rc, h->rl_ref, h->lflags,
-                                               force_rebuild ? 1 : 0, h->cond[0], h->cond[1],
-                                               set_cond ? 1 : 0);
+    k_list_check<<<cgrid, 256, 0, h->stream>>>(h->b, h->x, h->x_ref, h->rc, h->rl_ref, h->sh_ref,
+                                               h->lflags, force_rebuild ? 1 : 0, h->cond[0],
+                                               h->cond[1], set_cond ? 1 : 0);
     const int *rebuild = h->lflags + LF_REBUILD;
-    const int *fill = h->lflags + (LF_WORDS - 1);
+    const int *fill = h->lflags + LF_FILL;
     if (h->list_warp) {
         Branch br;
         int r = branch_open(h, br, 1, 0);

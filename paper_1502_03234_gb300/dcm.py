@@ -57,7 +57,8 @@ class dcm_params(C.Structure):
                 ("cfsm_iter_max", C.c_int32), ("cfsm_eps", C.c_double),
                 ("precision", C.c_int32), ("n_classes", C.c_int32), ("cell_min", C.c_double),
                 ("skin", C.c_double), ("list_density", C.c_float),
-                ("list_margin", C.c_float), ("reserved", C.c_int32 * 4)]
+                ("list_margin", C.c_float), ("skin_time", C.c_float),
+                ("skin_floor", C.c_float), ("reserved", C.c_int32 * 2)]
 
 
 class dcm_tuning(C.Structure):

@@ -239,7 +239,7 @@ class DcmBackend(Backend):
     the state stays on the device between chunks."""
 
     def __init__(self, precision: int | None = None, tune: dict | None = None,
-                 skin: float | None = None):
+                 skin: float | None = None, skin_time: float = 0.0, skin_floor: float = 0.0):
         import torch
 
         from . import dcm
@@ -249,12 +249,15 @@ class DcmBackend(Backend):
         self.precision = dcm.DCM_MIXED if precision is None else precision
         self.tune = tune or {}
         self.skin = skin
+        self.skin_time, self.skin_floor = skin_time, skin_floor
 
     def _params(self, job: Job):
         p = job.params if job.params is not None else self.dcm.default_params()
         p.precision = self.precision
         if self.skin is not None:
             p.skin = self.skin
+            p.skin_time = self.skin_time
+            p.skin_floor = self.skin_floor
         return p
 
     def estimate(self, job: Job) -> int:
@@ -304,12 +307,13 @@ def trace_jobs(requests, min_edge: float | None = 17.0) -> list:
 
 def serve_trace(count=400, rate=20.0, n_min=2048, n_max=524288, steps_min=100, steps_max=2000,
                 budget_gb=120.0, max_slots=16, chunk=50, seed=0, precision=None,
-                realtime=True, skin=None) -> Report:
+                realtime=True, skin=None, skin_time=0.0, skin_floor=0.0) -> Report:
     from . import slabgen
 
     reqs = slabgen.make_trace(count, rate, n_min, n_max, steps_min, steps_max, seed=seed)
     jobs = trace_jobs(reqs)
-    srv = Server(DcmBackend(precision, skin=skin), int(budget_gb * 2**30), max_slots, chunk)
+    srv = Server(DcmBackend(precision, skin=skin, skin_time=skin_time, skin_floor=skin_floor),
+                 int(budget_gb * 2**30), max_slots, chunk)
     return srv.run(jobs, realtime=realtime)
 
 

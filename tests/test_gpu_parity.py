@@ -187,12 +187,20 @@ def test_list_mode_forces(dcm, orc, prec, skin, walk):
     assert np.all(err <= FP64_ABS + FP64_REL * fmag + extra), err.max()
 
 
-@pytest.mark.parametrize("prec,walk", [(0, "lanes"), (1, "warp"), (1, "lanes")])
-def test_list_mode_stays_complete_while_reused(dcm, orc, prec, walk):
+# velocity-adaptive skin shares: (skin, skin_time, skin_floor)
+ADAPTIVE = {"uniform": (0.3, 0.0, 0.0), "adaptive": (0.6, 0.04, 0.05)}
+
+
+@pytest.mark.parametrize("prec,walk,skins", [(0, "lanes", "uniform"), (1, "warp", "uniform"),
+                                             (1, "lanes", "uniform"), (1, "warp", "adaptive"),
+                                             (0, "lanes", "adaptive")])
+def test_list_mode_stays_complete_while_reused(dcm, orc, prec, walk, skins):
     # after many steps of list reuse and rebuilds the interacting pairs must
     # still be exactly those of the definition at the current positions
     s = slabgen.make_slab(9001, seed=41)
-    with dcm.System(s.box, len(s.x), precision=prec, skin=0.3) as sy:
+    skin, tau, floor = ADAPTIVE[skins]
+    with dcm.System(s.box, len(s.x), precision=prec, skin=skin, skin_time=tau,
+                    skin_floor=floor) as sy:
         sy.set_tuning([2, 1, 2, 2], 128, WALKS[walk])
         sy.set_state(s.x, s.v)
         sy.step(150)
@@ -212,13 +220,16 @@ def test_list_mode_stays_complete_while_reused(dcm, orc, prec, walk):
     assert np.all(err <= FP64_ABS + FP64_REL * fmag + extra), err.max()
 
 
-@pytest.mark.parametrize("lanes", [4, 8, 16])
-def test_list_force_kernel_on_a_reuse_step(dcm, orc, lanes):
+@pytest.mark.parametrize("lanes,skins", [(4, "uniform"), (8, "uniform"), (16, "uniform"),
+                                         (8, "adaptive")])
+def test_list_force_kernel_on_a_reuse_step(dcm, orc, lanes, skins):
     # the forces of a step that reused its lists come from the list kernel
     # (4, 8 or 16 lanes per particle): the same pairs as the definition at
     # the current positions
     s = slabgen.make_slab(12000, seed=44)
-    with dcm.System(s.box, len(s.x), precision=1, skin=0.4) as sy:
+    skin, tau, floor = ADAPTIVE[skins]
+    with dcm.System(s.box, len(s.x), precision=1, skin=skin + 0.1, skin_time=tau,
+                    skin_floor=floor) as sy:
         sy.set_tuning([2, 1, 2, 2], 128, WALKS["warp"], lanes)
         sy.set_state(s.x, s.v)
         sy.step(3)
@@ -230,6 +241,36 @@ def test_list_force_kernel_on_a_reuse_step(dcm, orc, lanes):
                 break
         else:
             pytest.fail("no step reused its lists")
+        npair = sy.pair_counts()
+        _, rc, _ = sy.cutoffs()
+        x, _, f = sy.get_state()
+        nc, _, _ = sy.cells()
+    ref = orc.forces(x, rc, s.box, nc)
+    assert np.array_equal(npair, ref.npair)
+    err = np.linalg.norm(f - ref.f, axis=1)
+    fmag = np.linalg.norm(ref.f, axis=1)
+    assert np.all(err <= FP64_ABS + FP64_REL * fmag + 5e-4), err.max()
+
+
+@pytest.mark.parametrize("first,then", [("warp", "lanes"), ("lanes", "warp")])
+def test_walk_switch_rebuilds_lists(dcm, orc, first, then):
+    # the warp and lanes kernels lay their lists out differently: switching
+    # the walk between steps rebuilds the lists at the next step, and the
+    # forces stay those of the definition
+    s = slabgen.make_slab(9001, seed=46)
+    with dcm.System(s.box, len(s.x), precision=1, skin=0.6, skin_time=0.04,
+                    skin_floor=0.05) as sy:
+        sy.set_tuning([2, 1, 2, 2], 128, WALKS[first])
+        sy.set_state(s.x, s.v)
+        sy.step(6)
+        sy.sync()
+        b0 = sy.stats().list_builds
+        sy.set_tuning([2, 1, 2, 2], 128, WALKS[then])
+        sy.step(1)
+        sy.sync()
+        assert sy.stats().list_builds == b0 + 1
+        sy.step(2)
+        sy.sync()
         npair = sy.pair_counts()
         _, rc, _ = sy.cutoffs()
         x, _, f = sy.get_state()
