@@ -62,9 +62,11 @@ FLOPS_PER_PAIR = 24              # 8 (distance test) + 16 (LJ force), per in-cut
 # DRAM bytes (read + write) per force launch from the committed ncu capture
 # (profiles/k_force_warp_N262144_mixed.md); None once the kernel changes
 FORCE_TRAFFIC = {"mixed": 14.96e6, "fp64": None}
-# DRAM bytes per launch of the Verlet-list force kernel (k_force_list_warp, skin 0.5,
-# N = 262,144) from the committed capture (profiles/k_force_list_warp_N262144_mixed.md)
-LIST_TRAFFIC = {"k_force_list_warp": 248.78e6 + 3.94e6}
+# DRAM bytes per launch of the Verlet-list force kernel (k_force_list_warp, N = 262,144,
+# skin 0.7 with skin_time 0.06, skin_floor 0.08) from the committed capture
+# (profiles/k_force_list_warp_N262144_mixed.md)
+LIST_TRAFFIC = {"k_force_list_warp": 206.55e6 + 4.27e6}
+LIST_TRAFFIC_CONFIG = (0.7, 0.06, 0.08, 1.0)    # skin, skin_time, skin_floor, list_margin
 # bytes the list kernel must move per particle besides its list entries: own
 # position, cutoff constants, id/cell, list start and count, queue slot, the
 # force written and the pair count
@@ -566,8 +568,9 @@ def main():
         achieved = alg_bytes / (l_ms * 1e-3) / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": HBM_PEAK_GBS, "unit": "GB/s",
                     "frac": achieved / HBM_PEAK_GBS,
-                    "traffic": (LIST_TRAFFIC.get(lkernel) if n == N_DEFAULT and args.skin == 0.5
-                                and args.list_margin == 1.0 else None),
+                    "traffic": (LIST_TRAFFIC.get(lkernel) if n == N_DEFAULT and
+                                (args.skin, args.skin_time, args.skin_floor, args.list_margin)
+                                == LIST_TRAFFIC_CONFIG else None),
                     "kernel": f"{lkernel} (mixed, Verlet lists)",
                     "peak_note": "measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                     "algorithmic_bytes_per_launch": alg_bytes, "list_entries": entries,
