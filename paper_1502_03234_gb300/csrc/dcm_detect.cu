@@ -369,6 +369,166 @@ __global__ void __launch_bounds__(DET_THREADS) k_kmeans(KmeansArgs a)
     }
 }
 
+// The same K-means for one system, with each thread's voxels held in
+// registers across the passes: the values never change during the
+// iteration, so a pass is a compare-and-add over registers, a block
+// reduction and the grid barrier (the multi-system kernel above re-reads the
+// field every pass).  A voxel is liquid when its value reaches the
+// threshold; for the exact integers held here that is u >= ceil(thr), the
+// same decision as the double comparison.
+constexpr int KM1_THREADS = 1024;
+constexpr int KM1_CACHE = 8;
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
+{
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+__global__ void __launch_bounds__(KM1_THREADS) k_kmeans1(KmeansArgs a)
+{
+    __shared__ unsigned long long s_a[3];
+    __shared__ double s_cl, s_cv, s_thr;
+    __shared__ long long s_prev;
+    __shared__ int s_done;
+    const int64_t NV = a.b.NV;
+    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    unsigned long long u[KM1_CACHE];
+    // phase A: extremes and total (exact integers); the first KM1_CACHE
+    // voxels of the thread stay in registers
+    unsigned long long mx = 0, mn = ~0ull, tot = 0;
+#pragma unroll
+    for (int c = 0; c < KM1_CACHE; ++c) {
+        const int64_t v = t + (int64_t)c * nth;
+        u[c] = v < NV ? exact_u64(a.Bs[v]) : ~0ull;     // ~0: no voxel
+        if (v < NV) {
+            mx = u[c] > mx ? u[c] : mx;
+            mn = u[c] < mn ? u[c] : mn;
+            tot += u[c];
+        }
+    }
+    for (int64_t v = t + (int64_t)KM1_CACHE * nth; v < NV; v += nth) {
+        const unsigned long long w = exact_u64(a.Bs[v]);
+        mx = w > mx ? w : mx;
+        mn = w < mn ? w : mn;
+        tot += w;
+    }
+    if (threadIdx.x == 0) {
+        s_a[0] = 0ull;
+        s_a[1] = ~0ull;
+        s_a[2] = 0ull;
+    }
+    __syncthreads();
+    for (int off = 16; off > 0; off >>= 1) {
+        unsigned long long o = __shfl_xor_sync(0xffffffffu, mx, off);
+        mx = o > mx ? o : mx;
+        o = __shfl_xor_sync(0xffffffffu, mn, off);
+        mn = o < mn ? o : mn;
+    }
+    tot = warp_sum_u64(tot);
+    if (lane == 0) {
+        atomicMax(&s_a[0], mx);
+        atomicMin(&s_a[1], mn);
+        atomicAdd(&s_a[2], tot);
+    }
+    __syncthreads();
+    const int slot = blockIdx.x % SPREAD;
+    unsigned long long *g = a.acc;
+    if (threadIdx.x == 0) {
+        atomicMax(&g[0 * SPREAD + slot], s_a[0]);
+        atomicMin(&g[1 * SPREAD + slot], s_a[1]);
+        atomicAdd(&g[2 * SPREAD + slot], s_a[2]);
+    }
+    if (!grid_barrier(a.bar, a.err)) return;
+    if (threadIdx.x == 0) {
+        unsigned long long gx = 0, gn = ~0ull;
+        for (int q = 0; q < SPREAD; ++q) {
+            unsigned long long hi = __ldcg(&g[q]), lo = __ldcg(&g[SPREAD + q]);
+            gx = hi > gx ? hi : gx;
+            gn = lo < gn ? lo : gn;
+        }
+        s_cl = (double)gx;
+        s_cv = (double)gn;
+        s_prev = -1;
+        s_done = 0;
+        s_thr = DMUL(DADD(s_cl, s_cv), 0.5);
+    }
+    __syncthreads();
+    int it = 0;
+    while (it < a.max_iter) {
+        const unsigned long long thr = (unsigned long long)ceil(s_thr);
+        if (threadIdx.x == 0) {
+            s_a[0] = 0ull;
+            s_a[1] = 0ull;
+        }
+        __syncthreads();
+        unsigned long long cnt = 0, sum = 0;
+#pragma unroll
+        for (int c = 0; c < KM1_CACHE; ++c) {
+            const bool in = u[c] != ~0ull && u[c] >= thr;
+            cnt += in ? 1ull : 0ull;
+            sum += in ? u[c] : 0ull;
+        }
+        for (int64_t v = t + (int64_t)KM1_CACHE * nth; v < NV; v += nth) {
+            const unsigned long long w = exact_u64(a.Bs[v]);
+            cnt += w >= thr ? 1ull : 0ull;
+            sum += w >= thr ? w : 0ull;
+        }
+        cnt = warp_sum_u64(cnt);
+        sum = warp_sum_u64(sum);
+        if (lane == 0 && cnt) {
+            atomicAdd(&s_a[0], cnt);
+            atomicAdd(&s_a[1], sum);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long *p = g + (3 + 2 * (it % 3)) * SPREAD;
+            if (s_a[0]) {
+                atomicAdd(&p[slot], s_a[0]);
+                atomicAdd(&p[SPREAD + slot], s_a[1]);
+            }
+            if (blockIdx.x == 0) {   // clear the pair of the next pass
+                unsigned long long *nx = g + (3 + 2 * ((it + 1) % 3)) * SPREAD;
+                for (int q = 0; q < 2 * SPREAD; ++q) nx[q] = 0ull;
+            }
+        }
+        if (!grid_barrier(a.bar, a.err)) return;
+        ++it;
+        if (threadIdx.x == 0) {
+            const unsigned long long *p = g + (3 + 2 * ((it - 1) % 3)) * SPREAD;
+            long long nl = (long long)spread_sum(p);
+            unsigned long long sl = spread_sum(p + SPREAD);
+            if (nl == s_prev) {      // same threshold set as the previous pass
+                s_done = 1;
+            } else {
+                long long nvap = NV - nl;
+                unsigned long long total = spread_sum(g + 2 * SPREAD);
+                if (nl > 0) s_cl = (double)sl / (double)nl;
+                if (nvap > 0) s_cv = (double)(total - sl) / (double)nvap;
+                s_prev = nl;
+                s_thr = DMUL(DADD(s_cl, s_cv), 0.5);
+            }
+        }
+        __syncthreads();
+        if (s_done) break;
+    }
+    const unsigned long long thr = (unsigned long long)ceil(s_thr);
+#pragma unroll
+    for (int c = 0; c < KM1_CACHE; ++c) {
+        const int64_t v = t + (int64_t)c * nth;
+        if (v < NV) a.S[v] = u[c] >= thr ? 0 : 1;
+    }
+    for (int64_t v = t + (int64_t)KM1_CACHE * nth; v < NV; v += nth)
+        a.S[v] = exact_u64(a.Bs[v]) >= thr ? 0 : 1;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.st->kmeans_iters = it;
+        a.st->c_liquid = s_cl;
+        a.st->c_vapor = s_cv;
+    }
+}
+
 // ---- CFSM (Algorithm 4.3) ------------------------------------------------------
 __device__ __forceinline__ int64_t vox(int x, int y, int z, int nx, int ny)
 {
@@ -667,11 +827,12 @@ int launch_classify_rc(dcm_handle *h)
     return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "classify launch");
 }
 
-static int coop_launch(dcm_handle *h, const void *fn, int grid, size_t smem, void **args)
+static int coop_launch(dcm_handle *h, const void *fn, int grid, size_t smem, void **args,
+                       int block = DET_THREADS)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(DET_THREADS);
+    cfg.blockDim = dim3(block);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = h->stream;
     cudaLaunchAttribute attr[1];
@@ -775,11 +936,19 @@ int launch_detect(dcm_handle *h)
         a.err = h->err;
         a.st = h->stats;
         void *args[] = {(void *)&a};
-        size_t smem = kmeans_smem(b.M);
-        int grid = coop_grid_size(h, (const void *)k_kmeans, DET_THREADS, smem);
-        int64_t need = (nv + DET_THREADS - 1) / DET_THREADS;
-        if (grid > need) grid = (int)(need > 0 ? need : 1);
-        int rc = coop_launch(h, (const void *)k_kmeans, grid, smem, args);
+        int rc;
+        if (b.M == 1) {
+            int grid = coop_grid_size(h, (const void *)k_kmeans1, KM1_THREADS, 0);
+            int64_t need = (nv + KM1_THREADS - 1) / KM1_THREADS;
+            if (grid > need) grid = (int)(need > 0 ? need : 1);
+            rc = coop_launch(h, (const void *)k_kmeans1, grid, 0, args, KM1_THREADS);
+        } else {
+            size_t smem = kmeans_smem(b.M);
+            int grid = coop_grid_size(h, (const void *)k_kmeans, DET_THREADS, smem);
+            int64_t need = (nv + DET_THREADS - 1) / DET_THREADS;
+            if (grid > need) grid = (int)(need > 0 ? need : 1);
+            rc = coop_launch(h, (const void *)k_kmeans, grid, smem, args);
+        }
         if (rc) return rc;
     }
     // CFSM
