@@ -35,6 +35,12 @@ namespace dcm {
 constexpr int FORCE_THREADS = 256;
 constexpr float GUARD = 3.814697265625e-06f;   // 2^-18
 
+// the cell and LJ constants of a single-system launch (kernel parameters)
+struct ListConst {
+    float cf[3], ncx, halfnc;
+    float sig2f, eps48f, eps24f, eps2f;
+};
+
 struct ForceArgs {
     Batch b;
     const int32_t *class_buf;     // [0..K) counts, [K..2K) offsets
@@ -65,6 +71,7 @@ struct ForceArgs {
     float *rl_ref;                // own list radius of each particle at the build (id order)
     float *sh_ref;                // skin share of each particle at the build (id order)
     const float *sh;              // skin share per sorted slot (warp fill)
+    ListConst lc;                 // one system: its cell and LJ constants
     const double *d;
     float list_delta;
     const int *gate;
@@ -646,7 +653,7 @@ constexpr int FW_ROWS = 128;                 // row table entries per warp
 constexpr int FW_GRAB = 4;                   // particles per queue grab
 constexpr int FW_LIST_G = 8;                 // lanes per particle of the list kernel
 constexpr int FW_LIST_U = 4;                 // list entries in flight per lane
-constexpr int FW_LIST_MINB = 6;              // resident blocks per SM of the list kernel (80 registers)
+constexpr int FW_LIST_MINB = 9;              // resident blocks per SM of the list kernel (56 registers)
 constexpr float FW_FIX_LIMIT = 65536.f;      // |partial| bound of the exact sum
 
 struct FwTable {
@@ -696,8 +703,10 @@ struct WarpAcc {
     float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f, v4 = 0.f, v5 = 0.f;
     int np = 0;
 
-    // one candidate (dx, dy, dz) = r_i - r_j with in = "inside r_c[i]"
-    __device__ __forceinline__ void pair(const Geom &g, float dx, float dy, float dz, float r2,
+    // one candidate (dx, dy, dz) = r_i - r_j with in = "inside r_c[i]";
+    // C: the system's LJ constants (a Geom, or the launch's ListConst)
+    template <class C>
+    __device__ __forceinline__ void pair(const C &g, float dx, float dy, float dz, float r2,
                                          bool in)
     {
         float r2inv = rcp_approx(r2);
@@ -971,21 +980,26 @@ __device__ __forceinline__ double group_tree_sum(float p)
 // (dz + 8) << 28; the cell x offset comes from the cell x indices stored
 // with the positions (every true offset is below half the cells along x).
 // Same pair rule and FP64 re-decision as the direct walk.  k < 0: an idle
-// group (past the end of the queue).
-template <bool ENERGY, int G>
+// group (past the end of the queue).  SINGLE (one system): the cell and LJ
+// constants come from the launch parameters (no registers held for them,
+// which lets 8 blocks of 128 threads share an SM).
+template <bool ENERGY, int G, bool SINGLE>
 __device__ __forceinline__ void particle_force_list_group(const ForceArgs &a, int k, int gl,
                                                           int &ng)
 {
     WarpAcc<ENERGY> acc;
     int i = 0;
     if (k >= 0) {
-        const Geom &g = a.b.sys[sys_p(a.b, k)];
+        const Geom &g = a.b.sys[SINGLE ? 0 : sys_p(a.b, k)];
         const float4 ui = a.sp4[k];
         const float4 q4 = a.rq[k];
         i = a.pk[k].x;
         const float rc2f = q4.x, rc2lo = q4.y, rc2hi = q4.z;
-        const float ncx = (float)g.nc[0], halfnc = 0.5f * (float)g.nc[0];
-        const float cf0 = g.cf[0], cf1 = g.cf[1], cf2 = g.cf[2];
+        const float ncx = SINGLE ? a.lc.ncx : (float)g.nc[0];
+        const float halfnc = SINGLE ? a.lc.halfnc : 0.5f * (float)g.nc[0];
+        const float cf0 = SINGLE ? a.lc.cf[0] : g.cf[0];
+        const float cf1 = SINGLE ? a.lc.cf[1] : g.cf[1];
+        const float cf2 = SINGLE ? a.lc.cf[2] : g.cf[2];
         const int32_t *list = a.nl + a.nl_start[k];
         const int cnt = a.nl_cnt[k];
         auto one = [&](int e, float4 uj) {
@@ -1005,7 +1019,10 @@ __device__ __forceinline__ void particle_force_list_group(const ForceArgs &a, in
                 in = fp64_inside(a, g, i, a.sorted_id[j], DMUL(rci, rci));
                 ++ng;
             }
-            acc.pair(g, dx, dy, dz, r2, in);
+            if constexpr (SINGLE)
+                acc.pair(a.lc, dx, dy, dz, r2, in);
+            else
+                acc.pair(g, dx, dy, dz, r2, in);
         };
         int p = gl;
         // FW_LIST_U entries of the lane in flight per iteration: all entry
@@ -1174,7 +1191,7 @@ __global__ void __launch_bounds__(FW_THREADS, 8) k_force_warp(ForceArgs a)
 
 // Verlet-list forces; runs only on a step that keeps its lists.  A warp
 // takes 32/G consecutive queue items per grab, one per lane group.
-template <bool ENERGY, int G>
+template <bool ENERGY, int G, bool SINGLE>
 __global__ void __launch_bounds__(FW_THREADS, FW_LIST_MINB) k_force_list_warp(ForceArgs a)
 {
     __shared__ FwQueue sq;
@@ -1202,7 +1219,7 @@ __global__ void __launch_bounds__(FW_THREADS, FW_LIST_MINB) k_force_list_warp(Fo
             int q = K - 1 - t;
             k = a.class_list[sq.off[q] + (item - sq.items[t])];
         }
-        particle_force_list_group<ENERGY, G>(a, k, gl, ng);
+        particle_force_list_group<ENERGY, G, SINGLE>(a, k, gl, ng);
     }
     block_counts(a, ng, 0);
 }
@@ -1260,16 +1277,19 @@ int launch_forces(dcm_handle *h, bool energy)
         cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), h->stream);
         const int G = h->tune.list_lanes > 0 ? h->tune.list_lanes : FW_LIST_G;
         const int gl = h->num_sms * FW_LIST_MINB;   // persistent: the resident blocks
+        const bool one = h->b.M == 1;
         if (energy) {
-            k_force_list_warp<true, 8><<<gl, FW_THREADS, 0, h->stream>>>(a);   // energy steps are rare
+            k_force_list_warp<true, 8, false><<<gl, FW_THREADS, 0, h->stream>>>(a);   // energy steps are rare
         } else if (G == 4) {
-            k_force_list_warp<false, 4><<<gl, FW_THREADS, 0, h->stream>>>(a);
+            if (one) k_force_list_warp<false, 4, true><<<gl, FW_THREADS, 0, h->stream>>>(a);
+            else k_force_list_warp<false, 4, false><<<gl, FW_THREADS, 0, h->stream>>>(a);
         } else if (G == 16) {
-            k_force_list_warp<false, 16><<<gl, FW_THREADS, 0, h->stream>>>(a);
+            k_force_list_warp<false, 16, false><<<gl, FW_THREADS, 0, h->stream>>>(a);
         } else if (G == 32) {
-            k_force_list_warp<false, 32><<<gl, FW_THREADS, 0, h->stream>>>(a);
+            k_force_list_warp<false, 32, false><<<gl, FW_THREADS, 0, h->stream>>>(a);
         } else {
-            k_force_list_warp<false, 8><<<gl, FW_THREADS, 0, h->stream>>>(a);
+            if (one) k_force_list_warp<false, 8, true><<<gl, FW_THREADS, 0, h->stream>>>(a);
+            else k_force_list_warp<false, 8, false><<<gl, FW_THREADS, 0, h->stream>>>(a);
         }
         if (cudaGetLastError() != cudaSuccess) r = fail(DCM_ERR_CUDA, "force launch");
         int r2 = branch_close(h, br);
@@ -1323,6 +1343,16 @@ static void fill_args(dcm_handle *h, ForceArgs &a)
     a.rl_ref = h->rl_ref;
     a.sh_ref = h->sh_ref;
     a.sh = h->sh;
+    {
+        const Geom &g0 = h->geo_host[0];
+        for (int q = 0; q < 3; ++q) a.lc.cf[q] = g0.cf[q];
+        a.lc.ncx = (float)g0.nc[0];
+        a.lc.halfnc = 0.5f * (float)g0.nc[0];
+        a.lc.sig2f = g0.sig2f;
+        a.lc.eps48f = g0.eps48f;
+        a.lc.eps24f = g0.eps24f;
+        a.lc.eps2f = g0.eps2f;
+    }
     a.d = h->d;
     a.list_delta = 0.f;
     a.gate = nullptr;
