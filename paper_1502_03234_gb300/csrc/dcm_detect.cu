@@ -877,6 +877,8 @@ static size_t kmeans_smem(int M) { return (size_t)M * (4 * 8 + 3 * 8 + 4); }
 
 int prepare_kernels(dcm_handle *h)
 {
+    int r = prepare_force_kernels();
+    if (r) return r;
     size_t smem = kmeans_smem(h->M);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute((const void *)k_kmeans,

@@ -222,13 +222,13 @@ __device__ __forceinline__ float list_radius(const Geom &g, double rci, double d
                                : fmaf((float)g.cut_a, exp2f((float)g.alpha * (rmax - dd)), (float)g.cut_b));
         r = fmaxf(r, ra);
     }
-    return r * 1.00001f + 1e-4f + share;
+    return fmaf(r, 1.00001f, 1e-4f) + share;
 }
 
 // an own list radius without the build margin (for the reuse check)
 __device__ __forceinline__ float list_radius_unpadded(float rl, float share)
 {
-    return (rl - share - 1e-4f) * 0.99999f + share;
+    return fmaf(rl - share - 1e-4f, 0.99999f, share);
 }
 
 // skin share of a particle with speed |v|: skin/2, or clamp(skin_time |v|,
@@ -268,7 +268,7 @@ __device__ __forceinline__ float4 rc_constants(double r)
 {
     float rc2f = (float)DMUL(r, r);
     return make_float4(rc2f, rc2f * (1.f - 3.814697265625e-06f), rc2f * (1.f + 3.814697265625e-06f),
-                       (float)r * 1.00002f + 1e-4f);
+                       fmaf((float)r, 1.00002f, 1e-4f));
 }
 
 }  // namespace dcm

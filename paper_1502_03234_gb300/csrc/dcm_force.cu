@@ -72,6 +72,7 @@ struct ForceArgs {
     float *sh_ref;                // skin share of each particle at the build (id order)
     const float *sh;              // skin share per sorted slot (warp fill)
     ListConst lc;                 // one system: its cell and LJ constants
+    Geom g0;                      // one system: its geometry (kernel parameter space)
     const double *d;
     float list_delta;
     const int *gate;
@@ -261,7 +262,7 @@ __device__ __forceinline__ void particle_force(const ForceArgs &a, int k, int la
     float rc2f = (float)rci2;
     float rc2lo = rc2f * (1.f - GUARD), rc2hi = rc2f * (1.f + GUARD);
     // conservative culling radius (covers FP32 geometry error and the guard)
-    float rcull = (float)rci * 1.00002f + 1e-4f;
+    float rcull = fmaf((float)rci, 1.00002f, 1e-4f);
     float rcull2 = rcull * rcull;
     int sx = min(g.smax[0], (int)ceilf(rcull * g.inv_cf[0]));
     int sy = min(g.smax[1], (int)ceilf(rcull * g.inv_cf[1]));
@@ -272,18 +273,18 @@ __device__ __forceinline__ void particle_force(const ForceArgs &a, int k, int la
     int np = 0;
     for (int dz = -sz; dz <= sz; ++dz) {
         float gz = box_gap(dz, ui.z, g.cf[2]);
-        float remz = rcull2 - gz * gz;
+        float remz = fmaf(-gz, gz, rcull2);
         if (remz < 0.f) continue;
         int czz = cz + dz;
         czz += czz < 0 ? g.nc[2] : (czz >= g.nc[2] ? -g.nc[2] : 0);
-        float az = ui.z - (float)dz * g.cf[2];
+        float az = fmaf(-(float)dz, g.cf[2], ui.z);
         for (int dy = -sy; dy <= sy; ++dy) {
             float gy = box_gap(dy, ui.y, g.cf[1]);
-            float w2 = remz - gy * gy;
+            float w2 = fmaf(-gy, gy, remz);
             if (w2 < 0.f) continue;
             int cyy = cy + dy;
             cyy += cyy < 0 ? g.nc[1] : (cyy >= g.nc[1] ? -g.nc[1] : 0);
-            float ay = ui.y - (float)dy * g.cf[1];
+            float ay = fmaf(-(float)dy, g.cf[1], ui.y);
             float w = sqrtf(w2);
             int xlo = max(-sx, (int)floorf((ui.x - w) * g.inv_cf[0]));
             int xhi = min(sx, (int)floorf((ui.x + w) * g.inv_cf[0]));
@@ -438,7 +439,7 @@ __device__ __forceinline__ void list_particle(const ForceArgs &a, int k, int lan
     const float share = 0.5f * (float)g.skin;
     float rl = list_radius(g, a.rc[i], a.d[i], a.list_delta, share) + share;
     float rl2 = rl * rl;
-    float rcull = rl * 1.00002f + 1e-4f;
+    float rcull = fmaf(rl, 1.00002f, 1e-4f);
     float rcull2 = rcull * rcull;
     int sx = min(g.smax[0], (int)ceilf(rcull * g.inv_cf[0]));
     int sy = min(g.smax[1], (int)ceilf(rcull * g.inv_cf[1]));
@@ -450,18 +451,18 @@ __device__ __forceinline__ void list_particle(const ForceArgs &a, int k, int lan
     int32_t *out = FILL ? a.nl_w + a.nl_start[k] : nullptr;
     for (int dz = -sz; dz <= sz; ++dz) {
         float gz = box_gap(dz, ui.z, g.cf[2]);
-        float remz = rcull2 - gz * gz;
+        float remz = fmaf(-gz, gz, rcull2);
         if (remz < 0.f) continue;
         int czz = cz + dz;
         czz += czz < 0 ? g.nc[2] : (czz >= g.nc[2] ? -g.nc[2] : 0);
-        float az = ui.z - (float)dz * g.cf[2];
+        float az = fmaf(-(float)dz, g.cf[2], ui.z);
         for (int dy = -sy; dy <= sy; ++dy) {
             float gy = box_gap(dy, ui.y, g.cf[1]);
-            float w2 = remz - gy * gy;
+            float w2 = fmaf(-gy, gy, remz);
             if (w2 < 0.f) continue;
             int cyy = cy + dy;
             cyy += cyy < 0 ? g.nc[1] : (cyy >= g.nc[1] ? -g.nc[1] : 0);
-            float ay = ui.y - (float)dy * g.cf[1];
+            float ay = fmaf(-(float)dy, g.cf[1], ui.y);
             float w = sqrtf(w2);
             int xlo = max(-sx, (int)floorf((ui.x - w) * g.inv_cf[0]));
             int xhi = min(sx, (int)floorf((ui.x + w) * g.inv_cf[0]));
@@ -653,6 +654,8 @@ constexpr int FW_ROWS = 128;                 // row table entries per warp
 constexpr int FW_GRAB = 4;                   // particles per queue grab
 constexpr int FW_LIST_G = 8;                 // lanes per particle of the list kernel
 constexpr int FW_LIST_U = 4;                 // list entries in flight per lane
+constexpr int FW_WALK_MINB = 8;              // resident blocks per SM of the direct walk (64 registers)
+constexpr int FW_WALK_MINB1 = 10;            // ... one system (48 registers, 206 KB of row tables)
 constexpr int FW_LIST_MINB = 9;              // resident blocks per SM of the list kernel (56 registers)
 constexpr float FW_FIX_LIMIT = 65536.f;      // |partial| bound of the exact sum
 
@@ -719,7 +722,7 @@ struct WarpAcc {
         fz = fmaf(fr, dz, fz);
         np += in ? 1 : 0;
         if constexpr (ENERGY) {
-            pe += in ? g.eps2f * sr6 * (sr6 - 1.f) : 0.f;
+            pe = in ? fmaf(g.eps2f * sr6, sr6 - 1.f, pe) : pe;
             float gx = fr * dx, gy = fr * dy, gz = fr * dz;
             v0 = fmaf(0.5f * dx, gx, v0);
             v1 = fmaf(0.5f * dy, gy, v1);
@@ -782,12 +785,12 @@ struct WarpAcc {
 // the walk also covers the list radius R_k of the gather kernel and appends
 // every neighbour within R_k to k's list, in walk order, up to the capacity
 // the gather kernel gave it; the forces still use r_c[i] only.
-template <bool ENERGY, bool FILL>
+template <bool ENERGY, bool FILL, bool SINGLE>
 __device__ __forceinline__ void particle_force_warp(const ForceArgs &a, FwTable &tb, int k,
                                                     int lane, int &ng, bool fill_on,
                                                     long long &entries)
 {
-    const Geom &g = a.b.sys[sys_p(a.b, k)];
+    const Geom &g = SINGLE ? a.g0 : a.b.sys[sys_p(a.b, k)];
     const float4 ui = a.sp4[k];
     const float4 q4 = a.rq[k];
     const int4 pk = a.pk[k];
@@ -802,7 +805,7 @@ __device__ __forceinline__ void particle_force_warp(const ForceArgs &a, FwTable 
             // pair (i, j) listed while closer than i's own radius + j's share
             rl = __int_as_float(pk.w);
             const float shmax = __int_as_float(a.list_flags[LF_SHMAX]);
-            rcull = fmaxf(rcull, (rl + shmax) * 1.00002f + 1e-4f);
+            rcull = fmaxf(rcull, fmaf(rl + shmax, 1.00002f, 1e-4f));
             out = a.nl_w + a.nl_start[k];
             cap = a.nl_cnt[k];
         }
@@ -828,16 +831,17 @@ __device__ __forceinline__ void particle_force_warp(const ForceArgs &a, FwTable 
             int dzi = (int)(((float)r + 0.5f) * inv_ny);    // r / ny_ (exact for these sizes)
             int dz = dzi - sz, dy = r - dzi * ny_ - sy;
             float gz = box_gap(dz, ui.z, g.cf[2]);
-            float remz = rcull2 - gz * gz;
+            float remz = fmaf(-gz, gz, rcull2);
             float gy = box_gap(dy, ui.y, g.cf[1]);
-            float w2 = remz - gy * gy;
+            float w2 = fmaf(-gy, gy, remz);
             if (remz >= 0.f && w2 >= 0.f) {
                 int czz = cz + dz;
                 czz += czz < 0 ? g.nc[2] : (czz >= g.nc[2] ? -g.nc[2] : 0);
                 int cyy = cy + dy;
                 cyy += cyy < 0 ? g.nc[1] : (cyy >= g.nc[1] ? -g.nc[1] : 0);
-                az = ui.z - (float)dz * g.cf[2];
-                ay = ui.y - (float)dy * g.cf[1];
+                // explicit fused forms: the same bits in every instantiation
+                az = fmaf(-(float)dz, g.cf[2], ui.z);
+                ay = fmaf(-(float)dy, g.cf[1], ui.y);
                 float w = sqrtf(w2);
                 int xlo = max(-sx, (int)floorf((ui.x - w) * g.inv_cf[0]));
                 int xhi = min(sx, (int)floorf((ui.x + w) * g.inv_cf[0]));
@@ -1165,8 +1169,9 @@ __device__ __forceinline__ void block_counts(const ForceArgs &a, int ng, long lo
 
 // direct walk; FILL: runs only on a Verlet-list rebuild step and fills the
 // lists when the fill gate is open
-template <bool ENERGY, bool FILL>
-__global__ void __launch_bounds__(FW_THREADS, 8) k_force_warp(ForceArgs a)
+template <bool ENERGY, bool FILL, bool SINGLE>
+__global__ void __launch_bounds__(FW_THREADS, SINGLE ? FW_WALK_MINB1 : FW_WALK_MINB)
+    k_force_warp(const __grid_constant__ ForceArgs a)
 {
     __shared__ FwTable s_tab[FW_WARPS];
     __shared__ FwQueue sq;
@@ -1184,7 +1189,7 @@ __global__ void __launch_bounds__(FW_THREADS, 8) k_force_warp(ForceArgs a)
     int ng = 0;
     long long entries = 0;
     sq.drain(a, lane, [&](int k) {
-        particle_force_warp<ENERGY, FILL>(a, tb, k, lane, ng, fill_on, entries);
+        particle_force_warp<ENERGY, FILL, SINGLE>(a, tb, k, lane, ng, fill_on, entries);
     });
     block_counts(a, ng, entries);
 }
@@ -1242,6 +1247,33 @@ int launch_list_walk(dcm_handle *h, bool fill, const int *gate, float delta)
     return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "list walk launch");
 }
 
+// the direct walk's persistent grid: its resident blocks
+template <bool ENERGY, bool FILL>
+static void launch_walk(dcm_handle *h, const ForceArgs &a)
+{
+    if (h->b.M == 1)
+        k_force_warp<ENERGY, FILL, true>
+            <<<h->num_sms * FW_WALK_MINB1, FW_THREADS, 0, h->stream>>>(a);
+    else
+        k_force_warp<ENERGY, FILL, false>
+            <<<h->num_sms * FW_WALK_MINB, FW_THREADS, 0, h->stream>>>(a);
+}
+
+// ten single-system walk blocks per SM need the largest shared-memory carveout
+int prepare_force_kernels()
+{
+    const void *fns[] = {(const void *)k_force_warp<false, false, true>,
+                         (const void *)k_force_warp<true, false, true>,
+                         (const void *)k_force_warp<false, true, true>,
+                         (const void *)k_force_warp<true, true, true>};
+    for (const void *f : fns) {
+        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                             (int)cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return fail_cuda(e, "walk carveout", __FILE__, __LINE__);
+    }
+    return DCM_OK;
+}
+
 int launch_forces(dcm_handle *h, bool energy)
 {
     ForceArgs a;
@@ -1251,12 +1283,11 @@ int launch_forces(dcm_handle *h, bool energy)
     int block = h->tune.block >= 64 && h->tune.block <= FORCE_THREADS ? h->tune.block : FORCE_THREADS;
     int grid = h->num_sms * (2048 / block);
     bool fp64 = h->p.precision == DCM_FP64;
-    const int g2 = h->num_sms * 8;
     if (!fp64 && !h->nl && h->tune.walk == DCM_WALK_WARP) {
         if (energy)
-            k_force_warp<true, false><<<g2, FW_THREADS, 0, h->stream>>>(a);
+            launch_walk<true, false>(h, a);
         else
-            k_force_warp<false, false><<<g2, FW_THREADS, 0, h->stream>>>(a);
+            launch_walk<false, false>(h, a);
         return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "force launch");
     }
     if (list_warp) {
@@ -1269,9 +1300,9 @@ int launch_forces(dcm_handle *h, bool energy)
         if (r) return r;
         cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), h->stream);
         if (energy)
-            k_force_warp<true, true><<<g2, FW_THREADS, 0, h->stream>>>(a);
+            launch_walk<true, true>(h, a);
         else
-            k_force_warp<false, true><<<g2, FW_THREADS, 0, h->stream>>>(a);
+            launch_walk<false, true>(h, a);
         r = branch_else(h, br);
         if (r) return r;
         cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), h->stream);
@@ -1343,6 +1374,7 @@ static void fill_args(dcm_handle *h, ForceArgs &a)
     a.rl_ref = h->rl_ref;
     a.sh_ref = h->sh_ref;
     a.sh = h->sh;
+    a.g0 = h->geo_host[0];
     {
         const Geom &g0 = h->geo_host[0];
         for (int q = 0; q < 3; ++q) a.lc.cf[q] = g0.cf[q];

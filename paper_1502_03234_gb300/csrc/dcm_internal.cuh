@@ -275,6 +275,7 @@ int branch_close(dcm_handle *h, Branch &b);
 // lower-level helpers
 int coop_grid_size(dcm_handle *h, const void *kernel, int block, size_t smem);
 int prepare_kernels(dcm_handle *h);      // per-handle kernel attributes
+int prepare_force_kernels();             // force-kernel attributes
 int launch_barrier_timeout_check(dcm_handle *h);
 
 }  // namespace dcm
