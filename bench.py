@@ -88,6 +88,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--skin", type=float, default=0.7,
                     help="Verlet-list skin in sigma (0: direct link-cell walk every step)")
+    ap.add_argument("--list-lanes", type=int, default=0, choices=[0, 4, 8, 16, 32],
+                    help="lanes per particle of the Verlet-list force (0: the library's default)")
     ap.add_argument("--step-graph", default="branched", choices=["branched", "flat"],
                     help="flat: no conditional nodes in the step graph (for per-kernel profiling)")
     ap.add_argument("--skin-time", type=float, default=0.08,
@@ -473,6 +475,9 @@ def main():
         sy = dcm.System(slab.box, n, precision=precision, stream=stream.cuda_stream,
                         skin=args.skin, list_margin=args.list_margin, skin_time=args.skin_time,
                         skin_floor=args.skin_floor)
+        if args.list_lanes:
+            t = dcm.dcm_get_tuning(sy.h)
+            sy.set_tuning(list(t.lanes), t.block, t.walk, args.list_lanes)
         if args.step_graph == "flat":
             sy.set_step_graph(dcm.DCM_GRAPH_FLAT)
         sy.set_state(slab.x, slab.v)
