@@ -761,6 +761,7 @@ static int enqueue_step(dcm_handle *h, bool detect, bool capturing)
 {
     list_mode(h);
     h->step_detect = detect;
+    h->fold_check = h->nl != nullptr;        // the reuse test rides on the drift / cutoff kernel
     mark(h, 0, capturing);
     int r = launch_kick_drift(h);
     mark(h, 1, capturing);
@@ -772,6 +773,7 @@ static int enqueue_step(dcm_handle *h, bool detect, bool capturing)
     mark(h, 4, capturing);
     if (!r) r = launch_kick(h);
     mark(h, 5, capturing);
+    h->fold_check = false;
     return r;
 }
 

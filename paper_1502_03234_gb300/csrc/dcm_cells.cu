@@ -242,8 +242,8 @@ int launch_scan(dcm_handle *h, const int32_t *in, int32_t *out, int32_t *tiles, 
 // streams from the current positions and the per-class lists.  With the
 // warp Verlet-list kernels the drift and the cutoff kernel keep the sorted
 // positions and cutoff constants current between builds, so the gather
-// runs only with the sort; the class lists are redone when the sort ran or
-// the classes changed (class_gate null: always).
+// runs only with the sort, and so do the class lists (launch_classes;
+// class_gate null: always), which only order the force kernels' work.
 int launch_sort_gather(dcm_handle *h, const int *gate)
 {
     cudaStream_t s = h->stream;

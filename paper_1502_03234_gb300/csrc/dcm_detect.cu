@@ -724,14 +724,17 @@ __global__ void __launch_bounds__(CFSM_TAIL_THREADS) k_cfsm_tail(CfsmArgs a)
 }
 
 // ---- Algorithm 3.1 + Eq. 7-8 ----------------------------------------------------
-// rq given (warp Verlet-list kernels): the new cutoff's force constants go
-// straight to the particle's sorted slot inv[i]
-__global__ void k_cutoff(Batch b, const double *__restrict__ x, const double *__restrict__ D0,
-                         const double *__restrict__ D1, const int *__restrict__ result, double *d,
-                         double *rc, uint8_t *cls, float4 *rq, const int32_t *__restrict__ inv)
+// Algorithm 3.1 (trilinear lookup of the distance grid) and Eq. 7 for
+// particle i.  rq given (warp Verlet-list kernels): the new cutoff's force
+// constants go straight to the particle's sorted slot inv[i].  With a reuse
+// test, the particle's headroom term for the new cutoff.
+__device__ __forceinline__ void cutoff_one(Batch b, int64_t i, const double *__restrict__ x,
+                                           const double *__restrict__ D0,
+                                           const double *__restrict__ D1,
+                                           const int *__restrict__ result, double *d, double *rc,
+                                           uint8_t *cls, float4 *rq, const int32_t *__restrict__ inv,
+                                           const ListTest &lt, float &mq)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= b.N) return;
     const Geom &g = b.sys[sys_p(b, i)];
     const double *D = (*result ? D1 : D0) + g.v0;
     int i0[3], i1[3];
@@ -799,6 +802,24 @@ __global__ void k_cutoff(Batch b, const double *__restrict__ x, const double *__
     rc[i] = r;
     cls[i] = (uint8_t)c;
     if (rq) rq[inv[i]] = rc_constants(r);
+    if (lt.lf) {
+        const size_t N = (size_t)b.N;
+        const float disp = list_disp(lt, g, N, i, x[i], x[N + i], x[2 * N + i]);
+        float unused = -3.0e38f;
+        list_terms(lt, i, disp, r, unused, mq);
+    }
+}
+
+__global__ void k_cutoff(Batch b, const double *__restrict__ x, const double *__restrict__ D0,
+                         const double *__restrict__ D1, const int *__restrict__ result, double *d,
+                         double *rc, uint8_t *cls, float4 *rq, const int32_t *__restrict__ inv,
+                         ListTest lt)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float mp = -3.0e38f, mq = -3.0e38f;
+    if (i < b.N) cutoff_one(b, i, x, D0, D1, result, d, rc, cls, rq, inv, lt, mq);
+    // the headroom term for the new cutoffs and the decision
+    if (lt.lf) list_test_block(lt, mp, mq);
 }
 
 // classes for cutoffs supplied directly (scheduling only)
@@ -1001,9 +1022,11 @@ int launch_detect(dcm_handle *h)
     }
     // Algorithm 3.1 + Eq. 7
     const bool wl = h->nl && h->list_warp;
+    ListTest lt = list_test(h, false, true, true);     // the drift added the other term
+    if (!h->fold_check) lt.lf = nullptr;
     k_cutoff<<<nblk(b.N, 256), 256, 0, s>>>(b, h->x, h->D0, h->D1,
                                             (const int *)&h->stats->barrier[3], h->d, h->rc, h->cls,
-                                            wl ? h->rq : nullptr, h->inv);
+                                            wl ? h->rq : nullptr, h->inv, lt);
     return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "detect launch");
 }
 

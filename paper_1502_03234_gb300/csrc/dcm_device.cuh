@@ -271,4 +271,105 @@ __device__ __forceinline__ float4 rc_constants(double r)
                        fmaf((float)r, 1.00002f, 1e-4f));
 }
 
+// ---- the Verlet-list reuse test (condition: dcm_list.cu) ----------------
+// Any kernel that visits every particle once can carry it: the drift on a
+// step without detection, the cutoff kernel (new cutoffs) and the drift
+// together on a step with one, the stand-alone check otherwise.
+struct ListTest {
+    int *lf;                           // null: no test in this kernel
+    const double *x_ref;
+    const float *rl_ref, *sh_ref;
+    int excess;                        // the headroom term here (needs the cutoffs)
+    int partner;                       // the displacement-share term here
+    int decide;                        // this kernel's last block decides
+    int force;                         // decide "rebuild" whatever the terms
+    int set_cond;                      // also set the step graph's branch conditions
+    cudaGraphConditionalHandle cond0, cond1;
+};
+
+// order-preserving int image of a float (for atomicMax over signed values);
+// the image is its own inverse
+__device__ __forceinline__ int ordered_int(float f)
+{
+    int b = __float_as_int(f);
+    return b >= 0 ? b : b ^ 0x7fffffff;
+}
+
+// |displacement| of particle i since the build; a coordinate wrapped through
+// the box shows up as a jump of about one edge and is folded back (moves are
+// far below half an edge)
+__device__ __forceinline__ float list_disp(const ListTest &t, const Geom &g, size_t N, int64_t i,
+                                           double x, double y, double z)
+{
+    float dx = (float)(x - t.x_ref[i]);
+    float dy = (float)(y - t.x_ref[N + i]);
+    float dz = (float)(z - t.x_ref[2 * N + i]);
+    const float Lx = (float)g.L[0], Ly = (float)g.L[1], Lz = (float)g.L[2];
+    dx -= Lx * rintf(dx / Lx);
+    dy -= Ly * rintf(dy / Ly);
+    dz -= Lz * rintf(dz / Lz);
+    return sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+}
+
+// particle i's two terms: partner |d_i| - s_i, headroom |d_i| - (R_i - r_c[i])
+__device__ __forceinline__ void list_terms(const ListTest &t, int64_t i, float disp, double rci,
+                                           float &mp, float &mq)
+{
+    const float s = t.sh_ref[i];
+    if (t.partner) mp = fmaxf(mp, disp - s);
+    if (t.excess) mq = fmaxf(mq, disp - (list_radius_unpadded(t.rl_ref[i], s) - (float)rci));
+}
+
+// the decision from the two maxima (one thread, after every block added its own)
+__device__ __forceinline__ void list_decide(const ListTest &t)
+{
+    int *lf = t.lf;
+    // reset both maxima to the image of -3.4e38 for the next step
+    float partner = __int_as_float(ordered_int(__int_as_float(atomicExch(&lf[LF_PARTNER], LF_EXCESS_RESET))));
+    float excess = __int_as_float(ordered_int(__int_as_float(atomicExch(&lf[LF_EXCESS], LF_EXCESS_RESET))));
+    int ok = atomicAdd(&lf[LF_OK], 0);
+    if (atomicExch(&lf[LF_OVERFLOW], 0)) {
+        // a particle had more neighbours than its capacity at the last
+        // fill: its list is incomplete, rebuild with 25 % more room
+        ok = 0;
+        lf[LF_OK] = 0;
+        lf[LF_SCALE] = __float_as_int(__int_as_float(lf[LF_SCALE]) * 1.25f);
+    }
+    int rebuild = t.force || !ok || (partner + excess >= 0.f);
+    lf[LF_REBUILD] = rebuild;
+    if (rebuild) lf[LF_SHMAX] = 0;          // the gather of the build takes the max
+    lf[LF_DONE] = 0;
+    if (t.set_cond) {
+        cudaGraphSetConditional(t.cond0, (unsigned)rebuild);
+        cudaGraphSetConditional(t.cond1, (unsigned)rebuild);
+    }
+}
+
+// the block's maxima into the control words and, in the last block of a
+// deciding kernel, the decision; every thread of the block calls it, and
+// t.lf and t.decide are the same for all of them
+__device__ __forceinline__ void list_test_block(const ListTest &t, float mp, float mq)
+{
+    for (int off = 16; off > 0; off >>= 1) {
+        mp = fmaxf(mp, __shfl_xor_sync(0xffffffffu, mp, off));
+        mq = fmaxf(mq, __shfl_xor_sync(0xffffffffu, mq, off));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (t.partner) atomicMax(&t.lf[LF_PARTNER], ordered_int(mp));
+        if (t.excess) atomicMax(&t.lf[LF_EXCESS], ordered_int(mq));
+    }
+    if (!t.decide) return;
+    __syncthreads();
+    __shared__ int s_last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&t.lf[LF_DONE], 1) == (int)(gridDim.x * gridDim.y * gridDim.z) - 1;
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        list_decide(t);
+    }
+}
+
 }  // namespace dcm

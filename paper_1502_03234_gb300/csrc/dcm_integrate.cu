@@ -15,32 +15,40 @@ namespace dcm {
 // cell of the last sort, so no gather pass is needed between list builds.
 __global__ void k_kick_drift(Batch b, double *__restrict__ x, double *__restrict__ v,
                              const double *__restrict__ f, int *err, float4 *sp4,
-                             const int32_t *__restrict__ inv, const int32_t *__restrict__ cell_of)
+                             const int32_t *__restrict__ inv, const int32_t *__restrict__ cell_of,
+                             const double *__restrict__ rc, ListTest t)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= b.N) return;
-    const Geom &g = b.sys[sys_p(b, i)];
-    int bad = 0;
-    double xn[3];
+    float mp = -3.0e38f, mq = -3.0e38f;
+    if (i < b.N) {
+        const Geom &g = b.sys[sys_p(b, i)];
+        int bad = 0;
+        double xn[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        size_t o = (size_t)a * b.N + i;
-        double vi = fma(g.hdtm, f[o], v[o]);
-        double xi = fma(g.dt, vi, x[o]);
-        // non-finite: exponent bits all ones
-        if (((__double_as_longlong(xi) >> 52) & 0x7ff) == 0x7ff ||
-            ((__double_as_longlong(vi) >> 52) & 0x7ff) == 0x7ff)
-            bad |= DEV_ERR_NONFINITE;
-        if (!wrap_coord_bits(xi, g.L[a])) {   // moved more than one box edge
-            bad |= DEV_ERR_JUMP;
-            xi = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            size_t o = (size_t)a * b.N + i;
+            double vi = fma(g.hdtm, f[o], v[o]);
+            double xi = fma(g.dt, vi, x[o]);
+            // non-finite: exponent bits all ones
+            if (((__double_as_longlong(xi) >> 52) & 0x7ff) == 0x7ff ||
+                ((__double_as_longlong(vi) >> 52) & 0x7ff) == 0x7ff)
+                bad |= DEV_ERR_NONFINITE;
+            if (!wrap_coord_bits(xi, g.L[a])) {   // moved more than one box edge
+                bad |= DEV_ERR_JUMP;
+                xi = 0.0;
+            }
+            v[o] = vi;
+            x[o] = xi;
+            xn[a] = xi;
         }
-        v[o] = vi;
-        x[o] = xi;
-        xn[a] = xi;
+        if (bad) atomicOr(err, bad);
+        if (sp4) sp4[inv[i]] = cell_rel_position(g, xn[0], xn[1], xn[2], cell_of[i] - (int)g.c0);
+        if (t.lf) {
+            const float d = list_disp(t, g, (size_t)b.N, i, xn[0], xn[1], xn[2]);
+            list_terms(t, i, d, t.excess ? rc[i] : 0.0, mp, mq);
+        }
     }
-    if (bad) atomicOr(err, bad);
-    if (sp4) sp4[inv[i]] = cell_rel_position(g, xn[0], xn[1], xn[2], cell_of[i] - (int)g.c0);
+    if (t.lf) list_test_block(t, mp, mq);
 }
 
 __global__ void k_iota(int32_t *p, int64_t n)
@@ -139,8 +147,14 @@ static inline int nblk(int64_t n, int b) { return (int)((n + b - 1) / b); }
 int launch_kick_drift(dcm_handle *h)
 {
     const bool wl = h->nl && h->list_warp;
+    // a captured step with lists runs the reuse test here: all of it on a
+    // step without detection, the displacement-share term on one with (the
+    // cutoff kernel adds the headroom term for the new cutoffs and decides)
+    ListTest t = list_test(h, true, !h->step_detect, !h->step_detect);
+    if (!h->fold_check) t.lf = nullptr;
     k_kick_drift<<<nblk(h->n, 256), 256, 0, h->stream>>>(h->b, h->x, h->v, h->f, h->err,
-                                                         wl ? h->sp4 : nullptr, h->inv, h->cell_of);
+                                                         wl ? h->sp4 : nullptr, h->inv, h->cell_of,
+                                                         h->rc, t);
     return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "kick_drift launch");
 }
 

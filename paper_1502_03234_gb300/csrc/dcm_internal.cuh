@@ -222,6 +222,7 @@ struct dcm_handle {
     cudaGraphConditionalHandle cond[2]; // of the graph being captured: list step, forces
                                         // (a handle serves one conditional node)
     bool branching;                     // enqueue_step is recording a graph with branches
+    bool fold_check;                    // the step's drift / cutoff kernel runs the reuse test
     int br_kernels[2];                  // kernels in bodies taken on rebuild / reuse
     // kernel nodes of one captured step: [plain, detect] x [rebuild, reuse]
     int kernels_plain, kernels_detect, kernels_plain_reuse, kernels_detect_reuse;
@@ -244,6 +245,8 @@ int launch_bin_gated(dcm_handle *h, const int *gate, const int *class_gate);  //
 int launch_sort_gather(dcm_handle *h, const int *gate);    // cell sort + gather
 int launch_classes(dcm_handle *h, const int *class_gate);  // class lists
 void list_mode(dcm_handle *h);          // sets list_warp from precision, tuning and lists
+struct ListTest;
+ListTest list_test(dcm_handle *h, bool partner, bool excess, bool decide);
 void launch_iota(dcm_handle *h, int32_t *p, int64_t n);
 void launch_sys_tables(dcm_handle *h);
 int launch_scan(dcm_handle *h, const int32_t *in, int32_t *out, int32_t *tiles, int64_t m,

@@ -31,77 +31,20 @@
 
 namespace dcm {
 
-// order-preserving int image of a float (for atomicMax over signed values)
-__device__ __forceinline__ int ordered_int(float f)
-{
-    int b = __float_as_int(f);
-    return b >= 0 ? b : b ^ 0x7fffffff;
-}
-
-// the two maxima of the reuse condition; the last block to finish turns
-// them into the decision
-__global__ void k_list_check(Batch b, const double *__restrict__ x, const double *__restrict__ x_ref,
-                             const double *__restrict__ rc, const float *__restrict__ rl_ref,
-                             const float *__restrict__ sh_ref, int *lf, int force,
-                             cudaGraphConditionalHandle cond0, cudaGraphConditionalHandle cond1,
-                             int set_cond)
+// the stand-alone reuse test (eager list steps and forced rebuilds; a
+// captured step folds it into the drift or the cutoff kernel)
+__global__ void k_list_check(Batch b, const double *__restrict__ x, const double *__restrict__ rc,
+                             ListTest t)
 {
     float mp = -3.0e38f, mq = -3.0e38f;
     const size_t N = (size_t)b.N;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < b.N;
          i += (int64_t)gridDim.x * blockDim.x) {
-        float dx = (float)(x[i] - x_ref[i]);
-        float dy = (float)(x[N + i] - x_ref[N + i]);
-        float dz = (float)(x[2 * N + i] - x_ref[2 * N + i]);
-        // a coordinate wrapped through the box shows up as a jump of about
-        // one box edge: fold it back (moves are far below half an edge)
         const Geom &g = b.sys[sys_p(b, i)];
-        float Lx = (float)g.L[0], Ly = (float)g.L[1], Lz = (float)g.L[2];
-        dx -= Lx * rintf(dx / Lx);
-        dy -= Ly * rintf(dy / Ly);
-        dz -= Lz * rintf(dz / Lz);
-        const float d = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-        const float s = sh_ref[i];
-        mp = fmaxf(mp, d - s);
-        mq = fmaxf(mq, d - (list_radius_unpadded(rl_ref[i], s) - (float)rc[i]));
+        const float d = list_disp(t, g, N, i, x[i], x[N + i], x[2 * N + i]);
+        list_terms(t, i, d, rc[i], mp, mq);
     }
-    for (int off = 16; off > 0; off >>= 1) {
-        mp = fmaxf(mp, __shfl_xor_sync(0xffffffffu, mp, off));
-        mq = fmaxf(mq, __shfl_xor_sync(0xffffffffu, mq, off));
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicMax(&lf[LF_PARTNER], ordered_int(mp));
-        atomicMax(&lf[LF_EXCESS], ordered_int(mq));
-    }
-    __syncthreads();
-    __shared__ int s_last;
-    if (threadIdx.x == 0) {
-        __threadfence();
-        s_last = atomicAdd(&lf[LF_DONE], 1) == (int)(gridDim.x * gridDim.y * gridDim.z) - 1;
-    }
-    __syncthreads();
-    if (s_last && threadIdx.x == 0) {
-        __threadfence();
-        // the images are their own inverses; reset both to that of -3.4e38
-        float partner = __int_as_float(ordered_int(__int_as_float(atomicExch(&lf[LF_PARTNER], LF_EXCESS_RESET))));
-        float excess = __int_as_float(ordered_int(__int_as_float(atomicExch(&lf[LF_EXCESS], LF_EXCESS_RESET))));
-        int ok = atomicAdd(&lf[LF_OK], 0);
-        if (atomicExch(&lf[LF_OVERFLOW], 0)) {
-            // a particle had more neighbours than its capacity at the last
-            // fill: its list is incomplete, rebuild with 25 % more room
-            ok = 0;
-            lf[LF_OK] = 0;
-            lf[LF_SCALE] = __float_as_int(__int_as_float(lf[LF_SCALE]) * 1.25f);
-        }
-        int rebuild = force || !ok || (partner + excess >= 0.f);
-        lf[LF_REBUILD] = rebuild;
-        if (rebuild) lf[LF_SHMAX] = 0;          // the gather of the build takes the max
-        lf[LF_DONE] = 0;
-        if (set_cond) {
-            cudaGraphSetConditional(cond0, (unsigned)rebuild);
-            cudaGraphSetConditional(cond1, (unsigned)rebuild);
-        }
-    }
+    list_test_block(t, mp, mq);
 }
 
 // after the count scan: does the list fit?  FILL gate = rebuild && fits
@@ -132,6 +75,23 @@ __global__ void k_list_save(int64_t N, const double *__restrict__ x, double *x_r
 
 static inline int nblk(int64_t n, int b) { return (int)((n + b - 1) / b); }
 
+ListTest list_test(dcm_handle *h, bool partner, bool excess, bool decide)
+{
+    ListTest t;
+    t.lf = h->lflags;
+    t.x_ref = h->x_ref;
+    t.rl_ref = h->rl_ref;
+    t.sh_ref = h->sh_ref;
+    t.partner = partner ? 1 : 0;
+    t.excess = excess ? 1 : 0;
+    t.decide = decide ? 1 : 0;
+    t.force = 0;
+    t.set_cond = h->branching ? 1 : 0;
+    t.cond0 = h->cond[0];
+    t.cond1 = h->cond[1];
+    return t;
+}
+
 void list_mode(dcm_handle *h)
 {
     h->list_warp = h->nl && h->p.precision == DCM_MIXED && h->tune.walk == DCM_WALK_WARP;
@@ -149,18 +109,22 @@ int launch_list_step(dcm_handle *h, bool force_rebuild)
     int64_t N = h->n;
     int cgrid = h->num_sms * 2;
     list_mode(h);
-    const bool set_cond = h->branching;
-    k_list_check<<<cgrid, 256, 0, h->stream>>>(h->b, h->x, h->x_ref, h->rc, h->rl_ref, h->sh_ref,
-                                               h->lflags, force_rebuild ? 1 : 0, h->cond[0],
-                                               h->cond[1], set_cond ? 1 : 0);
+    if (force_rebuild || !h->fold_check) {
+        ListTest t = list_test(h, true, true, true);
+        t.force = force_rebuild ? 1 : 0;
+        k_list_check<<<cgrid, 256, 0, h->stream>>>(h->b, h->x, h->rc, t);
+    }
     const int *rebuild = h->lflags + LF_REBUILD;
     const int *fill = h->lflags + LF_FILL;
     if (h->list_warp) {
         Branch br;
         int r = branch_open(h, br, 1, 0);
         if (!r) r = launch_sort_gather(h, rebuild);
-        // class lists change with a detection or with the sort
-        if (!r && !h->step_detect) r = launch_classes(h, rebuild);
+        // the class lists only order the work queue: they are redone with
+        // the sort (new slots) and left as they are after a detection that
+        // keeps the lists (every slot is still in exactly one list; the
+        // order is slightly off until the next build)
+        if (!r) r = launch_classes(h, rebuild);
         if (!r) {
             // the gather wrote each particle's capacity into nl_cnt
             cudaStream_t s = h->stream;
@@ -170,9 +134,7 @@ int launch_list_step(dcm_handle *h, bool force_rebuild)
             if (cudaGetLastError() != cudaSuccess) r = fail(DCM_ERR_CUDA, "list launch");
         }
         int r2 = branch_close(h, br);
-        if (!r) r = r2;
-        if (!r && h->step_detect) r = launch_classes(h, nullptr);
-        return r;
+        return r ? r : r2;
     }
     cudaStream_t s = h->stream;
     int r = launch_bin_gated(h, rebuild, nullptr);
