@@ -88,6 +88,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--skin", type=float, default=0.7,
                     help="Verlet-list skin in sigma (0: direct link-cell walk every step)")
+    ap.add_argument("--cell-min", type=float, default=0.0,
+                    help="link-cell edge target in sigma (0: the library's, r_c,min / 2)")
     ap.add_argument("--list-lanes", type=int, default=0, choices=[0, 4, 8, 16, 32],
                     help="lanes per particle of the Verlet-list force (0: the library's default)")
     ap.add_argument("--step-graph", default="branched", choices=["branched", "flat"],
@@ -474,7 +476,7 @@ def main():
     def make_system(precision):
         sy = dcm.System(slab.box, n, precision=precision, stream=stream.cuda_stream,
                         skin=args.skin, list_margin=args.list_margin, skin_time=args.skin_time,
-                        skin_floor=args.skin_floor)
+                        skin_floor=args.skin_floor, cell_min=args.cell_min)
         if args.list_lanes:
             t = dcm.dcm_get_tuning(sy.h)
             sy.set_tuning(list(t.lanes), t.block, t.walk, args.list_lanes)
@@ -653,6 +655,7 @@ def main():
         cfg = workload_config(n, args.precision)
         cfg["skin"] = args.skin
         cfg["list_margin"] = args.list_margin
+        cfg["cell_min"] = args.cell_min
         cfg["skin_time"] = args.skin_time
         cfg["skin_floor"] = args.skin_floor
         cfg["phase_ms_avg"] = {k: v / phase_steps for k, v in phase_sum.items()}

@@ -900,6 +900,7 @@ __device__ __forceinline__ void particle_force_warp(const ForceArgs &a, FwTable 
             int p = base + lane;
             bool hit = false;
             int j = 0;
+            float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 3.0e38f;
             if (p < T) {
                 int4 ri = tb.ri[rowi];
                 float4 rf = tb.rf[rowi];
@@ -908,22 +909,29 @@ __device__ __forceinline__ void particle_force_warp(const ForceArgs &a, FwTable 
                 j = wr ? ri.w + (t - ri.z) : ri.y + t;
                 float ax = wr ? rf.y : rf.x;
                 float4 uj = a.sp4[j];
-                float dx = fmaf(ax - uj.w, cf0, ui.x - uj.x);
-                float dy = rf.z - uj.y;
-                float dz = rf.w - uj.z;
-                float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                bool in = r2 < rc2f && j != k;
-                if (r2 >= rc2lo && r2 < rc2hi && j != k) {
-                    double rci = a.rc[i];
-                    in = fp64_inside(a, g, i, a.sorted_id[j], DMUL(rci, rci));
-                    ++ng;
-                }
-                acc.pair(g, dx, dy, dz, r2, in);
+                dx = fmaf(ax - uj.w, cf0, ui.x - uj.x);
+                dy = rf.z - uj.y;
+                dz = rf.w - uj.z;
+                r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                 if constexpr (FILL) {
                     if (fill_on) {
                         const float rp = rl + a.sh[j];
                         hit = r2 < rp * rp && j != k;
                     }
+                }
+            }
+            // the fill walks out to the list radius: a chunk of candidates
+            // all beyond the cutoff adds nothing (exact zeros) and skips the
+            // force arithmetic
+            if (!FILL || __any_sync(0xffffffffu, r2 < rc2hi)) {
+                if (p < T) {
+                    bool in = r2 < rc2f && j != k;
+                    if (r2 >= rc2lo && r2 < rc2hi && j != k) {
+                        double rci = a.rc[i];
+                        in = fp64_inside(a, g, i, a.sorted_id[j], DMUL(rci, rci));
+                        ++ng;
+                    }
+                    acc.pair(g, dx, dy, dz, r2, in);
                 }
             }
             if constexpr (FILL) {
