@@ -63,10 +63,10 @@ FLOPS_PER_PAIR = 24              # 8 (distance test) + 16 (LJ force), per in-cut
 # (profiles/k_force_warp_N262144_mixed.md); None once the kernel changes
 FORCE_TRAFFIC = {"mixed": 14.96e6, "fp64": None}
 # DRAM bytes per launch of the Verlet-list force kernel (k_force_list_warp, N = 262,144,
-# skin 0.7 with skin_time 0.06, skin_floor 0.08) from the committed capture
+# skin 0.7 with skin_time 0.08, skin_floor 0.1) from the committed capture
 # (profiles/k_force_list_warp_N262144_mixed.md)
-LIST_TRAFFIC = {"k_force_list_warp": 206.55e6 + 4.27e6}
-LIST_TRAFFIC_CONFIG = (0.7, 0.06, 0.08, 1.0)    # skin, skin_time, skin_floor, list_margin
+LIST_TRAFFIC = {"k_force_list_warp": 222.93e6 + 4.59e6}
+LIST_TRAFFIC_CONFIG = (0.7, 0.08, 0.1, 1.0)     # skin, skin_time, skin_floor, list_margin
 # bytes the list kernel must move per particle besides its list entries: own
 # position, cutoff constants, id/cell, list start and count, queue slot, the
 # force written and the pair count
