@@ -111,14 +111,23 @@ __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p)
     return v;
 }
 
+// arrival with release semantics at GPU scope: after the block's bar.sync it
+// publishes every write of the block (release is cumulative), so no separate
+// fence is needed; the acquire loads of the poll order what follows
+__device__ __forceinline__ unsigned int atom_add_release_u32(unsigned int *p, unsigned int v)
+{
+    unsigned int old;
+    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
 __device__ __forceinline__ bool grid_barrier(unsigned int *words, int *err)
 {
     __syncthreads();
     __shared__ int s_ok;
     if (threadIdx.x == 0) {
         const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
-        __threadfence();
-        const unsigned int arrived = atomicAdd(words, 1u);
+        const unsigned int arrived = atom_add_release_u32(words, 1u);
         const unsigned int target = (arrived / nb + 1u) * nb;
         int ok = 1;
         // tight polling first (a healthy barrier completes in a few
@@ -140,7 +149,6 @@ __device__ __forceinline__ bool grid_barrier(unsigned int *words, int *err)
             }
             if (polls > 4096) __nanosleep(128);
         }
-        __threadfence();
         s_ok = ok;
     }
     __syncthreads();
