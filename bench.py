@@ -94,10 +94,10 @@ def parse():
                     help="lanes per particle of the Verlet-list force (0: the library's default)")
     ap.add_argument("--step-graph", default="branched", choices=["branched", "flat"],
                     help="flat: no conditional nodes in the step graph (for per-kernel profiling)")
-    ap.add_argument("--skin-time", type=float, default=0.08,
-                    help="velocity-adaptive skin shares: share = clamp(skin_time |v|, skin_floor, "
-                         "skin/2); 0: skin/2 for every particle")
-    ap.add_argument("--skin-floor", type=float, default=0.1)
+    ap.add_argument("--skin-time", type=float, default=0.06,
+                    help="adaptive skin shares: share = clamp(skin_time |v| + skin_time^2 |F| / 2m, "
+                         "skin_floor, skin/2); 0: skin/2 for every particle")
+    ap.add_argument("--skin-floor", type=float, default=0.07)
     ap.add_argument("--list-margin", type=float, default=1.0,
                     help="interface-distance margin of the Verlet-list radius in sigma")
     ap.add_argument("--workload", default="slab", choices=["slab", "wavy", "ensemble", "serving"])

@@ -107,13 +107,15 @@ typedef struct {
        a rebuild at every detection.  0: 1 sigma; < 0: no margin (per
        handle: system 0's value). */
     float list_margin;
-    /* Velocity-adaptive skins (skin_time > 0): instead of skin/2 for every
-       particle, particle i's share of a pair's skin is
-       clamp(skin_time x |v_i|, skin_floor, skin/2) at the build, and the
-       pair (i, j) is listed while it is closer than i's anticipated cutoff
-       plus both shares.  Slow particles then carry short lists and fast
-       ones do not force early rebuilds; skin still bounds every pair's
-       skin.  skin_time = 0: uniform shares. */
+    /* Adaptive skins (skin_time > 0): instead of skin/2 for every
+       particle, particle i's share of a pair's skin is the distance it
+       would cover in skin_time at constant acceleration,
+       skin_time |v_i| + skin_time^2 |F_i| / (2 m), clamped to
+       [skin_floor, skin/2] at the build, and the pair (i, j) is listed while
+       it is closer than i's anticipated cutoff plus both shares.  Slow,
+       weakly pushed particles then carry short lists and fast or strongly
+       pushed ones do not force early rebuilds; skin still bounds every
+       pair's skin.  skin_time = 0: uniform shares. */
     float skin_time;
     float skin_floor;
     int32_t reserved[2];

@@ -125,6 +125,7 @@ __global__ void k_cell_sort(int64_t ncell, const int32_t *__restrict__ start, in
 // sorted position streams: sp4 = (x - cell corner in FP32, cell x index),
 // spd = absolute FP64 position (FP64 path only)
 __global__ void k_gather(Batch b, const double *__restrict__ x, const double *__restrict__ v,
+                         const double *__restrict__ f,
                          const int32_t *__restrict__ sorted_id,
                          const int32_t *__restrict__ cell_of, float4 *sp4, double4_32a *spd,
                          const double *__restrict__ rc, float4 *rq, int4 *pk, float *sh,
@@ -150,13 +151,15 @@ __global__ void k_gather(Batch b, const double *__restrict__ x, const double *__
         int cz = c / (g.nc[0] * g.nc[1]);
         int w = 0;
         if (capk && lf[LF_REBUILD]) {
-            // a Verlet-list build follows: the skin share and own list
-            // radius of this particle, and its entry capacity, (4/3) pi R^3
+            // a Verlet-list build follows: the skin share (from the
+            // particle's speed and force) and own list radius of this particle, and its entry capacity, (4/3) pi R^3
             // for R = own radius + the largest share at the density bound
             // scale (1.0 sigma^-3 unless a list overflowed before) + 8
             const size_t N = (size_t)b.N;
             const float vx = (float)v[i], vy = (float)v[N + i], vz = (float)v[2 * N + i];
-            const float share = skin_share(g, sqrtf(fmaf(vx, vx, fmaf(vy, vy, vz * vz))));
+            const float fx = (float)f[i], fy = (float)f[N + i], fz = (float)f[2 * N + i];
+            const float share = skin_share(g, sqrtf(fmaf(vx, vx, fmaf(vy, vy, vz * vz))),
+                                           sqrtf(fmaf(fx, fx, fmaf(fy, fy, fz * fz))));
             const float rl = list_radius(g, r, dist[i], delta, share);
             const float R = rl + 0.5f * (float)g.skin;
             float scale = __int_as_float(lf[LF_SCALE]);
@@ -255,7 +258,7 @@ int launch_sort_gather(dcm_handle *h, const int *gate)
                                                 h->sorted_id, gate);
     k_cell_sort<<<nblk(h->ncell, 256), 256, 0, s>>>(h->ncell, h->cell_start, h->sorted_id, gate);
     const bool wl = h->nl && h->list_warp;
-    k_gather<<<nblk(n, 256), 256, 0, s>>>(h->b, h->x, h->v, h->sorted_id, h->cell_of, h->sp4,
+    k_gather<<<nblk(n, 256), 256, 0, s>>>(h->b, h->x, h->v, h->f, h->sorted_id, h->cell_of, h->sp4,
                                           h->p.precision == DCM_FP64 ? h->spd : nullptr, h->rc,
                                           h->rq, h->pk, h->sh, h->d, h->lflags,
                                           h->cut_detected ? h->list_margin : 0.0f, wl ? h->nl_cnt : nullptr,

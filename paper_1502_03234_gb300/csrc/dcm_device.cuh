@@ -239,13 +239,17 @@ __device__ __forceinline__ float list_radius_unpadded(float rl, float share)
     return fmaf(rl - share - 1e-4f, 0.99999f, share);
 }
 
-// skin share of a particle with speed |v|: skin/2, or clamp(skin_time |v|,
-// skin_floor, skin/2) with velocity-adaptive skins
-__device__ __forceinline__ float skin_share(const Geom &g, float speed)
+// skin share of a particle with speed |v| under force |F|: skin/2, or with
+// adaptive skins the distance it would cover in skin_time at constant
+// acceleration, tau |v| + tau^2 |F| / (2 m), clamped to [skin_floor, skin/2]
+__device__ __forceinline__ float skin_share(const Geom &g, float speed, float force)
 {
     const float half = 0.5f * (float)g.skin;
     if (g.skin_time <= 0.f) return half;
-    return fminf(fmaxf(g.skin_time * speed, g.skin_floor), half);
+    const float tau = g.skin_time;
+    const float inv_m = (float)(2.0 * g.hdtm / g.dt);      // hdtm = dt / (2 m)
+    const float reach = tau * fmaf(0.5f * tau * inv_m, force, speed);
+    return fminf(fmaxf(reach, g.skin_floor), half);
 }
 
 // FP32 position of a particle relative to the corner of its link cell
