@@ -585,7 +585,15 @@ struct CfsmArgs {
 
 // one pass k of the frontier iteration: items q = tid, tid + nth, ... of
 // frontier list k & 3 (nf items), pushes into list (k + 1) & 3
-__device__ __forceinline__ void cfsm_pass(const CfsmArgs &a, int k, int nf, int64_t tid, int64_t nth)
+// the list entry this thread takes first in pass k, loaded before the
+// frontier size is known (the two reads overlap; beyond the size it is unused)
+__device__ __forceinline__ int32_t cfsm_first(const CfsmArgs &a, int k, int64_t tid)
+{
+    return tid < a.cap ? __ldcg(&a.lists[(int64_t)(k & 3) * a.cap + tid]) : 0;
+}
+
+__device__ __forceinline__ void cfsm_pass(const CfsmArgs &a, int k, int nf, int64_t tid, int64_t nth,
+                                          int32_t first)
 {
     const double *X = (k & 1) ? a.D1 : a.D0;
     double *Y = (k & 1) ? a.D0 : a.D1;
@@ -598,7 +606,7 @@ __device__ __forceinline__ void cfsm_pass(const CfsmArgs &a, int k, int nf, int6
         int32_t push[7];
         int npush = 0;
         if (q < nf) {
-            int v = __ldcg(&F[q]);
+            int v = q0 == tid - lane ? first : __ldcg(&F[q]);
             const Geom &g = a.b.sys[sys_v(a.b, v)];
             const int nx = g.gd[0], ny = g.gd[1], nz = g.gd[2];
             const int v0 = (int)g.v0;
@@ -676,9 +684,10 @@ __global__ void __launch_bounds__(DET_THREADS) k_cfsm(CfsmArgs a)
     const int64_t nth = (int64_t)gridDim.x * blockDim.x;
     int k = 0;
     for (; k < a.iter_max; ++k) {
+        const int32_t first = cfsm_first(a, k, tid);
         const int nf = ((volatile int32_t *)a.fcount)[k & 3];
         if (nf < a.nf_switch) break;             // (also nf == 0: converged)
-        cfsm_pass(a, k, nf, tid, nth);
+        cfsm_pass(a, k, nf, tid, nth, first);
         if (!grid_barrier(a.bar, a.err)) return;
     }
     if (tid == 0) *a.kpass = k;
@@ -707,12 +716,13 @@ __global__ void __launch_bounds__(CFSM_TAIL_THREADS) k_cfsm_tail(CfsmArgs a)
     int k = __ldcg(a.kpass);
     bool converged = false;
     for (; k < a.iter_max; ++k) {
+        const int32_t first = cfsm_first(a, k, tid);
         const int nf = ((volatile int32_t *)a.fcount)[k & 3];
         if (nf == 0) {
             converged = true;
             break;
         }
-        cfsm_pass(a, k, nf, tid, nth);
+        cfsm_pass(a, k, nf, tid, nth, first);
         cluster_sync_all();
     }
     if (tid == 0) {

@@ -316,10 +316,12 @@ __device__ __forceinline__ float list_disp(const ListTest &t, const Geom &g, siz
     float dx = (float)(x - t.x_ref[i]);
     float dy = (float)(y - t.x_ref[N + i]);
     float dz = (float)(z - t.x_ref[2 * N + i]);
+    // (an approximate reciprocal suffices: rint only decides between 0 and
+    // +-1 edges, and a move near half an edge cannot happen)
     const float Lx = (float)g.L[0], Ly = (float)g.L[1], Lz = (float)g.L[2];
-    dx -= Lx * rintf(dx / Lx);
-    dy -= Ly * rintf(dy / Ly);
-    dz -= Lz * rintf(dz / Lz);
+    dx -= Lx * rintf(dx * rcp_approx(Lx));
+    dy -= Ly * rintf(dy * rcp_approx(Ly));
+    dz -= Lz * rintf(dz * rcp_approx(Lz));
     return sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
 }
 
