@@ -59,9 +59,9 @@ def _hbm_peak():
 
 HBM_PEAK_GBS = _hbm_peak()
 FLOPS_PER_PAIR = 24              # 8 (distance test) + 16 (LJ force), per in-cutoff pair
-# DRAM bytes (read + write) per force launch of the direct walk (skin 0) from a committed
-# ncu capture of the current kernel; None: the walk changed since the last capture
-FORCE_TRAFFIC = {"mixed": None, "fp64": None}
+# DRAM bytes (read + write) per force launch of the direct walk (skin 0) from the committed
+# capture (profiles/k_force_warp_N262144_mixed.md); None: not captured
+FORCE_TRAFFIC = {"mixed": 14.96e6, "fp64": None}
 # DRAM bytes per launch of the Verlet-list force kernel (k_force_list_warp, N = 262,144,
 # skin 0.7 with skin_time 0.08, skin_floor 0.1) from the committed capture
 # (profiles/k_force_list_warp_N262144_mixed.md)

@@ -113,8 +113,9 @@ static int check_params(const dcm_box *box, int64_t n, const dcm_params *p)
         return fail(DCM_ERR_ARG, "n_classes must be 2..%d", DCM_MAX_CLASSES);
     if (p->detect_every < 0) return fail(DCM_ERR_ARG, "detect_every must be >= 0");
     if (!(p->skin >= 0) || p->skin > 2.0) return fail(DCM_ERR_ARG, "skin must be in [0, 2] sigma");
+    // (the shares only matter with lists)
     if (!(p->skin_time >= 0.f) || !(p->skin_floor >= 0.f) ||
-        (p->skin_time > 0.f && p->skin_floor > 0.5 * p->skin))
+        (p->skin > 0 && p->skin_time > 0.f && p->skin_floor > 0.5 * p->skin))
         return fail(DCM_ERR_ARG, "skin_time, skin_floor must be >= 0, skin_floor <= skin/2");
     return DCM_OK;
 }

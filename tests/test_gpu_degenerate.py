@@ -88,3 +88,18 @@ def test_empty_system_is_rejected(dcm):
     with pytest.raises(dcm.DcmError) as e:
         dcm.System((20.0, 20.0, 80.0), 0)
     assert e.value.code == dcm.DCM_ERR_ARG
+
+
+def test_skin_share_parameters(dcm):
+    # the adaptive-share parameters only matter with lists: accepted with
+    # skin 0, rejected when the floor exceeds half the skin
+    s = slabgen.make_slab(4000, seed=53)
+    with dcm.System(s.box, len(s.x), precision=1, skin=0.0, skin_time=0.06, skin_floor=0.07):
+        pass
+    with pytest.raises(dcm.DcmError) as e:
+        dcm.System(s.box, len(s.x), precision=1, skin=0.4, skin_time=0.06, skin_floor=0.3)
+    assert e.value.code == dcm.DCM_ERR_ARG
+    with pytest.raises(dcm.DcmError) as e:
+        dcm.System(s.box, len(s.x), precision=1, skin=0.4, skin_time=-1.0)
+    assert e.value.code == dcm.DCM_ERR_ARG
+
