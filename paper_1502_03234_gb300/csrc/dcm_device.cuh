@@ -364,25 +364,36 @@ __device__ __forceinline__ void list_decide(const ListTest &t)
 // t.lf and t.decide are the same for all of them
 __device__ __forceinline__ void list_test_block(const ListTest &t, float mp, float mq)
 {
+    // warp maxima, then the block's in shared memory: one atomic per word
+    // and block (the kernels that carry the test launch a block per 256
+    // particles; per-warp atomics on two words serialised in L2)
     for (int off = 16; off > 0; off >>= 1) {
         mp = fmaxf(mp, __shfl_xor_sync(0xffffffffu, mp, off));
         mq = fmaxf(mq, __shfl_xor_sync(0xffffffffu, mq, off));
     }
+    __shared__ float s_mp[32], s_mq[32];
+    __shared__ int s_last;
+    const int warp = threadIdx.x >> 5, nwarps = (blockDim.x + 31) >> 5;
     if ((threadIdx.x & 31) == 0) {
+        s_mp[warp] = mp;
+        s_mq[warp] = mq;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < nwarps; ++w) {
+            mp = fmaxf(mp, s_mp[w]);
+            mq = fmaxf(mq, s_mq[w]);
+        }
         if (t.partner) atomicMax(&t.lf[LF_PARTNER], ordered_int(mp));
         if (t.excess) atomicMax(&t.lf[LF_EXCESS], ordered_int(mq));
-    }
-    if (!t.decide) return;
-    __syncthreads();
-    __shared__ int s_last;
-    if (threadIdx.x == 0) {
-        __threadfence();
-        s_last = atomicAdd(&t.lf[LF_DONE], 1) == (int)(gridDim.x * gridDim.y * gridDim.z) - 1;
-    }
-    __syncthreads();
-    if (s_last && threadIdx.x == 0) {
-        __threadfence();
-        list_decide(t);
+        if (t.decide) {
+            __threadfence();
+            s_last = atomicAdd(&t.lf[LF_DONE], 1) == (int)(gridDim.x * gridDim.y * gridDim.z) - 1;
+            if (s_last) {
+                __threadfence();
+                list_decide(t);
+            }
+        }
     }
 }
 
