@@ -153,6 +153,7 @@ static int setup_geometry(const dcm_box *box, int64_t n, const dcm_params *p, Ge
     for (int a = 0; a < 3; ++a) {
         g.L[a] = L[a];
         g.halfL[a] = 0.5 * L[a];
+        g.halfLf[a] = (float)g.halfL[a];
         g.cf[a] = (float)g.cedge[a];
         g.inv_cf[a] = (float)g.inv_c[a];
         int gd = (int)floor(L[a] / p->voxel);
@@ -221,7 +222,7 @@ static int64_t bytes_for(const Geom &g, int64_t n, int precision)
     per_p += 36;   // spd (FP64) or rq + pk + inv (MIXED)
     int64_t per_v = 4 + 4 + 4 + 8 + 1 + 8 + 8 + 4 + 16 + 2;
     int64_t ntiles = (ncell + 2047) / 2048 + 1;
-    int64_t lists = g.skin > 0 ? 4 * list_cap(g, n) + n * (4 + 4 + 24 + 8 + 8) : 0;
+    int64_t lists = g.skin > 0 ? 4 * list_cap(g, n) + n * (4 + 4 + 24 + 8 + 8 + 20) : 0;
     return n * per_p + ncell * 8 + 8 + nv * per_v + ntiles * 4 + 4096 + 256 * 8 * 8 + lists;
 }
 
@@ -259,12 +260,14 @@ extern "C" int dcm_destroy(dcm_handle *h)
                     h->class_count_dev, h->B, h->sm1, h->sm2, h->Bs, h->S, h->D0, h->D1, h->stamp,
                     h->flist, h->fcount, h->kacc, h->npair, h->pe, h->vir, h->red_part, h->red_out,
                     h->err, h->stats, h->tmp3n, h->geo_dev, h->off_dev, h->nl, h->nl_cnt,
-                    h->nl_start, h->nl_tiles, h->x_ref, h->rl_ref, h->sh_ref, h->sh, h->lflags};
+                    h->nl_start, h->nl_tiles, h->x_ref, h->rl_ref, h->sh_ref, h->sh, h->u_ref,
+                    h->disp, h->corner, h->lflags};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     if (h->side) cudaStreamDestroy(h->side);
     delete[] h->geo_host;
+    delete[] h->corner_host;
     delete[] h->par_host;
     delete[] h->off_host;
     delete h;
@@ -321,6 +324,21 @@ static int create_systems(int M, const dcm_box *boxes, const int64_t *ns, const 
         co[k + 1] = co[k] + g.ncell;
         vo[k + 1] = vo[k] + g.nvox;
     }
+    // cell corner coordinates c * L/n of every axis and system (IEEE
+    // products, the same on the host as on the device)
+    int64_t ncorner = 0;
+    for (int k = 0; k < M; ++k) {
+        Geom &g = h->geo_host[k];
+        g.corner_off = ncorner;
+        ncorner += (int64_t)g.nc[0] + g.nc[1] + g.nc[2];
+    }
+    h->corner_host = new double[ncorner];
+    for (int k = 0; k < M; ++k) {
+        const Geom &g = h->geo_host[k];
+        double *c = h->corner_host + g.corner_off;
+        for (int a = 0, o = 0; a < 3; o += g.nc[a], ++a)
+            for (int q = 0; q < g.nc[a]; ++q) c[o + q] = (double)q * g.cedge[a];
+    }
     if (co[M] > (int64_t)0x7fffffff - 2 || vo[M] > (int64_t)0x7fffffff / 4) {
         dcm_destroy(h);
         return fail(DCM_ERR_ARG, "too many cells or voxels in total");
@@ -355,6 +373,7 @@ static int create_systems(int M, const dcm_box *boxes, const int64_t *ns, const 
     }
     ALLOC(h->geo_dev, M);
     ALLOC(h->off_dev, 3 * (M + 1));
+    ALLOC(h->corner, ncorner);
     ALLOC(h->x, 3 * N);
     ALLOC(h->v, 3 * N);
     ALLOC(h->f, 3 * N);
@@ -425,6 +444,8 @@ static int create_systems(int M, const dcm_box *boxes, const int64_t *ns, const 
         ALLOC(h->rl_ref, N);
         ALLOC(h->sh_ref, N);
         ALLOC(h->sh, N);
+        ALLOC(h->u_ref, N);
+        ALLOC(h->disp, N);
         ALLOC(h->lflags, LF_WORDS);
     }
 #undef ALLOC
@@ -434,12 +455,15 @@ static int create_systems(int M, const dcm_box *boxes, const int64_t *ns, const 
     h->b.v_off = h->off_dev + 2 * (M + 1);
     h->b.psys = h->psys;
     h->b.vsys = h->vsys;
+    h->b.corner = h->corner;
     h->b.M = M;
     h->b.K = h->p.n_classes;
     h->b.N = N;
     h->b.NC = nc;
     h->b.NV = nv;
     cudaMemcpyAsync(h->geo_dev, h->geo_host, sizeof(Geom) * M, cudaMemcpyHostToDevice, h->stream);
+    cudaMemcpyAsync(h->corner, h->corner_host, sizeof(double) * ncorner, cudaMemcpyHostToDevice,
+                    h->stream);
     cudaMemcpyAsync(h->off_dev, h->off_host, sizeof(int64_t) * 3 * (M + 1), cudaMemcpyHostToDevice,
                     h->stream);
     cudaMemsetAsync(h->err, 0, sizeof(int), h->stream);
@@ -467,6 +491,8 @@ static int create_systems(int M, const dcm_box *boxes, const int64_t *ns, const 
         cudaMemsetAsync(h->rl_ref, 0, sizeof(float) * N, h->stream);
         cudaMemsetAsync(h->sh_ref, 0, sizeof(float) * N, h->stream);
         cudaMemsetAsync(h->sh, 0, sizeof(float) * N, h->stream);
+        cudaMemsetAsync(h->u_ref, 0, sizeof(float4) * N, h->stream);
+        cudaMemsetAsync(h->disp, 0, sizeof(float) * N, h->stream);
     }
     cudaError_t e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {

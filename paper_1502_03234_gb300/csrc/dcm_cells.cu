@@ -139,7 +139,7 @@ __global__ void k_gather(Batch b, const double *__restrict__ x, const double *__
     int i = sorted_id[k];
     int c = cell_of[i] - (int)g.c0;
     double px = x[i], py = x[(size_t)b.N + i], pz = x[2 * (size_t)b.N + i];
-    sp4[k] = cell_rel_position(g, px, py, pz, c);
+    sp4[k] = cell_rel_position(b, g, px, py, pz, c);
     if (spd) spd[k] = make_double4_32a(px, py, pz, 0.0);
     if (inv) inv[i] = (int32_t)k;
     if (rq) {

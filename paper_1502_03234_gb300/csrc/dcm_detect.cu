@@ -813,8 +813,9 @@ __device__ __forceinline__ void cutoff_one(Batch b, int64_t i, const double *__r
     cls[i] = (uint8_t)c;
     if (rq) rq[inv[i]] = rc_constants(r);
     if (lt.lf) {
+        // the displacement the drift found this step (warp lists), or in FP64
         const size_t N = (size_t)b.N;
-        const float disp = list_disp(lt, g, N, i, x[i], x[N + i], x[2 * N + i]);
+        const float disp = lt.disp ? lt.disp[i] : list_disp(lt, g, N, i, x[i], x[N + i], x[2 * N + i]);
         float unused = -3.0e38f;
         list_terms(lt, i, disp, r, unused, mq);
     }

@@ -256,22 +256,29 @@ __device__ __forceinline__ float skin_share(const Geom &g, float speed, float fo
 // (cell index c_local within its system) and that cell's x index; a particle
 // that wrapped through the box since its cell was assigned (between
 // Verlet-list builds) is folded back next to that cell.  Shared by the
-// gather kernel and the drift, which must produce the same bits.
-__device__ __forceinline__ float4 cell_rel_position(const Geom &g, double px, double py, double pz,
-                                                   int c_local)
+// gather kernel and the drift, which must produce the same bits.  The
+// corner coordinates c * L/n come from a table (the same rounded products
+// as computing them here), which keeps this to one FP64 subtraction and one
+// conversion per axis: the FP64 pipe runs at 1/64 of the FP32 rate.
+__device__ __forceinline__ float4 cell_rel_position(const Batch &b, const Geom &g, double px,
+                                                   double py, double pz, int c_local)
 {
     int cx = c_local % g.nc[0];
     int cy = (c_local / g.nc[0]) % g.nc[1];
     int cz = c_local / (g.nc[0] * g.nc[1]);
-    double u[3] = {DSUB(px, DMUL((double)cx, g.cedge[0])), DSUB(py, DMUL((double)cy, g.cedge[1])),
-                   DSUB(pz, DMUL((double)cz, g.cedge[2]))};
+    const double *corner = b.corner + g.corner_off;
+    const double p[3] = {px, py, pz};
+    const int c[3] = {cx, g.nc[0] + cy, g.nc[0] + g.nc[1] + cz};
+    float uf[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        float uf = (float)u[a];
-        if (uf > (float)g.halfL[a]) u[a] = DSUB(u[a], g.L[a]);
-        else if (uf < -(float)g.halfL[a]) u[a] = DADD(u[a], g.L[a]);
+        const double u = DSUB(p[a], corner[c[a]]);
+        float f = (float)u;
+        if (f > g.halfLf[a]) f = (float)DSUB(u, g.L[a]);
+        else if (f < -g.halfLf[a]) f = (float)DADD(u, g.L[a]);
+        uf[a] = f;
     }
-    return make_float4((float)u[0], (float)u[1], (float)u[2], (float)cx);
+    return make_float4(uf[0], uf[1], uf[2], (float)cx);
 }
 
 // the force walks' per-particle cutoff constants: FP32 r_c^2, its 2^-18
@@ -291,6 +298,8 @@ struct ListTest {
     int *lf;                           // null: no test in this kernel
     const double *x_ref;
     const float *rl_ref, *sh_ref;
+    const float4 *u_ref;               // warp lists: FP32 cell-relative positions at the build
+    float *disp;                       // warp lists: this step's |displacement| per particle
     int excess;                        // the headroom term here (needs the cutoffs)
     int partner;                       // the displacement-share term here
     int decide;                        // this kernel's last block decides
@@ -322,6 +331,15 @@ __device__ __forceinline__ float list_disp(const ListTest &t, const Geom &g, siz
     dx -= Lx * rintf(dx * rcp_approx(Lx));
     dy -= Ly * rintf(dy * rcp_approx(Ly));
     dz -= Lz * rintf(dz * rcp_approx(Lz));
+    return sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+}
+
+// the same from the FP32 cell-relative positions now and at the build: the
+// cell of a particle is fixed between builds, so the difference is the
+// displacement (FP32 only)
+__device__ __forceinline__ float list_disp32(float4 u, float4 u0)
+{
+    const float dx = u.x - u0.x, dy = u.y - u0.y, dz = u.z - u0.z;
     return sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
 }
 

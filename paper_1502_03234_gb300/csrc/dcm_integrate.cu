@@ -42,9 +42,21 @@ __global__ void k_kick_drift(Batch b, double *__restrict__ x, double *__restrict
             xn[a] = xi;
         }
         if (bad) atomicOr(err, bad);
-        if (sp4) sp4[inv[i]] = cell_rel_position(g, xn[0], xn[1], xn[2], cell_of[i] - (int)g.c0);
+        float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (sp4) {
+            u = cell_rel_position(b, g, xn[0], xn[1], xn[2], cell_of[i] - (int)g.c0);
+            sp4[inv[i]] = u;
+        }
         if (t.lf) {
-            const float d = list_disp(t, g, (size_t)b.N, i, xn[0], xn[1], xn[2]);
+            // warp lists: the displacement from the FP32 cell-relative
+            // positions (kept for the cutoff kernel's term); else in FP64
+            float d;
+            if (t.u_ref) {
+                d = list_disp32(u, t.u_ref[i]);
+                t.disp[i] = d;
+            } else {
+                d = list_disp(t, g, (size_t)b.N, i, xn[0], xn[1], xn[2]);
+            }
             list_terms(t, i, d, t.excess ? rc[i] : 0.0, mp, mq);
         }
     }

@@ -96,6 +96,8 @@ struct Geom {
     double dt, hdtm;             // dt, dt/(2m)
     double eps, sigma;
     double skin;                 // Verlet-list skin (0: direct cell walk)
+    int64_t corner_off;          // this system's cell corner coordinates in Batch::corner
+    float halfLf[3];             // FP32 half edges
     float skin_time, skin_floor; // velocity-adaptive skin shares (skin_time 0: skin/2 each)
     double eps24, eps48, eps2, sig2;     // LJ force/energy constants
     float eps24f, eps48f, eps2f, sig2f;
@@ -112,6 +114,7 @@ struct Batch {
     const int64_t *v_off;        // [M+1] voxel offsets
     const uint16_t *psys;        // [N] system of each particle (null when M == 1)
     const uint16_t *vsys;        // [NV] system of each voxel (null when M == 1)
+    const double *corner;        // cell corner coordinate c * L/n per axis and system
     int M;
     int K;                       // cutoff classes (same for all systems)
     int64_t N, NC, NV;           // totals
@@ -158,6 +161,7 @@ struct dcm_handle {
     int num_sms;
     int64_t ncell, nvox;
     int64_t bytes;
+    double *corner, *corner_host;   // cell corner coordinates (device, host copy)
 
     // state
     double *x, *v, *f;
@@ -191,6 +195,8 @@ struct dcm_handle {
     float *rl_ref;               // own list radius of each particle at the build (id order)
     float *sh_ref;               // skin share of each particle at the build (id order)
     float *sh;                   // skin share per sorted slot (the fill's partners)
+    float4 *u_ref;               // warp lists: cell-relative FP32 position at the build (id order)
+    float *disp;                 // warp lists: |displacement| since the build, this step (id order)
     bool cut_detected;           // cutoffs come from detection (lists anticipate d moves)
     bool list_warp;              // lists built and walked by the warp kernels (set per capture)
     bool step_detect;            // the step being enqueued re-detects the interface

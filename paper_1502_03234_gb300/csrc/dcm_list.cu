@@ -64,13 +64,18 @@ __global__ void k_list_total(int64_t N, const int32_t *__restrict__ start, int64
     st->list_entries = fill_counts ? 0ull : (unsigned long long)total;
 }
 
-__global__ void k_list_save(int64_t N, const double *__restrict__ x, double *x_ref, const int *gate)
+// the build's positions: FP64, and with the warp lists the FP32
+// cell-relative ones of the fresh sort (id order)
+__global__ void k_list_save(int64_t N, const double *__restrict__ x, double *x_ref, const int *gate,
+                            const float4 *__restrict__ sp4, const int32_t *__restrict__ inv,
+                            float4 *u_ref)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N || *gate == 0) return;
     x_ref[i] = x[i];
     x_ref[N + i] = x[N + i];
     x_ref[2 * N + i] = x[2 * N + i];
+    if (u_ref) u_ref[i] = sp4[inv[i]];
 }
 
 static inline int nblk(int64_t n, int b) { return (int)((n + b - 1) / b); }
@@ -82,6 +87,9 @@ ListTest list_test(dcm_handle *h, bool partner, bool excess, bool decide)
     t.x_ref = h->x_ref;
     t.rl_ref = h->rl_ref;
     t.sh_ref = h->sh_ref;
+    // the warp kernels keep FP32 cell-relative positions current every step
+    t.u_ref = h->list_warp ? h->u_ref : nullptr;
+    t.disp = h->list_warp ? h->disp : nullptr;
     t.partner = partner ? 1 : 0;
     t.excess = excess ? 1 : 0;
     t.decide = decide ? 1 : 0;
@@ -130,7 +138,8 @@ int launch_list_step(dcm_handle *h, bool force_rebuild)
             cudaStream_t s = h->stream;
             launch_scan(h, h->nl_cnt, h->nl_start, h->nl_tiles, N, -1, rebuild);
             k_list_total<<<1, 1, 0, s>>>(N, h->nl_start, h->nl_cap, h->lflags, h->stats, 1);
-            k_list_save<<<nblk(N, 256), 256, 0, s>>>(N, h->x, h->x_ref, fill);
+            k_list_save<<<nblk(N, 256), 256, 0, s>>>(N, h->x, h->x_ref, fill, h->sp4, h->inv,
+                                                     h->u_ref);
             if (cudaGetLastError() != cudaSuccess) r = fail(DCM_ERR_CUDA, "list launch");
         }
         int r2 = branch_close(h, br);
@@ -146,7 +155,7 @@ int launch_list_step(dcm_handle *h, bool force_rebuild)
     k_list_total<<<1, 1, 0, s>>>(N, h->nl_start, h->nl_cap, h->lflags, h->stats, 0);
     r = launch_list_walk(h, true, fill, delta);
     if (r) return r;
-    k_list_save<<<nblk(N, 256), 256, 0, s>>>(N, h->x, h->x_ref, fill);
+    k_list_save<<<nblk(N, 256), 256, 0, s>>>(N, h->x, h->x_ref, fill, nullptr, nullptr, nullptr);
     return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "list launch");
 }
 
