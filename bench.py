@@ -585,6 +585,9 @@ def main():
                     "flops_view": {"achieved": FLOPS_PER_PAIR * pairs / (l_ms * 1e-3) / 1e12,
                                    "peak": fp32_peak, "unit": "TFLOP/s",
                                    "frac": FLOPS_PER_PAIR * pairs / (l_ms * 1e-3) / 1e12 / fp32_peak},
+                    "phase_note": ("with the step graph's single conditional node the force phase "
+                                   "of a rebuild step also holds the list build (sort, gather, "
+                                   "class lists, capacity scan); the binning phase is empty"),
                     "rebuild_steps": sum(rebuilt),
                     "rebuild_force_ms_avg": (sum(t for t, r in zip(force_ms, rebuilt) if r) /
                                              max(1, sum(rebuilt))),

@@ -698,7 +698,7 @@ static void mark(dcm_handle *h, int q, bool capturing)
 // ---- conditional branches of a captured step ----------------------------
 namespace dcm {
 
-int branch_open(dcm_handle *h, Branch &b, int nbody, int which)
+int branch_open(dcm_handle *h, Branch &b, int nbody)
 {
     b.active = false;
     if (!h->branching) return DCM_OK;
@@ -711,7 +711,7 @@ int branch_open(dcm_handle *h, Branch &b, int nbody, int which)
     if (e != cudaSuccess) return fail_cuda(e, "capture info", __FILE__, __LINE__);
     if (st != cudaStreamCaptureStatusActive) return fail(DCM_ERR_STATE, "branch outside a capture");
     cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
-    p.conditional.handle = h->cond[which];
+    p.conditional.handle = h->cond;
     p.conditional.type = cudaGraphCondTypeIf;
     p.conditional.size = (unsigned)nbody;
     cudaGraphNode_t node;
@@ -794,9 +794,26 @@ static int enqueue_step(dcm_handle *h, bool detect, bool capturing)
     mark(h, 1, capturing);
     if (!r && detect) r = launch_detect(h);
     mark(h, 2, capturing);
-    if (!r) r = h->nl ? launch_list_step(h, false) : launch_bin(h);
-    mark(h, 3, capturing);
-    if (!r) r = launch_forces(h, false);
+    if (h->branching) {
+        // warp Verlet lists in a captured graph: one IF node on the rebuild
+        // decision holds the list build and the force walk of a rebuild step
+        // (body 0) and the list force of every other step (body 1).  Events
+        // cannot sit in a body, so the binning phase is empty here and the
+        // force phase covers both.
+        mark(h, 3, capturing);
+        Branch br = {};
+        if (!r) r = branch_open(h, br, 2);
+        if (!r) r = launch_list_step(h, false);
+        if (!r) r = launch_list_forces(h, false, 0);
+        if (!r) r = branch_else(h, br);
+        if (!r) r = launch_list_forces(h, false, 1);
+        int r2 = branch_close(h, br);
+        if (!r) r = r2;
+    } else {
+        if (!r) r = h->nl ? launch_list_step(h, false) : launch_bin(h);
+        mark(h, 3, capturing);
+        if (!r) r = launch_forces(h, false);
+    }
     mark(h, 4, capturing);
     if (!r) r = launch_kick(h);
     mark(h, 5, capturing);
@@ -822,8 +839,8 @@ static int capture(dcm_handle *h, bool detect, cudaGraphExec_t *exec)
         cudaStreamCaptureStatus st;
         cudaGraph_t g = nullptr;
         e = cudaStreamGetCaptureInfo(main, &st, nullptr, &g);
-        for (int q = 0; q < 2 && e == cudaSuccess; ++q)
-            e = cudaGraphConditionalHandleCreate(&h->cond[q], g, 1, cudaGraphCondAssignDefault);
+        if (e == cudaSuccess)
+            e = cudaGraphConditionalHandleCreate(&h->cond, g, 1, cudaGraphCondAssignDefault);
     }
     int r = e == cudaSuccess ? DCM_OK : fail_cuda(e, "conditional handle", __FILE__, __LINE__);
     h->br_kernels[0] = h->br_kernels[1] = 0;

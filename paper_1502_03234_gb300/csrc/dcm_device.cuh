@@ -304,8 +304,8 @@ struct ListTest {
     int partner;                       // the displacement-share term here
     int decide;                        // this kernel's last block decides
     int force;                         // decide "rebuild" whatever the terms
-    int set_cond;                      // also set the step graph's branch conditions
-    cudaGraphConditionalHandle cond0, cond1;
+    int set_cond;                      // also set the step graph's branch condition
+    cudaGraphConditionalHandle cond;
 };
 
 // order-preserving int image of a float (for atomicMax over signed values);
@@ -371,10 +371,7 @@ __device__ __forceinline__ void list_decide(const ListTest &t)
     lf[LF_REBUILD] = rebuild;
     if (rebuild) lf[LF_SHMAX] = 0;          // the gather of the build takes the max
     lf[LF_DONE] = 0;
-    if (t.set_cond) {
-        cudaGraphSetConditional(t.cond0, (unsigned)rebuild);
-        cudaGraphSetConditional(t.cond1, (unsigned)rebuild);
-    }
+    if (t.set_cond) cudaGraphSetConditional(t.cond, (unsigned)rebuild);
 }
 
 // the block's maxima into the control words and, in the last block of a

@@ -1282,37 +1282,22 @@ int prepare_force_kernels()
     return DCM_OK;
 }
 
-int launch_forces(dcm_handle *h, bool energy)
+// rebuild step (part 0): direct walk + list fill; other steps (part 1): the
+// lists.  Eagerly (part 2) both are launched and each returns at once unless
+// it is its step; a captured step puts them in the two bodies of its graph
+// IF node on the rebuild decision.
+int launch_list_forces(dcm_handle *h, bool energy, int part)
 {
     ForceArgs a;
     fill_args(h, a);
-    const bool list_warp = h->nl && h->list_warp;
-    if (!list_warp) cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), h->stream);
-    int block = h->tune.block >= 64 && h->tune.block <= FORCE_THREADS ? h->tune.block : FORCE_THREADS;
-    int grid = h->num_sms * (2048 / block);
-    bool fp64 = h->p.precision == DCM_FP64;
-    if (!fp64 && !h->nl && h->tune.walk == DCM_WALK_WARP) {
-        if (energy)
-            launch_walk<true, false>(h, a);
-        else
-            launch_walk<false, false>(h, a);
-        return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "force launch");
-    }
-    if (list_warp) {
-        // rebuild step: direct walk + list fill; other steps: the lists.
-        // Eagerly both are launched and each returns at once unless it is
-        // its step; a captured step holds them in the two bodies of a graph
-        // IF node on the rebuild decision.
-        Branch br;
-        int r = branch_open(h, br, 2, 1);
-        if (r) return r;
+    if (part != 1) {
         cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), h->stream);
         if (energy)
             launch_walk<true, true>(h, a);
         else
             launch_walk<false, true>(h, a);
-        r = branch_else(h, br);
-        if (r) return r;
+    }
+    if (part != 0) {
         cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), h->stream);
         const int G = h->tune.list_lanes > 0 ? h->tune.list_lanes : FW_LIST_G;
         const int gl = h->num_sms * FW_LIST_MINB;   // persistent: the resident blocks
@@ -1330,10 +1315,27 @@ int launch_forces(dcm_handle *h, bool energy)
             if (one) k_force_list_warp<false, 8, true><<<gl, FW_THREADS, 0, h->stream>>>(a);
             else k_force_list_warp<false, 8, false><<<gl, FW_THREADS, 0, h->stream>>>(a);
         }
-        if (cudaGetLastError() != cudaSuccess) r = fail(DCM_ERR_CUDA, "force launch");
-        int r2 = branch_close(h, br);
-        return r ? r : r2;
     }
+    return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "force launch");
+}
+
+int launch_forces(dcm_handle *h, bool energy)
+{
+    ForceArgs a;
+    fill_args(h, a);
+    const bool list_warp = h->nl && h->list_warp;
+    if (!list_warp) cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), h->stream);
+    int block = h->tune.block >= 64 && h->tune.block <= FORCE_THREADS ? h->tune.block : FORCE_THREADS;
+    int grid = h->num_sms * (2048 / block);
+    bool fp64 = h->p.precision == DCM_FP64;
+    if (!fp64 && !h->nl && h->tune.walk == DCM_WALK_WARP) {
+        if (energy)
+            launch_walk<true, false>(h, a);
+        else
+            launch_walk<false, false>(h, a);
+        return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "force launch");
+    }
+    if (list_warp) return launch_list_forces(h, energy, 2);
     if (fp64) {
         if (energy)
             k_force<DCM_FP64, true><<<grid, block, 0, h->stream>>>(a);

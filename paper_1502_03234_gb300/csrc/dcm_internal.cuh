@@ -225,8 +225,7 @@ struct dcm_handle {
     // conditional branches of a captured step: k_list_check sets `cond` to
     // the rebuild decision, graph IF nodes on it hold the rebuild-only work
     cudaStream_t side;                  // records the branch bodies
-    cudaGraphConditionalHandle cond[2]; // of the graph being captured: list step, forces
-                                        // (a handle serves one conditional node)
+    cudaGraphConditionalHandle cond;    // the rebuild decision of the graph being captured
     bool branching;                     // enqueue_step is recording a graph with branches
     bool fold_check;                    // the step's drift / cutoff kernel runs the reuse test
     int br_kernels[2];                  // kernels in bodies taken on rebuild / reuse
@@ -260,13 +259,17 @@ int launch_scan(dcm_handle *h, const int32_t *in, int32_t *out, int32_t *tiles, 
 int launch_list_step(dcm_handle *h, bool force_rebuild);  // decide, [rebin], lists
 int launch_list_walk(dcm_handle *h, bool fill, const int *gate, float delta);
 int launch_forces(dcm_handle *h, bool energy);   // list mode when skin > 0 and the lists are ok
+// warp Verlet-list forces: part 0 the rebuild step's direct walk + fill,
+// part 1 the list force, 2 both (each kernel returns at once when it is not
+// its step)
+int launch_list_forces(dcm_handle *h, bool energy, int part);
 int launch_detect(dcm_handle *h);
 int launch_reduce_energy(dcm_handle *h, int k);
 int launch_reduce_pairs(dcm_handle *h);
 int launch_classify_rc(dcm_handle *h);   // classes from supplied rc
 
 // A branch of a captured step on the Verlet-list rebuild decision (a CUDA
-// graph IF node on one of h->cond).  Between branch_open and branch_close the work
+// graph IF node on h->cond).  Between branch_open and branch_close the work
 // enqueued on h->stream is recorded into body 0, taken on a step that
 // rebuilds the lists, and after branch_else into body 1, taken on a step that
 // reuses them.  Outside a capture, or without the warp list kernels, the
@@ -277,7 +280,7 @@ struct Branch {
     cudaGraph_t body[2];
     cudaStream_t main;
 };
-int branch_open(dcm_handle *h, Branch &b, int nbody, int which);   // which: h->cond[which]
+int branch_open(dcm_handle *h, Branch &b, int nbody);     // an IF node on h->cond
 int branch_else(dcm_handle *h, Branch &b);
 int branch_close(dcm_handle *h, Branch &b);
 

@@ -95,8 +95,7 @@ ListTest list_test(dcm_handle *h, bool partner, bool excess, bool decide)
     t.decide = decide ? 1 : 0;
     t.force = 0;
     t.set_cond = h->branching ? 1 : 0;
-    t.cond0 = h->cond[0];
-    t.cond1 = h->cond[1];
+    t.cond = h->cond;
     return t;
 }
 
@@ -108,9 +107,9 @@ void list_mode(dcm_handle *h)
 // decide, [cell sort], gather + classes, then
 //  warp kernels (MIXED, warp walk): [capacity scan, total, save]; the list
 //      fill happens in the force phase, inside the direct force walk of the
-//      rebuild step (launch_forces).  In a captured step the bracketed work
-//      sits in a graph IF node on the decision, so a step that reuses its
-//      lists launches none of it;
+//      rebuild step (launch_list_forces).  In a captured step the bracketed
+//      work sits in the rebuild body of the step's graph IF node (see
+//      enqueue_step), so a step that reuses its lists launches none of it;
 //  lanes kernels: [list count, scan, total, fill, save]
 int launch_list_step(dcm_handle *h, bool force_rebuild)
 {
@@ -125,9 +124,7 @@ int launch_list_step(dcm_handle *h, bool force_rebuild)
     const int *rebuild = h->lflags + LF_REBUILD;
     const int *fill = h->lflags + LF_FILL;
     if (h->list_warp) {
-        Branch br;
-        int r = branch_open(h, br, 1, 0);
-        if (!r) r = launch_sort_gather(h, rebuild);
+        int r = launch_sort_gather(h, rebuild);
         // the class lists only order the work queue: they are redone with
         // the sort (new slots) and left as they are after a detection that
         // keeps the lists (every slot is still in exactly one list; the
@@ -142,8 +139,7 @@ int launch_list_step(dcm_handle *h, bool force_rebuild)
                                                      h->u_ref);
             if (cudaGetLastError() != cudaSuccess) r = fail(DCM_ERR_CUDA, "list launch");
         }
-        int r2 = branch_close(h, br);
-        return r ? r : r2;
+        return r;
     }
     cudaStream_t s = h->stream;
     int r = launch_bin_gated(h, rebuild, nullptr);
