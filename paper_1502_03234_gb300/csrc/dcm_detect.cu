@@ -130,6 +130,15 @@ __global__ void __launch_bounds__(256) k_smooth8(Batch b, const TIN *__restrict_
         const TIN *p = line + (int64_t)(c - 4) * stride;
 #pragma unroll
         for (int k = 0; k < 9; ++k) sum += (ACC)W[k] * (ACC)(uint32_t)p[(int64_t)k * stride];
+    } else if (n > 8) {
+        // near the seam: one conditional wrap (the kernel fits in the line)
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            int q = c + k - 4;
+            q += q < 0 ? n : 0;
+            q -= q >= n ? n : 0;
+            sum += (ACC)W[k] * (ACC)(uint32_t)line[(int64_t)q * stride];
+        }
     } else {
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
