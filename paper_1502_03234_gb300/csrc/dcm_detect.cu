@@ -158,12 +158,21 @@ __global__ void __launch_bounds__(256) k_smooth8(Batch b, const TIN *__restrict_
 constexpr int SPREAD = 16;
 constexpr int KACC = 9 * SPREAD;
 
-__global__ void k_kmeans_init(int M, unsigned long long *acc)
+// the detection's zeroed state in one launch: the density grid (Eq. 9
+// accumulates into it), the K-means accumulators, the grid-barrier words and
+// the CFSM frontier counters
+__global__ void k_detect_init(int64_t nv, int32_t *B, int M, unsigned long long *acc,
+                              unsigned int *bar, int32_t *fcount)
 {
-    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= (int64_t)M * KACC) return;
-    int w = (int)(q % KACC) / SPREAD;
-    acc[q] = w == 1 ? ~0ull : 0ull;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = t; v < nv; v += nth) B[v] = 0;
+    for (int64_t q = t; q < (int64_t)M * KACC; q += nth) {
+        int w = (int)(q % KACC) / SPREAD;
+        acc[q] = w == 1 ? ~0ull : 0ull;
+    }
+    if (t < 2) bar[t] = 0u;
+    if (t < 4) fcount[t] = 0;
 }
 
 __device__ __forceinline__ unsigned long long spread_sum(const unsigned long long *p)
@@ -547,9 +556,10 @@ __device__ __forceinline__ int64_t vox(int x, int y, int z, int nx, int ny)
 // D0 = D1 = 0 on vapor, +inf on liquid; frontier 0 = liquid voxels with a
 // vapor face neighbour (the "interfacial boxes")
 __global__ void k_cfsm_init(Batch b, const uint8_t *__restrict__ S, double *D0, double *D1,
-                            int32_t *stamp, int32_t *list0, int32_t *fcount)
+                            int32_t *stamp, int32_t *list0, int32_t *fcount, unsigned int *bar)
 {
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < 2) bar[v] = 0u;                  // the K-means kernel is done with them
     if (v >= b.NV) return;
     bool vap = S[v] == 1;
     double d = vap ? 0.0 : __longlong_as_double(0x7ff0000000000000ll);
@@ -935,7 +945,8 @@ int launch_detect(dcm_handle *h)
     const Batch &b = h->b;
     int64_t nv = b.NV;
     // Eq. 9
-    cudaMemsetAsync(h->B, 0, sizeof(int32_t) * nv, s);
+    k_detect_init<<<h->num_sms * 4, 256, 0, s>>>(nv, h->B, b.M, h->kacc, h->stats->barrier,
+                                                 h->fcount);
     k_density<<<nblk(b.N, 256), 256, 0, s>>>(b, h->x, h->B);
     // smoothing
     int order = h->p.smooth_order;
@@ -965,9 +976,7 @@ int launch_detect(dcm_handle *h)
         w.bmax = 0xffffffffu;
         k_smooth<0, int32_t, double><<<vb, DET_THREADS, 0, s>>>(b, h->B, h->Bs, w, h->err);
     }
-    // K-means labels
-    k_kmeans_init<<<nblk((int64_t)b.M * KACC, 256), 256, 0, s>>>(b.M, h->kacc);
-    cudaMemsetAsync(h->stats->barrier, 0, 2 * sizeof(unsigned int), s);
+    // K-means labels (accumulators and barrier words zeroed by k_detect_init)
     {
         KmeansArgs a;
         a.b = b;
@@ -994,10 +1003,9 @@ int launch_detect(dcm_handle *h)
         }
         if (rc) return rc;
     }
-    // CFSM
-    cudaMemsetAsync(h->fcount, 0, 4 * sizeof(int32_t), s);
-    k_cfsm_init<<<vb, DET_THREADS, 0, s>>>(b, h->S, h->D0, h->D1, h->stamp, h->flist, h->fcount);
-    cudaMemsetAsync(h->stats->barrier, 0, 2 * sizeof(unsigned int), s);
+    // CFSM (frontier counters zeroed by k_detect_init, barrier words by k_cfsm_init)
+    k_cfsm_init<<<vb, DET_THREADS, 0, s>>>(b, h->S, h->D0, h->D1, h->stamp, h->flist, h->fcount,
+                                           h->stats->barrier);
     {
         CfsmArgs a;
         a.b = b;
