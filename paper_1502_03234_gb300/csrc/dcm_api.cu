@@ -471,6 +471,7 @@ static int create_systems(int M, const dcm_box *boxes, const int64_t *ns, const 
     cudaMemsetAsync(h->v, 0, sizeof(double) * 3 * N, h->stream);
     cudaMemsetAsync(h->f, 0, sizeof(double) * 3 * N, h->stream);
     cudaMemsetAsync(h->cls, 0, N, h->stream);
+    cudaMemsetAsync(h->cell_count, 0, sizeof(int32_t) * nc, h->stream);
     if (h->inv) launch_iota(h, h->inv, N);       // a valid permutation before the first sort
     if (M > 1) launch_sys_tables(h);
     if (h->nl) {
@@ -789,6 +790,7 @@ static int enqueue_step(dcm_handle *h, bool detect, bool capturing)
     list_mode(h);
     h->step_detect = detect;
     h->fold_check = h->nl != nullptr;        // the reuse test rides on the drift / cutoff kernel
+    h->in_step = true;
     mark(h, 0, capturing);
     int r = launch_kick_drift(h);
     mark(h, 1, capturing);
@@ -818,6 +820,7 @@ static int enqueue_step(dcm_handle *h, bool detect, bool capturing)
     if (!r) r = launch_kick(h);
     mark(h, 5, capturing);
     h->fold_check = false;
+    h->in_step = false;
     return r;
 }
 

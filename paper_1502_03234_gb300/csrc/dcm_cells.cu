@@ -130,10 +130,13 @@ __global__ void k_gather(Batch b, const double *__restrict__ x, const double *__
                          const int32_t *__restrict__ cell_of, float4 *sp4, double4_32a *spd,
                          const double *__restrict__ rc, float4 *rq, int4 *pk, float *sh,
                          const double *__restrict__ dist, int *lf, float delta, int32_t *capk,
-                         int32_t *inv, const int *gate)
+                         int32_t *inv, const int *gate, int32_t *cell_count)
 {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= b.N || gated_off(gate)) return;
+    if (gated_off(gate)) return;
+    // the cell counts have served the scan: zero them for the next sort
+    for (int64_t c = k; c < b.NC; c += (int64_t)gridDim.x * blockDim.x) cell_count[c] = 0;
+    if (k >= b.N) return;
     // sorted slots keep the systems' particle ranges
     const Geom &g = b.sys[sys_p(b, k)];
     int i = sorted_id[k];
@@ -251,7 +254,8 @@ int launch_sort_gather(dcm_handle *h, const int *gate)
 {
     cudaStream_t s = h->stream;
     int n = (int)h->n;
-    cudaMemsetAsync(h->cell_count, 0, sizeof(int32_t) * h->ncell, s);
+    // cell_count is zero here: zeroed at creation and again by the gather
+    // once the scan has used it
     k_cell_count<<<nblk(n, 256), 256, 0, s>>>(h->b, h->x, h->cell_of, h->slot, h->cell_count, gate);
     launch_scan(h, h->cell_count, h->cell_start, h->scan_tmp, h->ncell, n, gate);
     k_cell_scatter<<<nblk(n, 256), 256, 0, s>>>(n, h->cell_of, h->slot, h->cell_start,
@@ -262,7 +266,7 @@ int launch_sort_gather(dcm_handle *h, const int *gate)
                                           h->p.precision == DCM_FP64 ? h->spd : nullptr, h->rc,
                                           h->rq, h->pk, h->sh, h->d, h->lflags,
                                           h->cut_detected ? h->list_margin : 0.0f, wl ? h->nl_cnt : nullptr,
-                                          h->inv, wl ? gate : nullptr);
+                                          h->inv, wl ? gate : nullptr, h->cell_count);
     return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "binning launch");
 }
 

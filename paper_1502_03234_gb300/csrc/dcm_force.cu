@@ -1290,15 +1290,17 @@ int launch_list_forces(dcm_handle *h, bool energy, int part)
 {
     ForceArgs a;
     fill_args(h, a);
+    // inside a captured step the drift has zeroed both queues
     if (part != 1) {
-        cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), h->stream);
+        if (!h->in_step) cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), h->stream);
         if (energy)
             launch_walk<true, true>(h, a);
         else
             launch_walk<false, true>(h, a);
     }
     if (part != 0) {
-        cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), h->stream);
+        a.queue = &h->stats->barrier[5];
+        if (!h->in_step) cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), h->stream);
         const int G = h->tune.list_lanes > 0 ? h->tune.list_lanes : FW_LIST_G;
         const int gl = h->num_sms * FW_LIST_MINB;   // persistent: the resident blocks
         const bool one = h->b.M == 1;
@@ -1324,7 +1326,10 @@ int launch_forces(dcm_handle *h, bool energy)
     ForceArgs a;
     fill_args(h, a);
     const bool list_warp = h->nl && h->list_warp;
-    if (!list_warp) cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), h->stream);
+    const bool warp_walk = h->p.precision == DCM_MIXED && h->tune.walk == DCM_WALK_WARP;
+    // (the lanes list walks use the queue before the forces of their step)
+    if (!list_warp && !(h->in_step && warp_walk && !h->nl))
+        cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), h->stream);
     int block = h->tune.block >= 64 && h->tune.block <= FORCE_THREADS ? h->tune.block : FORCE_THREADS;
     int grid = h->num_sms * (2048 / block);
     bool fp64 = h->p.precision == DCM_FP64;

@@ -16,9 +16,14 @@ namespace dcm {
 __global__ void k_kick_drift(Batch b, double *__restrict__ x, double *__restrict__ v,
                              const double *__restrict__ f, int *err, float4 *sp4,
                              const int32_t *__restrict__ inv, const int32_t *__restrict__ cell_of,
-                             const double *__restrict__ rc, ListTest t)
+                             const double *__restrict__ rc, ListTest t, unsigned int *queues)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // the step's force work queues (a captured step has no memset nodes)
+    if (queues && i == 0) {
+        queues[0] = 0u;
+        queues[3] = 0u;
+    }
     float mp = -3.0e38f, mq = -3.0e38f;
     if (i < b.N) {
         const Geom &g = b.sys[sys_p(b, i)];
@@ -166,7 +171,8 @@ int launch_kick_drift(dcm_handle *h)
     if (!h->fold_check) t.lf = nullptr;
     k_kick_drift<<<nblk(h->n, 256), 256, 0, h->stream>>>(h->b, h->x, h->v, h->f, h->err,
                                                          wl ? h->sp4 : nullptr, h->inv, h->cell_of,
-                                                         h->rc, t);
+                                                         h->rc, t,
+                                                         h->in_step ? &h->stats->barrier[2] : nullptr);
     return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "kick_drift launch");
 }
 

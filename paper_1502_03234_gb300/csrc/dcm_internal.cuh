@@ -57,7 +57,7 @@ struct DevStats {
     double c_vapor;
     int class_count[DCM_MAX_CLASSES];
     unsigned int barrier[6];     // [0..1] grid barrier, [2] force queue, [3] CFSM result buffer,
-                                 // [4] first CFSM pass of the cluster tail
+                                 // [4] first CFSM pass of the cluster tail, [5] list-force queue
     unsigned long long list_builds;
     unsigned long long list_entries;
 };
@@ -228,6 +228,7 @@ struct dcm_handle {
     cudaGraphConditionalHandle cond;    // the rebuild decision of the graph being captured
     bool branching;                     // enqueue_step is recording a graph with branches
     bool fold_check;                    // the step's drift / cutoff kernel runs the reuse test
+    bool in_step;                       // enqueue_step: the drift zeroes the force queues
     int br_kernels[2];                  // kernels in bodies taken on rebuild / reuse
     // kernel nodes of one captured step: [plain, detect] x [rebuild, reuse]
     int kernels_plain, kernels_detect, kernels_plain_reuse, kernels_detect_reuse;
