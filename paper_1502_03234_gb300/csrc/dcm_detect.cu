@@ -158,15 +158,18 @@ __global__ void __launch_bounds__(256) k_smooth8(Batch b, const TIN *__restrict_
 constexpr int SPREAD = 16;
 constexpr int KACC = 9 * SPREAD;
 
-// the detection's zeroed state in one launch: the density grid (Eq. 9
-// accumulates into it), the K-means accumulators, the grid-barrier words and
-// the CFSM frontier counters
-__global__ void k_detect_init(int64_t nv, int32_t *B, int M, unsigned long long *acc,
-                              unsigned int *bar, int32_t *fcount)
+// the detection's initial state in one launch: the density grid (Eq. 9
+// accumulates into it), the CFSM stamps, the K-means accumulators, the
+// grid-barrier words and the CFSM frontier counters
+__global__ void k_detect_init(int64_t nv, int32_t *B, int32_t *stamp, int M,
+                              unsigned long long *acc, unsigned int *bar, int32_t *fcount)
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nth = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t v = t; v < nv; v += nth) B[v] = 0;
+    for (int64_t v = t; v < nv; v += nth) {
+        B[v] = 0;
+        stamp[v] = -1;                           // no CFSM pass has claimed the voxel
+    }
     for (int64_t q = t; q < (int64_t)M * KACC; q += nth) {
         int w = (int)(q % KACC) / SPREAD;
         acc[q] = w == 1 ? ~0ull : 0ull;
@@ -553,36 +556,115 @@ __device__ __forceinline__ int64_t vox(int x, int y, int z, int nx, int ny)
     return x + (int64_t)nx * (y + (int64_t)ny * z);
 }
 
-// D0 = D1 = 0 on vapor, +inf on liquid; frontier 0 = liquid voxels with a
-// vapor face neighbour (the "interfacial boxes")
-__global__ void k_cfsm_init(Batch b, const uint8_t *__restrict__ S, double *D0, double *D1,
-                            int32_t *stamp, int32_t *list0, int32_t *fcount, unsigned int *bar)
+// one voxel's Jacobi update (Algorithm 4.3): the Godunov solve from its face
+// neighbours' values a{x,y,z} (Eq. 16-19); true when it lowers the voxel's
+// value within the band r_grid.  Any solution is at least min(a) +
+// 1/sqrt(sum w): when that cannot beat the current value the solve is
+// skipped (a lower bound with a relative margin, so no update is lost).
+__device__ __forceinline__ bool cfsm_solve(const Geom &g, double old, double ax, double ay,
+                                           double az, double &dbar)
 {
-    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v < 2) bar[v] = 0u;                  // the K-means kernel is done with them
-    if (v >= b.NV) return;
-    bool vap = S[v] == 1;
-    double d = vap ? 0.0 : __longlong_as_double(0x7ff0000000000000ll);
-    D0[v] = d;
-    D1[v] = d;
-    int st = -1;
-    if (!vap) {
-        const Geom &g = b.sys[sys_v(b, v)];
-        const int nx = g.gd[0], ny = g.gd[1], nz = g.gd[2];
-        const uint8_t *Sg = S + g.v0;
-        int lv = (int)(v - g.v0);
-        int x = lv % nx, yz = lv / nx;
-        int y = yz % ny, z = yz / ny;
-        int xm = x ? x - 1 : nx - 1, xp = x + 1 < nx ? x + 1 : 0;
-        int ym = y ? y - 1 : ny - 1, yp = y + 1 < ny ? y + 1 : 0;
-        int zm = z ? z - 1 : nz - 1, zp = z + 1 < nz ? z + 1 : 0;
-        if (Sg[vox(xm, y, z, nx, ny)] | Sg[vox(xp, y, z, nx, ny)] | Sg[vox(x, ym, z, nx, ny)] |
-            Sg[vox(x, yp, z, nx, ny)] | Sg[vox(x, y, zm, nx, ny)] | Sg[vox(x, y, zp, nx, ny)]) {
-            list0[atomicAdd(&fcount[0], 1)] = (int32_t)v;
-            st = 0;
-        }
+    double amin = dmin_nonneg(ax, dmin_nonneg(ay, az));
+    dbar = old;
+    if (isinf(amin) ||
+        __double_as_longlong(old) <= __double_as_longlong(amin + 0.999999 * g.e_min))
+        return false;
+    dbar = godunov_w(ax, ay, az, g.h[0], g.h[1], g.h[2], g.w_h[0], g.w_h[1], g.w_h[2]);
+    // non-negative doubles: compare the bit patterns
+    return __double_as_longlong(dbar) < __double_as_longlong(old) &&
+           __double_as_longlong(dbar) <= __double_as_longlong(g.r_grid);
+}
+
+// a changed voxel v: itself (so the other buffer catches up next pass) and
+// its liquid face neighbours go to pass k+1's frontier, each once (stamp
+// k+1; the seven exchanges are independent of each other); returns how many
+// this thread claimed into push
+__device__ __forceinline__ int cfsm_claim(int v, const int nb[6], const bool liq[7], int k,
+                                          int32_t *stamp, int32_t push[7])
+{
+    const int cand[7] = {v, nb[0], nb[1], nb[2], nb[3], nb[4], nb[5]};
+    int prev[7];
+#pragma unroll
+    for (int e = 0; e < 7; ++e) prev[e] = liq[e] ? atomicExch(&stamp[cand[e]], k + 1) : k + 1;
+    int n = 0;
+#pragma unroll
+    for (int e = 0; e < 7; ++e)
+        if (prev[e] != k + 1) push[n++] = cand[e];
+    return n;
+}
+
+// the lanes' claims appended to the next frontier, one atomic per warp
+// (every lane of the warp calls it)
+__device__ __forceinline__ void cfsm_append(const int32_t push[7], int npush, int32_t *count,
+                                            int32_t *Fn, int lane)
+{
+    int incl = npush;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += t;
     }
-    stamp[v] = st;
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total) {
+        int base = 0;
+        if (lane == 31) base = atomicAdd(count, total);
+        base = __shfl_sync(0xffffffffu, base, 31) + incl - npush;
+        for (int e = 0; e < npush; ++e) Fn[base + e] = push[e];
+    }
+}
+
+// the initial values, D = 0 on vapor and +inf on liquid (buffer D0), and the
+// first pass of the iteration done in place: it reads only those values, so
+// the liquid voxels with a vapor face neighbour (the "interfacial boxes")
+// solve here (into D1) and claim the next frontier (list 1) as any pass
+// would.  The stamps are -1 (k_detect_init).
+__global__ void k_cfsm_init(Batch b, const uint8_t *__restrict__ S, double *D0, double *D1,
+                            int32_t *stamp, int32_t *list1, int32_t *fcount, unsigned int *bar)
+{
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = (int)(threadIdx.x & 31);
+    if (v < 2) bar[v] = 0u;                  // the K-means kernel is done with them
+    int32_t push[7];
+    int npush = 0;
+    if (v < b.NV) {
+        const double inf = __longlong_as_double(0x7ff0000000000000ll);
+        const bool vap = S[v] == 1;
+        const double d0 = vap ? 0.0 : inf;
+        D0[v] = d0;
+        double d1 = d0;
+        if (!vap) {
+            const Geom &g = b.sys[sys_v(b, v)];
+            const int nx = g.gd[0], ny = g.gd[1], nz = g.gd[2];
+            const int v0 = (int)g.v0;
+            int lv = (int)(v - v0);
+            int x = lv % nx, yz = lv / nx;
+            int y = yz % ny, z = yz / ny;
+            int xm = x ? x - 1 : nx - 1, xp = x + 1 < nx ? x + 1 : 0;
+            int ym = y ? y - 1 : ny - 1, yp = y + 1 < ny ? y + 1 : 0;
+            int zm = z ? z - 1 : nz - 1, zp = z + 1 < nz ? z + 1 : 0;
+            const int nb[6] = {v0 + xm + nx * yz, v0 + xp + nx * yz,
+                               v0 + x + nx * (ym + ny * z), v0 + x + nx * (yp + ny * z),
+                               v0 + x + nx * (y + ny * zm), v0 + x + nx * (y + ny * zp)};
+            bool liq[7];
+            liq[0] = true;
+#pragma unroll
+            for (int e = 1; e < 7; ++e) liq[e] = S[nb[e - 1]] == 0;
+            if (!(liq[1] && liq[2] && liq[3] && liq[4] && liq[5] && liq[6])) {
+                // pass 0 on an interfacial box: the face values are 0 (vapor)
+                // or +inf (liquid), as in D0
+                const double ax = dmin_nonneg(liq[1] ? inf : 0.0, liq[2] ? inf : 0.0);
+                const double ay = dmin_nonneg(liq[3] ? inf : 0.0, liq[4] ? inf : 0.0);
+                const double az = dmin_nonneg(liq[5] ? inf : 0.0, liq[6] ? inf : 0.0);
+                double dbar;
+                if (cfsm_solve(g, d0, ax, ay, az, dbar)) {
+                    d1 = dbar;
+                    npush = cfsm_claim((int)v, nb, liq, 0, stamp, push);
+                }
+            }
+        }
+        D1[v] = d1;
+    }
+    cfsm_append(push, npush, &fcount[1], list1, lane);
 }
 
 struct CfsmArgs {
@@ -650,47 +732,12 @@ __device__ __forceinline__ void cfsm_pass(const CfsmArgs &a, int k, int nf, int6
             liq[0] = true;
 #pragma unroll
             for (int e = 1; e < 7; ++e) liq[e] = __ldg(&a.S[nb[e - 1]]) == 0;
-            // any Godunov solution is at least min(a) + 1/sqrt(sum w): when
-            // that cannot beat the current value the solve is skipped
-            // (a lower bound with a relative margin, so no update is lost)
-            double amin = dmin_nonneg(ax, dmin_nonneg(ay, az));
-            bool changed = false;
-            double dbar = old;
-            if (!isinf(amin) &&
-                __double_as_longlong(old) > __double_as_longlong(amin + 0.999999 * g.e_min)) {
-                dbar = godunov_w(ax, ay, az, g.h[0], g.h[1], g.h[2], g.w_h[0], g.w_h[1], g.w_h[2]);
-                // non-negative doubles: compare the bit patterns
-                changed = __double_as_longlong(dbar) < __double_as_longlong(old) &&
-                          __double_as_longlong(dbar) <= __double_as_longlong(g.r_grid);
-            }
+            double dbar;
+            const bool changed = cfsm_solve(g, old, ax, ay, az, dbar);
             Y[v] = changed ? dbar : old;
-            if (changed) {
-                // the voxel itself (so Y catches up next pass) and its
-                // liquid face neighbours are recomputed in the next pass;
-                // the seven stamp exchanges are independent of each other
-                int cand[7] = {v, nb[0], nb[1], nb[2], nb[3], nb[4], nb[5]};
-                int prev[7];
-#pragma unroll
-                for (int e = 0; e < 7; ++e) prev[e] = liq[e] ? atomicExch(&a.stamp[cand[e]], k + 1) : k + 1;
-#pragma unroll
-                for (int e = 0; e < 7; ++e)
-                    if (prev[e] != k + 1) push[npush++] = cand[e];
-            }
+            if (changed) npush = cfsm_claim(v, nb, liq, k, a.stamp, push);
         }
-        // one append per warp: exclusive scan of the lanes' counts
-        int incl = npush;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            int t = __shfl_up_sync(0xffffffffu, incl, off);
-            if (lane >= off) incl += t;
-        }
-        int total = __shfl_sync(0xffffffffu, incl, 31);
-        if (total) {
-            int base = 0;
-            if (lane == 31) base = atomicAdd(&a.fcount[(k + 1) & 3], total);
-            base = __shfl_sync(0xffffffffu, base, 31) + incl - npush;
-            for (int e = 0; e < npush; ++e) Fn[base + e] = push[e];
-        }
+        cfsm_append(push, npush, &a.fcount[(k + 1) & 3], Fn, lane);
     }
 }
 
@@ -701,7 +748,7 @@ __global__ void __launch_bounds__(DET_THREADS) k_cfsm(CfsmArgs a)
 {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nth = (int64_t)gridDim.x * blockDim.x;
-    int k = 0;
+    int k = 1;                                   // pass 0 ran in k_cfsm_init
     for (; k < a.iter_max; ++k) {
         const int32_t first = cfsm_first(a, k, tid);
         const int nf = ((volatile int32_t *)a.fcount)[k & 3];
@@ -945,8 +992,8 @@ int launch_detect(dcm_handle *h)
     const Batch &b = h->b;
     int64_t nv = b.NV;
     // Eq. 9
-    k_detect_init<<<h->num_sms * 4, 256, 0, s>>>(nv, h->B, b.M, h->kacc, h->stats->barrier,
-                                                 h->fcount);
+    k_detect_init<<<h->num_sms * 4, 256, 0, s>>>(nv, h->B, h->stamp, b.M, h->kacc,
+                                                 h->stats->barrier, h->fcount);
     k_density<<<nblk(b.N, 256), 256, 0, s>>>(b, h->x, h->B);
     // smoothing
     int order = h->p.smooth_order;
@@ -1004,8 +1051,8 @@ int launch_detect(dcm_handle *h)
         if (rc) return rc;
     }
     // CFSM (frontier counters zeroed by k_detect_init, barrier words by k_cfsm_init)
-    k_cfsm_init<<<vb, DET_THREADS, 0, s>>>(b, h->S, h->D0, h->D1, h->stamp, h->flist, h->fcount,
-                                           h->stats->barrier);
+    k_cfsm_init<<<vb, DET_THREADS, 0, s>>>(b, h->S, h->D0, h->D1, h->stamp, h->flist + nv,
+                                           h->fcount, h->stats->barrier);
     {
         CfsmArgs a;
         a.b = b;
