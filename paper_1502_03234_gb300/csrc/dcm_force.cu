@@ -1203,35 +1203,29 @@ __global__ void __launch_bounds__(FW_THREADS, SINGLE ? FW_WALK_MINB1 : FW_WALK_M
 }
 
 // Verlet-list forces; runs only on a step that keeps its lists.  A warp
-// takes 32/G consecutive queue items per grab, one per lane group.
+// takes 32/G consecutive sorted slots per grab, one per lane group: in cell
+// order the warps resident on an SM work on nearby particles and share
+// their neighbours' positions in L1 (a class-ordered queue, heaviest
+// particles first, was 3.5 % slower: the lists' lengths are already known
+// to be within a few times of each other and the queue balances them)
 template <bool ENERGY, int G, bool SINGLE>
 __global__ void __launch_bounds__(FW_THREADS, FW_LIST_MINB) k_force_list_warp(ForceArgs a)
 {
-    __shared__ FwQueue sq;
     __shared__ int s_run;
-    sq.init(a);
     if (threadIdx.x == 0) s_run = a.list_flags[LF_REBUILD] == 0;
     __syncthreads();
     if (!s_run) return;
     constexpr int PER = 32 / G;
     const int lane = threadIdx.x & 31;
     const int grp = lane / G, gl = lane & (G - 1);
-    const int K = a.b.K;
-    const int total = sq.items[K];
+    const int total = (int)a.b.N;
     int ng = 0;
     while (true) {
         int item0 = 0;
         if (lane == 0) item0 = (int)atomicAdd(a.queue, (unsigned)PER);
         item0 = __shfl_sync(0xffffffffu, item0, 0);
         if (item0 >= total) break;
-        const int item = item0 + grp;
-        int k = -1;
-        if (item < total) {
-            int t = 0;
-            while (t + 1 < K && item >= sq.items[t + 1]) ++t;
-            int q = K - 1 - t;
-            k = a.class_list[sq.off[q] + (item - sq.items[t])];
-        }
+        const int k = item0 + grp < total ? item0 + grp : -1;
         particle_force_list_group<ENERGY, G, SINGLE>(a, k, gl, ng);
     }
     block_counts(a, ng, 0);
