@@ -64,6 +64,8 @@ def _load():
         "orc_density": (None, [i64, vp, vp, vp, vp]),
         "orc_smooth": (None, [vp, vp, C.c_int, vp]),
         "orc_kmeans": (C.c_int, [i64, vp, C.c_int, vp, vp, vp]),
+        "orc_label_components": (i64, [vp, vp, C.c_int, vp]),
+        "orc_remove_small_components": (i64, [vp, vp, C.c_int]),
         "orc_godunov": (d, [vp, vp]),
         "orc_fsm": (C.c_int, [vp, vp, vp, d, vp]),
         "orc_cfsm": (C.c_int, [vp, vp, vp, d, C.c_int, d, vp]),
@@ -227,6 +229,24 @@ def kmeans(Bs, max_iter=100):
     return S, cl.value, cv.value, it
 
 
+def label_components(dims, S, phase):
+    """Section 4.2 / Algorithm 4.1: (labels, count) of the phase's components."""
+    d = _i32(dims)
+    S = np.ascontiguousarray(S, dtype=np.uint8).ravel()
+    lab = np.zeros(max(S.size, 1), np.int32)
+    nc = _load().orc_label_components(_p(d), _p(S), int(phase), _p(lab))
+    return lab[: S.size], int(nc)
+
+
+def remove_small_components(dims, S, min_voxels):
+    """Section 4.2: (new labels, voxels changed) after removing the small
+    liquid, then vapor components."""
+    d = _i32(dims)
+    out = np.array(np.ascontiguousarray(S, dtype=np.uint8).ravel())
+    flipped = _load().orc_remove_small_components(_p(d), _p(out), int(min_voxels))
+    return out, int(flipped)
+
+
 def godunov(a, h) -> float:
     a = _f64(a)
     h = _f64(h)
@@ -267,7 +287,8 @@ class _DetectParams(C.Structure):
     _fields_ = [("rc_min", C.c_double), ("rc_max", C.c_double), ("alpha", C.c_double),
                 ("voxel", C.c_double), ("smooth_order", C.c_int),
                 ("kmeans_max_iter", C.c_int), ("cfsm_iter_max", C.c_int),
-                ("cfsm_eps", C.c_double), ("n_classes", C.c_int)]
+                ("cfsm_eps", C.c_double), ("n_classes", C.c_int),
+                ("min_component_voxels", C.c_int)]
 
 
 class _RunParams(C.Structure):
@@ -287,11 +308,12 @@ class DetectParams:
     cfsm_iter_max: int = 0
     cfsm_eps: float = 0.0
     n_classes: int = 4
+    min_component_voxels: int = 0
 
     def _c(self) -> _DetectParams:
         return _DetectParams(self.rc_min, self.rc_max, self.alpha, self.voxel,
                              self.smooth_order, self.kmeans_max_iter, self.cfsm_iter_max,
-                             self.cfsm_eps, self.n_classes)
+                             self.cfsm_eps, self.n_classes, self.min_component_voxels)
 
 
 @dataclass

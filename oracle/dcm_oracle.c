@@ -433,6 +433,131 @@ int orc_kmeans(int64_t nvox, const double *Bs, int max_iter, uint8_t *S,
     return it;
 }
 
+/* Section 4.2, Algorithm 4.1: connected-component labelling of one phase.
+ * The thesis gives the 2D row-major pass and says the 3D extension with
+ * periodic boundaries is direct; the reading here:
+ *   - connectivity: the 6 face neighbours (the thesis does not say);
+ *   - pass: z, then y, then x innermost (row-major, x fastest as in the
+ *     grid layout); a voxel of the phase looks at its already-visited face
+ *     neighbours inside the grid (-x, -y, -z; no wrap during the pass):
+ *     none labelled -> a new label; otherwise the smallest of their labels,
+ *     and all of their labels are marked equivalent;
+ *   - periodic boundaries: afterwards, every pair of voxels of the phase on
+ *     opposite faces (0 and n-1 along an axis) marks its labels equivalent;
+ *   - merge: equivalent labels are merged (union-find over the provisional
+ *     labels, linking the larger root under the smaller), and the merged
+ *     labels renumbered 0, 1, ... in order of first appearance in the pass.
+ * label[v] = component of v, or -1 for voxels of the other phase.  Returns
+ * the number of components. */
+static int64_t uf_find(int64_t *par, int64_t a)
+{
+    while (par[a] != a) a = par[a];
+    return a;
+}
+
+static void uf_union(int64_t *par, int64_t a, int64_t b)
+{
+    a = uf_find(par, a);
+    b = uf_find(par, b);
+    if (a == b) return;
+    if (a < b) par[b] = a;
+    else par[a] = b;
+}
+
+int64_t orc_label_components(const int dims[3], const uint8_t *S, int phase, int32_t *label)
+{
+    const int64_t nx = dims[0], ny = dims[1], nz = dims[2];
+    const int64_t nv = nx * ny * nz;
+    int64_t *prov = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nv > 0 ? nv : 1));
+    int64_t *par = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nv > 0 ? nv : 1));
+    int64_t next = 0;
+    for (int64_t z = 0; z < nz; ++z)
+        for (int64_t y = 0; y < ny; ++y)
+            for (int64_t x = 0; x < nx; ++x) {
+                const int64_t v = x + nx * (y + ny * z);
+                prov[v] = -1;
+                if (S[v] != phase) continue;
+                int64_t nb[3];
+                int m = 0;
+                if (x > 0 && S[v - 1] == phase) nb[m++] = prov[v - 1];
+                if (y > 0 && S[v - nx] == phase) nb[m++] = prov[v - nx];
+                if (z > 0 && S[v - nx * ny] == phase) nb[m++] = prov[v - nx * ny];
+                if (m == 0) {
+                    par[next] = next;
+                    prov[v] = next++;
+                } else {
+                    int64_t lo = nb[0];
+                    for (int q = 1; q < m; ++q)
+                        if (nb[q] < lo) lo = nb[q];
+                    prov[v] = lo;
+                    for (int q = 0; q < m; ++q) uf_union(par, lo, nb[q]);
+                }
+            }
+    /* periodic faces */
+    for (int64_t z = 0; z < nz; ++z)
+        for (int64_t y = 0; y < ny; ++y) {
+            const int64_t a = nx * (y + ny * z), b = a + nx - 1;
+            if (nx > 1 && S[a] == phase && S[b] == phase) uf_union(par, prov[a], prov[b]);
+        }
+    for (int64_t z = 0; z < nz; ++z)
+        for (int64_t x = 0; x < nx; ++x) {
+            const int64_t a = x + nx * ny * z, b = a + nx * (ny - 1);
+            if (ny > 1 && S[a] == phase && S[b] == phase) uf_union(par, prov[a], prov[b]);
+        }
+    for (int64_t y = 0; y < ny; ++y)
+        for (int64_t x = 0; x < nx; ++x) {
+            const int64_t a = x + nx * y, b = a + nx * ny * (nz - 1);
+            if (nz > 1 && S[a] == phase && S[b] == phase) uf_union(par, prov[a], prov[b]);
+        }
+    /* merge and renumber in order of first appearance */
+    int64_t *num = (int64_t *)malloc(sizeof(int64_t) * (size_t)(next > 0 ? next : 1));
+    for (int64_t l = 0; l < next; ++l) num[l] = -1;
+    int64_t ncomp = 0;
+    for (int64_t v = 0; v < nv; ++v) {
+        if (prov[v] < 0) {
+            label[v] = -1;
+            continue;
+        }
+        const int64_t r = uf_find(par, prov[v]);
+        if (num[r] < 0) num[r] = ncomp++;
+        label[v] = (int32_t)num[r];
+    }
+    free(num);
+    free(par);
+    free(prov);
+    return ncomp;
+}
+
+/* Section 4.2 (Fig. 20-21): removal of small connected components.  The
+ * outline removes the small components of the liquid phase and then those
+ * of the vapor phase; the reading here: the liquid components (s = 0) of
+ * fewer than min_voxels voxels become vapor, then the vapor components
+ * (s = 1) of the resulting grid with fewer than min_voxels voxels become
+ * liquid (the thesis's example removes every component smaller than 5).
+ * min_voxels <= 0: nothing changes.  Returns the number of voxels whose
+ * phase changed. */
+int64_t orc_remove_small_components(const int dims[3], uint8_t *S, int min_voxels)
+{
+    if (min_voxels <= 0) return 0;
+    const int64_t nv = (int64_t)dims[0] * dims[1] * dims[2];
+    int32_t *label = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nv > 0 ? nv : 1));
+    int64_t flipped = 0;
+    for (int phase = 0; phase <= 1; ++phase) {
+        const int64_t nc = orc_label_components(dims, S, phase, label);
+        int64_t *size = (int64_t *)calloc((size_t)(nc > 0 ? nc : 1), sizeof(int64_t));
+        for (int64_t v = 0; v < nv; ++v)
+            if (label[v] >= 0) size[label[v]]++;
+        for (int64_t v = 0; v < nv; ++v)
+            if (label[v] >= 0 && size[label[v]] < min_voxels) {
+                S[v] = (uint8_t)(1 - phase);
+                flipped++;
+            }
+        free(size);
+    }
+    free(label);
+    return flipped;
+}
+
 /* Eq. 16-18 generalised to three axes and per-axis spacing h_k: the
  * solution d of sum_k ((d - a_k)^+ / h_k)^2 = 1, found by growing the active
  * set in ascending a (ties broken by axis order). */
@@ -661,6 +786,7 @@ int orc_detect(int64_t n, const double *x, const double L[3],
     orc_density(n, x, L, dims, B);
     orc_smooth(dims, B, p->smooth_order, Bs);
     orc_kmeans(nv, Bs, p->kmeans_max_iter > 0 ? p->kmeans_max_iter : 100, S, NULL, NULL);
+    orc_remove_small_components(dims, S, p->min_component_voxels);
     double h[3] = {L[0] / dims[0], L[1] / dims[1], L[2] / dims[2]};
     double hmax = h[0];
     if (h[1] > hmax) hmax = h[1];

@@ -113,6 +113,17 @@ void orc_smooth(const int dims[3], const int32_t *B, int order, double *Bs);
 int orc_kmeans(int64_t nvox, const double *Bs, int max_iter, uint8_t *S,
                double *c_l, double *c_v);
 
+/* ---- Section 4.2, Algorithm 4.1: small connected components ------------------
+ * orc_label_components: components of the voxels with S == phase, face
+ * (6-) connectivity across the periodic faces, by the row-major two-pass
+ * labelling of Algorithm 4.1; label[v] = 0, 1, ... in order of first
+ * appearance (x fastest), -1 for the other phase.  Returns the count.
+ * orc_remove_small_components: liquid components of fewer than min_voxels
+ * voxels become vapor, then vapor components (of that result) of fewer than
+ * min_voxels become liquid; <= 0: none.  Returns the voxels changed. */
+int64_t orc_label_components(const int dims[3], const uint8_t *S, int phase, int32_t *label);
+int64_t orc_remove_small_components(const int dims[3], uint8_t *S, int min_voxels);
+
 /* ---- Eq. 15-19: Godunov upwind local solve ------------------------------------
  * Returns the Eq. 19 candidate dbar for a voxel whose per-axis neighbour
  * minima are a[3] (Eq. 17) with spacings h[3]; +inf if all a are +inf. */
@@ -137,7 +148,8 @@ void orc_particle_distance(int64_t n, const double *x, const double L[3],
                            const int dims[3], const double *D, double *d);
 
 /* ---- full interface detection (Fig. 14 order) ---------------------------------
- * density -> smoothing -> K-means labels -> CFSM distance (cap r_grid =
+ * density -> smoothing -> K-means labels -> [small-component removal, when
+ * min_component_voxels > 0] -> CFSM distance (cap r_grid =
  * rc_max + max h) -> particle distance -> cutoff (Eq. 7) -> class.  All
  * output arrays are nullable except d/rc/cls.  Returns CFSM passes (or -1). */
 typedef struct {
@@ -148,6 +160,7 @@ typedef struct {
     int cfsm_iter_max; /* <= 0: 4 * max(dims) */
     double cfsm_eps;
     int n_classes;
+    int min_component_voxels; /* Section 4.2; <= 0: no removal */
 } orc_detect_params;
 
 int orc_detect(int64_t n, const double *x, const double L[3],
