@@ -92,14 +92,17 @@ typedef struct {
        displacement since the build plus the largest displacement reaches
        its headroom R_i - r_c[i](t), or when the list storage would
        overflow (that step falls back to the direct walk).  Requires at most
-       2^24 particles per handle and a stencil of at most 7 cells in y and
-       z. */
+       2^24 particles per handle, a stencil of at most 7 cells in y and z,
+       and list storage (n x min((4/3) pi (r_c,max + skin)^3,
+       4 pi (r_c,min + skin)^3) entries) below 2^31 entries; dcm_create
+       returns DCM_ERR_ARG otherwise. */
     double skin;
     /* Verlet lists built by the warp walk (DCM_MIXED, DCM_WALK_WARP): each
-       particle's entry capacity is list_density x (4/3) pi R^3 + 8 for its
-       list radius R; <= 0: 1.0 per sigma^3.  A list that would overflow
-       leaves that step's forces to the direct walk and raises the density
-       by 25 % for the next build (per handle: system 0's value). */
+       particle's entry capacity is list_density x (4/3) pi R^3 + 8,
+       rounded up to a multiple of 8, for its list radius R; <= 0: 1.0 per
+       sigma^3.  A list that would overflow leaves that step's forces to the
+       direct walk and raises the density by 25 % for the next build (per
+       handle: system 0's value). */
     float list_density;
     /* With detected cutoffs, each list radius is the cutoff the particle
        would get if its interface distance fell by list_margin sigma, plus

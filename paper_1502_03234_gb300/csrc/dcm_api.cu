@@ -435,6 +435,11 @@ static int create_systems(int M, const dcm_box *boxes, const int64_t *ns, const 
             dcm_destroy(h);
             return fail(DCM_ERR_ARG, "Verlet lists hold at most 2^24 particles per handle");
         }
+        if (cap > 0x7fffffffLL) {
+            dcm_destroy(h);
+            return fail(DCM_ERR_ARG, "Verlet lists need %lld entries, above the 2^31 a handle "
+                                     "can index: fewer particles or a smaller skin", (long long)cap);
+        }
         h->nl_cap = cap;
         ALLOC(h->nl, cap);
         ALLOC(h->nl_cnt, N);

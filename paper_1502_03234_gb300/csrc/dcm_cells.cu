@@ -155,9 +155,13 @@ __global__ void k_gather(Batch b, const double *__restrict__ x, const double *__
         int w = 0;
         if (capk && lf[LF_REBUILD]) {
             // a Verlet-list build follows: the skin share (from the
-            // particle's speed and force) and own list radius of this particle, and its entry capacity, (4/3) pi R^3
-            // for R = own radius + the largest share at the density bound
-            // scale (1.0 sigma^-3 unless a list overflowed before) + 8
+            // particle's speed and force) and own list radius of this
+            // particle, and its entry capacity, (4/3) pi R^3 for R = own
+            // radius + the largest share at the density bound scale (1.0
+            // sigma^-3 unless a list overflowed before) + 8, rounded up to
+            // 8 entries so that every list starts on a 32-byte sector (the
+            // force kernel's 8-lane loads then touch one sector each) and
+            // capped so that the int32 offset scan cannot wrap
             const size_t N = (size_t)b.N;
             const float vx = (float)v[i], vy = (float)v[N + i], vz = (float)v[2 * N + i];
             const float fx = (float)f[i], fy = (float)f[N + i], fz = (float)f[2 * N + i];
@@ -166,7 +170,8 @@ __global__ void k_gather(Batch b, const double *__restrict__ x, const double *__
             const float rl = list_radius(g, r, dist[i], delta, share);
             const float R = rl + 0.5f * (float)g.skin;
             float scale = __int_as_float(lf[LF_SCALE]);
-            capk[k] = (int32_t)ceilf(scale * 4.18879020f * R * R * R) + 8;
+            const float capmax = (float)((int32_t)((0x7fffffffLL - 1024) / b.N) & ~7);
+            capk[k] = (int32_t)fminf(ceilf(scale * 4.18879020f * R * R * R) + 15.0f, capmax) & ~7;
             w = __float_as_int(rl);
             sh[k] = share;
             // non-negative floats order like their bit patterns; one

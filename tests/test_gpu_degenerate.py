@@ -103,3 +103,14 @@ def test_skin_share_parameters(dcm):
         dcm.System(s.box, len(s.x), precision=1, skin=0.4, skin_time=-1.0)
     assert e.value.code == dcm.DCM_ERR_ARG
 
+
+
+def test_list_storage_above_int32_offsets_is_rejected(dcm):
+    # list offsets are int32: storage for n x min((4/3) pi (6 + 0.7)^3,
+    # 4 pi (3 + 0.7)^3) = 637 n entries passes 2^31 at n = 3.38 M
+    n = 3_400_000
+    L = (n / 0.32 / 4.0) ** (1.0 / 3.0)          # slab-shaped box, mean density 0.32
+    with pytest.raises(dcm.DcmError) as e:
+        dcm.System((L, L, 4.0 * L), n, precision=1, skin=0.7)
+    assert e.value.code == dcm.DCM_ERR_ARG
+    assert "2^31" in str(e.value)
