@@ -98,6 +98,9 @@ def parse():
                     help="adaptive skin shares: share = clamp(skin_time |v| + skin_time^2 |F| / 2m, "
                          "skin_floor, skin/2); 0: skin/2 for every particle")
     ap.add_argument("--skin-floor", type=float, default=0.07)
+    ap.add_argument("--min-component", type=int, default=0,
+                    help="small-component removal (Section 4.2): components of either phase "
+                         "below this many voxels change phase; 0: off")
     ap.add_argument("--list-margin", type=float, default=1.0,
                     help="interface-distance margin of the Verlet-list radius in sigma")
     ap.add_argument("--workload", default="slab", choices=["slab", "wavy", "ensemble", "serving"])
@@ -189,7 +192,8 @@ class Clocks:
 
 
 # ---- reference arm: the FP64 CPU oracle ----------------------------------------------
-def oracle_rate(n_sample: int, target_s: float, max_steps: int = 2000, seed: int = 1):
+def oracle_rate(n_sample: int, target_s: float, max_steps: int = 2000, seed: int = 1,
+                min_component: int = 0):
     """atom-steps/s of the FP64 oracle (all host cores) on an n_sample slab
     with the same densities, cutoffs and cadence."""
     import oracle
@@ -198,7 +202,8 @@ def oracle_rate(n_sample: int, target_s: float, max_steps: int = 2000, seed: int
     cores = os.cpu_count() or 1
     oracle.set_threads(cores)
     s = slabgen.make_slab(n_sample, seed=seed)
-    p = oracle.RunParams(det=oracle.DetectParams(rc_min=3.0, rc_max=6.0, voxel=1.0),
+    p = oracle.RunParams(det=oracle.DetectParams(rc_min=3.0, rc_max=6.0, voxel=1.0,
+                                                 min_component_voxels=min_component),
                          dt=0.005, cell_min=1.5, detect_every=2)
     t0 = time.perf_counter()
     oracle.run(s.x, s.v, s.box, p, 2)                  # setup + 2 steps: calibration
@@ -221,7 +226,8 @@ def run_reference(args):
     oracle.set_threads(cores)
     n_sample = 16384
     s = slabgen.make_slab(n_sample, seed=1)
-    p = oracle.RunParams(det=oracle.DetectParams(rc_min=3.0, rc_max=6.0, voxel=1.0),
+    p = oracle.RunParams(det=oracle.DetectParams(rc_min=3.0, rc_max=6.0, voxel=1.0,
+                                                 min_component_voxels=args.min_component),
                          dt=0.005, cell_min=1.5, detect_every=2)
     x, v = s.x, s.v
     if args.warmup > 0:
@@ -476,7 +482,8 @@ def main():
     def make_system(precision):
         sy = dcm.System(slab.box, n, precision=precision, stream=stream.cuda_stream,
                         skin=args.skin, list_margin=args.list_margin, skin_time=args.skin_time,
-                        skin_floor=args.skin_floor, cell_min=args.cell_min)
+                        skin_floor=args.skin_floor, cell_min=args.cell_min,
+                        min_component_voxels=args.min_component)
         if args.list_lanes:
             t = dcm.dcm_get_tuning(sy.h)
             sy.set_tuning(list(t.lanes), t.block, t.walk, args.list_lanes)
@@ -646,7 +653,8 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        rate, cores, csteps, cdt = oracle_rate(16384, target_s=12.0)
+        rate, cores, csteps, cdt = oracle_rate(16384, target_s=12.0,
+                                               min_component=args.min_component)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"N=16384 slab of the same shape, {csteps} oracle steps "
                          f"({cdt:.1f} s) after a 2-step calibration"}
@@ -661,6 +669,7 @@ def main():
         cfg["cell_min"] = args.cell_min
         cfg["skin_time"] = args.skin_time
         cfg["skin_floor"] = args.skin_floor
+        cfg["min_component_voxels"] = args.min_component
         cfg["phase_ms_avg"] = {k: v / phase_steps for k, v in phase_sum.items()}
         cfg["phase_note"] = ("per-phase CUDA events inside the step graph, on a second run of the "
                              "same steps from the same start (the timed run records none)")

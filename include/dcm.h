@@ -121,7 +121,13 @@ typedef struct {
        pair's skin.  skin_time = 0: uniform shares. */
     float skin_time;
     float skin_floor;
-    int32_t reserved[2];
+    /* Section 4.2 (Fig. 20-21): after the segmentation, liquid components
+       of fewer than this many voxels become vapor, then vapor components
+       (of that result) of fewer than this many become liquid, before the
+       distance pass.  Components are 6-connected across the periodic
+       faces.  0 (default): no removal.  Per system. */
+    int32_t min_component_voxels;
+    int32_t reserved[1];
 } dcm_params;
 
 /* Force walk variants (dcm_tuning.walk).  DCM_WALK_WARP: one warp per
@@ -171,7 +177,9 @@ typedef struct {
                                               Verlet lists (= kernels_plain
                                               without lists) */
     int32_t kernels_detect_reuse;          /* ... in a step with detection */
-    int64_t reserved[2];
+    int64_t cc_flipped;                    /* voxels the small-component removal
+                                              changed in the last detection */
+    int64_t reserved[1];
 } dcm_stats;
 
 /* Phases of one step, in order, for dcm_get_phase_times. */
@@ -269,6 +277,20 @@ int dcm_ensemble_get_state(dcm_handle *h, int k, double *x, double *v, double *f
                            int mem);
 int dcm_ensemble_energy_virial(dcm_handle *h, int k, double *pe, double *ke,
                                double w[6]);
+
+/* Section 4.2 on a caller's label grid (diagnostics and tests): labels is
+ * system 0's voxel grid in the layout of dcm_get_grid (x fastest; 0 liquid,
+ * 1 vapor; other values belong to neither phase and stay), host or device
+ * (mem), rewritten in place with the liquid components of fewer than
+ * min_voxels voxels made vapor and then the vapor components of fewer than
+ * min_voxels made liquid (min_voxels 0: unchanged).  flipped (nullable)
+ * receives the voxels changed.  Uses the handle's stream and synchronises;
+ * allocates the component forests on first use when the handle was created
+ * without min_component_voxels.  The handle's own labels are untouched.
+ * Errors: DCM_ERR_ARG, DCM_ERR_STATE (during stream capture), DCM_ERR_OOM,
+ * DCM_ERR_CUDA, DCM_ERR_DEVICE_CHECK (a union ran out of attempts). */
+int dcm_remove_small_components(dcm_handle *h, uint8_t *labels, int32_t min_voxels, int mem,
+                                int64_t *flipped);
 
 /* Waits for the handle's stream; returns the sticky device error, if any. */
 int dcm_sync(dcm_handle *h);

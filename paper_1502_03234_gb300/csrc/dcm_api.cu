@@ -117,6 +117,7 @@ static int check_params(const dcm_box *box, int64_t n, const dcm_params *p)
     if (!(p->skin_time >= 0.f) || !(p->skin_floor >= 0.f) ||
         (p->skin > 0 && p->skin_time > 0.f && p->skin_floor > 0.5 * p->skin))
         return fail(DCM_ERR_ARG, "skin_time, skin_floor must be >= 0, skin_floor <= skin/2");
+    if (p->min_component_voxels < 0) return fail(DCM_ERR_ARG, "min_component_voxels must be >= 0");
     return DCM_OK;
 }
 
@@ -188,6 +189,7 @@ static int setup_geometry(const dcm_box *box, int64_t n, const dcm_params *p, Ge
     g.skin = p->skin > 0 ? p->skin : 0.0;
     g.skin_time = p->skin_time;
     g.skin_floor = p->skin_floor;
+    g.cc_min = p->min_component_voxels;
     g.eps24 = 24.0 * p->eps;
     g.eps48 = 48.0 * p->eps;
     g.eps2 = 2.0 * p->eps;
@@ -214,13 +216,37 @@ static int64_t list_cap(const Geom &g, int64_t n)
     return n * (int64_t)ceil(big < small ? big : small) + 1024;
 }
 
+// the small-component buffers (5 ints per voxel) and the systems' tile
+// offsets, on creation with min_component_voxels or on first use
+template <typename T>
+static int dalloc(dcm_handle *h, T **ptr, int64_t count);
+
+static int cc_setup(dcm_handle *h)
+{
+    if (h->cc) return DCM_OK;
+    if (h->b.NV > 0x7fffffffLL) return fail(DCM_ERR_ARG, "small-component removal indexes at most 2^31 voxels");
+    std::vector<int64_t> off(h->M + 1, 0);
+    for (int k = 0; k < h->M; ++k) {
+        const Geom &g = h->geo_host[k];
+        off[k + 1] = off[k] + (int64_t)((g.gd[0] + 7) / 8) * ((g.gd[1] + 7) / 8) * ((g.gd[2] + 7) / 8);
+    }
+    int rc;
+    if ((rc = dalloc(h, &h->cc, 5 * h->b.NV))) return rc;
+    if ((rc = dalloc(h, &h->cc_tiles, (int64_t)h->M + 1))) return rc;
+    DCM_CHECK_CUDA(cudaMemcpy(h->cc_tiles, off.data(), sizeof(int64_t) * (h->M + 1),
+                              cudaMemcpyHostToDevice));
+    h->cc_ntiles = off[h->M];
+    h->cc_ntiles0 = off[1];
+    return DCM_OK;
+}
+
 static int64_t bytes_for(const Geom &g, int64_t n, int precision)
 {
     int64_t ncell = g.ncell;
     int64_t nv = g.nvox;
     int64_t per_p = 3 * 8 * 3 + 8 + 8 + 1 + 4 * 3 + 16 + 4 + 4 + 8 + 48 + 24 + 2;
     per_p += 36;   // spd (FP64) or rq + pk + inv (MIXED)
-    int64_t per_v = 4 + 4 + 4 + 8 + 1 + 8 + 8 + 4 + 16 + 2;
+    int64_t per_v = 4 + 4 + 4 + 8 + 1 + 8 + 8 + 4 + 16 + 2 + (g.cc_min > 0 ? 20 : 0);
     int64_t ntiles = (ncell + 2047) / 2048 + 1;
     int64_t lists = g.skin > 0 ? 4 * list_cap(g, n) + n * (4 + 4 + 24 + 8 + 8 + 20) : 0;
     return n * per_p + ncell * 8 + 8 + nv * per_v + ntiles * 4 + 4096 + 256 * 8 * 8 + lists;
@@ -261,7 +287,7 @@ extern "C" int dcm_destroy(dcm_handle *h)
                     h->flist, h->fcount, h->kacc, h->npair, h->pe, h->vir, h->red_part, h->red_out,
                     h->err, h->stats, h->tmp3n, h->geo_dev, h->off_dev, h->nl, h->nl_cnt,
                     h->nl_start, h->nl_tiles, h->x_ref, h->rl_ref, h->sh_ref, h->sh, h->u_ref,
-                    h->disp, h->corner, h->lflags};
+                    h->disp, h->corner, h->lflags, h->cc, h->cc_tiles};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -409,6 +435,7 @@ static int create_systems(int M, const dcm_box *boxes, const int64_t *ns, const 
     ALLOC(h->D1, nv);
     ALLOC(h->stamp, nv);
     ALLOC(h->flist, 4 * nv);
+    for (int k = 0; k < M; ++k) h->cc_on = h->cc_on || h->geo_host[k].cc_min > 0;
     ALLOC(h->fcount, 4);
     ALLOC(h->kacc, 9 * 16 * (int64_t)M);   // K-means sums, 16 spread slots each
     ALLOC(h->npair, N);
@@ -466,6 +493,10 @@ static int create_systems(int M, const dcm_box *boxes, const int64_t *ns, const 
     h->b.N = N;
     h->b.NC = nc;
     h->b.NV = nv;
+    if (h->cc_on && (rc = cc_setup(h))) {       // small-component buffers (Section 4.2)
+        dcm_destroy(h);
+        return rc;
+    }
     cudaMemcpyAsync(h->geo_dev, h->geo_host, sizeof(Geom) * M, cudaMemcpyHostToDevice, h->stream);
     cudaMemcpyAsync(h->corner, h->corner_host, sizeof(double) * ncorner, cudaMemcpyHostToDevice,
                     h->stream);
@@ -994,6 +1025,41 @@ extern "C" int dcm_get_grid(dcm_handle *h, int32_t dims[3], int32_t *counts, dou
     return DCM_OK;
 }
 
+extern "C" int dcm_remove_small_components(dcm_handle *h, uint8_t *labels, int32_t min_voxels,
+                                           int mem, int64_t *flipped)
+{
+    if (!h || !labels) return fail(DCM_ERR_ARG, "null handle or labels");
+    if (min_voxels < 0) return fail(DCM_ERR_ARG, "min_voxels must be >= 0");
+    if (mem != DCM_HOST && mem != DCM_DEVICE) return fail(DCM_ERR_ARG, "mem must be DCM_HOST or DCM_DEVICE");
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    DCM_CHECK_CUDA(cudaStreamIsCapturing(h->stream, &cap));
+    if (cap != cudaStreamCaptureStatusNone) return fail(DCM_ERR_STATE, "not callable during stream capture");
+    const int64_t nv = h->g.nvox;   // system 0 (its voxels come first)
+    int rc;
+    if ((rc = cc_setup(h))) return rc;
+    uint8_t *S = nullptr;
+    if ((rc = dalloc(h, &S, nv))) return rc;
+    cudaMemcpyKind in = mem == DCM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    cudaMemcpyKind out = mem == DCM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    cudaError_t e = cudaMemcpyAsync(S, labels, (size_t)nv, in, h->stream);
+    Batch b0 = h->b;              // system 0 alone
+    b0.M = 1;
+    b0.NV = nv;
+    b0.vsys = nullptr;
+    if (e == cudaSuccess) rc = launch_components(h, b0, S, min_voxels, h->cc_ntiles0);
+    if (e == cudaSuccess && rc == DCM_OK) e = cudaMemcpyAsync(labels, S, (size_t)nv, out, h->stream);
+    DevStats st;
+    if (e == cudaSuccess && rc == DCM_OK)
+        e = cudaMemcpyAsync(&st, h->stats, sizeof(st), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(S);
+    h->bytes -= nv > 0 ? nv : 1;
+    if (e != cudaSuccess) return fail_cuda(e, "small-component removal", __FILE__, __LINE__);
+    if (rc) return rc;
+    if (flipped) *flipped = (int64_t)st.cc_flipped;
+    return dcm_sync(h);
+}
+
 extern "C" int dcm_get_cutoffs(dcm_handle *h, double *d, double *rc, uint8_t *cls)
 {
     if (!h) return fail(DCM_ERR_ARG, "null handle");
@@ -1060,6 +1126,7 @@ extern "C" int dcm_get_stats(dcm_handle *h, dcm_stats *s)
     s->kernels_detect_reuse = h->kernels_detect_reuse;
     s->list_builds = (int64_t)st.list_builds;
     s->list_entries = (int64_t)st.list_entries;
+    s->cc_flipped = (int64_t)st.cc_flipped;
     return DCM_OK;
 }
 
@@ -1107,7 +1174,8 @@ extern "C" int dcm_sync(dcm_handle *h)
     if (err & DEV_ERR_CFSM_CAP)
         return fail(DCM_ERR_NOT_CONVERGED, "CFSM reached its iteration cap (device flags 0x%x)", err);
     return fail(DCM_ERR_DEVICE_CHECK, "device check failed (flags 0x%x: 1 non-finite, 2 jump, "
-                                      "4 barrier timeout, 16 density, 64 bounds)", err);
+                                      "4 barrier timeout, 16 density, 64 bounds, 128 union)",
+                err);
 }
 
 extern "C" int64_t dcm_device_bytes(const dcm_handle *h) { return h ? h->bytes : 0; }

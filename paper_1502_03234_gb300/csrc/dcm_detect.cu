@@ -13,6 +13,7 @@
 //             bit-identical to the definition.  Liquid sets of successive
 //             iterations are threshold sets, hence nested: equal counts
 //             mean an unchanged assignment (the stopping rule).
+//   small components (Section 4.2, optional): dcm_components.cu
 //   CFSM      Algorithm 4.3 as a Jacobi fixed point over a frontier: each
 //             pass recomputes only the voxels whose neighbours changed in
 //             the previous pass, writes the other buffer, and stops when
@@ -1048,6 +1049,11 @@ int launch_detect(dcm_handle *h)
             if (grid > need) grid = (int)(need > 0 ? need : 1);
             rc = coop_launch(h, (const void *)k_kmeans, grid, smem, args);
         }
+        if (rc) return rc;
+    }
+    // Section 4.2: small components of either phase change phase
+    if (h->cc_on) {
+        int rc = launch_components(h, b, h->S, -1, h->cc_ntiles);
         if (rc) return rc;
     }
     // CFSM (frontier counters zeroed by k_detect_init, barrier words by k_cfsm_init)

@@ -44,7 +44,8 @@ enum : int {
     DEV_ERR_CFSM_CAP = 8,        // CFSM hit iter_max
     DEV_ERR_DENSITY = 16,        // voxel count too large for exact smoothing
     DEV_ERR_CANCEL = 32,         // cancel flag observed
-    DEV_ERR_BOUNDS = 64          // an index check failed
+    DEV_ERR_BOUNDS = 64,         // an index check failed
+    DEV_ERR_UNION = 128          // a component union ran out of attempts
 };
 
 // counters written by device code, read back for dcm_get_stats
@@ -60,6 +61,7 @@ struct DevStats {
                                  // [4] first CFSM pass of the cluster tail, [5] list-force queue
     unsigned long long list_builds;
     unsigned long long list_entries;
+    unsigned long long cc_flipped;   // voxels the small-component removal changed (last detection)
 };
 
 // Verlet-list control words (device): see dcm_list.cu
@@ -99,6 +101,7 @@ struct Geom {
     int64_t corner_off;          // this system's cell corner coordinates in Batch::corner
     float halfLf[3];             // FP32 half edges
     float skin_time, skin_floor; // velocity-adaptive skin shares (skin_time 0: skin/2 each)
+    int cc_min;                  // Section 4.2: components below this many voxels change phase (0: off)
     double eps24, eps48, eps2, sig2;     // LJ force/energy constants
     float eps24f, eps48f, eps2f, sig2f;
     // this system's slices of the concatenated arrays
@@ -187,6 +190,10 @@ struct dcm_handle {
     int32_t *stamp;
     int32_t *flist;              // 4 * nvox
     int32_t *fcount;             // 4 counters
+    int32_t *cc;                 // small components: parent and count of each phase, local sizes (5 * nvox)
+    int64_t *cc_tiles;           // [M+1] offsets of the systems' 8^3 tiles (device)
+    int64_t cc_ntiles, cc_ntiles0;   // tiles of all systems / of system 0
+    bool cc_on;                  // some system removes small components
     // Verlet lists (skin > 0), indexed by sorted slot of the last build
     int32_t *nl;                 // entries: j | (dy+8) << 24 | (dz+8) << 28
     int64_t nl_cap;
@@ -265,6 +272,9 @@ int launch_forces(dcm_handle *h, bool energy);   // list mode when skin > 0 and 
 // its step)
 int launch_list_forces(dcm_handle *h, bool energy, int part);
 int launch_detect(dcm_handle *h);
+// Section 4.2 on labels S of the systems in b (thr >= 0 overrides every
+// system's min_component_voxels); tiles: their 8^3 tiles
+int launch_components(dcm_handle *h, const Batch &b, uint8_t *S, int thr, int64_t tiles);
 int launch_reduce_energy(dcm_handle *h, int k);
 int launch_reduce_pairs(dcm_handle *h);
 int launch_classify_rc(dcm_handle *h);   // classes from supplied rc

@@ -34,6 +34,7 @@ EXPORTS = [
     "dcm_set_timing", "dcm_get_phase_times", "dcm_ensemble_create", "dcm_system_count",
     "dcm_system_range", "dcm_ensemble_set_state", "dcm_ensemble_get_state",
     "dcm_ensemble_energy_virial", "dcm_check_bounded_wait", "dcm_cell_sort_noalloc",
+    "dcm_remove_small_components",
 ]
 DCM_NUM_PHASES = 5
 PHASES = ("kick_drift", "detect", "bin", "force", "kick")
@@ -58,7 +59,8 @@ class dcm_params(C.Structure):
                 ("precision", C.c_int32), ("n_classes", C.c_int32), ("cell_min", C.c_double),
                 ("skin", C.c_double), ("list_density", C.c_float),
                 ("list_margin", C.c_float), ("skin_time", C.c_float),
-                ("skin_floor", C.c_float), ("reserved", C.c_int32 * 2)]
+                ("skin_floor", C.c_float), ("min_component_voxels", C.c_int32),
+                ("reserved", C.c_int32 * 1)]
 
 
 class dcm_tuning(C.Structure):
@@ -75,7 +77,7 @@ class dcm_stats(C.Structure):
                 ("kernels_plain", C.c_int32), ("kernels_detect", C.c_int32),
                 ("list_builds", C.c_int64), ("list_entries", C.c_int64),
                 ("kernels_plain_reuse", C.c_int32), ("kernels_detect_reuse", C.c_int32),
-                ("reserved", C.c_int64 * 2)]
+                ("cc_flipped", C.c_int64), ("reserved", C.c_int64 * 1)]
 
 
 _lib = None
@@ -104,6 +106,7 @@ def lib() -> C.CDLL:
         "dcm_step": (C.c_int, [vp, i64]),
         "dcm_energy_virial": (C.c_int, [vp, dp, dp, dp]),
         "dcm_get_grid": (C.c_int, [vp, dp, dp, dp, dp, dp]),
+        "dcm_remove_small_components": (C.c_int, [vp, dp, i32, C.c_int, P(i64)]),
         "dcm_get_cutoffs": (C.c_int, [vp, dp, dp, dp]),
         "dcm_get_cells": (C.c_int, [vp, dp, dp, dp]),
         "dcm_get_pair_counts": (C.c_int, [vp, dp]),
@@ -228,6 +231,26 @@ def dcm_get_grid(h):
     check(lib().dcm_get_grid(h, _ptr(dims)[0], _ptr(counts)[0], _ptr(sm)[0], _ptr(lab)[0],
                              _ptr(dist)[0]))
     return tuple(int(q) for q in dims), counts, sm, lab, dist
+
+
+def dcm_remove_small_components(h, labels, min_voxels: int):
+    """Section 4.2 on a label grid of system 0 (numpy uint8, or a CUDA
+    tensor rewritten in place); returns (labels, voxels changed)."""
+    dims = np.zeros(3, np.int32)
+    check(lib().dcm_get_grid(h, _ptr(dims)[0], None, None, None, None))
+    if not (hasattr(labels, "data_ptr") and getattr(labels, "is_cuda", False)):
+        labels = np.array(np.ascontiguousarray(labels, dtype=np.uint8).ravel())
+        size = labels.size
+    else:
+        if labels.dtype.itemsize != 1 or not labels.is_contiguous():
+            raise ValueError("labels must be a contiguous uint8 tensor")
+        size = labels.numel()
+    if size != int(np.prod(dims)):
+        raise ValueError(f"labels hold {size} voxels, the grid {int(np.prod(dims))}")
+    p, mem = _ptr(labels)
+    fl = C.c_int64(0)
+    check(lib().dcm_remove_small_components(h, p, int(min_voxels), mem, C.byref(fl)))
+    return labels, int(fl.value)
 
 
 def dcm_get_cutoffs(h, n: int):
@@ -411,6 +434,9 @@ class System:
 
     def grid(self):
         return dcm_get_grid(self.h)
+
+    def remove_small_components(self, labels, min_voxels: int):
+        return dcm_remove_small_components(self.h, labels, min_voxels)
 
     def cutoffs(self):
         return dcm_get_cutoffs(self.h, self.n)
