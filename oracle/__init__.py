@@ -53,6 +53,8 @@ def _load():
         "orc_cutoff": (d, [d, d, d, d]),
         "orc_class_thresholds": (None, [d, d, d, C.c_int, vp]),
         "orc_cutoff_class": (C.c_int, [d, d, C.c_int, vp]),
+        "orc_cutoff_linear": (d, [d, d, d]),
+        "orc_class_thresholds_linear": (None, [d, d, C.c_int, vp]),
         "orc_grid_dims": (None, [vp, d, vp]),
         "orc_cell_dims": (None, [vp, d, vp]),
         "orc_bin_index": (C.c_int, [d, C.c_int, d]),
@@ -117,6 +119,16 @@ def cutoff(d: float, rc_min: float, rc_max: float, alpha: float = -0.5) -> float
 def class_thresholds(rc_min, rc_max, alpha, K) -> np.ndarray:
     thr = np.zeros(max(K - 2, 1), np.float64)
     _load().orc_class_thresholds(float(rc_min), float(rc_max), float(alpha), int(K), _p(thr))
+    return thr[: max(K - 2, 0)]
+
+
+def cutoff_linear(d: float, rc_min: float, rc_max: float) -> float:
+    return _load().orc_cutoff_linear(float(d), float(rc_min), float(rc_max))
+
+
+def class_thresholds_linear(rc_min, rc_max, K) -> np.ndarray:
+    thr = np.zeros(max(K - 2, 1), np.float64)
+    _load().orc_class_thresholds_linear(float(rc_min), float(rc_max), int(K), _p(thr))
     return thr[: max(K - 2, 0)]
 
 
@@ -288,7 +300,7 @@ class _DetectParams(C.Structure):
                 ("voxel", C.c_double), ("smooth_order", C.c_int),
                 ("kmeans_max_iter", C.c_int), ("cfsm_iter_max", C.c_int),
                 ("cfsm_eps", C.c_double), ("n_classes", C.c_int),
-                ("min_component_voxels", C.c_int)]
+                ("min_component_voxels", C.c_int), ("cutoff_fn", C.c_int)]
 
 
 class _RunParams(C.Structure):
@@ -309,11 +321,13 @@ class DetectParams:
     cfsm_eps: float = 0.0
     n_classes: int = 4
     min_component_voxels: int = 0
+    cutoff_fn: int = 0
 
     def _c(self) -> _DetectParams:
         return _DetectParams(self.rc_min, self.rc_max, self.alpha, self.voxel,
                              self.smooth_order, self.kmeans_max_iter, self.cfsm_iter_max,
-                             self.cfsm_eps, self.n_classes, self.min_component_voxels)
+                             self.cfsm_eps, self.n_classes, self.min_component_voxels,
+                             self.cutoff_fn)
 
 
 @dataclass

@@ -71,6 +71,26 @@ void orc_class_thresholds(double rc_min, double rc_max, double alpha, int K,
     }
 }
 
+/* Section 3.1, Fig. 12: the "linear" cutoff function, read as the straight
+ * line from (0, rc_max) to (rc_max, rc_min), with the same outer cases as
+ * Eq. 7 */
+double orc_cutoff_linear(double d, double rc_min, double rc_max)
+{
+    if (d <= 0.0) return rc_max;
+    if (d >= rc_max) return rc_min;
+    return rc_max - (rc_max - rc_min) * d / rc_max;
+}
+
+/* class edges of the linear function: d(r_k) = (rc_max - r_k) rc_max / (rc_max - rc_min) */
+void orc_class_thresholds_linear(double rc_min, double rc_max, int K, double *thr)
+{
+    if (K < 3) return;
+    for (int k = 1; k <= K - 2; ++k) {
+        double r = rc_min + (rc_max - rc_min) * (double)k / (double)(K - 1);
+        thr[k - 1] = (rc_max - r) * rc_max / (rc_max - rc_min);
+    }
+}
+
 int orc_cutoff_class(double d, double rc_max, int K, const double *thr)
 {
     if (d >= rc_max) return 0;
@@ -800,9 +820,14 @@ int orc_detect(int64_t n, const double *x, const double L[3],
     orc_particle_distance(n, x, L, dims, D, d);
     int K = p->n_classes < 2 ? 2 : p->n_classes;
     double thr[16];
-    orc_class_thresholds(p->rc_min, p->rc_max, p->alpha, K, thr);
+    const int lin = p->cutoff_fn == 1 && p->rc_max > p->rc_min;
+    if (lin)
+        orc_class_thresholds_linear(p->rc_min, p->rc_max, K, thr);
+    else
+        orc_class_thresholds(p->rc_min, p->rc_max, p->alpha, K, thr);
     for (int64_t i = 0; i < n; ++i) {
-        rc[i] = orc_cutoff(d[i], p->rc_min, p->rc_max, p->alpha);
+        rc[i] = lin ? orc_cutoff_linear(d[i], p->rc_min, p->rc_max)
+                    : orc_cutoff(d[i], p->rc_min, p->rc_max, p->alpha);
         if (cls) cls[i] = (uint8_t)orc_cutoff_class(d[i], p->rc_max, K, thr);
     }
     if (dims_out) memcpy(dims_out, dims, sizeof(dims));

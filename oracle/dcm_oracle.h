@@ -60,6 +60,14 @@ void orc_class_thresholds(double rc_min, double rc_max, double alpha, int K,
                           double *thr /* K-2 entries */);
 int orc_cutoff_class(double d, double rc_max, int K, const double *thr);
 
+/* ---- Section 3.1, Fig. 12: linear cutoff function -------------------------
+ * r_c(d) = rc_max for d <= 0; rc_max - (rc_max-rc_min) d / rc_max for
+ * 0 < d < rc_max; rc_min for d >= rc_max (a reading of the figure: the
+ * thesis draws it and gives no formula).  Class edges as above, from
+ * inverting this line. */
+double orc_cutoff_linear(double d, double rc_min, double rc_max);
+void orc_class_thresholds_linear(double rc_min, double rc_max, int K, double *thr);
+
 /* ---- bins ---------------------------------------------------------------*/
 /* Eq. 10 with the reading N_x = max(3, floor(L_x / b)). */
 void orc_grid_dims(const double L[3], double b, int dims[3]);
@@ -161,6 +169,7 @@ typedef struct {
     double cfsm_eps;
     int n_classes;
     int min_component_voxels; /* Section 4.2; <= 0: no removal */
+    int cutoff_fn;            /* 0: exponential (Eq. 7), 1: linear (Fig. 12) */
 } orc_detect_params;
 
 int orc_detect(int64_t n, const double *x, const double L[3],

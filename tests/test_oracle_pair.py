@@ -108,6 +108,62 @@ def test_cutoff_classes(orc):
         assert lo - 1e-9 <= r <= hi + 1e-9
 
 
+def test_linear_cutoff_closed_forms(orc):
+    # Section 3.1 / Fig. 12 (r_c 4.5 / 9): the line from (0, r_c,max) to
+    # (r_c,max, r_c,min) -- halfway in d is halfway in r_c
+    assert orc.cutoff_linear(4.5, 4.5, 9.0) == 6.75
+    assert orc.cutoff_linear(0.0, 4.5, 9.0) == 9.0
+    assert orc.cutoff_linear(-3.0, 4.5, 9.0) == 9.0
+    assert orc.cutoff_linear(9.0, 4.5, 9.0) == 4.5
+    assert orc.cutoff_linear(20.0, 4.5, 9.0) == 4.5
+    assert orc.cutoff_linear(1.5, 3.0, 6.0) == pytest.approx(5.25, abs=1e-15)
+    # a straight line: zero second differences, slope -(max - min)/max
+    d = np.linspace(0.3, 5.7, 19)
+    r = np.array([orc.cutoff_linear(x, 3.0, 6.0) for x in d])
+    np.testing.assert_allclose(np.diff(r, 2), 0.0, atol=1e-13)
+    np.testing.assert_allclose(np.diff(r) / np.diff(d), -0.5, rtol=1e-12)
+    # the static limit
+    assert orc.cutoff_linear(2.0, 4.0, 4.0) == 4.0
+
+
+def test_exponential_cutoff_lies_above_the_linear_one(orc):
+    # Eq. 7 with alpha < 0 is concave in d, so it lies above its chord, which
+    # is the linear function: the reason the thesis gives for the
+    # exponential function's higher accuracy (it assigns larger cutoffs)
+    for rcmin, rcmax in ((3.0, 6.0), (4.5, 9.0), (3.0, 7.0)):
+        for alpha in (-0.25, -0.5, -1.0):
+            for d in np.linspace(0.01, rcmax - 0.01, 60):
+                assert orc.cutoff(d, rcmin, rcmax, alpha) > orc.cutoff_linear(d, rcmin, rcmax)
+
+
+def test_linear_cutoff_classes(orc):
+    rcmin, rcmax, K = 3.0, 6.0, 4
+    thr = orc.class_thresholds_linear(rcmin, rcmax, K)
+    # edges 4 and 5 are crossed at d = 4 and 2
+    np.testing.assert_allclose(thr, [2.0, 4.0][::-1], rtol=1e-15)
+    for k, t in enumerate(thr, start=1):
+        edge = rcmin + (rcmax - rcmin) * k / (K - 1)
+        assert orc.cutoff_linear(t, rcmin, rcmax) == pytest.approx(edge, rel=1e-14)
+    for d in np.linspace(0.001, rcmax - 0.001, 300):
+        c = orc.cutoff_class(d, rcmax, K, thr)
+        r = orc.cutoff_linear(d, rcmin, rcmax)
+        assert rcmin + (rcmax - rcmin) * (c - 1) / (K - 1) - 1e-12 <= r
+        assert r <= rcmin + (rcmax - rcmin) * c / (K - 1) + 1e-12
+
+
+def test_detection_with_the_linear_function(orc):
+    from paper_1502_03234_gb300 import slabgen
+    s = slabgen.make_slab(5000, seed=4)
+    ex = orc.detect(s.x, s.box, orc.DetectParams())
+    li = orc.detect(s.x, s.box, orc.DetectParams(cutoff_fn=1))
+    assert np.array_equal(ex.S, li.S) and np.array_equal(ex.d, li.d)
+    ref = np.array([orc.cutoff_linear(x, 3.0, 6.0) for x in li.d])
+    assert np.array_equal(li.rc, ref)
+    assert np.all(li.rc <= ex.rc)
+    thr = orc.class_thresholds_linear(3.0, 6.0, 4)
+    assert np.array_equal(li.cls, [orc.cutoff_class(x, 6.0, 4, thr) for x in li.d])
+
+
 def test_bin_index_geometry(orc):
     L, n = 23.94, 17
     rng = np.random.default_rng(3)
