@@ -62,11 +62,12 @@ FLOPS_PER_PAIR = 24              # 8 (distance test) + 16 (LJ force), per in-cut
 # DRAM bytes (read + write) per force launch of the direct walk (skin 0) from the committed
 # capture (profiles/k_force_warp_N262144_mixed.md); None: not captured
 FORCE_TRAFFIC = {"mixed": 14.96e6, "fp64": None}
-# DRAM bytes per launch of the Verlet-list force kernel (k_force_list_warp, N = 262,144,
-# skin 0.7 with skin_time 0.08, skin_floor 0.1) from the committed capture
-# (profiles/k_force_list_warp_N262144_mixed.md)
-LIST_TRAFFIC = {"k_force_list_warp": 222.93e6 + 4.59e6}
-LIST_TRAFFIC_CONFIG = (0.7, 0.08, 0.1, 1.0)     # skin, skin_time, skin_floor, list_margin
+# DRAM bytes (read + write) per launch of the Verlet-list force kernel
+# (k_force_list_warp, N = 262,144, skin 0.7, skin_time 0.06, skin_floor 0.07) from the
+# committed capture (profiles/k_force_list_warp_N262144_mixed.md), with the list entries in
+# use at the captured launches; the reported traffic scales it by the algorithmic bytes
+LIST_TRAFFIC = {"k_force_list_warp": {"bytes": 201.02e6 + 4.53e6, "entries": 39291834}}
+LIST_TRAFFIC_CONFIG = (0.7, 0.06, 0.07, 1.0)    # skin, skin_time, skin_floor, list_margin
 # bytes the list kernel must move per particle besides its list entries: own
 # position, cutoff constants, id/cell, list start and count, queue slot, the
 # force written and the pair count
@@ -103,14 +104,15 @@ def parse():
                          "below this many voxels change phase; 0: off")
     ap.add_argument("--list-margin", type=float, default=1.0,
                     help="interface-distance margin of the Verlet-list radius in sigma")
-    ap.add_argument("--workload", default="slab", choices=["slab", "wavy", "ensemble", "serving"])
+    ap.add_argument("--workload", default="slab",
+                    choices=["slab", "wavy", "ensemble", "serving", "accuracy"])
     ap.add_argument("--sweep", default="131072,262144,524288,1048576",
                     help="wavy: further N of the weak-scaling sweep")
     ap.add_argument("--sweep-steps", type=int, default=40)
     ap.add_argument("--requests", type=int, default=120, help="serving: trace length")
     a = ap.parse_args()
     if a.steps is None:
-        a.steps = {"slab": 1000, "wavy": 200, "ensemble": 500, "serving": 0}[a.workload]
+        a.steps = {"slab": 1000, "wavy": 200, "ensemble": 500, "serving": 0, "accuracy": 0}[a.workload]
     return a
 
 
@@ -286,10 +288,12 @@ def _launches(st, kinds):
 
 
 def _kind(sy, builds_before):
-    """(detected, rebuilt) of the step just run"""
+    """(detected, rebuilt) of the step just run, the list builds so far and
+    the entries of the lists in use"""
     st = sy.stats()
     every = sy.params.detect_every
-    return (every > 0 and st.step % every == 0, st.list_builds != builds_before), st.list_builds
+    return ((every > 0 and st.step % every == 0, st.list_builds != builds_before), st.list_builds,
+            int(st.list_entries))
 
 
 def _timed(sy, stream, flush, k, warm):
@@ -321,7 +325,7 @@ def _timed(sy, stream, flush, k, warm):
                     phase[key] = phase.get(key, 0.0) + val / nsteps
             e1.synchronize()
             out.append(e0.elapsed_time(e1))
-            kind, builds = _kind(sy, builds)
+            kind, builds, _ = _kind(sy, builds)
             kinds.append(kind)
         return out, phase, kinds
 
@@ -335,6 +339,81 @@ def _timed(sy, stream, flush, k, warm):
 def _pct(v, q):
     v = sorted(v)
     return v[min(len(v) - 1, max(0, int(math.ceil(q / 100.0 * len(v))) - 1))]
+
+
+def force_error(f, ref):
+    """Eq. 20 as printed, sqrt(mean_i (|F_i - F_i^ref| / |F_i^ref|)^2), and the
+    norm ratio sqrt(sum |F_i - F_i^ref|^2 / sum |F_i^ref|^2)"""
+    import numpy as np
+
+    d = np.linalg.norm(f - ref, axis=1)
+    r = np.linalg.norm(ref, axis=1)
+    return float(np.sqrt(np.mean((d / r) ** 2))), float(np.sqrt((d * d).sum() / (r * r).sum()))
+
+
+ACCURACY_GRID = [(3.0, 4.5), (3.0, 5.0), (3.0, 5.5), (3.0, 6.0), (3.0, 7.0), (3.0, 8.0),
+                 (4.0, 6.0), (4.0, 7.0), (4.0, 8.0), (4.5, 9.0)]
+ACCURACY_REF_RC = 12.0
+
+
+def accuracy_study(dcm, slabgen, stream, np, torch, n=262144):
+    """Section 6.1.1 (Fig. 34, 36): force error of DCM against a large static
+    cutoff (r_c = 12 sigma, FP64, standing in for the thesis's Ewald sums) on
+    the benchmark slab, for the exponential (Eq. 7) and linear (Fig. 12)
+    cutoff functions over a grid of (r_c,min, r_c,max); FP64 forces, one
+    force evaluation per setting at the same positions"""
+    s = slabgen.make_slab(n, seed=1)
+
+    def forces(rc_min, rc_max, fn, prec=dcm.DCM_FP64):
+        sy = dcm.System(s.box, n, precision=prec, rc_min=rc_min, rc_max=rc_max, cutoff_fn=fn,
+                        stream=stream.cuda_stream)
+        sy.set_state(s.x, s.v)
+        sy.detect_interface()
+        sy.compute_forces()                                  # warm
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sy.compute_forces()
+        e1.record(stream)
+        e1.synchronize()
+        _, _, f = sy.get_state()
+        st = sy.stats()
+        sy.close()
+        return f, st.pairs / n, e0.elapsed_time(e1)
+
+    ref, ref_pairs, ref_ms = forces(ACCURACY_REF_RC, ACCURACY_REF_RC, dcm.DCM_CUTOFF_EXP)
+    rows = []
+    for fn, name in ((dcm.DCM_CUTOFF_EXP, "exponential"), (dcm.DCM_CUTOFF_LINEAR, "linear")):
+        for rc_min, rc_max in ACCURACY_GRID:
+            f, pairs, ms = forces(rc_min, rc_max, fn)
+            e20, enorm = force_error(f, ref)
+            rows.append({"cutoff_fn": name, "rc_min": rc_min, "rc_max": rc_max,
+                         "eq20_rms_rel": e20, "norm_ratio": enorm,
+                         "pairs_per_particle": pairs, "force_ms_fp64": ms})
+    static = []
+    for rc in (3.0, 4.0, 6.0):
+        f, pairs, ms = forces(rc, rc, dcm.DCM_CUTOFF_EXP)
+        e20, enorm = force_error(f, ref)
+        static.append({"rc": rc, "eq20_rms_rel": e20, "norm_ratio": enorm,
+                       "pairs_per_particle": pairs, "force_ms_fp64": ms})
+    # the mixed-precision path's own error at the default cutoffs, for scale
+    f64, _, _ = forces(3.0, 6.0, dcm.DCM_CUTOFF_EXP)
+    fmx, _, _ = forces(3.0, 6.0, dcm.DCM_CUTOFF_EXP, dcm.DCM_MIXED)
+    mixed = dict(zip(("eq20_rms_rel", "norm_ratio"), force_error(fmx, f64)))
+    default = next(r for r in rows if r["cutoff_fn"] == "exponential" and r["rc_max"] == 6.0
+                   and r["rc_min"] == 3.0)
+    return {"metric": "RMS relative force error of DCM (Eq. 20) against a static r_c = 12 sigma",
+            "value": default["eq20_rms_rel"], "unit": "relative", "higher_is_better": False,
+            "dtype": "f64", "steps": None, "ms_per_step": None,
+            "config": {"workload": f"LJ liquid/vapor slab N={n}, L x L x 4L periodic, rho_l=0.8, "
+                                   f"T*=0.7, synthetic start (jittered FCC liquid), 1-sigma voxels; "
+                                   f"reference: static truncated cutoff {ACCURACY_REF_RC} sigma in "
+                                   f"FP64 (stand-in for Ewald sums)",
+                       "n": n, "reference_pairs_per_particle": ref_pairs,
+                       "reference_force_ms_fp64": ref_ms, "dcm": rows, "static": static,
+                       "mixed_vs_fp64_at_3_6": mixed,
+                       "note": ("value = Eq. 20 for r_c 3/6 with the exponential function; "
+                                "norm_ratio = sqrt(sum |dF|^2 / sum |F|^2), which tiny reference "
+                                "forces cannot dominate")}}
 
 
 def run_workload(args):
@@ -391,6 +470,8 @@ def run_workload(args):
                            "l2": L2_NOTE},
                 "latency_ms": {"p50": _pct(ms, 50), "p99": _pct(ms, 99), "unit": "ms per step"},
                 "weak_scaling_in_n": {"unit": UNIT, "steps": args.sweep_steps, "values": sweep}})
+        elif args.workload == "accuracy":
+            line.update(accuracy_study(dcm, slabgen, stream, np, torch))
         elif args.workload == "ensemble":
             mem = slabgen.make_ensemble(64, 4096, 131072, 0.65, 0.85, seed=0)
             boxes = [m.slab.box for m in mem]
@@ -506,7 +587,7 @@ def main():
         sy.sync()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(k)]
-        force_ms, phase_sum, rebuilt, kinds = [], {}, [], []
+        force_ms, phase_sum, rebuilt, kinds, ents = [], {}, [], [], []
         b_prev = sy.stats().list_builds
         for q in range(k):
             with torch.cuda.stream(stream):
@@ -520,13 +601,15 @@ def main():
                 force_ms.append(ph["force"])
                 for key, val in ph.items():
                     phase_sum[key] = phase_sum.get(key, 0.0) + val
-            kind, b_now = _kind(sy, b_prev)              # (outside the timed events)
+            kind, b_now, e_now = _kind(sy, b_prev)      # (outside the timed events)
             kinds.append(kind)
             rebuilt.append(b_now != b_prev)
+            ents.append(e_now)
             b_prev = b_now
         sy.sync()
         timed_steps.rebuilt = rebuilt
         timed_steps.kinds = kinds
+        timed_steps.entries = ents
         return [a.elapsed_time(b) for a, b in ev], force_ms, phase_sum
 
     sy = make_system(prec)
@@ -535,6 +618,7 @@ def main():
     torch.cuda.synchronize()
     with Clocks(local) as clk:
         step_ms, _, _ = timed_steps(sy, args.steps, args.warmup, False)
+    head_entries = timed_steps.entries
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
@@ -576,15 +660,25 @@ def main():
         # empty launch of the rebuild kernel).  It streams each particle's
         # list from HBM (arithmetic intensity ~3 flop/B, under the HBM roof)
         l_ms = sum(list_steps) / len(list_steps)
-        entries = st.list_entries
+        # the lists' entries averaged over the timed list steps (they change
+        # with every build)
+        list_ents = [e for e, r in zip(timed_steps.entries, rebuilt) if not r]
+        entries = sum(list_ents) / len(list_ents)
         lkernel = "k_force_list_warp"
         alg_bytes = LIST_BYTES_PER_ENTRY * entries + LIST_BYTES_PER_PARTICLE * n
         achieved = alg_bytes / (l_ms * 1e-3) / 1e9
+        cap = LIST_TRAFFIC.get(lkernel) or {}
+        traffic = None
+        if (cap.get("bytes") and n == N_DEFAULT and
+                (args.skin, args.skin_time, args.skin_floor, args.list_margin) == LIST_TRAFFIC_CONFIG):
+            cap_alg = LIST_BYTES_PER_ENTRY * cap["entries"] + LIST_BYTES_PER_PARTICLE * n
+            traffic = cap["bytes"] * alg_bytes / cap_alg
         roofline = {"bound": "hbm", "achieved": achieved, "peak": HBM_PEAK_GBS, "unit": "GB/s",
                     "frac": achieved / HBM_PEAK_GBS,
-                    "traffic": (LIST_TRAFFIC.get(lkernel) if n == N_DEFAULT and
-                                (args.skin, args.skin_time, args.skin_floor, args.list_margin)
-                                == LIST_TRAFFIC_CONFIG else None),
+                    "traffic": traffic,
+                    "traffic_note": ("ncu DRAM bytes of one captured launch, scaled from that "
+                                     "launch's list entries to this run's mean by the algorithmic "
+                                     "bytes"),
                     "kernel": f"{lkernel} (mixed, Verlet lists)",
                     "peak_note": "measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                     "algorithmic_bytes_per_launch": alg_bytes, "list_entries": entries,
@@ -670,6 +764,10 @@ def main():
         cfg["skin_time"] = args.skin_time
         cfg["skin_floor"] = args.skin_floor
         cfg["min_component_voxels"] = args.min_component
+        if args.steps <= 64 and args.skin > 0:
+            # list entries after each timed step (to match profiler captures
+            # of single launches)
+            cfg["list_entries_steps"] = head_entries
         cfg["phase_ms_avg"] = {k: v / phase_steps for k, v in phase_sum.items()}
         cfg["phase_note"] = ("per-phase CUDA events inside the step graph, on a second run of the "
                              "same steps from the same start (the timed run records none)")

@@ -60,6 +60,7 @@ enum { DCM_FP64 = 0,   /* FP64 pair distances, forces and accumulation */
                           (2 x FP32) accumulation, FP64 state and reductions */
 };
 enum { DCM_HOST = 0, DCM_DEVICE = 1 };
+enum { DCM_CUTOFF_EXP = 0, DCM_CUTOFF_LINEAR = 1 };
 
 #define DCM_MAX_CLASSES 8
 
@@ -127,7 +128,11 @@ typedef struct {
        distance pass.  Components are 6-connected across the periodic
        faces.  0 (default): no removal.  Per system. */
     int32_t min_component_voxels;
-    int32_t reserved[1];
+    /* Cutoff function of particle i's distance to the interface:
+       DCM_CUTOFF_EXP (default) is Eq. 7-8 with alpha; DCM_CUTOFF_LINEAR is
+       the straight line of Section 3.1 / Fig. 12 from (0, rc_max) to
+       (rc_max, rc_min), with Eq. 7's outer cases.  Per system. */
+    int32_t cutoff_fn;
 } dcm_params;
 
 /* Force walk variants (dcm_tuning.walk).  DCM_WALK_WARP: one warp per

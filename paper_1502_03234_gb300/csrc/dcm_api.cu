@@ -118,6 +118,8 @@ static int check_params(const dcm_box *box, int64_t n, const dcm_params *p)
         (p->skin > 0 && p->skin_time > 0.f && p->skin_floor > 0.5 * p->skin))
         return fail(DCM_ERR_ARG, "skin_time, skin_floor must be >= 0, skin_floor <= skin/2");
     if (p->min_component_voxels < 0) return fail(DCM_ERR_ARG, "min_component_voxels must be >= 0");
+    if (p->cutoff_fn != DCM_CUTOFF_EXP && p->cutoff_fn != DCM_CUTOFF_LINEAR)
+        return fail(DCM_ERR_ARG, "cutoff_fn must be DCM_CUTOFF_EXP or DCM_CUTOFF_LINEAR");
     return DCM_OK;
 }
 
@@ -170,7 +172,19 @@ static int setup_geometry(const dcm_box *box, int64_t n, const dcm_params *p, Ge
     g.rc_max = p->rc_max;
     g.alpha = p->alpha;
     g.K = p->n_classes;
-    if (p->rc_max > p->rc_min) {
+    g.cut_fn = p->cutoff_fn;
+    g.cut_slope = 0.0;
+    if (p->rc_max > p->rc_min && p->cutoff_fn == DCM_CUTOFF_LINEAR) {
+        // Fig. 12's line; the class edges invert it
+        g.cut_a = 0.0;
+        g.cut_b = p->rc_min;
+        g.cut_slope = (p->rc_max - p->rc_min) / p->rc_max;
+        for (int k = 1; k <= g.K - 2; ++k) {
+            double r = p->rc_min + (p->rc_max - p->rc_min) * (double)k / (double)(g.K - 1);
+            g.thr[k - 1] = (p->rc_max - r) * p->rc_max / (p->rc_max - p->rc_min);
+        }
+    } else if (p->rc_max > p->rc_min) {
+        g.cut_fn = DCM_CUTOFF_EXP;
         g.cut_a = (p->rc_max - p->rc_min) / (pow(2.0, p->alpha * p->rc_max) - 1.0);
         g.cut_b = p->rc_min - g.cut_a;
         for (int k = 1; k <= g.K - 2; ++k) {
@@ -178,6 +192,7 @@ static int setup_geometry(const dcm_box *box, int64_t n, const dcm_params *p, Ge
             g.thr[k - 1] = p->rc_max - log2((r - g.cut_b) / g.cut_a) / p->alpha;
         }
     } else {
+        g.cut_fn = DCM_CUTOFF_EXP;
         g.cut_a = 0.0;
         g.cut_b = p->rc_min;
         for (int k = 1; k <= g.K - 2; ++k) g.thr[k - 1] = 0.0;

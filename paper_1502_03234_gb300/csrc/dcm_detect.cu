@@ -867,8 +867,10 @@ __device__ __forceinline__ void cutoff_one(Batch b, int64_t i, const double *__r
         r = g.rc_max;
     else if (db >= rmaxb)
         r = g.rc_min;
+    else if (g.cut_fn == DCM_CUTOFF_LINEAR)
+        r = DSUB(g.rc_max, DMUL(g.cut_slope, di));                  // Fig. 12
     else
-        r = DADD(DMUL(g.cut_a, exp2(DMUL(g.alpha, DSUB(g.rc_max, di)))), g.cut_b);
+        r = DADD(DMUL(g.cut_a, exp2(DMUL(g.alpha, DSUB(g.rc_max, di)))), g.cut_b);   // Eq. 7
     int c = 0;
     if (db < rmaxb) {
         c = 1;

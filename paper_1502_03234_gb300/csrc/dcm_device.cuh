@@ -227,7 +227,9 @@ __device__ __forceinline__ float list_radius(const Geom &g, double rci, double d
         float rmax = (float)g.rc_max, rmin = (float)g.rc_min;
         float ra = dd <= 0.f ? rmax
                  : (dd >= rmax ? rmin
-                               : fmaf((float)g.cut_a, exp2f((float)g.alpha * (rmax - dd)), (float)g.cut_b));
+                    : (g.cut_fn == DCM_CUTOFF_LINEAR
+                           ? fmaf(-(float)g.cut_slope, dd, rmax)
+                           : fmaf((float)g.cut_a, exp2f((float)g.alpha * (rmax - dd)), (float)g.cut_b)));
         r = fmaxf(r, ra);
     }
     return fmaf(r, 1.00001f, 1e-4f) + share;

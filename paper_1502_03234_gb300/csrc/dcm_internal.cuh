@@ -93,6 +93,8 @@ struct Geom {
     double w_h[3];               // 1 / h^2 per axis (the Godunov weights)
     double e_min;                // 1 / sqrt(sum w): smallest possible Godunov step
     double rc_min, rc_max, alpha, cut_a, cut_b;
+    int cut_fn;                  // DCM_CUTOFF_EXP (Eq. 7) or DCM_CUTOFF_LINEAR (Fig. 12)
+    double cut_slope;            // linear: (rc_max - rc_min) / rc_max
     int K;
     double thr[DCM_MAX_CLASSES]; // class thresholds on d (descending)
     double dt, hdtm;             // dt, dt/(2m)

@@ -20,6 +20,7 @@ DCM_ERR_ARG, DCM_ERR_OOM, DCM_ERR_CUDA, DCM_ERR_BOX_TOO_SMALL = 1, 2, 3, 4
 DCM_ERR_NOT_CONVERGED, DCM_ERR_DEVICE_CHECK, DCM_ERR_CANCELLED, DCM_ERR_STATE = 5, 6, 7, 8
 DCM_FP64, DCM_MIXED = 0, 1
 DCM_HOST, DCM_DEVICE = 0, 1
+DCM_CUTOFF_EXP, DCM_CUTOFF_LINEAR = 0, 1
 DCM_MAX_CLASSES = 8
 DCM_WALK_WARP, DCM_WALK_LANES = 0, 1
 DCM_GRAPH_BRANCHED, DCM_GRAPH_FLAT = 0, 1
@@ -60,7 +61,7 @@ class dcm_params(C.Structure):
                 ("skin", C.c_double), ("list_density", C.c_float),
                 ("list_margin", C.c_float), ("skin_time", C.c_float),
                 ("skin_floor", C.c_float), ("min_component_voxels", C.c_int32),
-                ("reserved", C.c_int32 * 1)]
+                ("cutoff_fn", C.c_int32)]
 
 
 class dcm_tuning(C.Structure):
