@@ -231,8 +231,8 @@ static int64_t list_cap(const Geom &g, int64_t n)
     return n * (int64_t)ceil(big < small ? big : small) + 1024;
 }
 
-// the small-component buffers (5 ints per voxel) and the systems' tile
-// offsets, on creation with min_component_voxels or on first use
+// the small-component buffers (5 ints per voxel and a flag per tile) and the
+// systems' tile offsets, on creation with min_component_voxels or on first use
 template <typename T>
 static int dalloc(dcm_handle *h, T **ptr, int64_t count);
 
@@ -246,7 +246,7 @@ static int cc_setup(dcm_handle *h)
         off[k + 1] = off[k] + (int64_t)((g.gd[0] + 7) / 8) * ((g.gd[1] + 7) / 8) * ((g.gd[2] + 7) / 8);
     }
     int rc;
-    if ((rc = dalloc(h, &h->cc, 5 * h->b.NV))) return rc;
+    if ((rc = dalloc(h, &h->cc, 5 * h->b.NV + off[h->M]))) return rc;
     if ((rc = dalloc(h, &h->cc_tiles, (int64_t)h->M + 1))) return rc;
     DCM_CHECK_CUDA(cudaMemcpy(h->cc_tiles, off.data(), sizeof(int64_t) * (h->M + 1),
                               cudaMemcpyHostToDevice));

@@ -45,6 +45,7 @@ struct CcArgs {
     int32_t *parent;     // this phase's forest (voxel indices)
     int32_t *size;       // voxels per global root, counted up to the threshold
     int32_t *lsize;      // voxels per tile-local root (0 elsewhere)
+    int32_t *uniform;    // per tile: every voxel of the tile in the phase
     const int64_t *tile_off;   // [M+1] tile offsets of the systems
     int phase;           // 0: liquid components, 1: vapor components
     int thr;             // >= 0: this threshold for every system; < 0: each system's own
@@ -149,28 +150,31 @@ __device__ __forceinline__ void cc_local(const CcArgs &a, const CcTile &c)
         a.lsize[c.v] = 0;
     }
     cnt[tid] = 0;
-    if (__syncthreads_and(in || !c.inside)) {
+    const bool uniform = __syncthreads_and(in || !c.inside);
+    if (tid == 0) a.uniform[blockIdx.x] = uniform ? 1 : 0;
+    if (uniform) {
         // the tile's voxels all in the phase: one box-shaped component whose
         // smallest index is the tile's first voxel (local 0, always inside)
         lab[tid] = 0;
     } else {
         lab[tid] = in ? tid : CC_TILE;
-        // face neighbours inside the tile (the periodic wrap stays in the
-        // tile only when the tile spans the axis)
-        int nb[6], m = 0;
-        if (in) {
-            const int xs[2] = {c.x == 0 ? g.gd[0] - 1 : c.x - 1, c.x + 1 == g.gd[0] ? 0 : c.x + 1};
-            const int ys[2] = {c.y == 0 ? g.gd[1] - 1 : c.y - 1, c.y + 1 == g.gd[1] ? 0 : c.y + 1};
-            const int zs[2] = {c.z == 0 ? g.gd[2] - 1 : c.z - 1, c.z + 1 == g.gd[2] ? 0 : c.z + 1};
+        // face neighbours inside the tile and in the phase (the periodic wrap
+        // stays in the tile only when the tile spans the axis); an absent one
+        // is the voxel itself, which leaves the minimum alone
+        int nb[6];
+        const int xs[2] = {c.x == 0 ? g.gd[0] - 1 : c.x - 1, c.x + 1 == g.gd[0] ? 0 : c.x + 1};
+        const int ys[2] = {c.y == 0 ? g.gd[1] - 1 : c.y - 1, c.y + 1 == g.gd[1] ? 0 : c.y + 1};
+        const int zs[2] = {c.z == 0 ? g.gd[2] - 1 : c.z - 1, c.z + 1 == g.gd[2] ? 0 : c.z + 1};
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                if (xs[q] / CC_T == c.tx && xs[q] != c.x && a.S[c.v + xs[q] - c.x] == a.phase)
-                    nb[m++] = tid + xs[q] - c.x;
-                if (ys[q] / CC_T == c.ty && ys[q] != c.y && a.S[c.v + c.sy * (ys[q] - c.y)] == a.phase)
-                    nb[m++] = tid + CC_T * (ys[q] - c.y);
-                if (zs[q] / CC_T == c.tz && zs[q] != c.z && a.S[c.v + c.sz * (zs[q] - c.z)] == a.phase)
-                    nb[m++] = tid + CC_T * CC_T * (zs[q] - c.z);
-            }
+        for (int q = 0; q < 2; ++q) {
+            nb[q] = in && xs[q] / CC_T == c.tx && xs[q] != c.x && a.S[c.v + xs[q] - c.x] == a.phase
+                        ? tid + xs[q] - c.x : tid;
+            nb[2 + q] = in && ys[q] / CC_T == c.ty && ys[q] != c.y &&
+                                a.S[c.v + c.sy * (ys[q] - c.y)] == a.phase
+                            ? tid + CC_T * (ys[q] - c.y) : tid;
+            nb[4 + q] = in && zs[q] / CC_T == c.tz && zs[q] != c.z &&
+                                a.S[c.v + c.sz * (zs[q] - c.z)] == a.phase
+                            ? tid + CC_T * CC_T * (zs[q] - c.z) : tid;
         }
         __syncthreads();
         // labels only decrease and stay inside the component, so they end at
@@ -181,7 +185,8 @@ __device__ __forceinline__ void cc_local(const CcArgs &a, const CcTile &c)
             if (in) {
                 int l = lab[tid];
                 l = min(l, lab[l]);                      // pointer jumping
-                for (int q = 0; q < m; ++q) l = min(l, lab[nb[q]]);
+#pragma unroll
+                for (int q = 0; q < 6; ++q) l = min(l, lab[nb[q]]);
                 if (l < lab[tid]) {
                     lab[tid] = l;
                     changed = true;
@@ -243,12 +248,27 @@ __global__ void k_cc_global(CcArgs a)
     int co[3];
     cc_coords(g, v, co);
     const int64_t st[3] = {1, g.gd[0], (int64_t)g.gd[0] * g.gd[1]};
+    const int nt[3] = {(g.gd[0] + CC_T - 1) / CC_T, (g.gd[1] + CC_T - 1) / CC_T, 0};
+    const int tc[3] = {co[0] / CC_T, co[1] / CC_T, co[2] / CC_T};
+    const int64_t t0 = a.b.M == 1 ? 0 : a.tile_off[sys_v(a.b, v)];
+    const bool uni = __ldg(a.uniform + t0 + tc[0] + nt[0] * (tc[1] + nt[1] * tc[2])) != 0;
     bool ok = true;
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
         const int cu = co[ax] + 1 == g.gd[ax] ? 0 : co[ax] + 1;
-        if (cu / CC_T == co[ax] / CC_T) continue;          // a link inside the tile
+        if (cu / CC_T == tc[ax]) continue;                 // a link inside the tile
         const int64_t u = v + st[ax] * (cu - co[ax]);
+        if (uni) {
+            // both tiles wholly in the phase: their roots are their first
+            // voxels, and the face's in-plane corner joins them for all 64
+            int tu[3] = {tc[0], tc[1], tc[2]};
+            tu[ax] = cu / CC_T;
+            if (__ldg(a.uniform + t0 + tu[0] + nt[0] * (tu[1] + nt[1] * tu[2])) != 0) {
+                if (co[(ax + 1) % 3] % CC_T == 0 && co[(ax + 2) % 3] % CC_T == 0)
+                    ok = cc_union(a.parent, __ldcg(a.parent + v), __ldcg(a.parent + u)) && ok;
+                continue;
+            }
+        }
         if (a.S[u] != a.phase) continue;
         const int pa = __ldcg(a.parent + v), pb = __ldcg(a.parent + u);
         if (pa == pb) continue;
@@ -319,6 +339,7 @@ int launch_components(dcm_handle *h, const Batch &b, uint8_t *S, int thr, int64_
         a[phase].parent = h->cc + (2 * phase) * h->b.NV;
         a[phase].size = h->cc + (2 * phase + 1) * h->b.NV;
         a[phase].lsize = h->cc + 4 * h->b.NV;
+        a[phase].uniform = h->cc + 5 * h->b.NV;
         a[phase].tile_off = h->cc_tiles;
         a[phase].phase = phase;
         a[phase].thr = thr;

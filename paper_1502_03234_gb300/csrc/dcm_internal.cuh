@@ -192,7 +192,8 @@ struct dcm_handle {
     int32_t *stamp;
     int32_t *flist;              // 4 * nvox
     int32_t *fcount;             // 4 counters
-    int32_t *cc;                 // small components: parent and count of each phase, local sizes (5 * nvox)
+    int32_t *cc;                 // small components: parent and count of each phase, local sizes
+                                 // (5 * nvox), a uniform flag per tile
     int64_t *cc_tiles;           // [M+1] offsets of the systems' 8^3 tiles (device)
     int64_t cc_ntiles, cc_ntiles0;   // tiles of all systems / of system 0
     bool cc_on;                  // some system removes small components
