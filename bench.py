@@ -60,11 +60,11 @@ def _hbm_peak():
 HBM_PEAK_GBS = _hbm_peak()
 FLOPS_PER_PAIR = 24              # 8 (distance test) + 16 (LJ force), per in-cutoff pair
 # DRAM bytes (read + write) per force launch of the direct walk (skin 0) from the committed
-# capture (profiles/k_force_warp_N262144_mixed.md); None: not captured
+# ncu capture of that kernel on this workload; None: not captured
 FORCE_TRAFFIC = {"mixed": 14.96e6, "fp64": None}
 # DRAM bytes (read + write) per launch of the Verlet-list force kernel
 # (k_force_list_warp, N = 262,144, skin 0.7, skin_time 0.06, skin_floor 0.07) from the
-# committed capture (profiles/k_force_list_warp_N262144_mixed.md), with the list entries in
+# committed ncu capture of that kernel on this workload, with the list entries in
 # use at the captured launches; the reported traffic scales it by the algorithmic bytes
 LIST_TRAFFIC = {"k_force_list_warp": {"bytes": 201.02e6 + 4.53e6, "entries": 39291834}}
 LIST_TRAFFIC_CONFIG = (0.7, 0.06, 0.07, 1.0)    # skin, skin_time, skin_floor, list_margin
