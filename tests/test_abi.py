@@ -55,3 +55,22 @@ def test_defaults_and_argument_errors_without_gpu(libdcm):
     assert dcm.dcm_estimate_bytes((11.0, 11.0, 40.0), 1000, dcm.default_params()) == -1
     est = dcm.dcm_estimate_bytes((61.56, 61.56, 246.2), 262144, dcm.default_params())
     assert 50e6 < est < 1e9
+
+
+def test_component_and_cutoff_parameters_without_gpu(libdcm):
+    # Section 4.2 and Fig. 12 parameters: validated and accounted for on the host
+    from paper_1502_03234_gb300 import dcm
+
+    box = (61.56, 61.56, 246.2)
+    p = dcm.default_params()
+    assert p.min_component_voxels == 0 and p.cutoff_fn == dcm.DCM_CUTOFF_EXP
+    base = dcm.dcm_estimate_bytes(box, 262144, p)
+    # the removal's buffers: parent and count per phase and a tile-local size
+    # (5 int32 per voxel) on the 61 x 61 x 246 voxel grid
+    cc = dcm.dcm_estimate_bytes(box, 262144, dcm.default_params(min_component_voxels=5))
+    assert cc - base == 20 * 61 * 61 * 246
+    lin = dcm.dcm_estimate_bytes(box, 262144, dcm.default_params(cutoff_fn=dcm.DCM_CUTOFF_LINEAR))
+    assert lin == base
+    assert dcm.dcm_estimate_bytes(box, 262144, dcm.default_params(min_component_voxels=-1)) == -1
+    assert dcm.dcm_estimate_bytes(box, 262144, dcm.default_params(cutoff_fn=2)) == -1
+    assert "cutoff_fn" in dcm.lib().dcm_last_error().decode()
