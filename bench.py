@@ -341,6 +341,23 @@ def _pct(v, q):
     return v[min(len(v) - 1, max(0, int(math.ceil(q / 100.0 * len(v))) - 1))]
 
 
+def max_over_ranks(v, dist, device):
+    """the largest v over the ranks (v itself without a process group)"""
+    if dist is None:
+        return float(v)
+    import torch
+
+    t = torch.tensor([float(v)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, n, steps, t_max_ms):
+    """atom-steps/s of the whole job: every rank steps its own n atoms, and the
+    slowest rank's time bounds the job"""
+    return world * n * steps / (t_max_ms * 1e-3)
+
+
 def force_error(f, ref):
     """Eq. 20 as printed, sqrt(mean_i (|F_i - F_i^ref| / |F_i^ref|)^2), and the
     norm ratio sqrt(sum |F_i - F_i^ref|^2 / sum |F_i^ref|^2)"""
@@ -641,12 +658,8 @@ def main():
     sy.sync()
 
     # max over ranks, whole-job throughput
-    t_max = total_ms
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * n * args.steps / (t_max * 1e-3)
+    t_max = max_over_ranks(total_ms, dist, "cuda")
+    value = whole_job_rate(world, n, args.steps, t_max)
 
     # roofline of the dominant kernel
     clocks = clk.summary()
