@@ -66,6 +66,8 @@ def _load():
         "orc_density": (None, [i64, vp, vp, vp, vp]),
         "orc_smooth": (None, [vp, vp, C.c_int, vp]),
         "orc_kmeans": (C.c_int, [i64, vp, C.c_int, vp, vp, vp]),
+        "orc_ms_energy": (d, [vp, vp, d, d, d, vp]),
+        "orc_ms_segment": (None, [vp, vp, d, d, d, C.c_int, vp, vp]),
         "orc_label_components": (i64, [vp, vp, C.c_int, vp]),
         "orc_remove_small_components": (i64, [vp, vp, C.c_int]),
         "orc_godunov": (d, [vp, vp]),
@@ -239,6 +241,25 @@ def kmeans(Bs, max_iter=100):
     cl, cv = C.c_double(), C.c_double()
     it = _load().orc_kmeans(Bs.size, _p(Bs), int(max_iter), _p(S), C.byref(cl), C.byref(cv))
     return S, cl.value, cv.value, it
+
+
+def ms_energy(dims, rho, c_l, c_v, nu, S) -> float:
+    """Eq. 13 of labels S with fixed densities (perimeter = liquid/vapor faces)"""
+    d = _i32(dims)
+    rho = _f64(rho).ravel()
+    S = np.ascontiguousarray(S, dtype=np.uint8).ravel()
+    return _load().orc_ms_energy(_p(d), _p(rho), float(c_l), float(c_v), float(nu), _p(S))
+
+
+def ms_segment(dims, rho, c_l, c_v, nu, iters):
+    """Eq. 13 minimised by the convex relaxation; returns (labels, relaxed u)"""
+    d = _i32(dims)
+    rho = _f64(rho).ravel()
+    S = np.zeros(rho.size, np.uint8)
+    u = np.zeros(rho.size)
+    _load().orc_ms_segment(_p(d), _p(rho), float(c_l), float(c_v), float(nu), int(iters),
+                           _p(S), _p(u))
+    return S, u
 
 
 def label_components(dims, S, phase):

@@ -121,6 +121,19 @@ void orc_smooth(const int dims[3], const int32_t *B, int order, double *Bs);
 int orc_kmeans(int64_t nvox, const double *Bs, int max_iter, uint8_t *S,
                double *c_l, double *c_v);
 
+/* ---- Eq. 13: two-phase piecewise-constant Mumford-Shah ------------------------
+ * orc_ms_energy: Eq. 13 of labels S (0 liquid, 1 vapor) on the image rho with
+ * fixed densities c_l, c_v: sum over liquid voxels of (rho - c_l)^2, over
+ * vapor voxels of (rho - c_v)^2, plus nu times the number of periodic grid
+ * faces between a liquid and a vapor voxel.  orc_ms_segment: its minimiser
+ * by the convex relaxation (Chan-Esedoglu-Nikolova) solved with `iters`
+ * Chambolle-Pock iterations from u = 1/2; S = 0 where u > 1/2; u_out
+ * (nullable) receives the relaxed solution. */
+double orc_ms_energy(const int dims[3], const double *rho, double c_l, double c_v, double nu,
+                     const uint8_t *S);
+void orc_ms_segment(const int dims[3], const double *rho, double c_l, double c_v, double nu,
+                    int iters, uint8_t *S, double *u_out);
+
 /* ---- Section 4.2, Algorithm 4.1: small connected components ------------------
  * orc_label_components: components of the voxels with S == phase, face
  * (6-) connectivity across the periodic faces, by the row-major two-pass
