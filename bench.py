@@ -195,14 +195,14 @@ class Clocks:
 
 # ---- reference arm: the FP64 CPU oracle ----------------------------------------------
 def oracle_rate(n_sample: int, target_s: float, max_steps: int = 2000, seed: int = 1,
-                min_component: int = 0):
-    """atom-steps/s of the FP64 oracle (all host cores) on an n_sample slab
-    with the same densities, cutoffs and cadence."""
+                min_component: int = 0, threads: int = 0):
+    """atom-steps/s of the FP64 oracle (all host cores, or `threads`) on an
+    n_sample slab with the same densities, cutoffs and cadence."""
     import oracle
     from paper_1502_03234_gb300 import slabgen
 
-    cores = os.cpu_count() or 1
-    oracle.set_threads(cores)
+    cores = threads if threads > 0 else (os.cpu_count() or 1)
+    cores = oracle.set_threads(cores)
     s = slabgen.make_slab(n_sample, seed=seed)
     p = oracle.RunParams(det=oracle.DetectParams(rc_min=3.0, rc_max=6.0, voxel=1.0,
                                                  min_component_voxels=min_component),
@@ -762,9 +762,13 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         rate, cores, csteps, cdt = oracle_rate(16384, target_s=12.0,
                                                min_component=args.min_component)
+        rate1, _, csteps1, cdt1 = oracle_rate(16384, target_s=5.0, threads=1,
+                                              min_component=args.min_component)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"N=16384 slab of the same shape, {csteps} oracle steps "
-                         f"({cdt:.1f} s) after a 2-step calibration"}
+                         f"({cdt:.1f} s) after a 2-step calibration",
+               "single_thread": {"value": rate1, "unit": UNIT, "cores": 1,
+                                 "sample": f"the same slab, {csteps1} oracle steps ({cdt1:.1f} s)"}}
 
     if rank == 0:
         sms = sorted(step_ms)
