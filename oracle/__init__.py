@@ -68,6 +68,7 @@ def _load():
         "orc_kmeans": (C.c_int, [i64, vp, C.c_int, vp, vp, vp]),
         "orc_ms_energy": (d, [vp, vp, d, d, d, vp]),
         "orc_ms_segment": (None, [vp, vp, d, d, d, C.c_int, vp, vp]),
+        "orc_ms_alternate": (C.c_int, [vp, vp, d, C.c_int, C.c_int, vp, vp, vp]),
         "orc_label_components": (i64, [vp, vp, C.c_int, vp]),
         "orc_remove_small_components": (i64, [vp, vp, C.c_int]),
         "orc_godunov": (d, [vp, vp]),
@@ -260,6 +261,18 @@ def ms_segment(dims, rho, c_l, c_v, nu, iters):
     _load().orc_ms_segment(_p(d), _p(rho), float(c_l), float(c_v), float(nu), int(iters),
                            _p(S), _p(u))
     return S, u
+
+
+def ms_alternate(dims, rho, nu, iters, max_outer, c_l, c_v):
+    """Eq. 13 over sets and densities; returns (labels, c_l, c_v, rounds)"""
+    d = _i32(dims)
+    rho = _f64(rho).ravel()
+    S = np.zeros(rho.size, np.uint8)
+    cl = C.c_double(c_l)
+    cv = C.c_double(c_v)
+    rounds = _load().orc_ms_alternate(_p(d), _p(rho), float(nu), int(iters), int(max_outer),
+                                      _p(S), C.byref(cl), C.byref(cv))
+    return S, cl.value, cv.value, rounds
 
 
 def label_components(dims, S, phase):

@@ -551,6 +551,43 @@ void orc_ms_segment(const int dims[3], const double *rho, double c_l, double c_v
     free(p);
 }
 
+/* Eq. 13 over the densities too: alternate the segmentation with fixed
+ * densities and the densities as the means of rho over each phase (the
+ * minimisers of the data terms for fixed sets), from the K-means centres
+ * (Eq. 14), until the labels repeat or max_outer rounds.  A phase left
+ * empty keeps its density.  Returns the rounds. */
+int orc_ms_alternate(const int dims[3], const double *rho, double nu, int iters, int max_outer,
+                     uint8_t *S, double *c_l_io, double *c_v_io)
+{
+    const int64_t nv = (int64_t)dims[0] * dims[1] * dims[2];
+    uint8_t *prev = (uint8_t *)malloc((size_t)(nv > 0 ? nv : 1));
+    double cl = *c_l_io, cv = *c_v_io;
+    int round = 0;
+    while (round < max_outer) {
+        orc_ms_segment(dims, rho, cl, cv, nu, iters, S, NULL);
+        round++;
+        if (round > 1 && memcmp(prev, S, (size_t)nv) == 0) break;
+        double sl = 0.0, sv = 0.0;
+        int64_t nl = 0, nvap = 0;
+        for (int64_t v = 0; v < nv; ++v) {
+            if (S[v] == 0) {
+                sl += rho[v];
+                nl++;
+            } else {
+                sv += rho[v];
+                nvap++;
+            }
+        }
+        if (nl > 0) cl = sl / (double)nl;
+        if (nvap > 0) cv = sv / (double)nvap;
+        memcpy(prev, S, (size_t)nv);
+    }
+    free(prev);
+    *c_l_io = cl;
+    *c_v_io = cv;
+    return round;
+}
+
 /* Section 4.2, Algorithm 4.1: connected-component labelling of one phase.
  * The thesis gives the 2D row-major pass and says the 3D extension with
  * periodic boundaries is direct; the reading here:

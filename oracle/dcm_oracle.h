@@ -133,6 +133,12 @@ double orc_ms_energy(const int dims[3], const double *rho, double c_l, double c_
                      const uint8_t *S);
 void orc_ms_segment(const int dims[3], const double *rho, double c_l, double c_v, double nu,
                     int iters, uint8_t *S, double *u_out);
+/* Eq. 13 over the densities as well: segmentation with fixed densities and
+ * densities as the phase means, alternated from *c_l_io, *c_v_io (the K-means
+ * centres) until the labels repeat or max_outer rounds; the final densities
+ * are written back.  Returns the rounds. */
+int orc_ms_alternate(const int dims[3], const double *rho, double nu, int iters, int max_outer,
+                     uint8_t *S, double *c_l_io, double *c_v_io);
 
 /* ---- Section 4.2, Algorithm 4.1: small connected components ------------------
  * orc_label_components: components of the voxels with S == phase, face

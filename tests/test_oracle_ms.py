@@ -76,3 +76,34 @@ def test_larger_nu_never_lengthens_the_perimeter():
         per.append(energy_by_hand(dims, rho, 0.8, 0.1, 1.0, S) - energy_by_hand(dims, rho, 0.8, 0.1,
                                                                                  0.0, S))
     assert all(a >= b for a, b in zip(per, per[1:]))
+
+
+def test_alternation_without_perimeter_is_kmeans():
+    # nu = 0: segmenting with fixed densities is the nearest-centre rule and
+    # the density update the centre update, so alternating from (max, min)
+    # is Lloyd's K-means (Eq. 14) -- same labels, same centres
+    rng = np.random.default_rng(21)
+    dims = (7, 6, 10)
+    rho = np.concatenate([rng.normal(0.8, 0.15, 200), rng.normal(0.1, 0.15, 220)])
+    rng.shuffle(rho)
+    Sk, cl_k, cv_k, _ = oracle.kmeans(rho)
+    S, cl, cv, rounds = oracle.ms_alternate(dims, rho, 0.0, 100, 50, rho.max(), rho.min())
+    assert np.array_equal(S, Sk)
+    assert cl == pytest.approx(cl_k, rel=1e-12) and cv == pytest.approx(cv_k, rel=1e-12)
+    assert rounds >= 2
+
+
+def test_alternation_lowers_the_energy():
+    dims = (8, 8, 24)
+    z = np.repeat(np.arange(24), 64)
+    clean = np.where((z >= 8) & (z < 16), 0, 1).astype(np.uint8)
+    rng = np.random.default_rng(6)
+    rho = np.where(clean == 0, 0.8, 0.05) + rng.uniform(-0.5, 0.5, clean.size)
+    c0 = (rho.max(), rho.min())
+    S1, _ = oracle.ms_segment(dims, rho, c0[0], c0[1], 0.2, 3000)
+    S, cl, cv, rounds = oracle.ms_alternate(dims, rho, 0.2, 3000, 20, *c0)
+    assert oracle.ms_energy(dims, rho, cl, cv, 0.2, S) <= oracle.ms_energy(dims, rho, *c0, 0.2, S1)
+    assert np.array_equal(S, clean)
+    assert cl == pytest.approx(rho[clean == 0].mean(), rel=1e-12)
+    assert cv == pytest.approx(rho[clean == 1].mean(), rel=1e-12)
+
