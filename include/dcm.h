@@ -297,6 +297,22 @@ int dcm_ensemble_energy_virial(dcm_handle *h, int k, double *pe, double *ke,
 int dcm_remove_small_components(dcm_handle *h, uint8_t *labels, int32_t min_voxels, int mem,
                                 int64_t *flipped);
 
+/* Eq. 13 (two-phase piecewise-constant Mumford-Shah) with fixed densities
+ * on an image of system 0's voxel grid (diagnostics and tests; the detection
+ * itself labels by K-means): rho (double[nvox], layout of dcm_get_grid, host
+ * or device per mem) is segmented by minimising
+ *   sum_liquid (rho - c_l)^2 + sum_vapor (rho - c_v)^2 + nu x (number of
+ *   periodic grid faces between a liquid and a vapor voxel)
+ * through the convex relaxation of Chan, Esedoglu and Nikolova, solved by
+ * `iters` Chambolle-Pock iterations (tau 1/4, sigma 1/3) from u = 1/2;
+ * labels (uint8[nvox]) = 0 where the relaxed u > 1/2, else 1; u_out
+ * (nullable, double[nvox]) receives u.  FP64 in a fixed operation order.
+ * Allocates and frees its scratch (7 doubles per voxel) and synchronises.
+ * Errors: DCM_ERR_ARG (null pointers, nu < 0, iters < 0), DCM_ERR_STATE
+ * (during stream capture), DCM_ERR_OOM, DCM_ERR_CUDA. */
+int dcm_ms_segment(dcm_handle *h, const double *rho, double c_l, double c_v, double nu,
+                   int32_t iters, uint8_t *labels, double *u_out, int mem);
+
 /* Waits for the handle's stream; returns the sticky device error, if any. */
 int dcm_sync(dcm_handle *h);
 /* Failure-detection self-check (no counterpart in the thesis): launches the

@@ -35,7 +35,7 @@ EXPORTS = [
     "dcm_set_timing", "dcm_get_phase_times", "dcm_ensemble_create", "dcm_system_count",
     "dcm_system_range", "dcm_ensemble_set_state", "dcm_ensemble_get_state",
     "dcm_ensemble_energy_virial", "dcm_check_bounded_wait", "dcm_cell_sort_noalloc",
-    "dcm_remove_small_components",
+    "dcm_remove_small_components", "dcm_ms_segment",
 ]
 DCM_NUM_PHASES = 5
 PHASES = ("kick_drift", "detect", "bin", "force", "kick")
@@ -108,6 +108,8 @@ def lib() -> C.CDLL:
         "dcm_energy_virial": (C.c_int, [vp, dp, dp, dp]),
         "dcm_get_grid": (C.c_int, [vp, dp, dp, dp, dp, dp]),
         "dcm_remove_small_components": (C.c_int, [vp, dp, i32, C.c_int, P(i64)]),
+        "dcm_ms_segment": (C.c_int, [vp, dp, C.c_double, C.c_double, C.c_double, i32, dp, dp,
+                                     C.c_int]),
         "dcm_get_cutoffs": (C.c_int, [vp, dp, dp, dp]),
         "dcm_get_cells": (C.c_int, [vp, dp, dp, dp]),
         "dcm_get_pair_counts": (C.c_int, [vp, dp]),
@@ -252,6 +254,22 @@ def dcm_remove_small_components(h, labels, min_voxels: int):
     fl = C.c_int64(0)
     check(lib().dcm_remove_small_components(h, p, int(min_voxels), mem, C.byref(fl)))
     return labels, int(fl.value)
+
+
+def dcm_ms_segment(h, rho, c_l: float, c_v: float, nu: float, iters: int):
+    """Eq. 13 with fixed densities on an image of system 0's grid (numpy);
+    returns (labels, relaxed u)"""
+    dims = np.zeros(3, np.int32)
+    check(lib().dcm_get_grid(h, _ptr(dims)[0], None, None, None, None))
+    nv = int(np.prod(dims))
+    rho = np.ascontiguousarray(rho, dtype=np.float64).ravel()
+    if rho.size != nv:
+        raise ValueError(f"image holds {rho.size} voxels, the grid {nv}")
+    lab = np.empty(nv, np.uint8)
+    u = np.empty(nv)
+    check(lib().dcm_ms_segment(h, _ptr(rho)[0], float(c_l), float(c_v), float(nu), int(iters),
+                               _ptr(lab)[0], _ptr(u)[0], DCM_HOST))
+    return lab, u
 
 
 def dcm_get_cutoffs(h, n: int):
@@ -438,6 +456,9 @@ class System:
 
     def remove_small_components(self, labels, min_voxels: int):
         return dcm_remove_small_components(self.h, labels, min_voxels)
+
+    def ms_segment(self, rho, c_l, c_v, nu, iters):
+        return dcm_ms_segment(self.h, rho, c_l, c_v, nu, iters)
 
     def cutoffs(self):
         return dcm_get_cutoffs(self.h, self.n)
