@@ -175,13 +175,15 @@ extern "C" int dcm_cell_sort_noalloc(const double *x, int64_t n, const dcm_box *
     na::Args a;
     for (int d = 0; d < 3; ++d) {
         if (!(L[d] > 0) || nc[d] < 1) return fail(DCM_ERR_ARG, "box edges and cell counts must be positive");
+        // each factor and each partial product stays within the limit, so
+        // the product never wraps (three int32 counts can exceed int64)
+        if ((int64_t)nc[d] > na::MAX_CELLS || ncell * (int64_t)nc[d] > na::MAX_CELLS)
+            return fail(DCM_ERR_ARG, "cells %d x %d x %d exceed DCM_NOALLOC_MAX_CELLS = %lld",
+                        nc[0], nc[1], nc[2], (long long)na::MAX_CELLS);
         a.nc[d] = nc[d];
         a.inv_c[d] = (double)nc[d] / L[d];
         ncell *= nc[d];
     }
-    if (ncell > na::MAX_CELLS)
-        return fail(DCM_ERR_ARG, "%lld cells exceed DCM_NOALLOC_MAX_CELLS = %lld", (long long)ncell,
-                    (long long)na::MAX_CELLS);
     int32_t *scratch = nullptr;
     int rc = na::scratch_on_current_device(&scratch);
     if (rc) return rc;

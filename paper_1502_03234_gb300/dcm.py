@@ -23,6 +23,8 @@ DCM_HOST, DCM_DEVICE = 0, 1
 DCM_CUTOFF_EXP, DCM_CUTOFF_LINEAR = 0, 1
 DCM_MAX_CLASSES = 8
 DCM_WALK_WARP, DCM_WALK_LANES = 0, 1
+# limits of the allocation-free cell sort (include/dcm.h)
+DCM_NOALLOC_MAX_PARTICLES, DCM_NOALLOC_MAX_CELLS = 1 << 19, 1 << 20
 DCM_GRAPH_BRANCHED, DCM_GRAPH_FLAT = 0, 1
 
 #: every entry point include/dcm.h declares (checked by the ABI test)
@@ -303,13 +305,16 @@ def dcm_get_stats(h) -> dcm_stats:
 
 
 def dcm_set_tuning(h, lanes, block: int = 256, walk: int = None, list_lanes: int = 8) -> None:
+    """lanes/block: the FP64 lanes walk; list_lanes: lanes per particle of
+    the mixed-precision list force; walk None keeps the handle's walk"""
+    cur = dcm_get_tuning(h)
     t = dcm_tuning()
     for q in range(DCM_MAX_CLASSES):
         t.lanes[q] = int(lanes[min(q, len(lanes) - 1)])
     t.block = int(block)
-    t.walk = DCM_WALK_LANES if walk is None else int(walk)
+    t.walk = cur.walk if walk is None else int(walk)
     t.list_lanes = int(list_lanes)
-    t.step_graph = dcm_get_tuning(h).step_graph          # kept (see set_step_graph)
+    t.step_graph = cur.step_graph          # kept (see set_step_graph)
     check(lib().dcm_set_tuning(h, C.byref(t)))
 
 
@@ -343,10 +348,33 @@ def dcm_estimate_bytes(box, n: int, params: dcm_params | None = None) -> int:
     return int(lib().dcm_estimate_bytes(C.byref(b), int(n), C.byref(p)))
 
 
+def _check_device_tensor(t, name: str, dtype: str, count: int) -> None:
+    # the C side sees only pointers: a buffer of the wrong type, place or
+    # length would be written out of bounds on the GPU
+    if not (hasattr(t, "is_cuda") and t.is_cuda):
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if str(t.dtype) != f"torch.{dtype}":
+        raise ValueError(f"{name} must be {dtype}, not {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.numel() < count:
+        raise ValueError(f"{name} holds {t.numel()} elements, needs at least {count}")
+
+
 def dcm_cell_sort_noalloc(x_dev, n: int, box, nc, cell_start_dev, sorted_id_dev,
                           stream=None) -> None:
     """Allocation-free link-cell sort on device buffers (torch CUDA tensors:
     x float64 [n, 3], cell_start int32 [ncell + 1], sorted_id int32 [n])."""
+    n = int(n)
+    if len(nc) != 3 or min(int(q) for q in nc) < 1:
+        raise ValueError("nc must be three positive cell counts")
+    ncell = int(np.prod([int(q) for q in nc], dtype=object))
+    if 1 <= n <= DCM_NOALLOC_MAX_PARTICLES and ncell <= DCM_NOALLOC_MAX_CELLS:
+        # (sizes beyond the scratch limits are left to the library, which
+        # rejects them before any launch)
+        _check_device_tensor(x_dev, "x", "float64", 3 * n)
+        _check_device_tensor(cell_start_dev, "cell_start", "int32", ncell + 1)
+        _check_device_tensor(sorted_id_dev, "sorted_id", "int32", n)
     b = dcm_box(*box)
     ncv = (C.c_int32 * 3)(*[int(q) for q in nc])
     s = C.c_void_p(stream) if stream else None
@@ -473,7 +501,10 @@ class System:
         return dcm_get_stats(self.h)
 
     def set_tuning(self, lanes, block=256, walk=None, list_lanes=8):
-        """lanes/block select the lanes walk unless walk=DCM_WALK_WARP"""
+        """lanes/block: the FP64 lanes walk (lanes per particle per cutoff
+        class, threads per block); list_lanes: lanes per particle of the
+        mixed-precision Verlet-list force; walk None keeps the current walk
+        (DCM_MIXED always runs the warp kernels)"""
         dcm_set_tuning(self.h, lanes, block, walk, list_lanes)
 
     def set_step_graph(self, shape: int):

@@ -74,3 +74,63 @@ def test_component_and_cutoff_parameters_without_gpu(libdcm):
     assert dcm.dcm_estimate_bytes(box, 262144, dcm.default_params(min_component_voxels=-1)) == -1
     assert dcm.dcm_estimate_bytes(box, 262144, dcm.default_params(cutoff_fn=2)) == -1
     assert "cutoff_fn" in dcm.lib().dcm_last_error().decode()
+
+
+def test_noalloc_sort_rejects_wrapping_cell_counts_without_gpu(libdcm):
+    # three int32 cell counts whose product wraps int64 (2^21 * 2^21 * 2^22 =
+    # 2^64 -> 0) or exceeds the fixed scratch are refused before any device
+    # call: nothing is launched, the status is DCM_ERR_ARG
+    from paper_1502_03234_gb300 import dcm
+
+    f = dcm.lib().dcm_cell_sort_noalloc
+    x = (ctypes.c_double * 3)()
+    out = (ctypes.c_int32 * 4)()
+    box = dcm.dcm_box(30.0, 30.0, 120.0)
+    for nc in ((1 << 21, 1 << 21, 1 << 22), (1 << 20, 1 << 20, 1 << 23), (1 << 21, 1, 1),
+               (1024, 1024, 2), (0x7fffffff, 0x7fffffff, 0x7fffffff)):
+        ncv = (ctypes.c_int32 * 3)(*nc)
+        rc = f(ctypes.cast(x, ctypes.c_void_p), 1, ctypes.byref(box), ncv,
+               ctypes.cast(out, ctypes.c_void_p), ctypes.cast(out, ctypes.c_void_p), None)
+        assert rc == dcm.DCM_ERR_ARG, nc
+        assert "DCM_NOALLOC_MAX_CELLS" in dcm.lib().dcm_last_error().decode()
+
+
+def test_noalloc_sort_binding_checks_buffers_without_gpu():
+    # the binding refuses buffers of the wrong place, type, layout or length
+    # (the library sees only pointers)
+    torch = pytest.importorskip("torch")
+    from paper_1502_03234_gb300 import dcm
+
+    n, nc = 100, (4, 4, 16)
+    box = (6.0, 6.0, 24.0)
+    x = torch.zeros((n, 3), dtype=torch.float64)
+    cs = torch.zeros(257, dtype=torch.int32)
+    sid = torch.zeros(n, dtype=torch.int32)
+    with pytest.raises(ValueError, match="CUDA"):
+        dcm.dcm_cell_sort_noalloc(x, n, box, nc, cs, sid)
+    with pytest.raises(ValueError, match="positive"):
+        dcm.dcm_cell_sort_noalloc(x, n, box, (4, 0, 16), cs, sid)
+
+    class FakeCuda:
+        # stands in for a CUDA tensor's metadata; never reaches the library
+        def __init__(self, dtype, numel, contiguous=True):
+            self.is_cuda, self.dtype, self._n, self._c = True, dtype, numel, contiguous
+
+        def numel(self):
+            return self._n
+
+        def is_contiguous(self):
+            return self._c
+
+    good = (FakeCuda(torch.float64, 3 * n), FakeCuda(torch.int32, 257), FakeCuda(torch.int32, n))
+    bad_cases = [
+        ((FakeCuda(torch.float32, 3 * n),) + good[1:], "float64"),
+        ((FakeCuda(torch.float64, 3 * n - 1),) + good[1:], "at least"),
+        ((good[0], FakeCuda(torch.int32, 256), good[2]), "at least"),
+        ((good[0], FakeCuda(torch.int64, 257), good[2]), "int32"),
+        ((good[0], good[1], FakeCuda(torch.int32, n - 1)), "at least"),
+        ((good[0], good[1], FakeCuda(torch.int32, n, contiguous=False)), "contiguous"),
+    ]
+    for (xb, cb, sb), msg in bad_cases:
+        with pytest.raises(ValueError, match=msg):
+            dcm.dcm_cell_sort_noalloc(xb, n, box, nc, cb, sb)

@@ -44,4 +44,8 @@ def test_noalloc_cell_sort_matches_handle_path_on_two_calls():
     with pytest.raises(dcm.DcmError) as e:
         dcm.dcm_cell_sort_noalloc(xd, n, s.box, (1024, 1024, 2), cs, sid)
     assert e.value.code == dcm.DCM_ERR_ARG
+    # cell counts whose product wraps a 64-bit integer to 0
+    with pytest.raises(dcm.DcmError) as e:
+        dcm.dcm_cell_sort_noalloc(xd, n, s.box, (1 << 21, 1 << 21, 1 << 22), cs, sid)
+    assert e.value.code == dcm.DCM_ERR_ARG
     del big
