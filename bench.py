@@ -127,9 +127,6 @@ def workload_config(n, precision):
 def force_kernel_name(dcm, sy, prec, skin):
     if prec != dcm.DCM_MIXED:
         return "k_force (fp64)"
-    walk = dcm.dcm_get_tuning(sy.h).walk
-    if walk != dcm.DCM_WALK_WARP:
-        return "k_force lanes walk (mixed)"
     return "k_force_list_warp + k_force_warp (mixed, Verlet lists)" if skin > 0 else "k_force_warp (mixed)"
 
 

@@ -56,8 +56,13 @@ enum dcm_status {
 };
 
 enum { DCM_FP64 = 0,   /* FP64 pair distances, forces and accumulation */
-       DCM_MIXED = 1   /* FP32 pair distances and forces, extended-precision
-                          (2 x FP32) accumulation, FP64 state and reductions */
+       DCM_MIXED = 1   /* FP32 pair distances and forces for pairs beyond
+                          1.5 sigma; closer pairs in double-float (2 x FP32)
+                          arithmetic from the exact displacement; exact
+                          fixed-point sums of the lane partials; FP64 state,
+                          integration and reductions.  Per-particle forces
+                          meet |F - F_FP64| <= 1e-6 + 1e-5 |F| for liquid
+                          states with link cells up to about 2 sigma. */
 };
 enum { DCM_HOST = 0, DCM_DEVICE = 1 };
 enum { DCM_CUTOFF_EXP = 0, DCM_CUTOFF_LINEAR = 1 };
@@ -98,7 +103,7 @@ typedef struct {
        4 pi (r_c,min + skin)^3) entries) below 2^31 entries; dcm_create
        returns DCM_ERR_ARG otherwise. */
     double skin;
-    /* Verlet lists built by the warp walk (DCM_MIXED, DCM_WALK_WARP): each
+    /* Verlet lists built by the warp walk (DCM_MIXED): each
        particle's entry capacity is list_density x (4/3) pi R^3 + 8,
        rounded up to a multiple of 8, for its list radius R; <= 0: 1.0 per
        sigma^3.  A list that would overflow leaves that step's forces to the
@@ -136,9 +141,11 @@ typedef struct {
 } dcm_params;
 
 /* Force walk variants (dcm_tuning.walk).  DCM_WALK_WARP: one warp per
- * particle over its flattened candidate list (DCM_MIXED without Verlet
- * lists; other configurations use DCM_WALK_LANES whatever is set).
- * DCM_WALK_LANES: lanes[] lanes per particle walk its stencil rows. */
+ * particle over its flattened candidate list, and with Verlet lists the
+ * list force with list_lanes lanes per particle; DCM_MIXED always runs
+ * these kernels (dcm_set_tuning refuses DCM_WALK_LANES for it with
+ * DCM_ERR_ARG).  DCM_WALK_LANES: lanes[] lanes per particle walk its
+ * stencil rows; DCM_FP64 always runs this walk, whatever is set. */
 enum { DCM_WALK_WARP = 0, DCM_WALK_LANES = 1 };
 
 /* Shape of the CUDA graph of one step (dcm_tuning.step_graph).  With the

@@ -157,7 +157,6 @@ static int setup_geometry(const dcm_box *box, int64_t n, const dcm_params *p, Ge
         g.L[a] = L[a];
         g.halfL[a] = 0.5 * L[a];
         g.halfLf[a] = (float)g.halfL[a];
-        g.cf[a] = (float)g.cedge[a];
         g.inv_cf[a] = (float)g.inv_c[a];
         int gd = (int)floor(L[a] / p->voxel);
         g.gd[a] = gd < 3 ? 3 : gd;
@@ -213,6 +212,34 @@ static int setup_geometry(const dcm_box *box, int64_t n, const dcm_params *p, Ge
     g.eps48f = (float)g.eps48;
     g.eps2f = (float)g.eps2;
     g.sig2f = (float)g.sig2;
+    g.eps24l = (float)(g.eps24 - (double)g.eps24f);
+    g.eps48l = (float)(g.eps48 - (double)g.eps48f);
+    g.sig2l = (float)(g.sig2 - (double)g.sig2f);
+    // Mixed precision: pairs closer than 1.5 sigma, whose forces are large
+    // and change fast with r, take the double-float path.  The FP32
+    // cell-relative positions live on a grid qpos = 2^(e - 24) with 2^e above
+    // every coordinate (a cell edge plus the drift allowed between list
+    // builds), every coordinate difference and every close-pair distance,
+    // so these all have at most 24 significant bits and the FP32 differences
+    // and cell shifts of a close pair are exact.
+    const double rclose = 1.5 * p->sigma;
+    g.rclose2 = (float)(rclose * rclose);
+    // The FP32 error left by the pairs beyond r_close is a few 1e-6
+    // epsilon/sigma at liquid density; a particle whose net force is below
+    // 2 epsilon/sigma (where the tolerance 1e-6 + 1e-5 |F| falls under
+    // about 2e-5) has all its pairs evaluated again in double-float.
+    const double fredo = 2.0 * p->eps / p->sigma;
+    g.redo_f2 = (float)(fredo * fredo);
+    double cmax = fmax(g.cedge[0], fmax(g.cedge[1], g.cedge[2]));
+    double bound = fmax(cmax + g.skin, rclose) + 0.25;
+    int e = (int)ceil(log2(bound));
+    g.qpos = (float)ldexp(1.0, e - 24);
+    g.inv_qpos = (float)ldexp(1.0, 24 - e);
+    for (int a = 0; a < 3; ++a) {
+        double cq = nearbyint(g.cedge[a] * (double)g.inv_qpos) * (double)g.qpos;
+        g.cf[a] = (float)cq;   // exact: below 2^24 grid steps
+        g.cfl[a] = (float)(g.cedge[a] - cq);
+    }
     g.ncell = (int64_t)g.nc[0] * g.nc[1] * g.nc[2];
     g.nvox = (int64_t)g.gd[0] * g.gd[1] * g.gd[2];
     return DCM_OK;
@@ -260,7 +287,7 @@ static int64_t bytes_for(const Geom &g, int64_t n, int precision)
     int64_t ncell = g.ncell;
     int64_t nv = g.nvox;
     int64_t per_p = 3 * 8 * 3 + 8 + 8 + 1 + 4 * 3 + 16 + 4 + 4 + 8 + 48 + 24 + 2;
-    per_p += 36;   // spd (FP64) or rq + pk + inv (MIXED)
+    per_p += precision == DCM_FP64 ? 36 : 52;   // spd (FP64) or spl4 + rq + pk + inv (MIXED)
     int64_t per_v = 4 + 4 + 4 + 8 + 1 + 8 + 8 + 4 + 16 + 2 + (g.cc_min > 0 ? 20 : 0);
     int64_t ntiles = (ncell + 2047) / 2048 + 1;
     int64_t lists = g.skin > 0 ? 4 * list_cap(g, n) + n * (4 + 4 + 24 + 8 + 8 + 20) : 0;
@@ -297,7 +324,7 @@ extern "C" int dcm_destroy(dcm_handle *h)
     for (int q = 0; q <= DCM_NUM_PHASES; ++q)
         if (h->ev[q]) cudaEventDestroy(h->ev[q]);
     void *ptrs[] = {h->x, h->v, h->f, h->d, h->rc, h->cls, h->cell_of, h->slot, h->cell_count,
-                    h->cell_start, h->sorted_id, h->scan_tmp, h->sp4, h->spd, h->rq, h->pk, h->inv, h->psys, h->vsys, h->class_list,
+                    h->cell_start, h->sorted_id, h->scan_tmp, h->sp4, h->spl4, h->spd, h->rq, h->pk, h->inv, h->psys, h->vsys, h->class_list,
                     h->class_count_dev, h->B, h->sm1, h->sm2, h->Bs, h->S, h->D0, h->D1, h->stamp,
                     h->flist, h->fcount, h->kacc, h->npair, h->pe, h->vir, h->red_part, h->red_out,
                     h->err, h->stats, h->tmp3n, h->geo_dev, h->off_dev, h->nl, h->nl_cnt,
@@ -435,6 +462,7 @@ static int create_systems(int M, const dcm_box *boxes, const int64_t *ns, const 
         ALLOC(h->vsys, nv);
     }
     if (h->p.precision != DCM_FP64) {
+        ALLOC(h->spl4, N);
         ALLOC(h->rq, N);
         ALLOC(h->pk, N);
         ALLOC(h->inv, N);
@@ -1156,6 +1184,8 @@ extern "C" int dcm_set_tuning(dcm_handle *h, const dcm_tuning *t)
         return fail(DCM_ERR_ARG, "block must be a multiple of 32 in 64..256");
     if (t->walk != DCM_WALK_WARP && t->walk != DCM_WALK_LANES)
         return fail(DCM_ERR_ARG, "walk must be DCM_WALK_WARP or DCM_WALK_LANES");
+    if (t->walk == DCM_WALK_LANES && h->p.precision == DCM_MIXED)
+        return fail(DCM_ERR_ARG, "DCM_WALK_LANES is the FP64 walk; DCM_MIXED runs the warp kernels");
     if (t->list_lanes != 0 && t->list_lanes != 4 && t->list_lanes != 8 && t->list_lanes != 16 &&
         t->list_lanes != 32)
         return fail(DCM_ERR_ARG, "list_lanes must be 4, 8, 16 or 32 (0: 8)");

@@ -123,11 +123,13 @@ __global__ void k_cell_sort(int64_t ncell, const int32_t *__restrict__ start, in
 }
 
 // sorted position streams: sp4 = (x - cell corner in FP32, cell x index),
-// spd = absolute FP64 position (FP64 path only)
+// spl4 = its FP32 remainder (mixed path), spd = absolute FP64 position (FP64
+// path only)
 __global__ void k_gather(Batch b, const double *__restrict__ x, const double *__restrict__ v,
                          const double *__restrict__ f,
                          const int32_t *__restrict__ sorted_id,
-                         const int32_t *__restrict__ cell_of, float4 *sp4, double4_32a *spd,
+                         const int32_t *__restrict__ cell_of, float4 *sp4, float4 *spl4,
+                         double4_32a *spd,
                          const double *__restrict__ rc, float4 *rq, int4 *pk, float *sh,
                          const double *__restrict__ dist, int *lf, float delta, int32_t *capk,
                          int32_t *inv, const int *gate, int32_t *cell_count)
@@ -142,7 +144,9 @@ __global__ void k_gather(Batch b, const double *__restrict__ x, const double *__
     int i = sorted_id[k];
     int c = cell_of[i] - (int)g.c0;
     double px = x[i], py = x[(size_t)b.N + i], pz = x[2 * (size_t)b.N + i];
-    sp4[k] = cell_rel_position(b, g, px, py, pz, c);
+    float4 lo;
+    sp4[k] = cell_rel_position(b, g, px, py, pz, c, lo);
+    if (spl4) spl4[k] = lo;
     if (spd) spd[k] = make_double4_32a(px, py, pz, 0.0);
     if (inv) inv[i] = (int32_t)k;
     if (rq) {
@@ -268,6 +272,7 @@ int launch_sort_gather(dcm_handle *h, const int *gate)
     k_cell_sort<<<nblk(h->ncell, 256), 256, 0, s>>>(h->ncell, h->cell_start, h->sorted_id, gate);
     const bool wl = h->nl && h->list_warp;
     k_gather<<<nblk(n, 256), 256, 0, s>>>(h->b, h->x, h->v, h->f, h->sorted_id, h->cell_of, h->sp4,
+                                          h->spl4,
                                           h->p.precision == DCM_FP64 ? h->spd : nullptr, h->rc,
                                           h->rq, h->pk, h->sh, h->d, h->lflags,
                                           h->cut_detected ? h->list_margin : 0.0f, wl ? h->nl_cnt : nullptr,

@@ -260,10 +260,16 @@ __device__ __forceinline__ float skin_share(const Geom &g, float speed, float fo
 // Verlet-list builds) is folded back next to that cell.  Shared by the
 // gather kernel and the drift, which must produce the same bits.  The
 // corner coordinates c * L/n come from a table (the same rounded products
-// as computing them here), which keeps this to one FP64 subtraction and one
-// conversion per axis: the FP64 pipe runs at 1/64 of the FP32 rate.
+// as computing them here), which keeps this to a few FP64 operations per
+// axis: the FP64 pipe runs at 1/64 of the FP32 rate.
+// The FP32 coordinate is a multiple of the system's grid qpos (a power of
+// two chosen so that coordinates, their differences and the cell shifts
+// have at most 24 significant bits), and lo receives the FP32 remainder
+// u - hi: the difference of two particles' coordinates and the cell shift
+// are then exact in FP32, and hi + lo carries the FP64 position to about
+// 2^-47 for the double-float close-pair forces.
 __device__ __forceinline__ float4 cell_rel_position(const Batch &b, const Geom &g, double px,
-                                                   double py, double pz, int c_local)
+                                                   double py, double pz, int c_local, float4 &lo)
 {
     int cx = c_local % g.nc[0];
     int cy = (c_local / g.nc[0]) % g.nc[1];
@@ -271,15 +277,23 @@ __device__ __forceinline__ float4 cell_rel_position(const Batch &b, const Geom &
     const double *corner = b.corner + g.corner_off;
     const double p[3] = {px, py, pz};
     const int c[3] = {cx, g.nc[0] + cy, g.nc[0] + g.nc[1] + cz};
-    float uf[3];
+    float uf[3], ul[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const double u = DSUB(p[a], corner[c[a]]);
+        double u = DSUB(p[a], corner[c[a]]);
         float f = (float)u;
-        if (f > g.halfLf[a]) f = (float)DSUB(u, g.L[a]);
-        else if (f < -g.halfLf[a]) f = (float)DADD(u, g.L[a]);
-        uf[a] = f;
+        if (f > g.halfLf[a]) {
+            u = DSUB(u, g.L[a]);
+            f = (float)u;
+        } else if (f < -g.halfLf[a]) {
+            u = DADD(u, g.L[a]);
+            f = (float)u;
+        }
+        const float q = __fmul_rn(rintf(__fmul_rn(f, g.inv_qpos)), g.qpos);   // exact scalings
+        uf[a] = q;
+        ul[a] = (float)DSUB(u, (double)q);
     }
+    lo = make_float4(ul[0], ul[1], ul[2], 0.f);
     return make_float4(uf[0], uf[1], uf[2], (float)cx);
 }
 

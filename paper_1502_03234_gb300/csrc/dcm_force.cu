@@ -10,22 +10,25 @@
 //    is contiguous in the sorted arrays.  Rows whose y/z box distance
 //    exceeds r_c[i] are skipped and each row is trimmed in x to the chord of
 //    the cutoff sphere, so the candidates approach the sphere volume.
-//  * G lanes (1..32, per cutoff class) share one particle and stride through
-//    the row, so loads of the sorted float4 stream are coalesced; a shuffle
-//    tree combines the G partial sums.
+//  * DCM_FP64 (the lanes walk, k_force): G lanes (1..32, per cutoff class)
+//    share one particle and stride through the row, so loads of the sorted
+//    double stream are coalesced; a shuffle tree combines the G partial
+//    sums.  Absolute FP64 positions, minimum image and r^2 evaluated exactly
+//    as the FP64 definition; FP64 forces and accumulation.
 //  * Work is handed out warp by warp from a device queue ordered from the
 //    largest-cutoff class down (the GPU analogue of the thesis's
 //    schedule(dynamic,20), Algorithm 5.1): interfacial particles, whose
 //    cutoff makes them 8-13x more expensive, start first and the cheap bulk
 //    fills in behind them.
-//  * DCM_MIXED: positions are stored relative to their cell corner in FP32,
-//    so pair distances carry ~1e-7 absolute error instead of the ~1e-5 of
-//    absolute FP32 coordinates; forces are computed in FP32 and folded
-//    into a 2 x FP32 (TwoSum) accumulator per row; pairs whose r^2 is
-//    within a relative 2^-18 of r_c^2 are re-decided in FP64 with the exact
-//    FP64 rule, so the set of interacting pairs is the same as in FP64.
-//  * DCM_FP64: absolute FP64 positions, minimum image and r^2 evaluated
-//    exactly as the FP64 definition; FP64 forces and accumulation.
+//  * DCM_MIXED (the warp kernels: direct walk k_force_warp, Verlet-list
+//    force k_force_list_warp): positions are stored relative to their cell
+//    corner in FP32 on a power-of-two grid, with their FP32 remainders
+//    beside them.  Pair distances and forces are FP32 for pairs beyond
+//    1.5 sigma; closer pairs, whose forces are large and cancel in the sum,
+//    are evaluated in double-float arithmetic from the exact displacement.
+//    Lane partials are summed exactly in fixed point.  Pairs whose FP32 r^2
+//    is within a relative 2^-18 of r_c^2 are re-decided in FP64 with the
+//    exact FP64 rule, so the set of interacting pairs is the same as in FP64.
 // Bound: FP32 pipe (mixed) or FP64 pipe (FP64); algorithmic work per
 // in-cutoff pair = 8 flops for the distance test + 16 for the force.
 #include "dcm_device.cuh"
@@ -37,8 +40,9 @@ constexpr float GUARD = 3.814697265625e-06f;   // 2^-18
 
 // the cell and LJ constants of a single-system launch (kernel parameters)
 struct ListConst {
-    float cf[3], ncx, halfnc;
+    float cf[3], cfl[3], ncx, halfnc;
     float sig2f, eps48f, eps24f, eps2f;
+    float sig2l, eps48l, eps24l, rclose2, redo_f2;
 };
 
 struct ForceArgs {
@@ -47,6 +51,7 @@ struct ForceArgs {
     const int32_t *class_list;    // sorted slots grouped by class
     int lanes[DCM_MAX_CLASSES];   // lanes per particle per class
     const float4 *sp4;
+    const float4 *spl4;           // MIXED: remainders of the cell-relative positions
     const double4_32a *spd;
     const float4 *rq;             // MIXED: r_c^2, guard band, culling radius per slot
     const int4 *pk;               // MIXED: id, cell y, cell z per slot
@@ -89,109 +94,41 @@ __device__ __forceinline__ bool fp64_inside(const ForceArgs &a, const Geom &g, i
     return r2_rn(dx, dy, dz) < rci2;
 }
 
-template <int PREC, bool ENERGY>
-struct Acc;
-
+// per-lane FP64 sums of one particle (the lanes walk of the FP64 path)
 template <bool ENERGY>
-struct Acc<DCM_MIXED, ENERGY> {
-    float hx = 0.f, lx = 0.f, hy = 0.f, ly = 0.f, hz = 0.f, lz = 0.f;   // 2xFP32 totals
-    float rx = 0.f, ry = 0.f, rz = 0.f;                                 // row partials
-    float pe = 0.f, v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    __device__ __forceinline__ void fold()
-    {
-        ff_add(hx, lx, rx);
-        ff_add(hy, ly, ry);
-        ff_add(hz, lz, rz);
-        rx = ry = rz = 0.f;
-    }
-};
-
-template <bool ENERGY>
-struct Acc<DCM_FP64, ENERGY> {
+struct Acc64 {
     double fx = 0.0, fy = 0.0, fz = 0.0, pe = 0.0;
     double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    __device__ __forceinline__ void fold() {}
 };
 
-template <int PREC, bool ENERGY>
-__device__ __forceinline__ void row_segment(const ForceArgs &a, const Geom &g, int k, int i,
-                                            int lane, int G,
-                                            int j0, int j1, float ax, float ay, float az,
-                                            float4 ui, double4_32a pi, float rc2f, float rc2lo,
-                                            float rc2hi, double rci2, Acc<PREC, ENERGY> &acc,
-                                            int &np, int &ng)
+// one FP64 pair (the definition's arithmetic: minimum image, r^2, the
+// strict test against r_c[i]^2)
+template <bool ENERGY>
+__device__ __forceinline__ void pair64(const Geom &g, double4_32a pi, double4_32a pj, double rci2,
+                                       bool self, Acc64<ENERGY> &acc, int &np)
 {
-    if constexpr (PREC == DCM_MIXED) {
-        // one candidate: FP32 distance on cell-relative coordinates
-        auto pair = [&](int j, float4 uj) {
-            float dx = fmaf(ax - uj.w, g.cf[0], ui.x - uj.x);
-            float dy = ay - uj.y;
-            float dz = az - uj.z;
-            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            if (r2 < rc2hi && j != k) {
-                bool in = r2 < rc2f;
-                if (r2 >= rc2lo) {
-                    in = fp64_inside(a, g, i, a.sorted_id[j], rci2);
-                    ++ng;
-                }
-                if (in) {
-                    float r2inv = rcp_approx(r2);
-                    float sr2 = g.sig2f * r2inv;
-                    float sr6 = sr2 * sr2 * sr2;
-                    float fr = r2inv * sr6 * fmaf(g.eps48f, sr6, -g.eps24f);
-                    acc.rx = fmaf(fr, dx, acc.rx);
-                    acc.ry = fmaf(fr, dy, acc.ry);
-                    acc.rz = fmaf(fr, dz, acc.rz);
-                    ++np;
-                    if constexpr (ENERGY) {
-                        acc.pe = fmaf(g.eps2f * sr6, sr6 - 1.f, acc.pe);
-                        float fx = fr * dx, fy = fr * dy, fz = fr * dz;
-                        acc.v[0] = fmaf(0.5f * dx, fx, acc.v[0]);
-                        acc.v[1] = fmaf(0.5f * dy, fy, acc.v[1]);
-                        acc.v[2] = fmaf(0.5f * dz, fz, acc.v[2]);
-                        acc.v[3] = fmaf(0.5f * dx, fy, acc.v[3]);
-                        acc.v[4] = fmaf(0.5f * dx, fz, acc.v[4]);
-                        acc.v[5] = fmaf(0.5f * dy, fz, acc.v[5]);
-                    }
-                }
-            }
-        };
-        int j = j0 + lane;
-        // two independent loads in flight before any arithmetic
-        for (; j + G < j1; j += 2 * G) {
-            float4 u0 = a.sp4[j], u1 = a.sp4[j + G];
-            pair(j, u0);
-            pair(j + G, u1);
-        }
-        for (; j < j1; j += G) pair(j, a.sp4[j]);
-        acc.fold();
-    } else {
-        for (int j = j0 + lane; j < j1; j += G) {
-            double4_32a pj = a.spd[j];
-            double dx = min_image(DSUB(pi.x, pj.x), g.L[0], g.halfL[0]);
-            double dy = min_image(DSUB(pi.y, pj.y), g.L[1], g.halfL[1]);
-            double dz = min_image(DSUB(pi.z, pj.z), g.L[2], g.halfL[2]);
-            double r2 = r2_rn(dx, dy, dz);
-            if (r2 < rci2 && j != k) {
-                double r2inv = 1.0 / r2;
-                double sr2 = g.sig2 * r2inv;
-                double sr6 = sr2 * sr2 * sr2;
-                double fr = r2inv * sr6 * (g.eps48 * sr6 - g.eps24);
-                acc.fx += fr * dx;
-                acc.fy += fr * dy;
-                acc.fz += fr * dz;
-                ++np;
-                if constexpr (ENERGY) {
-                    acc.pe += g.eps2 * sr6 * (sr6 - 1.0);
-                    double fx = fr * dx, fy = fr * dy, fz = fr * dz;
-                    acc.v[0] += 0.5 * dx * fx;
-                    acc.v[1] += 0.5 * dy * fy;
-                    acc.v[2] += 0.5 * dz * fz;
-                    acc.v[3] += 0.5 * dx * fy;
-                    acc.v[4] += 0.5 * dx * fz;
-                    acc.v[5] += 0.5 * dy * fz;
-                }
-            }
+    double dx = min_image(DSUB(pi.x, pj.x), g.L[0], g.halfL[0]);
+    double dy = min_image(DSUB(pi.y, pj.y), g.L[1], g.halfL[1]);
+    double dz = min_image(DSUB(pi.z, pj.z), g.L[2], g.halfL[2]);
+    double r2 = r2_rn(dx, dy, dz);
+    if (r2 < rci2 && !self) {
+        double r2inv = 1.0 / r2;
+        double sr2 = g.sig2 * r2inv;
+        double sr6 = sr2 * sr2 * sr2;
+        double fr = r2inv * sr6 * (g.eps48 * sr6 - g.eps24);
+        acc.fx += fr * dx;
+        acc.fy += fr * dy;
+        acc.fz += fr * dz;
+        ++np;
+        if constexpr (ENERGY) {
+            acc.pe += g.eps2 * sr6 * (sr6 - 1.0);
+            double fx = fr * dx, fy = fr * dy, fz = fr * dz;
+            acc.v[0] += 0.5 * dx * fx;
+            acc.v[1] += 0.5 * dy * fy;
+            acc.v[2] += 0.5 * dz * fz;
+            acc.v[3] += 0.5 * dx * fy;
+            acc.v[4] += 0.5 * dx * fz;
+            acc.v[5] += 0.5 * dy * fz;
         }
     }
 }
@@ -204,21 +141,12 @@ __device__ __forceinline__ float box_gap(int d, float u, float c)
     return gap > 0.f ? gap : 0.f;
 }
 
-template <int PREC, bool ENERGY>
-__device__ __forceinline__ void reduce_and_store(const ForceArgs &a, Acc<PREC, ENERGY> &acc, int i,
+template <bool ENERGY>
+__device__ __forceinline__ void reduce_and_store(const ForceArgs &a, Acc64<ENERGY> &acc, int i,
                                                  int lane, int G, unsigned gmask, int np)
 {
     // combine the G lanes of this particle
-    double fx, fy, fz, pe = 0.0, vir[6] = {0, 0, 0, 0, 0, 0};
-    if constexpr (PREC == DCM_MIXED) {
-        fx = (double)acc.hx + (double)acc.lx;
-        fy = (double)acc.hy + (double)acc.ly;
-        fz = (double)acc.hz + (double)acc.lz;
-    } else {
-        fx = acc.fx;
-        fy = acc.fy;
-        fz = acc.fz;
-    }
+    double fx = acc.fx, fy = acc.fy, fz = acc.fz, pe = 0.0, vir[6] = {0, 0, 0, 0, 0, 0};
     if constexpr (ENERGY) {
         pe = acc.pe;
         for (int q = 0; q < 6; ++q) vir[q] = acc.v[q];
@@ -246,8 +174,11 @@ __device__ __forceinline__ void reduce_and_store(const ForceArgs &a, Acc<PREC, E
     }
 }
 
-
-template <int PREC, bool ENERGY>
+// FP64 lanes walk of particle k (sorted slot): G lanes stride through each
+// stencil row; rows beyond r_c[i] are skipped and each row is trimmed in x
+// to the chord of the cutoff sphere (FP32 geometry on the cell-relative
+// positions, conservative by the culling margin)
+template <bool ENERGY>
 __device__ __forceinline__ void particle_force(const ForceArgs &a, int k, int lane, int G, unsigned gmask, int &ng)
 {
     const Geom &g = a.b.sys[sys_p(a.b, k)];
@@ -259,32 +190,30 @@ __device__ __forceinline__ void particle_force(const ForceArgs &a, int k, int la
     int cz = c / (g.nc[0] * g.nc[1]);
     double rci = a.rc[i];
     double rci2 = DMUL(rci, rci);
-    float rc2f = (float)rci2;
-    float rc2lo = rc2f * (1.f - GUARD), rc2hi = rc2f * (1.f + GUARD);
-    // conservative culling radius (covers FP32 geometry error and the guard)
+    // conservative culling radius (covers the FP32 geometry error)
     float rcull = fmaf((float)rci, 1.00002f, 1e-4f);
     float rcull2 = rcull * rcull;
     int sx = min(g.smax[0], (int)ceilf(rcull * g.inv_cf[0]));
     int sy = min(g.smax[1], (int)ceilf(rcull * g.inv_cf[1]));
     int sz = min(g.smax[2], (int)ceilf(rcull * g.inv_cf[2]));
-    double4_32a pi = make_double4_32a(0, 0, 0, 0);
-    if constexpr (PREC == DCM_FP64) pi = a.spd[k];
-    Acc<PREC, ENERGY> acc;
+    const double4_32a pi = a.spd[k];
+    Acc64<ENERGY> acc;
     int np = 0;
+    auto segment = [&](int j0, int j1) {
+        for (int j = j0 + lane; j < j1; j += G) pair64<ENERGY>(g, pi, a.spd[j], rci2, j == k, acc, np);
+    };
     for (int dz = -sz; dz <= sz; ++dz) {
         float gz = box_gap(dz, ui.z, g.cf[2]);
         float remz = fmaf(-gz, gz, rcull2);
         if (remz < 0.f) continue;
         int czz = cz + dz;
         czz += czz < 0 ? g.nc[2] : (czz >= g.nc[2] ? -g.nc[2] : 0);
-        float az = fmaf(-(float)dz, g.cf[2], ui.z);
         for (int dy = -sy; dy <= sy; ++dy) {
             float gy = box_gap(dy, ui.y, g.cf[1]);
             float w2 = fmaf(-gy, gy, remz);
             if (w2 < 0.f) continue;
             int cyy = cy + dy;
             cyy += cyy < 0 ? g.nc[1] : (cyy >= g.nc[1] ? -g.nc[1] : 0);
-            float ay = fmaf(-(float)dy, g.cf[1], ui.y);
             float w = sqrtf(w2);
             int xlo = max(-sx, (int)floorf((ui.x - w) * g.inv_cf[0]));
             int xhi = min(sx, (int)floorf((ui.x + w) * g.inv_cf[0]));
@@ -292,133 +221,42 @@ __device__ __forceinline__ void particle_force(const ForceArgs &a, int k, int la
             int lo = cx + xlo, hi = cx + xhi;
             if (lo < 0) {
                 // cells at the top end seen through the x = 0 face
-                row_segment<PREC, ENERGY>(a, g, k, i, lane, G, a.cell_start[row + lo + g.nc[0]],
-                                          a.cell_start[row + g.nc[0]], (float)(cx + g.nc[0]), ay,
-                                          az, ui, pi, rc2f, rc2lo, rc2hi, rci2, acc, np, ng);
+                segment(a.cell_start[row + lo + g.nc[0]], a.cell_start[row + g.nc[0]]);
                 lo = 0;
             }
             if (hi >= g.nc[0]) {
-                row_segment<PREC, ENERGY>(a, g, k, i, lane, G, a.cell_start[row],
-                                          a.cell_start[row + hi - g.nc[0] + 1],
-                                          (float)(cx - g.nc[0]), ay, az, ui, pi, rc2f, rc2lo,
-                                          rc2hi, rci2, acc, np, ng);
+                segment(a.cell_start[row], a.cell_start[row + hi - g.nc[0] + 1]);
                 hi = g.nc[0] - 1;
             }
-            if (lo <= hi)
-                row_segment<PREC, ENERGY>(a, g, k, i, lane, G, a.cell_start[row + lo],
-                                          a.cell_start[row + hi + 1], (float)cx, ay, az, ui, pi,
-                                          rc2f, rc2lo, rc2hi, rci2, acc, np, ng);
+            if (lo <= hi) segment(a.cell_start[row + lo], a.cell_start[row + hi + 1]);
         }
     }
-    reduce_and_store<PREC, ENERGY>(a, acc, i, lane, G, gmask, np);
+    reduce_and_store<ENERGY>(a, acc, i, lane, G, gmask, np);
 }
 
 // Algorithm 3.2 over particle k's Verlet list (entries: sorted slot j,
-// cell row offsets dy, dz); same pair rule, same FP64 re-decision at the
-// cutoff edge, so the interacting pairs are those of the direct walk
-template <int PREC, bool ENERGY>
+// cell row offsets dy, dz) in FP64: the same pair rule, so the interacting
+// pairs are those of the direct walk
+template <bool ENERGY>
 __device__ __forceinline__ void particle_force_list(const ForceArgs &a, int k, int lane, int G,
                                                     unsigned gmask, int &ng)
 {
     const Geom &g = a.b.sys[sys_p(a.b, k)];
     int i = a.sorted_id[k];
-    float4 ui = a.sp4[k];
     double rci = a.rc[i];
     double rci2 = DMUL(rci, rci);
-    float rc2f = (float)rci2;
-    float rc2lo = rc2f * (1.f - GUARD), rc2hi = rc2f * (1.f + GUARD);
-    const float ncx = (float)g.nc[0], halfnc = 0.5f * (float)g.nc[0];
-    const float cx0 = g.cf[0], cy0 = g.cf[1], cz0 = g.cf[2];
-    double4_32a pi = make_double4_32a(0, 0, 0, 0);
-    if constexpr (PREC == DCM_FP64) pi = a.spd[k];
-    Acc<PREC, ENERGY> acc;
+    const double4_32a pi = a.spd[k];
+    Acc64<ENERGY> acc;
     int np = 0;
     const int e0 = a.nl_start[k], e1 = a.nl_start[k + 1];
-    auto one = [&](int e, float4 uj) {
-        int j = e & 0xffffff;
-        if constexpr (PREC == DCM_MIXED) {
-            float dyc = (float)(((e >> 24) & 15) - 8);
-            float dzc = (float)((int)((unsigned)e >> 28) - 8);
-            float dcx = ui.w - uj.w;
-            dcx -= dcx > halfnc ? ncx : 0.f;
-            dcx += dcx < -halfnc ? ncx : 0.f;
-            float dx = fmaf(dcx, cx0, ui.x - uj.x);
-            float dy = fmaf(-dyc, cy0, ui.y) - uj.y;
-            float dz = fmaf(-dzc, cz0, ui.z) - uj.z;
-            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            if (r2 < rc2hi) {
-                bool in = r2 < rc2f;
-                if (r2 >= rc2lo) {
-                    in = fp64_inside(a, g, i, a.sorted_id[j], rci2);
-                    ++ng;
-                }
-                if (in) {
-                    float r2inv = rcp_approx(r2);
-                    float sr2 = g.sig2f * r2inv;
-                    float sr6 = sr2 * sr2 * sr2;
-                    float fr = r2inv * sr6 * fmaf(g.eps48f, sr6, -g.eps24f);
-                    acc.rx = fmaf(fr, dx, acc.rx);
-                    acc.ry = fmaf(fr, dy, acc.ry);
-                    acc.rz = fmaf(fr, dz, acc.rz);
-                    ++np;
-                    if constexpr (ENERGY) {
-                        acc.pe = fmaf(g.eps2f * sr6, sr6 - 1.f, acc.pe);
-                        float fx = fr * dx, fy = fr * dy, fz = fr * dz;
-                        acc.v[0] = fmaf(0.5f * dx, fx, acc.v[0]);
-                        acc.v[1] = fmaf(0.5f * dy, fy, acc.v[1]);
-                        acc.v[2] = fmaf(0.5f * dz, fz, acc.v[2]);
-                        acc.v[3] = fmaf(0.5f * dx, fy, acc.v[3]);
-                        acc.v[4] = fmaf(0.5f * dx, fz, acc.v[4]);
-                        acc.v[5] = fmaf(0.5f * dy, fz, acc.v[5]);
-                    }
-                }
-            }
-        } else {
-            double4_32a pj = a.spd[j];
-            double dx = min_image(DSUB(pi.x, pj.x), g.L[0], g.halfL[0]);
-            double dy = min_image(DSUB(pi.y, pj.y), g.L[1], g.halfL[1]);
-            double dz = min_image(DSUB(pi.z, pj.z), g.L[2], g.halfL[2]);
-            double r2 = r2_rn(dx, dy, dz);
-            if (r2 < rci2) {
-                double r2inv = 1.0 / r2;
-                double sr2 = g.sig2 * r2inv;
-                double sr6 = sr2 * sr2 * sr2;
-                double fr = r2inv * sr6 * (g.eps48 * sr6 - g.eps24);
-                acc.fx += fr * dx;
-                acc.fy += fr * dy;
-                acc.fz += fr * dz;
-                ++np;
-                if constexpr (ENERGY) {
-                    acc.pe += g.eps2 * sr6 * (sr6 - 1.0);
-                    double fx = fr * dx, fy = fr * dy, fz = fr * dz;
-                    acc.v[0] += 0.5 * dx * fx;
-                    acc.v[1] += 0.5 * dy * fy;
-                    acc.v[2] += 0.5 * dz * fz;
-                    acc.v[3] += 0.5 * dx * fy;
-                    acc.v[4] += 0.5 * dx * fz;
-                    acc.v[5] += 0.5 * dy * fz;
-                }
-            }
-        }
-    };
     int p = e0 + lane;
-    constexpr bool MIX = PREC == DCM_MIXED;
     for (; p + G < e1; p += 2 * G) {
         int ea = a.nl[p], eb = a.nl[p + G];
-        float4 ua = MIX ? a.sp4[ea & 0xffffff] : make_float4(0, 0, 0, 0);
-        float4 ub = MIX ? a.sp4[eb & 0xffffff] : make_float4(0, 0, 0, 0);
-        one(ea, ua);
-        one(eb, ub);
-        if constexpr (MIX) {
-            if (((p - e0) & (64 * G - 1)) == 0) acc.fold();   // 2xFP32 fold every 64 pairs
-        }
+        pair64<ENERGY>(g, pi, a.spd[ea & 0xffffff], rci2, false, acc, np);
+        pair64<ENERGY>(g, pi, a.spd[eb & 0xffffff], rci2, false, acc, np);
     }
-    for (; p < e1; p += G) {
-        int ea = a.nl[p];
-        one(ea, MIX ? a.sp4[ea & 0xffffff] : make_float4(0, 0, 0, 0));
-    }
-    acc.fold();
-    reduce_and_store<PREC, ENERGY>(a, acc, i, lane, G, gmask, np);
+    for (; p < e1; p += G) pair64<ENERGY>(g, pi, a.spd[a.nl[p] & 0xffffff], rci2, false, acc, np);
+    reduce_and_store<ENERGY>(a, acc, i, lane, G, gmask, np);
 }
 
 // one particle of the list build: the direct row walk with radius
@@ -574,8 +412,8 @@ __global__ void __launch_bounds__(FORCE_THREADS, 3) k_list_walk(ForceArgs a)
     }
 }
 
-// persistent warps draining the class-ordered work queue
-template <int PREC, bool ENERGY>
+// persistent warps draining the class-ordered work queue (FP64 path)
+template <bool ENERGY>
 __global__ void __launch_bounds__(FORCE_THREADS, 3) k_force(ForceArgs a)
 {
     __shared__ int s_cnt[DCM_MAX_CLASSES], s_off[DCM_MAX_CLASSES], s_items[DCM_MAX_CLASSES + 1];
@@ -615,9 +453,9 @@ __global__ void __launch_bounds__(FORCE_THREADS, 3) k_force(ForceArgs a)
         if (local < s_cnt[q]) {
             int k = a.class_list[s_off[q] + local];
             if (use_list)
-                particle_force_list<PREC, ENERGY>(a, k, lane, G, gmask, ng);
+                particle_force_list<ENERGY>(a, k, lane, G, gmask, ng);
             else
-                particle_force<PREC, ENERGY>(a, k, lane, G, gmask, ng);
+                particle_force<ENERGY>(a, k, lane, G, gmask, ng);
         }
         __syncwarp();
     }
@@ -644,7 +482,14 @@ __global__ void __launch_bounds__(FORCE_THREADS, 3) k_force(ForceArgs a)
 //     reduction and a popcount), so a chunk may span any number of rows;
 //     the pair test and the force are evaluated without branches (the FP64
 //     re-decision at the cutoff edge is the only branch, and it is rare);
-//  3. the 32 lane partials are summed exactly: each FP32 partial is split
+//  3. close pairs (FP32 r^2 below r_close^2 = (1.5 sigma)^2, about 13 of a
+//     liquid particle's ~110 pairs) are not evaluated there: they are
+//     appended to a per-warp stash (a ballot keeps the warp converged) and
+//     evaluated together at the end of the particle in double-float
+//     arithmetic (close_pair): their forces are large (up to a few hundred
+//     epsilon/sigma), cancel in the sum, and change fast with r, so their
+//     FP32 rounding would dominate the per-particle error;
+//  4. the lane partials are summed exactly: each FP32 partial is split
 //     into a multiple of 2^-8 and a remainder, both scaled to integers and
 //     added with warp integer reductions, so the total is the exact sum of
 //     the partials (up to 2^-30 per partial), independent of lane order.
@@ -657,7 +502,10 @@ constexpr int FW_LIST_U = 4;                 // list entries in flight per lane
 constexpr int FW_WALK_MINB = 8;              // resident blocks per SM of the direct walk (64 registers)
 constexpr int FW_WALK_MINB1 = 10;            // ... one system (48 registers, 206 KB of row tables)
 constexpr int FW_LIST_MINB = 9;              // resident blocks per SM of the list kernel (56 registers)
-constexpr float FW_FIX_LIMIT = 65536.f;      // |partial| bound of the exact sum
+constexpr float FW_FIX_LIMIT = 32768.f;      // |partial| bound of the exact sum
+constexpr int FW_CLOSE = 64;                 // close-pair stash of a direct-walk warp (one particle)
+constexpr int FW_LIST_CLOSE = 64;            // close-pair stash of a list-kernel group (all its lanes)
+constexpr float FW_CMAGIC = 3072.f;          // 1.5 * 2^11: (x + m) - m rounds |x| < 2^10 to 2^-12
 
 struct FwTable {
     int4 ri[FW_ROWS];        // list offset P, main start, main length, wrapped start
@@ -666,17 +514,28 @@ struct FwTable {
     int rt[FW_ROWS];         // Verlet-list tag of the row: (dy + 8) << 24 | (dz + 8) << 28
 };
 
-// Exact warp sum of FP32 partials whose magnitude is below FW_FIX_LIMIT, as
-// the fixed-point integer V = sum * 2^30 (|V| < 2^52).  Integer pipes only:
-// on this GPU one FP64 warp instruction costs as much issue time as dozens
-// of FP32 ones, and this runs once per particle, not once per pair.
-__device__ __forceinline__ long long warp_fixed_sum(float p)
+// fixed-point image of an FP32 value with |p| < FW_FIX_LIMIT: p = hp * 2^-8
+// + lp * 2^-30 up to 2^-31 (rem is exact, and lp its rounding to 2^-30)
+__device__ __forceinline__ void fixed_split(float p, int &hp, int &lp)
 {
-    int hp = __float2int_rn(p * 256.f);
+    hp = __float2int_rn(p * 256.f);
     float rem = fmaf((float)hp, -0.00390625f, p);          // exact
-    int lp = __float2int_rn(rem * 1073741824.f);            // rem * 2^30, |.| <= 2^21
-    long long H = __reduce_add_sync(0xffffffffu, hp);
-    long long Lo = __reduce_add_sync(0xffffffffu, lp);
+    lp = __float2int_rn(rem * 1073741824.f);                // rem * 2^30, |.| <= 2^21
+}
+
+// Exact warp sum of three FP32 partials per lane whose magnitudes are below
+// FW_FIX_LIMIT, as the fixed-point integer V = sum * 2^30 (|V| < 2^52).
+// Integer pipes only: on this GPU one FP64 warp instruction costs as much
+// issue time as dozens of FP32 ones, and this runs once per particle, not
+// once per pair.
+__device__ __forceinline__ long long warp_fixed_sum(float p, float q, float r)
+{
+    int h0, l0, h1, l1, h2, l2;
+    fixed_split(p, h0, l0);
+    fixed_split(q, h1, l1);
+    fixed_split(r, h2, l2);
+    long long H = __reduce_add_sync(0xffffffffu, h0 + h1 + h2);
+    long long Lo = __reduce_add_sync(0xffffffffu, l0 + l1 + l2);
     return H * 4194304ll + Lo;
 }
 
@@ -692,11 +551,63 @@ __device__ __forceinline__ double fixed_to_double(long long V)
         (long long)(sign | ((unsigned long long)(e - 30 + 1023) << 52) | mant));
 }
 
-__device__ __forceinline__ double warp_tree_sum(float p)
+__device__ __forceinline__ double warp_tree_sum(float p, float q, float r)
 {
-    double d = (double)p;
+    double d = ((double)p + (double)q) + (double)r;
     for (int off = 16; off > 0; off >>= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
     return d;
+}
+
+// ---- close pairs in double-float arithmetic --------------------------------
+// A value is carried as hi + lo (two FP32 numbers): products take their
+// exact rounding error from an FMA, sums from TwoSum, and the cross terms
+// are kept to first order.  One pair's force scalar g = F/r then carries
+// about 2^-44 relative error instead of FP32's ~2^-21.  The displacement
+// d = dh + dl is exact: dh from the FP32 grid positions and cell shift (no
+// rounding, see cell_rel_position), dl from their FP32 remainders and the
+// low part of the cell edge.
+//
+// c: the system's constants (a Geom or the launch's ListConst): sig2f/l,
+// eps48f/l, eps24f/l.  Returns g = (gh, gl) and the FP32 (sigma/r)^6.
+template <class C>
+__device__ __forceinline__ void close_force_scalar(const C &c, float dxh, float dyh, float dzh,
+                                                   float dxl, float dyl, float dzl, float &gh,
+                                                   float &gl, float &s6)
+{
+    // q = |d|^2
+    const float p1 = __fmul_rn(dxh, dxh), e1 = fmaf(dxh, dxh, -p1);
+    const float p2 = __fmul_rn(dyh, dyh), e2 = fmaf(dyh, dyh, -p2);
+    const float p3 = __fmul_rn(dzh, dzh), e3 = fmaf(dzh, dzh, -p3);
+    float s12, es, qh, eq;
+    two_sum(p1, p2, s12, es);
+    two_sum(s12, p3, qh, eq);
+    const float cr = fmaf(dzh, dzl, fmaf(dyh, dyl, __fmul_rn(dxh, dxl)));
+    const float ql =
+        fmaf(2.f, cr, __fadd_rn(__fadd_rn(__fadd_rn(e1, e2), __fadd_rn(e3, es)), eq));
+    // w = 1/q: approximate reciprocal, then its residual (q and the low part)
+    const float wh = rcp_approx(qh);
+    const float rho = fmaf(-ql, wh, fmaf(-qh, wh, 1.f));
+    const float wl = __fmul_rn(wh, rho);
+    // s = sigma^2 w
+    const float sh = __fmul_rn(c.sig2f, wh);
+    const float sl = fmaf(c.sig2f, wl, fmaf(c.sig2l, wh, fmaf(c.sig2f, wh, -sh)));
+    // s^2, then s6 = (sigma/r)^6
+    const float s2h = __fmul_rn(sh, sh);
+    const float s2l = fmaf(__fmul_rn(2.f, sh), sl, fmaf(sh, sh, -s2h));
+    const float s6h = __fmul_rn(s2h, sh);
+    const float s6l = fmaf(s2h, sl, fmaf(s2l, sh, fmaf(s2h, sh, -s6h)));
+    // u = 48 eps s6 - 24 eps
+    const float mh = __fmul_rn(c.eps48f, s6h);
+    const float ml = fmaf(c.eps48f, s6l, fmaf(c.eps48l, s6h, fmaf(c.eps48f, s6h, -mh)));
+    float uh, ue;
+    two_sum(mh, -c.eps24f, uh, ue);
+    const float ul = __fsub_rn(__fadd_rn(ue, ml), c.eps24l);
+    // v = s6 u, g = w v
+    const float vh = __fmul_rn(s6h, uh);
+    const float vl = fmaf(s6h, ul, fmaf(s6l, uh, fmaf(s6h, uh, -vh)));
+    gh = __fmul_rn(wh, vh);
+    gl = fmaf(wh, vl, fmaf(wl, vh, fmaf(wh, vh, -gh)));
+    s6 = s6h;
 }
 
 // lane partials of one particle: pair force, pair count, PE, virial
@@ -704,6 +615,9 @@ template <bool ENERGY>
 struct WarpAcc {
     float fx = 0.f, fy = 0.f, fz = 0.f, pe = 0.f;
     float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f, v4 = 0.f, v5 = 0.f;
+    // close pairs: hi parts rounded to multiples of 2^-12 (their FP32 sums
+    // are exact while below 2^11 in magnitude), and the small remainders
+    float cx = 0.f, cy = 0.f, cz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
     int np = 0;
 
     // one candidate (dx, dy, dz) = r_i - r_j with in = "inside r_c[i]";
@@ -733,70 +647,159 @@ struct WarpAcc {
         }
     }
 
-    // sum the lane partials and store particle i's results; lane q writes value q
-    __device__ __forceinline__ void store(const ForceArgs &a, int i, int lane)
+    // one close pair from its exact displacement dh + dl: the force g d in
+    // double-float, its hi part rounded to 2^-12 into the exact sums and
+    // the rest into the remainders
+    template <class C>
+    __device__ __forceinline__ void close(const C &g, float dxh, float dyh, float dzh, float dxl,
+                                          float dyl, float dzl)
     {
-        bool small = fabsf(fx) < FW_FIX_LIMIT && fabsf(fy) < FW_FIX_LIMIT && fabsf(fz) < FW_FIX_LIMIT;
+        float gh, gl, s6;
+        close_force_scalar(g, dxh, dyh, dzh, dxl, dyl, dzl, gh, gl, s6);
+        add_close(gh, gl, dxh, dxl, cx, lx);
+        add_close(gh, gl, dyh, dyl, cy, ly);
+        add_close(gh, gl, dzh, dzl, cz, lz);
+        ++np;
+        if constexpr (ENERGY) {
+            pe = fmaf(g.eps2f * s6, s6 - 1.f, pe);
+            float gx = gh * dxh, gy = gh * dyh, gz = gh * dzh;
+            v0 = fmaf(0.5f * dxh, gx, v0);
+            v1 = fmaf(0.5f * dyh, gy, v1);
+            v2 = fmaf(0.5f * dzh, gz, v2);
+            v3 = fmaf(0.5f * dxh, gy, v3);
+            v4 = fmaf(0.5f * dxh, gz, v4);
+            v5 = fmaf(0.5f * dyh, gz, v5);
+        }
+    }
+
+    static __device__ __forceinline__ void add_close(float gh, float gl, float dh, float dl,
+                                                     float &c, float &l)
+    {
+        const float Fh = __fmul_rn(gh, dh);
+        const float Fl = fmaf(gh, dl, fmaf(gl, dh, fmaf(gh, dh, -Fh)));
+        const float q = __fsub_rn(__fadd_rn(Fh, FW_CMAGIC), FW_CMAGIC);
+        c = __fadd_rn(c, q);
+        l = __fadd_rn(l, __fadd_rn(__fsub_rn(Fh, q), Fl));
+    }
+
+    __device__ __forceinline__ bool small() const
+    {
+        bool s = fabsf(fx) < FW_FIX_LIMIT && fabsf(fy) < FW_FIX_LIMIT && fabsf(fz) < FW_FIX_LIMIT &&
+                 fabsf(cx) < FW_FIX_LIMIT && fabsf(cy) < FW_FIX_LIMIT && fabsf(cz) < FW_FIX_LIMIT &&
+                 fabsf(lx) < FW_FIX_LIMIT && fabsf(ly) < FW_FIX_LIMIT && fabsf(lz) < FW_FIX_LIMIT;
         if constexpr (ENERGY)
-            small = small && fabsf(pe) < FW_FIX_LIMIT && fabsf(v0) < FW_FIX_LIMIT &&
-                    fabsf(v1) < FW_FIX_LIMIT && fabsf(v2) < FW_FIX_LIMIT &&
-                    fabsf(v3) < FW_FIX_LIMIT && fabsf(v4) < FW_FIX_LIMIT && fabsf(v5) < FW_FIX_LIMIT;
+            s = s && fabsf(pe) < FW_FIX_LIMIT && fabsf(v0) < FW_FIX_LIMIT &&
+                fabsf(v1) < FW_FIX_LIMIT && fabsf(v2) < FW_FIX_LIMIT && fabsf(v3) < FW_FIX_LIMIT &&
+                fabsf(v4) < FW_FIX_LIMIT && fabsf(v5) < FW_FIX_LIMIT;
+        return s;
+    }
+
+    // sum the lane partials and store particle i's results; lane q writes
+    // value q.  Returns |F|^2 of the stored force in every lane.
+    __device__ __forceinline__ float store(const ForceArgs &a, int i, int lane)
+    {
         const size_t n = (size_t)a.b.N;
         const int npt = __reduce_add_sync(0xffffffffu, np);
         if (lane == 3) a.npair[i] = npt;
-        if (__all_sync(0xffffffffu, small)) {
+        float fc = 0.f;
+        if (__all_sync(0xffffffffu, small())) {
             long long V = 0, t;
-            t = warp_fixed_sum(fx); V = lane == 0 ? t : V;
-            t = warp_fixed_sum(fy); V = lane == 1 ? t : V;
-            t = warp_fixed_sum(fz); V = lane == 2 ? t : V;
+            t = warp_fixed_sum(fx, cx, lx); V = lane == 0 ? t : V;
+            t = warp_fixed_sum(fy, cy, ly); V = lane == 1 ? t : V;
+            t = warp_fixed_sum(fz, cz, lz); V = lane == 2 ? t : V;
             if constexpr (ENERGY) {
-                t = warp_fixed_sum(pe); V = lane == 4 ? t : V;
-                t = warp_fixed_sum(v0); V = lane == 5 ? t : V;
-                t = warp_fixed_sum(v1); V = lane == 6 ? t : V;
-                t = warp_fixed_sum(v2); V = lane == 7 ? t : V;
-                t = warp_fixed_sum(v3); V = lane == 8 ? t : V;
-                t = warp_fixed_sum(v4); V = lane == 9 ? t : V;
-                t = warp_fixed_sum(v5); V = lane == 10 ? t : V;
+                t = warp_fixed_sum(pe, 0.f, 0.f); V = lane == 4 ? t : V;
+                t = warp_fixed_sum(v0, 0.f, 0.f); V = lane == 5 ? t : V;
+                t = warp_fixed_sum(v1, 0.f, 0.f); V = lane == 6 ? t : V;
+                t = warp_fixed_sum(v2, 0.f, 0.f); V = lane == 7 ? t : V;
+                t = warp_fixed_sum(v3, 0.f, 0.f); V = lane == 8 ? t : V;
+                t = warp_fixed_sum(v4, 0.f, 0.f); V = lane == 9 ? t : V;
+                t = warp_fixed_sum(v5, 0.f, 0.f); V = lane == 10 ? t : V;
             }
             const double out = fixed_to_double(V);
-            if (lane < 3) a.f[lane * n + i] = out;
+            if (lane < 3) {
+                a.f[lane * n + i] = out;
+                fc = (float)out;
+            }
             if constexpr (ENERGY) {
                 if (lane == 4) a.pe[i] = out;
                 if (lane >= 5 && lane < 11) a.vir[(lane - 5) * n + i] = out;
             }
         } else {
             // a partial beyond the fixed-point range (or not finite): FP64 tree
-            double Fx = warp_tree_sum(fx), Fy = warp_tree_sum(fy), Fz = warp_tree_sum(fz);
+            double Fx = warp_tree_sum(fx, cx, lx), Fy = warp_tree_sum(fy, cy, ly),
+                   Fz = warp_tree_sum(fz, cz, lz);
             if (lane < 3) a.f[lane * n + i] = lane == 0 ? Fx : (lane == 1 ? Fy : Fz);
+            fc = lane == 0 ? (float)Fx : (lane == 1 ? (float)Fy : (lane == 2 ? (float)Fz : 0.f));
             if constexpr (ENERGY) {
-                double s7[7] = {warp_tree_sum(pe), warp_tree_sum(v0), warp_tree_sum(v1),
-                                warp_tree_sum(v2), warp_tree_sum(v3), warp_tree_sum(v4),
-                                warp_tree_sum(v5)};
+                double s7[7] = {warp_tree_sum(pe, 0.f, 0.f), warp_tree_sum(v0, 0.f, 0.f),
+                                warp_tree_sum(v1, 0.f, 0.f), warp_tree_sum(v2, 0.f, 0.f),
+                                warp_tree_sum(v3, 0.f, 0.f), warp_tree_sum(v4, 0.f, 0.f),
+                                warp_tree_sum(v5, 0.f, 0.f)};
                 if (lane == 4) a.pe[i] = s7[0];
 #pragma unroll
                 for (int e = 0; e < 6; ++e)
                     if (lane == 5 + e) a.vir[e * n + i] = s7[1 + e];
             }
         }
+        const float f2 = fc * fc;
+        return __shfl_sync(0xffffffffu, f2, 0) + __shfl_sync(0xffffffffu, f2, 1) +
+               __shfl_sync(0xffffffffu, f2, 2);
     }
 };
+
+// the exact displacement r_i - r_j of a close pair from both particles' FP32
+// grid positions u and remainders ul: the cell x offset (wrapped like the
+// list entries: every true offset is below half the cells along x), the
+// y/z cell row offsets dyc, dzc of j's row
+template <class C>
+__device__ __forceinline__ void close_disp(const C &c, float ncx, float halfnc, float4 ui,
+                                           float4 uli, float4 uj, float4 ulj, float dyc,
+                                           float dzc, float &dxh, float &dyh, float &dzh,
+                                           float &dxl, float &dyl, float &dzl)
+{
+    float dcx = ui.w - uj.w;
+    dcx -= dcx > halfnc ? ncx : 0.f;
+    dcx += dcx < -halfnc ? ncx : 0.f;
+    dxh = fmaf(dcx, c.cf[0], __fsub_rn(ui.x, uj.x));
+    dyh = fmaf(-dyc, c.cf[1], __fsub_rn(ui.y, uj.y));
+    dzh = fmaf(-dzc, c.cf[2], __fsub_rn(ui.z, uj.z));
+    dxl = fmaf(dcx, c.cfl[0], __fsub_rn(uli.x, ulj.x));
+    dyl = fmaf(-dyc, c.cfl[1], __fsub_rn(uli.y, ulj.y));
+    dzl = fmaf(-dzc, c.cfl[2], __fsub_rn(uli.z, ulj.z));
+}
+
+__device__ __forceinline__ float entry_dy(int e) { return (float)(((e >> 24) & 15) - 8); }
+__device__ __forceinline__ float entry_dz(int e) { return (float)((int)((unsigned)e >> 28) - 8); }
+
+template <bool ENERGY, bool SINGLE>
+__device__ __noinline__ void particle_force_warp_ff(const ForceArgs &a, FwTable &tb, int k,
+                                                     int lane);
 
 // Direct walk of particle k (sorted slot).  FILL (a Verlet-list rebuild):
 // the walk also covers the list radius R_k of the gather kernel and appends
 // every neighbour within R_k to k's list, in walk order, up to the capacity
-// the gather kernel gave it; the forces still use r_c[i] only.
-template <bool ENERGY, bool FILL, bool SINGLE>
-__device__ __forceinline__ void particle_force_warp(const ForceArgs &a, FwTable &tb, int k,
-                                                    int lane, int &ng, bool fill_on,
+// the gather kernel gave it; the forces still use r_c[i] only.  stash: the
+// warp's FW_CLOSE close-pair slots; an entry is (j - k) in 24 bits with
+// the row's cell offsets on top (the list-entry tag).  A particle with more
+// than FW_CLOSE close pairs (far denser than a liquid) evaluates the rest
+// in FP32.
+template <bool ENERGY, bool FILL, bool SINGLE, bool FF = false>
+__device__ __forceinline__ void particle_force_warp(const ForceArgs &a, FwTable &tb, int *stash,
+                                                    int k, int lane, int &ng, bool fill_on,
                                                     long long &entries)
 {
+    static_assert(!(FF && FILL), "the refinement pass does not fill lists");
     const Geom &g = SINGLE ? a.g0 : a.b.sys[sys_p(a.b, k)];
     const float4 ui = a.sp4[k];
+    float4 uli0 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if constexpr (FF) uli0 = a.spl4[k];
     const float4 q4 = a.rq[k];
     const int4 pk = a.pk[k];
     const int i = pk.x, cy = pk.y, cz = pk.z;
     const int cx = (int)ui.w;
     const float rc2f = q4.x, rc2lo = q4.y, rc2hi = q4.z;
+    const float rcl2 = fminf(g.rclose2, rc2lo);
     float rl = 0.f, rcull = q4.w;
     int32_t *out = nullptr;
     int cap = 0, cnt = 0;
@@ -821,7 +824,7 @@ __device__ __forceinline__ void particle_force_warp(const ForceArgs &a, FwTable 
     const float cf0 = g.cf[0];
     const unsigned lane_le = 0xffffffffu >> (31 - lane);
     WarpAcc<ENERGY> acc;
-    int ntab = 0, T = 0;
+    int ntab = 0, T = 0, ncs = 0;
     for (int r0 = 0; r0 < nrows; r0 += 32) {
         // ---- 1. one stencil row per lane
         const int r = r0 + lane;
@@ -883,7 +886,7 @@ __device__ __forceinline__ void particle_force_warp(const ForceArgs &a, FwTable 
             tb.ri[e] = make_int4(P, j0a, len1, j0b);
             tb.rf[e] = make_float4(fa, fb, ay, az);
             tb.rp[e] = P;
-            if constexpr (FILL) tb.rt[e] = tag;
+            tb.rt[e] = tag;
         }
         ntab += __popc(ne);
         T += __shfl_sync(0xffffffffu, incl, 31);
@@ -924,14 +927,35 @@ __device__ __forceinline__ void particle_force_warp(const ForceArgs &a, FwTable 
             // all beyond the cutoff adds nothing (exact zeros) and skips the
             // force arithmetic
             if (!FILL || __any_sync(0xffffffffu, r2 < rc2hi)) {
+                bool in = false, cl = false;
                 if (p < T) {
-                    bool in = r2 < rc2f && j != k;
+                    in = r2 < rc2f && j != k;
                     if (r2 >= rc2lo && r2 < rc2hi && j != k) {
                         double rci = a.rc[i];
                         in = fp64_inside(a, g, i, a.sorted_id[j], DMUL(rci, rci));
-                        ++ng;
+                        if (!FF) ++ng;
                     }
-                    acc.pair(g, dx, dy, dz, r2, in);
+                    // close pairs go to the stash (the slot offset j - k
+                    // must fit its 24 bits)
+                    cl = r2 < rcl2 && j != k && (unsigned)(j - k + (1 << 23)) < (1u << 24);
+                }
+                if constexpr (FF) {
+                    // refinement: every pair of the particle in double-float
+                    if (in) {
+                        const int e = tb.rt[rowi];
+                        float dxh, dyh, dzh, dxl, dyl, dzl;
+                        close_disp(g, (float)nc0, 0.5f * (float)nc0, ui, uli0, a.sp4[j],
+                                   a.spl4[j], entry_dy(e), entry_dz(e), dxh, dyh, dzh, dxl, dyl,
+                                   dzl);
+                        acc.close(g, dxh, dyh, dzh, dxl, dyl, dzl);
+                    }
+                } else {
+                    const unsigned cm = __ballot_sync(0xffffffffu, cl);
+                    const int at = ncs + __popc(cm & (lane_le >> 1));
+                    cl = cl && at < FW_CLOSE;
+                    if (cl) stash[at] = ((j - k) & 0xffffff) | tb.rt[rowi];
+                    ncs = min(ncs + __popc(cm), FW_CLOSE);
+                    if (p < T) acc.pair(g, dx, dy, dz, r2, in && !cl);
                 }
             }
             if constexpr (FILL) {
@@ -947,6 +971,20 @@ __device__ __forceinline__ void particle_force_warp(const ForceArgs &a, FwTable 
         ntab = 0;
         T = 0;
     }
+    // ---- 3. the close pairs, one per lane, in double-float
+    if (ncs > 0) {
+        const float4 uli = a.spl4[k];
+        const float ncx = (float)nc0, halfnc = 0.5f * (float)nc0;
+        for (int t = lane; t < ncs; t += 32) {
+            const int e = stash[t];
+            const int j = k + ((int)((unsigned)e << 8) >> 8);
+            float dxh, dyh, dzh, dxl, dyl, dzl;
+            close_disp(g, ncx, halfnc, ui, uli, a.sp4[j], a.spl4[j], entry_dy(e), entry_dz(e),
+                       dxh, dyh, dzh, dxl, dyl, dzl);
+            acc.close(g, dxh, dyh, dzh, dxl, dyl, dzl);
+        }
+        __syncwarp();
+    }
     if constexpr (FILL) {
         if (fill_on && lane == 0) {
             a.nl_cnt[k] = min(cnt, cap);
@@ -956,18 +994,36 @@ __device__ __forceinline__ void particle_force_warp(const ForceArgs &a, FwTable 
             entries += min(cnt, cap);
         }
     }
-    acc.store(a, i, lane);
+    const float f2 = acc.store(a, i, lane);
+    if constexpr (!FF) {
+        // a net force small against the FP32 error of the pairs beyond
+        // r_close: all of this particle's pairs again in double-float
+        if (f2 < g.redo_f2) particle_force_warp_ff<ENERGY, SINGLE>(a, tb, k, lane);
+    }
 }
 
-// exact sum over the G lanes of one group (G a power of two <= 32): the
-// same split into a multiple of 2^-8 and a remainder as warp_fixed_sum,
-// added by an integer butterfly inside the group
-template <int G>
-__device__ __forceinline__ long long group_fixed_sum(float p)
+// the refinement pass of one particle, out of line: it keeps the
+// double-float arithmetic out of the main walk's register budget
+template <bool ENERGY, bool SINGLE>
+__device__ __noinline__ void particle_force_warp_ff(const ForceArgs &a, FwTable &tb, int k,
+                                                     int lane)
 {
-    int hp = __float2int_rn(p * 256.f);
-    float rem = fmaf((float)hp, -0.00390625f, p);
-    int lp = __float2int_rn(rem * 1073741824.f);
+    int ng = 0;
+    long long entries = 0;
+    particle_force_warp<ENERGY, false, SINGLE, true>(a, tb, nullptr, k, lane, ng, false, entries);
+}
+
+// exact sum over the G lanes of one group (G a power of two <= 32) of three
+// FP32 partials per lane: the same split into a multiple of 2^-8 and a
+// remainder as warp_fixed_sum, added by an integer butterfly inside the group
+template <int G>
+__device__ __forceinline__ long long group_fixed_sum(float p, float q, float r)
+{
+    int h0, l0, h1, l1, h2, l2;
+    fixed_split(p, h0, l0);
+    fixed_split(q, h1, l1);
+    fixed_split(r, h2, l2);
+    int hp = h0 + h1 + h2, lp = l0 + l1 + l2;
 #pragma unroll
     for (int off = G >> 1; off > 0; off >>= 1) {
         hp += __shfl_xor_sync(0xffffffffu, hp, off);
@@ -977,13 +1033,85 @@ __device__ __forceinline__ long long group_fixed_sum(float p)
 }
 
 template <int G>
-__device__ __forceinline__ double group_tree_sum(float p)
+__device__ __forceinline__ double group_tree_sum(float p, float q, float r)
 {
-    double d = (double)p;
+    double d = ((double)p + (double)q) + (double)r;
 #pragma unroll
     for (int off = G >> 1; off > 0; off >>= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
     return d;
 }
+
+// Sum one group's lane partials (every lane of the warp calls this: the
+// sums shuffle across the whole warp) and, when write, store particle i's
+// results, lane q of the group writing value q.  Returns |F|^2 of the
+// particle in every lane of the group.
+template <bool ENERGY, int G>
+__device__ __forceinline__ float group_store(const ForceArgs &a, const WarpAcc<ENERGY> &acc,
+                                             bool write, int i, int gl)
+{
+    const size_t n = (size_t)a.b.N;
+    const int wl = threadIdx.x & 31, gb = wl & ~(G - 1);
+    int npt = acc.np;
+#pragma unroll
+    for (int off = G >> 1; off > 0; off >>= 1) npt += __shfl_xor_sync(0xffffffffu, npt, off);
+    float fc = 0.f;
+    if (__all_sync(0xffffffffu, acc.small())) {
+        long long V = 0, t;
+        t = group_fixed_sum<G>(acc.fx, acc.cx, acc.lx); V = gl == 0 ? t : V;
+        t = group_fixed_sum<G>(acc.fy, acc.cy, acc.ly); V = gl == 1 ? t : V;
+        t = group_fixed_sum<G>(acc.fz, acc.cz, acc.lz); V = gl == 2 ? t : V;
+        if constexpr (ENERGY) {
+            t = group_fixed_sum<G>(acc.pe, 0.f, 0.f); V = gl == 4 ? t : V;
+            t = group_fixed_sum<G>(acc.v0, 0.f, 0.f); V = gl == 5 ? t : V;
+            t = group_fixed_sum<G>(acc.v1, 0.f, 0.f); V = gl == 6 ? t : V;
+            t = group_fixed_sum<G>(acc.v2, 0.f, 0.f); V = gl == 7 ? t : V;
+            t = group_fixed_sum<G>(acc.v3, 0.f, 0.f); V = gl == 8 ? t : V;
+            t = group_fixed_sum<G>(acc.v4, 0.f, 0.f); V = gl == 9 ? t : V;
+            t = group_fixed_sum<G>(acc.v5, 0.f, 0.f); V = gl == 10 ? t : V;
+        }
+        const double out = fixed_to_double(V);
+        if (gl < 3) fc = (float)out;
+        if (write) {
+            if (gl < 3) a.f[gl * n + i] = out;
+            if (gl == 3) a.npair[i] = npt;
+            if constexpr (ENERGY) {
+                if (gl == 4) a.pe[i] = out;
+                if (gl >= 5 && gl < 11) a.vir[(gl - 5) * n + i] = out;
+            }
+        }
+    } else {
+        double F[3] = {group_tree_sum<G>(acc.fx, acc.cx, acc.lx),
+                       group_tree_sum<G>(acc.fy, acc.cy, acc.ly),
+                       group_tree_sum<G>(acc.fz, acc.cz, acc.lz)};
+        double s7[7] = {0, 0, 0, 0, 0, 0, 0};
+        if constexpr (ENERGY) {
+            s7[0] = group_tree_sum<G>(acc.pe, 0.f, 0.f);
+            s7[1] = group_tree_sum<G>(acc.v0, 0.f, 0.f);
+            s7[2] = group_tree_sum<G>(acc.v1, 0.f, 0.f);
+            s7[3] = group_tree_sum<G>(acc.v2, 0.f, 0.f);
+            s7[4] = group_tree_sum<G>(acc.v3, 0.f, 0.f);
+            s7[5] = group_tree_sum<G>(acc.v4, 0.f, 0.f);
+            s7[6] = group_tree_sum<G>(acc.v5, 0.f, 0.f);
+        }
+        if (gl < 3) fc = (float)F[gl];
+        if (write && gl == 0) {
+            for (int c = 0; c < 3; ++c) a.f[c * n + i] = F[c];
+            a.npair[i] = npt;
+            if constexpr (ENERGY) {
+                a.pe[i] = s7[0];
+                for (int c = 0; c < 6; ++c) a.vir[c * n + i] = s7[1 + c];
+            }
+        }
+    }
+    const float f2 = fc * fc;
+    return __shfl_sync(0xffffffffu, f2, gb) + __shfl_sync(0xffffffffu, f2, gb + 1) +
+           __shfl_sync(0xffffffffu, f2, gb + 2);
+}
+
+// close-pair slots of one list-kernel lane (slot-major over the block's
+// threads); a lane that meets more close pairs evaluates the rest in FP32
+template <int G>
+constexpr int list_close_slots() { return FW_LIST_CLOSE / G > 4 ? FW_LIST_CLOSE / G : 4; }
 
 // Particle k over its Verlet list, G lanes (one group) per particle, 32/G
 // particles per warp: the list is flat, so a group needs no row structure
@@ -991,24 +1119,29 @@ __device__ __forceinline__ double group_tree_sum(float p)
 // 32/G particles per warp instruction.  Entries: j | (dy + 8) << 24 |
 // (dz + 8) << 28; the cell x offset comes from the cell x indices stored
 // with the positions (every true offset is below half the cells along x).
-// Same pair rule and FP64 re-decision as the direct walk.  k < 0: an idle
-// group (past the end of the queue).  SINGLE (one system): the cell and LJ
-// constants come from the launch parameters (no registers held for them,
-// which lets 8 blocks of 128 threads share an SM).
+// Same pair rule and FP64 re-decision as the direct walk.  Close pairs are
+// set aside in the lane's stash slots (stash[s * FW_THREADS + thread]) and
+// evaluated in double-float after the list, spread over the group's lanes.
+// k < 0: an idle group (past the end of the queue).  SINGLE (one system):
+// the cell and LJ constants come from the launch parameters (no registers
+// held for them, which lets 9 blocks of 128 threads share an SM).
 template <bool ENERGY, int G, bool SINGLE>
-__device__ __forceinline__ void particle_force_list_group(const ForceArgs &a, int k, int gl,
-                                                          int &ng)
+__device__ __forceinline__ void particle_force_list_group(const ForceArgs &a, int *stash, int k,
+                                                          int gl, int &ng)
 {
+    constexpr int CSL = list_close_slots<G>();
     WarpAcc<ENERGY> acc;
-    int i = 0;
+    int i = 0, ncl = 0;
+    const Geom &g = a.b.sys[SINGLE ? 0 : (k >= 0 ? sys_p(a.b, k) : 0)];
+    const float ncx = SINGLE ? a.lc.ncx : (float)g.nc[0];
+    const float halfnc = SINGLE ? a.lc.halfnc : 0.5f * (float)g.nc[0];
+    float4 ui = make_float4(0.f, 0.f, 0.f, 0.f);
     if (k >= 0) {
-        const Geom &g = a.b.sys[SINGLE ? 0 : sys_p(a.b, k)];
-        const float4 ui = a.sp4[k];
+        ui = a.sp4[k];
         const float4 q4 = a.rq[k];
         i = a.pk[k].x;
         const float rc2f = q4.x, rc2lo = q4.y, rc2hi = q4.z;
-        const float ncx = SINGLE ? a.lc.ncx : (float)g.nc[0];
-        const float halfnc = SINGLE ? a.lc.halfnc : 0.5f * (float)g.nc[0];
+        const float rcl2 = fminf(SINGLE ? a.lc.rclose2 : g.rclose2, rc2lo);
         const float cf0 = SINGLE ? a.lc.cf[0] : g.cf[0];
         const float cf1 = SINGLE ? a.lc.cf[1] : g.cf[1];
         const float cf2 = SINGLE ? a.lc.cf[2] : g.cf[2];
@@ -1016,14 +1149,15 @@ __device__ __forceinline__ void particle_force_list_group(const ForceArgs &a, in
         const int cnt = a.nl_cnt[k];
         auto one = [&](int e, float4 uj) {
             int j = e & 0xffffff;
-            float dyc = (float)(((e >> 24) & 15) - 8);
-            float dzc = (float)((int)((unsigned)e >> 28) - 8);
+            float dyc = entry_dy(e);
+            float dzc = entry_dz(e);
             float dcx = ui.w - uj.w;
             dcx -= dcx > halfnc ? ncx : 0.f;
             dcx += dcx < -halfnc ? ncx : 0.f;
+            // coordinate differences first: exact for a close pair
             float dx = fmaf(dcx, cf0, ui.x - uj.x);
-            float dy = fmaf(-dyc, cf1, ui.y) - uj.y;
-            float dz = fmaf(-dzc, cf2, ui.z) - uj.z;
+            float dy = fmaf(-dyc, cf1, ui.y - uj.y);
+            float dz = fmaf(-dzc, cf2, ui.z - uj.z);
             float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             bool in = r2 < rc2f;
             if (r2 >= rc2lo && r2 < rc2hi) {
@@ -1031,10 +1165,15 @@ __device__ __forceinline__ void particle_force_list_group(const ForceArgs &a, in
                 in = fp64_inside(a, g, i, a.sorted_id[j], DMUL(rci, rci));
                 ++ng;
             }
+            const bool cl = r2 < rcl2 && ncl < CSL;
+            if (cl) {
+                stash[ncl * FW_THREADS + threadIdx.x] = e;
+                ++ncl;
+            }
             if constexpr (SINGLE)
-                acc.pair(a.lc, dx, dy, dz, r2, in);
+                acc.pair(a.lc, dx, dy, dz, r2, in && !cl);
             else
-                acc.pair(g, dx, dy, dz, r2, in);
+                acc.pair(g, dx, dy, dz, r2, in && !cl);
         };
         int p = gl;
         // FW_LIST_U entries of the lane in flight per iteration: all entry
@@ -1054,62 +1193,94 @@ __device__ __forceinline__ void particle_force_list_group(const ForceArgs &a, in
             one(e0, a.sp4[e0 & 0xffffff]);
         }
     }
-    // ---- sums over the group; lane q of the group writes value q
-    bool small = fabsf(acc.fx) < FW_FIX_LIMIT && fabsf(acc.fy) < FW_FIX_LIMIT &&
-                 fabsf(acc.fz) < FW_FIX_LIMIT;
-    if constexpr (ENERGY)
-        small = small && fabsf(acc.pe) < FW_FIX_LIMIT && fabsf(acc.v0) < FW_FIX_LIMIT &&
-                fabsf(acc.v1) < FW_FIX_LIMIT && fabsf(acc.v2) < FW_FIX_LIMIT &&
-                fabsf(acc.v3) < FW_FIX_LIMIT && fabsf(acc.v4) < FW_FIX_LIMIT &&
-                fabsf(acc.v5) < FW_FIX_LIMIT;
-    const size_t n = (size_t)a.b.N;
-    int npt = acc.np;
+    // ---- the group's close pairs, spread over its lanes: item t of the
+    // group's concatenated slots lives in the slots of the last lane whose
+    // exclusive offset is <= t (a binary search over the G offsets)
+    {
+        const int wl = threadIdx.x & 31, gb = wl & ~(G - 1);
+        int incl = ncl;
 #pragma unroll
-    for (int off = G >> 1; off > 0; off >>= 1) npt += __shfl_xor_sync(0xffffffffu, npt, off);
-    if (__all_sync(0xffffffffu, small)) {
-        long long V = 0, t;
-        t = group_fixed_sum<G>(acc.fx); V = gl == 0 ? t : V;
-        t = group_fixed_sum<G>(acc.fy); V = gl == 1 ? t : V;
-        t = group_fixed_sum<G>(acc.fz); V = gl == 2 ? t : V;
-        if constexpr (ENERGY) {
-            t = group_fixed_sum<G>(acc.pe); V = gl == 4 ? t : V;
-            t = group_fixed_sum<G>(acc.v0); V = gl == 5 ? t : V;
-            t = group_fixed_sum<G>(acc.v1); V = gl == 6 ? t : V;
-            t = group_fixed_sum<G>(acc.v2); V = gl == 7 ? t : V;
-            t = group_fixed_sum<G>(acc.v3); V = gl == 8 ? t : V;
-            t = group_fixed_sum<G>(acc.v4); V = gl == 9 ? t : V;
-            t = group_fixed_sum<G>(acc.v5); V = gl == 10 ? t : V;
+        for (int off = 1; off < G; off <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, off, G);
+            if (gl >= off) incl += t;
         }
-        if (k >= 0) {
-            const double out = fixed_to_double(V);
-            if (gl < 3) a.f[gl * n + i] = out;
-            if (gl == 3) a.npair[i] = npt;
-            if constexpr (ENERGY) {
-                if (gl == 4) a.pe[i] = out;
-                if (gl >= 5 && gl < 11) a.vir[(gl - 5) * n + i] = out;
+        const int total = __shfl_sync(0xffffffffu, incl, G - 1, G);
+        const int excl = incl - ncl;
+        float4 uli = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (total > 0) uli = a.spl4[k];
+        for (int base = 0; __any_sync(0xffffffffu, base < total); base += G) {
+            const int t = base + gl;
+            int o = 0;
+#pragma unroll
+            for (int st = G >> 1; st > 0; st >>= 1) {
+                const int ex = __shfl_sync(0xffffffffu, excl, gb + o + st);
+                o = ex <= t ? o + st : o;
+            }
+            const int exo = __shfl_sync(0xffffffffu, excl, gb + o);
+            if (t < total) {
+                const int e = stash[(t - exo) * FW_THREADS + (threadIdx.x & ~31) + gb + o];
+                const int j = e & 0xffffff;
+                float dxh, dyh, dzh, dxl, dyl, dzl;
+                if constexpr (SINGLE) {
+                    close_disp(a.lc, ncx, halfnc, ui, uli, a.sp4[j], a.spl4[j], entry_dy(e),
+                               entry_dz(e), dxh, dyh, dzh, dxl, dyl, dzl);
+                    acc.close(a.lc, dxh, dyh, dzh, dxl, dyl, dzl);
+                } else {
+                    close_disp(g, ncx, halfnc, ui, uli, a.sp4[j], a.spl4[j], entry_dy(e),
+                               entry_dz(e), dxh, dyh, dzh, dxl, dyl, dzl);
+                    acc.close(g, dxh, dyh, dzh, dxl, dyl, dzl);
+                }
             }
         }
-    } else {
-        double F[3] = {group_tree_sum<G>(acc.fx), group_tree_sum<G>(acc.fy),
-                       group_tree_sum<G>(acc.fz)};
-        double s7[7] = {0, 0, 0, 0, 0, 0, 0};
-        if constexpr (ENERGY) {
-            s7[0] = group_tree_sum<G>(acc.pe);
-            s7[1] = group_tree_sum<G>(acc.v0);
-            s7[2] = group_tree_sum<G>(acc.v1);
-            s7[3] = group_tree_sum<G>(acc.v2);
-            s7[4] = group_tree_sum<G>(acc.v3);
-            s7[5] = group_tree_sum<G>(acc.v4);
-            s7[6] = group_tree_sum<G>(acc.v5);
-        }
-        if (k >= 0 && gl == 0) {
-            for (int c = 0; c < 3; ++c) a.f[c * n + i] = F[c];
-            a.npair[i] = npt;
-            if constexpr (ENERGY) {
-                a.pe[i] = s7[0];
-                for (int c = 0; c < 6; ++c) a.vir[c * n + i] = s7[1 + c];
+    }
+    // ---- sums over the group; lane q of the group writes value q
+    float f2 = group_store<ENERGY, G>(a, acc, k >= 0, i, gl);
+    // a net force small against the FP32 error of the pairs beyond r_close:
+    // the particle's whole list again, every in-cutoff pair in double-float
+    // (same pair decisions), and its results stored again
+    const bool redo = k >= 0 && f2 < (SINGLE ? a.lc.redo_f2 : g.redo_f2);
+    if (__any_sync(0xffffffffu, redo)) {
+        WarpAcc<ENERGY> acc2;
+        if (redo) {
+            const float4 uli = a.spl4[k];
+            const float4 q4 = a.rq[k];
+            const float rc2f = q4.x, rc2lo = q4.y, rc2hi = q4.z;
+            const float cf0 = SINGLE ? a.lc.cf[0] : g.cf[0];
+            const float cf1 = SINGLE ? a.lc.cf[1] : g.cf[1];
+            const float cf2 = SINGLE ? a.lc.cf[2] : g.cf[2];
+            const int32_t *list = a.nl + a.nl_start[k];
+            const int cnt = a.nl_cnt[k];
+            for (int p = gl; p < cnt; p += G) {
+                const int e = list[p];
+                const int j = e & 0xffffff;
+                const float4 uj = a.sp4[j];
+                float dcx = ui.w - uj.w;
+                dcx -= dcx > halfnc ? ncx : 0.f;
+                dcx += dcx < -halfnc ? ncx : 0.f;
+                float dx = fmaf(dcx, cf0, ui.x - uj.x);
+                float dy = fmaf(-entry_dy(e), cf1, ui.y - uj.y);
+                float dz = fmaf(-entry_dz(e), cf2, ui.z - uj.z);
+                float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                bool in = r2 < rc2f;
+                if (r2 >= rc2lo && r2 < rc2hi) {
+                    double rci = a.rc[i];
+                    in = fp64_inside(a, g, i, a.sorted_id[j], DMUL(rci, rci));
+                }
+                if (in) {
+                    float dxh, dyh, dzh, dxl, dyl, dzl;
+                    if constexpr (SINGLE) {
+                        close_disp(a.lc, ncx, halfnc, ui, uli, uj, a.spl4[j], entry_dy(e),
+                                   entry_dz(e), dxh, dyh, dzh, dxl, dyl, dzl);
+                        acc2.close(a.lc, dxh, dyh, dzh, dxl, dyl, dzl);
+                    } else {
+                        close_disp(g, ncx, halfnc, ui, uli, uj, a.spl4[j], entry_dy(e),
+                                   entry_dz(e), dxh, dyh, dzh, dxl, dyl, dzl);
+                        acc2.close(g, dxh, dyh, dzh, dxl, dyl, dzl);
+                    }
+                }
             }
         }
+        group_store<ENERGY, G>(a, acc2, redo, i, gl);
     }
 }
 
@@ -1182,6 +1353,7 @@ __global__ void __launch_bounds__(FW_THREADS, SINGLE ? FW_WALK_MINB1 : FW_WALK_M
     k_force_warp(const __grid_constant__ ForceArgs a)
 {
     __shared__ FwTable s_tab[FW_WARPS];
+    __shared__ int s_close[FW_WARPS][FW_CLOSE];
     __shared__ FwQueue sq;
     __shared__ int s_run, s_fill;
     sq.init(a);
@@ -1197,7 +1369,8 @@ __global__ void __launch_bounds__(FW_THREADS, SINGLE ? FW_WALK_MINB1 : FW_WALK_M
     int ng = 0;
     long long entries = 0;
     sq.drain(a, lane, [&](int k) {
-        particle_force_warp<ENERGY, FILL, SINGLE>(a, tb, k, lane, ng, fill_on, entries);
+        particle_force_warp<ENERGY, FILL, SINGLE>(a, tb, s_close[threadIdx.x >> 5], k, lane, ng,
+                                                  fill_on, entries);
     });
     block_counts(a, ng, entries);
 }
@@ -1212,6 +1385,7 @@ template <bool ENERGY, int G, bool SINGLE>
 __global__ void __launch_bounds__(FW_THREADS, FW_LIST_MINB) k_force_list_warp(ForceArgs a)
 {
     __shared__ int s_run;
+    __shared__ int s_close[list_close_slots<G>() * FW_THREADS];
     if (threadIdx.x == 0) s_run = a.list_flags[LF_REBUILD] == 0;
     __syncthreads();
     if (!s_run) return;
@@ -1226,7 +1400,7 @@ __global__ void __launch_bounds__(FW_THREADS, FW_LIST_MINB) k_force_list_warp(Fo
         item0 = __shfl_sync(0xffffffffu, item0, 0);
         if (item0 >= total) break;
         const int k = item0 + grp < total ? item0 + grp : -1;
-        particle_force_list_group<ENERGY, G, SINGLE>(a, k, gl, ng);
+        particle_force_list_group<ENERGY, G, SINGLE>(a, s_close, k, gl, ng);
     }
     block_counts(a, ng, 0);
 }
@@ -1320,32 +1494,25 @@ int launch_forces(dcm_handle *h, bool energy)
     ForceArgs a;
     fill_args(h, a);
     const bool list_warp = h->nl && h->list_warp;
-    const bool warp_walk = h->p.precision == DCM_MIXED && h->tune.walk == DCM_WALK_WARP;
-    // (the lanes list walks use the queue before the forces of their step)
-    if (!list_warp && !(h->in_step && warp_walk && !h->nl))
-        cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), h->stream);
-    int block = h->tune.block >= 64 && h->tune.block <= FORCE_THREADS ? h->tune.block : FORCE_THREADS;
-    int grid = h->num_sms * (2048 / block);
-    bool fp64 = h->p.precision == DCM_FP64;
-    if (!fp64 && !h->nl && h->tune.walk == DCM_WALK_WARP) {
+    const bool fp64 = h->p.precision == DCM_FP64;
+    if (list_warp) return launch_list_forces(h, energy, 2);
+    // (the lanes list walks use the queue before the forces of their step;
+    // a captured step's drift zeroes the warp walk's queue)
+    if (fp64 || !h->in_step) cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), h->stream);
+    if (!fp64) {
+        // DCM_MIXED: the warp walk
         if (energy)
             launch_walk<true, false>(h, a);
         else
             launch_walk<false, false>(h, a);
         return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "force launch");
     }
-    if (list_warp) return launch_list_forces(h, energy, 2);
-    if (fp64) {
-        if (energy)
-            k_force<DCM_FP64, true><<<grid, block, 0, h->stream>>>(a);
-        else
-            k_force<DCM_FP64, false><<<grid, block, 0, h->stream>>>(a);
-    } else {
-        if (energy)
-            k_force<DCM_MIXED, true><<<grid, block, 0, h->stream>>>(a);
-        else
-            k_force<DCM_MIXED, false><<<grid, block, 0, h->stream>>>(a);
-    }
+    int block = h->tune.block >= 64 && h->tune.block <= FORCE_THREADS ? h->tune.block : FORCE_THREADS;
+    int grid = h->num_sms * (2048 / block);
+    if (energy)
+        k_force<true><<<grid, block, 0, h->stream>>>(a);
+    else
+        k_force<false><<<grid, block, 0, h->stream>>>(a);
     return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "force launch");
 }
 
@@ -1359,6 +1526,7 @@ static void fill_args(dcm_handle *h, ForceArgs &a)
         a.lanes[q] = (G >= 1 && G <= 32 && (G & (G - 1)) == 0) ? G : 1;
     }
     a.sp4 = h->sp4;
+    a.spl4 = h->spl4;
     a.spd = h->spd;
     a.rq = h->rq;
     a.pk = h->pk;
@@ -1386,13 +1554,21 @@ static void fill_args(dcm_handle *h, ForceArgs &a)
     a.g0 = h->geo_host[0];
     {
         const Geom &g0 = h->geo_host[0];
-        for (int q = 0; q < 3; ++q) a.lc.cf[q] = g0.cf[q];
+        for (int q = 0; q < 3; ++q) {
+            a.lc.cf[q] = g0.cf[q];
+            a.lc.cfl[q] = g0.cfl[q];
+        }
         a.lc.ncx = (float)g0.nc[0];
         a.lc.halfnc = 0.5f * (float)g0.nc[0];
         a.lc.sig2f = g0.sig2f;
         a.lc.eps48f = g0.eps48f;
         a.lc.eps24f = g0.eps24f;
         a.lc.eps2f = g0.eps2f;
+        a.lc.sig2l = g0.sig2l;
+        a.lc.eps48l = g0.eps48l;
+        a.lc.eps24l = g0.eps24l;
+        a.lc.rclose2 = g0.rclose2;
+        a.lc.redo_f2 = g0.redo_f2;
     }
     a.d = h->d;
     a.list_delta = 0.f;

@@ -11,10 +11,11 @@ namespace dcm {
 // GB300 issues FP64 at 1/64 of the FP32 rate, so the update uses two fused
 // multiply-adds per component and integer tests of the exponent bits.
 // With sp4 given (warp Verlet-list kernels) the drift also refreshes the
-// particle's FP32 cell-relative position at its sorted slot inv[i], in the
-// cell of the last sort, so no gather pass is needed between list builds.
+// particle's FP32 cell-relative position and its remainder (spl4) at its
+// sorted slot inv[i], in the cell of the last sort, so no gather pass is
+// needed between list builds.
 __global__ void k_kick_drift(Batch b, double *__restrict__ x, double *__restrict__ v,
-                             const double *__restrict__ f, int *err, float4 *sp4,
+                             const double *__restrict__ f, int *err, float4 *sp4, float4 *spl4,
                              const int32_t *__restrict__ inv, const int32_t *__restrict__ cell_of,
                              const double *__restrict__ rc, ListTest t, unsigned int *queues)
 {
@@ -49,8 +50,11 @@ __global__ void k_kick_drift(Batch b, double *__restrict__ x, double *__restrict
         if (bad) atomicOr(err, bad);
         float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
         if (sp4) {
-            u = cell_rel_position(b, g, xn[0], xn[1], xn[2], cell_of[i] - (int)g.c0);
-            sp4[inv[i]] = u;
+            float4 lo;
+            u = cell_rel_position(b, g, xn[0], xn[1], xn[2], cell_of[i] - (int)g.c0, lo);
+            const int k = inv[i];
+            sp4[k] = u;
+            spl4[k] = lo;
         }
         if (t.lf) {
             // warp lists: the displacement from the FP32 cell-relative
@@ -170,7 +174,8 @@ int launch_kick_drift(dcm_handle *h)
     ListTest t = list_test(h, true, !h->step_detect, !h->step_detect);
     if (!h->fold_check) t.lf = nullptr;
     k_kick_drift<<<nblk(h->n, 256), 256, 0, h->stream>>>(h->b, h->x, h->v, h->f, h->err,
-                                                         wl ? h->sp4 : nullptr, h->inv, h->cell_of,
+                                                         wl ? h->sp4 : nullptr, h->spl4, h->inv,
+                                                         h->cell_of,
                                                          h->rc, t,
                                                          h->in_step ? &h->stats->barrier[2] : nullptr);
     return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "kick_drift launch");

@@ -12,8 +12,10 @@
 //   cutoffs   d, rc   : double [N];  cls : uint8 [N]   (id order)
 //   link cells        : cell_of[N], slot[N] (id order); cell_count[Nc],
 //                       cell_start[Nc+1], sorted_id[N]; sp4[N] float4
-//                       (cell-relative x,y,z in FP32, cell x index) and
-//                       spd[N] double4_32a (absolute x,y,z) in cell order;
+//                       (cell-relative x,y,z in FP32 on the grid qpos, cell
+//                       x index), MIXED: spl4[N] float4 (the FP32 remainders
+//                       of the cell-relative x,y,z) and FP64: spd[N]
+//                       double4_32a (absolute x,y,z), all in cell order;
 //                       MIXED: rq[N] float4 (r_c^2 and its guard band, culling
 //                       radius) and pk[N] int4 (id, cell y, cell z) in cell order
 //   voxel grid        : B int32, sm1/sm2 uint32 (smoothing passes), Bs double,
@@ -84,7 +86,10 @@ struct Geom {
     int nc[3];                   // link cells per axis
     double inv_c[3];             // nc / L  (cell index = floor(x * inv_c))
     double cedge[3];             // L / nc
-    float cf[3], inv_cf[3];      // FP32 copies for the mixed kernels
+    float cf[3], inv_cf[3];      // FP32 cell edges (cf: a multiple of qpos) and inverses
+    float cfl[3];                // cedge - cf in FP32 (the low part of the cell edge)
+    float qpos;                  // grid of the FP32 cell-relative positions (a power of two)
+    float inv_qpos;              // 1 / qpos (exact)
     int smax[3];                 // largest stencil radius in cells
     int gd[3];                   // voxels per axis
     double inv_h[3];             // gd / L
@@ -106,6 +111,9 @@ struct Geom {
     int cc_min;                  // Section 4.2: components below this many voxels change phase (0: off)
     double eps24, eps48, eps2, sig2;     // LJ force/energy constants
     float eps24f, eps48f, eps2f, sig2f;
+    float eps24l, eps48l, sig2l;         // low parts: eps48 - eps48f, ... (close pairs)
+    float rclose2;               // mixed: pairs with FP32 r^2 below this take the double-float path
+    float redo_f2;               // mixed: a particle whose |F|^2 is below this is redone in double-float
     // this system's slices of the concatenated arrays
     int64_t p0, c0, v0;
     int64_t ncell, nvox;
@@ -176,6 +184,7 @@ struct dcm_handle {
     // link cells
     int32_t *cell_of, *slot, *cell_count, *cell_start, *sorted_id, *scan_tmp;
     float4 *sp4;
+    float4 *spl4;                // MIXED: low parts of the cell-relative positions
     double4_32a *spd;
     float4 *rq;                  // MIXED: per sorted slot r_c^2, guard band, culling radius
     int32_t *inv;                // sorted slot of each particle (id order), MIXED

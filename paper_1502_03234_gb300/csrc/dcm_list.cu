@@ -101,7 +101,7 @@ ListTest list_test(dcm_handle *h, bool partner, bool excess, bool decide)
 
 void list_mode(dcm_handle *h)
 {
-    h->list_warp = h->nl && h->p.precision == DCM_MIXED && h->tune.walk == DCM_WALK_WARP;
+    h->list_warp = h->nl && h->p.precision == DCM_MIXED;
 }
 
 // decide, [cell sort], gather + classes, then

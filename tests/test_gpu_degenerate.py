@@ -55,8 +55,7 @@ def _check(dcm, orc, x, v, box, prec, skin=0.0):
     assert np.array_equal(npair, ref.npair)
     err = np.linalg.norm(f - ref.f, axis=1)
     fmag = np.linalg.norm(ref.f, axis=1)
-    extra = 0.0 if prec == dcm.DCM_FP64 else 5e-4
-    assert np.all(err <= FP64_ABS + FP64_REL * fmag + extra), err.max()
+    assert np.all(err <= FP64_ABS + FP64_REL * fmag), (err.max(), prec)
     return S
 
 
