@@ -59,6 +59,8 @@ def _hbm_peak():
 
 HBM_PEAK_GBS = _hbm_peak()
 FLOPS_PER_PAIR = 24              # 8 (distance test) + 16 (LJ force), per in-cutoff pair
+FLOPS_PER_CHECK = 8              # per candidate distance check (a Verlet-list entry)
+FLOPS_PER_FORCE = 16             # per in-cutoff pair: rcp, (s/r)^6, the scalar, 3 FMA
 # DRAM bytes (read + write) per force launch of the direct walk (skin 0) from the committed
 # ncu capture of that kernel on this workload; None: not captured
 FORCE_TRAFFIC = {"mixed": 14.96e6, "fp64": None}
@@ -588,17 +590,21 @@ def main():
         sy.compute_forces()
         return sy
 
-    def timed_steps(sy, k, warm, phases):
+    def timed_steps(sy, k, warm, phases, on_ready=None):
         """per-step device times (ms), L2 flushed before each step; with
         phases, the step graph also records the library's per-phase events
         (force time per step for the roofline), which adds event nodes to
-        every step, so the headline pass runs without them"""
+        every step, so the headline pass runs without them.  on_ready runs
+        after the warm-up, before the timed steps (outside the timing)"""
         sy.set_timing(phases)
         for _ in range(warm):
             with torch.cuda.stream(stream):
                 flush()
             sy.step(1)
         sy.sync()
+        if on_ready is not None:
+            on_ready()
+            sy.sync()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(k)]
         force_ms, phase_sum, rebuilt, kinds, ents = [], {}, [], [], []
@@ -626,14 +632,21 @@ def main():
         timed_steps.entries = ents
         return [a.elapsed_time(b) for a, b in ev], force_ms, phase_sum
 
+    def total_energy(sy_):
+        pe, ke, _ = sy_.energy_virial()
+        return pe + ke
+
+    energy = {}
     sy = make_system(prec)
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
     with Clocks(local) as clk:
-        step_ms, _, _ = timed_steps(sy, args.steps, args.warmup, False)
+        step_ms, _, _ = timed_steps(sy, args.steps, args.warmup, False,
+                                    on_ready=lambda: energy.update(e0=total_energy(sy)))
     head_entries = timed_steps.entries
     torch.cuda.synchronize()
+    energy["e1"] = total_energy(sy)
     if dist is not None:
         dist.barrier()
     total_ms = sum(step_ms)
@@ -676,26 +689,35 @@ def main():
         entries = sum(list_ents) / len(list_ents)
         lkernel = "k_force_list_warp"
         alg_bytes = LIST_BYTES_PER_ENTRY * entries + LIST_BYTES_PER_PARTICLE * n
-        achieved = alg_bytes / (l_ms * 1e-3) / 1e9
+        achieved_gbs = alg_bytes / (l_ms * 1e-3) / 1e9
+        # algorithmic work: 8 flops per distance check (every list entry)
+        # and 16 more per in-cutoff pair (rcp, (s/r)^6, the scalar, 3 FMA)
+        alg_flops = FLOPS_PER_CHECK * entries + FLOPS_PER_FORCE * pairs
+        achieved = alg_flops / (l_ms * 1e-3) / 1e12
         cap = LIST_TRAFFIC.get(lkernel) or {}
         traffic = None
         if (cap.get("bytes") and n == N_DEFAULT and
                 (args.skin, args.skin_time, args.skin_floor, args.list_margin) == LIST_TRAFFIC_CONFIG):
             cap_alg = LIST_BYTES_PER_ENTRY * cap["entries"] + LIST_BYTES_PER_PARTICLE * n
             traffic = cap["bytes"] * alg_bytes / cap_alg
-        roofline = {"bound": "hbm", "achieved": achieved, "peak": HBM_PEAK_GBS, "unit": "GB/s",
-                    "frac": achieved / HBM_PEAK_GBS,
+        roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                    "frac": achieved / fp32_peak,
                     "traffic": traffic,
                     "traffic_note": ("ncu DRAM bytes of one captured launch, scaled from that "
                                      "launch's list entries to this run's mean by the algorithmic "
                                      "bytes"),
                     "kernel": f"{lkernel} (mixed, Verlet lists)",
-                    "peak_note": "measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                    "algorithmic_bytes_per_launch": alg_bytes, "list_entries": entries,
+                    "peak_note": ("FP32 FMA peak derived from 152 SMs x 128 lanes x 2 flops x the "
+                                  "median SM clock sampled during the timed region"),
+                    "algorithmic_flops_per_launch": alg_flops,
+                    "flops_convention": "8 per distance check (list entry) + 16 per in-cutoff pair",
+                    "list_entries": entries,
                     "launch_ms_avg": l_ms, "launches": len(list_steps),
-                    "flops_view": {"achieved": FLOPS_PER_PAIR * pairs / (l_ms * 1e-3) / 1e12,
-                                   "peak": fp32_peak, "unit": "TFLOP/s",
-                                   "frac": FLOPS_PER_PAIR * pairs / (l_ms * 1e-3) / 1e12 / fp32_peak},
+                    "hbm_view": {"achieved": achieved_gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                                 "frac": achieved_gbs / HBM_PEAK_GBS,
+                                 "algorithmic_bytes_per_launch": alg_bytes,
+                                 "bytes_convention": "4 B per list entry + 88 B per particle",
+                                 "peak_note": "measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
                     "phase_note": ("with the step graph's single conditional node the force phase "
                                    "of a rebuild step also holds the list build (sort, gather, "
                                    "class lists, capacity scan); the binning phase is empty"),
@@ -714,14 +736,38 @@ def main():
                                  "median SM clock sampled during the timed region",
                     "pairs_per_launch": pairs, "force_ms_avg": f_avg_ms}
 
-    # the plain FP64 GPU path on the same system (the comparison the metric names)
+    # the plain FP64 GPU path on the same system (the comparison the metric
+    # names), timed exactly like the headline: the same steps and warm-up,
+    # no per-phase events, L2 flushed before every step
     fp64_info = None
+    accuracy = None
     if not args.no_fp64_compare and prec == dcm.DCM_MIXED and rank == 0:
         sy64 = make_system(dcm.DCM_FP64)
-        k64 = max(4, min(20, args.steps // 10) // 2 * 2)
-        s64, f64, _ = timed_steps(sy64, k64, 2, True)
-        fp64_info = {"value": n * k64 / (sum(s64) * 1e-3), "unit": UNIT, "steps": k64,
-                     "ms_per_step": sum(s64) / k64, "force_ms_avg": sum(f64) / len(f64)}
+        e64 = {}
+        s64, _, _ = timed_steps(sy64, args.steps, args.warmup, False,
+                                on_ready=lambda: e64.update(e0=total_energy(sy64)))
+        e64["e1"] = total_energy(sy64)
+        t64 = sum(s64)
+        fp64_info = {"value": n * args.steps / (t64 * 1e-3), "unit": UNIT, "steps": args.steps,
+                     "warmup": args.warmup, "ms_per_step": t64 / args.steps,
+                     "energy_drift": abs(e64["e1"] - e64["e0"]) / abs(e64["e0"]),
+                     "speedup_of_mixed": t64 / total_ms,
+                     "kernel": "k_force (FP64 lanes walk over the Verlet lists)"}
+        # the mixed path's forces against FP64 forces at its final positions
+        # and cutoffs (per particle, the parity bar 1e-6 + 1e-5 |F|)
+        x_end, v_end, f_mix = sy.get_state()
+        _, rc_end, _ = sy.cutoffs()
+        sy64.set_state(x_end, v_end)
+        sy64.set_cutoffs(rc_end)
+        sy64.compute_forces()
+        _, _, f_ref = sy64.get_state()
+        err = np.linalg.norm(f_mix - f_ref, axis=1)
+        fmag = np.linalg.norm(f_ref, axis=1)
+        accuracy = {"max_abs": float(err.max()), "p99_abs": float(np.percentile(err, 99)),
+                    "max_err_over_bar": float(np.max(err / (1e-6 + 1e-5 * fmag))),
+                    "bar": "|F_mixed - F_fp64| <= 1e-6 + 1e-5 |F_fp64| per particle",
+                    "at": f"the final state of the timed run ({args.steps} steps)",
+                    "refined_last_step": int(sy.stats().refined)}
         sy64.close()
 
     # end to end through the public API with host buffers
@@ -786,6 +832,11 @@ def main():
         cfg["phase_note"] = ("per-phase CUDA events inside the step graph, on a second run of the "
                              "same steps from the same start (the timed run records none)")
         cfg["fp64_gpu_path"] = fp64_info
+        cfg["energy_drift"] = {"rel": abs(energy["e1"] - energy["e0"]) / abs(energy["e0"]),
+                               "steps": args.steps,
+                               "note": "|E(K) - E(0)| / |E(0)| over the timed steps (NVE; the "
+                                       "potential is truncated and unshifted, and r_c moves)"}
+        cfg["mixed_vs_fp64_forces"] = accuracy
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

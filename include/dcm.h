@@ -191,7 +191,10 @@ typedef struct {
     int32_t kernels_detect_reuse;          /* ... in a step with detection */
     int64_t cc_flipped;                    /* voxels the small-component removal
                                               changed in the last detection */
-    int64_t reserved[1];
+    int64_t refined;                       /* MIXED: particles whose forces the last
+                                              force pass evaluated again in
+                                              double-float (net force below
+                                              0.5 epsilon/sigma) */
 } dcm_stats;
 
 /* Phases of one step, in order, for dcm_get_phase_times. */

@@ -219,22 +219,23 @@ static int setup_geometry(const dcm_box *box, int64_t n, const dcm_params *p, Ge
     // and change fast with r, take the double-float path.  The FP32
     // cell-relative positions live on a grid qpos = 2^(e - 24) with 2^e above
     // every coordinate (a cell edge plus the drift allowed between list
-    // builds), every coordinate difference and every close-pair distance,
-    // so these all have at most 24 significant bits and the FP32 differences
-    // and cell shifts of a close pair are exact.
+    // builds) and every close-pair distance, so these have at most 24
+    // significant bits: a close pair's cell shift is then exact in FP32, and
+    // the rounding of its coordinate difference is recovered by TwoSum.
     const double rclose = 1.5 * p->sigma;
     g.rclose2 = (float)(rclose * rclose);
-    // The FP32 error left by the pairs beyond r_close is a few 1e-6
+    // The FP32 error left by the pairs beyond r_close is at most a few 1e-6
     // epsilon/sigma at liquid density; a particle whose net force is below
-    // 2 epsilon/sigma (where the tolerance 1e-6 + 1e-5 |F| falls under
-    // about 2e-5) has all its pairs evaluated again in double-float.
-    const double fredo = 2.0 * p->eps / p->sigma;
+    // 0.5 epsilon/sigma (where the tolerance 1e-6 + 1e-5 |F| falls under
+    // 6e-6) has all its pairs evaluated again in double-float.
+    const double fredo = 0.5 * p->eps / p->sigma;
     g.redo_f2 = (float)(fredo * fredo);
     double cmax = fmax(g.cedge[0], fmax(g.cedge[1], g.cedge[2]));
-    double bound = fmax(cmax + g.skin, rclose) + 0.25;
+    double bound = fmax(cmax + 0.5 * g.skin, rclose);
     int e = (int)ceil(log2(bound));
     g.qpos = (float)ldexp(1.0, e - 24);
     g.inv_qpos = (float)ldexp(1.0, 24 - e);
+    g.qtop = (float)ldexp(1.0, e);
     for (int a = 0; a < 3; ++a) {
         double cq = nearbyint(g.cedge[a] * (double)g.inv_qpos) * (double)g.qpos;
         g.cf[a] = (float)cq;   // exact: below 2^24 grid steps
@@ -287,7 +288,7 @@ static int64_t bytes_for(const Geom &g, int64_t n, int precision)
     int64_t ncell = g.ncell;
     int64_t nv = g.nvox;
     int64_t per_p = 3 * 8 * 3 + 8 + 8 + 1 + 4 * 3 + 16 + 4 + 4 + 8 + 48 + 24 + 2;
-    per_p += precision == DCM_FP64 ? 36 : 52;   // spd (FP64) or spl4 + rq + pk + inv (MIXED)
+    per_p += precision == DCM_FP64 ? 36 : 56;   // spd (FP64) or spl4 + refq + rq + pk + inv (MIXED)
     int64_t per_v = 4 + 4 + 4 + 8 + 1 + 8 + 8 + 4 + 16 + 2 + (g.cc_min > 0 ? 20 : 0);
     int64_t ntiles = (ncell + 2047) / 2048 + 1;
     int64_t lists = g.skin > 0 ? 4 * list_cap(g, n) + n * (4 + 4 + 24 + 8 + 8 + 20) : 0;
@@ -324,7 +325,7 @@ extern "C" int dcm_destroy(dcm_handle *h)
     for (int q = 0; q <= DCM_NUM_PHASES; ++q)
         if (h->ev[q]) cudaEventDestroy(h->ev[q]);
     void *ptrs[] = {h->x, h->v, h->f, h->d, h->rc, h->cls, h->cell_of, h->slot, h->cell_count,
-                    h->cell_start, h->sorted_id, h->scan_tmp, h->sp4, h->spl4, h->spd, h->rq, h->pk, h->inv, h->psys, h->vsys, h->class_list,
+                    h->cell_start, h->sorted_id, h->scan_tmp, h->sp4, h->spl4, h->refq, h->spd, h->rq, h->pk, h->inv, h->psys, h->vsys, h->class_list,
                     h->class_count_dev, h->B, h->sm1, h->sm2, h->Bs, h->S, h->D0, h->D1, h->stamp,
                     h->flist, h->fcount, h->kacc, h->npair, h->pe, h->vir, h->red_part, h->red_out,
                     h->err, h->stats, h->tmp3n, h->geo_dev, h->off_dev, h->nl, h->nl_cnt,
@@ -463,6 +464,7 @@ static int create_systems(int M, const dcm_box *boxes, const int64_t *ns, const 
     }
     if (h->p.precision != DCM_FP64) {
         ALLOC(h->spl4, N);
+        ALLOC(h->refq, N);
         ALLOC(h->rq, N);
         ALLOC(h->pk, N);
         ALLOC(h->inv, N);
@@ -1170,6 +1172,7 @@ extern "C" int dcm_get_stats(dcm_handle *h, dcm_stats *s)
     s->list_builds = (int64_t)st.list_builds;
     s->list_entries = (int64_t)st.list_entries;
     s->cc_flipped = (int64_t)st.cc_flipped;
+    s->refined = (int64_t)st.barrier[6];
     return DCM_OK;
 }
 

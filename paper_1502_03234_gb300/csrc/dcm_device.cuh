@@ -263,11 +263,10 @@ __device__ __forceinline__ float skin_share(const Geom &g, float speed, float fo
 // as computing them here), which keeps this to a few FP64 operations per
 // axis: the FP64 pipe runs at 1/64 of the FP32 rate.
 // The FP32 coordinate is a multiple of the system's grid qpos (a power of
-// two chosen so that coordinates, their differences and the cell shifts
-// have at most 24 significant bits), and lo receives the FP32 remainder
-// u - hi: the difference of two particles' coordinates and the cell shift
-// are then exact in FP32, and hi + lo carries the FP64 position to about
-// 2^-47 for the double-float close-pair forces.
+// two chosen so that coordinates and close-pair distances have at most 24
+// significant bits), and lo receives the FP32 remainder u - hi: a close
+// pair's cell shift is then exact in FP32, and hi + lo carries the FP64
+// position to about 2^-47 for the double-float close-pair forces.
 __device__ __forceinline__ float4 cell_rel_position(const Batch &b, const Geom &g, double px,
                                                    double py, double pz, int c_local, float4 &lo)
 {

@@ -42,7 +42,7 @@ constexpr float GUARD = 3.814697265625e-06f;   // 2^-18
 struct ListConst {
     float cf[3], cfl[3], ncx, halfnc;
     float sig2f, eps48f, eps24f, eps2f;
-    float sig2l, eps48l, eps24l, rclose2, redo_f2;
+    float sig2l, eps48l, eps24l, rclose2, redo_f2, qtop;
 };
 
 struct ForceArgs {
@@ -52,6 +52,8 @@ struct ForceArgs {
     int lanes[DCM_MAX_CLASSES];   // lanes per particle per class
     const float4 *sp4;
     const float4 *spl4;           // MIXED: remainders of the cell-relative positions
+    int32_t *refq;                // MIXED: sorted slots queued for the double-float refinement
+    unsigned int *refq_n;         // ... and their number
     const double4_32a *spd;
     const float4 *rq;             // MIXED: r_c^2, guard band, culling radius per slot
     const int4 *pk;               // MIXED: id, cell y, cell z per slot
@@ -761,20 +763,25 @@ __device__ __forceinline__ void close_disp(const C &c, float ncx, float halfnc, 
     float dcx = ui.w - uj.w;
     dcx -= dcx > halfnc ? ncx : 0.f;
     dcx += dcx < -halfnc ? ncx : 0.f;
-    dxh = fmaf(dcx, c.cf[0], __fsub_rn(ui.x, uj.x));
-    dyh = fmaf(-dyc, c.cf[1], __fsub_rn(ui.y, uj.y));
-    dzh = fmaf(-dzc, c.cf[2], __fsub_rn(ui.z, uj.z));
-    dxl = fmaf(dcx, c.cfl[0], __fsub_rn(uli.x, ulj.x));
-    dyl = fmaf(-dyc, c.cfl[1], __fsub_rn(uli.y, ulj.y));
-    dzl = fmaf(-dzc, c.cfl[2], __fsub_rn(uli.z, ulj.z));
+    // the coordinate differences on the grid: exact below qtop; a rare
+    // larger one (two particles drifted apart out of their cells) keeps
+    // what its rounding drops by TwoSum
+    float ax = __fsub_rn(ui.x, uj.x), ay = __fsub_rn(ui.y, uj.y), az = __fsub_rn(ui.z, uj.z);
+    float ex = 0.f, ey = 0.f, ez = 0.f;
+    if (fabsf(ax) >= c.qtop) two_sum(ui.x, -uj.x, ax, ex);
+    if (fabsf(ay) >= c.qtop) two_sum(ui.y, -uj.y, ay, ey);
+    if (fabsf(az) >= c.qtop) two_sum(ui.z, -uj.z, az, ez);
+    // plus the cell shift: exact, the result is a short multiple of the grid
+    dxh = fmaf(dcx, c.cf[0], ax);
+    dyh = fmaf(-dyc, c.cf[1], ay);
+    dzh = fmaf(-dzc, c.cf[2], az);
+    dxl = __fadd_rn(fmaf(dcx, c.cfl[0], __fsub_rn(uli.x, ulj.x)), ex);
+    dyl = __fadd_rn(fmaf(-dyc, c.cfl[1], __fsub_rn(uli.y, ulj.y)), ey);
+    dzl = __fadd_rn(fmaf(-dzc, c.cfl[2], __fsub_rn(uli.z, ulj.z)), ez);
 }
 
 __device__ __forceinline__ float entry_dy(int e) { return (float)(((e >> 24) & 15) - 8); }
 __device__ __forceinline__ float entry_dz(int e) { return (float)((int)((unsigned)e >> 28) - 8); }
-
-template <bool ENERGY, bool SINGLE>
-__device__ __noinline__ void particle_force_warp_ff(const ForceArgs &a, FwTable &tb, int k,
-                                                     int lane);
 
 // Direct walk of particle k (sorted slot).  FILL (a Verlet-list rebuild):
 // the walk also covers the list radius R_k of the gather kernel and appends
@@ -950,11 +957,15 @@ __device__ __forceinline__ void particle_force_warp(const ForceArgs &a, FwTable 
                         acc.close(g, dxh, dyh, dzh, dxl, dyl, dzl);
                     }
                 } else {
+                    // (most chunks hold no close pair: one vote skips the
+                    // stash bookkeeping for them)
                     const unsigned cm = __ballot_sync(0xffffffffu, cl);
-                    const int at = ncs + __popc(cm & (lane_le >> 1));
-                    cl = cl && at < FW_CLOSE;
-                    if (cl) stash[at] = ((j - k) & 0xffffff) | tb.rt[rowi];
-                    ncs = min(ncs + __popc(cm), FW_CLOSE);
+                    if (cm) {
+                        const int at = ncs + __popc(cm & (lane_le >> 1));
+                        cl = cl && at < FW_CLOSE;
+                        if (cl) stash[at] = ((j - k) & 0xffffff) | tb.rt[rowi];
+                        ncs = min(ncs + __popc(cm), FW_CLOSE);
+                    }
                     if (p < T) acc.pair(g, dx, dy, dz, r2, in && !cl);
                 }
             }
@@ -997,20 +1008,9 @@ __device__ __forceinline__ void particle_force_warp(const ForceArgs &a, FwTable 
     const float f2 = acc.store(a, i, lane);
     if constexpr (!FF) {
         // a net force small against the FP32 error of the pairs beyond
-        // r_close: all of this particle's pairs again in double-float
-        if (f2 < g.redo_f2) particle_force_warp_ff<ENERGY, SINGLE>(a, tb, k, lane);
+        // r_close: queued for k_force_refine (all its pairs in double-float)
+        if (f2 < g.redo_f2 && lane == 0) a.refq[atomicAdd(a.refq_n, 1u)] = k;
     }
-}
-
-// the refinement pass of one particle, out of line: it keeps the
-// double-float arithmetic out of the main walk's register budget
-template <bool ENERGY, bool SINGLE>
-__device__ __noinline__ void particle_force_warp_ff(const ForceArgs &a, FwTable &tb, int k,
-                                                     int lane)
-{
-    int ng = 0;
-    long long entries = 0;
-    particle_force_warp<ENERGY, false, SINGLE, true>(a, tb, nullptr, k, lane, ng, false, entries);
 }
 
 // exact sum over the G lanes of one group (G a power of two <= 32) of three
@@ -1236,51 +1236,80 @@ __device__ __forceinline__ void particle_force_list_group(const ForceArgs &a, in
     // ---- sums over the group; lane q of the group writes value q
     float f2 = group_store<ENERGY, G>(a, acc, k >= 0, i, gl);
     // a net force small against the FP32 error of the pairs beyond r_close:
-    // the particle's whole list again, every in-cutoff pair in double-float
-    // (same pair decisions), and its results stored again
-    const bool redo = k >= 0 && f2 < (SINGLE ? a.lc.redo_f2 : g.redo_f2);
-    if (__any_sync(0xffffffffu, redo)) {
-        WarpAcc<ENERGY> acc2;
-        if (redo) {
-            const float4 uli = a.spl4[k];
-            const float4 q4 = a.rq[k];
-            const float rc2f = q4.x, rc2lo = q4.y, rc2hi = q4.z;
-            const float cf0 = SINGLE ? a.lc.cf[0] : g.cf[0];
-            const float cf1 = SINGLE ? a.lc.cf[1] : g.cf[1];
-            const float cf2 = SINGLE ? a.lc.cf[2] : g.cf[2];
-            const int32_t *list = a.nl + a.nl_start[k];
-            const int cnt = a.nl_cnt[k];
-            for (int p = gl; p < cnt; p += G) {
-                const int e = list[p];
-                const int j = e & 0xffffff;
-                const float4 uj = a.sp4[j];
-                float dcx = ui.w - uj.w;
-                dcx -= dcx > halfnc ? ncx : 0.f;
-                dcx += dcx < -halfnc ? ncx : 0.f;
-                float dx = fmaf(dcx, cf0, ui.x - uj.x);
-                float dy = fmaf(-entry_dy(e), cf1, ui.y - uj.y);
-                float dz = fmaf(-entry_dz(e), cf2, ui.z - uj.z);
-                float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                bool in = r2 < rc2f;
-                if (r2 >= rc2lo && r2 < rc2hi) {
-                    double rci = a.rc[i];
-                    in = fp64_inside(a, g, i, a.sorted_id[j], DMUL(rci, rci));
-                }
-                if (in) {
-                    float dxh, dyh, dzh, dxl, dyl, dzl;
-                    if constexpr (SINGLE) {
-                        close_disp(a.lc, ncx, halfnc, ui, uli, uj, a.spl4[j], entry_dy(e),
-                                   entry_dz(e), dxh, dyh, dzh, dxl, dyl, dzl);
-                        acc2.close(a.lc, dxh, dyh, dzh, dxl, dyl, dzl);
-                    } else {
-                        close_disp(g, ncx, halfnc, ui, uli, uj, a.spl4[j], entry_dy(e),
-                                   entry_dz(e), dxh, dyh, dzh, dxl, dyl, dzl);
-                        acc2.close(g, dxh, dyh, dzh, dxl, dyl, dzl);
-                    }
-                }
-            }
+    // queued for k_force_refine (all its pairs in double-float)
+    if (k >= 0 && gl == 0 && f2 < (SINGLE ? a.lc.redo_f2 : g.redo_f2))
+        a.refq[atomicAdd(a.refq_n, 1u)] = k;
+}
+
+// One queued particle again over its Verlet list, one warp per particle,
+// every in-cutoff pair in double-float (the same pair decisions as the list
+// kernel: FP32 r^2 from the grid positions, FP64 re-decision in the guard
+// band), its results stored again.
+template <bool ENERGY, bool SINGLE>
+__device__ __forceinline__ void refine_list(const ForceArgs &a, int k, int lane)
+{
+    const Geom &g = a.b.sys[SINGLE ? 0 : sys_p(a.b, k)];
+    const float ncx = (float)g.nc[0], halfnc = 0.5f * (float)g.nc[0];
+    const float4 ui = a.sp4[k], uli = a.spl4[k], q4 = a.rq[k];
+    const int i = a.pk[k].x;
+    const float rc2f = q4.x, rc2lo = q4.y, rc2hi = q4.z;
+    const int32_t *list = a.nl + a.nl_start[k];
+    const int cnt = a.nl_cnt[k];
+    WarpAcc<ENERGY> acc;
+    for (int p = lane; p < cnt; p += 32) {
+        const int e = list[p];
+        const int j = e & 0xffffff;
+        const float4 uj = a.sp4[j];
+        float dcx = ui.w - uj.w;
+        dcx -= dcx > halfnc ? ncx : 0.f;
+        dcx += dcx < -halfnc ? ncx : 0.f;
+        const float dx = fmaf(dcx, g.cf[0], ui.x - uj.x);
+        const float dy = fmaf(-entry_dy(e), g.cf[1], ui.y - uj.y);
+        const float dz = fmaf(-entry_dz(e), g.cf[2], ui.z - uj.z);
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        bool in = r2 < rc2f;
+        if (r2 >= rc2lo && r2 < rc2hi) {
+            double rci = a.rc[i];
+            in = fp64_inside(a, g, i, a.sorted_id[j], DMUL(rci, rci));
         }
-        group_store<ENERGY, G>(a, acc2, redo, i, gl);
+        if (in) {
+            float dxh, dyh, dzh, dxl, dyl, dzl;
+            close_disp(g, ncx, halfnc, ui, uli, uj, a.spl4[j], entry_dy(e), entry_dz(e), dxh, dyh,
+                       dzh, dxl, dyl, dzl);
+            acc.close(g, dxh, dyh, dzh, dxl, dyl, dzl);
+        }
+    }
+    acc.store(a, i, lane);
+}
+
+// The double-float refinement of the particles the force kernels queued
+// (net force below 0.5 epsilon/sigma, about 2-4 % of a slab's particles,
+// mostly vapor): a warp per particle.  On a step that keeps its Verlet
+// lists, over the particle's list (complete by the reuse test); otherwise
+// (no lists, or a rebuild step: the cell sort is fresh) by the direct walk.
+// Runs after the force kernels of the step, so the queue is complete.
+template <bool ENERGY, bool SINGLE>
+__global__ void __launch_bounds__(FW_THREADS) k_force_refine(const __grid_constant__ ForceArgs a)
+{
+    __shared__ FwTable s_tab[FW_WARPS];
+    const int lane = threadIdx.x & 31;
+    const int w = blockIdx.x * FW_WARPS + (threadIdx.x >> 5);
+    const int nw = gridDim.x * FW_WARPS;
+    const int total = (int)*(volatile unsigned int *)a.refq_n;
+    // the lists are complete on a step that keeps them, and on a rebuild
+    // step once the fill ran and no particle overflowed its capacity
+    const bool lists = a.nl != nullptr &&
+                       (a.list_flags[LF_REBUILD] == 0 ||
+                        (a.list_flags[LF_FILL] != 0 && a.list_flags[LF_OVERFLOW] == 0));
+    int ng = 0;
+    long long entries = 0;
+    for (int t = w; t < total; t += nw) {
+        const int k = a.refq[t];
+        if (lists)
+            refine_list<ENERGY, SINGLE>(a, k, lane);
+        else
+            particle_force_warp<ENERGY, false, SINGLE, true>(a, s_tab[threadIdx.x >> 5], nullptr,
+                                                             k, lane, ng, false, entries);
     }
 }
 
@@ -1435,6 +1464,17 @@ static void launch_walk(dcm_handle *h, const ForceArgs &a)
             <<<h->num_sms * FW_WALK_MINB, FW_THREADS, 0, h->stream>>>(a);
 }
 
+// the refinement of the queued particles (after the step's force kernels)
+template <bool ENERGY>
+static void launch_refine(dcm_handle *h, const ForceArgs &a)
+{
+    const int grid = h->num_sms * 4;
+    if (h->b.M == 1)
+        k_force_refine<ENERGY, true><<<grid, FW_THREADS, 0, h->stream>>>(a);
+    else
+        k_force_refine<ENERGY, false><<<grid, FW_THREADS, 0, h->stream>>>(a);
+}
+
 // ten single-system walk blocks per SM need the largest shared-memory carveout
 int prepare_force_kernels()
 {
@@ -1447,6 +1487,19 @@ int prepare_force_kernels()
                                              (int)cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return fail_cuda(e, "walk carveout", __FILE__, __LINE__);
     }
+    // the list force's close-pair slots take shared memory; ask for the
+    // smallest carveout that holds them, which leaves the rest of the unified
+    // L1 to the neighbour positions it gathers
+    const void *lf[] = {(const void *)k_force_list_warp<false, 8, true>,
+                        (const void *)k_force_list_warp<false, 8, false>,
+                        (const void *)k_force_list_warp<false, 4, true>,
+                        (const void *)k_force_list_warp<false, 4, false>,
+                        (const void *)k_force_list_warp<false, 16, false>,
+                        (const void *)k_force_list_warp<false, 32, false>};
+    for (const void *f : lf) {
+        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 16);
+        if (e != cudaSuccess) return fail_cuda(e, "list carveout", __FILE__, __LINE__);
+    }
     return DCM_OK;
 }
 
@@ -1458,7 +1511,8 @@ int launch_list_forces(dcm_handle *h, bool energy, int part)
 {
     ForceArgs a;
     fill_args(h, a);
-    // inside a captured step the drift has zeroed both queues
+    // inside a captured step the drift has zeroed the queues
+    if (!h->in_step) cudaMemsetAsync(a.refq_n, 0, sizeof(unsigned int), h->stream);
     if (part != 1) {
         if (!h->in_step) cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), h->stream);
         if (energy)
@@ -1486,6 +1540,10 @@ int launch_list_forces(dcm_handle *h, bool energy, int part)
             else k_force_list_warp<false, 8, false><<<gl, FW_THREADS, 0, h->stream>>>(a);
         }
     }
+    if (energy)
+        launch_refine<true>(h, a);
+    else
+        launch_refine<false>(h, a);
     return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "force launch");
 }
 
@@ -1500,11 +1558,15 @@ int launch_forces(dcm_handle *h, bool energy)
     // a captured step's drift zeroes the warp walk's queue)
     if (fp64 || !h->in_step) cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), h->stream);
     if (!fp64) {
-        // DCM_MIXED: the warp walk
-        if (energy)
+        // DCM_MIXED: the warp walk, then the refinement of what it queued
+        if (!h->in_step) cudaMemsetAsync(a.refq_n, 0, sizeof(unsigned int), h->stream);
+        if (energy) {
             launch_walk<true, false>(h, a);
-        else
+            launch_refine<true>(h, a);
+        } else {
             launch_walk<false, false>(h, a);
+            launch_refine<false>(h, a);
+        }
         return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "force launch");
     }
     int block = h->tune.block >= 64 && h->tune.block <= FORCE_THREADS ? h->tune.block : FORCE_THREADS;
@@ -1527,6 +1589,8 @@ static void fill_args(dcm_handle *h, ForceArgs &a)
     }
     a.sp4 = h->sp4;
     a.spl4 = h->spl4;
+    a.refq = h->refq;
+    a.refq_n = &h->stats->barrier[6];
     a.spd = h->spd;
     a.rq = h->rq;
     a.pk = h->pk;
@@ -1569,6 +1633,7 @@ static void fill_args(dcm_handle *h, ForceArgs &a)
         a.lc.eps24l = g0.eps24l;
         a.lc.rclose2 = g0.rclose2;
         a.lc.redo_f2 = g0.redo_f2;
+        a.lc.qtop = g0.qtop;
     }
     a.d = h->d;
     a.list_delta = 0.f;

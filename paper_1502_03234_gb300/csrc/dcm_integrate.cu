@@ -20,10 +20,12 @@ __global__ void k_kick_drift(Batch b, double *__restrict__ x, double *__restrict
                              const double *__restrict__ rc, ListTest t, unsigned int *queues)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    // the step's force work queues (a captured step has no memset nodes)
+    // the step's force work queues and refinement queue (a captured step
+    // has no memset nodes)
     if (queues && i == 0) {
         queues[0] = 0u;
         queues[3] = 0u;
+        queues[4] = 0u;
     }
     float mp = -3.0e38f, mq = -3.0e38f;
     if (i < b.N) {

@@ -59,8 +59,9 @@ struct DevStats {
     double c_liquid;             // system 0
     double c_vapor;
     int class_count[DCM_MAX_CLASSES];
-    unsigned int barrier[6];     // [0..1] grid barrier, [2] force queue, [3] CFSM result buffer,
-                                 // [4] first CFSM pass of the cluster tail, [5] list-force queue
+    unsigned int barrier[8];     // [0..1] grid barrier, [2] force queue, [3] CFSM result buffer,
+                                 // [4] first CFSM pass of the cluster tail, [5] list-force queue,
+                                 // [6] particles queued for the double-float refinement
     unsigned long long list_builds;
     unsigned long long list_entries;
     unsigned long long cc_flipped;   // voxels the small-component removal changed (last detection)
@@ -90,6 +91,7 @@ struct Geom {
     float cfl[3];                // cedge - cf in FP32 (the low part of the cell edge)
     float qpos;                  // grid of the FP32 cell-relative positions (a power of two)
     float inv_qpos;              // 1 / qpos (exact)
+    float qtop;                  // 2^24 qpos: grid values below it in magnitude are exact in FP32
     int smax[3];                 // largest stencil radius in cells
     int gd[3];                   // voxels per axis
     double inv_h[3];             // gd / L
@@ -185,6 +187,7 @@ struct dcm_handle {
     int32_t *cell_of, *slot, *cell_count, *cell_start, *sorted_id, *scan_tmp;
     float4 *sp4;
     float4 *spl4;                // MIXED: low parts of the cell-relative positions
+    int32_t *refq;               // MIXED: sorted slots queued for the double-float refinement
     double4_32a *spd;
     float4 *rq;                  // MIXED: per sorted slot r_c^2, guard band, culling radius
     int32_t *inv;                // sorted slot of each particle (id order), MIXED

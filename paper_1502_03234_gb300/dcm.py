@@ -80,7 +80,7 @@ class dcm_stats(C.Structure):
                 ("kernels_plain", C.c_int32), ("kernels_detect", C.c_int32),
                 ("list_builds", C.c_int64), ("list_entries", C.c_int64),
                 ("kernels_plain_reuse", C.c_int32), ("kernels_detect_reuse", C.c_int32),
-                ("cc_flipped", C.c_int64), ("reserved", C.c_int64 * 1)]
+                ("cc_flipped", C.c_int64), ("refined", C.c_int64)]
 
 
 _lib = None
