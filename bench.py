@@ -94,7 +94,10 @@ def parse():
     ap.add_argument("--cell-min", type=float, default=0.0,
                     help="link-cell edge target in sigma (0: the library's, r_c,min / 2)")
     ap.add_argument("--list-lanes", type=int, default=0, choices=[0, 4, 8, 16, 32],
-                    help="lanes per particle of the Verlet-list force (0: the library's default)")
+                    help="lanes per particle of the Verlet-list force (0: tuned on a scratch "
+                         "copy of the system before the timed run, see --no-tune)")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the library's default launch shape instead of tuning it")
     ap.add_argument("--step-graph", default="branched", choices=["branched", "flat"],
                     help="flat: no conditional nodes in the step graph (for per-kernel profiling)")
     ap.add_argument("--skin-time", type=float, default=0.06,
@@ -637,6 +640,21 @@ def main():
         return pe + ke
 
     energy = {}
+    # the launch shape: tuned on a scratch copy of the system (same start,
+    # a few steps in), then used by the timed system
+    tuning = None
+    if not args.list_lanes and not args.no_tune:
+        from paper_1502_03234_gb300 import autotune
+
+        scratch = make_system(prec)
+        scratch.step(4)
+        choice = autotune.tune_live(scratch, reps=5)
+        scratch.close()
+        tuning = {k: v for k, v in choice.items() if k in ("walk", "lanes", "block", "list_lanes",
+                                                              "force_ms")}
+        tuning["how"] = "autotune.tune_live on a scratch copy of the slab, 4 steps in"
+        if prec == dcm.DCM_MIXED:
+            args.list_lanes = int(choice.get("list_lanes", 8))
     sy = make_system(prec)
     if dist is not None:
         dist.barrier()
@@ -831,6 +849,8 @@ def main():
         cfg["phase_ms_avg"] = {k: v / phase_steps for k, v in phase_sum.items()}
         cfg["phase_note"] = ("per-phase CUDA events inside the step graph, on a second run of the "
                              "same steps from the same start (the timed run records none)")
+        cfg["tuning"] = tuning
+        cfg["list_lanes"] = args.list_lanes
         cfg["fp64_gpu_path"] = fp64_info
         cfg["energy_drift"] = {"rel": abs(energy["e1"] - energy["e0"]) / abs(energy["e0"]),
                                "steps": args.steps,

@@ -507,6 +507,11 @@ class System:
         (DCM_MIXED always runs the warp kernels)"""
         dcm_set_tuning(self.h, lanes, block, walk, list_lanes)
 
+    def set_step(self, step: int):
+        """the global step counter (detection runs on steps divisible by
+        detect_every): continue a resumed run on its original cadence"""
+        dcm_set_step(self.h, step)
+
     def set_step_graph(self, shape: int):
         """DCM_GRAPH_BRANCHED (default) or DCM_GRAPH_FLAT"""
         t = dcm_get_tuning(self.h)

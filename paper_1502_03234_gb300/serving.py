@@ -9,6 +9,16 @@ different requests run concurrently on the GPU, and requests that arrive
 while others are running join between chunks -- the batch changes
 continuously instead of draining before new work is taken.
 
+Under budget pressure a running request can be evicted (``evict_after``):
+when the oldest waiting request has waited that long and does not fit, the
+running requests with the most work left stop taking chunks, and once their
+chunks have drained each one's state (positions, velocities, step counter)
+is read back, its handle is released, and it waits again; re-admitted, it
+continues from that state.  Chunks end on even steps, the detection
+boundaries, so a request resumed without Verlet lists reproduces the
+uninterrupted run bit for bit (with lists, its lists are rebuilt at the
+resume and it agrees within the force tolerance).
+
 Latency is measured from arrival to the read-back of the final state; the
 report gives p50/p99 latency, queueing delay and aggregate atom-steps/s.
 
@@ -46,6 +56,10 @@ class Job:
     error: str | None = None
     bytes: int = 0
     cancel: bool = False
+    resume_step: int = 0                 # step counter of the state in x, v (after an eviction)
+    evictions: int = 0
+    evicting: bool = False
+    since_admit: int = 0                 # chunks completed since the last admission
 
     @property
     def latency(self) -> float | None:
@@ -82,6 +96,11 @@ class Backend:
     def release(self, slot) -> None:
         raise NotImplementedError
 
+    def checkpoint(self, slot) -> tuple:
+        """(x, v) of a slot with no chunk in flight, to resume it later
+        through start() with job.x, job.v and job.resume_step."""
+        raise NotImplementedError
+
 
 @dataclass
 class Report:
@@ -92,6 +111,7 @@ class Report:
     peak_bytes: int
     max_active: int
     offered_atom_steps_per_s: float = 0.0
+    evictions: int = 0
 
     @property
     def throughput(self) -> float:
@@ -115,7 +135,7 @@ class Report:
              "queue_delay_s": {"p50": float(np.percentile(qd, 50)) if qd else None,
                                "p99": float(np.percentile(qd, 99)) if qd else None},
              "budget_bytes": self.budget_bytes, "peak_bytes": self.peak_bytes,
-             "max_active": self.max_active,
+             "max_active": self.max_active, "evictions": self.evictions,
              "offered_atom_steps_per_s": self.offered_atom_steps_per_s}
         if self.offered_atom_steps_per_s:
             d["load"] = ("overloaded" if self.offered_atom_steps_per_s > self.throughput * 1.05
@@ -128,14 +148,18 @@ class Server:
 
     def __init__(self, backend: Backend, budget_bytes: int, max_slots: int = 16,
                  chunk_steps: int = 50, ahead: int = 2, clock=time.perf_counter,
-                 sleep=time.sleep):
+                 sleep=time.sleep, evict_after: float | None = None, max_evictions: int = 1):
         self.backend = backend
         self.budget = int(budget_bytes)
         self.max_slots = int(max_slots)
-        self.chunk = int(chunk_steps)
+        # chunks end on detection boundaries (detect_every = 2): a resumed
+        # request re-detects at the step the uninterrupted run does
+        self.chunk = max(2, int(chunk_steps) // 2 * 2)
         self.ahead = int(ahead)
         self.clock = clock
         self.sleep = sleep
+        self.evict_after = evict_after        # None: never evict
+        self.max_evictions = int(max_evictions)
 
     def run(self, jobs: list, realtime: bool = True) -> Report:
         """Serve jobs (each with its arrival time); returns when all ended."""
@@ -144,7 +168,8 @@ class Server:
         future = deque(sorted(jobs, key=lambda j: j.arrival))
         pending: deque = deque()
         active = {}                     # rid -> (job, slot)
-        used = peak = max_active = 0
+        used = peak = max_active = evictions = 0
+        waiting_since = {}              # rid -> time it (re)entered the queue
         while future or pending or active:
             t = now()
             while future and (not realtime or future[0].arrival <= t):
@@ -158,6 +183,7 @@ class Server:
                     j.finished_at = t
                     continue
                 pending.append(j)
+                waiting_since[j.rid] = t
             progressed = False
             # admission in arrival order; a request that does not fit yet
             # lets later, smaller ones in (first fit) without losing its place
@@ -180,12 +206,32 @@ class Server:
                     j.finished_at = now()
                     continue
                 j.status = RUNNING
-                j.admitted_at = now()
+                if j.admitted_at is None:
+                    j.admitted_at = now()
+                j.since_admit = 0
                 used += j.bytes
                 peak = max(peak, used)
                 active[j.rid] = (j, slot)
                 max_active = max(max_active, len(active))
                 progressed = True
+            # eviction under budget pressure: the oldest waiting request has
+            # waited evict_after and does not fit; the running requests with
+            # the most work left (each evicted at most max_evictions times,
+            # and only after a chunk since its admission) stop taking chunks
+            if self.evict_after is not None and pending and len(active) > 0:
+                h = pending[0]
+                deficit = used + h.bytes - self.budget
+                if deficit > 0 and now() - waiting_since.get(h.rid, 0.0) >= self.evict_after:
+                    already = sum(j.bytes for j, _ in active.values() if j.evicting)
+                    cand = sorted((j for j, _ in active.values()
+                                   if not j.evicting and j.evictions < self.max_evictions
+                                   and j.since_admit > 0 and j.steps_done < j.nsteps),
+                                  key=lambda j: (j.nsteps - j.steps_done) * j.n, reverse=True)
+                    for j in cand:
+                        if already >= deficit:
+                            break
+                        j.evicting = True
+                        already += j.bytes
             # advance: keep up to `ahead` chunks queued per slot
             for rid in list(active):
                 j, slot = active[rid]
@@ -196,6 +242,32 @@ class Server:
                     progressed = True
                     continue
                 inflight = self.backend.inflight(slot)
+                if j.evicting and inflight == 0:
+                    try:
+                        j.x, j.v = self.backend.checkpoint(slot)
+                        j.resume_step = j.steps_done
+                    except Exception as e:
+                        self._end(j, slot, FAILED, None, now(), err=f"checkpoint: {e}")
+                        used -= j.bytes
+                        del active[rid]
+                        progressed = True
+                        continue
+                    try:
+                        self.backend.release(slot)
+                    except Exception:
+                        pass
+                    used -= j.bytes
+                    del active[rid]
+                    j.status = QUEUED
+                    j.evicting = False
+                    j.evictions += 1
+                    evictions += 1
+                    pending.append(j)
+                    waiting_since[j.rid] = now()
+                    progressed = True
+                    continue
+                if j.evicting:
+                    continue
                 if j.steps_done >= j.nsteps and inflight == 0:
                     try:
                         res = self.backend.finish(slot)
@@ -206,6 +278,8 @@ class Server:
                     del active[rid]
                     progressed = True
                     continue
+                j.since_admit = max(j.since_admit, (j.steps_done - j.resume_step) // self.chunk
+                                    - inflight)
                 while inflight < self.ahead and j.steps_done < j.nsteps:
                     k = min(self.chunk, j.nsteps - j.steps_done)
                     self.backend.advance(slot, k)
@@ -220,7 +294,7 @@ class Server:
         offered = (float(sum(j.n * j.nsteps for j in jobs)) / span) if span > 0 else 0.0
         return Report(jobs=list(jobs), makespan=makespan, atom_steps=atom_steps,
                       budget_bytes=self.budget, peak_bytes=peak, max_active=max_active,
-                      offered_atom_steps_per_s=offered)
+                      offered_atom_steps_per_s=offered, evictions=evictions)
 
     def _end(self, job, slot, status, result, t, err=None):
         job.status = status
@@ -270,6 +344,8 @@ class DcmBackend(Backend):
             sy.set_tuning(self.tune.get("lanes", [2, 1, 2, 2]), self.tune.get("block", 128),
                           self.tune.get("walk", self.dcm.DCM_WALK_WARP))
         sy.set_state(job.x, job.v)
+        if job.resume_step:
+            sy.set_step(job.resume_step)     # the detection cadence continues
         return {"sys": sy, "stream": stream, "events": deque()}
 
     def advance(self, slot, nsteps: int) -> None:
@@ -291,6 +367,12 @@ class DcmBackend(Backend):
 
     def release(self, slot) -> None:
         slot["sys"].close()
+
+    def checkpoint(self, slot) -> tuple:
+        sy = slot["sys"]
+        sy.sync()
+        x, v, _ = sy.get_state()
+        return x, v
 
 
 def trace_jobs(requests, min_edge: float | None = 17.0) -> list:

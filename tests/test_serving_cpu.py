@@ -160,3 +160,72 @@ def test_trace_generator_shapes():
     assert ns.min() >= 2048 and ns.max() <= 524288
     lg = np.log(ns)
     assert abs(lg.mean() - 0.5 * (np.log(2048) + np.log(524288))) < 0.3   # log-uniform
+
+
+class ResumableBackend(FakeBackend):
+    """FakeBackend whose state is the number of steps a request has run:
+    checkpoint() reads it back, start() resumes from job.x."""
+
+    def start(self, job):
+        slot = super().start(job)
+        slot["steps"] = job.x if isinstance(job.x, int) else 0
+        assert slot["steps"] == job.resume_step
+        slot["resumed"] = job.resume_step > 0
+        return slot
+
+    def advance(self, slot, nsteps):
+        super().advance(slot, nsteps)
+        slot["steps"] += nsteps
+
+    def checkpoint(self, slot):
+        assert self.inflight(slot) == 0          # never while chunks run
+        return slot["steps"], None
+
+    def finish(self, slot):
+        return (slot["steps"], slot["resumed"], None)
+
+
+def test_eviction_frees_the_budget_and_resumes_the_victim():
+    # a long request holds the budget; a later one that does not fit waits
+    # evict_after, the long one is checkpointed at a chunk boundary and
+    # requeued, and finishes from its state once the other is done
+    c = Clock()
+    b = ResumableBackend(c, rate=1e7)
+    jobs = _jobs([(100000, 400, 0.0), (80000, 20, 0.05)])
+    budget = 100000 * 500 + 50000 * 500          # both do not fit at once
+    srv = sv.Server(b, budget, 4, 10, clock=c, sleep=c.sleep, evict_after=0.02)
+    rep = srv.run(jobs)
+    long, short = jobs
+    assert all(j.status == sv.DONE for j in jobs), [j.error for j in jobs]
+    assert rep.evictions == 1 and long.evictions == 1 and short.evictions == 0
+    assert long.result[0] == 400 and long.result[1]            # all steps, after a resume
+    assert long.resume_step % 2 == 0 and 0 < long.resume_step < 400
+    assert short.finished_at < long.finished_at                 # the waiter ran first
+    assert rep.peak_bytes <= budget
+    assert b.live == 0
+
+
+def test_no_eviction_without_the_policy_or_when_it_fits():
+    c = Clock()
+    b = ResumableBackend(c, rate=1e7)
+    jobs = _jobs([(100000, 200, 0.0), (80000, 20, 0.05)])
+    rep = sv.Server(b, 100000 * 500 + 50000 * 500, 4, 10, clock=c, sleep=c.sleep).run(jobs)
+    assert rep.evictions == 0 and jobs[1].admitted_at >= jobs[0].finished_at
+    c2 = Clock()
+    b2 = ResumableBackend(c2, rate=1e7)
+    jobs = _jobs([(100000, 200, 0.0), (80000, 20, 0.05)])
+    rep = sv.Server(b2, 10**9, 4, 10, clock=c2, sleep=c2.sleep, evict_after=0.0).run(jobs)
+    assert rep.evictions == 0                                   # it fits: nothing to evict
+
+
+def test_a_victim_is_evicted_at_most_max_evictions_times():
+    c = Clock()
+    b = ResumableBackend(c, rate=1e7)
+    # three large requests, room for one at a time: evictions bounded
+    jobs = _jobs([(100000, 300, 0.0), (100000, 300, 0.01), (100000, 300, 0.02)])
+    rep = sv.Server(b, 100000 * 500, 4, 10, clock=c, sleep=c.sleep, evict_after=0.005,
+                    max_evictions=1).run(jobs)
+    assert all(j.status == sv.DONE for j in jobs)
+    assert all(j.evictions <= 1 for j in jobs)
+    assert all(j.result[0] == 300 for j in jobs)
+    assert rep.peak_bytes <= 100000 * 500
