@@ -69,6 +69,7 @@ def _load():
         "orc_ms_energy": (d, [vp, vp, d, d, d, vp]),
         "orc_ms_segment": (None, [vp, vp, d, d, d, C.c_int, vp, vp]),
         "orc_ms_alternate": (C.c_int, [vp, vp, d, C.c_int, C.c_int, vp, vp, vp]),
+        "orc_ms_detect": (C.c_int, [vp, vp, d, d, C.c_int, C.c_int, vp]),
         "orc_label_components": (i64, [vp, vp, C.c_int, vp]),
         "orc_remove_small_components": (i64, [vp, vp, C.c_int]),
         "orc_godunov": (d, [vp, vp]),
@@ -275,6 +276,17 @@ def ms_alternate(dims, rho, nu, iters, max_outer, c_l, c_v):
     return S, cl.value, cv.value, rounds
 
 
+def ms_detect(dims, Bs, inv_scale, nu, iters, max_outer, S):
+    """Eq. 13 as the detection's segmentation step from labels S on
+    rho = Bs * inv_scale; returns (labels, rounds)"""
+    d = _i32(dims)
+    Bs = _f64(Bs).ravel()
+    S = np.ascontiguousarray(S, dtype=np.uint8).ravel().copy()
+    rounds = _load().orc_ms_detect(_p(d), _p(Bs), float(inv_scale), float(nu), int(iters),
+                                   int(max_outer), _p(S))
+    return S, rounds
+
+
 def label_components(dims, S, phase):
     """Section 4.2 / Algorithm 4.1: (labels, count) of the phase's components."""
     d = _i32(dims)
@@ -334,7 +346,9 @@ class _DetectParams(C.Structure):
                 ("voxel", C.c_double), ("smooth_order", C.c_int),
                 ("kmeans_max_iter", C.c_int), ("cfsm_iter_max", C.c_int),
                 ("cfsm_eps", C.c_double), ("n_classes", C.c_int),
-                ("min_component_voxels", C.c_int), ("cutoff_fn", C.c_int)]
+                ("min_component_voxels", C.c_int), ("cutoff_fn", C.c_int),
+                ("segmentation", C.c_int), ("ms_iters", C.c_int), ("ms_outer", C.c_int),
+                ("ms_nu", C.c_double)]
 
 
 class _RunParams(C.Structure):
@@ -356,12 +370,17 @@ class DetectParams:
     n_classes: int = 4
     min_component_voxels: int = 0
     cutoff_fn: int = 0
+    segmentation: int = 0
+    ms_iters: int = 50
+    ms_outer: int = 4
+    ms_nu: float = 0.005
 
     def _c(self) -> _DetectParams:
         return _DetectParams(self.rc_min, self.rc_max, self.alpha, self.voxel,
                              self.smooth_order, self.kmeans_max_iter, self.cfsm_iter_max,
                              self.cfsm_eps, self.n_classes, self.min_component_voxels,
-                             self.cutoff_fn)
+                             self.cutoff_fn, self.segmentation, self.ms_iters, self.ms_outer,
+                             self.ms_nu)
 
 
 @dataclass

@@ -465,9 +465,13 @@ int orc_kmeans(int64_t nvox, const double *Bs, int max_iter, uint8_t *S,
  * whose thresholded minimisers are exact minimisers of Eq. 13 for this
  * perimeter (discrete coarea formula).  It is solved by the first-order
  * primal-dual iteration of Chambolle and Pock with one dual variable per
- * face (|p| <= nu), step sizes tau = 1/4, sigma = 1/3 (tau sigma |grad|^2
- * <= 1 with |grad|^2 <= 12 in 3D), u starting at 1/2, a fixed number of
- * iterations; labels: liquid (s = 0) where u > 1/2. */
+ * face (|p| <= nu), step sizes tau = sigma = 0.99 / sqrt(12) (the method
+ * converges for tau sigma |grad|^2 < 1, and |grad|^2 = 12 for periodic
+ * forward differences in 3D, reached by the checkerboard mode), u starting
+ * at 1/2, a fixed number of iterations; labels: liquid (s = 0) where
+ * u > 1/2.  After a fixed number of iterations the relaxed u is converged
+ * only approximately; its threshold is an exact minimiser of Eq. 13 once u
+ * is converged. */
 double orc_ms_energy(const int dims[3], const double *rho, double c_l, double c_v, double nu,
                      const uint8_t *S)
 {
@@ -496,7 +500,7 @@ void orc_ms_segment(const int dims[3], const double *rho, double c_l, double c_v
     const int64_t nx = dims[0], ny = dims[1], nz = dims[2];
     const int64_t nv = nx * ny * nz;
     const int64_t n[3] = {nx, ny, nz};
-    const double tau = 0.25, sigma = 1.0 / 3.0;
+    const double tau = 0.99 / sqrt(12.0), sigma = tau;
     double *u = (double *)malloc(sizeof(double) * (size_t)nv);
     double *ub = (double *)malloc(sizeof(double) * (size_t)nv);
     double *r = (double *)malloc(sizeof(double) * (size_t)nv);
@@ -585,6 +589,49 @@ int orc_ms_alternate(const int dims[3], const double *rho, double nu, int iters,
     free(prev);
     *c_l_io = cl;
     *c_v_io = cv;
+    return round;
+}
+
+/* Eq. 13 as the segmentation step of the interface detection: on the
+ * smoothed density image of the detection, rho_v = Bs_v * inv_scale (the
+ * number density, inv_scale = 1 / (2^(3 order) V) for voxel volume V and
+ * smoothing order `order`), starting from the labels in S (the K-means
+ * labelling).  Each round takes the phase means of the current labels,
+ * c = (sum of Bs over the phase / its voxels) * inv_scale, with the sums
+ * exact (integers below 2^53), segments with those densities fixed
+ * (orc_ms_segment), and stops once the labels repeat, or after max_outer
+ * rounds.  A labelling with an empty phase is left as it is (no interface).
+ * S is updated in place; returns the rounds. */
+int orc_ms_detect(const int dims[3], const double *Bs, double inv_scale, double nu, int iters,
+                  int max_outer, uint8_t *S)
+{
+    const int64_t nv = (int64_t)dims[0] * dims[1] * dims[2];
+    double *rho = (double *)malloc(sizeof(double) * (size_t)(nv > 0 ? nv : 1));
+    uint8_t *prev = (uint8_t *)malloc((size_t)(nv > 0 ? nv : 1));
+    for (int64_t v = 0; v < nv; ++v) rho[v] = Bs[v] * inv_scale;
+    int round = 0;
+    while (round < max_outer) {
+        double sl = 0.0, sv = 0.0;
+        int64_t nl = 0, nvap = 0;
+        for (int64_t v = 0; v < nv; ++v) {
+            if (S[v] == 0) {
+                sl += Bs[v];
+                nl++;
+            } else {
+                sv += Bs[v];
+                nvap++;
+            }
+        }
+        if (nl == 0 || nvap == 0) break;
+        const double cl = (sl / (double)nl) * inv_scale;
+        const double cv = (sv / (double)nvap) * inv_scale;
+        memcpy(prev, S, (size_t)nv);
+        orc_ms_segment(dims, rho, cl, cv, nu, iters, S, NULL);
+        round++;
+        if (memcmp(prev, S, (size_t)nv) == 0) break;
+    }
+    free(rho);
+    free(prev);
     return round;
 }
 
@@ -941,6 +988,12 @@ int orc_detect(int64_t n, const double *x, const double L[3],
     orc_density(n, x, L, dims, B);
     orc_smooth(dims, B, p->smooth_order, Bs);
     orc_kmeans(nv, Bs, p->kmeans_max_iter > 0 ? p->kmeans_max_iter : 100, S, NULL, NULL);
+    if (p->segmentation == 1) {
+        const double V = (L[0] / dims[0]) * (L[1] / dims[1]) * (L[2] / dims[2]);
+        const double inv_scale = 1.0 / ldexp(V, 3 * (p->smooth_order > 0 ? p->smooth_order : 0));
+        orc_ms_detect(dims, Bs, inv_scale, p->ms_nu, p->ms_iters > 0 ? p->ms_iters : 50,
+                      p->ms_outer > 0 ? p->ms_outer : 4, S);
+    }
     orc_remove_small_components(dims, S, p->min_component_voxels);
     double h[3] = {L[0] / dims[0], L[1] / dims[1], L[2] / dims[2]};
     double hmax = h[0];

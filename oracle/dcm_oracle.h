@@ -137,6 +137,12 @@ void orc_ms_segment(const int dims[3], const double *rho, double c_l, double c_v
  * densities as the phase means, alternated from *c_l_io, *c_v_io (the K-means
  * centres) until the labels repeat or max_outer rounds; the final densities
  * are written back.  Returns the rounds. */
+/* Eq. 13 as the detection's segmentation step: on rho = Bs * inv_scale from
+ * the labels in S (updated in place), rounds of exact phase means and
+ * segmentation until the labels repeat or max_outer rounds; returns the
+ * rounds (see dcm_oracle.c). */
+int orc_ms_detect(const int dims[3], const double *Bs, double inv_scale, double nu, int iters,
+                  int max_outer, uint8_t *S);
 int orc_ms_alternate(const int dims[3], const double *rho, double nu, int iters, int max_outer,
                      uint8_t *S, double *c_l_io, double *c_v_io);
 
@@ -175,7 +181,8 @@ void orc_particle_distance(int64_t n, const double *x, const double L[3],
                            const int dims[3], const double *D, double *d);
 
 /* ---- full interface detection (Fig. 14 order) ---------------------------------
- * density -> smoothing -> K-means labels -> [small-component removal, when
+ * density -> smoothing -> K-means labels -> [Eq. 13 segmentation from them,
+ * when segmentation == 1] -> [small-component removal, when
  * min_component_voxels > 0] -> CFSM distance (cap r_grid =
  * rc_max + max h) -> particle distance -> cutoff (Eq. 7) -> class.  All
  * output arrays are nullable except d/rc/cls.  Returns CFSM passes (or -1). */
@@ -189,6 +196,10 @@ typedef struct {
     int n_classes;
     int min_component_voxels; /* Section 4.2; <= 0: no removal */
     int cutoff_fn;            /* 0: exponential (Eq. 7), 1: linear (Fig. 12) */
+    int segmentation;         /* 0: K-means labels (Eq. 11-14); 1: then Eq. 13 (orc_ms_detect) */
+    int ms_iters;             /* Eq. 13: primal-dual iterations per round; <= 0: 50 */
+    int ms_outer;             /* Eq. 13: rounds of segmentation and phase means; <= 0: 4 */
+    double ms_nu;             /* Eq. 13: perimeter weight (number-density units) */
 } orc_detect_params;
 
 int orc_detect(int64_t n, const double *x, const double L[3],
