@@ -89,6 +89,8 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--seg-steps", type=int, default=20,
+                    help="steps of the detection-with-Eq.-13 comparison (0: skip)")
     ap.add_argument("--skin", type=float, default=0.7,
                     help="Verlet-list skin in sigma (0: direct link-cell walk every step)")
     ap.add_argument("--cell-min", type=float, default=0.0,
@@ -754,6 +756,37 @@ def main():
                                  "median SM clock sampled during the timed region",
                     "pairs_per_launch": pairs, "force_ms_avg": f_avg_ms}
 
+    # detection with Eq. 13 (Section 4.1, DCM_SEG_MUMFORD_SHAH) in place of
+    # the K-means labels: per-phase times over a short run of the same slab
+    seg_info = None
+    if rank == 0 and prec == dcm.DCM_MIXED and args.seg_steps > 0:
+        def detect_ms(seg):
+            syx = dcm.System(slab.box, n, precision=prec, stream=stream.cuda_stream,
+                             skin=args.skin, list_margin=args.list_margin,
+                             skin_time=args.skin_time, skin_floor=args.skin_floor,
+                             cell_min=args.cell_min, segmentation=seg)
+            if args.list_lanes:
+                t = dcm.dcm_get_tuning(syx.h)
+                syx.set_tuning(list(t.lanes), t.block, t.walk, args.list_lanes)
+            syx.set_state(slab.x, slab.v)
+            syx.compute_forces()
+            ms_, ph_, _ = timed_steps(syx, args.seg_steps, 2, True)
+            st_ = syx.stats()
+            syx.close()
+            det_steps = max(1, args.seg_steps // 2)       # detection every second step
+            return {"ms_per_step": sum(ms_) / len(ms_),
+                    "detect_ms_per_detection": ph_.get("detect", 0.0) / det_steps,
+                    "kernels_detect_step": int(st_.kernels_detect)}
+        km = detect_ms(dcm.DCM_SEG_KMEANS)
+        mu = detect_ms(dcm.DCM_SEG_MUMFORD_SHAH)
+        seg_info = {"kmeans": km, "eq13": mu, "steps": args.seg_steps,
+                    "eq13_params": {"nu": 0.005, "iters": 50, "rounds_max": 4},
+                    "segmentation_share_of_detection":
+                        1.0 - km["detect_ms_per_detection"] / mu["detect_ms_per_detection"]
+                        if mu["detect_ms_per_detection"] > 0 else None,
+                    "note": "per-phase CUDA events over a short run from the same start; the "
+                            "share is that of the Eq. 13 step in a detection (thesis: 75-80 %)"}
+
     # the plain FP64 GPU path on the same system (the comparison the metric
     # names), timed exactly like the headline: the same steps and warm-up,
     # no per-phase events, L2 flushed before every step
@@ -852,6 +885,7 @@ def main():
         cfg["tuning"] = tuning
         cfg["list_lanes"] = args.list_lanes
         cfg["fp64_gpu_path"] = fp64_info
+        cfg["segmentation_eq13"] = seg_info
         cfg["energy_drift"] = {"rel": abs(energy["e1"] - energy["e0"]) / abs(energy["e0"]),
                                "steps": args.steps,
                                "note": "|E(K) - E(0)| / |E(0)| over the timed steps (NVE; the "

@@ -66,6 +66,7 @@ enum { DCM_FP64 = 0,   /* FP64 pair distances, forces and accumulation */
 };
 enum { DCM_HOST = 0, DCM_DEVICE = 1 };
 enum { DCM_CUTOFF_EXP = 0, DCM_CUTOFF_LINEAR = 1 };
+enum { DCM_SEG_KMEANS = 0, DCM_SEG_MUMFORD_SHAH = 1 };
 
 #define DCM_MAX_CLASSES 8
 
@@ -138,6 +139,19 @@ typedef struct {
        the straight line of Section 3.1 / Fig. 12 from (0, rc_max) to
        (rc_max, rc_min), with Eq. 7's outer cases.  Per system. */
     int32_t cutoff_fn;
+    /* Segmentation of the density image (Section 4.1).  DCM_SEG_KMEANS
+       (default): two-class K-means on the smoothed density (Eq. 11-14).
+       DCM_SEG_MUMFORD_SHAH: from those labels, Eq. 13 on the smoothed
+       number density rho = Bs / (2^(3 smooth_order) V) with perimeter weight
+       ms_nu (the thesis's 0.005 by default): rounds of exact phase means and
+       ms_iters primal-dual iterations of its convex relaxation (Chan,
+       Esedoglu, Nikolova; Chambolle-Pock, tau = sigma = 0.99/sqrt(12)), until
+       the labels repeat or ms_outer rounds.  Per handle (system 0's; every
+       system of an ensemble must agree). */
+    int32_t segmentation;
+    int32_t ms_iters;                      /* <= 0: 50 */
+    int32_t ms_outer;                      /* <= 0: 4 */
+    double ms_nu;                          /* >= 0; default 0.005 */
 } dcm_params;
 
 /* Force walk variants (dcm_tuning.walk).  DCM_WALK_WARP: one warp per

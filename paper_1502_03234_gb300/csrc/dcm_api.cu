@@ -90,6 +90,10 @@ extern "C" void dcm_default_params(dcm_params *p)
     p->precision = DCM_FP64;
     p->n_classes = 4;
     p->cell_min = 0.0;
+    p->segmentation = DCM_SEG_KMEANS;
+    p->ms_iters = 50;
+    p->ms_outer = 4;
+    p->ms_nu = 0.005;
 }
 
 extern "C" const char *dcm_last_error(void) { return g_errmsg; }
@@ -118,6 +122,10 @@ static int check_params(const dcm_box *box, int64_t n, const dcm_params *p)
         (p->skin > 0 && p->skin_time > 0.f && p->skin_floor > 0.5 * p->skin))
         return fail(DCM_ERR_ARG, "skin_time, skin_floor must be >= 0, skin_floor <= skin/2");
     if (p->min_component_voxels < 0) return fail(DCM_ERR_ARG, "min_component_voxels must be >= 0");
+    if (p->segmentation != DCM_SEG_KMEANS && p->segmentation != DCM_SEG_MUMFORD_SHAH)
+        return fail(DCM_ERR_ARG, "segmentation must be DCM_SEG_KMEANS or DCM_SEG_MUMFORD_SHAH");
+    if (!(p->ms_nu >= 0) || p->ms_iters > 100000 || p->ms_outer > 1000)
+        return fail(DCM_ERR_ARG, "need ms_nu >= 0, ms_iters <= 100000, ms_outer <= 1000");
     if (p->cutoff_fn != DCM_CUTOFF_EXP && p->cutoff_fn != DCM_CUTOFF_LINEAR)
         return fail(DCM_ERR_ARG, "cutoff_fn must be DCM_CUTOFF_EXP or DCM_CUTOFF_LINEAR");
     return DCM_OK;
@@ -165,6 +173,12 @@ static int setup_geometry(const dcm_box *box, int64_t n, const dcm_params *p, Ge
     }
     double hmax = fmax(g.h[0], fmax(g.h[1], g.h[2]));
     g.r_grid = p->rc_max + hmax;
+    // the same expression as the oracle's: voxel volume from the three
+    // quotients L / n, scaled by the smoothing mass 2^(3 order)
+    {
+        const double V = (L[0] / g.gd[0]) * (L[1] / g.gd[1]) * (L[2] / g.gd[2]);
+        g.ms_inv_scale = 1.0 / ldexp(V, 3 * (p->smooth_order > 0 ? p->smooth_order : 0));
+    }
     for (int a = 0; a < 3; ++a) g.w_h[a] = 1.0 / (g.h[a] * g.h[a]);
     g.e_min = 1.0 / sqrt(g.w_h[0] + g.w_h[1] + g.w_h[2]);
     g.rc_min = p->rc_min;
@@ -204,6 +218,8 @@ static int setup_geometry(const dcm_box *box, int64_t n, const dcm_params *p, Ge
     g.skin_time = p->skin_time;
     g.skin_floor = p->skin_floor;
     g.cc_min = p->min_component_voxels;
+    g.ms_nu = p->ms_nu;
+    g.ms_seg = p->segmentation == DCM_SEG_MUMFORD_SHAH ? 1 : 0;
     g.eps24 = 24.0 * p->eps;
     g.eps48 = 48.0 * p->eps;
     g.eps2 = 2.0 * p->eps;
@@ -289,7 +305,8 @@ static int64_t bytes_for(const Geom &g, int64_t n, int precision)
     int64_t nv = g.nvox;
     int64_t per_p = 3 * 8 * 3 + 8 + 8 + 1 + 4 * 3 + 16 + 4 + 4 + 8 + 48 + 24 + 2;
     per_p += precision == DCM_FP64 ? 36 : 56;   // spd (FP64) or spl4 + refq + rq + pk + inv (MIXED)
-    int64_t per_v = 4 + 4 + 4 + 8 + 1 + 8 + 8 + 4 + 16 + 2 + (g.cc_min > 0 ? 20 : 0);
+    int64_t per_v = 4 + 4 + 4 + 8 + 1 + 8 + 8 + 4 + 16 + 2 + (g.cc_min > 0 ? 20 : 0) +
+                    (g.ms_seg ? 80 : 0);
     int64_t ntiles = (ncell + 2047) / 2048 + 1;
     int64_t lists = g.skin > 0 ? 4 * list_cap(g, n) + n * (4 + 4 + 24 + 8 + 8 + 20) : 0;
     return n * per_p + ncell * 8 + 8 + nv * per_v + ntiles * 4 + 4096 + 256 * 8 * 8 + lists;
@@ -330,7 +347,8 @@ extern "C" int dcm_destroy(dcm_handle *h)
                     h->flist, h->fcount, h->kacc, h->npair, h->pe, h->vir, h->red_part, h->red_out,
                     h->err, h->stats, h->tmp3n, h->geo_dev, h->off_dev, h->nl, h->nl_cnt,
                     h->nl_start, h->nl_tiles, h->x_ref, h->rl_ref, h->sh_ref, h->sh, h->u_ref,
-                    h->disp, h->corner, h->lflags, h->cc, h->cc_tiles};
+                    h->disp, h->corner, h->lflags, h->cc, h->cc_tiles,
+                    h->msbuf, h->msacc, h->msc, h->msflag};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -359,9 +377,12 @@ static int create_systems(int M, const dcm_box *boxes, const int64_t *ns, const 
         if (rc) return rc;
         const dcm_params &a = ps[0], &q = ps[k];
         if (q.precision != a.precision || q.detect_every != a.detect_every ||
-            q.n_classes != a.n_classes || q.smooth_order != a.smooth_order)
-            return fail(DCM_ERR_ARG, "system %d: precision, detect_every, n_classes and "
-                                     "smooth_order must match system 0", k);
+            q.n_classes != a.n_classes || q.smooth_order != a.smooth_order ||
+            q.segmentation != a.segmentation || q.ms_iters != a.ms_iters ||
+            q.ms_outer != a.ms_outer)
+            return fail(DCM_ERR_ARG, "system %d: precision, detect_every, n_classes, "
+                                     "smooth_order, segmentation, ms_iters and ms_outer must "
+                                     "match system 0", k);
         ntot += ns[k];
     }
     if (ntot > (int64_t)0x7fffffff / 4) return fail(DCM_ERR_ARG, "too many particles in total");
@@ -483,6 +504,12 @@ static int create_systems(int M, const dcm_box *boxes, const int64_t *ns, const 
     for (int k = 0; k < M; ++k) h->cc_on = h->cc_on || h->geo_host[k].cc_min > 0;
     ALLOC(h->fcount, 4);
     ALLOC(h->kacc, 9 * 16 * (int64_t)M);   // K-means sums, 16 spread slots each
+    if (h->p.segmentation == DCM_SEG_MUMFORD_SHAH) {
+        ALLOC(h->msbuf, 10 * nv);
+        ALLOC(h->msacc, 4 * (int64_t)M);
+        ALLOC(h->msc, 2 * (int64_t)M);
+        ALLOC(h->msflag, 2 * (int64_t)M);
+    }
     ALLOC(h->npair, N);
     ALLOC(h->pe, N);
     ALLOC(h->vir, 6 * N);

@@ -1053,6 +1053,11 @@ int launch_detect(dcm_handle *h)
         }
         if (rc) return rc;
     }
+    // Eq. 13 from the K-means labels
+    if (h->p.segmentation == DCM_SEG_MUMFORD_SHAH) {
+        int rc = launch_ms_detect(h);
+        if (rc) return rc;
+    }
     // Section 4.2: small components of either phase change phase
     if (h->cc_on) {
         int rc = launch_components(h, b, h->S, -1, h->cc_ntiles);

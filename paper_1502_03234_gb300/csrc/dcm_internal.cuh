@@ -111,6 +111,9 @@ struct Geom {
     float halfLf[3];             // FP32 half edges
     float skin_time, skin_floor; // velocity-adaptive skin shares (skin_time 0: skin/2 each)
     int cc_min;                  // Section 4.2: components below this many voxels change phase (0: off)
+    double ms_nu;                // Eq. 13: perimeter weight (number-density units)
+    int ms_seg;                  // Eq. 13 segmentation after K-means (DCM_SEG_MUMFORD_SHAH)
+    double ms_inv_scale;         // Eq. 13: 1 / (2^(3 smooth_order) V): smoothed counts -> number density
     double eps24, eps48, eps2, sig2;     // LJ force/energy constants
     float eps24f, eps48f, eps2f, sig2f;
     float eps24l, eps48l, sig2l;         // low parts: eps48 - eps48f, ... (close pairs)
@@ -207,6 +210,10 @@ struct dcm_handle {
     int32_t *cc;                 // small components: parent and count of each phase, local sizes
                                  // (5 * nvox), a uniform flag per tile
     int64_t *cc_tiles;           // [M+1] offsets of the systems' 8^3 tiles (device)
+    double *msbuf;               // Eq. 13 segmentation: u, u-bar x 2, r, duals x 2 x 3 (10 * nvox)
+    unsigned long long *msacc;   // ... per system: phase sums and voxel counts (4 * M)
+    double *msc;                 // ... per system: the round's densities (2 * M)
+    int *msflag;                 // ... per system: segmenting, changed (2 * M)
     int64_t cc_ntiles, cc_ntiles0;   // tiles of all systems / of system 0
     bool cc_on;                  // some system removes small components
     // Verlet lists (skin > 0), indexed by sorted slot of the last build
@@ -287,6 +294,7 @@ int launch_forces(dcm_handle *h, bool energy);   // list mode when skin > 0 and 
 // its step)
 int launch_list_forces(dcm_handle *h, bool energy, int part);
 int launch_detect(dcm_handle *h);
+int launch_ms_detect(dcm_handle *h);     // Eq. 13 from the K-means labels (DCM_SEG_MUMFORD_SHAH)
 // Section 4.2 on labels S of the systems in b (thr >= 0 overrides every
 // system's min_component_voxels); tiles: their 8^3 tiles
 int launch_components(dcm_handle *h, const Batch &b, uint8_t *S, int thr, int64_t tiles);

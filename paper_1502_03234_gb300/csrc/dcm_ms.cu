@@ -1,102 +1,335 @@
 // dcm_ms.cu -- two-phase piecewise-constant Mumford-Shah segmentation (Eq. 13)
-// with the densities fixed, on a voxel image: the convex relaxation of Chan,
-// Esedoglu and Nikolova,
+// on a voxel image: the convex relaxation of Chan, Esedoglu and Nikolova,
 //     min over u in [0,1] of  sum_v u_v r_v + nu sum_faces |u_a - u_b|,
 //     r_v = (rho_v - c_l)^2 - (rho_v - c_v)^2   (u = 1: liquid),
 // solved by the first-order primal-dual iteration of Chambolle and Pock with
-// one dual variable per grid face (|p| <= nu), tau = 1/4, sigma = 1/3, u from
-// 1/2, a fixed number of iterations; liquid (s = 0) where u > 1/2.  The
-// perimeter counts the periodic faces between liquid and vapor voxels, for
-// which thresholded relaxed minimisers are exact minimisers of Eq. 13.
+// one dual variable per grid face (|p| <= nu), step sizes tau = sigma =
+// 0.99/sqrt(12) (convergence needs tau sigma |grad|^2 < 1, and |grad|^2 = 12
+// for periodic forward differences in 3D), u from 1/2, a fixed number of
+// iterations; liquid (s = 0) where u > 1/2.  The perimeter counts the
+// periodic faces between liquid and vapor voxels, for which thresholded
+// relaxed minimisers are exact minimisers of Eq. 13.
 //
-// Each iteration is two element-wise passes (the faces, then the voxels), in
-// FP64 with round-to-nearest intrinsics in a fixed order and no reduction, so
-// the result does not depend on the thread layout.  Bound: HBM (per voxel and
-// iteration ~100 B: u-bar and the 3 face values read and written, u, r).
+// Two uses:
+//  * dcm_ms_segment: the densities fixed, on a caller's image;
+//  * the segmentation step of the interface detection (DCM_SEG_MUMFORD_SHAH):
+//    on the smoothed number density rho = Bs * inv_scale, from the K-means
+//    labels, rounds of exact phase means (integer sums of Bs) and
+//    segmentation until the labels repeat or ms_outer rounds, for every
+//    system of the handle at once (a system whose labels repeated, or with
+//    an empty phase, stops; its later rounds are no-ops).
+//
+// One iteration is one kernel: each voxel updates the duals of its three
+// upper faces and recomputes, with the same expression, the new duals of
+// its three lower faces (which the voxel below also writes), then its
+// primal value, reading the previous iteration's u-bar and duals and
+// writing the next ones (two buffers of each, alternating): in FP64 with
+// round-to-nearest intrinsics in the oracle's operation order and no
+// reduction, so the result does not depend on the thread layout and equals
+// the oracle's two-pass iteration bit for bit.  Bound: L2/HBM, about 130 B
+// per voxel and iteration.
 #include "dcm_device.cuh"
 
 namespace dcm {
 
 constexpr int MS_THREADS = 256;
 
-struct MsGrid {
-    int nx, ny, nz;
-    int64_t nv;
+static inline int ms_blocks(int64_t n) { return (int)((n + MS_THREADS - 1) / MS_THREADS); }
+
+// the step sizes (host: the same expression as the oracle's)
+static double ms_tau() { return 0.99 / sqrt(12.0); }
+
+// the iteration's buffers: u, u-bar (two), duals (two x 3 per voxel), r
+struct MsBufs {
+    double *u, *ub[2], *p[2], *r;
 };
 
-__device__ __forceinline__ void ms_coords(const MsGrid &g, int64_t v, int &x, int &y, int &z)
+// one system's voxel grid and the voxel's coordinates in it
+struct MsCell {
+    int nx, ny, nz;
+    int64_t v0;        // first voxel of the system
+};
+
+__device__ __forceinline__ MsCell ms_cell(const Batch &b, int64_t v, int &sys)
 {
-    const int64_t t = v / g.nx;
-    x = (int)(v - t * g.nx);
-    y = (int)(t % g.ny);
-    z = (int)(t / g.ny);
+    sys = sys_v(b, v);
+    const Geom &g = b.sys[sys];
+    MsCell c;
+    c.nx = g.gd[0];
+    c.ny = g.gd[1];
+    c.nz = g.gd[2];
+    c.v0 = g.v0;
+    return c;
 }
 
-__global__ void k_ms_init(MsGrid g, const double *__restrict__ rho, double c_l, double c_v,
-                          double *u, double *ub, double *r, double *p)
+// One Chambolle-Pock iteration at voxel v (global index), system grid c:
+// reads ub_in, p_in (the previous iteration), writes ub_out, p_out, u.
+__device__ __forceinline__ void ms_iter_voxel(const MsCell &c, int64_t v, const double *ub_in,
+                                              const double *p_in, double *ub_out, double *p_out,
+                                              double *u, const double *r, double tau,
+                                              double sigma, double nu)
 {
-    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= g.nv) return;
-    const double a = DSUB(rho[v], c_l), b = DSUB(rho[v], c_v);
-    r[v] = DSUB(DMUL(a, a), DMUL(b, b));
-    u[v] = 0.5;
-    ub[v] = 0.5;
-    p[3 * v] = 0.0;
-    p[3 * v + 1] = 0.0;
-    p[3 * v + 2] = 0.0;
-}
-
-// dual ascent on the three upper faces of each voxel, projected on |p| <= nu
-__global__ void k_ms_dual(MsGrid g, const double *__restrict__ ub, double *p, double sigma,
-                          double nu)
-{
-    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= g.nv) return;
-    int x, y, z;
-    ms_coords(g, v, x, y, z);
-    const int n[3] = {g.nx, g.ny, g.nz};
-    const int64_t up[3] = {v + (x + 1 < g.nx ? 1 : -(int64_t)(g.nx - 1)),
-                           v + (y + 1 < g.ny ? (int64_t)g.nx : -(int64_t)(g.ny - 1) * g.nx),
-                           v + (z + 1 < g.nz ? (int64_t)g.nx * g.ny
-                                             : -(int64_t)(g.nz - 1) * g.nx * g.ny)};
-    const double ubv = ub[v];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        double q = n[a] > 1 ? DADD(p[3 * v + a], DMUL(sigma, DSUB(ub[up[a]], ubv))) : 0.0;
-        if (q > nu) q = nu;
-        if (q < -nu) q = -nu;
-        p[3 * v + a] = q;
-    }
-}
-
-// primal descent u -= tau (grad^T p + r), clipped to [0, 1], and the
-// extrapolation u-bar = 2 u_new - u_old
-__global__ void k_ms_primal(MsGrid g, const double *__restrict__ p, const double *__restrict__ r,
-                            double *u, double *ub, double tau)
-{
-    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= g.nv) return;
-    int x, y, z;
-    ms_coords(g, v, x, y, z);
-    const int64_t dn[3] = {v + (x > 0 ? -1 : (int64_t)(g.nx - 1)),
-                           v + (y > 0 ? -(int64_t)g.nx : (int64_t)(g.ny - 1) * g.nx),
-                           v + (z > 0 ? -(int64_t)g.nx * g.ny : (int64_t)(g.nz - 1) * g.nx * g.ny)};
+    const int64_t lv = v - c.v0;
+    const int64_t t = lv / c.nx;
+    const int x = (int)(lv - t * c.nx), y = (int)(t % c.ny), z = (int)(t / c.ny);
+    const int n[3] = {c.nx, c.ny, c.nz};
+    const int64_t sxy = (int64_t)c.nx * c.ny;
+    const int64_t up[3] = {v + (x + 1 < c.nx ? 1 : -(int64_t)(c.nx - 1)),
+                           v + (y + 1 < c.ny ? (int64_t)c.nx : -(int64_t)(c.ny - 1) * c.nx),
+                           v + (z + 1 < c.nz ? sxy : -(int64_t)(c.nz - 1) * sxy)};
+    const int64_t dn[3] = {v + (x > 0 ? -1 : (int64_t)(c.nx - 1)),
+                           v + (y > 0 ? -(int64_t)c.nx : (int64_t)(c.ny - 1) * c.nx),
+                           v + (z > 0 ? -sxy : (int64_t)(c.nz - 1) * sxy)};
+    const double ubv = ub_in[v];
     double gtp = 0.0;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) gtp = DADD(gtp, DSUB(p[3 * dn[a] + a], p[3 * v + a]));
+    for (int a = 0; a < 3; ++a) {
+        // dual ascent on the face above v, projected on |p| <= nu
+        double q = n[a] > 1 ? DADD(p_in[3 * v + a], DMUL(sigma, DSUB(ub_in[up[a]], ubv))) : 0.0;
+        if (q > nu) q = nu;
+        if (q < -nu) q = -nu;
+        p_out[3 * v + a] = q;
+        // the same on the face below v (the lower voxel's upper face)
+        double qd =
+            n[a] > 1 ? DADD(p_in[3 * dn[a] + a], DMUL(sigma, DSUB(ubv, ub_in[dn[a]]))) : 0.0;
+        if (qd > nu) qd = nu;
+        if (qd < -nu) qd = -nu;
+        // grad^T p at v: inflow from the lower face minus outflow
+        gtp = DADD(gtp, DSUB(qd, q));
+    }
+    // primal descent u -= tau (grad^T p + r), clipped to [0, 1], and the
+    // extrapolation u-bar = 2 u_new - u_old
     const double uo = u[v];
     double un = DSUB(uo, DMUL(tau, DADD(gtp, r[v])));
     if (un < 0.0) un = 0.0;
     if (un > 1.0) un = 1.0;
-    ub[v] = DSUB(DMUL(2.0, un), uo);
+    ub_out[v] = DSUB(DMUL(2.0, un), uo);
     u[v] = un;
 }
 
-__global__ void k_ms_labels(MsGrid g, const double *__restrict__ u, uint8_t *S)
+// ---- dcm_ms_segment: one image, densities fixed -----------------------------
+__global__ void k_ms_init(MsCell c, int64_t nv, const double *__restrict__ rho, double c_l,
+                          double c_v, MsBufs m)
 {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= g.nv) return;
+    if (v >= nv) return;
+    const double a = DSUB(rho[v], c_l), b = DSUB(rho[v], c_v);
+    m.r[v] = DSUB(DMUL(a, a), DMUL(b, b));
+    m.u[v] = 0.5;
+    m.ub[0][v] = 0.5;
+    m.p[0][3 * v] = 0.0;
+    m.p[0][3 * v + 1] = 0.0;
+    m.p[0][3 * v + 2] = 0.0;
+}
+
+__global__ void k_ms_iter(MsCell c, int64_t nv, MsBufs m, int k, double tau, double sigma,
+                          double nu)
+{
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    ms_iter_voxel(c, v, m.ub[k], m.p[k], m.ub[k ^ 1], m.p[k ^ 1], m.u, m.r, tau, sigma, nu);
+}
+
+__global__ void k_ms_labels(int64_t nv, const double *__restrict__ u, uint8_t *S)
+{
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv) return;
     S[v] = u[v] > 0.5 ? 0 : 1;
+}
+
+// ---- the detection's segmentation step, every system of the handle --------
+// per system: [0] liquid sum of Bs, [1] liquid voxels, [2] vapor sum, [3]
+// vapor voxels (exact: Bs holds integers below 2^53); c[2s], c[2s + 1] the
+// round's densities; flag[2s] the system is still segmenting, flag[2s + 1]
+// this round changed a label
+struct MsSys {
+    unsigned long long *acc;
+    double *c;
+    int *flag;
+};
+
+// the phase sums of labels S for the systems still segmenting: warp sums,
+// then one atomic per counter and block when the whole block lies in one
+// system (per warp otherwise), so a large grid does not serialise on the
+// four counters of its system
+__global__ void __launch_bounds__(MS_THREADS) k_ms_sums(Batch b, const double *__restrict__ Bs,
+                                                       const uint8_t *__restrict__ S, MsSys ms)
+{
+    constexpr int W = MS_THREADS / 32;
+    __shared__ unsigned long long s_acc[W][4];
+    __shared__ int s_sys[W];
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int sys = -1;
+    unsigned long long q[4] = {0ull, 0ull, 0ull, 0ull};
+    if (v < b.NV) {
+        sys = sys_v(b, v);
+        if (ms.flag[2 * sys]) {
+            const unsigned long long val = (unsigned long long)Bs[v];
+            const int o = S[v] == 0 ? 0 : 2;
+            q[o] = val;
+            q[o + 1] = 1ull;
+        }
+    }
+    // (lanes past the end take the first lane's system: they add zeros)
+    const int s0 = __shfl_sync(full, sys, 0);
+    if (sys < 0) sys = s0;
+    const bool uniform = __all_sync(full, sys == s0);
+    if (uniform) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            for (int off = 16; off > 0; off >>= 1) q[c] += __shfl_xor_sync(full, q[c], off);
+        if (lane == 0) {
+            for (int c = 0; c < 4; ++c) s_acc[w][c] = q[c];
+            s_sys[w] = s0;
+        }
+    } else {
+        if (lane == 0) s_sys[w] = -1;
+        if (sys >= 0 && (q[1] | q[3])) {
+            unsigned long long *a = ms.acc + 4 * sys;
+            for (int c = 0; c < 4; ++c)
+                if (q[c]) atomicAdd(a + c, q[c]);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // warps of one system add up first
+        for (int i = 0; i < W; ++i) {
+            if (s_sys[i] < 0) continue;
+            unsigned long long t[4] = {s_acc[i][0], s_acc[i][1], s_acc[i][2], s_acc[i][3]};
+            for (int j = i + 1; j < W; ++j)
+                if (s_sys[j] == s_sys[i]) {
+                    for (int c = 0; c < 4; ++c) t[c] += s_acc[j][c];
+                    s_sys[j] = -1;
+                }
+            unsigned long long *a = ms.acc + 4 * s_sys[i];
+            for (int c = 0; c < 4; ++c)
+                if (t[c]) atomicAdd(a + c, t[c]);
+        }
+    }
+}
+
+// every system segments from its K-means labels; accumulators at zero
+__global__ void k_ms_start(Batch b, MsSys ms)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= b.M) return;
+    ms.flag[2 * s] = 1;
+    ms.flag[2 * s + 1] = 0;
+    unsigned long long *a = ms.acc + 4 * s;
+    a[0] = a[1] = a[2] = a[3] = 0ull;
+}
+
+// a round's start, one thread per system: the densities from the sums (the
+// oracle's (sum / count) * inv_scale), the sums cleared for the next round;
+// a system with an empty phase stops
+__global__ void k_ms_begin(Batch b, MsSys ms)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= b.M) return;
+    unsigned long long *a = ms.acc + 4 * s;
+    if (a[1] == 0 || a[3] == 0) ms.flag[2 * s] = 0;
+    if (ms.flag[2 * s]) {
+        const double inv = b.sys[s].ms_inv_scale;
+        ms.c[2 * s] = DMUL(__ddiv_rn((double)a[0], (double)a[1]), inv);
+        ms.c[2 * s + 1] = DMUL(__ddiv_rn((double)a[2], (double)a[3]), inv);
+    }
+    ms.flag[2 * s + 1] = 0;
+    a[0] = a[1] = a[2] = a[3] = 0ull;
+}
+
+// the relaxation's start for the systems still segmenting
+__global__ void k_ms_prep(Batch b, const double *__restrict__ Bs, MsSys ms, MsBufs m)
+{
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= b.NV) return;
+    const int s = sys_v(b, v);
+    if (!ms.flag[2 * s]) return;
+    const double rho = DMUL(Bs[v], b.sys[s].ms_inv_scale);
+    const double a = DSUB(rho, ms.c[2 * s]), c = DSUB(rho, ms.c[2 * s + 1]);
+    m.r[v] = DSUB(DMUL(a, a), DMUL(c, c));
+    m.u[v] = 0.5;
+    m.ub[0][v] = 0.5;
+    m.p[0][3 * v] = 0.0;
+    m.p[0][3 * v + 1] = 0.0;
+    m.p[0][3 * v + 2] = 0.0;
+}
+
+__global__ void k_ms_iter_sys(Batch b, MsSys ms, MsBufs m, int k, double tau, double sigma)
+{
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= b.NV) return;
+    int s;
+    const MsCell c = ms_cell(b, v, s);
+    if (!ms.flag[2 * s]) return;
+    ms_iter_voxel(c, v, m.ub[k], m.p[k], m.ub[k ^ 1], m.p[k ^ 1], m.u, m.r, tau, sigma,
+                  b.sys[s].ms_nu);
+}
+
+// the round's labels and whether any changed
+__global__ void k_ms_end(Batch b, MsSys ms, const double *u, uint8_t *S)
+{
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= b.NV) return;
+    const int s = sys_v(b, v);
+    if (!ms.flag[2 * s]) return;
+    const uint8_t nl = u[v] > 0.5 ? 0 : 1;
+    if (nl != S[v]) {
+        S[v] = nl;
+        if (!*(volatile int *)&ms.flag[2 * s + 1]) atomicOr(&ms.flag[2 * s + 1], 1);
+    }
+}
+
+// a system whose labels repeated stops
+__global__ void k_ms_check(Batch b, MsSys ms)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= b.M) return;
+    if (!ms.flag[2 * s + 1]) ms.flag[2 * s] = 0;
+}
+
+static MsBufs ms_bufs(double *base, int64_t nv)
+{
+    MsBufs m;
+    m.u = base;
+    m.ub[0] = base + nv;
+    m.ub[1] = base + 2 * nv;
+    m.r = base + 3 * nv;
+    m.p[0] = base + 4 * nv;
+    m.p[1] = base + 7 * nv;
+    return m;
+}
+
+int launch_ms_detect(dcm_handle *h)
+{
+    const Batch &b = h->b;
+    cudaStream_t s = h->stream;
+    const int64_t nv = b.NV;
+    MsBufs m = ms_bufs(h->msbuf, nv);
+    MsSys ms;
+    ms.acc = h->msacc;
+    ms.c = h->msc;
+    ms.flag = h->msflag;
+    const double tau = ms_tau();
+    const int iters = h->p.ms_iters > 0 ? h->p.ms_iters : 50;
+    const int outer = h->p.ms_outer > 0 ? h->p.ms_outer : 4;
+    const int vb = ms_blocks(nv), sb = (b.M + 127) / 128;
+    // the sums of the K-means labels (every system starts segmenting; the
+    // accumulators are left at zero by each round's begin)
+    k_ms_start<<<sb, 128, 0, s>>>(b, ms);
+    k_ms_sums<<<vb, MS_THREADS, 0, s>>>(b, h->Bs, h->S, ms);
+    for (int round = 0; round < outer; ++round) {
+        k_ms_begin<<<sb, 128, 0, s>>>(b, ms);
+        k_ms_prep<<<vb, MS_THREADS, 0, s>>>(b, h->Bs, ms, m);
+        for (int it = 0; it < iters; ++it)
+            k_ms_iter_sys<<<vb, MS_THREADS, 0, s>>>(b, ms, m, it & 1, tau, tau);
+        // (the last iteration wrote u; u-bar and the duals are not read)
+        k_ms_end<<<vb, MS_THREADS, 0, s>>>(b, ms, m.u, h->S);
+        k_ms_check<<<sb, 128, 0, s>>>(b, ms);
+        if (round + 1 < outer) k_ms_sums<<<vb, MS_THREADS, 0, s>>>(b, h->Bs, h->S, ms);
+    }
+    return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "segmentation launch");
 }
 
 }  // namespace dcm
@@ -112,39 +345,39 @@ extern "C" int dcm_ms_segment(dcm_handle *h, const double *rho, double c_l, doub
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     DCM_CHECK_CUDA(cudaStreamIsCapturing(h->stream, &cap));
     if (cap != cudaStreamCaptureStatusNone) return fail(DCM_ERR_STATE, "not callable during stream capture");
-    MsGrid g;
-    g.nx = h->g.gd[0];
-    g.ny = h->g.gd[1];
-    g.nz = h->g.gd[2];
-    g.nv = (int64_t)g.nx * g.ny * g.nz;
-    const size_t nv = (size_t)g.nv;
+    MsCell c;
+    c.nx = h->g.gd[0];
+    c.ny = h->g.gd[1];
+    c.nz = h->g.gd[2];
+    c.v0 = 0;
+    const int64_t nvi = (int64_t)c.nx * c.ny * c.nz;
+    const size_t nv = (size_t)nvi;
     double *buf = nullptr;
     uint8_t *S = nullptr;
-    cudaError_t e = cudaMalloc((void **)&buf, sizeof(double) * 7 * nv);
+    cudaError_t e = cudaMalloc((void **)&buf, sizeof(double) * 11 * nv);
     if (e == cudaSuccess) e = cudaMalloc((void **)&S, nv);
     if (e != cudaSuccess) {
         cudaFree(buf);
         cudaFree(S);
         return fail(DCM_ERR_OOM, "segmentation buffers");
     }
-    double *u = buf, *ub = buf + nv, *r = buf + 2 * nv, *rh = buf + 3 * nv, *p = buf + 4 * nv;
+    MsBufs m = ms_bufs(buf, nvi);
+    double *rh = buf + 10 * nv;
     cudaStream_t s = h->stream;
     const cudaMemcpyKind in = mem == DCM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     const cudaMemcpyKind out = mem == DCM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     e = cudaMemcpyAsync(rh, rho, sizeof(double) * nv, in, s);
-    const unsigned grid = (unsigned)((g.nv + MS_THREADS - 1) / MS_THREADS);
-    const double tau = 0.25, sigma = 1.0 / 3.0;
+    const int grid = ms_blocks(nvi);
+    const double tau = ms_tau();
     if (e == cudaSuccess) {
-        k_ms_init<<<grid, MS_THREADS, 0, s>>>(g, rh, c_l, c_v, u, ub, r, p);
-        for (int it = 0; it < iters; ++it) {
-            k_ms_dual<<<grid, MS_THREADS, 0, s>>>(g, ub, p, sigma, nu);
-            k_ms_primal<<<grid, MS_THREADS, 0, s>>>(g, p, r, u, ub, tau);
-        }
-        k_ms_labels<<<grid, MS_THREADS, 0, s>>>(g, u, S);
+        k_ms_init<<<grid, MS_THREADS, 0, s>>>(c, nvi, rh, c_l, c_v, m);
+        for (int it = 0; it < iters; ++it)
+            k_ms_iter<<<grid, MS_THREADS, 0, s>>>(c, nvi, m, it & 1, tau, tau, nu);
+        k_ms_labels<<<grid, MS_THREADS, 0, s>>>(nvi, m.u, S);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(labels, S, nv, out, s);
-    if (e == cudaSuccess && u_out) e = cudaMemcpyAsync(u_out, u, sizeof(double) * nv, out, s);
+    if (e == cudaSuccess && u_out) e = cudaMemcpyAsync(u_out, m.u, sizeof(double) * nv, out, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(buf);
     cudaFree(S);

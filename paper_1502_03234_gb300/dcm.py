@@ -23,6 +23,7 @@ DCM_HOST, DCM_DEVICE = 0, 1
 DCM_CUTOFF_EXP, DCM_CUTOFF_LINEAR = 0, 1
 DCM_MAX_CLASSES = 8
 DCM_WALK_WARP, DCM_WALK_LANES = 0, 1
+DCM_SEG_KMEANS, DCM_SEG_MUMFORD_SHAH = 0, 1
 # limits of the allocation-free cell sort (include/dcm.h)
 DCM_NOALLOC_MAX_PARTICLES, DCM_NOALLOC_MAX_CELLS = 1 << 19, 1 << 20
 DCM_GRAPH_BRANCHED, DCM_GRAPH_FLAT = 0, 1
@@ -63,7 +64,8 @@ class dcm_params(C.Structure):
                 ("skin", C.c_double), ("list_density", C.c_float),
                 ("list_margin", C.c_float), ("skin_time", C.c_float),
                 ("skin_floor", C.c_float), ("min_component_voxels", C.c_int32),
-                ("cutoff_fn", C.c_int32)]
+                ("cutoff_fn", C.c_int32), ("segmentation", C.c_int32), ("ms_iters", C.c_int32),
+                ("ms_outer", C.c_int32), ("ms_nu", C.c_double)]
 
 
 class dcm_tuning(C.Structure):
