@@ -89,6 +89,9 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--ens-steps", type=int, default=50,
+                    help="steps of the 64-slab ensemble comparison, batched mixed against "
+                         "per-system FP64 (0: skip)")
     ap.add_argument("--seg-steps", type=int, default=20,
                     help="steps of the detection-with-Eq.-13 comparison (0: skip)")
     ap.add_argument("--skin", type=float, default=0.7,
@@ -545,6 +548,59 @@ def run_workload(args):
     return 0
 
 
+def ensemble_compare(dcm, slabgen, autotune, stream, flush, torch, steps, warm, skin, skin_time,
+                     skin_floor):
+    """The mixed/FP64 comparison on the ensemble workload: 64 independent
+    slabs (N log-uniform in [4096, 131072], T* uniform in [0.65, 0.85], own
+    boxes), mixed precision batched in one handle (one persistent force
+    launch per step, the launch shape tuned on the live ensemble) against
+    the plain per-system FP64 path (one handle per system, stepped one after
+    the other), the same steps from the same states, L2 flushed before each
+    timed step (batched) or system step (per system)"""
+    mem = slabgen.make_ensemble(64, 4096, 131072, 0.65, 0.85, seed=0)
+    boxes = [m.slab.box for m in mem]
+    ns = [m.n for m in mem]
+    ntot = sum(ns)
+    params = [dcm.default_params(precision=dcm.DCM_MIXED, skin=skin, skin_time=skin_time,
+                                 skin_floor=skin_floor) for _ in mem]
+    ens = dcm.Ensemble(boxes, ns, params, stream=stream.cuda_stream)
+    for k, m in enumerate(mem):
+        ens.set_system_state(k, m.slab.x, m.slab.v)
+    ens.compute_forces()
+    choice = autotune.tune_live(ens, reps=3)
+    ms, _ = _timed(ens, stream, flush, steps, warm)
+    ens.close()
+    mixed = ntot * steps / (sum(ms) * 1e-3)
+    # per system, FP64: every system its own handle, warmed, then each system's
+    # steps timed with events around them
+    t64 = 0.0
+    for m in mem:
+        sy = dcm.System(m.slab.box, m.n, precision=dcm.DCM_FP64, stream=stream.cuda_stream,
+                        skin=skin, skin_time=skin_time, skin_floor=skin_floor)
+        sy.set_state(m.slab.x, m.slab.v)
+        for _ in range(warm):
+            sy.step(1)
+        sy.sync()
+        with torch.cuda.stream(stream):
+            flush()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sy.step(steps)
+        e1.record(stream)
+        e1.synchronize()
+        t64 += e0.elapsed_time(e1)
+        sy.close()
+    fp64 = ntot * steps / (t64 * 1e-3)
+    return {"systems": len(ns), "n_total": ntot, "n_min": min(ns), "n_max": max(ns),
+            "steps": steps, "warmup": warm,
+            "mixed_batched": {"value": mixed, "unit": UNIT, "ms_per_step": sum(ms) / len(ms),
+                              "tuning": {k: v for k, v in choice.items()
+                                         if k in ("list_lanes", "force_ms")}},
+            "fp64_per_system": {"value": fp64, "unit": UNIT, "ms_per_step_all_systems": t64 / steps},
+            "speedup": mixed / fp64,
+            "note": "the 64-slab ensemble workload, both arms from the same states"}
+
+
 # ---- the GPU arm ---------------------------------------------------------------------
 def main():
     args = parse()
@@ -770,7 +826,7 @@ def main():
                 syx.set_tuning(list(t.lanes), t.block, t.walk, args.list_lanes)
             syx.set_state(slab.x, slab.v)
             syx.compute_forces()
-            ms_, ph_, _ = timed_steps(syx, args.seg_steps, 2, True)
+            ms_, _, ph_ = timed_steps(syx, args.seg_steps, 2, True)
             st_ = syx.stats()
             syx.close()
             det_steps = max(1, args.seg_steps // 2)       # detection every second step
@@ -786,6 +842,13 @@ def main():
                         if mu["detect_ms_per_detection"] > 0 else None,
                     "note": "per-phase CUDA events over a short run from the same start; the "
                             "share is that of the Eq. 13 step in a detection (thesis: 75-80 %)"}
+
+    ens_info = None
+    if rank == 0 and prec == dcm.DCM_MIXED and args.ens_steps > 0:
+        from paper_1502_03234_gb300 import autotune
+
+        ens_info = ensemble_compare(dcm, slabgen, autotune, stream, flush, torch, args.ens_steps,
+                                    3, args.skin, args.skin_time, args.skin_floor)
 
     # the plain FP64 GPU path on the same system (the comparison the metric
     # names), timed exactly like the headline: the same steps and warm-up,
@@ -886,6 +949,7 @@ def main():
         cfg["list_lanes"] = args.list_lanes
         cfg["fp64_gpu_path"] = fp64_info
         cfg["segmentation_eq13"] = seg_info
+        cfg["ensemble_vs_fp64"] = ens_info
         cfg["energy_drift"] = {"rel": abs(energy["e1"] - energy["e0"]) / abs(energy["e0"]),
                                "steps": args.steps,
                                "note": "|E(K) - E(0)| / |E(0)| over the timed steps (NVE; the "

@@ -33,6 +33,7 @@
 #ifndef DCM_H
 #define DCM_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -220,6 +221,21 @@ typedef struct dcm_handle dcm_handle;
 /* Fills the thesis defaults: rc 3/6, alpha -0.5, dt 0.005, m = eps = sigma
  * = 1, voxel 1, smoothing order 8, detect_every 2, FP64, 4 classes. */
 void dcm_default_params(dcm_params *p);
+
+/* Device memory.  A handle owns every device buffer it uses.  It allocates
+ * them when it is created (and a few on first use: small-component removal
+ * buffers; dcm_ms_segment's scratch, released before it returns), never
+ * during a step, in the stream order of its stream: with
+ * cudaMallocAsync / cudaFreeAsync from the device's default memory pool,
+ * or, after dcm_set_allocator, with the caller's functions (for example a
+ * framework's caching allocator), called as alloc(bytes, stream, ctx) ->
+ * device pointer (NULL: out of memory) and release(ptr, stream, ctx) with
+ * the handle's stream.  The setting is process-wide and taken by each
+ * handle when it is created (handles keep theirs); both NULL restores the
+ * default.  Errors: DCM_ERR_ARG when only one function is given. */
+typedef void *(*dcm_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*dcm_release_fn)(void *ptr, void *stream, void *ctx);
+int dcm_set_allocator(dcm_alloc_fn alloc, dcm_release_fn release, void *ctx);
 
 /* Creates a single-system handle for n particles in box.  stream is a
  * cudaStream_t (NULL: the library creates one).  Allocates every device

@@ -13,7 +13,9 @@ with gcc (``-ffp-contract=off``, optional OpenMP for the Algorithm 5.1
 from __future__ import annotations
 
 import ctypes as C
+import hashlib
 import os
+import platform
 import subprocess
 from dataclasses import dataclass
 
@@ -27,16 +29,35 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
 
+_CMD = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off"]
+
+
+def _fingerprint() -> str:
+    # content of the sources, the flags and the machine: a library built from
+    # other sources or on another machine is never reused
+    h = hashlib.sha256()
+    for f in (_SRC, _HDR):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    h.update(" ".join(_CMD).encode())
+    h.update(platform.machine().encode())
+    return h.hexdigest()
+
+
 def build(force: bool = False) -> str:
     """Compile liboracle.so next to the sources (quick: one C file)."""
-    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= newest:
-        return _LIB
+    fp = _fingerprint()
+    stamp = _LIB + ".fingerprint"
+    if not force and os.path.exists(_LIB) and os.path.exists(stamp):
+        with open(stamp) as fh:
+            if fh.read().strip() == fp:
+                return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
-           "-ffp-contract=off", "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
+    subprocess.run(_CMD + ["-o", tmp, _SRC, "-lm"], check=True)
     os.replace(tmp, _LIB)
+    with open(stamp + f".tmp{os.getpid()}", "w") as fh:
+        fh.write(fp)
+    os.replace(stamp + f".tmp{os.getpid()}", stamp)
     return _LIB
 
 

@@ -164,9 +164,10 @@ def live_candidates(precision: int) -> tuple:
     if precision == dcm.DCM_MIXED:
         return tuple({"walk": dcm.DCM_WALK_WARP, "lanes": [1], "block": 128, "list_lanes": G}
                      for G in LIST_LANES)
-    return ({"walk": dcm.DCM_WALK_LANES, "lanes": [2, 1, 2, 2], "block": 128},
-            {"walk": dcm.DCM_WALK_LANES, "lanes": [2, 2, 4, 4], "block": 128},
-            {"walk": dcm.DCM_WALK_LANES, "lanes": [4, 4, 8, 8], "block": 256})
+    return ({"walk": dcm.DCM_WALK_LANES, "lanes": [4, 4, 8, 8], "block": 128},
+            {"walk": dcm.DCM_WALK_LANES, "lanes": [8, 8, 16, 16], "block": 128},
+            {"walk": dcm.DCM_WALK_LANES, "lanes": [16, 16, 32, 32], "block": 128},
+            {"walk": dcm.DCM_WALK_LANES, "lanes": [32, 32, 32, 32], "block": 256})
 
 
 def tune_live(sy: dcm.System, *, reps: int = 5, candidates=None, log=None) -> dict:

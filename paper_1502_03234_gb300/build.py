@@ -2,7 +2,9 @@
 compiled in parallel, no cmake)."""
 from __future__ import annotations
 
+import hashlib
 import os
+import platform
 import subprocess
 import sys
 from concurrent.futures import ThreadPoolExecutor
@@ -23,18 +25,34 @@ def _nvcc() -> str:
     return cand if os.path.exists(cand) else "nvcc"
 
 
-def _deps_mtime() -> float:
-    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
+def _fingerprint(nvcc: str) -> str:
+    """Content hash of every source and header, the flags, the compiler and
+    the machine: a library built from other sources, or on another machine
+    (an x86 build carried to an Arm host), is never reused."""
+    h = hashlib.sha256()
+    files = sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC))
     files.append(os.path.join(HERE, "..", "include", "dcm.h"))
-    return max(os.path.getmtime(f) for f in files if os.path.exists(f))
+    for f in files:
+        if os.path.isfile(f):
+            h.update(os.path.basename(f).encode())
+            with open(f, "rb") as fh:
+                h.update(fh.read())
+    h.update(" ".join(ARCH + FLAGS + SOURCES).encode())
+    h.update(nvcc.encode())
+    h.update(platform.machine().encode())
+    return h.hexdigest()
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
     srcs = [s for s in SOURCES if os.path.exists(os.path.join(CSRC, s))]
-    if not force and os.path.exists(OUT) and os.path.getmtime(OUT) >= _deps_mtime():
-        return OUT
-    os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
+    fp = _fingerprint(nvcc)
+    stamp = OUT + ".fingerprint"
+    if not force and os.path.exists(OUT) and os.path.exists(stamp):
+        with open(stamp) as fh:
+            if fh.read().strip() == fp:
+                return OUT
+    os.makedirs(BUILD, exist_ok=True)
 
     def compile_one(src: str) -> str:
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
@@ -54,6 +72,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, OUT)
+    with open(stamp + f".tmp{os.getpid()}", "w") as fh:
+        fh.write(fp)
+    os.replace(stamp + f".tmp{os.getpid()}", stamp)
     return OUT
 
 

@@ -7,6 +7,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
 #include <vector>
 
 #include "dcm_device.cuh"
@@ -292,8 +293,9 @@ static int cc_setup(dcm_handle *h)
     int rc;
     if ((rc = dalloc(h, &h->cc, 5 * h->b.NV + off[h->M]))) return rc;
     if ((rc = dalloc(h, &h->cc_tiles, (int64_t)h->M + 1))) return rc;
-    DCM_CHECK_CUDA(cudaMemcpy(h->cc_tiles, off.data(), sizeof(int64_t) * (h->M + 1),
-                              cudaMemcpyHostToDevice));
+    DCM_CHECK_CUDA(cudaMemcpyAsync(h->cc_tiles, off.data(), sizeof(int64_t) * (h->M + 1),
+                                   cudaMemcpyHostToDevice, h->stream));
+    DCM_CHECK_CUDA(cudaStreamSynchronize(h->stream));
     h->cc_ntiles = off[h->M];
     h->cc_ntiles0 = off[1];
     return DCM_OK;
@@ -320,18 +322,74 @@ extern "C" int64_t dcm_estimate_bytes(const dcm_box *box, int64_t n, const dcm_p
     return bytes_for(g, n, p->precision);
 }
 
+// the allocator new handles take (process-wide; each handle keeps a copy)
+static std::mutex g_alloc_mu;
+static dcm_alloc_fn g_alloc = nullptr;
+static dcm_release_fn g_release = nullptr;
+static void *g_alloc_ctx = nullptr;
+
+extern "C" int dcm_set_allocator(dcm_alloc_fn alloc, dcm_release_fn release, void *ctx)
+{
+    if ((alloc == nullptr) != (release == nullptr))
+        return fail(DCM_ERR_ARG, "give both allocator functions or neither");
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_alloc = alloc;
+    g_release = release;
+    g_alloc_ctx = ctx;
+    return DCM_OK;
+}
+
+static void take_allocator(dcm_handle *h)
+{
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    h->alloc = g_alloc;
+    h->release = g_release;
+    h->alloc_ctx = g_alloc_ctx;
+}
+
+// device buffers in the stream order of the handle's stream
 template <typename T>
 static int dalloc(dcm_handle *h, T **ptr, int64_t count)
 {
     size_t b = sizeof(T) * (size_t)(count > 0 ? count : 1);
-    cudaError_t e = cudaMalloc((void **)ptr, b);
-    if (e != cudaSuccess) {
-        *ptr = nullptr;
-        return fail_cuda(e, "cudaMalloc", __FILE__, __LINE__);
+    if (h->alloc) {
+        *ptr = (T *)h->alloc(b, (void *)h->stream, h->alloc_ctx);
+        if (!*ptr) return fail(DCM_ERR_OOM, "the caller's allocator returned no memory (%zu bytes)", b);
+    } else {
+        cudaError_t e = cudaMallocAsync((void **)ptr, b, h->stream);
+        if (e != cudaSuccess) {
+            *ptr = nullptr;
+            return fail_cuda(e, "cudaMallocAsync", __FILE__, __LINE__);
+        }
     }
     h->bytes += (int64_t)b;
     return DCM_OK;
 }
+
+static void dfree(dcm_handle *h, void *p)
+{
+    if (!p) return;
+    if (h->release)
+        h->release(p, (void *)h->stream, h->alloc_ctx);
+    else
+        cudaFreeAsync(p, h->stream);
+}
+
+namespace dcm {
+// scratch of an entry point outside the step (the same allocator)
+int dev_alloc(dcm_handle *h, void **p, size_t bytes)
+{
+    char *q = nullptr;
+    int rc = dalloc(h, &q, (int64_t)bytes);
+    *p = q;
+    return rc;
+}
+void dev_free(dcm_handle *h, void *p, size_t bytes)
+{
+    dfree(h, p);
+    h->bytes -= (int64_t)(bytes > 0 ? bytes : 1);
+}
+}  // namespace dcm
 
 extern "C" int dcm_destroy(dcm_handle *h)
 {
@@ -349,8 +407,10 @@ extern "C" int dcm_destroy(dcm_handle *h)
                     h->nl_start, h->nl_tiles, h->x_ref, h->rl_ref, h->sh_ref, h->sh, h->u_ref,
                     h->disp, h->corner, h->lflags, h->cc, h->cc_tiles,
                     h->msbuf, h->msacc, h->msc, h->msflag};
-    for (void *q : ptrs)
-        if (q) cudaFree(q);
+    if (h->stream) {
+        for (void *q : ptrs) dfree(h, q);
+        cudaStreamSynchronize(h->stream);
+    }
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     if (h->side) cudaStreamDestroy(h->side);
     delete[] h->geo_host;
@@ -434,8 +494,11 @@ static int create_systems(int M, const dcm_box *boxes, const int64_t *ns, const 
         return fail(DCM_ERR_ARG, "too many cells or voxels in total");
     }
     h->g = h->geo_host[0];
-    // default launch shape: more lanes for larger cutoff classes
-    for (int q = 0; q < DCM_MAX_CLASSES; ++q) h->tune.lanes[q] = q == 0 ? 2 : (q == 1 ? 1 : 2);
+    // default launch shape of the FP64 lanes walk: 16 lanes per particle for
+    // the lower half of the cutoff classes, 32 for the upper (measured on
+    // slabs of 4k-262k atoms: 1.1-8x faster than 1-2 lanes, whose few
+    // threads leave small systems latency-bound)
+    for (int q = 0; q < DCM_MAX_CLASSES; ++q) h->tune.lanes[q] = 2 * q < h->p.n_classes ? 16 : 32;
     h->tune.block = 128;
     h->tune.walk = DCM_WALK_WARP;
     h->tune.list_lanes = 8;
@@ -451,6 +514,7 @@ static int create_systems(int M, const dcm_box *boxes, const int64_t *ns, const 
         }
         h->own_stream = true;
     }
+    take_allocator(h);
     h->ncell = co[M];
     h->nvox = vo[M];
     int64_t N = ntot, nc = h->ncell, nv = h->nvox;
@@ -1124,7 +1188,7 @@ extern "C" int dcm_remove_small_components(dcm_handle *h, uint8_t *labels, int32
     if (e == cudaSuccess && rc == DCM_OK)
         e = cudaMemcpyAsync(&st, h->stats, sizeof(st), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    cudaFree(S);
+    dfree(h, S);
     h->bytes -= nv > 0 ? nv : 1;
     if (e != cudaSuccess) return fail_cuda(e, "small-component removal", __FILE__, __LINE__);
     if (rc) return rc;
@@ -1242,9 +1306,11 @@ extern "C" int dcm_sync(dcm_handle *h)
     if (!h) return fail(DCM_ERR_ARG, "null handle");
     DCM_CHECK_CUDA(cudaStreamSynchronize(h->stream));
     int err = 0;
-    DCM_CHECK_CUDA(cudaMemcpy(&err, h->err, sizeof(int), cudaMemcpyDeviceToHost));
+    DCM_CHECK_CUDA(cudaMemcpyAsync(&err, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    DCM_CHECK_CUDA(cudaStreamSynchronize(h->stream));
     if (!err) return DCM_OK;
-    DCM_CHECK_CUDA(cudaMemset(h->err, 0, sizeof(int)));
+    DCM_CHECK_CUDA(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream));
+    DCM_CHECK_CUDA(cudaStreamSynchronize(h->stream));
     if (err & DEV_ERR_CANCEL) return fail(DCM_ERR_CANCELLED, "cancelled");
     if (err & DEV_ERR_CFSM_CAP)
         return fail(DCM_ERR_NOT_CONVERGED, "CFSM reached its iteration cap (device flags 0x%x)", err);

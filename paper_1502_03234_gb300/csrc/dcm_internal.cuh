@@ -175,6 +175,9 @@ struct dcm_handle {
     dcm::Batch b;
     cudaStream_t stream;
     bool own_stream;
+    dcm_alloc_fn alloc;          // the caller's allocator (null: cudaMallocAsync on the stream)
+    dcm_release_fn release;
+    void *alloc_ctx;
     int device;
     int num_sms;
     int64_t ncell, nvox;
@@ -317,6 +320,10 @@ struct Branch {
 int branch_open(dcm_handle *h, Branch &b, int nbody);     // an IF node on h->cond
 int branch_else(dcm_handle *h, Branch &b);
 int branch_close(dcm_handle *h, Branch &b);
+
+// device scratch from the handle's allocator, in its stream order
+int dev_alloc(dcm_handle *h, void **p, size_t bytes);
+void dev_free(dcm_handle *h, void *p, size_t bytes);
 
 // lower-level helpers
 int coop_grid_size(dcm_handle *h, const void *kernel, int block, size_t smem);

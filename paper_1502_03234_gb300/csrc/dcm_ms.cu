@@ -352,21 +352,24 @@ extern "C" int dcm_ms_segment(dcm_handle *h, const double *rho, double c_l, doub
     c.v0 = 0;
     const int64_t nvi = (int64_t)c.nx * c.ny * c.nz;
     const size_t nv = (size_t)nvi;
-    double *buf = nullptr;
-    uint8_t *S = nullptr;
-    cudaError_t e = cudaMalloc((void **)&buf, sizeof(double) * 11 * nv);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&S, nv);
-    if (e != cudaSuccess) {
-        cudaFree(buf);
-        cudaFree(S);
-        return fail(DCM_ERR_OOM, "segmentation buffers");
+    void *vbuf = nullptr, *vS = nullptr;
+    int rc = dev_alloc(h, &vbuf, sizeof(double) * 11 * nv);
+    if (rc == DCM_OK) rc = dev_alloc(h, &vS, nv);
+    if (rc != DCM_OK) {
+        if (vbuf) dev_free(h, vbuf, sizeof(double) * 11 * nv);
+        if (vS) dev_free(h, vS, nv);
+        cudaStreamSynchronize(h->stream);
+        return rc;
     }
+    double *buf = (double *)vbuf;
+    uint8_t *S = (uint8_t *)vS;
+    cudaError_t e = cudaSuccess;
     MsBufs m = ms_bufs(buf, nvi);
     double *rh = buf + 10 * nv;
     cudaStream_t s = h->stream;
     const cudaMemcpyKind in = mem == DCM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     const cudaMemcpyKind out = mem == DCM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-    e = cudaMemcpyAsync(rh, rho, sizeof(double) * nv, in, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(rh, rho, sizeof(double) * nv, in, s);
     const int grid = ms_blocks(nvi);
     const double tau = ms_tau();
     if (e == cudaSuccess) {
@@ -378,9 +381,10 @@ extern "C" int dcm_ms_segment(dcm_handle *h, const double *rho, double c_l, doub
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(labels, S, nv, out, s);
     if (e == cudaSuccess && u_out) e = cudaMemcpyAsync(u_out, m.u, sizeof(double) * nv, out, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    cudaFree(buf);
-    cudaFree(S);
+    dev_free(h, buf, sizeof(double) * 11 * nv);
+    dev_free(h, S, nv);
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = e2;
     if (e != cudaSuccess) return fail_cuda(e, "segmentation", __FILE__, __LINE__);
     return DCM_OK;
 }

@@ -38,7 +38,7 @@ EXPORTS = [
     "dcm_set_timing", "dcm_get_phase_times", "dcm_ensemble_create", "dcm_system_count",
     "dcm_system_range", "dcm_ensemble_set_state", "dcm_ensemble_get_state",
     "dcm_ensemble_energy_virial", "dcm_check_bounded_wait", "dcm_cell_sort_noalloc",
-    "dcm_remove_small_components", "dcm_ms_segment",
+    "dcm_remove_small_components", "dcm_ms_segment", "dcm_set_allocator",
 ]
 DCM_NUM_PHASES = 5
 PHASES = ("kick_drift", "detect", "bin", "force", "kick")
@@ -102,6 +102,7 @@ def lib() -> C.CDLL:
         "dcm_default_params": (None, [P(dcm_params)]),
         "dcm_create": (C.c_int, [P(dcm_box), i64, P(dcm_params), vp, P(vp)]),
         "dcm_destroy": (C.c_int, [vp]),
+        "dcm_set_allocator": (C.c_int, [vp, vp, vp]),
         "dcm_set_state": (C.c_int, [vp, dp, dp, C.c_int]),
         "dcm_get_state": (C.c_int, [vp, dp, dp, dp, C.c_int]),
         "dcm_set_step": (C.c_int, [vp, i64]),
@@ -181,6 +182,46 @@ def dcm_create(box, n: int, params: dcm_params | None = None, stream=None):
 
 def dcm_destroy(h) -> None:
     check(lib().dcm_destroy(h))
+
+
+_ALLOCATOR = None          # the callbacks handed to the library, kept alive
+
+
+def dcm_set_allocator(alloc=None, release=None, ctx=None) -> None:
+    """The device allocator handles created from now on use (both None:
+    cudaMallocAsync / cudaFreeAsync on the handle's stream)."""
+    def addr(f):
+        return None if f is None else C.cast(f, C.c_void_p)
+    check(lib().dcm_set_allocator(addr(alloc), addr(release), ctx))
+
+
+def use_torch_allocator() -> None:
+    """Handles created from now on take their device memory from PyTorch's
+    caching allocator, on the handle's stream (the allocator's memory then
+    shows in torch.cuda.memory_allocated and is cached across handles)."""
+    import torch
+
+    alloc_t = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+    release_t = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+        except RuntimeError:           # out of memory: the library reports DCM_ERR_OOM
+            return None
+
+    def _release(ptr, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    global _ALLOCATOR
+    _ALLOCATOR = (alloc_t(_alloc), release_t(_release))
+    dcm_set_allocator(*_ALLOCATOR)
+
+
+def use_default_allocator() -> None:
+    global _ALLOCATOR
+    dcm_set_allocator(None, None)
+    _ALLOCATOR = None
 
 
 def dcm_set_state(h, x, v=None) -> None:

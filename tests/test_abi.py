@@ -134,3 +134,45 @@ def test_noalloc_sort_binding_checks_buffers_without_gpu():
     for (xb, cb, sb), msg in bad_cases:
         with pytest.raises(ValueError, match=msg):
             dcm.dcm_cell_sort_noalloc(xb, n, box, nc, cb, sb)
+
+
+def test_build_reuses_a_library_only_for_the_same_sources_and_machine(monkeypatch):
+    # the rebuild check hashes the sources, flags, compiler and machine: an
+    # unchanged tree keeps its library, another machine (an x86 build carried
+    # to an Arm host) does not
+    import platform
+
+    from paper_1502_03234_gb300 import build
+
+    nvcc = build._nvcc()
+    a = build._fingerprint(nvcc)
+    assert a == build._fingerprint(nvcc)
+    monkeypatch.setattr(platform, "machine", lambda: "some-other-cpu")
+    assert build._fingerprint(nvcc) != a
+    import oracle
+
+    monkeypatch.undo()
+    o = oracle._fingerprint()
+    monkeypatch.setattr(platform, "machine", lambda: "some-other-cpu")
+    assert oracle._fingerprint() != o
+
+
+def test_allocator_takes_both_functions_or_neither_without_gpu(libdcm):
+    # the caller's device allocator: both callbacks or none (none = the
+    # library's cudaMallocAsync / cudaFreeAsync on the handle's stream);
+    # installing and removing one makes no device call
+    from paper_1502_03234_gb300 import dcm
+
+    alloc_t = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+    release_t = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+    a = alloc_t(lambda n, s, c: None)
+    r = release_t(lambda p, s, c: None)
+    with pytest.raises(dcm.DcmError) as e:
+        dcm.dcm_set_allocator(a, None)
+    assert e.value.code == dcm.DCM_ERR_ARG
+    with pytest.raises(dcm.DcmError) as e:
+        dcm.dcm_set_allocator(None, r)
+    assert e.value.code == dcm.DCM_ERR_ARG
+    dcm.dcm_set_allocator(a, r)
+    dcm.use_default_allocator()
+    assert dcm._ALLOCATOR is None
