@@ -471,7 +471,11 @@ int orc_kmeans(int64_t nvox, const double *Bs, int max_iter, uint8_t *S,
  * at 1/2, a fixed number of iterations; labels: liquid (s = 0) where
  * u > 1/2.  After a fixed number of iterations the relaxed u is converged
  * only approximately; its threshold is an exact minimiser of Eq. 13 once u
- * is converged. */
+ * is converged.  Precision: the thesis fixes none for the segmentation, and
+ * the labels are a threshold decision, so the iteration runs in single
+ * precision (u, u-bar, the duals, the step sizes and nu as float; the data
+ * term r is formed in double and rounded once to float), every operation a
+ * separately rounded float operation in the order written here. */
 double orc_ms_energy(const int dims[3], const double *rho, double c_l, double c_v, double nu,
                      const uint8_t *S)
 {
@@ -500,15 +504,15 @@ void orc_ms_segment(const int dims[3], const double *rho, double c_l, double c_v
     const int64_t nx = dims[0], ny = dims[1], nz = dims[2];
     const int64_t nv = nx * ny * nz;
     const int64_t n[3] = {nx, ny, nz};
-    const double tau = 0.99 / sqrt(12.0), sigma = tau;
-    double *u = (double *)malloc(sizeof(double) * (size_t)nv);
-    double *ub = (double *)malloc(sizeof(double) * (size_t)nv);
-    double *r = (double *)malloc(sizeof(double) * (size_t)nv);
-    double *p = (double *)calloc((size_t)(3 * nv), sizeof(double));
+    const float tau = (float)(0.99 / sqrt(12.0)), sigma = tau, nuf = (float)nu;
+    float *u = (float *)malloc(sizeof(float) * (size_t)(nv > 0 ? nv : 1));
+    float *ub = (float *)malloc(sizeof(float) * (size_t)(nv > 0 ? nv : 1));
+    float *r = (float *)malloc(sizeof(float) * (size_t)(nv > 0 ? nv : 1));
+    float *p = (float *)calloc((size_t)(3 * (nv > 0 ? nv : 1)), sizeof(float));
     for (int64_t v = 0; v < nv; ++v) {
-        u[v] = 0.5;
-        ub[v] = 0.5;
-        r[v] = (rho[v] - c_l) * (rho[v] - c_l) - (rho[v] - c_v) * (rho[v] - c_v);
+        u[v] = 0.5f;
+        ub[v] = 0.5f;
+        r[v] = (float)((rho[v] - c_l) * (rho[v] - c_l) - (rho[v] - c_v) * (rho[v] - c_v));
     }
     for (int it = 0; it < iters; ++it) {
         /* dual ascent on the faces: p_a(v) on the face between v and v + e_a */
@@ -520,9 +524,9 @@ void orc_ms_segment(const int dims[3], const double *rho, double c_l, double c_v
                                            x + nx * (((y + 1) % ny) + ny * z),
                                            x + nx * (y + ny * ((z + 1) % nz))};
                     for (int a = 0; a < 3; ++a) {
-                        double q = n[a] > 1 ? p[3 * v + a] + sigma * (ub[up[a]] - ub[v]) : 0.0;
-                        if (q > nu) q = nu;
-                        if (q < -nu) q = -nu;
+                        float q = n[a] > 1 ? p[3 * v + a] + sigma * (ub[up[a]] - ub[v]) : 0.0f;
+                        if (q > nuf) q = nuf;
+                        if (q < -nuf) q = -nuf;
                         p[3 * v + a] = q;
                     }
                 }
@@ -536,18 +540,18 @@ void orc_ms_segment(const int dims[3], const double *rho, double c_l, double c_v
                                            x + nx * (((y + ny - 1) % ny) + ny * z),
                                            x + nx * (y + ny * ((z + nz - 1) % nz))};
                     /* grad^T p at v: inflow from the lower faces minus outflow */
-                    double gtp = 0.0;
+                    float gtp = 0.0f;
                     for (int a = 0; a < 3; ++a) gtp += p[3 * dn[a] + a] - p[3 * v + a];
-                    double un = u[v] - tau * (gtp + r[v]);
-                    if (un < 0.0) un = 0.0;
-                    if (un > 1.0) un = 1.0;
-                    ub[v] = 2.0 * un - u[v];
+                    float un = u[v] - tau * (gtp + r[v]);
+                    if (un < 0.0f) un = 0.0f;
+                    if (un > 1.0f) un = 1.0f;
+                    ub[v] = 2.0f * un - u[v];
                     u[v] = un;
                 }
     }
     for (int64_t v = 0; v < nv; ++v) {
-        S[v] = u[v] > 0.5 ? 0 : 1;
-        if (u_out) u_out[v] = u[v];
+        S[v] = u[v] > 0.5f ? 0 : 1;
+        if (u_out) u_out[v] = (double)u[v];
     }
     free(u);
     free(ub);
