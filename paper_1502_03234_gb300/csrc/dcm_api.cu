@@ -180,6 +180,9 @@ static int setup_geometry(const dcm_box *box, int64_t n, const dcm_params *p, Ge
         const double V = (L[0] / g.gd[0]) * (L[1] / g.gd[1]) * (L[2] / g.gd[2]);
         g.ms_inv_scale = 1.0 / ldexp(V, 3 * (p->smooth_order > 0 ? p->smooth_order : 0));
     }
+    // q = floor(n / d) = high word of n * ceil(2^64 / d) for every 32-bit n
+    // (the product's error n (ceil(2^64/d) - 2^64/d) / 2^64 stays below 1/d)
+    for (int a = 0; a < 2; ++a) g.div_gd[a] = ~0ull / (unsigned long long)g.gd[a] + 1ull;
     for (int a = 0; a < 3; ++a) g.w_h[a] = 1.0 / (g.h[a] * g.h[a]);
     g.e_min = 1.0 / sqrt(g.w_h[0] + g.w_h[1] + g.w_h[2]);
     g.rc_min = p->rc_min;
@@ -260,6 +263,9 @@ static int setup_geometry(const dcm_box *box, int64_t n, const dcm_params *p, Ge
     }
     g.ncell = (int64_t)g.nc[0] * g.nc[1] * g.nc[2];
     g.nvox = (int64_t)g.gd[0] * g.gd[1] * g.gd[2];
+    if (g.nvox > INT32_MAX)
+        return fail(DCM_ERR_ARG, "voxel grid of %lld voxels: at most 2^31 - 1 per system (raise voxel)",
+                    (long long)g.nvox);
     return DCM_OK;
 }
 
@@ -308,7 +314,7 @@ static int64_t bytes_for(const Geom &g, int64_t n, int precision)
     int64_t per_p = 3 * 8 * 3 + 8 + 8 + 1 + 4 * 3 + 16 + 4 + 4 + 8 + 48 + 24 + 2;
     per_p += precision == DCM_FP64 ? 36 : 56;   // spd (FP64) or spl4 + refq + rq + pk + inv (MIXED)
     int64_t per_v = 4 + 4 + 4 + 8 + 1 + 8 + 8 + 4 + 16 + 2 + (g.cc_min > 0 ? 20 : 0) +
-                    (g.ms_seg ? 80 : 0);
+                    (g.ms_seg ? 40 : 0);
     int64_t ntiles = (ncell + 2047) / 2048 + 1;
     int64_t lists = g.skin > 0 ? 4 * list_cap(g, n) + n * (4 + 4 + 24 + 8 + 8 + 20) : 0;
     return n * per_p + ncell * 8 + 8 + nv * per_v + ntiles * 4 + 4096 + 256 * 8 * 8 + lists;

@@ -114,6 +114,8 @@ struct Geom {
     double ms_nu;                // Eq. 13: perimeter weight (number-density units)
     int ms_seg;                  // Eq. 13 segmentation after K-means (DCM_SEG_MUMFORD_SHAH)
     double ms_inv_scale;         // Eq. 13: 1 / (2^(3 smooth_order) V): smoothed counts -> number density
+    unsigned long long div_gd[2];  // ceil(2^64 / gd[a]), a = 0, 1: exact 32-bit division by gd[a]
+                                   // as the high word of a 64-bit product (Granlund-Montgomery)
     double eps24, eps48, eps2, sig2;     // LJ force/energy constants
     float eps24f, eps48f, eps2f, sig2f;
     float eps24l, eps48l, sig2l;         // low parts: eps48 - eps48f, ... (close pairs)
@@ -213,7 +215,7 @@ struct dcm_handle {
     int32_t *cc;                 // small components: parent and count of each phase, local sizes
                                  // (5 * nvox), a uniform flag per tile
     int64_t *cc_tiles;           // [M+1] offsets of the systems' 8^3 tiles (device)
-    double *msbuf;               // Eq. 13 segmentation: u, u-bar x 2, r, duals x 2 x 3 (10 * nvox)
+    float *msbuf;                // Eq. 13 segmentation (FP32): u, u-bar x 2, r, duals x 2 x 3 planes (10 * nvox)
     unsigned long long *msacc;   // ... per system: phase sums and voxel counts (4 * M)
     double *msc;                 // ... per system: the round's densities (2 * M)
     int *msflag;                 // ... per system: segmenting, changed (2 * M)

@@ -23,11 +23,16 @@
 // upper faces and recomputes, with the same expression, the new duals of
 // its three lower faces (which the voxel below also writes), then its
 // primal value, reading the previous iteration's u-bar and duals and
-// writing the next ones (two buffers of each, alternating): in FP64 with
-// round-to-nearest intrinsics in the oracle's operation order and no
-// reduction, so the result does not depend on the thread layout and equals
-// the oracle's two-pass iteration bit for bit.  Bound: L2/HBM, about 130 B
-// per voxel and iteration.
+// writing the next ones (two buffers of each, alternating).  The thesis
+// fixes no precision for the segmentation and the labels are a threshold
+// decision, so the iteration runs in FP32 (the data term is formed in FP64
+// and rounded once), with round-to-nearest intrinsics in the oracle's
+// operation order and no reduction: the result does not depend on the
+// thread layout and equals the oracle's two-pass single-precision iteration
+// bit for bit.  (In FP64 the ~40 FP64 operations per voxel made each
+// iteration FP64-pipe bound, 1/64 of the FP32 rate on this GPU.)  Bound:
+// L2 (the iteration's ~40 B per voxel stay resident), then launch latency.
+// Duals are stored as three planes (x, y, z faces) for coalesced access.
 #include "dcm_device.cuh"
 
 namespace dcm {
@@ -39,15 +44,17 @@ static inline int ms_blocks(int64_t n) { return (int)((n + MS_THREADS - 1) / MS_
 // the step sizes (host: the same expression as the oracle's)
 static double ms_tau() { return 0.99 / sqrt(12.0); }
 
-// the iteration's buffers: u, u-bar (two), duals (two x 3 per voxel), r
+// the iteration's buffers: u, u-bar (two), duals (two x 3 planes), r
 struct MsBufs {
-    double *u, *ub[2], *p[2], *r;
+    float *u, *ub[2], *p[2], *r;
+    int64_t ps;        // plane stride of the duals
 };
 
 // one system's voxel grid and the voxel's coordinates in it
 struct MsCell {
     int nx, ny, nz;
-    int64_t v0;        // first voxel of the system
+    int64_t v0;                    // first voxel of the system
+    unsigned long long mx, my;     // exact division by nx, ny (Geom::div_gd)
 };
 
 __device__ __forceinline__ MsCell ms_cell(const Batch &b, int64_t v, int &sys)
@@ -59,82 +66,108 @@ __device__ __forceinline__ MsCell ms_cell(const Batch &b, int64_t v, int &sys)
     c.ny = g.gd[1];
     c.nz = g.gd[2];
     c.v0 = g.v0;
+    c.mx = g.div_gd[0];
+    c.my = g.div_gd[1];
     return c;
 }
 
-// One Chambolle-Pock iteration at voxel v (global index), system grid c:
-// reads ub_in, p_in (the previous iteration), writes ub_out, p_out, u.
-__device__ __forceinline__ void ms_iter_voxel(const MsCell &c, int64_t v, const double *ub_in,
-                                              const double *p_in, double *ub_out, double *p_out,
-                                              double *u, const double *r, double tau,
-                                              double sigma, double nu)
+// The duals of one axis at voxel v: the face above v (stored) and, with the
+// same expression, the face below v (the lower voxel's upper face);
+// returns their contribution to grad^T p at v.  live: the axis has more
+// than one voxel (otherwise its faces carry no dual).
+__device__ __forceinline__ float ms_axis(const float *__restrict__ pa, float *__restrict__ po,
+                                         const float *__restrict__ ubi, int64_t v, float ubv,
+                                         int upo, int dno, bool live, float sigma, float nu)
 {
-    const int64_t lv = v - c.v0;
-    const int64_t t = lv / c.nx;
-    const int x = (int)(lv - t * c.nx), y = (int)(t % c.ny), z = (int)(t / c.ny);
-    const int n[3] = {c.nx, c.ny, c.nz};
-    const int64_t sxy = (int64_t)c.nx * c.ny;
-    const int64_t up[3] = {v + (x + 1 < c.nx ? 1 : -(int64_t)(c.nx - 1)),
-                           v + (y + 1 < c.ny ? (int64_t)c.nx : -(int64_t)(c.ny - 1) * c.nx),
-                           v + (z + 1 < c.nz ? sxy : -(int64_t)(c.nz - 1) * sxy)};
-    const int64_t dn[3] = {v + (x > 0 ? -1 : (int64_t)(c.nx - 1)),
-                           v + (y > 0 ? -(int64_t)c.nx : (int64_t)(c.ny - 1) * c.nx),
-                           v + (z > 0 ? -sxy : (int64_t)(c.nz - 1) * sxy)};
-    const double ubv = ub_in[v];
-    double gtp = 0.0;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        // dual ascent on the face above v, projected on |p| <= nu
-        double q = n[a] > 1 ? DADD(p_in[3 * v + a], DMUL(sigma, DSUB(ub_in[up[a]], ubv))) : 0.0;
-        if (q > nu) q = nu;
-        if (q < -nu) q = -nu;
-        p_out[3 * v + a] = q;
-        // the same on the face below v (the lower voxel's upper face)
-        double qd =
-            n[a] > 1 ? DADD(p_in[3 * dn[a] + a], DMUL(sigma, DSUB(ubv, ub_in[dn[a]]))) : 0.0;
-        if (qd > nu) qd = nu;
-        if (qd < -nu) qd = -nu;
-        // grad^T p at v: inflow from the lower face minus outflow
-        gtp = DADD(gtp, DSUB(qd, q));
-    }
+    // dual ascent on the face above v, projected on |p| <= nu
+    float q = live ? __fadd_rn(pa[v], __fmul_rn(sigma, __fsub_rn(ubi[v + upo], ubv))) : 0.0f;
+    if (q > nu) q = nu;
+    if (q < -nu) q = -nu;
+    po[v] = q;
+    float qd = live ? __fadd_rn(pa[v + dno], __fmul_rn(sigma, __fsub_rn(ubv, ubi[v + dno]))) : 0.0f;
+    if (qd > nu) qd = nu;
+    if (qd < -nu) qd = -nu;
+    // inflow from the lower face minus outflow
+    return __fsub_rn(qd, q);
+}
+
+// One Chambolle-Pock iteration at voxel v (global index), system grid c:
+// reads u-bar and the duals of buffer k (the previous iteration), writes
+// those of buffer k ^ 1 and u.  Voxel coordinates and neighbour offsets in
+// 32 bits (a system's grid holds fewer than 2^31 voxels).
+__device__ __forceinline__ void ms_iter_voxel(const MsCell &c, int64_t v, const MsBufs &m, int k,
+                                              float tau, float sigma, float nu)
+{
+    const unsigned nx = (unsigned)c.nx, ny = (unsigned)c.ny, nz = (unsigned)c.nz;
+    const unsigned lv = (unsigned)(v - c.v0);
+    const unsigned t = (unsigned)__umul64hi(lv, c.mx);          // lv / nx
+    const unsigned z = (unsigned)__umul64hi(t, c.my);           // t / ny
+    const unsigned x = lv - t * nx, y = t - z * ny;
+    const int sxy = (int)(nx * ny), sv = (int)(nz * (unsigned)sxy);
+    // (selects, not m.ub[k]: a run-time index into the parameter struct
+    // would copy it to local memory)
+    const float *__restrict__ ubi = k ? m.ub[1] : m.ub[0];
+    float *ubo = k ? m.ub[0] : m.ub[1];
+    const float *pi = k ? m.p[1] : m.p[0];
+    float *po = k ? m.p[0] : m.p[1];
+    const float ubv = ubi[v];
+    // grad^T p at v, axes in order x, y, z (periodic neighbours)
+    float gtp = 0.0f;
+    gtp = __fadd_rn(gtp, ms_axis(pi, po, ubi, v, ubv, x + 1 < nx ? 1 : 1 - (int)nx,
+                                 x > 0 ? -1 : (int)nx - 1, nx > 1, sigma, nu));
+    gtp = __fadd_rn(gtp, ms_axis(pi + m.ps, po + m.ps, ubi, v, ubv,
+                                 y + 1 < ny ? (int)nx : (int)nx - sxy,
+                                 y > 0 ? -(int)nx : sxy - (int)nx, ny > 1, sigma, nu));
+    gtp = __fadd_rn(gtp, ms_axis(pi + 2 * m.ps, po + 2 * m.ps, ubi, v, ubv,
+                                 z + 1 < nz ? sxy : sxy - sv, z > 0 ? -sxy : sv - sxy, nz > 1,
+                                 sigma, nu));
     // primal descent u -= tau (grad^T p + r), clipped to [0, 1], and the
     // extrapolation u-bar = 2 u_new - u_old
-    const double uo = u[v];
-    double un = DSUB(uo, DMUL(tau, DADD(gtp, r[v])));
-    if (un < 0.0) un = 0.0;
-    if (un > 1.0) un = 1.0;
-    ub_out[v] = DSUB(DMUL(2.0, un), uo);
-    u[v] = un;
+    const float uo = m.u[v];
+    float un = __fsub_rn(uo, __fmul_rn(tau, __fadd_rn(gtp, m.r[v])));
+    if (un < 0.0f) un = 0.0f;
+    if (un > 1.0f) un = 1.0f;
+    ubo[v] = __fsub_rn(__fmul_rn(2.0f, un), uo);
+    m.u[v] = un;
+}
+
+// the relaxation's start at voxel v: data term (FP64, rounded once), u and
+// u-bar at 1/2, duals at 0
+__device__ __forceinline__ void ms_start_voxel(const MsBufs &m, int64_t v, double rho, double c_l,
+                                               double c_v)
+{
+    const double a = DSUB(rho, c_l), b = DSUB(rho, c_v);
+    m.r[v] = __double2float_rn(DSUB(DMUL(a, a), DMUL(b, b)));
+    m.u[v] = 0.5f;
+    m.ub[0][v] = 0.5f;
+    m.p[0][v] = 0.0f;
+    m.p[0][m.ps + v] = 0.0f;
+    m.p[0][2 * m.ps + v] = 0.0f;
 }
 
 // ---- dcm_ms_segment: one image, densities fixed -----------------------------
-__global__ void k_ms_init(MsCell c, int64_t nv, const double *__restrict__ rho, double c_l,
-                          double c_v, MsBufs m)
+__global__ void k_ms_init(int64_t nv, const double *__restrict__ rho, double c_l, double c_v,
+                          MsBufs m)
 {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= nv) return;
-    const double a = DSUB(rho[v], c_l), b = DSUB(rho[v], c_v);
-    m.r[v] = DSUB(DMUL(a, a), DMUL(b, b));
-    m.u[v] = 0.5;
-    m.ub[0][v] = 0.5;
-    m.p[0][3 * v] = 0.0;
-    m.p[0][3 * v + 1] = 0.0;
-    m.p[0][3 * v + 2] = 0.0;
+    ms_start_voxel(m, v, rho[v], c_l, c_v);
 }
 
-__global__ void k_ms_iter(MsCell c, int64_t nv, MsBufs m, int k, double tau, double sigma,
-                          double nu)
+__global__ void k_ms_iter(MsCell c, int64_t nv, MsBufs m, int k, float tau, float sigma, float nu)
 {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= nv) return;
-    ms_iter_voxel(c, v, m.ub[k], m.p[k], m.ub[k ^ 1], m.p[k ^ 1], m.u, m.r, tau, sigma, nu);
+    ms_iter_voxel(c, v, m, k, tau, sigma, nu);
 }
 
-__global__ void k_ms_labels(int64_t nv, const double *__restrict__ u, uint8_t *S)
+// labels (liquid where u > 1/2) and u in double for the caller
+__global__ void k_ms_labels(int64_t nv, const float *__restrict__ u, uint8_t *S, double *u_out)
 {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= nv) return;
-    S[v] = u[v] > 0.5 ? 0 : 1;
+    S[v] = u[v] > 0.5f ? 0 : 1;
+    u_out[v] = (double)u[v];
 }
 
 // ---- the detection's segmentation step, every system of the handle --------
@@ -167,9 +200,11 @@ __global__ void __launch_bounds__(MS_THREADS) k_ms_sums(Batch b, const double *_
         sys = sys_v(b, v);
         if (ms.flag[2 * sys]) {
             const unsigned long long val = (unsigned long long)Bs[v];
-            const int o = S[v] == 0 ? 0 : 2;
-            q[o] = val;
-            q[o + 1] = 1ull;
+            const bool liq = S[v] == 0;
+            q[0] = liq ? val : 0ull;
+            q[1] = liq ? 1ull : 0ull;
+            q[2] = liq ? 0ull : val;
+            q[3] = liq ? 0ull : 1ull;
         }
     }
     // (lanes past the end take the first lane's system: they add zeros)
@@ -246,35 +281,27 @@ __global__ void k_ms_prep(Batch b, const double *__restrict__ Bs, MsSys ms, MsBu
     if (v >= b.NV) return;
     const int s = sys_v(b, v);
     if (!ms.flag[2 * s]) return;
-    const double rho = DMUL(Bs[v], b.sys[s].ms_inv_scale);
-    const double a = DSUB(rho, ms.c[2 * s]), c = DSUB(rho, ms.c[2 * s + 1]);
-    m.r[v] = DSUB(DMUL(a, a), DMUL(c, c));
-    m.u[v] = 0.5;
-    m.ub[0][v] = 0.5;
-    m.p[0][3 * v] = 0.0;
-    m.p[0][3 * v + 1] = 0.0;
-    m.p[0][3 * v + 2] = 0.0;
+    ms_start_voxel(m, v, DMUL(Bs[v], b.sys[s].ms_inv_scale), ms.c[2 * s], ms.c[2 * s + 1]);
 }
 
-__global__ void k_ms_iter_sys(Batch b, MsSys ms, MsBufs m, int k, double tau, double sigma)
+__global__ void k_ms_iter_sys(Batch b, MsSys ms, MsBufs m, int k, float tau, float sigma)
 {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= b.NV) return;
     int s;
     const MsCell c = ms_cell(b, v, s);
     if (!ms.flag[2 * s]) return;
-    ms_iter_voxel(c, v, m.ub[k], m.p[k], m.ub[k ^ 1], m.p[k ^ 1], m.u, m.r, tau, sigma,
-                  b.sys[s].ms_nu);
+    ms_iter_voxel(c, v, m, k, tau, sigma, __double2float_rn(b.sys[s].ms_nu));
 }
 
 // the round's labels and whether any changed
-__global__ void k_ms_end(Batch b, MsSys ms, const double *u, uint8_t *S)
+__global__ void k_ms_end(Batch b, MsSys ms, const float *u, uint8_t *S)
 {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= b.NV) return;
     const int s = sys_v(b, v);
     if (!ms.flag[2 * s]) return;
-    const uint8_t nl = u[v] > 0.5 ? 0 : 1;
+    const uint8_t nl = u[v] > 0.5f ? 0 : 1;
     if (nl != S[v]) {
         S[v] = nl;
         if (!*(volatile int *)&ms.flag[2 * s + 1]) atomicOr(&ms.flag[2 * s + 1], 1);
@@ -289,7 +316,7 @@ __global__ void k_ms_check(Batch b, MsSys ms)
     if (!ms.flag[2 * s + 1]) ms.flag[2 * s] = 0;
 }
 
-static MsBufs ms_bufs(double *base, int64_t nv)
+static MsBufs ms_bufs(float *base, int64_t nv)
 {
     MsBufs m;
     m.u = base;
@@ -298,6 +325,7 @@ static MsBufs ms_bufs(double *base, int64_t nv)
     m.r = base + 3 * nv;
     m.p[0] = base + 4 * nv;
     m.p[1] = base + 7 * nv;
+    m.ps = nv;
     return m;
 }
 
@@ -311,7 +339,7 @@ int launch_ms_detect(dcm_handle *h)
     ms.acc = h->msacc;
     ms.c = h->msc;
     ms.flag = h->msflag;
-    const double tau = ms_tau();
+    const float tau = (float)ms_tau();
     const int iters = h->p.ms_iters > 0 ? h->p.ms_iters : 50;
     const int outer = h->p.ms_outer > 0 ? h->p.ms_outer : 4;
     const int vb = ms_blocks(nv), sb = (b.M + 127) / 128;
@@ -350,38 +378,42 @@ extern "C" int dcm_ms_segment(dcm_handle *h, const double *rho, double c_l, doub
     c.ny = h->g.gd[1];
     c.nz = h->g.gd[2];
     c.v0 = 0;
+    c.mx = h->g.div_gd[0];
+    c.my = h->g.div_gd[1];
     const int64_t nvi = (int64_t)c.nx * c.ny * c.nz;
     const size_t nv = (size_t)nvi;
+    // 10 floats per voxel for the iteration, then the image (double)
+    const size_t bytes = sizeof(float) * 10 * nv + sizeof(double) * nv;
     void *vbuf = nullptr, *vS = nullptr;
-    int rc = dev_alloc(h, &vbuf, sizeof(double) * 11 * nv);
+    int rc = dev_alloc(h, &vbuf, bytes);
     if (rc == DCM_OK) rc = dev_alloc(h, &vS, nv);
     if (rc != DCM_OK) {
-        if (vbuf) dev_free(h, vbuf, sizeof(double) * 11 * nv);
+        if (vbuf) dev_free(h, vbuf, bytes);
         if (vS) dev_free(h, vS, nv);
         cudaStreamSynchronize(h->stream);
         return rc;
     }
-    double *buf = (double *)vbuf;
+    float *buf = (float *)vbuf;
     uint8_t *S = (uint8_t *)vS;
     cudaError_t e = cudaSuccess;
     MsBufs m = ms_bufs(buf, nvi);
-    double *rh = buf + 10 * nv;
+    double *rh = (double *)(buf + 10 * nv);    // the image; after the start, u as double
     cudaStream_t s = h->stream;
     const cudaMemcpyKind in = mem == DCM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     const cudaMemcpyKind out = mem == DCM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     if (e == cudaSuccess) e = cudaMemcpyAsync(rh, rho, sizeof(double) * nv, in, s);
     const int grid = ms_blocks(nvi);
-    const double tau = ms_tau();
+    const float tau = (float)ms_tau();
     if (e == cudaSuccess) {
-        k_ms_init<<<grid, MS_THREADS, 0, s>>>(c, nvi, rh, c_l, c_v, m);
+        k_ms_init<<<grid, MS_THREADS, 0, s>>>(nvi, rh, c_l, c_v, m);
         for (int it = 0; it < iters; ++it)
-            k_ms_iter<<<grid, MS_THREADS, 0, s>>>(c, nvi, m, it & 1, tau, tau, nu);
-        k_ms_labels<<<grid, MS_THREADS, 0, s>>>(nvi, m.u, S);
+            k_ms_iter<<<grid, MS_THREADS, 0, s>>>(c, nvi, m, it & 1, tau, tau, (float)nu);
+        k_ms_labels<<<grid, MS_THREADS, 0, s>>>(nvi, m.u, S, rh);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(labels, S, nv, out, s);
-    if (e == cudaSuccess && u_out) e = cudaMemcpyAsync(u_out, m.u, sizeof(double) * nv, out, s);
-    dev_free(h, buf, sizeof(double) * 11 * nv);
+    if (e == cudaSuccess && u_out) e = cudaMemcpyAsync(u_out, rh, sizeof(double) * nv, out, s);
+    dev_free(h, buf, bytes);
     dev_free(h, S, nv);
     cudaError_t e2 = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = e2;
