@@ -101,6 +101,9 @@ def parse():
     ap.add_argument("--list-lanes", type=int, default=0, choices=[0, 4, 8, 16, 32],
                     help="lanes per particle of the Verlet-list force (0: tuned on a scratch "
                          "copy of the system before the timed run, see --no-tune)")
+    ap.add_argument("--list-lanes-class", default=None,
+                    help="with --list-lanes: lanes per cutoff class, comma-separated (the "
+                         "class-ordered list force), e.g. 8,8,16,16")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the library's default launch shape instead of tuning it")
     ap.add_argument("--step-graph", default="branched", choices=["branched", "flat"],
@@ -121,6 +124,8 @@ def parse():
     ap.add_argument("--sweep-steps", type=int, default=40)
     ap.add_argument("--requests", type=int, default=120, help="serving: trace length")
     a = ap.parse_args()
+    if a.list_lanes_class:
+        a.list_lanes_class = [int(g) for g in a.list_lanes_class.split(",")]
     if a.steps is None:
         a.steps = {"slab": 1000, "wavy": 200, "ensemble": 500, "serving": 0, "accuracy": 0}[a.workload]
     return a
@@ -595,7 +600,8 @@ def ensemble_compare(dcm, slabgen, autotune, stream, flush, torch, steps, warm, 
             "steps": steps, "warmup": warm,
             "mixed_batched": {"value": mixed, "unit": UNIT, "ms_per_step": sum(ms) / len(ms),
                               "tuning": {k: v for k, v in choice.items()
-                                         if k in ("list_lanes", "force_ms")}},
+                                         if k in ("list_lanes", "list_lanes_class",
+                                                  "force_ms")}},
             "fp64_per_system": {"value": fp64, "unit": UNIT, "ms_per_step_all_systems": t64 / steps},
             "speedup": mixed / fp64,
             "note": "the 64-slab ensemble workload, both arms from the same states"}
@@ -644,7 +650,7 @@ def main():
                         min_component_voxels=args.min_component)
         if args.list_lanes:
             t = dcm.dcm_get_tuning(sy.h)
-            sy.set_tuning(list(t.lanes), t.block, t.walk, args.list_lanes)
+            sy.set_tuning(list(t.lanes), t.block, t.walk, args.list_lanes, args.list_lanes_class)
         if args.step_graph == "flat":
             sy.set_step_graph(dcm.DCM_GRAPH_FLAT)
         sy.set_state(slab.x, slab.v)
@@ -709,10 +715,11 @@ def main():
         choice = autotune.tune_live(scratch, reps=5)
         scratch.close()
         tuning = {k: v for k, v in choice.items() if k in ("walk", "lanes", "block", "list_lanes",
-                                                              "force_ms")}
+                                                              "list_lanes_class", "force_ms")}
         tuning["how"] = "autotune.tune_live on a scratch copy of the slab, 4 steps in"
         if prec == dcm.DCM_MIXED:
             args.list_lanes = int(choice.get("list_lanes", 8))
+            args.list_lanes_class = choice.get("list_lanes_class")
     sy = make_system(prec)
     if dist is not None:
         dist.barrier()
@@ -763,7 +770,7 @@ def main():
         # with every build)
         list_ents = [e for e, r in zip(timed_steps.entries, rebuilt) if not r]
         entries = sum(list_ents) / len(list_ents)
-        lkernel = "k_force_list_warp"
+        lkernel = "k_force_list_cls" if args.list_lanes_class else "k_force_list_warp"
         alg_bytes = LIST_BYTES_PER_ENTRY * entries + LIST_BYTES_PER_PARTICLE * n
         achieved_gbs = alg_bytes / (l_ms * 1e-3) / 1e9
         # algorithmic work: 8 flops per distance check (every list entry)
@@ -823,7 +830,8 @@ def main():
                              cell_min=args.cell_min, segmentation=seg)
             if args.list_lanes:
                 t = dcm.dcm_get_tuning(syx.h)
-                syx.set_tuning(list(t.lanes), t.block, t.walk, args.list_lanes)
+                syx.set_tuning(list(t.lanes), t.block, t.walk, args.list_lanes,
+                               args.list_lanes_class)
             syx.set_state(slab.x, slab.v)
             syx.compute_forces()
             ms_, _, ph_ = timed_steps(syx, args.seg_steps, 2, True)
@@ -947,6 +955,7 @@ def main():
                              "same steps from the same start (the timed run records none)")
         cfg["tuning"] = tuning
         cfg["list_lanes"] = args.list_lanes
+        cfg["list_lanes_class"] = args.list_lanes_class
         cfg["fp64_gpu_path"] = fp64_info
         cfg["segmentation_eq13"] = seg_info
         cfg["ensemble_vs_fp64"] = ens_info

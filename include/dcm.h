@@ -181,6 +181,13 @@ typedef struct {
     int32_t list_lanes;                    /* warp walk + Verlet lists: lanes per particle of
                                               the list force, 4, 8, 16 or 32 (0: 8) */
     int32_t step_graph;                    /* DCM_GRAPH_BRANCHED or DCM_GRAPH_FLAT */
+    int32_t list_lanes_class[DCM_MAX_CLASSES]; /* all 0 (default): list_lanes for every
+                                              particle, in sorted-slot order.  Otherwise the
+                                              list force runs class by class (heaviest
+                                              first) with list_lanes_class[q] lanes (4, 8,
+                                              16 or 32) per particle of cutoff class q, for
+                                              every q < n_classes (Section 5.1's per-class
+                                              schedule) */
     int32_t reserved[4];
 } dcm_tuning;
 

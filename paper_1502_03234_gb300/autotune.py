@@ -9,7 +9,9 @@ tuned on the live system and depends on the precision:
   has no shape parameter; with lists, list_lanes sets how many lanes share
   one particle of the list force (4, 8, 16 or 32): few lanes suit the short
   lists of bulk particles (r_c,min), many lanes the long lists of
-  interfacial ones (up to r_c,max, 8-13x the pairs).
+  interfacial ones (up to r_c,max, 8-13x the pairs).  After the uniform
+  choice, list_lanes_class tries lanes per cutoff class (the class-ordered
+  list force), by coordinate descent from the heaviest class.
 * DCM_FP64 runs the lanes walk: per cutoff class the number of lanes that
   share one particle (1..32), searched by coordinate descent heaviest class
   first, and the threads per block.
@@ -49,10 +51,11 @@ class Tuning:
     force_ms: float = float("nan")
     walk: int = dcm.DCM_WALK_WARP
     list_lanes: int = 8
+    list_lanes_class: list = None      # per cutoff class (class-ordered list force), or None
 
 
 def key(n: int, rc_min: float, rc_max: float, precision: int, skin: float = 0.0) -> str:
-    return f"v3|n2^{round(math.log2(max(n, 1)))}|rc{rc_min:g}/{rc_max:g}|p{precision}|s{skin:g}"
+    return f"v4|n2^{round(math.log2(max(n, 1)))}|rc{rc_min:g}/{rc_max:g}|p{precision}|s{skin:g}"
 
 
 def load_cache(path: str = CACHE) -> dict:
@@ -90,8 +93,33 @@ def _system(box, x, v, params: dcm.dcm_params, cell_min: float, stream=None) -> 
     return sy
 
 
+def _tune_list_classes(sy, K: int, G0: int, t0: float, reps: int, list_lanes, log=None):
+    """lanes per cutoff class of the class-ordered list force: coordinate
+    descent from G0 everywhere, heaviest class first.  Returns (lanes per
+    class, force ms), or (None, t0) when no per-class shape beats t0."""
+    cur = [G0] * dcm.DCM_MAX_CLASSES
+    sy.set_tuning([1], 128, dcm.DCM_WALK_WARP, G0, cur)
+    t_cur = force_ms(sy, reps)
+    if log:
+        log(f"list lanes per class {cur[:K]}: force {t_cur:.4f} ms")
+    for q in reversed(range(K)):
+        for G in list_lanes:
+            if G == cur[q]:
+                continue
+            trial = list(cur)
+            trial[q] = G
+            sy.set_tuning([1], 128, dcm.DCM_WALK_WARP, G0, trial)
+            t = force_ms(sy, reps)
+            if log:
+                log(f"list lanes per class {trial[:K]}: force {t:.4f} ms")
+            if t < t_cur:
+                cur, t_cur = trial, t
+    return (cur, t_cur) if t_cur < t0 else (None, t0)
+
+
 def _tune_mixed(sy: dcm.System, params, reps, list_lanes, log, cell):
-    """the warp kernels: list_lanes with Verlet lists, nothing without"""
+    """the warp kernels: list_lanes with Verlet lists (uniform, then per
+    cutoff class), nothing without"""
     best = None
     shapes = list_lanes if params.skin > 0 else (8,)
     for G in shapes:
@@ -102,6 +130,11 @@ def _tune_mixed(sy: dcm.System, params, reps, list_lanes, log, cell):
         if best is None or t < best.force_ms:
             best = Tuning(cell_min=cell, block=128, lanes=[1] * dcm.DCM_MAX_CLASSES,
                           force_ms=t, walk=dcm.DCM_WALK_WARP, list_lanes=G)
+    if params.skin > 0 and params.n_classes > 1:
+        cls, t = _tune_list_classes(sy, params.n_classes, best.list_lanes, best.force_ms, reps,
+                                    list_lanes, log)
+        if cls is not None:
+            best.list_lanes_class, best.force_ms = cls, t
     return best
 
 
@@ -170,10 +203,13 @@ def live_candidates(precision: int) -> tuple:
             {"walk": dcm.DCM_WALK_LANES, "lanes": [32, 32, 32, 32], "block": 256})
 
 
-def tune_live(sy: dcm.System, *, reps: int = 5, candidates=None, log=None) -> dict:
+def tune_live(sy: dcm.System, *, reps: int = 5, candidates=None, per_class: bool = True,
+              log=None) -> dict:
     """Time each launch shape on a live handle (a System or an Ensemble: the
     ensemble's one persistent force launch covers every member), keep the
-    fastest and leave it set.  Returns the choice with its force time."""
+    fastest and leave it set.  With DCM_MIXED Verlet lists and per_class,
+    lanes per cutoff class are tried after the uniform shapes.  Returns the
+    choice with its force time."""
     if candidates is None:
         candidates = live_candidates(sy.params.precision)
     best = None
@@ -188,7 +224,15 @@ def tune_live(sy: dcm.System, *, reps: int = 5, candidates=None, log=None) -> di
                 f"{c.get('list_lanes', 8)}: force {t:.4f} ms")
         if best is None or t < best["force_ms"]:
             best = dict(c, force_ms=t)
-    sy.set_tuning(best["lanes"], best["block"], best["walk"], best.get("list_lanes", 8))
+    p = sy.params
+    if (per_class and p.precision == dcm.DCM_MIXED and p.skin > 0 and p.n_classes > 1
+            and "list_lanes" in best):
+        cls, t = _tune_list_classes(sy, p.n_classes, best["list_lanes"], best["force_ms"], reps,
+                                    LIST_LANES, log)
+        if cls is not None:
+            best = dict(best, list_lanes_class=cls, force_ms=t)
+    sy.set_tuning(best["lanes"], best["block"], best["walk"], best.get("list_lanes", 8),
+                  best.get("list_lanes_class"))
     return best
 
 
@@ -203,5 +247,5 @@ def tuned_system(box, x, v, params: dcm.dcm_params, *, stream=None, cache_path: 
         save_cache(cache, cache_path)
     t = Tuning(**cache[k])
     sy = _system(box, x, v, params, t.cell_min, stream)
-    sy.set_tuning(t.lanes, t.block, t.walk, t.list_lanes)
+    sy.set_tuning(t.lanes, t.block, t.walk, t.list_lanes, t.list_lanes_class)
     return sy, t

@@ -1291,6 +1291,17 @@ extern "C" int dcm_set_tuning(dcm_handle *h, const dcm_tuning *t)
         return fail(DCM_ERR_ARG, "list_lanes must be 4, 8, 16 or 32 (0: 8)");
     if (t->step_graph != DCM_GRAPH_BRANCHED && t->step_graph != DCM_GRAPH_FLAT)
         return fail(DCM_ERR_ARG, "step_graph must be DCM_GRAPH_BRANCHED or DCM_GRAPH_FLAT");
+    bool per_class = false;
+    for (int q = 0; q < DCM_MAX_CLASSES; ++q) per_class = per_class || t->list_lanes_class[q] != 0;
+    if (per_class) {
+        for (int q = 0; q < h->p.n_classes; ++q) {
+            const int G = t->list_lanes_class[q];
+            if (G != 4 && G != 8 && G != 16 && G != 32)
+                return fail(DCM_ERR_ARG, "list_lanes_class[%d] must be 4, 8, 16 or 32 (or all 0)", q);
+        }
+        if (h->p.precision != DCM_MIXED)
+            return fail(DCM_ERR_ARG, "list_lanes_class applies to the DCM_MIXED list force");
+    }
     h->tune = *t;
     invalidate_graphs(h);
     // the two list layouts differ (the warp kernels place each list at its

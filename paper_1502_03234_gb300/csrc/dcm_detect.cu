@@ -17,7 +17,8 @@
 //   CFSM      Algorithm 4.3 as a Jacobi fixed point over a frontier: each
 //             pass recomputes only the voxels whose neighbours changed in
 //             the previous pass, writes the other buffer, and stops when
-//             nothing changes (eps = 0) or at iter_max; voxels whose
+//             nothing changes (an update must lower a value by more than 16
+//             ulps, so eps ~ 1e-15 relative) or at iter_max; voxels whose
 //             solution exceeds r_grid = r_c,max + h are never updated.  The
 //             result is independent of thread scheduling.
 //   cutoff    trilinear interpolation from the lower-left-front voxel
@@ -108,16 +109,18 @@ __global__ void __launch_bounds__(256) k_smooth8(Batch b, const TIN *__restrict_
     const int nx = g.gd[0], ny = g.gd[1], nz = g.gd[2];
     const int lv = (int)(v - g.v0);
     int c, n, stride;
+    // exact divisions by nx, ny (Geom::div_gd)
+    const int yz = (int)__umul64hi((unsigned)lv, g.div_gd[0]);
     if constexpr (AXIS == 0) {
-        c = lv % nx;
+        c = lv - yz * nx;
         n = nx;
         stride = 1;
     } else if constexpr (AXIS == 1) {
-        c = (lv / nx) % ny;
+        c = yz - (int)__umul64hi((unsigned)yz, g.div_gd[1]) * ny;
         n = ny;
         stride = nx;
     } else {
-        c = lv / (nx * ny);
+        c = (int)__umul64hi((unsigned)yz, g.div_gd[1]);
         n = nz;
         stride = nx * ny;
     }
@@ -235,6 +238,23 @@ __device__ __forceinline__ unsigned long long exact_u64(double d)
     return m >> (52 - e);
 }
 
+// The systems met by the voxel range [lo, hi): calls fn(s, a0, a1) for each
+// segment [a0, a1) of system s, in order (every thread of the block calls
+// it; the segments are the same for all of them)
+template <typename F>
+__device__ __forceinline__ void for_segments(const Batch &b, int64_t lo, int64_t hi, F &&fn)
+{
+    if (lo >= hi) return;
+    for (int s = b.M == 1 ? 0 : sys_of(b.v_off, b.M, lo); s < b.M; ++s) {
+        const int64_t a0 = lo > b.v_off[s] ? lo : b.v_off[s];
+        const int64_t a1 = hi < b.v_off[s + 1] ? hi : b.v_off[s + 1];
+        if (a0 >= hi) break;
+        if (a0 < a1) fn(s, a0, a1);
+    }
+}
+
+constexpr int KM_U = 4;      // voxel loads in flight per thread in the K-means passes
+
 // per-block shared state: centres, previous liquid count, threshold and the
 // done flag of every system (every block derives the same values from the
 // same global sums, so no broadcast is needed)
@@ -255,38 +275,36 @@ __global__ void __launch_bounds__(DET_THREADS) k_kmeans(KmeansArgs a)
     int64_t chunk = (NV + gridDim.x - 1) / gridDim.x;
     int64_t lo = (int64_t)blockIdx.x * chunk, hi = lo + chunk < NV ? lo + chunk : NV;
 
-    // phase A: extremes and totals (exact integers)
+    // phase A: extremes and totals (exact integers), segment by segment of
+    // the block's range, KM_U independent loads in flight per thread
     for (int s = threadIdx.x; s < M; s += blockDim.x) {
         s_c0[s] = 0ull;
         s_c1[s] = ~0ull;
         s_c2[s] = 0ull;
     }
     __syncthreads();
-    {
-        int cur = -1;
+    for_segments(a.b, lo, hi, [&](int sg, int64_t a0, int64_t a1) {
         unsigned long long mx = 0, mn = ~0ull, tot = 0;
-        for (int64_t v = lo + threadIdx.x; v < hi; v += blockDim.x) {
-            int s = sys_v(a.b, v);
-            if (s != cur) {
-                if (cur >= 0) {
-                    atomicMax(&s_c0[cur], mx);
-                    atomicMin(&s_c1[cur], mn);
-                    atomicAdd(&s_c2[cur], tot);
-                }
-                cur = s;
-                mx = 0;
-                mn = ~0ull;
-                tot = 0;
+        for (int64_t v = a0 + threadIdx.x; v < a1; v += (int64_t)KM_U * blockDim.x) {
+            double d[KM_U];
+#pragma unroll
+            for (int q = 0; q < KM_U; ++q) {
+                const int64_t w = v + (int64_t)q * blockDim.x;
+                d[q] = w < a1 ? __ldg(&a.Bs[w]) : -1.0;
             }
-            unsigned long long bv = exact_u64(a.Bs[v]);
-            mx = bv > mx ? bv : mx;
-            mn = bv < mn ? bv : mn;
-            tot += bv;
+#pragma unroll
+            for (int q = 0; q < KM_U; ++q) {
+                if (__double_as_longlong(d[q]) < 0) continue;   // (past the segment)
+                const unsigned long long bv = exact_u64(d[q]);
+                mx = bv > mx ? bv : mx;
+                mn = bv < mn ? bv : mn;
+                tot += bv;
+            }
         }
-        warp_flush<1>(cur, mx, s_c0);
-        warp_flush<2>(cur, mn, s_c1);
-        warp_flush<0>(cur, tot, s_c2);
-    }
+        warp_flush<1>(sg, mx, s_c0);
+        warp_flush<2>(sg, mn, s_c1);
+        warp_flush<0>(sg, tot, s_c2);
+    });
     __syncthreads();
     const int slot = blockIdx.x % SPREAD;
     for (int s = threadIdx.x; s < M; s += blockDim.x) {
@@ -321,28 +339,28 @@ __global__ void __launch_bounds__(DET_THREADS) k_kmeans(KmeansArgs a)
             s_c1[s] = 0ull;
         }
         __syncthreads();
-        int cur = -1;
-        unsigned long long cnt = 0, sum = 0;
-        for (int64_t v = lo + threadIdx.x; v < hi; v += blockDim.x) {
-            int s = sys_v(a.b, v);
-            if (s != cur) {
-                if (cur >= 0 && cnt) {
-                    atomicAdd(&s_c0[cur], cnt);
-                    atomicAdd(&s_c1[cur], sum);
+        for_segments(a.b, lo, hi, [&](int sg, int64_t a0, int64_t a1) {
+            if (s_done[sg]) return;
+            const long long thr = __double_as_longlong(s_thr[sg]);
+            unsigned long long cnt = 0, sum = 0;
+            for (int64_t v = a0 + threadIdx.x; v < a1; v += (int64_t)KM_U * blockDim.x) {
+                double d[KM_U];
+#pragma unroll
+                for (int q = 0; q < KM_U; ++q) {
+                    const int64_t w = v + (int64_t)q * blockDim.x;
+                    d[q] = w < a1 ? __ldg(&a.Bs[w]) : -1.0;
                 }
-                cur = s;
-                cnt = 0;
-                sum = 0;
+#pragma unroll
+                for (int q = 0; q < KM_U; ++q) {
+                    if (__double_as_longlong(d[q]) >= thr) {   // (-1.0: negative bits, never)
+                        cnt++;
+                        sum += exact_u64(d[q]);
+                    }
+                }
             }
-            if (s_done[s]) continue;
-            double bv = a.Bs[v];
-            if (__double_as_longlong(bv) >= __double_as_longlong(s_thr[s])) {
-                cnt++;
-                sum += exact_u64(bv);
-            }
-        }
-        warp_flush<0>(cur, cnt, s_c0);
-        warp_flush<0>(cur, sum, s_c1);
+            warp_flush<0>(sg, cnt, s_c0);
+            warp_flush<0>(sg, sum, s_c1);
+        });
         __syncthreads();
         for (int s = threadIdx.x; s < M; s += blockDim.x) {
             unsigned long long *g = a.acc + (int64_t)KACC * s + (3 + 2 * (it % 3)) * SPREAD;
@@ -380,10 +398,11 @@ __global__ void __launch_bounds__(DET_THREADS) k_kmeans(KmeansArgs a)
         __syncthreads();
         if (s_left == 0) break;
     }
-    for (int64_t v = lo + threadIdx.x; v < hi; v += blockDim.x) {
-        int s = sys_v(a.b, v);
-        a.S[v] = __double_as_longlong(a.Bs[v]) >= __double_as_longlong(s_thr[s]) ? 0 : 1;
-    }
+    for_segments(a.b, lo, hi, [&](int sg, int64_t a0, int64_t a1) {
+        const long long thr = __double_as_longlong(s_thr[sg]);
+        for (int64_t v = a0 + threadIdx.x; v < a1; v += blockDim.x)
+            a.S[v] = __double_as_longlong(__ldg(&a.Bs[v])) >= thr ? 0 : 1;
+    });
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.st->kmeans_iters = it;
         a.st->c_liquid = s_cl[0];
@@ -571,8 +590,12 @@ __device__ __forceinline__ bool cfsm_solve(const Geom &g, double old, double ax,
         __double_as_longlong(old) <= __double_as_longlong(amin + 0.999999 * g.e_min))
         return false;
     dbar = godunov_w(ax, ay, az, g.h[0], g.h[1], g.h[2], g.w_h[0], g.w_h[1], g.w_h[2]);
-    // non-negative doubles: compare the bit patterns
-    return __double_as_longlong(dbar) < __double_as_longlong(old) &&
+    // non-negative doubles: compare the bit patterns.  An update must lower
+    // the value by more than 16 units in the last place: the root of the
+    // local solve carries ~1e-14 relative error, and without the margin two
+    // neighbours can trade last-bit decreases for many passes (the values
+    // stay within ~1e-13 of the exact fixed point)
+    return __double_as_longlong(dbar) + 16 < __double_as_longlong(old) &&
            __double_as_longlong(dbar) <= __double_as_longlong(g.r_grid);
 }
 
@@ -638,8 +661,10 @@ __global__ void k_cfsm_init(Batch b, const uint8_t *__restrict__ S, double *D0, 
             const int nx = g.gd[0], ny = g.gd[1], nz = g.gd[2];
             const int v0 = (int)g.v0;
             int lv = (int)(v - v0);
-            int x = lv % nx, yz = lv / nx;
-            int y = yz % ny, z = yz / ny;
+            // exact divisions by nx, ny (Geom::div_gd)
+            int yz = (int)__umul64hi((unsigned)lv, g.div_gd[0]);
+            int z = (int)__umul64hi((unsigned)yz, g.div_gd[1]);
+            int x = lv - yz * nx, y = yz - z * ny;
             int xm = x ? x - 1 : nx - 1, xp = x + 1 < nx ? x + 1 : 0;
             int ym = y ? y - 1 : ny - 1, yp = y + 1 < ny ? y + 1 : 0;
             int zm = z ? z - 1 : nz - 1, zp = z + 1 < nz ? z + 1 : 0;
@@ -713,8 +738,9 @@ __device__ __forceinline__ void cfsm_pass(const CfsmArgs &a, int k, int nf, int6
             const int nx = g.gd[0], ny = g.gd[1], nz = g.gd[2];
             const int v0 = (int)g.v0;
             int lv = v - v0;                         // 32-bit index math
-            int x = lv % nx, yz = lv / nx;
-            int y = yz % ny, z = yz / ny;
+            int yz = (int)__umul64hi((unsigned)lv, g.div_gd[0]);     // lv / nx
+            int z = (int)__umul64hi((unsigned)yz, g.div_gd[1]);      // yz / ny
+            int x = lv - yz * nx, y = yz - z * ny;
             int xm = x ? x - 1 : nx - 1, xp = x + 1 < nx ? x + 1 : 0;
             int ym = y ? y - 1 : ny - 1, yp = y + 1 < ny ? y + 1 : 0;
             int zm = z ? z - 1 : nz - 1, zp = z + 1 < nz ? z + 1 : 0;

@@ -48,6 +48,7 @@ struct ListConst {
 struct ForceArgs {
     Batch b;
     const int32_t *class_buf;     // [0..K) counts, [K..2K) offsets
+    int list_g[DCM_MAX_CLASSES];  // list force, per-class schedule: lanes per particle of class q
     const int32_t *class_list;    // sorted slots grouped by class
     int lanes[DCM_MAX_CLASSES];   // lanes per particle per class
     const float4 *sp4;
@@ -1434,6 +1435,65 @@ __global__ void __launch_bounds__(FW_THREADS, FW_LIST_MINB) k_force_list_warp(Fo
     block_counts(a, ng, 0);
 }
 
+// The same Verlet-list forces class by class, heaviest class first, with
+// the lanes per particle of each cutoff class (a.list_g[q]): the per-class
+// schedule of Section 5.1 applied to the list force.  A work unit is one
+// warp's grab of 32/G consecutive entries of class q's slot list (the class
+// lists of the last list build, in cell order within a class).  Which group
+// and lanes a particle gets does not depend on the other particles of its
+// warp: its result is that of its own list and G alone.
+template <bool ENERGY, bool SINGLE>
+__global__ void __launch_bounds__(FW_THREADS, FW_LIST_MINB) k_force_list_cls(ForceArgs a)
+{
+    __shared__ int s_run, s_total;
+    __shared__ int s_close[list_close_slots<4>() * FW_THREADS];   // the most slots (G = 4)
+    __shared__ int s_off[DCM_MAX_CLASSES], s_cnt[DCM_MAX_CLASSES], s_g[DCM_MAX_CLASSES];
+    __shared__ int s_items[DCM_MAX_CLASSES + 1];
+    const int K = a.b.K;
+    if (threadIdx.x == 0) {
+        s_run = a.list_flags[LF_REBUILD] == 0;
+        int run = 0;
+        for (int t = 0; t < K; ++t) {            // unit order: class K-1 first
+            const int q = K - 1 - t;
+            const int G = a.list_g[q];
+            s_cnt[t] = a.class_buf[q];
+            s_off[t] = a.class_buf[K + q];
+            s_g[t] = G;
+            s_items[t] = run;
+            run += (s_cnt[t] + 32 / G - 1) / (32 / G);
+        }
+        s_items[K] = run;
+        s_total = run;
+    }
+    __syncthreads();
+    if (!s_run) return;
+    const int lane = threadIdx.x & 31;
+    const int total = s_total;
+    int ng = 0;
+    while (true) {
+        int u = 0;
+        if (lane == 0) u = (int)atomicAdd(a.queue, 1u);
+        u = __shfl_sync(0xffffffffu, u, 0);
+        if (u >= total) break;
+        int t = 0;
+        while (t + 1 < K && u >= s_items[t + 1]) ++t;
+        const int G = s_g[t];
+        const int grp = lane / G;
+        const int local = (u - s_items[t]) * (32 / G) + grp;
+        const int k = local < s_cnt[t] ? a.class_list[s_off[t] + local] : -1;
+        // (a warp-uniform branch: every lane of the warp has the same G)
+        if (G == 4)
+            particle_force_list_group<ENERGY, 4, SINGLE>(a, s_close, k, lane & 3, ng);
+        else if (G == 8)
+            particle_force_list_group<ENERGY, 8, SINGLE>(a, s_close, k, lane & 7, ng);
+        else if (G == 16)
+            particle_force_list_group<ENERGY, 16, SINGLE>(a, s_close, k, lane & 15, ng);
+        else
+            particle_force_list_group<ENERGY, 32, SINGLE>(a, s_close, k, lane, ng);
+    }
+    block_counts(a, ng, 0);
+}
+
 static void fill_args(dcm_handle *h, ForceArgs &a);
 
 int launch_list_walk(dcm_handle *h, bool fill, const int *gate, float delta)
@@ -1526,7 +1586,16 @@ int launch_list_forces(dcm_handle *h, bool energy, int part)
         const int G = h->tune.list_lanes > 0 ? h->tune.list_lanes : FW_LIST_G;
         const int gl = h->num_sms * FW_LIST_MINB;   // persistent: the resident blocks
         const bool one = h->b.M == 1;
-        if (energy) {
+        if (h->tune.list_lanes_class[0] != 0) {
+            // per-class lanes (validated by dcm_set_tuning)
+            if (energy) {
+                if (one) k_force_list_cls<true, true><<<gl, FW_THREADS, 0, h->stream>>>(a);
+                else k_force_list_cls<true, false><<<gl, FW_THREADS, 0, h->stream>>>(a);
+            } else {
+                if (one) k_force_list_cls<false, true><<<gl, FW_THREADS, 0, h->stream>>>(a);
+                else k_force_list_cls<false, false><<<gl, FW_THREADS, 0, h->stream>>>(a);
+            }
+        } else if (energy) {
             k_force_list_warp<true, 8, false><<<gl, FW_THREADS, 0, h->stream>>>(a);   // energy steps are rare
         } else if (G == 4) {
             if (one) k_force_list_warp<false, 4, true><<<gl, FW_THREADS, 0, h->stream>>>(a);
@@ -1582,6 +1651,10 @@ static void fill_args(dcm_handle *h, ForceArgs &a)
 {
     a.b = h->b;
     a.class_buf = h->class_count_dev;
+    for (int q = 0; q < DCM_MAX_CLASSES; ++q) {
+        const int G = h->tune.list_lanes_class[q];
+        a.list_g[q] = G == 4 || G == 16 || G == 32 ? G : 8;
+    }
     a.class_list = h->class_list;
     for (int q = 0; q < DCM_MAX_CLASSES; ++q) {
         int G = h->tune.lanes[q];

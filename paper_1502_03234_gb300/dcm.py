@@ -71,7 +71,7 @@ class dcm_params(C.Structure):
 class dcm_tuning(C.Structure):
     _fields_ = [("lanes", C.c_int32 * DCM_MAX_CLASSES), ("block", C.c_int32),
                 ("walk", C.c_int32), ("list_lanes", C.c_int32), ("step_graph", C.c_int32),
-                ("reserved", C.c_int32 * 4)]
+                ("list_lanes_class", C.c_int32 * DCM_MAX_CLASSES), ("reserved", C.c_int32 * 4)]
 
 
 class dcm_stats(C.Structure):
@@ -347,9 +347,12 @@ def dcm_get_stats(h) -> dcm_stats:
     return s
 
 
-def dcm_set_tuning(h, lanes, block: int = 256, walk: int = None, list_lanes: int = 8) -> None:
+def dcm_set_tuning(h, lanes, block: int = 256, walk: int = None, list_lanes: int = 8,
+                   list_lanes_class=None) -> None:
     """lanes/block: the FP64 lanes walk; list_lanes: lanes per particle of
-    the mixed-precision list force; walk None keeps the handle's walk"""
+    the mixed-precision list force; list_lanes_class: per cutoff class
+    instead (the class-ordered list force; None: list_lanes for all); walk
+    None keeps the handle's walk"""
     cur = dcm_get_tuning(h)
     t = dcm_tuning()
     for q in range(DCM_MAX_CLASSES):
@@ -358,6 +361,9 @@ def dcm_set_tuning(h, lanes, block: int = 256, walk: int = None, list_lanes: int
     t.walk = cur.walk if walk is None else int(walk)
     t.list_lanes = int(list_lanes)
     t.step_graph = cur.step_graph          # kept (see set_step_graph)
+    if list_lanes_class is not None:
+        for q in range(DCM_MAX_CLASSES):
+            t.list_lanes_class[q] = int(list_lanes_class[min(q, len(list_lanes_class) - 1)])
     check(lib().dcm_set_tuning(h, C.byref(t)))
 
 
@@ -543,12 +549,13 @@ class System:
     def stats(self) -> dcm_stats:
         return dcm_get_stats(self.h)
 
-    def set_tuning(self, lanes, block=256, walk=None, list_lanes=8):
+    def set_tuning(self, lanes, block=256, walk=None, list_lanes=8, list_lanes_class=None):
         """lanes/block: the FP64 lanes walk (lanes per particle per cutoff
         class, threads per block); list_lanes: lanes per particle of the
-        mixed-precision Verlet-list force; walk None keeps the current walk
-        (DCM_MIXED always runs the warp kernels)"""
-        dcm_set_tuning(self.h, lanes, block, walk, list_lanes)
+        mixed-precision Verlet-list force, or list_lanes_class per cutoff
+        class; walk None keeps the current walk (DCM_MIXED always runs the
+        warp kernels)"""
+        dcm_set_tuning(self.h, lanes, block, walk, list_lanes, list_lanes_class)
 
     def set_step(self, step: int):
         """the global step counter (detection runs on steps divisible by

@@ -45,8 +45,12 @@ def test_tune_live_list_lanes_single_system(dcm, orc):
         sy.step(4)
         best = autotune.tune_live(sy, reps=3, log=log.append)
         assert best["list_lanes"] in autotune.LIST_LANES
-        assert len(log) == len(autotune.LIST_LANES)        # every shape was timed
+        # every uniform shape was timed, then the per-class descent
+        assert len(log) >= len(autotune.LIST_LANES) + 1
         assert dcm.dcm_get_tuning(sy.h).list_lanes == best["list_lanes"]
+        cls = best.get("list_lanes_class")
+        got = list(dcm.dcm_get_tuning(sy.h).list_lanes_class)
+        assert got[:4] == (list(cls)[:4] if cls else [0, 0, 0, 0])
         assert best["force_ms"] > 0
         sy.step(3)
         sy.sync()
@@ -128,3 +132,35 @@ def test_tuned_system_caches_the_choice(dcm, orc, tmp_path):
         npair = sy.pair_counts()
         nc, _, _ = sy.cells()
     _check_against_oracle(orc, x, f, rc, npair, s.box, nc)
+
+
+@pytest.mark.parametrize("lanes", [[4, 8, 16, 32], [32, 16, 8, 4], [4, 4, 4, 4]])
+def test_per_class_list_lanes_match_oracle(dcm, orc, lanes):
+    # the class-ordered list force with lanes per cutoff class: the same pair
+    # set and forces within the bar, whatever lanes each class gets
+    s = slabgen.make_slab(12000, seed=64)
+    with dcm.System(s.box, len(s.x), precision=dcm.DCM_MIXED, **LISTS) as sy:
+        sy.set_state(s.x, s.v)
+        sy.step(2)
+        sy.set_tuning([1], 128, dcm.DCM_WALK_WARP, 8, lanes)
+        assert list(dcm.dcm_get_tuning(sy.h).list_lanes_class)[:4] == lanes
+        sy.step(5)
+        sy.sync()
+        assert sy.stats().list_builds >= 1
+        x, _, f = sy.get_state()
+        _, rc, _ = sy.cutoffs()
+        npair = sy.pair_counts()
+        nc, _, _ = sy.cells()
+    _check_against_oracle(orc, x, f, rc, npair, s.box, nc)
+
+
+def test_per_class_list_lanes_rejected_where_they_do_not_apply(dcm):
+    s = slabgen.make_slab(4001, seed=65)
+    with dcm.System(s.box, len(s.x), precision=dcm.DCM_FP64) as sy:
+        with pytest.raises(dcm.DcmError) as e:
+            sy.set_tuning([16], 128, dcm.DCM_WALK_LANES, 8, [4, 8, 16, 32])
+        assert e.value.code == dcm.DCM_ERR_ARG
+    with dcm.System(s.box, len(s.x), precision=dcm.DCM_MIXED, **LISTS) as sy:
+        with pytest.raises(dcm.DcmError) as e:
+            sy.set_tuning([1], 128, dcm.DCM_WALK_WARP, 8, [4, 8, 12, 32])
+        assert e.value.code == dcm.DCM_ERR_ARG
