@@ -33,6 +33,8 @@
 namespace dcm {
 
 constexpr int DET_THREADS = 256;
+constexpr int CFSM_THREADS = 512;           // the grid-wide passes: one block per SM, of
+                                            // 256 threads for one system, 512 for several
 constexpr int CFSM_TAIL_CTAS = 8;           // one portable cluster
 constexpr int CFSM_TAIL_THREADS = 512;
 
@@ -254,11 +256,12 @@ __device__ __forceinline__ void for_segments(const Batch &b, int64_t lo, int64_t
 }
 
 constexpr int KM_U = 4;      // voxel loads in flight per thread in the K-means passes
+constexpr int KM_THREADS = 512;   // the multi-system K-means: one block of 512 per SM
 
 // per-block shared state: centres, previous liquid count, threshold and the
 // done flag of every system (every block derives the same values from the
 // same global sums, so no broadcast is needed)
-__global__ void __launch_bounds__(DET_THREADS) k_kmeans(KmeansArgs a)
+__global__ void __launch_bounds__(KM_THREADS) k_kmeans(KmeansArgs a)
 {
     extern __shared__ unsigned char smem[];
     const int M = a.b.M;
@@ -710,30 +713,33 @@ struct CfsmArgs {
     DevStats *st;
 };
 
-// one pass k of the frontier iteration: items q = tid, tid + nth, ... of
-// frontier list k & 3 (nf items), pushes into list (k + 1) & 3
+// one pass k of the frontier iteration: items q = pos, pos + nth, ... of
+// frontier list k & 3 (nf items), pushes into list (k + 1) & 3.  With pos =
+// threadIdx.x * blocks + block consecutive items go to different blocks, so
+// a small frontier spreads over every SM (its FP64 solves would otherwise
+// crowd the SMs of the first few blocks)
 // the list entry this thread takes first in pass k, loaded before the
 // frontier size is known (the two reads overlap; beyond the size it is unused)
-__device__ __forceinline__ int32_t cfsm_first(const CfsmArgs &a, int k, int64_t tid)
+__device__ __forceinline__ int32_t cfsm_first(const CfsmArgs &a, int k, int64_t pos)
 {
-    return tid < a.cap ? __ldcg(&a.lists[(int64_t)(k & 3) * a.cap + tid]) : 0;
+    return pos < a.cap ? __ldcg(&a.lists[(int64_t)(k & 3) * a.cap + pos]) : 0;
 }
 
-__device__ __forceinline__ void cfsm_pass(const CfsmArgs &a, int k, int nf, int64_t tid, int64_t nth,
+__device__ __forceinline__ void cfsm_pass(const CfsmArgs &a, int k, int nf, int64_t pos, int64_t nth,
                                           int32_t first)
 {
     const double *X = (k & 1) ? a.D1 : a.D0;
     double *Y = (k & 1) ? a.D0 : a.D1;
     int32_t *F = a.lists + (int64_t)(k & 3) * a.cap;
     int32_t *Fn = a.lists + (int64_t)((k + 1) & 3) * a.cap;
-    if (tid == 0) a.fcount[(k + 2) & 3] = 0;   // list two passes ahead
+    if (pos == 0) a.fcount[(k + 2) & 3] = 0;   // list two passes ahead
     const int lane = (int)(threadIdx.x & 31);
-    for (int64_t q0 = tid - lane; q0 < nf; q0 += nth) {
-        int q = (int)q0 + lane;
+    for (int64_t q0 = 0; __any_sync(0xffffffffu, q0 + pos < nf); q0 += nth) {
+        const int64_t q = q0 + pos;
         int32_t push[7];
         int npush = 0;
         if (q < nf) {
-            int v = q0 == tid - lane ? first : __ldcg(&F[q]);
+            int v = q0 == 0 ? first : __ldcg(&F[q]);
             const Geom &g = a.b.sys[sys_v(a.b, v)];
             const int nx = g.gd[0], ny = g.gd[1], nz = g.gd[2];
             const int v0 = (int)g.v0;
@@ -771,19 +777,25 @@ __device__ __forceinline__ void cfsm_pass(const CfsmArgs &a, int k, int nf, int6
 // the passes over large frontiers, all SMs, a grid barrier between passes;
 // once the frontier falls below nf_switch the tail kernel takes over (its
 // passes are short latency chains that a grid barrier would dominate)
-__global__ void __launch_bounds__(DET_THREADS) k_cfsm(CfsmArgs a)
+__global__ void __launch_bounds__(CFSM_THREADS) k_cfsm(CfsmArgs a)
 {
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // items of a frontier smaller than the grid go round-robin over the
+    // blocks (pos_c); a larger one in contiguous runs per block (pos_l),
+    // whose list reads coalesce and whose neighbours share L1.  Both first
+    // entries are loaded before the frontier size is known.
+    const int64_t pos_c = (int64_t)threadIdx.x * gridDim.x + blockIdx.x;
+    const int64_t pos_l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nth = (int64_t)gridDim.x * blockDim.x;
     int k = 1;                                   // pass 0 ran in k_cfsm_init
     for (; k < a.iter_max; ++k) {
-        const int32_t first = cfsm_first(a, k, tid);
+        const int32_t first_c = cfsm_first(a, k, pos_c), first_l = cfsm_first(a, k, pos_l);
         const int nf = ((volatile int32_t *)a.fcount)[k & 3];
         if (nf < a.nf_switch) break;             // (also nf == 0: converged)
-        cfsm_pass(a, k, nf, tid, nth, first);
+        const bool rr = nf <= nth;
+        cfsm_pass(a, k, nf, rr ? pos_c : pos_l, nth, rr ? first_c : first_l);
         if (!grid_barrier(a.bar, a.err)) return;
     }
-    if (tid == 0) *a.kpass = k;
+    if (pos_l == 0) *a.kpass = k;
 }
 
 __device__ __forceinline__ void cluster_sync_all()
@@ -804,21 +816,21 @@ __device__ __forceinline__ unsigned cluster_rank()
 // the not-converged flag)
 __global__ void __launch_bounds__(CFSM_TAIL_THREADS) k_cfsm_tail(CfsmArgs a)
 {
-    const int64_t tid = (int64_t)cluster_rank() * blockDim.x + threadIdx.x;
+    const int64_t pos = (int64_t)threadIdx.x * CFSM_TAIL_CTAS + cluster_rank();
     const int64_t nth = (int64_t)CFSM_TAIL_CTAS * blockDim.x;
     int k = __ldcg(a.kpass);
     bool converged = false;
     for (; k < a.iter_max; ++k) {
-        const int32_t first = cfsm_first(a, k, tid);
+        const int32_t first = cfsm_first(a, k, pos);
         const int nf = ((volatile int32_t *)a.fcount)[k & 3];
         if (nf == 0) {
             converged = true;
             break;
         }
-        cfsm_pass(a, k, nf, tid, nth, first);
+        cfsm_pass(a, k, nf, pos, nth, first);
         cluster_sync_all();
     }
-    if (tid == 0) {
+    if (pos == 0) {
         // after pass k-1 the current values are in the buffer it wrote
         *a.result = (k & 1) ? 1 : 0;
         a.st->cfsm_iters = k;
@@ -1065,17 +1077,21 @@ int launch_detect(dcm_handle *h)
         a.st = h->stats;
         void *args[] = {(void *)&a};
         int rc;
+        // one block per SM where the registers hold every voxel: each pass
+        // ends in a grid barrier, whose cost grows with the arrivals
         if (b.M == 1) {
             int grid = coop_grid_size(h, (const void *)k_kmeans1, KM1_THREADS, 0);
+            if ((int64_t)h->num_sms * KM1_THREADS * KM1_CACHE >= nv) grid = h->num_sms;
             int64_t need = (nv + KM1_THREADS - 1) / KM1_THREADS;
             if (grid > need) grid = (int)(need > 0 ? need : 1);
             rc = coop_launch(h, (const void *)k_kmeans1, grid, 0, args, KM1_THREADS);
         } else {
             size_t smem = kmeans_smem(b.M);
-            int grid = coop_grid_size(h, (const void *)k_kmeans, DET_THREADS, smem);
-            int64_t need = (nv + DET_THREADS - 1) / DET_THREADS;
+            int grid = coop_grid_size(h, (const void *)k_kmeans, KM_THREADS, smem);
+            if (grid > h->num_sms) grid = h->num_sms;
+            int64_t need = (nv + KM_THREADS - 1) / KM_THREADS;
             if (grid > need) grid = (int)(need > 0 ? need : 1);
-            rc = coop_launch(h, (const void *)k_kmeans, grid, smem, args);
+            rc = coop_launch(h, (const void *)k_kmeans, grid, smem, args, KM_THREADS);
         }
         if (rc) return rc;
     }
@@ -1117,7 +1133,8 @@ int launch_detect(dcm_handle *h)
         // frontier, and the grid barrier costs less with half the arrivals
         // (measured: 0.302 against 0.359 ms per detection at 262k atoms)
         int grid = h->num_sms;
-        int rc = coop_launch(h, (const void *)k_cfsm, grid, 0, args);
+        int rc = coop_launch(h, (const void *)k_cfsm, grid, 0, args,
+                             b.M == 1 ? CFSM_THREADS / 2 : CFSM_THREADS);
         if (rc) return rc;
         // the small frontiers of the last passes: one cluster of 8 SMs
         cudaLaunchConfig_t cfg = {};

@@ -503,8 +503,8 @@ constexpr int FW_GRAB = 4;                   // particles per queue grab
 constexpr int FW_LIST_G = 8;                 // lanes per particle of the list kernel
 constexpr int FW_LIST_U = 4;                 // list entries in flight per lane
 constexpr int FW_WALK_MINB = 8;              // resident blocks per SM of the direct walk (64 registers)
-constexpr int FW_WALK_MINB1 = 10;            // ... one system (48 registers, 206 KB of row tables)
-constexpr int FW_LIST_MINB = 9;              // resident blocks per SM of the list kernel (56 registers)
+constexpr int FW_WALK_MINB1 = 9;             // ... one system (56 registers, 186 KB of row tables)
+constexpr int FW_LIST_MINB = 8;              // resident blocks per SM of the list kernel (64 registers)
 constexpr float FW_FIX_LIMIT = 32768.f;      // |partial| bound of the exact sum
 constexpr int FW_CLOSE = 64;                 // close-pair stash of a direct-walk warp (one particle)
 constexpr int FW_LIST_CLOSE = 64;            // close-pair stash of a list-kernel group (all its lanes)
