@@ -63,12 +63,12 @@ FLOPS_PER_CHECK = 8              # per candidate distance check (a Verlet-list e
 FLOPS_PER_FORCE = 16             # per in-cutoff pair: rcp, (s/r)^6, the scalar, 3 FMA
 # DRAM bytes (read + write) per force launch of the direct walk (skin 0) from the committed
 # ncu capture of that kernel on this workload; None: not captured
-FORCE_TRAFFIC = {"mixed": 14.96e6, "fp64": None}
+FORCE_TRAFFIC = {"mixed": None, "fp64": None}
 # DRAM bytes (read + write) per launch of the Verlet-list force kernel
 # (k_force_list_warp, N = 262,144, skin 0.7, skin_time 0.06, skin_floor 0.07) from the
 # committed ncu capture of that kernel on this workload, with the list entries in
 # use at the captured launches; the reported traffic scales it by the algorithmic bytes
-LIST_TRAFFIC = {"k_force_list_warp": {"bytes": 201.02e6 + 4.53e6, "entries": 39291834}}
+LIST_TRAFFIC = {"k_force_list_warp": {"bytes": 205.31e6 + 4.64e6, "entries": 39320880}}
 LIST_TRAFFIC_CONFIG = (0.7, 0.06, 0.07, 1.0)    # skin, skin_time, skin_floor, list_margin
 # bytes the list kernel must move per particle besides its list entries: own
 # position, cutoff constants, id/cell, list start and count, queue slot, the
@@ -818,6 +818,17 @@ def main():
                     "peak_note": "FP32 FMA peak derived from 152 SMs x 128 lanes x 2 flops x the "
                                  "median SM clock sampled during the timed region",
                     "pairs_per_launch": pairs, "force_ms_avg": f_avg_ms}
+    # the FP32 FMA throughput measured on this GPU in this run (an FMA chain
+    # on every SM): the derived peak above is the unit-count figure the
+    # roofline is quoted against; this is the reachable one beside it
+    try:
+        ffma, ffma_ms = dcm.dcm_fp32_peak(100000)
+        roofline["ffma_measured"] = {
+            "value": ffma, "unit": "TFLOP/s", "frac": roofline["achieved"] / ffma,
+            "ms": ffma_ms, "note": "dcm_fp32_peak: 8 dependent FMA chains per thread, 64 warps "
+                                  "per SM on every SM, timed by CUDA events after the timed steps"}
+    except dcm.DcmError as e:
+        roofline["ffma_measured"] = {"error": str(e)}
 
     # detection with Eq. 13 (Section 4.1, DCM_SEG_MUMFORD_SHAH) in place of
     # the K-means labels: per-phase times over a short run of the same slab

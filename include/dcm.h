@@ -370,6 +370,15 @@ int dcm_sync(dcm_handle *h);
  * bounded. */
 int dcm_check_bounded_wait(dcm_handle *h);
 
+/* Measurement aid (no counterpart in the thesis): the FP32 FMA throughput of
+ * the current device, from 8 independent chains of iters dependent FMAs per
+ * thread on every SM, timed by CUDA events on a stream of its own.
+ *   iters   chain length (>= 1; ~1e5 gives a launch of tens of ms)
+ *   tflops  out: 2 * FMAs / time, in TFLOP/s
+ *   ms      out (may be NULL): the timed launch's duration
+ * Errors: DCM_ERR_ARG, DCM_ERR_CUDA. */
+int dcm_fp32_peak(int32_t iters, double *tflops, double *ms);
+
 /* ---- allocation-free link-cell sort ------------------------------------------
  * The thesis has no counterpart to this entry point; it exists for callers
  * that cannot allocate device memory when they need a cell list -- a host

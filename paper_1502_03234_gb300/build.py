@@ -17,7 +17,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 SOURCES = ["dcm_api.cu", "dcm_cells.cu", "dcm_force.cu", "dcm_detect.cu", "dcm_integrate.cu",
            "dcm_noalloc.cu", "dcm_list.cu", "dcm_components.cu",
-           "dcm_ms.cu"]
+           "dcm_ms.cu", "dcm_peak.cu"]
 
 
 def _nvcc() -> str:

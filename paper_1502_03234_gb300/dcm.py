@@ -38,7 +38,7 @@ EXPORTS = [
     "dcm_set_timing", "dcm_get_phase_times", "dcm_ensemble_create", "dcm_system_count",
     "dcm_system_range", "dcm_ensemble_set_state", "dcm_ensemble_get_state",
     "dcm_ensemble_energy_virial", "dcm_check_bounded_wait", "dcm_cell_sort_noalloc",
-    "dcm_remove_small_components", "dcm_ms_segment", "dcm_set_allocator",
+    "dcm_remove_small_components", "dcm_ms_segment", "dcm_set_allocator", "dcm_fp32_peak",
 ]
 DCM_NUM_PHASES = 5
 PHASES = ("kick_drift", "detect", "bin", "force", "kick")
@@ -103,6 +103,7 @@ def lib() -> C.CDLL:
         "dcm_create": (C.c_int, [P(dcm_box), i64, P(dcm_params), vp, P(vp)]),
         "dcm_destroy": (C.c_int, [vp]),
         "dcm_set_allocator": (C.c_int, [vp, vp, vp]),
+        "dcm_fp32_peak": (C.c_int, [i32, P(C.c_double), P(C.c_double)]),
         "dcm_set_state": (C.c_int, [vp, dp, dp, C.c_int]),
         "dcm_get_state": (C.c_int, [vp, dp, dp, dp, C.c_int]),
         "dcm_set_step": (C.c_int, [vp, i64]),
@@ -182,6 +183,13 @@ def dcm_create(box, n: int, params: dcm_params | None = None, stream=None):
 
 def dcm_destroy(h) -> None:
     check(lib().dcm_destroy(h))
+
+
+def dcm_fp32_peak(iters: int = 100000) -> tuple:
+    """(TFLOP/s, ms) of an FP32 FMA chain on every SM of the current device"""
+    t, ms = C.c_double(), C.c_double()
+    check(lib().dcm_fp32_peak(int(iters), C.byref(t), C.byref(ms)))
+    return t.value, ms.value
 
 
 _ALLOCATOR = None          # the callbacks handed to the library, kept alive
