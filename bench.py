@@ -648,7 +648,7 @@ def main():
                         skin=args.skin, list_margin=args.list_margin, skin_time=args.skin_time,
                         skin_floor=args.skin_floor, cell_min=args.cell_min,
                         min_component_voxels=args.min_component)
-        if args.list_lanes:
+        if args.list_lanes and precision == dcm.DCM_MIXED:    # (the list force's lanes)
             t = dcm.dcm_get_tuning(sy.h)
             sy.set_tuning(list(t.lanes), t.block, t.walk, args.list_lanes, args.list_lanes_class)
         if args.step_graph == "flat":

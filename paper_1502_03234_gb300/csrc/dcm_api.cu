@@ -223,6 +223,7 @@ static int setup_geometry(const dcm_box *box, int64_t n, const dcm_params *p, Ge
     g.skin_floor = p->skin_floor;
     g.cc_min = p->min_component_voxels;
     g.ms_nu = p->ms_nu;
+    g.ms_nuf = (float)p->ms_nu;
     g.ms_seg = p->segmentation == DCM_SEG_MUMFORD_SHAH ? 1 : 0;
     g.eps24 = 24.0 * p->eps;
     g.eps48 = 48.0 * p->eps;

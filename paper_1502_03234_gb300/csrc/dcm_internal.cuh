@@ -112,6 +112,7 @@ struct Geom {
     float skin_time, skin_floor; // velocity-adaptive skin shares (skin_time 0: skin/2 each)
     int cc_min;                  // Section 4.2: components below this many voxels change phase (0: off)
     double ms_nu;                // Eq. 13: perimeter weight (number-density units)
+    float ms_nuf;                // ... rounded to FP32 once (the iteration's precision)
     int ms_seg;                  // Eq. 13 segmentation after K-means (DCM_SEG_MUMFORD_SHAH)
     double ms_inv_scale;         // Eq. 13: 1 / (2^(3 smooth_order) V): smoothed counts -> number density
     unsigned long long div_gd[2];  // ceil(2^64 / gd[a]), a = 0, 1: exact 32-bit division by gd[a]

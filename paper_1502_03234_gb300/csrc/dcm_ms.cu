@@ -291,7 +291,7 @@ __global__ void k_ms_iter_sys(Batch b, MsSys ms, MsBufs m, int k, float tau, flo
     int s;
     const MsCell c = ms_cell(b, v, s);
     if (!ms.flag[2 * s]) return;
-    ms_iter_voxel(c, v, m, k, tau, sigma, __double2float_rn(b.sys[s].ms_nu));
+    ms_iter_voxel(c, v, m, k, tau, sigma, b.sys[s].ms_nuf);
 }
 
 // the round's labels and whether any changed
