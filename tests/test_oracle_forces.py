@@ -138,3 +138,26 @@ def test_rejects_cutoff_beyond_half_box(orc):
     x = _gas(50, L, 10)
     with pytest.raises(ValueError):
         orc.forces(x, np.full(len(x), 5.0), L, orc.cell_dims(L, 1.5))
+
+
+def test_forces_equal_an_independent_numpy_statement(orc):
+    # Algorithm 3.2 restated in numpy (shares no code with the oracle's pair
+    # routine): minimum image, j counted for i iff 0 < |r_ij| < r_c[i],
+    # F_i += 24 eps (2 (s/r)^12 - (s/r)^6) / r^2 * r_ij, PE_i += 2 eps ((s/r)^12 - (s/r)^6)
+    L = np.array([12.0, 13.0, 15.0])
+    x = _gas(600, tuple(L), 9)
+    rng = np.random.default_rng(17)
+    rc = rng.uniform(2.5, 5.5, len(x))
+    ref = orc.forces(x, rc, tuple(L), orc.cell_dims(tuple(L), 1.5))
+    d = x[:, None, :] - x[None, :, :]
+    d -= L * np.round(d / L)
+    r2 = (d * d).sum(-1)
+    np.fill_diagonal(r2, np.inf)
+    inside = r2 < (rc * rc)[:, None]
+    s6 = np.where(inside, 1.0 / r2 ** 3, 0.0)
+    fr = np.where(inside, 24.0 * (2.0 * s6 * s6 - s6) / np.where(inside, r2, 1.0), 0.0)
+    f = (fr[:, :, None] * d).sum(1)
+    pe = (2.0 * (s6 * s6 - s6)).sum(1)
+    assert np.array_equal(ref.npair, inside.sum(1))
+    assert np.max(np.abs(ref.f - f)) < 1e-10 * max(1.0, np.abs(f).max())
+    assert np.max(np.abs(ref.pe - pe)) < 1e-10 * max(1.0, np.abs(pe).max())

@@ -175,3 +175,28 @@ def test_bin_index_geometry(orc):
     assert orc.wrap(-1e-18, L) in (0.0,) or orc.wrap(-1e-18, L) < L
     assert 0.0 <= orc.wrap(L, L) < L
     assert orc.wrap(-0.5, L) == pytest.approx(L - 0.5)
+
+
+def test_lj_printed_values(orc):
+    # the ten-digit values of the survey's closed-form table (Eq. 4, epsilon =
+    # sigma = 1): V(r) and the radial force F . r_hat = fr * r (negative:
+    # attractive)
+    for r, V_ref, F_ref in [(1.5, -0.3203365943, -1.1580288310),
+                            (3.0, -0.0054794417, -0.0109438301),
+                            (2.0 ** (1.0 / 6.0), -1.0, 0.0)]:
+        V, fr = orc.lj(r)
+        assert V == pytest.approx(V_ref, abs=5e-11)
+        assert fr * r == pytest.approx(F_ref, abs=5e-11)
+
+
+def test_cutoff_printed_values(orc):
+    # Eq. 7 at the survey's printed points: (3, 6) gives a = -3.428571428571,
+    # b = 6.428571428571 (r_c(0) = 6, r_c(6) = 3); (3, 7) a = -4.387833338551
+    for d, ref in [(1.0, 5.822479901840), (2.0, 5.571428571429), (3.0, 5.216388375109),
+                   (4.5, 4.389930659995)]:
+        assert orc.cutoff(d, 3.0, 6.0, -0.5) == pytest.approx(ref, abs=5e-12)
+    assert orc.cutoff(3.0, 3.0, 7.0, -0.5) == pytest.approx(6.290875003913, abs=5e-12)
+    # a from the endpoints: r_c(d) - b = a 2^(alpha (r_max - d)) with b = r_min - a
+    a = -3.428571428571
+    assert orc.cutoff(1e-9, 3.0, 6.0, -0.5) == pytest.approx(a * 2 ** (-0.5 * 6.0) + (3.0 - a),
+                                                           abs=1e-9)
