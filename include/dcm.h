@@ -255,6 +255,18 @@ int dcm_destroy(dcm_handle *h);
 /* Copies positions (wrapped into the box) and velocities (NULL: zero) in.
  * Resets the step counter and marks cutoffs and forces stale. */
 int dcm_set_state(dcm_handle *h, const double *x, const double *v, int mem);
+/* Replaces the state of a running system (a host-side update inside a run:
+ * a thermostat, a constraint, the host's copy handed back): positions
+ * (wrapped into the box) and velocities (NULL: zero) in; the step counter,
+ * the cutoffs of the last detection (refreshed at the next detection step,
+ * Eq. 7 on the cadence of detect_every) and the Verlet lists are kept.  The
+ * forces are recomputed from the new positions before the next step, and the
+ * lists are rebuilt then only if the skin criterion (Algorithm 3.3, the
+ * library's per-particle reuse test) finds that a particle moved beyond its
+ * share since the last build.  Before the first force evaluation it acts as
+ * dcm_set_state without resetting the step counter.  Single-system handles.
+ * Errors: as dcm_set_state. */
+int dcm_update_state(dcm_handle *h, const double *x, const double *v, int mem);
 /* Copies positions, velocities and forces out; each pointer nullable. */
 int dcm_get_state(dcm_handle *h, double *x, double *v, double *f, int mem);
 int dcm_set_step(dcm_handle *h, int64_t step);

@@ -771,7 +771,44 @@ extern "C" int dcm_set_state(dcm_handle *h, const double *x, const double *v, in
     if (!h || !x) return fail(DCM_ERR_ARG, "null handle or positions");
     int r = set_state_range(h, 0, h->n, x, v, mem);
     if (!r) h->step = 0;
+    h->keep_lists = false;
     return r;
+}
+
+// the FP32 cell-relative positions of every particle from x, in the cell
+// of the last sort (what the drift writes in a step): a state update that
+// keeps the Verlet lists
+__global__ void k_refresh_rel(Batch b, const double *__restrict__ x,
+                              const int32_t *__restrict__ cell_of, const int32_t *__restrict__ inv,
+                              float4 *sp4, float4 *spl4)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b.N) return;
+    const Geom &g = b.sys[sys_p(b, i)];
+    const size_t N = (size_t)b.N;
+    float4 lo;
+    const float4 u = cell_rel_position(b, g, x[i], x[N + i], x[2 * N + i], cell_of[i] - (int)g.c0, lo);
+    const int32_t k = inv[i];
+    sp4[k] = u;
+    spl4[k] = lo;
+}
+
+extern "C" int dcm_update_state(dcm_handle *h, const double *x, const double *v, int mem)
+{
+    if (!h || !x) return fail(DCM_ERR_ARG, "null handle or positions");
+    if (h->M != 1) return fail(DCM_ERR_ARG, "dcm_update_state takes single-system handles");
+    const bool keep = h->have_state && h->have_cut && h->forces_valid;
+    int r = set_state_range(h, 0, h->n, x, v, mem);
+    if (r) return r;
+    if (!keep) return DCM_OK;                    // (set_state, the step counter kept)
+    h->have_cut = true;                          // the last detection's cutoffs stay
+    h->keep_lists = h->nl != nullptr;
+    if (h->nl && h->list_warp) {
+        k_refresh_rel<<<nblk(h->n, 256), 256, 0, h->stream>>>(h->b, h->x, h->cell_of, h->inv,
+                                                              h->sp4, h->spl4);
+        DCM_CHECK_CUDA(cudaGetLastError());
+    }
+    return DCM_OK;
 }
 
 extern "C" int dcm_ensemble_set_state(dcm_handle *h, int k, const double *x, const double *v,
@@ -851,7 +888,11 @@ static int forces_now(dcm_handle *h, bool energy)
         h->cut_detected = true;
     }
     h->step_detect = true;                       // classes may have changed
-    int r = h->nl ? launch_list_step(h, true) : launch_bin(h);
+    // after dcm_update_state the reuse test decides whether the lists are
+    // rebuilt; after anything else they are
+    const bool rebuild = !h->keep_lists;
+    h->keep_lists = false;
+    int r = h->nl ? launch_list_step(h, rebuild) : launch_bin(h);
     if (r) return r;
     r = launch_forces(h, energy);
     if (r) return r;

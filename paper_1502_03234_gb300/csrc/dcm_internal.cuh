@@ -250,6 +250,7 @@ struct dcm_handle {
 
     // host-side status
     bool have_state, have_cut, forces_valid, cells_valid;
+    bool keep_lists;             // the next eager force evaluation lets the reuse test decide
     int64_t step;
     int class_count_host[DCM_MAX_CLASSES];
 

@@ -31,6 +31,7 @@ DCM_GRAPH_BRANCHED, DCM_GRAPH_FLAT = 0, 1
 #: every entry point include/dcm.h declares (checked by the ABI test)
 EXPORTS = [
     "dcm_default_params", "dcm_create", "dcm_destroy", "dcm_set_state", "dcm_get_state",
+    "dcm_update_state",
     "dcm_set_step", "dcm_set_cutoffs", "dcm_detect_interface", "dcm_compute_forces",
     "dcm_step", "dcm_energy_virial", "dcm_get_grid", "dcm_get_cutoffs", "dcm_get_cells",
     "dcm_get_pair_counts", "dcm_get_stats", "dcm_set_tuning", "dcm_get_tuning", "dcm_sync",
@@ -105,6 +106,7 @@ def lib() -> C.CDLL:
         "dcm_set_allocator": (C.c_int, [vp, vp, vp]),
         "dcm_fp32_peak": (C.c_int, [i32, P(C.c_double), P(C.c_double)]),
         "dcm_set_state": (C.c_int, [vp, dp, dp, C.c_int]),
+        "dcm_update_state": (C.c_int, [vp, dp, dp, C.c_int]),
         "dcm_get_state": (C.c_int, [vp, dp, dp, dp, C.c_int]),
         "dcm_set_step": (C.c_int, [vp, i64]),
         "dcm_set_cutoffs": (C.c_int, [vp, dp, C.c_int]),
@@ -238,6 +240,16 @@ def dcm_set_state(h, x, v=None) -> None:
     if v is not None and mv != mx:
         raise ValueError("x and v must live in the same memory space")
     check(lib().dcm_set_state(h, px, pv, mx))
+
+
+def dcm_update_state(h, x, v=None) -> None:
+    """replace the state of a running system, keeping its step counter,
+    cutoffs and Verlet lists (the reuse test decides on a rebuild)"""
+    px, mx = _ptr(x)
+    pv, mv = _ptr(v)
+    if v is not None and mv != mx:
+        raise ValueError("x and v must live in the same memory space")
+    check(lib().dcm_update_state(h, px, pv, mx))
 
 
 def dcm_get_state(h, n: int):
@@ -517,6 +529,14 @@ class System:
             x = np.ascontiguousarray(x, np.float64)
             v = None if v is None else np.ascontiguousarray(v, np.float64)
         dcm_set_state(self.h, x, v)
+
+    def update_state(self, x, v=None):
+        """the state of the running system replaced (step counter, cutoffs
+        and lists kept; forces recomputed before the next step)"""
+        if not (hasattr(x, "is_cuda") and x.is_cuda):
+            x = np.ascontiguousarray(x, np.float64)
+            v = None if v is None else np.ascontiguousarray(v, np.float64)
+        dcm_update_state(self.h, x, v)
 
     def get_state(self):
         return dcm_get_state(self.h, self.n)
