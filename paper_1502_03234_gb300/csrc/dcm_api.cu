@@ -318,7 +318,8 @@ static int64_t bytes_for(const Geom &g, int64_t n, int precision)
                     (g.ms_seg ? 40 : 0);
     int64_t ntiles = (ncell + 2047) / 2048 + 1;
     int64_t lists = g.skin > 0 ? 4 * list_cap(g, n) + n * (4 + 4 + 24 + 8 + 8 + 20) : 0;
-    return n * per_p + ncell * 8 + 8 + nv * per_v + ntiles * 4 + 4096 + 256 * 8 * 8 + lists;
+    return n * per_p + ncell * 8 + 8 + nv * per_v + ntiles * 4 + 4096 + 256 * 8 * 8 +
+           8 * 1024 * 8 + lists;
 }
 
 extern "C" int64_t dcm_estimate_bytes(const dcm_box *box, int64_t n, const dcm_params *p)
@@ -574,7 +575,9 @@ static int create_systems(int M, const dcm_box *boxes, const int64_t *ns, const 
     ALLOC(h->flist, 4 * nv);
     for (int k = 0; k < M; ++k) h->cc_on = h->cc_on || h->geo_host[k].cc_min > 0;
     ALLOC(h->fcount, 4);
-    ALLOC(h->kacc, 9 * 16 * (int64_t)M);   // K-means sums, 16 spread slots each
+    // K-means sums, 16 spread slots each, then the single-system kernel's
+    // per-block partials (8 x 1024)
+    ALLOC(h->kacc, 9 * 16 * (int64_t)M + 8 * 1024);
     if (h->p.segmentation == DCM_SEG_MUMFORD_SHAH) {
         ALLOC(h->msbuf, 10 * nv);
         ALLOC(h->msacc, 4 * (int64_t)M);
@@ -753,6 +756,7 @@ static int get_state_range(dcm_handle *h, int64_t p0, int64_t n, double *x, doub
     size_t bytes = sizeof(double) * 3 * (size_t)n;
     double *src[3] = {h->x, h->v, h->f};
     double *dst[3] = {x, v, f};
+    // (the staging buffer is reused in stream order: one wait at the end)
     for (int q = 0; q < 3; ++q) {
         if (!dst[q]) continue;
         k_soa_to_aos<<<nblk(n, 256), 256, 0, h->stream>>>(h->n, p0, n, src[q], h->tmp3n);
@@ -761,8 +765,8 @@ static int get_state_range(dcm_handle *h, int64_t p0, int64_t n, double *x, doub
                                        mem == DCM_DEVICE ? cudaMemcpyDeviceToDevice
                                                          : cudaMemcpyDeviceToHost,
                                        h->stream));
-        if (mem != DCM_DEVICE) DCM_CHECK_CUDA(cudaStreamSynchronize(h->stream));
     }
+    if (mem != DCM_DEVICE) DCM_CHECK_CUDA(cudaStreamSynchronize(h->stream));
     return DCM_OK;
 }
 

@@ -198,6 +198,7 @@ struct KmeansArgs {
     uint8_t *S;
     int max_iter;
     unsigned long long *acc;
+    unsigned long long *part;     // per-block partials (single-system kernel)
     unsigned int *bar;
     int *err;
     DevStats *st;
@@ -429,16 +430,26 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
     return v;
 }
 
+// per-block partials of the single-system K-means: [0, 4G) the extremes and
+// total of phase A (max, min, total, -), then two parities of (count, sum)
+// per block for the Lloyd passes (G <= KM1_MAX_BLOCKS blocks)
+constexpr int KM1_MAX_BLOCKS = 1024;
+constexpr int KM1_PART = 8 * KM1_MAX_BLOCKS;
+
 __global__ void __launch_bounds__(KM1_THREADS) k_kmeans1(KmeansArgs a)
 {
-    __shared__ unsigned long long s_a[3];
+    constexpr int NW = KM1_THREADS / 32;
+    __shared__ unsigned long long s_w[3][NW];
     __shared__ double s_cl, s_cv, s_thr;
+    __shared__ unsigned long long s_thru, s_total;
     __shared__ long long s_prev;
-    __shared__ int s_done;
+    __shared__ int s_done, s_ok;
     const int64_t NV = a.b.NV;
     const int64_t nth = (int64_t)gridDim.x * blockDim.x;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int G = gridDim.x;
+    unsigned long long *partA = a.part, *partL = a.part + 4 * KM1_MAX_BLOCKS;
     unsigned long long u[KM1_CACHE];
     // phase A: extremes and total (exact integers); the first KM1_CACHE
     // voxels of the thread stay in registers
@@ -454,17 +465,11 @@ __global__ void __launch_bounds__(KM1_THREADS) k_kmeans1(KmeansArgs a)
         }
     }
     for (int64_t v = t + (int64_t)KM1_CACHE * nth; v < NV; v += nth) {
-        const unsigned long long w = exact_u64(a.Bs[v]);
-        mx = w > mx ? w : mx;
-        mn = w < mn ? w : mn;
-        tot += w;
+        const unsigned long long x = exact_u64(a.Bs[v]);
+        mx = x > mx ? x : mx;
+        mn = x < mn ? x : mn;
+        tot += x;
     }
-    if (threadIdx.x == 0) {
-        s_a[0] = 0ull;
-        s_a[1] = ~0ull;
-        s_a[2] = 0ull;
-    }
-    __syncthreads();
     for (int off = 16; off > 0; off >>= 1) {
         unsigned long long o = __shfl_xor_sync(0xffffffffu, mx, off);
         mx = o > mx ? o : mx;
@@ -473,41 +478,68 @@ __global__ void __launch_bounds__(KM1_THREADS) k_kmeans1(KmeansArgs a)
     }
     tot = warp_sum_u64(tot);
     if (lane == 0) {
-        atomicMax(&s_a[0], mx);
-        atomicMin(&s_a[1], mn);
-        atomicAdd(&s_a[2], tot);
+        s_w[0][w] = mx;
+        s_w[1][w] = mn;
+        s_w[2][w] = tot;
     }
     __syncthreads();
-    const int slot = blockIdx.x % SPREAD;
-    unsigned long long *g = a.acc;
-    if (threadIdx.x == 0) {
-        atomicMax(&g[0 * SPREAD + slot], s_a[0]);
-        atomicMin(&g[1 * SPREAD + slot], s_a[1]);
-        atomicAdd(&g[2 * SPREAD + slot], s_a[2]);
-    }
-    if (!grid_barrier(a.bar, a.err)) return;
-    if (threadIdx.x == 0) {
-        unsigned long long gx = 0, gn = ~0ull;
-        for (int q = 0; q < SPREAD; ++q) {
-            unsigned long long hi = __ldcg(&g[q]), lo = __ldcg(&g[SPREAD + q]);
-            gx = hi > gx ? hi : gx;
-            gn = lo < gn ? lo : gn;
+    // one warp: the block's partial out, the grid barrier, every block's
+    // partial back in (plain stores ordered by the barrier's release, reads
+    // through L2), the centres of the first pass
+    if (w == 0) {
+        mx = lane < NW ? s_w[0][lane] : 0ull;
+        mn = lane < NW ? s_w[1][lane] : ~0ull;
+        tot = lane < NW ? s_w[2][lane] : 0ull;
+        for (int off = 16; off > 0; off >>= 1) {
+            unsigned long long o = __shfl_xor_sync(0xffffffffu, mx, off);
+            mx = o > mx ? o : mx;
+            o = __shfl_xor_sync(0xffffffffu, mn, off);
+            mn = o < mn ? o : mn;
         }
-        s_cl = (double)gx;
-        s_cv = (double)gn;
-        s_prev = -1;
-        s_done = 0;
-        s_thr = DMUL(DADD(s_cl, s_cv), 0.5);
+        tot = warp_sum_u64(tot);
+        int ok = 1;
+        if (lane == 0) {
+            partA[4 * blockIdx.x] = mx;
+            partA[4 * blockIdx.x + 1] = mn;
+            partA[4 * blockIdx.x + 2] = tot;
+            ok = grid_arrive_wait(a.bar, a.err) ? 1 : 0;
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        __syncwarp();
+        if (ok) {
+            mx = 0ull;
+            mn = ~0ull;
+            tot = 0ull;
+            for (int q = lane; q < G; q += 32) {
+                const unsigned long long x = __ldcg(&partA[4 * q]), y = __ldcg(&partA[4 * q + 1]);
+                mx = x > mx ? x : mx;
+                mn = y < mn ? y : mn;
+                tot += __ldcg(&partA[4 * q + 2]);
+            }
+            for (int off = 16; off > 0; off >>= 1) {
+                unsigned long long o = __shfl_xor_sync(0xffffffffu, mx, off);
+                mx = o > mx ? o : mx;
+                o = __shfl_xor_sync(0xffffffffu, mn, off);
+                mn = o < mn ? o : mn;
+            }
+            tot = warp_sum_u64(tot);
+            if (lane == 0) {
+                s_cl = (double)mx;
+                s_cv = (double)mn;
+                s_total = tot;
+                s_prev = -1;
+                s_done = 0;
+                s_thr = DMUL(DADD(s_cl, s_cv), 0.5);
+                s_thru = (unsigned long long)ceil(s_thr);
+            }
+        }
+        if (lane == 0) s_ok = ok;
     }
     __syncthreads();
+    if (!s_ok) return;
     int it = 0;
     while (it < a.max_iter) {
-        const unsigned long long thr = (unsigned long long)ceil(s_thr);
-        if (threadIdx.x == 0) {
-            s_a[0] = 0ull;
-            s_a[1] = 0ull;
-        }
-        __syncthreads();
+        const unsigned long long thr = s_thru;
         unsigned long long cnt = 0, sum = 0;
 #pragma unroll
         for (int c = 0; c < KM1_CACHE; ++c) {
@@ -516,49 +548,62 @@ __global__ void __launch_bounds__(KM1_THREADS) k_kmeans1(KmeansArgs a)
             sum += in ? u[c] : 0ull;
         }
         for (int64_t v = t + (int64_t)KM1_CACHE * nth; v < NV; v += nth) {
-            const unsigned long long w = exact_u64(a.Bs[v]);
-            cnt += w >= thr ? 1ull : 0ull;
-            sum += w >= thr ? w : 0ull;
+            const unsigned long long x = exact_u64(a.Bs[v]);
+            cnt += x >= thr ? 1ull : 0ull;
+            sum += x >= thr ? x : 0ull;
         }
         cnt = warp_sum_u64(cnt);
         sum = warp_sum_u64(sum);
-        if (lane == 0 && cnt) {
-            atomicAdd(&s_a[0], cnt);
-            atomicAdd(&s_a[1], sum);
+        if (lane == 0) {
+            s_w[0][w] = cnt;
+            s_w[1][w] = sum;
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            unsigned long long *p = g + (3 + 2 * (it % 3)) * SPREAD;
-            if (s_a[0]) {
-                atomicAdd(&p[slot], s_a[0]);
-                atomicAdd(&p[SPREAD + slot], s_a[1]);
+        if (w == 0) {
+            unsigned long long *P = partL + (it & 1) * 2 * KM1_MAX_BLOCKS;
+            cnt = lane < NW ? s_w[0][lane] : 0ull;
+            sum = lane < NW ? s_w[1][lane] : 0ull;
+            cnt = warp_sum_u64(cnt);
+            sum = warp_sum_u64(sum);
+            int ok = 1;
+            if (lane == 0) {
+                P[2 * blockIdx.x] = cnt;
+                P[2 * blockIdx.x + 1] = sum;
+                ok = grid_arrive_wait(a.bar, a.err) ? 1 : 0;
             }
-            if (blockIdx.x == 0) {   // clear the pair of the next pass
-                unsigned long long *nx = g + (3 + 2 * ((it + 1) % 3)) * SPREAD;
-                for (int q = 0; q < 2 * SPREAD; ++q) nx[q] = 0ull;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            __syncwarp();
+            if (ok) {
+                cnt = 0ull;
+                sum = 0ull;
+                for (int q = lane; q < G; q += 32) {
+                    cnt += __ldcg(&P[2 * q]);
+                    sum += __ldcg(&P[2 * q + 1]);
+                }
+                cnt = warp_sum_u64(cnt);
+                sum = warp_sum_u64(sum);
+                if (lane == 0) {
+                    const long long nl = (long long)cnt;
+                    if (nl == s_prev) {      // same threshold set as the previous pass
+                        s_done = 1;
+                    } else {
+                        const long long nvap = NV - nl;
+                        if (nl > 0) s_cl = (double)sum / (double)nl;
+                        if (nvap > 0) s_cv = (double)(s_total - sum) / (double)nvap;
+                        s_prev = nl;
+                        s_thr = DMUL(DADD(s_cl, s_cv), 0.5);
+                        s_thru = (unsigned long long)ceil(s_thr);
+                    }
+                }
             }
+            if (lane == 0) s_ok = ok;
         }
-        if (!grid_barrier(a.bar, a.err)) return;
+        __syncthreads();
+        if (!s_ok) return;
         ++it;
-        if (threadIdx.x == 0) {
-            const unsigned long long *p = g + (3 + 2 * ((it - 1) % 3)) * SPREAD;
-            long long nl = (long long)spread_sum(p);
-            unsigned long long sl = spread_sum(p + SPREAD);
-            if (nl == s_prev) {      // same threshold set as the previous pass
-                s_done = 1;
-            } else {
-                long long nvap = NV - nl;
-                unsigned long long total = spread_sum(g + 2 * SPREAD);
-                if (nl > 0) s_cl = (double)sl / (double)nl;
-                if (nvap > 0) s_cv = (double)(total - sl) / (double)nvap;
-                s_prev = nl;
-                s_thr = DMUL(DADD(s_cl, s_cv), 0.5);
-            }
-        }
-        __syncthreads();
         if (s_done) break;
     }
-    const unsigned long long thr = (unsigned long long)ceil(s_thr);
+    const unsigned long long thr = s_thru;
 #pragma unroll
     for (int c = 0; c < KM1_CACHE; ++c) {
         const int64_t v = t + (int64_t)c * nth;
@@ -1072,6 +1117,7 @@ int launch_detect(dcm_handle *h)
         a.S = h->S;
         a.max_iter = h->p.kmeans_max_iter > 0 ? h->p.kmeans_max_iter : 100;
         a.acc = h->kacc;
+        a.part = h->kacc + 9 * 16 * (int64_t)b.M;   // after the multi-system accumulators
         a.bar = h->stats->barrier;
         a.err = h->err;
         a.st = h->stats;
@@ -1082,6 +1128,7 @@ int launch_detect(dcm_handle *h)
         if (b.M == 1) {
             int grid = coop_grid_size(h, (const void *)k_kmeans1, KM1_THREADS, 0);
             if ((int64_t)h->num_sms * KM1_THREADS * KM1_CACHE >= nv) grid = h->num_sms;
+            if (grid > KM1_MAX_BLOCKS) grid = KM1_MAX_BLOCKS;
             int64_t need = (nv + KM1_THREADS - 1) / KM1_THREADS;
             if (grid > need) grid = (int)(need > 0 ? need : 1);
             rc = coop_launch(h, (const void *)k_kmeans1, grid, 0, args, KM1_THREADS);

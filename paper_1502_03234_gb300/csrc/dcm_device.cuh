@@ -121,6 +121,29 @@ __device__ __forceinline__ unsigned int atom_add_release_u32(unsigned int *p, un
     return old;
 }
 
+// the arrival and the wait of grid_barrier for one thread, the caller
+// synchronising its block around it (a block whose other threads have
+// nothing to do across the barrier); true when every block arrived
+__device__ __forceinline__ bool grid_arrive_wait(unsigned int *words, int *err)
+{
+    const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
+    const unsigned int arrived = atom_add_release_u32(words, 1u);
+    const unsigned int target = (arrived / nb + 1u) * nb;
+    long long polls = 0;
+    while ((int)(ld_acquire_u32(words) - target) < 0) {
+        ++polls;
+        if ((polls & 255) == 0) {
+            if (polls > (1ll << 21)) {
+                atomicOr(err, DEV_ERR_BARRIER);
+                return false;
+            }
+            if (*(volatile int *)err & DEV_ERR_BARRIER) return false;
+        }
+        if (polls > 4096) __nanosleep(128);
+    }
+    return true;
+}
+
 __device__ __forceinline__ bool grid_barrier(unsigned int *words, int *err)
 {
     __syncthreads();
