@@ -85,17 +85,21 @@ def _bar(f, ref_f, label):
 HEADLINE = dict(skin=0.7, skin_time=0.06, skin_floor=0.07, list_margin=1.0, warmup=10)
 
 
-def test_fullsize_headline_configuration(dcm, orc):
+@pytest.mark.parametrize("lanes", [None, [4, 8, 8, 8]], ids=["slot-order", "per-class"])
+def test_fullsize_headline_configuration(dcm, orc, lanes):
     # the exact configuration of the benchmark line: after the warm-up, run
     # until at least 20 list-reuse steps and two rebuilds have happened, then
     # compare the forces of a reuse step (the list kernel's) and of the
-    # steps' positions with the oracle
+    # steps' positions with the oracle; both list-force launch shapes the
+    # bench's tuner can pick (8 lanes in slot order, or lanes per class)
     c = CASES["slab_262144"]
     h = HEADLINE
     s = slabgen.make_slab(c["n"], seed=c["seed"])
     with dcm.System(s.box, c["n"], precision=dcm.DCM_MIXED, skin=h["skin"],
                     skin_time=h["skin_time"], skin_floor=h["skin_floor"],
                     list_margin=h["list_margin"]) as sy:
+        if lanes is not None:
+            sy.set_tuning([1], 128, dcm.DCM_WALK_WARP, 8, lanes)
         sy.set_state(s.x, s.v)
         sy.step(h["warmup"])
         sy.sync()
