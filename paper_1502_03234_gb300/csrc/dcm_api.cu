@@ -10,7 +10,20 @@
 #include <mutex>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "dcm_device.cuh"
+
+// NVTX range around an entry point (for a host-side timeline in Nsight
+// Systems; a no-op when no tool is attached)
+namespace {
+struct Trace {
+    explicit Trace(const char *name) { nvtxRangePushA(name); }
+    ~Trace() { nvtxRangePop(); }
+    Trace(const Trace &) = delete;
+    Trace &operator=(const Trace &) = delete;
+};
+}  // namespace
 
 static thread_local char g_errmsg[512] = "";
 
@@ -694,6 +707,7 @@ static int create_systems(int M, const dcm_box *boxes, const int64_t *ns, const 
 extern "C" int dcm_create(const dcm_box *box, int64_t n, const dcm_params *p, void *stream,
                           dcm_handle **out)
 {
+    Trace trace("dcm_create");
     if (!box || !p) return fail(DCM_ERR_ARG, "null box or params");
     return create_systems(1, box, &n, p, stream, out);
 }
@@ -701,6 +715,7 @@ extern "C" int dcm_create(const dcm_box *box, int64_t n, const dcm_params *p, vo
 extern "C" int dcm_ensemble_create(int count, const dcm_box *boxes, const int64_t *n,
                                    const dcm_params *params, void *stream, dcm_handle **out)
 {
+    Trace trace("dcm_ensemble_create");
     return create_systems(count, boxes, n, params, stream, out);
 }
 
@@ -772,6 +787,7 @@ static int get_state_range(dcm_handle *h, int64_t p0, int64_t n, double *x, doub
 
 extern "C" int dcm_set_state(dcm_handle *h, const double *x, const double *v, int mem)
 {
+    Trace trace("dcm_set_state");
     if (!h || !x) return fail(DCM_ERR_ARG, "null handle or positions");
     int r = set_state_range(h, 0, h->n, x, v, mem);
     if (!r) h->step = 0;
@@ -799,6 +815,7 @@ __global__ void k_refresh_rel(Batch b, const double *__restrict__ x,
 
 extern "C" int dcm_update_state(dcm_handle *h, const double *x, const double *v, int mem)
 {
+    Trace trace("dcm_update_state");
     if (!h || !x) return fail(DCM_ERR_ARG, "null handle or positions");
     if (h->M != 1) return fail(DCM_ERR_ARG, "dcm_update_state takes single-system handles");
     const bool keep = h->have_state && h->have_cut && h->forces_valid;
@@ -838,6 +855,7 @@ extern "C" int dcm_set_step(dcm_handle *h, int64_t step)
 
 extern "C" int dcm_get_state(dcm_handle *h, double *x, double *v, double *f, int mem)
 {
+    Trace trace("dcm_get_state");
     if (!h) return fail(DCM_ERR_ARG, "null handle");
     return get_state_range(h, 0, h->n, x, v, f, mem);
 }
@@ -872,6 +890,7 @@ extern "C" int dcm_set_cutoffs(dcm_handle *h, const double *rc, int mem)
 
 extern "C" int dcm_detect_interface(dcm_handle *h)
 {
+    Trace trace("dcm_detect_interface");
     if (!h) return fail(DCM_ERR_ARG, "null handle");
     if (!h->have_state) return fail(DCM_ERR_STATE, "no state set");
     if (!h->cut_detected) invalidate_graphs(h);   // list builds anticipate detected cutoffs
@@ -906,6 +925,7 @@ static int forces_now(dcm_handle *h, bool energy)
 
 extern "C" int dcm_compute_forces(dcm_handle *h)
 {
+    Trace trace("dcm_compute_forces");
     if (!h) return fail(DCM_ERR_ARG, "null handle");
     if (!h->have_state) return fail(DCM_ERR_STATE, "no state set");
     return forces_now(h, false);
@@ -1095,6 +1115,7 @@ static int capture(dcm_handle *h, bool detect, cudaGraphExec_t *exec)
 
 extern "C" int dcm_step(dcm_handle *h, int64_t nsteps)
 {
+    Trace trace("dcm_step");
     if (!h || nsteps < 0) return fail(DCM_ERR_ARG, "bad handle or nsteps");
     if (!h->have_state) return fail(DCM_ERR_STATE, "no state set");
     if (nsteps == 0) return DCM_OK;
@@ -1170,6 +1191,7 @@ static void energy_of(const dcm_handle *h, const double *o, int k, double *pe, d
 
 extern "C" int dcm_energy_virial(dcm_handle *h, double *pe, double *ke, double w[6])
 {
+    Trace trace("dcm_energy_virial");
     if (!h) return fail(DCM_ERR_ARG, "null handle");
     std::vector<double> out;
     int r = energies(h, out);
