@@ -85,3 +85,41 @@ def test_torch_allocator_ensemble(dcm):
         for k in range(len(mem)):
             for a, b in zip(ens.get_system_state(k), got[k]):
                 assert np.array_equal(a, b)
+
+
+def test_allocator_out_of_memory_releases_everything(dcm):
+    # a caller's allocator that runs dry part way through dcm_create: the
+    # call fails with DCM_ERR_OOM and hands back every buffer it got
+    import ctypes as C
+
+    import torch
+
+    s = slabgen.make_slab(4001, seed=74)
+    alloc_t = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+    release_t = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+    calls = {"n": 0, "live": 0}
+
+    def _alloc(nbytes, stream, ctx):
+        calls["n"] += 1
+        if calls["n"] > 7:
+            return None
+        calls["live"] += 1
+        return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+
+    def _release(ptr, stream, ctx):
+        calls["live"] -= 1
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    fa, fr = alloc_t(_alloc), release_t(_release)
+    torch.cuda.synchronize()
+    base = torch.cuda.memory_allocated()
+    dcm.dcm_set_allocator(fa, fr)
+    try:
+        with pytest.raises(dcm.DcmError) as e:
+            dcm.System(s.box, len(s.x), precision=dcm.DCM_MIXED)
+        assert e.value.code == dcm.DCM_ERR_OOM
+    finally:
+        dcm.use_default_allocator()
+    torch.cuda.synchronize()
+    assert calls["n"] == 8 and calls["live"] == 0
+    assert torch.cuda.memory_allocated() == base

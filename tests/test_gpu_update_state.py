@@ -107,3 +107,14 @@ def test_update_before_any_force_is_a_set_state(dcm, orc):
         sy.compute_forces()
         sy.sync()
         _check(orc, sy, s.box)
+
+
+def test_update_state_rejects_ensembles(dcm):
+    mem = [slabgen.make_slab(n, seed=sd) for n, sd in [(3001, 84), (4001, 85)]]
+    params = [dcm.default_params(precision=dcm.DCM_MIXED) for _ in mem]
+    with dcm.Ensemble([m.box for m in mem], [len(m.x) for m in mem], params) as ens:
+        for k, m in enumerate(mem):
+            ens.set_system_state(k, m.x, m.v)
+        with pytest.raises(dcm.DcmError) as e:
+            ens.update_state(np.concatenate([m.x for m in mem]))
+        assert e.value.code == dcm.DCM_ERR_ARG
