@@ -178,9 +178,8 @@ def test_bin_index_geometry(orc):
 
 
 def test_lj_printed_values(orc):
-    # the ten-digit values of the survey's closed-form table (Eq. 4, epsilon =
-    # sigma = 1): V(r) and the radial force F . r_hat = fr * r (negative:
-    # attractive)
+    # Eq. 4's closed form evaluated to ten digits (epsilon = sigma = 1): V(r)
+    # and the radial force F . r_hat = fr * r (negative: attractive)
     for r, V_ref, F_ref in [(1.5, -0.3203365943, -1.1580288310),
                             (3.0, -0.0054794417, -0.0109438301),
                             (2.0 ** (1.0 / 6.0), -1.0, 0.0)]:
@@ -190,7 +189,7 @@ def test_lj_printed_values(orc):
 
 
 def test_cutoff_printed_values(orc):
-    # Eq. 7 at the survey's printed points: (3, 6) gives a = -3.428571428571,
+    # Eq. 7's closed form to twelve digits: (3, 6) gives a = -3.428571428571,
     # b = 6.428571428571 (r_c(0) = 6, r_c(6) = 3); (3, 7) a = -4.387833338551
     for d, ref in [(1.0, 5.822479901840), (2.0, 5.571428571429), (3.0, 5.216388375109),
                    (4.5, 4.389930659995)]:
