@@ -834,11 +834,11 @@ def main():
     # the K-means labels: per-phase times over a short run of the same slab
     seg_info = None
     if rank == 0 and prec == dcm.DCM_MIXED and args.seg_steps > 0:
-        def detect_ms(seg):
+        def detect_ms(seg, **ms):
             syx = dcm.System(slab.box, n, precision=prec, stream=stream.cuda_stream,
                              skin=args.skin, list_margin=args.list_margin,
                              skin_time=args.skin_time, skin_floor=args.skin_floor,
-                             cell_min=args.cell_min, segmentation=seg)
+                             cell_min=args.cell_min, segmentation=seg, **ms)
             if args.list_lanes:
                 t = dcm.dcm_get_tuning(syx.h)
                 syx.set_tuning(list(t.lanes), t.block, t.walk, args.list_lanes,
@@ -853,9 +853,11 @@ def main():
                     "detect_ms_per_detection": ph_.get("detect", 0.0) / det_steps,
                     "kernels_detect_step": int(st_.kernels_detect)}
         km = detect_ms(dcm.DCM_SEG_KMEANS)
-        mu = detect_ms(dcm.DCM_SEG_MUMFORD_SHAH)
-        seg_info = {"kmeans": km, "eq13": mu, "steps": args.seg_steps,
-                    "eq13_params": {"nu": 0.005, "iters": 50, "rounds_max": 4},
+        mu = detect_ms(dcm.DCM_SEG_MUMFORD_SHAH)                 # the defaults: one round
+        mu4 = detect_ms(dcm.DCM_SEG_MUMFORD_SHAH, ms_outer=4)    # densities alternated
+        seg_info = {"kmeans": km, "eq13": mu, "eq13_alternating_4_rounds": mu4,
+                    "steps": args.seg_steps,
+                    "eq13_params": {"nu": 0.005, "iters": 50, "rounds": 1},
                     "segmentation_share_of_detection":
                         1.0 - km["detect_ms_per_detection"] / mu["detect_ms_per_detection"]
                         if mu["detect_ms_per_detection"] > 0 else None,

@@ -147,11 +147,13 @@ typedef struct {
        ms_nu (the thesis's 0.005 by default): rounds of exact phase means and
        ms_iters primal-dual iterations of its convex relaxation (Chan,
        Esedoglu, Nikolova; Chambolle-Pock, tau = sigma = 0.99/sqrt(12)), until
-       the labels repeat or ms_outer rounds.  Per handle (system 0's; every
+       the labels repeat or ms_outer rounds (1 by default: the K-means
+       densities, then Eq. 13, as in Section 4.1; more rounds alternate the
+       densities and the segmentation).  Per handle (system 0's; every
        system of an ensemble must agree). */
     int32_t segmentation;
     int32_t ms_iters;                      /* <= 0: 50 */
-    int32_t ms_outer;                      /* <= 0: 4 */
+    int32_t ms_outer;                      /* <= 0: 1 */
     double ms_nu;                          /* >= 0; default 0.005 */
 } dcm_params;
 

@@ -393,7 +393,7 @@ class DetectParams:
     cutoff_fn: int = 0
     segmentation: int = 0
     ms_iters: int = 50
-    ms_outer: int = 4
+    ms_outer: int = 1
     ms_nu: float = 0.005
 
     def _c(self) -> _DetectParams:

@@ -996,7 +996,7 @@ int orc_detect(int64_t n, const double *x, const double L[3],
         const double V = (L[0] / dims[0]) * (L[1] / dims[1]) * (L[2] / dims[2]);
         const double inv_scale = 1.0 / ldexp(V, 3 * (p->smooth_order > 0 ? p->smooth_order : 0));
         orc_ms_detect(dims, Bs, inv_scale, p->ms_nu, p->ms_iters > 0 ? p->ms_iters : 50,
-                      p->ms_outer > 0 ? p->ms_outer : 4, S);
+                      p->ms_outer > 0 ? p->ms_outer : 1, S);
     }
     orc_remove_small_components(dims, S, p->min_component_voxels);
     double h[3] = {L[0] / dims[0], L[1] / dims[1], L[2] / dims[2]};

@@ -198,7 +198,7 @@ typedef struct {
     int cutoff_fn;            /* 0: exponential (Eq. 7), 1: linear (Fig. 12) */
     int segmentation;         /* 0: K-means labels (Eq. 11-14); 1: then Eq. 13 (orc_ms_detect) */
     int ms_iters;             /* Eq. 13: primal-dual iterations per round; <= 0: 50 */
-    int ms_outer;             /* Eq. 13: rounds of segmentation and phase means; <= 0: 4 */
+    int ms_outer;             /* Eq. 13: rounds of segmentation and phase means; <= 0: 1 */
     double ms_nu;             /* Eq. 13: perimeter weight (number-density units) */
 } orc_detect_params;
 

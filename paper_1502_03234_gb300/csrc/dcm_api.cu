@@ -106,7 +106,7 @@ extern "C" void dcm_default_params(dcm_params *p)
     p->cell_min = 0.0;
     p->segmentation = DCM_SEG_KMEANS;
     p->ms_iters = 50;
-    p->ms_outer = 4;
+    p->ms_outer = 1;
     p->ms_nu = 0.005;
 }
 

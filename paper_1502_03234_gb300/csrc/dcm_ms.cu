@@ -15,7 +15,9 @@
 //  * the segmentation step of the interface detection (DCM_SEG_MUMFORD_SHAH):
 //    on the smoothed number density rho = Bs * inv_scale, from the K-means
 //    labels, rounds of exact phase means (integer sums of Bs) and
-//    segmentation until the labels repeat or ms_outer rounds, for every
+//    segmentation (one round by default: the thesis's flow, K-means
+//    densities then Eq. 13; more alternate) until the labels repeat or
+//    ms_outer rounds, for every
 //    system of the handle at once (a system whose labels repeated, or with
 //    an empty phase, stops; its later rounds are no-ops).
 //
@@ -341,7 +343,7 @@ int launch_ms_detect(dcm_handle *h)
     ms.flag = h->msflag;
     const float tau = (float)ms_tau();
     const int iters = h->p.ms_iters > 0 ? h->p.ms_iters : 50;
-    const int outer = h->p.ms_outer > 0 ? h->p.ms_outer : 4;
+    const int outer = h->p.ms_outer > 0 ? h->p.ms_outer : 1;
     const int vb = ms_blocks(nv), sb = (b.M + 127) / 128;
     // the sums of the K-means labels (every system starts segmenting; the
     // accumulators are left at zero by each round's begin)

@@ -63,23 +63,25 @@ def test_argument_errors(dcm):
 MS = dict(segmentation=1, ms_nu=0.005, ms_iters=50, ms_outer=4)
 
 
-def _detect_both(dcm, orc, x, box, rc=(3.0, 6.0), **kw):
-    with dcm.System(box, len(x), rc_min=rc[0], rc_max=rc[1], **MS, **kw) as sy:
+def _detect_both(dcm, orc, x, box, rc=(3.0, 6.0), ms=MS, **kw):
+    with dcm.System(box, len(x), rc_min=rc[0], rc_max=rc[1], **ms, **kw) as sy:
         sy.set_state(x, None)
         sy.detect_interface()
         dims, B, Bs, S, D = sy.grid()
         d, rcv, cls = sy.cutoffs()
         xg, _, _ = sy.get_state()
     det = orc.detect(xg, box, orc.DetectParams(rc_min=rc[0], rc_max=rc[1], voxel=1.0,
-                                               segmentation=1, ms_nu=MS["ms_nu"],
-                                               ms_iters=MS["ms_iters"], ms_outer=MS["ms_outer"]))
+                                               segmentation=1, ms_nu=ms["ms_nu"],
+                                               ms_iters=ms["ms_iters"], ms_outer=ms["ms_outer"]))
     return (dims, B, Bs, S, D, d, rcv, cls), det
 
 
+@pytest.mark.parametrize("rounds", [4, 1], ids=["alternating", "default-one-round"])
 @pytest.mark.parametrize("n,seed,amp", [(16000, 91, 0.0), (262144, 92, 0.0), (65536, 93, 1.0)])
-def test_detection_with_eq13_bit_exact(dcm, orc, n, seed, amp):
+def test_detection_with_eq13_bit_exact(dcm, orc, n, seed, amp, rounds):
     s = slabgen.make_slab(n, seed=seed, capillary_amp=amp)
-    (dims, B, Bs, S, D, d, rcv, cls), det = _detect_both(dcm, orc, s.x, s.box)
+    ms = dict(MS, ms_outer=rounds)
+    (dims, B, Bs, S, D, d, rcv, cls), det = _detect_both(dcm, orc, s.x, s.box, ms=ms)
     assert dims == det.dims
     assert np.array_equal(B, det.B) and np.array_equal(Bs, det.Bs)
     assert np.array_equal(S, det.S)                   # Eq. 13 labels, bit-exact
