@@ -164,3 +164,34 @@ def test_fullsize_ten_steps_match_oracle(dcm, orc, cfg):
     dx = np.abs(_minimg(x - xr, s.box)).max()
     print(f"262144 atoms ({cfg}), 10 steps: max |x - x_oracle| = {dx:.3e}")
     assert dx < 1e-4
+
+
+def test_mixed_forces_stay_within_the_bar_over_a_long_run(dcm):
+    # the headline configuration over 10,000 steps: every 2,000 steps the
+    # mixed path's forces against the FP64 path's on the same positions and
+    # cutoffs (FP64 pairs, the same Verlet-list pair rule), per particle
+    c = CASES["slab_262144"]
+    h = HEADLINE
+    s = slabgen.make_slab(c["n"], seed=c["seed"])
+    kw = dict(skin=h["skin"], skin_time=h["skin_time"], skin_floor=h["skin_floor"],
+              list_margin=h["list_margin"])
+    worst = 0.0
+    with dcm.System(s.box, c["n"], precision=dcm.DCM_MIXED, **kw) as sy, \
+            dcm.System(s.box, c["n"], precision=dcm.DCM_FP64, **kw) as ref:
+        sy.set_state(s.x, s.v)
+        for block in range(5):
+            sy.step(2000)
+            sy.sync()
+            x, v, f = sy.get_state()
+            _, rc, _ = sy.cutoffs()
+            ref.set_state(x, v)
+            ref.set_cutoffs(rc)
+            ref.compute_forces()
+            ref.sync()
+            _, _, f64 = ref.get_state()
+            err = np.linalg.norm(f - f64, axis=1)
+            bar = 1e-6 + 1e-5 * np.linalg.norm(f64, axis=1)
+            worst = max(worst, float(np.max(err / bar)))
+            assert np.all(err <= bar), (block, err.max(), np.max(err / bar))
+            assert np.array_equal(sy.pair_counts(), ref.pair_counts())
+    print(f"largest error over the bar in 10,000 steps: {worst:.3f}")
