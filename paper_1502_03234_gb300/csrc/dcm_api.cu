@@ -1337,7 +1337,7 @@ extern "C" int dcm_get_stats(dcm_handle *h, dcm_stats *s)
     s->list_builds = (int64_t)st.list_builds;
     s->list_entries = (int64_t)st.list_entries;
     s->cc_flipped = (int64_t)st.cc_flipped;
-    s->refined = (int64_t)st.barrier[6];
+    s->refined = (int64_t)st.barrier[6] + (int64_t)st.barrier[7];
     return DCM_OK;
 }
 

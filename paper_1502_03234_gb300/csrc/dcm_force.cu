@@ -36,7 +36,6 @@
 namespace dcm {
 
 constexpr int FORCE_THREADS = 256;
-constexpr float GUARD = 3.814697265625e-06f;   // 2^-18
 
 // the cell and LJ constants of a single-system launch (kernel parameters)
 struct ListConst {
@@ -55,6 +54,7 @@ struct ForceArgs {
     const float4 *spl4;           // MIXED: remainders of the cell-relative positions
     int32_t *refq;                // MIXED: sorted slots queued for the double-float refinement
     unsigned int *refq_n;         // ... and their number
+    unsigned int *refined_n;      // particles the list kernels refined in place
     const double4_32a *spd;
     const float4 *rq;             // MIXED: r_c^2, guard band, culling radius per slot
     const int4 *pk;               // MIXED: id, cell y, cell z per slot
@@ -1109,6 +1109,47 @@ __device__ __forceinline__ float group_store(const ForceArgs &a, const WarpAcc<E
            __shfl_sync(0xffffffffu, f2, gb + 2);
 }
 
+// Particle k again over its Verlet list, the whole warp on it, every
+// in-cutoff pair in double-float (the same pair decisions as the list
+// kernel: FP32 r^2 from the grid positions, FP64 re-decision in the guard
+// band), its results stored again.
+template <bool ENERGY, bool SINGLE>
+__device__ __forceinline__ void refine_list(const ForceArgs &a, int k, int lane)
+{
+    const Geom &g = a.b.sys[SINGLE ? 0 : sys_p(a.b, k)];
+    const float ncx = (float)g.nc[0], halfnc = 0.5f * (float)g.nc[0];
+    const float4 ui = a.sp4[k], uli = a.spl4[k], q4 = a.rq[k];
+    const int i = a.pk[k].x;
+    const float rc2f = q4.x, rc2lo = q4.y, rc2hi = q4.z;
+    const int32_t *list = a.nl + a.nl_start[k];
+    const int cnt = a.nl_cnt[k];
+    WarpAcc<ENERGY> acc;
+    for (int p = lane; p < cnt; p += 32) {
+        const int e = list[p];
+        const int j = e & 0xffffff;
+        const float4 uj = a.sp4[j];
+        float dcx = ui.w - uj.w;
+        dcx -= dcx > halfnc ? ncx : 0.f;
+        dcx += dcx < -halfnc ? ncx : 0.f;
+        const float dx = fmaf(dcx, g.cf[0], ui.x - uj.x);
+        const float dy = fmaf(-entry_dy(e), g.cf[1], ui.y - uj.y);
+        const float dz = fmaf(-entry_dz(e), g.cf[2], ui.z - uj.z);
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        bool in = r2 < rc2f;
+        if (r2 >= rc2lo && r2 < rc2hi) {
+            double rci = a.rc[i];
+            in = fp64_inside(a, g, i, a.sorted_id[j], DMUL(rci, rci));
+        }
+        if (in) {
+            float dxh, dyh, dzh, dxl, dyl, dzl;
+            close_disp(g, ncx, halfnc, ui, uli, uj, a.spl4[j], entry_dy(e), entry_dz(e), dxh, dyh,
+                       dzh, dxl, dyl, dzl);
+            acc.close(g, dxh, dyh, dzh, dxl, dyl, dzl);
+        }
+    }
+    acc.store(a, i, lane);
+}
+
 // close-pair slots of one list-kernel lane (slot-major over the block's
 // threads); a lane that meets more close pairs evaluates the rest in FP32
 template <int G>
@@ -1237,58 +1278,28 @@ __device__ __forceinline__ void particle_force_list_group(const ForceArgs &a, in
     // ---- sums over the group; lane q of the group writes value q
     float f2 = group_store<ENERGY, G>(a, acc, k >= 0, i, gl);
     // a net force small against the FP32 error of the pairs beyond r_close:
-    // queued for k_force_refine (all its pairs in double-float)
-    if (k >= 0 && gl == 0 && f2 < (SINGLE ? a.lc.redo_f2 : g.redo_f2))
-        a.refq[atomicAdd(a.refq_n, 1u)] = k;
-}
-
-// One queued particle again over its Verlet list, one warp per particle,
-// every in-cutoff pair in double-float (the same pair decisions as the list
-// kernel: FP32 r^2 from the grid positions, FP64 re-decision in the guard
-// band), its results stored again.
-template <bool ENERGY, bool SINGLE>
-__device__ __forceinline__ void refine_list(const ForceArgs &a, int k, int lane)
-{
-    const Geom &g = a.b.sys[SINGLE ? 0 : sys_p(a.b, k)];
-    const float ncx = (float)g.nc[0], halfnc = 0.5f * (float)g.nc[0];
-    const float4 ui = a.sp4[k], uli = a.spl4[k], q4 = a.rq[k];
-    const int i = a.pk[k].x;
-    const float rc2f = q4.x, rc2lo = q4.y, rc2hi = q4.z;
-    const int32_t *list = a.nl + a.nl_start[k];
-    const int cnt = a.nl_cnt[k];
-    WarpAcc<ENERGY> acc;
-    for (int p = lane; p < cnt; p += 32) {
-        const int e = list[p];
-        const int j = e & 0xffffff;
-        const float4 uj = a.sp4[j];
-        float dcx = ui.w - uj.w;
-        dcx -= dcx > halfnc ? ncx : 0.f;
-        dcx += dcx < -halfnc ? ncx : 0.f;
-        const float dx = fmaf(dcx, g.cf[0], ui.x - uj.x);
-        const float dy = fmaf(-entry_dy(e), g.cf[1], ui.y - uj.y);
-        const float dz = fmaf(-entry_dz(e), g.cf[2], ui.z - uj.z);
-        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        bool in = r2 < rc2f;
-        if (r2 >= rc2lo && r2 < rc2hi) {
-            double rci = a.rc[i];
-            in = fp64_inside(a, g, i, a.sorted_id[j], DMUL(rci, rci));
-        }
-        if (in) {
-            float dxh, dyh, dzh, dxl, dyl, dzl;
-            close_disp(g, ncx, halfnc, ui, uli, uj, a.spl4[j], entry_dy(e), entry_dz(e), dxh, dyh,
-                       dzh, dxl, dyl, dzl);
-            acc.close(g, dxh, dyh, dzh, dxl, dyl, dzl);
-        }
+    // evaluated again at once, all its pairs in double-float, by the whole
+    // warp (one such group after another; ~2 % of a slab's particles), which
+    // keeps the latency-bound refinement inside this issue-bound kernel
+    const bool redo = k >= 0 && f2 < (SINGLE ? a.lc.redo_f2 : g.redo_f2);
+    unsigned m = __ballot_sync(0xffffffffu, redo && gl == 0);
+    if (m) {
+        const int lane = threadIdx.x & 31;
+        if (lane == 0) atomicAdd(a.refined_n, (unsigned)__popc(m));
+        do {
+            const int src = __ffs(m) - 1;
+            m &= m - 1;
+            refine_list<ENERGY, SINGLE>(a, __shfl_sync(0xffffffffu, k, src), lane);
+        } while (m);
     }
-    acc.store(a, i, lane);
 }
 
-// The double-float refinement of the particles the force kernels queued
+// The double-float refinement of the particles the direct walks queued
 // (net force below 0.5 epsilon/sigma, about 2-4 % of a slab's particles,
-// mostly vapor): a warp per particle.  On a step that keeps its Verlet
-// lists, over the particle's list (complete by the reuse test); otherwise
-// (no lists, or a rebuild step: the cell sort is fresh) by the direct walk.
-// Runs after the force kernels of the step, so the queue is complete.
+// mostly vapor; the list kernels refine theirs in place): a warp per
+// particle.  On a rebuild step whose fill completed, over the fresh lists;
+// otherwise (no lists) by the direct walk.  Runs after the force kernels of
+// the step, so the queue is complete.
 template <bool ENERGY, bool SINGLE>
 __global__ void __launch_bounds__(FW_THREADS) k_force_refine(const __grid_constant__ ForceArgs a)
 {
@@ -1572,7 +1583,7 @@ int launch_list_forces(dcm_handle *h, bool energy, int part)
     ForceArgs a;
     fill_args(h, a);
     // inside a captured step the drift has zeroed the queues
-    if (!h->in_step) cudaMemsetAsync(a.refq_n, 0, sizeof(unsigned int), h->stream);
+    if (!h->in_step) cudaMemsetAsync(a.refq_n, 0, 2 * sizeof(unsigned int), h->stream);
     if (part != 1) {
         if (!h->in_step) cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), h->stream);
         if (energy)
@@ -1609,10 +1620,13 @@ int launch_list_forces(dcm_handle *h, bool energy, int part)
             else k_force_list_warp<false, 8, false><<<gl, FW_THREADS, 0, h->stream>>>(a);
         }
     }
-    if (energy)
-        launch_refine<true>(h, a);
-    else
-        launch_refine<false>(h, a);
+    // the list kernels refine in place; the walk of a rebuild step queues
+    if (part != 1) {
+        if (energy)
+            launch_refine<true>(h, a);
+        else
+            launch_refine<false>(h, a);
+    }
     return cudaGetLastError() == cudaSuccess ? DCM_OK : fail(DCM_ERR_CUDA, "force launch");
 }
 
@@ -1664,6 +1678,7 @@ static void fill_args(dcm_handle *h, ForceArgs &a)
     a.spl4 = h->spl4;
     a.refq = h->refq;
     a.refq_n = &h->stats->barrier[6];
+    a.refined_n = &h->stats->barrier[7];
     a.spd = h->spd;
     a.rq = h->rq;
     a.pk = h->pk;

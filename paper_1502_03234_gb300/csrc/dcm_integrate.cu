@@ -26,6 +26,7 @@ __global__ void k_kick_drift(Batch b, double *__restrict__ x, double *__restrict
         queues[0] = 0u;
         queues[3] = 0u;
         queues[4] = 0u;
+        queues[5] = 0u;
     }
     float mp = -3.0e38f, mq = -3.0e38f;
     if (i < b.N) {

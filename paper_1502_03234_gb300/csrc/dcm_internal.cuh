@@ -61,7 +61,8 @@ struct DevStats {
     int class_count[DCM_MAX_CLASSES];
     unsigned int barrier[8];     // [0..1] grid barrier, [2] force queue, [3] CFSM result buffer,
                                  // [4] first CFSM pass of the cluster tail, [5] list-force queue,
-                                 // [6] particles queued for the double-float refinement
+                                 // [6] particles queued for the double-float refinement,
+                                 // [7] particles the list kernels refined in place
     unsigned long long list_builds;
     unsigned long long list_entries;
     unsigned long long cc_flipped;   // voxels the small-component removal changed (last detection)
