@@ -1109,44 +1109,81 @@ __device__ __forceinline__ float group_store(const ForceArgs &a, const WarpAcc<E
            __shfl_sync(0xffffffffu, f2, gb + 2);
 }
 
-// Particle k again over its Verlet list, the whole warp on it, every
-// in-cutoff pair in double-float (the same pair decisions as the list
-// kernel: FP32 r^2 from the grid positions, FP64 re-decision in the guard
-// band), its results stored again.
+// Particle k again over its Verlet list, the whole warp on it, its results
+// stored again: the same pair decisions as the list kernel (FP32 r^2 from
+// the grid positions, FP64 re-decision in the guard band), the in-cutoff
+// pairs within 2.5 sigma in double-float and the rest in FP32.  Beyond
+// 2.5 sigma a pair force is below 0.04 epsilon/sigma and its slope below
+// 0.11 epsilon/sigma^2 (falling as r^-8), so the rounding of the FP32 grid
+// positions (~1e-7 sigma) moves it by ~1e-8, a hundredth of the smallest
+// per-particle bar.  The near pairs are gathered in 64 stash slots of the warp
+// (slot t at st[(t >> 5) * stride + (t & 31)]) and evaluated 32 at a time,
+// so the double-float work runs on full warps however near and far entries
+// interleave in the list.
+constexpr float REFINE_NEAR2 = 6.25f;         // (2.5 sigma)^2 in units of sigma^2
+
 template <bool ENERGY, bool SINGLE>
-__device__ __forceinline__ void refine_list(const ForceArgs &a, int k, int lane)
+__device__ __forceinline__ void refine_list(const ForceArgs &a, int k, int lane, int *st,
+                                            int stride)
 {
+    const unsigned full = 0xffffffffu;
     const Geom &g = a.b.sys[SINGLE ? 0 : sys_p(a.b, k)];
     const float ncx = (float)g.nc[0], halfnc = 0.5f * (float)g.nc[0];
     const float4 ui = a.sp4[k], uli = a.spl4[k], q4 = a.rq[k];
     const int i = a.pk[k].x;
     const float rc2f = q4.x, rc2lo = q4.y, rc2hi = q4.z;
+    const float near2 = REFINE_NEAR2 * g.sig2f;
     const int32_t *list = a.nl + a.nl_start[k];
     const int cnt = a.nl_cnt[k];
+    const unsigned lane_lt = (1u << lane) - 1u;
     WarpAcc<ENERGY> acc;
-    for (int p = lane; p < cnt; p += 32) {
-        const int e = list[p];
+    auto slot = [&](int t) -> int & { return st[(t >> 5) * stride + (t & 31)]; };
+    auto near_pair = [&](int e) {
         const int j = e & 0xffffff;
-        const float4 uj = a.sp4[j];
-        float dcx = ui.w - uj.w;
-        dcx -= dcx > halfnc ? ncx : 0.f;
-        dcx += dcx < -halfnc ? ncx : 0.f;
-        const float dx = fmaf(dcx, g.cf[0], ui.x - uj.x);
-        const float dy = fmaf(-entry_dy(e), g.cf[1], ui.y - uj.y);
-        const float dz = fmaf(-entry_dz(e), g.cf[2], ui.z - uj.z);
-        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        bool in = r2 < rc2f;
-        if (r2 >= rc2lo && r2 < rc2hi) {
-            double rci = a.rc[i];
-            in = fp64_inside(a, g, i, a.sorted_id[j], DMUL(rci, rci));
+        float dxh, dyh, dzh, dxl, dyl, dzl;
+        close_disp(g, ncx, halfnc, ui, uli, a.sp4[j], a.spl4[j], entry_dy(e), entry_dz(e), dxh, dyh,
+                   dzh, dxl, dyl, dzl);
+        acc.close(g, dxh, dyh, dzh, dxl, dyl, dzl);
+    };
+    int ns = 0;                                   // stash fill (the same in every lane)
+    for (int p0 = 0; p0 < cnt; p0 += 32) {
+        const int p = p0 + lane;
+        bool nr = false;
+        int e = 0;
+        if (p < cnt) {
+            e = list[p];
+            const int j = e & 0xffffff;
+            const float4 uj = a.sp4[j];
+            float dcx = ui.w - uj.w;
+            dcx -= dcx > halfnc ? ncx : 0.f;
+            dcx += dcx < -halfnc ? ncx : 0.f;
+            const float dx = fmaf(dcx, g.cf[0], ui.x - uj.x);
+            const float dy = fmaf(-entry_dy(e), g.cf[1], ui.y - uj.y);
+            const float dz = fmaf(-entry_dz(e), g.cf[2], ui.z - uj.z);
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            bool in = r2 < rc2f;
+            if (r2 >= rc2lo && r2 < rc2hi) {
+                double rci = a.rc[i];
+                in = fp64_inside(a, g, i, a.sorted_id[j], DMUL(rci, rci));
+            }
+            nr = in && r2 < near2;
+            if (in && !nr) acc.pair(g, dx, dy, dz, r2, true);
         }
-        if (in) {
-            float dxh, dyh, dzh, dxl, dyl, dzl;
-            close_disp(g, ncx, halfnc, ui, uli, uj, a.spl4[j], entry_dy(e), entry_dz(e), dxh, dyh,
-                       dzh, dxl, dyl, dzl);
-            acc.close(g, dxh, dyh, dzh, dxl, dyl, dzl);
+        const unsigned m = __ballot_sync(full, nr);
+        if (nr) slot(ns + __popc(m & lane_lt)) = e;
+        ns += __popc(m);
+        if (ns >= 32) {
+            __syncwarp();
+            near_pair(slot(lane));
+            __syncwarp();
+            if (lane < ns - 32) slot(lane) = slot(32 + lane);
+            ns -= 32;
+            __syncwarp();
         }
     }
+    __syncwarp();
+    if (lane < ns) near_pair(slot(lane));
+    __syncwarp();
     acc.store(a, i, lane);
 }
 
@@ -1289,7 +1326,8 @@ __device__ __forceinline__ void particle_force_list_group(const ForceArgs &a, in
         do {
             const int src = __ffs(m) - 1;
             m &= m - 1;
-            refine_list<ENERGY, SINGLE>(a, __shfl_sync(0xffffffffu, k, src), lane);
+            refine_list<ENERGY, SINGLE>(a, __shfl_sync(0xffffffffu, k, src), lane,
+                                        stash + (threadIdx.x & ~31), FW_THREADS);
         } while (m);
     }
 }
@@ -1318,7 +1356,7 @@ __global__ void __launch_bounds__(FW_THREADS) k_force_refine(const __grid_consta
     for (int t = w; t < total; t += nw) {
         const int k = a.refq[t];
         if (lists)
-            refine_list<ENERGY, SINGLE>(a, k, lane);
+            refine_list<ENERGY, SINGLE>(a, k, lane, s_tab[threadIdx.x >> 5].rt, 32);
         else
             particle_force_warp<ENERGY, false, SINGLE, true>(a, s_tab[threadIdx.x >> 5], nullptr,
                                                              k, lane, ng, false, entries);
