@@ -505,7 +505,7 @@ constexpr int FW_LIST_U = 4;                 // list entries in flight per lane
 constexpr int FW_WALK_MINB = 8;              // resident blocks per SM of the direct walk (64 registers)
 constexpr int FW_WALK_MINB1 = 9;             // ... one system (56 registers, 186 KB of row tables)
 constexpr int FW_LIST_MINB = 8;              // resident blocks per SM of the list kernel (64 registers)
-constexpr float FW_FIX_LIMIT = 32768.f;      // |partial| bound of the exact sum
+constexpr float FW_FIX_LIMIT = 16384.f;      // |partial| bound of the exact sum
 constexpr int FW_CLOSE = 64;                 // close-pair stash of a direct-walk warp (one particle)
 constexpr int FW_LIST_CLOSE = 64;            // close-pair stash of a list-kernel group (all its lanes)
 constexpr float FW_CMAGIC = 3072.f;          // 1.5 * 2^11: (x + m) - m rounds |x| < 2^10 to 2^-12
@@ -521,9 +521,13 @@ struct FwTable {
 // + lp * 2^-30 up to 2^-31 (rem is exact, and lp its rounding to 2^-30)
 __device__ __forceinline__ void fixed_split(float p, int &hp, int &lp)
 {
-    hp = __float2int_rn(p * 256.f);
-    float rem = fmaf((float)hp, -0.00390625f, p);          // exact
-    lp = __float2int_rn(rem * 1073741824.f);                // rem * 2^30, |.| <= 2^21
+    // nearest integers by the 1.5 * 2^23 shift (exact for |x| <= 2^22, and
+    // |p| < FW_FIX_LIMIT = 2^14 keeps p * 256 there): no conversion pipe
+    const float M = 12582912.f;
+    const float t = fmaf(p, 256.f, M);
+    hp = __float_as_int(t) - 0x4B400000;
+    const float rem = fmaf(__fsub_rn(t, M), -0.00390625f, p);   // exact
+    lp = __float_as_int(fmaf(rem, 1073741824.f, M)) - 0x4B400000;   // rem * 2^30, |.| <= 2^21
 }
 
 // Exact warp sum of three FP32 partials per lane whose magnitudes are below
