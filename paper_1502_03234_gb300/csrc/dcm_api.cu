@@ -276,6 +276,7 @@ static int setup_geometry(const dcm_box *box, int64_t n, const dcm_params *p, Ge
         g.cfl[a] = (float)(g.cedge[a] - cq);
     }
     g.ncell = (int64_t)g.nc[0] * g.nc[1] * g.nc[2];
+    for (int a = 0; a < 2; ++a) g.div_nc[a] = ~0ull / (unsigned long long)g.nc[a] + 1ull;
     g.nvox = (int64_t)g.gd[0] * g.gd[1] * g.gd[2];
     if (g.nvox > INT32_MAX)
         return fail(DCM_ERR_ARG, "voxel grid of %lld voxels: at most 2^31 - 1 per system (raise voxel)",

@@ -305,14 +305,50 @@ __device__ __forceinline__ float skin_share(const Geom &g, float speed, float fo
     return fminf(fmaxf(reach, g.skin_floor), half);
 }
 
+// The FP32 grid value and remainder of a cell-relative coordinate u: hi is u
+// rounded (to nearest, ties to even) to a multiple of the grid step 2^gexp,
+// or to 24 significant bits where those are coarser (|u| >= 2^(gexp + 24),
+// a particle that drifted beyond the bound the grid was sized for); lo is
+// the rest u - hi rounded to FP32.  Computed from the bits of u with integer
+// instructions: on this GPU a double/float conversion issues at the FP64
+// rate, 1/64 of FP32, and this runs for three coordinates of every particle
+// every step.  |u| below 2^-70 gives hi = lo = 0.
+__device__ __forceinline__ void grid_split(double u, int gexp, float &hi, float &lo)
+{
+    const long long b = __double_as_longlong(u);
+    const int E = (int)((b >> 52) & 0x7ff) - 1075;        // u = +-M 2^E, M < 2^53
+    if (E < -1075 + 1023 - 70) {
+        hi = 0.f;
+        lo = 0.f;
+        return;
+    }
+    const long long M = (b & 0xFFFFFFFFFFFFFll) | (1ll << 52);
+    int s = gexp - E;                                      // bits of M below the step
+    s = s < 29 ? 29 : s;
+    long long N = 0, r = M;
+    if (s < 54) {
+        N = M >> s;
+        const long long rem = M - (N << s), half = 1ll << (s - 1);
+        N += (rem > half || (rem == half && (N & 1))) ? 1 : 0;
+        r = M - (N << s);                                  // |r| <= 2^(s-1)
+    }
+    // N <= 2^24 and |r| < 2^53: both convert exactly or correctly rounded;
+    // the scales are powers of two inside the normal FP32 range
+    const float h = __int2float_rn((int)N) * __int_as_float((s + E + 127) << 23);
+    const float l = __ll2float_rn(r) * __int_as_float((E + 127) << 23);
+    hi = b < 0 ? -h : h;
+    lo = b < 0 ? -l : l;
+}
+
 // FP32 position of a particle relative to the corner of its link cell
 // (cell index c_local within its system) and that cell's x index; a particle
 // that wrapped through the box since its cell was assigned (between
 // Verlet-list builds) is folded back next to that cell.  Shared by the
 // gather kernel and the drift, which must produce the same bits.  The
 // corner coordinates c * L/n come from a table (the same rounded products
-// as computing them here), which keeps this to a few FP64 operations per
-// axis: the FP64 pipe runs at 1/64 of the FP32 rate.
+// as computing them here), and the cell coordinates from exact magic-number
+// divisions, which keeps this to one FP64 subtraction per axis: the FP64
+// pipe runs at 1/64 of the FP32 rate.
 // The FP32 coordinate is a multiple of the system's grid qpos (a power of
 // two chosen so that coordinates and close-pair distances have at most 24
 // significant bits), and lo receives the FP32 remainder u - hi: a close
@@ -321,27 +357,26 @@ __device__ __forceinline__ float skin_share(const Geom &g, float speed, float fo
 __device__ __forceinline__ float4 cell_rel_position(const Batch &b, const Geom &g, double px,
                                                    double py, double pz, int c_local, float4 &lo)
 {
-    int cx = c_local % g.nc[0];
-    int cy = (c_local / g.nc[0]) % g.nc[1];
-    int cz = c_local / (g.nc[0] * g.nc[1]);
+    const int yz = (int)__umul64hi((unsigned)c_local, g.div_nc[0]);      // c / nc0
+    const int cx = c_local - yz * g.nc[0];
+    const int cz = (int)__umul64hi((unsigned)yz, g.div_nc[1]);           // yz / nc1
+    const int cy = yz - cz * g.nc[1];
     const double *corner = b.corner + g.corner_off;
     const double p[3] = {px, py, pz};
     const int c[3] = {cx, g.nc[0] + cy, g.nc[0] + g.nc[1] + cz};
+    const int gexp = ((__float_as_int(g.qpos) >> 23) & 0xff) - 127;
     float uf[3], ul[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         double u = DSUB(p[a], corner[c[a]]);
-        float f = (float)u;
-        if (f > g.halfLf[a]) {
-            u = DSUB(u, g.L[a]);
-            f = (float)u;
-        } else if (f < -g.halfLf[a]) {
-            u = DADD(u, g.L[a]);
-            f = (float)u;
-        }
-        const float q = __fmul_rn(rintf(__fmul_rn(f, g.inv_qpos)), g.qpos);   // exact scalings
-        uf[a] = q;
-        ul[a] = (float)DSUB(u, (double)q);
+        // wrapped through the box: |u| above half the box (integer compare
+        // of the magnitudes' bits; the FP32 half box widened exactly)
+        const unsigned hb = (unsigned)__float_as_int(g.halfLf[a]);
+        const long long half_bits = ((long long)((hb >> 23) + 896) << 52) |
+                                    ((long long)(hb & 0x7fffff) << 29);
+        const long long ub = __double_as_longlong(u);
+        if ((ub & 0x7FFFFFFFFFFFFFFFll) > half_bits) u = ub < 0 ? DADD(u, g.L[a]) : DSUB(u, g.L[a]);
+        grid_split(u, gexp, uf[a], ul[a]);
     }
     lo = make_float4(ul[0], ul[1], ul[2], 0.f);
     return make_float4(uf[0], uf[1], uf[2], (float)cx);

@@ -117,6 +117,7 @@ struct Geom {
     int ms_seg;                  // Eq. 13 segmentation after K-means (DCM_SEG_MUMFORD_SHAH)
     double ms_inv_scale;         // Eq. 13: 1 / (2^(3 smooth_order) V): smoothed counts -> number density
     unsigned long long div_gd[2];  // ceil(2^64 / gd[a]), a = 0, 1: exact 32-bit division by gd[a]
+    unsigned long long div_nc[2];  // ceil(2^64 / nc[a]), a = 0, 1: exact 32-bit division by nc[a]
                                    // as the high word of a 64-bit product (Granlund-Montgomery)
     double eps24, eps48, eps2, sig2;     // LJ force/energy constants
     float eps24f, eps48f, eps2f, sig2f;
