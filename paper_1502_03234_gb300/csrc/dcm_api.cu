@@ -287,14 +287,16 @@ static int setup_geometry(const dcm_box *box, int64_t n, const dcm_params *p, Ge
 // Verlet-list entries reserved for one system: every particle may hold
 // the neighbours of a sphere of r_c,max + skin, but no more than three times
 // those of r_c,min + skin (bulk particles are the vast majority), at a
-// density bound of 1.0
+// density bound of 1.0, plus the 15 entries of slack and the rounding up to
+// 8 that each particle's own capacity adds (without them a box of uniform
+// cutoff at liquid density asks for more than this and never keeps a list)
 static int64_t list_cap(const Geom &g, int64_t n)
 {
     if (g.skin <= 0) return 0;
     const double c43pi = 4.18879020478639;
     double big = c43pi * pow(g.rc_max + g.skin, 3.0);
     double small = 3.0 * c43pi * pow(g.rc_min + g.skin, 3.0);
-    return n * (int64_t)ceil(big < small ? big : small) + 1024;
+    return n * ((int64_t)ceil(big < small ? big : small) + 23) + 1024;
 }
 
 // the small-component buffers (5 ints per voxel and a flag per tile) and the

@@ -74,6 +74,43 @@ def test_all_liquid_box(dcm, orc, prec, skin):
     _check(dcm, orc, x, v, box, prec, skin)
 
 
+@pytest.mark.parametrize("lanes", [4, 8, 16, 32])
+def test_lattice_refined_in_place(dcm, orc, lanes):
+    # a nearly perfect lattice at rest under one cutoff (r_c,min = r_c,max:
+    # the detection of a box without interface then changes nothing): every
+    # net force is close to zero, so on a step that reuses its Verlet lists
+    # nearly every particle falls under the refinement threshold and the list
+    # kernel evaluates it again in place (each warp takes its groups'
+    # particles one after another); the bar 1e-6 + 1e-5 |F| is then close to
+    # its absolute floor for all of them
+    x, box = _fcc(10, slabgen.fcc_edge(0.8), 1e-3, seed=61)        # 4000 atoms
+    n = len(x)
+    with dcm.System(box, n, precision=1, skin=0.5, rc_min=3.0, rc_max=3.0) as sy:
+        sy.set_tuning([2, 1, 2, 2], 128, 0, lanes)
+        sy.set_state(x, np.zeros_like(x))
+        sy.step(2)
+        for _ in range(20):
+            b0 = sy.stats().list_builds
+            sy.step(1)
+            sy.sync()
+            if sy.stats().list_builds == b0:
+                break
+        else:
+            pytest.fail("no step reused its lists")
+        refined = sy.stats().refined
+        npair = sy.pair_counts()
+        _, rc, _ = sy.cutoffs()
+        xg, _, f = sy.get_state()
+        nc, _, _ = sy.cells()
+    ref = orc.forces(xg, rc, box, nc)
+    fmag = np.linalg.norm(ref.f, axis=1)
+    assert np.mean(fmag < 0.5) > 0.9                 # the lattice is nearly at rest
+    assert refined >= int(np.sum(fmag < 0.45))       # all of those were refined
+    assert np.array_equal(npair, ref.npair)
+    err = np.linalg.norm(f - ref.f, axis=1)
+    assert np.all(err <= FP64_ABS + FP64_REL * fmag), (err.max(), lanes)
+
+
 @pytest.mark.parametrize("edge,skin", [(13.6, 0.0), (16.6, 0.5)])
 def test_smallest_box_for_the_stencil(dcm, orc, edge, skin):
     # the cell stencil must not wrap onto itself: 2 s_max + 1 <= cells per
