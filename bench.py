@@ -92,6 +92,12 @@ def parse():
     ap.add_argument("--ens-steps", type=int, default=50,
                     help="steps of the 64-slab ensemble comparison, batched mixed against "
                          "per-system FP64 (0: skip)")
+    ap.add_argument("--wavy-steps", type=int, default=30,
+                    help="steps of the 2.1M-atom capillary-wave slab leg of the default line "
+                         "(0: skip)")
+    ap.add_argument("--serve-requests", type=int, default=24,
+                    help="requests of the serving leg of the default line (nsteps up to 500; "
+                         "0: skip)")
     ap.add_argument("--seg-steps", type=int, default=20,
                     help="steps of the detection-with-Eq.-13 comparison (0: skip)")
     ap.add_argument("--skin", type=float, default=0.7,
@@ -445,6 +451,42 @@ def accuracy_study(dcm, slabgen, stream, np, torch, n=262144):
                                 "forces cannot dominate")}}
 
 
+def wavy_run(dcm, slabgen, np, stream, flush, n, steps, warm, skin, skin_time, skin_floor):
+    """the capillary-wave slab (two interfaces with sinusoidal z offsets of
+    amplitude 1 sigma), DCM r_c 3/7, timed like the headline: per-step device
+    times with L2 flushed before each step"""
+    s = slabgen.make_slab(n, seed=3, capillary_amp=1.0)
+    sy = dcm.System(s.box, n, precision=dcm.DCM_MIXED, rc_min=3.0, rc_max=7.0, skin=skin,
+                    skin_time=skin_time, skin_floor=skin_floor, stream=stream.cuda_stream)
+    sy.set_state(s.x, s.v)
+    sy.compute_forces()
+    ms, ph = _timed(sy, stream, flush, steps, warm)
+    st = sy.stats()
+    x, _, _ = sy.get_state()
+    sy.close()
+    if not np.all(np.isfinite(x)):
+        raise RuntimeError("non-finite positions")
+    return n * steps / (sum(ms) * 1e-3), ms, ph, st
+
+
+WAVY_N = 2097152
+
+
+def serving_run(dcm, serving, count, steps_max, skin, skin_time, skin_floor):
+    """a Poisson stream of slab requests through the serving loop (HBM-budget
+    admission, continuous batching); its summary"""
+    rep = serving.serve_trace(count=count, rate=20.0, n_min=2048, n_max=524288, steps_min=100,
+                              steps_max=steps_max, budget_gb=120.0, precision=dcm.DCM_MIXED,
+                              skin=skin, skin_time=skin_time, skin_floor=skin_floor)
+    return rep.summary()
+
+
+def serving_workload(count, steps_max):
+    return (f"Poisson stream of {count} slab requests at 20 req/s, N log-uniform in [2048, "
+            f"524288], nsteps uniform in [100, {steps_max}], 120 GB HBM budget, continuous "
+            f"batching (up to 16 resident slots, 50-step chunks), mixed precision")
+
+
 def run_workload(args):
     import numpy as np
     import torch
@@ -465,21 +507,10 @@ def run_workload(args):
     with Clocks(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
         if args.workload == "wavy":
             def wavy(n, steps, warm):
-                s = slabgen.make_slab(n, seed=3, capillary_amp=1.0)
-                sy = dcm.System(s.box, n, precision=dcm.DCM_MIXED, rc_min=3.0, rc_max=7.0,
-                                skin=args.skin, skin_time=args.skin_time,
-                                skin_floor=args.skin_floor, stream=stream.cuda_stream)
-                sy.set_state(s.x, s.v)
-                sy.compute_forces()
-                ms, ph = _timed(sy, stream, flush, steps, warm)
-                st = sy.stats()
-                x, _, _ = sy.get_state()
-                sy.close()
-                if not np.all(np.isfinite(x)):
-                    raise RuntimeError("non-finite positions")
-                return n * steps / (sum(ms) * 1e-3), ms, ph, st
+                return wavy_run(dcm, slabgen, np, stream, flush, n, steps, warm, args.skin,
+                                args.skin_time, args.skin_floor)
 
-            n = 2097152
+            n = WAVY_N
             value, ms, ph, st = wavy(n, args.steps, args.warmup)
             sweep = {}
             for nn in [int(q) for q in args.sweep.split(",") if q]:
@@ -533,19 +564,13 @@ def run_workload(args):
                 "latency_ms": {"p50": _pct(ms, 50), "p99": _pct(ms, 99), "unit": "ms per step"},
                 "gpu_launches": int(kernels)})
         else:
-            rep = serving.serve_trace(count=args.requests, rate=20.0, n_min=2048, n_max=524288,
-                                      steps_min=100, steps_max=2000, budget_gb=120.0,
-                                      precision=dcm.DCM_MIXED, skin=args.skin,
-                                      skin_time=args.skin_time, skin_floor=args.skin_floor)
-            summ = rep.summary()
+            summ = serving_run(dcm, serving, args.requests, 2000, args.skin, args.skin_time,
+                               args.skin_floor)
             line.update({
                 "metric": "aggregate atom-steps/s of a served request stream; p50/p99 latency",
                 "value": summ["atom_steps_per_s"], "steps": None, "ms_per_step": None,
-                "config": {"workload": f"Poisson stream of {args.requests} slab requests at 20 "
-                                       f"req/s, N log-uniform in [2048, 524288], nsteps uniform "
-                                       f"in [100, 2000], 120 GB HBM budget, continuous batching "
-                                       f"(up to 16 resident slots, 50-step chunks), mixed "
-                                       f"precision", "requests": args.requests, "skin": args.skin,
+                "config": {"workload": serving_workload(args.requests, 2000),
+                           "requests": args.requests, "skin": args.skin,
                            "skin_time": args.skin_time, "skin_floor": args.skin_floor},
                 "latency_s": summ["latency_s"], "serving": summ})
     line["clocks"] = clk.summary()
@@ -871,6 +896,29 @@ def main():
         ens_info = ensemble_compare(dcm, slabgen, autotune, stream, flush, torch, args.ens_steps,
                                     3, args.skin, args.skin_time, args.skin_floor)
 
+    # the other workloads of the method, short: the 2.1M-atom capillary-wave
+    # slab (timed like the headline) and a served request stream
+    wavy_info = None
+    if rank == 0 and prec == dcm.DCM_MIXED and args.wavy_steps > 0:
+        wv, wms, wph, wst = wavy_run(dcm, slabgen, np, stream, flush, WAVY_N, args.wavy_steps, 3,
+                                     args.skin, args.skin_time, args.skin_floor)
+        wavy_info = {"value": wv, "unit": UNIT, "n": WAVY_N, "steps": args.wavy_steps,
+                     "warmup": 3, "ms_per_step": sum(wms) / len(wms),
+                     "latency_ms": {"p50": _pct(wms, 50), "p99": _pct(wms, 99)},
+                     "pairs_per_particle": wst.pairs / WAVY_N, "phase_ms_avg": wph,
+                     "workload": f"LJ slab N={WAVY_N}, L x L x 4L periodic, two interfaces with "
+                                 f"sinusoidal z offsets (amplitude 1 sigma, random phases), DCM "
+                                 f"r_c 3/7, detection every 2 steps, mixed precision; L2 flushed "
+                                 f"before every timed step"}
+    serve_info = None
+    if rank == 0 and prec == dcm.DCM_MIXED and args.serve_requests > 0:
+        from paper_1502_03234_gb300 import serving
+
+        summ = serving_run(dcm, serving, args.serve_requests, 500, args.skin, args.skin_time,
+                           args.skin_floor)
+        serve_info = dict(summ)
+        serve_info["workload"] = serving_workload(args.serve_requests, 500)
+
     # the plain FP64 GPU path on the same system (the comparison the metric
     # names), timed exactly like the headline: the same steps and warm-up,
     # no per-phase events, L2 flushed before every step
@@ -980,6 +1028,8 @@ def main():
         cfg["fp64_gpu_path"] = fp64_info
         cfg["segmentation_eq13"] = seg_info
         cfg["ensemble_vs_fp64"] = ens_info
+        cfg["wavy_slab"] = wavy_info
+        cfg["serving"] = serve_info
         cfg["energy_drift"] = {"rel": abs(energy["e1"] - energy["e0"]) / abs(energy["e0"]),
                                "steps": args.steps,
                                "note": "|E(K) - E(0)| / |E(0)| over the timed steps (NVE; the "
