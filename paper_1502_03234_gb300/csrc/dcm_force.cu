@@ -39,7 +39,7 @@ constexpr int FORCE_THREADS = 256;
 
 // the cell and LJ constants of a single-system launch (kernel parameters)
 struct ListConst {
-    float cf[3], cfl[3], ncx, halfnc;
+    float cf[3], cfl[3], ncx, halfnc, inv_ncx;
     float sig2f, eps48f, eps24f, eps2f;
     float sig2l, eps48l, eps24l, rclose2, redo_f2, qtop;
 };
@@ -785,6 +785,17 @@ __device__ __forceinline__ void close_disp(const C &c, float ncx, float halfnc, 
     dzl = __fadd_rn(fmaf(-dzc, c.cfl[2], __fsub_rn(uli.z, ulj.z)), ez);
 }
 
+// The cell x offset of a list pair folded into (-n/2, n/2] with one
+// rounding: dcx / n rounded to an integer by the 1.5 * 2^23 shift, then that
+// multiple of n taken off (exact: small integers).  Every listed pair has
+// |offset| <= s_max with 2 s_max + 1 <= n, so the quotient stays clear of
+// 1/2 and the result is the same as comparing against n/2 twice.
+__device__ __forceinline__ float wrap_cells(float dcx, float ncx, float inv_ncx)
+{
+    const float k = __fsub_rn(fmaf(dcx, inv_ncx, 12582912.f), 12582912.f);
+    return fmaf(-k, ncx, dcx);
+}
+
 __device__ __forceinline__ float entry_dy(int e) { return (float)(((e >> 24) & 15) - 8); }
 __device__ __forceinline__ float entry_dz(int e) { return (float)((int)((unsigned)e >> 28) - 8); }
 
@@ -1132,7 +1143,7 @@ __device__ __forceinline__ void refine_list(const ForceArgs &a, int k, int lane,
 {
     const unsigned full = 0xffffffffu;
     const Geom &g = a.b.sys[SINGLE ? 0 : sys_p(a.b, k)];
-    const float ncx = (float)g.nc[0], halfnc = 0.5f * (float)g.nc[0];
+    const float ncx = (float)g.nc[0], halfnc = 0.5f * (float)g.nc[0], inv_ncx = 1.f / ncx;
     const float4 ui = a.sp4[k], uli = a.spl4[k], q4 = a.rq[k];
     const int i = a.pk[k].x;
     const float rc2f = q4.x, rc2lo = q4.y, rc2hi = q4.z;
@@ -1158,9 +1169,7 @@ __device__ __forceinline__ void refine_list(const ForceArgs &a, int k, int lane,
             e = list[p];
             const int j = e & 0xffffff;
             const float4 uj = a.sp4[j];
-            float dcx = ui.w - uj.w;
-            dcx -= dcx > halfnc ? ncx : 0.f;
-            dcx += dcx < -halfnc ? ncx : 0.f;
+            const float dcx = wrap_cells(ui.w - uj.w, ncx, inv_ncx);
             const float dx = fmaf(dcx, g.cf[0], ui.x - uj.x);
             const float dy = fmaf(-entry_dy(e), g.cf[1], ui.y - uj.y);
             const float dz = fmaf(-entry_dz(e), g.cf[2], ui.z - uj.z);
@@ -1218,6 +1227,7 @@ __device__ __forceinline__ void particle_force_list_group(const ForceArgs &a, in
     const Geom &g = a.b.sys[SINGLE ? 0 : (k >= 0 ? sys_p(a.b, k) : 0)];
     const float ncx = SINGLE ? a.lc.ncx : (float)g.nc[0];
     const float halfnc = SINGLE ? a.lc.halfnc : 0.5f * (float)g.nc[0];
+    const float inv_ncx = SINGLE ? a.lc.inv_ncx : 1.f / (float)g.nc[0];
     float4 ui = make_float4(0.f, 0.f, 0.f, 0.f);
     if (k >= 0) {
         ui = a.sp4[k];
@@ -1234,9 +1244,7 @@ __device__ __forceinline__ void particle_force_list_group(const ForceArgs &a, in
             int j = e & 0xffffff;
             float dyc = entry_dy(e);
             float dzc = entry_dz(e);
-            float dcx = ui.w - uj.w;
-            dcx -= dcx > halfnc ? ncx : 0.f;
-            dcx += dcx < -halfnc ? ncx : 0.f;
+            const float dcx = wrap_cells(ui.w - uj.w, ncx, inv_ncx);
             // coordinate differences first: exact for a close pair
             float dx = fmaf(dcx, cf0, ui.x - uj.x);
             float dy = fmaf(-dyc, cf1, ui.y - uj.y);
@@ -1754,6 +1762,7 @@ static void fill_args(dcm_handle *h, ForceArgs &a)
         }
         a.lc.ncx = (float)g0.nc[0];
         a.lc.halfnc = 0.5f * (float)g0.nc[0];
+        a.lc.inv_ncx = 1.f / (float)g0.nc[0];
         a.lc.sig2f = g0.sig2f;
         a.lc.eps48f = g0.eps48f;
         a.lc.eps24f = g0.eps24f;
