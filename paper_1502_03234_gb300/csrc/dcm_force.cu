@@ -1692,7 +1692,8 @@ int launch_forces(dcm_handle *h, bool energy)
     if (fp64 || !h->in_step) cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), h->stream);
     if (!fp64) {
         // DCM_MIXED: the warp walk, then the refinement of what it queued
-        if (!h->in_step) cudaMemsetAsync(a.refq_n, 0, sizeof(unsigned int), h->stream);
+        // (and no particle refined in place by a list kernel this time)
+        if (!h->in_step) cudaMemsetAsync(a.refq_n, 0, 2 * sizeof(unsigned int), h->stream);
         if (energy) {
             launch_walk<true, false>(h, a);
             launch_refine<true>(h, a);
